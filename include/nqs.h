@@ -1,0 +1,214 @@
+/*
+ * nqs.h -- C-ABI of the B300 (sm_103a) regularized-minSR step for
+ * autoregressive GRU wave functions (arXiv 2608.18065).
+ *
+ * One call of nqs_minsr_step performs one iteration of the paper's
+ * Algorithm 1 on one GPU: exact autoregressive sampling, local energies over
+ * every connected configuration, the per-sample log-derivative matrix O,
+ * centring, the real representation, T = O'^T O', the Tikhonov-regularized
+ * FP64 solve, delta theta = eta O' (T + lambda I)^{-1} eps', momentum and the
+ * parameter update.  The other entry points expose the stages one by one.
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" must point to CUDA device memory of the current
+ *    device; the caller owns all of them.  The library owns only its context
+ *    (host memory) and the small device tables it builds in nqs_create.
+ *  - Every call that takes a stream is asynchronous on that stream
+ *    (cudaStream_t passed as void*; NULL = legacy default stream).
+ *    Argument errors are detected on the host and returned at once; errors
+ *    found on the device (non-finite values, a non-positive Cholesky pivot)
+ *    are written to the status field of the device-side nqs_step_stats.
+ *  - Spins: sigma in {0,1} is the one-hot index, s^z = 1 - 2 sigma.  A
+ *    configuration is N = Lx*Ly bytes in the order of the zig-zag path
+ *    pi(k) of Sec. II.B (for 1D chains the site order).
+ *  - log Psi is stored as (re, im) doubles: re = 1/2 log P (Sec. II.A),
+ *    im = sum_k phi_k (softsign head, Sec. II.A) + pi (sigma_A mod 2) with the
+ *    Marshall sign of Sec. III.C on sublattice A = {(i,j): i+j odd}.
+ *  - theta is the FP64 master copy, flat, row-major blocks in this order
+ *    (App. A; hidden-state columns first, then one-hot input columns):
+ *      2D only:  U1[dh x dh], U2[dh x dh]
+ *      Wu[dh x (dh+din)], bu[dh], Wr[dh x (dh+din)], br[dh],
+ *      Wh[dh x dh], bh[dh], Win[dh x din], bin[dh], U[2 x dh], c[2],
+ *      complex head only: Uphi[2 x dh], cphi[2]
+ *    with din = 2 (1D) or 4 (2D: one-hots of the horizontal then vertical
+ *    neighbour).  The GRU is App. A literally: u, r = sigmoid(W[h';x] + b),
+ *    c = tanh(r * (Wh h' + bh) + Win x + bin), h = (1-u) h' + u c, with
+ *    h' = h_{k-1} (1D) or U1 h_hor + U2 h_ver (2D).
+ *  - Random numbers: u(s,k) = Philox4x32-10 (Salmon et al., SC'11) with
+ *    key = (lo32 seed, hi32 seed) and counter = (k, s, lo32 step, hi32 step);
+ *    u = ((out1 << 32 | out0) >> 11) * 2^-53; sigma_k = 0 iff u < p_k(0).
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NQS_OK = 0,
+  NQS_ERR_ARG = 1,          /* invalid argument (host-side check) */
+  NQS_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  NQS_ERR_UNSUPPORTED = 3,  /* model size not compiled into this library */
+  NQS_ERR_NONFINITE = 4,    /* device: non-finite E, eps or delta theta */
+  NQS_ERR_NOT_SPD = 5,      /* device: Cholesky pivot of T + lambda I <= 0 */
+  NQS_ERR_TIMEOUT = 6,      /* device: a bounded wait ran out */
+  NQS_ERR_WORKSPACE = 7     /* no workspace, or smaller than required */
+} nqs_status;
+
+typedef enum { NQS_PREC_FP64 = 0, NQS_PREC_MIXED = 1 } nqs_precision;
+
+typedef enum {
+  NQS_HAM_TFIM = 0,          /* -J sum Z_i Z_{i+1} - h sum X_i, open chain (Sec. III.A) */
+  NQS_HAM_CLUSTER_ZXZ = 1,   /* -sum_{i=2}^{N-1} Z_{i-1} X_i Z_{i+1}, open chain */
+  NQS_HAM_CLUSTER_PAPER = 2, /* Sec. III.B: XZX bulk + 3 boundary terms, E_0 = -N */
+  NQS_HAM_J1J2 = 3           /* Sec. III.C: J1/4 sum_<ij> s.s + J2/4 sum_<<ij>> s.s, open */
+} nqs_ham_family;
+
+typedef struct {
+  int dim;      /* 1 or 2 */
+  int Lx, Ly;   /* N = Lx*Ly; Ly = 1 for dim 1 */
+  int dh;       /* hidden size: 8, 16, 32 or 64 in this build */
+  int cplx;     /* 1: softsign phase head (cRNN), 0: positive (pRNN) */
+  int marshall; /* 1: Marshall sign (-1)^{sigma_A} (Sec. III.C) */
+  int zmask;    /* 1: zero-magnetisation mask during sampling (N even) */
+} nqs_model_desc;
+
+typedef struct {
+  int family;   /* nqs_ham_family */
+  double J, h;  /* TFIM couplings */
+  double J1, J2;/* J1-J2 couplings */
+} nqs_ham_desc;
+
+typedef struct {
+  double eta0;         /* base learning rate */
+  double decay_T;      /* eta_t = eta0 / (1 + t/decay_T); <= 0: no decay (Tab. I) */
+  double mu;           /* momentum (App. B) */
+  double lambda;       /* constant Tikhonov shift (lambda_mode 0) */
+  double lambda_coeff; /* lambda_mode 1: lambda = coeff * ||T||_F^pow (Sec. III.C) */
+  double lambda_pow;
+  int32_t lambda_mode; /* 0 constant, 1 norm power */
+  int32_t trust_region;/* 1: eta* = eta_t / ||tau||, tau = (I - lambda (T+lambda I)^-1) eps' (App. F) */
+  int64_t step_index;  /* t: Philox step counter and lr decay */
+  uint64_t seed;       /* Philox key */
+  int64_t n_samples;   /* Ns, <= the ctx's max_samples */
+} nqs_step_hparams;
+
+typedef struct {
+  double E_re, E_im;   /* E = mean eps (Eq. energy) */
+  double var;          /* mean |eps - E|^2 */
+  double vscore;       /* N var / E_re^2 (Eq. vscore, E_inf = 0) */
+  double lambda;       /* shift used */
+  double normT;        /* ||T||_F before the shift */
+  double eta_eff;      /* eta_t or eta* */
+  double tau_norm;     /* ||tau|| */
+  int32_t status;      /* nqs_status of the device-side checks */
+  int32_t pad;
+} nqs_step_stats;
+
+/* Optional device outputs of nqs_minsr_step_ex (any pointer may be NULL). */
+typedef struct {
+  uint8_t *spins;   /* [Ns*N] */
+  double *logpsi;   /* [Ns*2] */
+  double *eloc;     /* [Ns*2] (re, im) */
+  double *T;        /* [R*R] FP64, before the shift; R = Ns (pRNN) or 2Ns */
+  double *eps;      /* [R] eps-bar' */
+  double *x;        /* [R] (T + lambda I)^{-1} eps-bar' */
+  double *dtheta;   /* [Np] delta theta (eta_eff included) */
+} nqs_step_outputs;
+
+typedef struct nqs_ctx nqs_ctx;
+
+/* Create a context for one model, Hamiltonian and precision on the current
+ * device.  precision: NQS_PREC_FP64 runs every stage in FP64 (the plain GPU
+ * path); NQS_PREC_MIXED runs the recurrences and O in FP32, T and O'x as
+ * split BF16x3 tensor-core products with FP32 accumulation, and the
+ * centring, reductions and the regularized solve in FP64.  max_samples
+ * bounds Ns of every later call.  *out receives the context; release it with
+ * nqs_destroy.  Errors: NQS_ERR_ARG for an invalid description,
+ * NQS_ERR_UNSUPPORTED for a hidden size not built. */
+nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham,
+                      int precision, int64_t max_samples, nqs_ctx **out);
+
+/* Release the context (host memory and its device tables).  Synchronises
+ * the device first. */
+nqs_status nqs_destroy(nqs_ctx *ctx);
+
+/* Number of parameters Np of the model (layout above). */
+nqs_status nqs_param_count(const nqs_ctx *ctx, int64_t *n_params);
+
+/* Bytes of device workspace the context needs for up to max_samples. */
+nqs_status nqs_workspace_size(const nqs_ctx *ctx, size_t *bytes);
+
+/* Attach caller-owned device workspace (>= nqs_workspace_size bytes,
+ * 256-byte aligned).  The workspace must stay valid while calls that use it
+ * are in flight; calls on one context must not overlap on the device. */
+nqs_status nqs_set_workspace(nqs_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Exact autoregressive sampling (Sec. II.A, Algorithm 1 line 3).
+ * theta: device [Np] FP64.  Writes spins (device [ns*N] uint8) and logpsi
+ * (device [ns*2] FP64) using u(seed, step, s, k).  Also fills the context's
+ * hidden-state cache used by later stages of a step. */
+nqs_status nqs_sample(nqs_ctx *ctx, const double *theta, int64_t ns,
+                      uint64_t seed, uint64_t step, uint8_t *spins,
+                      double *logpsi, void *stream);
+
+/* log Psi of n given configurations (device spins [n*N]) -> device logpsi
+ * [n*2].  n <= max_samples. */
+nqs_status nqs_logpsi(nqs_ctx *ctx, const double *theta, const uint8_t *spins,
+                      int64_t n, double *logpsi, void *stream);
+
+/* Local energies eps(sigma) = sum_s' H_ss' Psi(s')/Psi(s) (Sec. II.C) of ns
+ * given configurations: device spins [ns*N] -> device eloc [ns*2] (re, im).
+ * Every connected s' is re-evaluated from the first site it differs at,
+ * starting from the cached hidden state of sigma. */
+nqs_status nqs_local_energy(nqs_ctx *ctx, const double *theta,
+                            const uint8_t *spins, int64_t ns, double *eloc,
+                            void *stream);
+
+/* Per-sample log-derivatives O[r][k] = d log Psi(sigma_s)/d theta_k
+ * (Sec. II.C), rows r = s for the real part and r = ns + s for the
+ * imaginary part (complex head only), without the 1/sqrt(Ns) factor.
+ * O: device [R*Np], FP64 for NQS_PREC_FP64, FP32 for NQS_PREC_MIXED. */
+nqs_status nqs_jacobian(nqs_ctx *ctx, const double *theta, const uint8_t *spins,
+                        int64_t ns, void *O, void *stream);
+
+/* T = A A^T (Algorithm 1 line 6) for a row-major A [R x np] of centred,
+ * scaled log-derivatives (rows = samples): FP64 A -> FP64 T on CUDA cores
+ * for the FP64 context; FP32 A -> FP64 T via BF16x3 tcgen05 products with
+ * FP32 accumulation for the mixed context.  T: device [R*R], both
+ * triangles written. */
+nqs_status nqs_gram(nqs_ctx *ctx, const void *A, int64_t R, int64_t np,
+                    double *T, void *stream);
+
+/* Solve (T + lambda I) x = b by FP64 Cholesky (Eq. minsrR).  T device
+ * [R*R] FP64 is overwritten by its factor; b, x device [R].  *dev_status
+ * (device int32) receives 0 or NQS_ERR_NOT_SPD. */
+nqs_status nqs_regularized_solve(nqs_ctx *ctx, double *T, int64_t R,
+                                 double lambda, const double *b, double *x,
+                                 int32_t *dev_status, void *stream);
+
+/* One minSR step (Algorithm 1 lines 3-9).  theta, momentum: device [Np]
+ * FP64, updated in place unless the device-side checks fail, in which case
+ * both are left unchanged.  dev_stats: device nqs_step_stats. */
+nqs_status nqs_minsr_step(nqs_ctx *ctx, double *theta, double *momentum,
+                          const nqs_step_hparams *hp, nqs_step_stats *dev_stats,
+                          void *stream);
+
+/* As nqs_minsr_step, also copying the step's intermediates to the non-NULL
+ * device pointers of out. */
+nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
+                             const nqs_step_hparams *hp,
+                             nqs_step_stats *dev_stats,
+                             const nqs_step_outputs *out, void *stream);
+
+/* Short text for a status code (static storage). */
+const char *nqs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

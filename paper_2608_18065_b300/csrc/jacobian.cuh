@@ -1,0 +1,513 @@
+// jacobian.cuh -- per-sample log-derivatives O = d log Psi / d theta.
+//
+// Stage 1 (k_jac_bwd): one reverse sweep per row (row = sample and adjoint
+// seed: d(1/2 log P) for the real rows, d(phi) for the imaginary rows of a
+// complex head) through the GRU of App. A.  The gate pre-activations of each
+// site are recomputed from the cached hidden states, the adjoint of h' is
+// one small GEMM [R x 3dh] x [3dh x dh] per site, and the per-site gate
+// adjoints are written out.
+// Stage 2 (k_jac_grad): the weight gradients of one row are sums over sites
+// of outer products (adjoint of a gate) x (its input), assembled into the
+// row of O in the flat parameter layout.
+#pragma once
+#include "recurrence.cuh"
+
+namespace nqs {
+
+template <typename T> struct BwdArgs {
+  const T *pack;
+  int N, Lx, cplx, zmask;
+  int64_t ns, nrows;        // nrows = ns (real head) or 2 ns (complex head)
+  int ntiles;
+  const uint8_t *spins;     // [ns][N]
+  const T *hcache;          // [ns][N][dh]
+  T *adj;                   // [nrows][N][adjw]
+  int adjw;
+  T *adjcol;                // 2D: [nrows][Lx][dh] pending vertical adjoints
+  int wg_in_smem;           // 1: backward weights staged in shared memory
+};
+
+// adjoint record of one site: dau | dar | dg | dac (4 dh) | dz0 dz1 dy0 dy1 |
+// 2D: dhp (dh) | hp (dh)
+template <int DH, int DIM> struct Adj {
+  static constexpr int W = 4 * DH + 4 + (DIM == 2 ? 2 * DH : 0);
+  static constexpr int DZ = 4 * DH, DHP = 4 * DH + 4, HP = 5 * DH + 4;
+};
+
+template <typename T, int DH, int DIM, int R>
+inline size_t bwd_smem_bytes(int N, bool wg_in_smem) {
+  constexpr int DIN = DIM == 2 ? 4 : 2;
+  size_t t = (size_t)DH * 3 * DH + (size_t)DIN * 3 * DH + (size_t)DH * 4 + 4 * DH + 8;
+  if (DIM == 2) t += 2 * (size_t)DH * DH;               // U12T
+  if (wg_in_smem) t += 3 * (size_t)DH * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);
+  t += (size_t)DH * R * (DIM == 2 ? 4 : 1) + 3 * (size_t)DH * R;  // shh shv shp sdp + sda
+  size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
+  return (b + 127) & ~size_t(127);
+}
+
+template <typename T, int DH, int DIM, int RT, int RG>
+__global__ void __launch_bounds__(Tile<DH>::UG * RG)
+k_jac_bwd(const BwdArgs<T> A) {
+  constexpr int UG = Tile<DH>::UG, UT = Tile<DH>::UT;
+  constexpr int R = RT * RG;
+  constexpr int NTH = UG * RG;
+  constexpr int DIN = DIM == 2 ? 4 : 2;
+  constexpr int C3 = 3 * DH;
+  using AJ = Adj<DH, DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sWgT = reinterpret_cast<T *>(smraw);
+  T *sxw = sWgT + DH * C3;
+  T *sbias = sxw + DIN * C3;
+  T *shead = sbias + DH * 4;
+  T *shc = shead + 4 * DH;
+  T *sU12T = shc + 8;
+  T *sp = sU12T + (DIM == 2 ? 2 * DH * DH : 0);
+  T *sWg = sp;
+  T *sU12 = sWg + (A.wg_in_smem ? C3 * DH : 0);
+  sp = sU12 + (A.wg_in_smem && DIM == 2 ? 2 * DH * DH : 0);
+  T *shh = sp;                               // h_{k-1} (1D) / h_hor (2D)
+  T *shv = shh + DH * R;                     // 2D: h_ver
+  T *shp = shv + (DIM == 2 ? DH * R : 0);    // 2D: h'
+  T *sdp = shp + (DIM == 2 ? DH * R : 0);    // 2D: adjoint of h'
+  T *sda = sdp + (DIM == 2 ? DH * R : 0);    // gate adjoints [3dh][R]
+  const int NP = (A.N + 15) & ~15;
+  uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * R);
+  int *srow = reinterpret_cast<int *>(ssp + R * NP);
+
+  const int tid = threadIdx.x;
+  const int ug = tid % UG, rg = tid / UG;
+  const int r0 = rg * RT, a0 = ug * UT;
+  const int N = A.N, Lx = A.Lx;
+  const int lane = tid & 31;
+
+  const T *p = A.pack;
+  auto al = [](int x) { return (x + 31) & ~31; };
+  const int oWgT = 0, oWg = al(oWgT + DH * C3), oxw = al(oWg + C3 * DH);
+  const int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
+  const int oU12T = al(ohc + 4), oU12 = al(oU12T + 2 * DH * DH);
+  for (int e = tid; e < DH * C3; e += NTH) sWgT[e] = p[oWgT + e];
+  for (int e = tid; e < DIN * C3; e += NTH) sxw[e] = p[oxw + e];
+  for (int e = tid; e < DH * 4; e += NTH) sbias[e] = p[obias + e];
+  for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
+  if (tid < 4) shc[tid] = p[ohc + tid];
+  if (DIM == 2)
+    for (int e = tid; e < 2 * DH * DH; e += NTH) sU12T[e] = p[oU12T + e];
+  if (A.wg_in_smem) {
+    for (int e = tid; e < C3 * DH; e += NTH) sWg[e] = p[oWg + e];
+    if (DIM == 2)
+      for (int e = tid; e < 2 * DH * DH; e += NTH) sU12[e] = p[oU12 + e];
+  }
+  const T *Wg = A.wg_in_smem ? sWg : p + oWg;
+  const T *U12 = A.wg_in_smem ? sU12 : p + oU12;
+
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    __syncthreads();
+    for (int r = tid; r < R; r += NTH) {
+      int64_t g = (int64_t)tile * R + r;
+      srow[r] = g < A.nrows ? (int)g : -1;
+    }
+    __syncthreads();
+    for (int e = tid; e < R * N; e += NTH) {
+      int r = e / N, k = e - r * N;
+      int g = srow[r];
+      ssp[r * NP + k] = g >= 0 ? A.spins[(g % A.ns) * (int64_t)N + k] : 0;
+    }
+    __syncthreads();
+    // per-row mask counters (lane ug == i): counts over [0, k] before site k
+    const int my_i = ug;
+    const int my_r = r0 + (my_i < RT ? my_i : 0);
+    int cnt_up = 0, cnt_dn = 0;
+    if (my_i < RT && A.zmask)
+      for (int k = 0; k < N; ++k) {
+        if (ssp[my_r * NP + k] == 0) ++cnt_up; else ++cnt_dn;
+      }
+    if (DIM == 2) {
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        int g = srow[r0 + i];
+        if (g < 0) continue;
+        for (int c = 0; c < Lx; ++c)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu)
+            A.adjcol[((int64_t)g * Lx + c) * DH + a0 + uu] = T(0);
+      }
+    }
+    T carry[RT][UT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+      for (int uu = 0; uu < UT; ++uu) carry[i][uu] = T(0);
+
+    for (int k = N - 1; k >= 0; --k) {
+      int hor_ok = k > 0, ver = -1, col = 0;
+      if (DIM == 2) {
+        int j = k / Lx, m = k - j * Lx;
+        col = (j & 1) ? (Lx - 1 - m) : m;
+        hor_ok = m != 0;
+        ver = (k >= Lx) ? k - 2 * m - 1 : -1;
+      }
+      // input states of site k
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        int r = r0 + i, g = srow[r];
+        int64_t s = g >= 0 ? g % A.ns : 0;
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) {
+          int a = a0 + uu;
+          shh[a * R + r] = (g >= 0 && hor_ok) ? A.hcache[(s * N + k - 1) * DH + a] : T(0);
+          if (DIM == 2)
+            shv[a * R + r] = (g >= 0 && ver >= 0) ? A.hcache[(s * N + ver) * DH + a] : T(0);
+        }
+      }
+      __syncthreads();
+      const T *Ag = shh;
+      if (DIM == 2) {
+        T acc1[RT][UT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) acc1[i][uu] = T(0);
+        if (hor_ok) mm_acc<T, RT, UT>(shh, R, r0, sU12T, DH, a0, DH, acc1);
+        if (ver >= 0) mm_acc<T, RT, UT>(shv, R, r0, sU12T + DH * DH, DH, a0, DH, acc1);
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) shp[(a0 + uu) * R + r0 + i] = acc1[i][uu];
+        __syncthreads();
+        Ag = shp;
+      }
+      T acc[RT][3 * UT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j2 = 0; j2 < 3 * UT; ++j2) acc[i][j2] = T(0);
+      if (DIM == 2 || k > 0) mm_acc<T, RT, 3 * UT>(Ag, R, r0, sWgT, C3, 3 * a0, DH, acc);
+
+      T dpd[RT][UT];  // (1-u) dh: the direct path of dh into h'
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int r = r0 + i, g = srow[r];
+        const int which = g >= 0 ? (int)(g / A.ns) : 0;
+        const int sk = ssp[r * NP + k];
+        int d0 = -1, d1 = -1;
+        if (DIM == 1) {
+          if (k > 0) d0 = ssp[r * NP + k - 1];
+        } else {
+          if (hor_ok) d0 = ssp[r * NP + k - 1];
+          if (ver >= 0) d1 = 2 + ssp[r * NP + ver];
+        }
+        T uv[UT], rv[UT], cv[UT], gv[UT], hv[UT], hpv[UT];
+        T z0 = T(0), z1 = T(0), y = T(0);
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) {
+          const int a = a0 + uu;
+          T au = acc[i][3 * uu + 0] + sbias[4 * a + 0];
+          T ar = acc[i][3 * uu + 1] + sbias[4 * a + 1];
+          T gg = acc[i][3 * uu + 2] + sbias[4 * a + 2];
+          T ai = sbias[4 * a + 3];
+          if (d0 >= 0) {
+            au += sxw[d0 * C3 + 3 * a + 0]; ar += sxw[d0 * C3 + 3 * a + 1];
+            ai += sxw[d0 * C3 + 3 * a + 2];
+          }
+          if (d1 >= 0) {
+            au += sxw[d1 * C3 + 3 * a + 0]; ar += sxw[d1 * C3 + 3 * a + 1];
+            ai += sxw[d1 * C3 + 3 * a + 2];
+          }
+          uv[uu] = sigm(au); rv[uu] = sigm(ar); gv[uu] = gg;
+          cv[uu] = tnh(rv[uu] * gg + ai);
+          hpv[uu] = (DIM == 2 || k > 0) ? Ag[a * R + r] : T(0);
+          hv[uu] = (T(1) - uv[uu]) * hpv[uu] + uv[uu] * cv[uu];
+          z0 += shead[a] * hv[uu];
+          z1 += shead[DH + a] * hv[uu];
+          if (A.cplx) y += shead[(2 + sk) * DH + a] * hv[uu];
+        }
+        z0 = group_sum<T, UG>(z0);
+        z1 = group_sum<T, UG>(z1);
+        if (A.cplx) y = group_sum<T, UG>(y);
+        // mask state of this row before site k, broadcast from lane ug == i
+        int forced_l = 0;
+        if (my_i == i) {
+          if (sk == 0) --cnt_up; else --cnt_dn;
+          forced_l = A.zmask && (cnt_up >= N / 2 || cnt_dn >= N / 2);
+        }
+        const int src = (lane & ~(UG - 1)) | i;
+        const int forced = __shfl_sync(0xffffffffu, forced_l, src, 32);
+        T dz0 = T(0), dz1 = T(0), dy = T(0);
+        if (which == 0) {
+          if (!forced) {
+            T lp0, lp1;
+            log_softmax2<T>(z0 + shc[0], z1 + shc[1], lp0, lp1);
+            dz0 = T(0.5) * ((sk == 0 ? T(1) : T(0)) - ex(lp0));
+            dz1 = T(0.5) * ((sk == 1 ? T(1) : T(0)) - ex(lp1));
+          }
+        } else {
+          T yy = y + shc[2 + sk];
+          T den = T(1) + (yy < T(0) ? -yy : yy);
+          dy = T(NQS_PI) / (den * den);
+        }
+        T *rec = A.adj + ((int64_t)(g >= 0 ? g : 0) * N + k) * A.adjw;
+        if (g >= 0 && ug == 0) {
+          rec[AJ::DZ + 0] = dz0; rec[AJ::DZ + 1] = dz1;
+          rec[AJ::DZ + 2] = sk == 0 ? dy : T(0);
+          rec[AJ::DZ + 3] = sk == 1 ? dy : T(0);
+        }
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) {
+          const int a = a0 + uu;
+          T dh = carry[i][uu] + shead[a] * dz0 + shead[DH + a] * dz1;
+          if (A.cplx) dh += shead[(2 + sk) * DH + a] * dy;
+          if (DIM == 2 && g >= 0) dh += A.adjcol[((int64_t)g * Lx + col) * DH + a];
+          const T dc = dh * uv[uu];
+          const T du = dh * (cv[uu] - hpv[uu]);
+          dpd[i][uu] = dh * (T(1) - uv[uu]);
+          const T dac = dc * (T(1) - cv[uu] * cv[uu]);
+          const T dr = dac * gv[uu];
+          const T dg = dac * rv[uu];
+          const T dar = dr * rv[uu] * (T(1) - rv[uu]);
+          const T dau = du * uv[uu] * (T(1) - uv[uu]);
+          sda[(3 * a + 0) * R + r] = dau;
+          sda[(3 * a + 1) * R + r] = dar;
+          sda[(3 * a + 2) * R + r] = dg;
+          if (g >= 0) {
+            rec[a] = dau; rec[DH + a] = dar; rec[2 * DH + a] = dg; rec[3 * DH + a] = dac;
+            if (DIM == 2) rec[AJ::HP + a] = hpv[uu];
+          }
+        }
+      }
+      __syncthreads();
+      T dh1[RT][UT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) dh1[i][uu] = dpd[i][uu];
+      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, R, r0, Wg, DH, a0, C3, dh1);
+      if (DIM == 1) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) carry[i][uu] = dh1[i][uu];
+      } else {
+        // d h' -> record, then route to the horizontal and vertical inputs
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          const int r = r0 + i, g = srow[r];
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) {
+            sdp[(a0 + uu) * R + r] = dh1[i][uu];
+            if (g >= 0) A.adj[((int64_t)g * N + k) * A.adjw + AJ::DHP + a0 + uu] = dh1[i][uu];
+          }
+        }
+        __syncthreads();
+        T dhh[RT][UT], dhv[RT][UT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) { dhh[i][uu] = T(0); dhv[i][uu] = T(0); }
+        mm_acc<T, RT, UT>(sdp, R, r0, U12, 2 * DH, a0, DH, dhh);
+        mm_acc<T, RT, UT>(sdp, R, r0, U12 + DH, 2 * DH, a0, DH, dhv);
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          const int g = srow[r0 + i];
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) {
+            carry[i][uu] = hor_ok ? dhh[i][uu] : T(0);
+            if (g >= 0)
+              A.adjcol[((int64_t)g * Lx + col) * DH + a0 + uu] = ver >= 0 ? dhv[i][uu] : T(0);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------ stage 2
+template <typename T, typename TO> struct GradArgs {
+  int N, Lx, cplx, dim;
+  int64_t ns, nrows;
+  const uint8_t *spins;
+  const T *hcache;
+  const T *adj;
+  int adjw;
+  TO *O;                    // [nrows][np]
+  int64_t np;
+  // layout offsets
+  int64_t U1, U2, Wu, bu, Wr, br, Wh, bh, Win, bin, Uo, co, Up, cp;
+};
+
+template <int DH> struct GTile {
+  static constexpr int TA = DH >= 16 ? DH / 16 : 1;       // tile edge per thread
+  static constexpr int GT = DH / TA;                       // threads per edge
+};
+
+template <typename T, typename TO, int DH, int DIM>
+__global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
+  constexpr int TA = GTile<DH>::TA, GT = GTile<DH>::GT;
+  constexpr int KC = (sizeof(T) == 8 && DH >= 64) ? 8 : 16;  // static smem <= 48 KB
+  constexpr int DIN = DIM == 2 ? 4 : 2;
+  constexpr int NB = DIM == 2 ? 5 : 3;  // big blocks: Wu_h Wr_h Wh (U1 U2)
+  using AJ = Adj<DH, DIM>;
+  const int row = blockIdx.x;
+  const int64_t s = row % A.ns;
+  const int N = A.N, Lx = A.Lx;
+  const int tid = threadIdx.x;
+  __shared__ T sadj[KC][AJ::W];
+  __shared__ T sQ[KC][DH];      // input state of the gates: h_{k-1} (1D) or h' (2D)
+  __shared__ T sH[KC][DH];      // h_k (heads)
+  __shared__ T sHh[DIM == 2 ? KC : 1][DH];  // 2D: h_hor
+  __shared__ T sHv[DIM == 2 ? KC : 1][DH];  // 2D: h_ver
+  __shared__ int sx[KC][2];     // active one-hot input columns of site k (-1: none)
+
+  const bool big = tid < GT * GT;
+  const int ta = (tid / GT) * TA, tb = (tid % GT) * TA;
+  T accB[NB][TA][TA];
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int j = 0; j < TA; ++j) accB[q][i][j] = T(0);
+  // small entries: heads (4 dh), x-columns (3 dh din), biases (4 dh + 4)
+  const int nsmall = 4 * DH + 3 * DH * DIN + 4 * DH + 4;
+  constexpr int SPT = (4 * DH + 3 * DH * DIN + 4 * DH + 4 + 255) / 256;
+  T accS[SPT];
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) accS[q] = T(0);
+
+  const T *adjrow = A.adj + (int64_t)row * N * A.adjw;
+  const T *hrow = A.hcache + s * N * DH;
+  const uint8_t *sprow = A.spins + s * N;
+  for (int k0 = 0; k0 < N; k0 += KC) {
+    const int kc = min(KC, N - k0);
+    __syncthreads();
+    for (int e = tid; e < kc * AJ::W; e += 256) {
+      int kk = e / AJ::W, w = e - kk * AJ::W;
+      sadj[kk][w] = adjrow[(int64_t)(k0 + kk) * A.adjw + w];
+    }
+    for (int e = tid; e < kc * DH; e += 256) {
+      int kk = e / DH, a = e - kk * DH, k = k0 + kk;
+      sH[kk][a] = hrow[(int64_t)k * DH + a];
+      if (DIM == 1) {
+        sQ[kk][a] = k > 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
+      } else {
+        int j = k / Lx, m = k - j * Lx;
+        int ver = k >= Lx ? k - 2 * m - 1 : -1;
+        sHh[kk][a] = m != 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
+        sHv[kk][a] = ver >= 0 ? hrow[(int64_t)ver * DH + a] : T(0);
+        sQ[kk][a] = adjrow[(int64_t)k * A.adjw + AJ::HP + a];
+      }
+    }
+    for (int kk = tid; kk < kc; kk += 256) {
+      int k = k0 + kk;
+      if (DIM == 1) {
+        sx[kk][0] = k > 0 ? sprow[k - 1] : -1;
+        sx[kk][1] = -1;
+      } else {
+        int j = k / Lx, m = k - j * Lx;
+        int ver = k >= Lx ? k - 2 * m - 1 : -1;
+        sx[kk][0] = m != 0 ? sprow[k - 1] : -1;
+        sx[kk][1] = ver >= 0 ? 2 + sprow[ver] : -1;
+      }
+    }
+    __syncthreads();
+    if (big) {
+      for (int kk = 0; kk < kc; ++kk) {
+        T q[TA];
+#pragma unroll
+        for (int j = 0; j < TA; ++j) q[j] = sQ[kk][tb + j];
+#pragma unroll
+        for (int i = 0; i < TA; ++i) {
+          const T pu = sadj[kk][ta + i], pr = sadj[kk][DH + ta + i], pg = sadj[kk][2 * DH + ta + i];
+#pragma unroll
+          for (int j = 0; j < TA; ++j) {
+            accB[0][i][j] = fma(pu, q[j], accB[0][i][j]);
+            accB[1][i][j] = fma(pr, q[j], accB[1][i][j]);
+            accB[2][i][j] = fma(pg, q[j], accB[2][i][j]);
+          }
+        }
+        if (DIM == 2) {
+#pragma unroll
+          for (int i = 0; i < TA; ++i) {
+            const T pd = sadj[kk][AJ::DHP + ta + i];
+#pragma unroll
+            for (int j = 0; j < TA; ++j) {
+              accB[NB - 2][i][j] = fma(pd, sHh[kk][tb + j], accB[NB - 2][i][j]);
+              accB[NB - 1][i][j] = fma(pd, sHv[kk][tb + j], accB[NB - 1][i][j]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      const int e = tid + 256 * q;
+      if (e >= nsmall) continue;
+      T v = accS[q];
+      if (e < 4 * DH) {  // heads: U (o<2) and Uphi (o>=2): sum_k dz/dy[k][o] h_k[b]
+        const int o = e / DH, b = e - o * DH;
+        for (int kk = 0; kk < kc; ++kk) v = fma(sadj[kk][AJ::DZ + o], sH[kk][b], v);
+      } else if (e < 4 * DH + 3 * DH * DIN) {  // x-columns of Wu, Wr, Win
+        const int e2 = e - 4 * DH;
+        const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;
+        const int a = rem / DIN, d = rem - a * DIN;
+        const int off = gsel == 0 ? 0 : (gsel == 1 ? DH : 3 * DH);  // dau, dar, dac
+        for (int kk = 0; kk < kc; ++kk)
+          if (sx[kk][0] == d || sx[kk][1] == d) v += sadj[kk][off + a];
+      } else {  // biases: bu br bh bin (sum of dau dar dg dac), then c, cphi
+        const int e2 = e - 4 * DH - 3 * DH * DIN;
+        if (e2 < 4 * DH) {
+          for (int kk = 0; kk < kc; ++kk) v += sadj[kk][e2];
+        } else {
+          for (int kk = 0; kk < kc; ++kk) v += sadj[kk][AJ::DZ + (e2 - 4 * DH)];
+        }
+      }
+      accS[q] = v;
+    }
+  }
+  // write the row of O
+  TO *Orow = A.O + (int64_t)row * A.np;
+  const int w = DH + DIN;
+  if (big) {
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int j = 0; j < TA; ++j) {
+        const int a = ta + i, b = tb + j;
+        Orow[A.Wu + (int64_t)a * w + b] = (TO)accB[0][i][j];
+        Orow[A.Wr + (int64_t)a * w + b] = (TO)accB[1][i][j];
+        Orow[A.Wh + (int64_t)a * DH + b] = (TO)accB[2][i][j];
+        if (DIM == 2) {
+          Orow[A.U1 + (int64_t)a * DH + b] = (TO)accB[NB - 2][i][j];
+          Orow[A.U2 + (int64_t)a * DH + b] = (TO)accB[NB - 1][i][j];
+        }
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) {
+    const int e = tid + 256 * q;
+    if (e >= nsmall) continue;
+    const TO v = (TO)accS[q];
+    if (e < 4 * DH) {
+      const int o = e / DH, b = e - o * DH;
+      if (o < 2) Orow[A.Uo + o * DH + b] = v;
+      else if (A.cplx) Orow[A.Up + (o - 2) * DH + b] = v;
+    } else if (e < 4 * DH + 3 * DH * DIN) {
+      const int e2 = e - 4 * DH;
+      const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;
+      const int a = rem / DIN, d = rem - a * DIN;
+      if (gsel == 0) Orow[A.Wu + (int64_t)a * w + DH + d] = v;
+      else if (gsel == 1) Orow[A.Wr + (int64_t)a * w + DH + d] = v;
+      else Orow[A.Win + (int64_t)a * DIN + d] = v;
+    } else {
+      const int e2 = e - 4 * DH - 3 * DH * DIN;
+      if (e2 < DH) Orow[A.bu + e2] = v;
+      else if (e2 < 2 * DH) Orow[A.br + e2 - DH] = v;
+      else if (e2 < 3 * DH) Orow[A.bh + e2 - 2 * DH] = v;
+      else if (e2 < 4 * DH) Orow[A.bin + e2 - 3 * DH] = v;
+      else if (e2 < 4 * DH + 2) Orow[A.co + e2 - 4 * DH] = v;
+      else if (A.cplx) Orow[A.cp + e2 - 4 * DH - 2] = v;
+    }
+  }
+}
+
+}  // namespace nqs

@@ -1,0 +1,578 @@
+// nqs_api.cu -- the C-ABI of libnqs (include/nqs.h): context, workspace
+// carving, Hamiltonian tables and the stream-ordered minSR step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gram_tc.h"
+#include "launch.h"
+#include "stages.cuh"
+
+using namespace nqs;
+
+namespace {
+
+struct WsOff {
+  size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, total;
+};
+
+}  // namespace
+
+struct nqs_ctx {
+  nqs_model_desc m;
+  nqs_ham_desc h;
+  int prec;  // nqs_precision
+  int64_t max_ns;
+  Layout L;
+  PackOff P;
+  RecDesc rd;
+  int n_off = 0, n_diag = 0;
+  OffOp *d_off = nullptr;
+  DiagOp *d_diag = nullptr;
+  int *d_opf = nullptr;
+  int eloc_grid = 0, eloc_R = 0;
+  int adjw = 0;
+  size_t es = 8;  // element size of the recurrence precision
+  WsOff off{};
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  int nsplit = 1;
+};
+
+namespace {
+
+inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool f32(const nqs_ctx *c) { return c->prec == NQS_PREC_MIXED; }
+
+// Off-diagonal and diagonal operator tables of the Hamiltonian families
+// (Sec. III), sites in path order.
+void build_hamiltonian(const nqs_model_desc &m, const nqs_ham_desc &h, std::vector<OffOp> &off,
+                       std::vector<DiagOp> &dg) {
+  const int N = m.Lx * m.Ly;
+  auto col = [&](int k) {
+    int j = k / m.Lx, r = k % m.Lx;
+    return (j % 2 == 0) ? r : m.Lx - 1 - r;
+  };
+  auto onA = [&](int k) { return ((col(k) + k / m.Lx) % 2) == 1; };
+  auto flip_op = [&](int kind, int f1, int f2, int z1, int z2, double coeff) {
+    OffOp o{};
+    o.kind = kind; o.f1 = f1; o.f2 = f2; o.z1 = z1; o.z2 = z2;
+    o.start = f2 >= 0 ? std::min(f1, f2) : f1;
+    double s = 1.0;
+    if (m.marshall) {
+      if (onA(f1)) s = -s;
+      if (f2 >= 0 && onA(f2)) s = -s;
+    }
+    o.coeff = coeff * s;
+    off.push_back(o);
+  };
+  switch (h.family) {
+    case NQS_HAM_TFIM:
+      for (int i = 0; i + 1 < N; ++i) dg.push_back(DiagOp{i, i + 1, -h.J});
+      for (int i = 0; i < N; ++i) flip_op(1, i, -1, -1, -1, -h.h);
+      break;
+    case NQS_HAM_CLUSTER_ZXZ:
+      for (int i = 1; i + 1 < N; ++i) flip_op(1, i, -1, i - 1, i + 1, -1.0);
+      break;
+    case NQS_HAM_CLUSTER_PAPER:
+      // 1-indexed k = 2..N-2: X_{k-1} Z_k X_{k+1} -> 0-indexed (k-2, k-1, k)
+      for (int k = 2; k <= N - 2; ++k) flip_op(1, k - 2, k, k - 1, -1, -1.0);
+      flip_op(1, 1, -1, 0, -1, -1.0);           // Z_1 X_2
+      flip_op(1, N - 2, N - 1, -1, -1, -1.0);   // X_{N-1} X_N
+      flip_op(1, N - 3, -1, N - 2, N - 1, -1.0);// X_{N-2} Z_{N-1} Z_N
+      break;
+    case NQS_HAM_J1J2: {
+      std::vector<int> idx((size_t)m.Lx * m.Ly);
+      for (int k = 0; k < N; ++k) idx[(size_t)(k / m.Lx) * m.Lx + col(k)] = k;
+      auto at = [&](int i, int j) {
+        return (i < 0 || i >= m.Lx || j < 0 || j >= m.Ly) ? -1 : idx[(size_t)j * m.Lx + i];
+      };
+      for (int j = 0; j < m.Ly; ++j)
+        for (int i = 0; i < m.Lx; ++i) {
+          const int k = at(i, j);
+          const int nb[4] = {at(i + 1, j), at(i, j + 1), at(i + 1, j + 1), at(i + 1, j - 1)};
+          const double J[4] = {h.J1, h.J1, h.J2, h.J2};
+          for (int q = 0; q < 4; ++q) {
+            if (nb[q] < 0 || J[q] == 0.0) continue;
+            dg.push_back(DiagOp{k, nb[q], J[q] / 4.0});
+            flip_op(2, k, nb[q], -1, -1, J[q] / 2.0);
+          }
+        }
+      break;
+    }
+  }
+  std::stable_sort(off.begin(), off.end(),
+                   [](const OffOp &a, const OffOp &b) { return a.start < b.start; });
+}
+
+nqs_status cu(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
+#define CU(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return NQS_ERR_CUDA; } while (0)
+#define ST(x) do { nqs_status _s = (x); if (_s != NQS_OK) return _s; } while (0)
+
+void carve(nqs_ctx *c) {
+  const int64_t ns = c->max_ns, N = c->L.N, dh = c->L.dh, np = c->L.np;
+  const int64_t R = c->L.cplx ? 2 * ns : ns;
+  const size_t es = c->es;
+  WsOff &o = c->off;
+  size_t p = 0;
+  auto take = [&](size_t bytes) { size_t at = p; p = al256(p + bytes); return at; };
+  o.pack = take(c->P.total * es);
+  o.spins = take(ns * N);
+  o.logpsi = take(ns * 2 * 8);
+  o.hcache = take(ns * N * dh * es);
+  o.lccache = take(ns * N * 2 * es);
+  o.eloc = take(ns * 2 * 8);
+  o.item_s = take((size_t)c->n_off * ns * 4);
+  o.item_e = take((size_t)c->n_off * ns * 8);
+  o.item_cnt = take((size_t)c->n_off * 4);
+  o.contrib = take((size_t)c->n_off * ns * 16);
+  o.colbuf = take(c->L.dim == 2 ? (size_t)c->eloc_grid * c->eloc_R * c->L.Lx * dh * es : 0);
+  o.adj = take(R * N * c->adjw * es);
+  o.adjcol = take(c->L.dim == 2 ? R * c->L.Lx * dh * es : 0);
+  o.O = take(R * np * es);
+  o.mean = take(2 * np * 8);
+  o.T = take(R * R * 8);
+  o.eps = take(R * 8);
+  o.x = take(R * 8);
+  c->nsplit = (int)((R + 63) / 64);
+  o.part = take((size_t)c->nsplit * np * 8);
+  o.dth = take(np * 8);
+  o.frob = take(1024 * 8);
+  o.sstat = take(64);
+  o.split = take(gram_tc_split_bytes(R, np));
+  o.total = p;
+}
+
+template <typename T> T *W(nqs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
+
+nqs_status need_ws(nqs_ctx *c) { return c->ws ? NQS_OK : NQS_ERR_WORKSPACE; }
+
+template <typename T> nqs_status pack_theta(nqs_ctx *c, const double *theta, cudaStream_t st) {
+  const int64_t tot = c->P.total;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
+  k_pack<T><<<blocks, 256, 0, st>>>(theta, W<T>(c, c->off.pack), c->L, c->P);
+  return cu(cudaGetLastError());
+}
+
+template <typename T>
+FwdArgs<T> fwd_args(nqs_ctx *c) {
+  FwdArgs<T> a{};
+  a.pack = W<T>(c, c->off.pack);
+  a.N = c->L.N; a.Lx = c->L.Lx; a.cplx = c->L.cplx; a.marshall = c->L.marshall; a.zmask = c->L.zmask;
+  a.hcache = W<T>(c, c->off.hcache);
+  a.lccache = W<T>(c, c->off.lccache);
+  return a;
+}
+
+template <typename T>
+nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t step, uint8_t *spins,
+                     double *logpsi, cudaStream_t st) {
+  FwdArgs<T> a = fwd_args<T>(c);
+  a.nrows = n; a.seed = seed; a.step = step; a.spins = spins; a.logpsi = logpsi;
+  return cu(run_forward<T>(c->rd, mode, a, 0, st));
+}
+
+nqs_status forward(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t step, uint8_t *spins,
+                   double *logpsi, cudaStream_t st) {
+  return f32(c) ? forward_T<float>(c, mode, n, seed, step, spins, logpsi, st)
+                : forward_T<double>(c, mode, n, seed, step, spins, logpsi, st);
+}
+
+template <typename T> nqs_status pack(nqs_ctx *c, const double *theta, cudaStream_t st) {
+  return pack_theta<T>(c, theta, st);
+}
+nqs_status pack_any(nqs_ctx *c, const double *theta, cudaStream_t st) {
+  return f32(c) ? pack<float>(c, theta, st) : pack<double>(c, theta, st);
+}
+
+// Local energies of the ns configurations whose hidden states are cached.
+template <typename T>
+nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cudaStream_t st) {
+  if (c->n_off > 0) {
+    k_eloc_gen<<<c->n_off, 256, 0, st>>>(c->d_off, spins, c->L.N, ns, W<int>(c, c->off.item_s),
+                                         W<double>(c, c->off.item_e), W<int>(c, c->off.item_cnt),
+                                         W<double>(c, c->off.contrib));
+    CU(cudaGetLastError());
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = ns;
+    a.spins = const_cast<uint8_t *>(spins);
+    a.tiles_per_op = (int)((ns + c->eloc_R - 1) / c->eloc_R);
+    a.ntiles = a.tiles_per_op * c->n_off;
+    a.op_f = c->d_opf;
+    a.item_s = W<int>(c, c->off.item_s);
+    a.item_e = W<double>(c, c->off.item_e);
+    a.item_cnt = W<int>(c, c->off.item_cnt);
+    a.contrib = W<double>(c, c->off.contrib);
+    a.colbuf = W<T>(c, c->off.colbuf);
+    CU(run_forward<T>(c->rd, MODE_ELOC, a, c->eloc_grid, st));
+  }
+  k_eloc_reduce<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(
+      c->d_diag, c->n_diag, c->n_off, spins, c->L.N, ns, W<double>(c, c->off.contrib), eloc);
+  return cu(cudaGetLastError());
+}
+
+nqs_status eloc_any(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cudaStream_t st) {
+  return f32(c) ? eloc_T<float>(c, ns, spins, eloc, st) : eloc_T<double>(c, ns, spins, eloc, st);
+}
+
+// Jacobian rows of the ns cached configurations into O (precision T).
+template <typename T>
+nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_t st) {
+  const int64_t R = c->L.cplx ? 2 * ns : ns;
+  BwdArgs<T> b{};
+  b.pack = W<T>(c, c->off.pack);
+  b.N = c->L.N; b.Lx = c->L.Lx; b.cplx = c->L.cplx; b.zmask = c->L.zmask;
+  b.ns = ns; b.nrows = R;
+  b.spins = spins;
+  b.hcache = W<T>(c, c->off.hcache);
+  b.adj = W<T>(c, c->off.adj);
+  b.adjw = c->adjw;
+  b.adjcol = W<T>(c, c->off.adjcol);
+  CU(run_bwd<T>(c->rd, b, st));
+  GradArgs<T, T> g{};
+  g.N = c->L.N; g.Lx = c->L.Lx; g.cplx = c->L.cplx; g.dim = c->L.dim;
+  g.ns = ns; g.nrows = R; g.spins = spins; g.hcache = b.hcache; g.adj = b.adj; g.adjw = c->adjw;
+  g.O = O; g.np = c->L.np;
+  g.U1 = c->L.U1; g.U2 = c->L.U2; g.Wu = c->L.Wu; g.bu = c->L.bu; g.Wr = c->L.Wr; g.br = c->L.br;
+  g.Wh = c->L.Wh; g.bh = c->L.bh; g.Win = c->L.Win; g.bin = c->L.bin; g.Uo = c->L.Uo;
+  g.co = c->L.co; g.Up = c->L.Up; g.cp = c->L.cp;
+  return cu(run_grad<T>(c->rd, g, st));
+}
+
+// T = A A^T in FP64 (see nqs_gram).
+nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T, cudaStream_t st) {
+  if (f32(c)) {
+    if (gram_tc_available())
+      return cu(gram_tc_bf16x3(reinterpret_cast<const float *>(A), R, np, T,
+                               c->ws + c->off.split, st));
+    dim3 g((unsigned)((R + 63) / 64), (unsigned)((R + 63) / 64));
+    k_gram_simt<float, float><<<g, 256, 0, st>>>(reinterpret_cast<const float *>(A), R, np, T);
+  } else {
+    dim3 g((unsigned)((R + 63) / 64), (unsigned)((R + 63) / 64));
+    k_gram_simt<double, double><<<g, 256, 0, st>>>(reinterpret_cast<const double *>(A), R, np, T);
+  }
+  return cu(cudaGetLastError());
+}
+
+__global__ void k_shift(double *T, int64_t R, double lam) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < R) T[i * R + i] += lam;
+}
+
+__global__ void k_frob_part(const double *__restrict__ T, int64_t n2, double *part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc += T[e] * T[e];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_lambda_finish(double *T, int64_t R, const double *part, int nparts, int mode,
+                                double lam_c, double coeff, double pw, nqs_step_stats *st) {
+  __shared__ double lam_s;
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < nparts; ++i) acc += part[i];
+    const double nT = sqrt(acc);
+    const double lam = mode == 1 ? coeff * pow(nT, pw) : lam_c;
+    st->normT = nT;
+    st->lambda = lam;
+    lam_s = lam;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < R; i += blockDim.x) T[i * R + i] += lam_s;
+}
+
+// Cholesky of the shifted T in place, then x = (T + lambda I)^{-1} b.
+nqs_status chol_solve(double *T, int64_t R, const double *b, double *x, int32_t *status,
+                      cudaStream_t st) {
+  const int np_ = (int)((R + CB - 1) / CB);
+  for (int p = 0; p < np_; ++p) {
+    const int rows = np_ - p;
+    k_chol_panel<<<rows, 256, 0, st>>>(T, R, p, status);
+    CU(cudaGetLastError());
+    const int64_t trail = R - (int64_t)(p + 1) * CB;
+    if (trail > 0) {
+      const unsigned t = (unsigned)((trail + 63) / 64);
+      k_chol_update<<<dim3(t, t), 256, 0, st>>>(T, R, p, status);
+      CU(cudaGetLastError());
+    }
+  }
+  const size_t smem = (size_t)R * 8;
+  if (smem > 48 * 1024)
+    CU(cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_chol_solve<<<1, 1024, smem, st>>>(T, R, b, x, status);
+  return cu(cudaGetLastError());
+}
+
+template <typename T>
+nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
+                  nqs_step_stats *stats, const nqs_step_outputs *out, cudaStream_t st) {
+  const int64_t ns = hp->n_samples, N = c->L.N, np = c->L.np;
+  const int64_t R = c->L.cplx ? 2 * ns : ns;
+  uint8_t *spins = W<uint8_t>(c, c->off.spins);
+  double *logpsi = W<double>(c, c->off.logpsi);
+  double *eloc = W<double>(c, c->off.eloc);
+  T *O = W<T>(c, c->off.O);
+  double *Tm = W<double>(c, c->off.T);
+  double *eps = W<double>(c, c->off.eps);
+  double *x = W<double>(c, c->off.x);
+  int32_t *sstat = W<int32_t>(c, c->off.sstat);
+  CU(cudaMemsetAsync(sstat, 0, 64, st));
+  // line 3: sample (also fills the hidden-state caches)
+  ST(pack_theta<T>(c, theta, st));
+  ST(forward_T<T>(c, MODE_SAMPLE, ns, hp->seed, (uint64_t)hp->step_index, spins, logpsi, st));
+  // line 4: local energies, E, variance; eps-bar'
+  ST(eloc_T<T>(c, ns, spins, eloc, st));
+  k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
+  CU(cudaGetLastError());
+  // line 5: O, centred over samples per block, / sqrt(Ns)
+  ST(jac_T<T>(c, ns, spins, O, st));
+  {
+    dim3 g((unsigned)((np + 255) / 256), c->L.cplx ? 2u : 1u);
+    k_colmean<T><<<g, 256, 0, st>>>(O, ns, np, W<double>(c, c->off.mean));
+    CU(cudaGetLastError());
+    const int64_t tot = R * np;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+    k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
+    CU(cudaGetLastError());
+  }
+  // line 6: T = O'^T O'
+  ST(gram_any(c, O, R, np, Tm, st));
+  if (out && out->T) CU(cudaMemcpyAsync(out->T, Tm, R * R * 8, cudaMemcpyDeviceToDevice, st));
+  // lambda and shift
+  {
+    const int nparts = 256;
+    k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
+    k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts, hp->lambda_mode,
+                                        hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats);
+    CU(cudaGetLastError());
+  }
+  // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
+  ST(chol_solve(Tm, R, eps, x, sstat, st));
+  double eta_t = hp->eta0;
+  if (hp->decay_T > 0.0 && std::isfinite(hp->decay_T))
+    eta_t = hp->eta0 / (1.0 + (double)hp->step_index / hp->decay_T);
+  k_eta<<<1, 1024, 0, st>>>(eps, x, R, eta_t, hp->trust_region, stats, sstat);
+  CU(cudaGetLastError());
+  {
+    const int rows_per = 64;
+    const int nparts = (int)((R + rows_per - 1) / rows_per);
+    dim3 g((unsigned)((np + 255) / 256), (unsigned)nparts);
+    k_gemv_part<T><<<g, 256, 0, st>>>(O, R, np, x, rows_per, W<double>(c, c->off.part));
+    k_dtheta<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts, np,
+                                                          stats, W<double>(c, c->off.dth));
+    // lines 8-9: momentum and update (skipped unless status is OK)
+    k_apply<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(theta, mom, W<double>(c, c->off.dth),
+                                                         np, hp->mu, stats);
+    CU(cudaGetLastError());
+  }
+  if (out) {
+    if (out->spins) CU(cudaMemcpyAsync(out->spins, spins, ns * N, cudaMemcpyDeviceToDevice, st));
+    if (out->logpsi) CU(cudaMemcpyAsync(out->logpsi, logpsi, ns * 16, cudaMemcpyDeviceToDevice, st));
+    if (out->eloc) CU(cudaMemcpyAsync(out->eloc, eloc, ns * 16, cudaMemcpyDeviceToDevice, st));
+    if (out->eps) CU(cudaMemcpyAsync(out->eps, eps, R * 8, cudaMemcpyDeviceToDevice, st));
+    if (out->x) CU(cudaMemcpyAsync(out->x, x, R * 8, cudaMemcpyDeviceToDevice, st));
+    if (out->dtheta)
+      CU(cudaMemcpyAsync(out->dtheta, W<double>(c, c->off.dth), np * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  return NQS_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int precision,
+                      int64_t max_samples, nqs_ctx **out) {
+  if (!model || !ham || !out || max_samples <= 0) return NQS_ERR_ARG;
+  *out = nullptr;
+  const nqs_model_desc &m = *model;
+  if (m.dim != 1 && m.dim != 2) return NQS_ERR_ARG;
+  if (m.Lx <= 0 || m.Ly <= 0 || (m.dim == 1 && m.Ly != 1)) return NQS_ERR_ARG;
+  const int N = m.Lx * m.Ly;
+  if (N < 2 || N > 4096) return NQS_ERR_ARG;
+  if (m.zmask && (N % 2)) return NQS_ERR_ARG;
+  if (precision != NQS_PREC_FP64 && precision != NQS_PREC_MIXED) return NQS_ERR_ARG;
+  if (ham->family < NQS_HAM_TFIM || ham->family > NQS_HAM_J1J2) return NQS_ERR_ARG;
+  if ((ham->family == NQS_HAM_J1J2) != (m.dim == 2)) return NQS_ERR_ARG;
+  if (ham->family == NQS_HAM_CLUSTER_PAPER && N < 4) return NQS_ERR_ARG;
+  if (!dh_supported(m.dh)) return NQS_ERR_UNSUPPORTED;
+  nqs_ctx *c = new (std::nothrow) nqs_ctx();
+  if (!c) return NQS_ERR_ARG;
+  c->m = m; c->h = *ham; c->prec = precision; c->max_ns = max_samples;
+  c->L = make_layout(m);
+  c->P = pack_offsets(c->L);
+  c->es = precision == NQS_PREC_MIXED ? 4 : 8;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return NQS_ERR_CUDA;
+  }
+  c->rd = RecDesc{m.dim, m.dh, N, m.Lx, m.cplx, m.marshall, m.zmask, sms};
+  c->adjw = 4 * m.dh + 4 + (m.dim == 2 ? 2 * m.dh : 0);
+  c->eloc_R = eloc_rows(c->rd, precision == NQS_PREC_MIXED);
+  c->eloc_grid = precision == NQS_PREC_MIXED ? eloc_max_grid<float>(c->rd) : eloc_max_grid<double>(c->rd);
+  if (c->eloc_grid <= 0) { delete c; return NQS_ERR_CUDA; }
+  std::vector<OffOp> off;
+  std::vector<DiagOp> dg;
+  build_hamiltonian(m, *ham, off, dg);
+  c->n_off = (int)off.size();
+  c->n_diag = (int)dg.size();
+  std::vector<int> opf(4 * std::max<size_t>(off.size(), 1));
+  for (size_t i = 0; i < off.size(); ++i) {
+    opf[4 * i] = off[i].f1; opf[4 * i + 1] = off[i].f2; opf[4 * i + 2] = off[i].start; opf[4 * i + 3] = 0;
+  }
+  bool ok = cudaMalloc(&c->d_off, sizeof(OffOp) * std::max<size_t>(off.size(), 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_diag, sizeof(DiagOp) * std::max<size_t>(dg.size(), 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_opf, sizeof(int) * opf.size()) == cudaSuccess;
+  if (ok && !off.empty())
+    ok = cudaMemcpy(c->d_off, off.data(), sizeof(OffOp) * off.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok && !dg.empty())
+    ok = cudaMemcpy(c->d_diag, dg.data(), sizeof(DiagOp) * dg.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) ok = cudaMemcpy(c->d_opf, opf.data(), sizeof(int) * opf.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) { nqs_destroy(c); return NQS_ERR_CUDA; }
+  carve(c);
+  *out = c;
+  return NQS_OK;
+}
+
+nqs_status nqs_destroy(nqs_ctx *c) {
+  if (!c) return NQS_ERR_ARG;
+  cudaDeviceSynchronize();
+  if (c->d_off) cudaFree(c->d_off);
+  if (c->d_diag) cudaFree(c->d_diag);
+  if (c->d_opf) cudaFree(c->d_opf);
+  delete c;
+  return NQS_OK;
+}
+
+nqs_status nqs_param_count(const nqs_ctx *c, int64_t *n) {
+  if (!c || !n) return NQS_ERR_ARG;
+  *n = c->L.np;
+  return NQS_OK;
+}
+
+nqs_status nqs_workspace_size(const nqs_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return NQS_ERR_ARG;
+  *bytes = c->off.total;
+  return NQS_OK;
+}
+
+nqs_status nqs_set_workspace(nqs_ctx *c, void *p, size_t bytes) {
+  if (!c || !p) return NQS_ERR_ARG;
+  if (bytes < c->off.total) return NQS_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(p) % 256) return NQS_ERR_ARG;
+  c->ws = static_cast<char *>(p);
+  c->ws_bytes = bytes;
+  return NQS_OK;
+}
+
+nqs_status nqs_sample(nqs_ctx *c, const double *theta, int64_t ns, uint64_t seed, uint64_t step,
+                      uint8_t *spins, double *logpsi, void *stream) {
+  if (!c || !theta || !spins || !logpsi || ns <= 0 || ns > c->max_ns) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ST(pack_any(c, theta, st));
+  return forward(c, MODE_SAMPLE, ns, seed, step, spins, logpsi, st);
+}
+
+nqs_status nqs_logpsi(nqs_ctx *c, const double *theta, const uint8_t *spins, int64_t n,
+                      double *logpsi, void *stream) {
+  if (!c || !theta || !spins || !logpsi || n <= 0 || n > c->max_ns) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ST(pack_any(c, theta, st));
+  return forward(c, MODE_GIVEN, n, 0, 0, const_cast<uint8_t *>(spins), logpsi, st);
+}
+
+nqs_status nqs_local_energy(nqs_ctx *c, const double *theta, const uint8_t *spins, int64_t ns,
+                            double *eloc, void *stream) {
+  if (!c || !theta || !spins || !eloc || ns <= 0 || ns > c->max_ns) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ST(pack_any(c, theta, st));
+  ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st));
+  return eloc_any(c, ns, spins, eloc, st);
+}
+
+nqs_status nqs_jacobian(nqs_ctx *c, const double *theta, const uint8_t *spins, int64_t ns, void *O,
+                        void *stream) {
+  if (!c || !theta || !spins || !O || ns <= 0 || ns > c->max_ns) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ST(pack_any(c, theta, st));
+  ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st));
+  return f32(c) ? jac_T<float>(c, ns, spins, static_cast<float *>(O), st)
+                : jac_T<double>(c, ns, spins, static_cast<double *>(O), st);
+}
+
+nqs_status nqs_gram(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T, void *stream) {
+  if (!c || !A || !T || R <= 0 || np <= 0) return NQS_ERR_ARG;
+  const int64_t Rmax = c->L.cplx ? 2 * c->max_ns : c->max_ns;
+  if (f32(c) && (R > Rmax || np > c->L.np)) return NQS_ERR_ARG;  // split buffer sized for these
+  ST(need_ws(c));
+  return gram_any(c, A, R, np, T, static_cast<cudaStream_t>(stream));
+}
+
+nqs_status nqs_regularized_solve(nqs_ctx *c, double *T, int64_t R, double lambda, const double *b,
+                                 double *x, int32_t *dev_status, void *stream) {
+  if (!c || !T || !b || !x || !dev_status || R <= 0 || !(lambda >= 0.0)) return NQS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), st));
+  if (lambda != 0.0) {
+    k_shift<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(T, R, lambda);
+    CU(cudaGetLastError());
+  }
+  return chol_solve(T, R, b, x, dev_status, st);
+}
+
+nqs_status nqs_minsr_step_ex(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
+                             nqs_step_stats *stats, const nqs_step_outputs *out, void *stream) {
+  if (!c || !theta || !mom || !hp || !stats) return NQS_ERR_ARG;
+  if (hp->n_samples < 2 || hp->n_samples > c->max_ns) return NQS_ERR_ARG;
+  if (hp->lambda_mode != 0 && hp->lambda_mode != 1) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? step_T<float>(c, theta, mom, hp, stats, out, st)
+                : step_T<double>(c, theta, mom, hp, stats, out, st);
+}
+
+nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
+                          nqs_step_stats *stats, void *stream) {
+  return nqs_minsr_step_ex(c, theta, mom, hp, stats, nullptr, stream);
+}
+
+const char *nqs_status_string(int s) {
+  switch (s) {
+    case NQS_OK: return "ok";
+    case NQS_ERR_ARG: return "invalid argument";
+    case NQS_ERR_CUDA: return "CUDA runtime error";
+    case NQS_ERR_UNSUPPORTED: return "hidden size not built into this library";
+    case NQS_ERR_NONFINITE: return "non-finite energy or update";
+    case NQS_ERR_NOT_SPD: return "T + lambda I not positive definite";
+    case NQS_ERR_TIMEOUT: return "bounded device wait ran out";
+    case NQS_ERR_WORKSPACE: return "workspace missing or too small";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"
+
+namespace nqs {
+bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32 || dh == 64; }
+}  // namespace nqs

@@ -1,0 +1,111 @@
+// recur_impl.cuh -- host launchers of the templated recurrence kernels,
+// dispatching the runtime hidden size and lattice dimension onto the
+// compile-time instantiations.
+#pragma once
+#include "launch.h"
+
+namespace nqs {
+
+#define NQS_DISPATCH_DH(dh, ...)                          \
+  switch (dh) {                                           \
+    case 8: { constexpr int DH = 8; __VA_ARGS__; } break;    \
+    case 16: { constexpr int DH = 16; __VA_ARGS__; } break;  \
+    case 32: { constexpr int DH = 32; __VA_ARGS__; } break;  \
+    case 64: { constexpr int DH = 64; __VA_ARGS__; } break;  \
+    default: return cudaErrorInvalidValue;                \
+  }
+
+template <typename T, int DH, int DIM, int RT, int RG, int MODE>
+static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStream_t st) {
+  constexpr int R = RT * RG;
+  auto kern = k_forward<T, DH, DIM, RT, RG, MODE>;
+  const size_t smem = fwd_smem_bytes<T, DH, DIM, R>(d.N);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (MODE != MODE_ELOC) a.ntiles = (int)((a.nrows + R - 1) / R);
+  int grid = a.ntiles;
+  if (MODE == MODE_ELOC) grid = grid < max_grid ? grid : max_grid;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, Tile<DH>::UG * RG, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int DH, int DIM>
+static cudaError_t fwd_dim(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, cudaStream_t st) {
+  constexpr int ERT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
+  if (mode == MODE_SAMPLE)
+    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_SAMPLE>(d, a, max_grid, st);
+  if (mode == MODE_GIVEN)
+    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_GIVEN>(d, a, max_grid, st);
+  return fwd_one<T, DH, DIM, ERT, Rows<T>::ELOC_RG, MODE_ELOC>(d, a, max_grid, st);
+}
+
+template <typename T>
+cudaError_t run_forward(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, cudaStream_t st) {
+  NQS_DISPATCH_DH(d.dh, {
+    if (d.dim == 1) return fwd_dim<T, DH, 1>(d, mode, a, max_grid, st);
+    return fwd_dim<T, DH, 2>(d, mode, a, max_grid, st);
+  });
+  return cudaSuccess;
+}
+
+template <typename T, int DH, int DIM>
+static int eloc_grid_dim(const RecDesc &d) {
+  constexpr int RT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
+  constexpr int RG = Rows<T>::ELOC_RG;
+  auto kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC>;
+  const size_t smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, Tile<DH>::UG * RG, smem) != cudaSuccess)
+    return 0;
+  return per * d.sm_count;
+}
+
+template <typename T> int eloc_max_grid(const RecDesc &d) {
+  switch (d.dh) {
+    case 8: return d.dim == 1 ? eloc_grid_dim<T, 8, 1>(d) : eloc_grid_dim<T, 8, 2>(d);
+    case 16: return d.dim == 1 ? eloc_grid_dim<T, 16, 1>(d) : eloc_grid_dim<T, 16, 2>(d);
+    case 32: return d.dim == 1 ? eloc_grid_dim<T, 32, 1>(d) : eloc_grid_dim<T, 32, 2>(d);
+    case 64: return d.dim == 1 ? eloc_grid_dim<T, 64, 1>(d) : eloc_grid_dim<T, 64, 2>(d);
+  }
+  return 0;
+}
+
+template <typename T, int DH, int DIM>
+static cudaError_t bwd_dim(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
+  constexpr int RT = Rows<T>::BWD_RT, RG = Rows<T>::BWD_RG, R = RT * RG;
+  auto kern = k_jac_bwd<T, DH, DIM, RT, RG>;
+  size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, true);
+  a.wg_in_smem = 1;
+  if (smem > 200 * 1024) {
+    smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+    a.wg_in_smem = 0;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  a.ntiles = (int)((a.nrows + R - 1) / R);
+  if (a.ntiles <= 0) return cudaSuccess;
+  kern<<<a.ntiles, Tile<DH>::UG * RG, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t run_bwd(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
+  NQS_DISPATCH_DH(d.dh, {
+    if (d.dim == 1) return bwd_dim<T, DH, 1>(d, a, st);
+    return bwd_dim<T, DH, 2>(d, a, st);
+  });
+  return cudaSuccess;
+}
+
+template <typename T> cudaError_t run_grad(const RecDesc &d, GradArgs<T, T> a, cudaStream_t st) {
+  if (a.nrows <= 0) return cudaSuccess;
+  NQS_DISPATCH_DH(d.dh, {
+    if (d.dim == 1) k_jac_grad<T, T, DH, 1><<<(unsigned)a.nrows, 256, 0, st>>>(a);
+    else k_jac_grad<T, T, DH, 2><<<(unsigned)a.nrows, 256, 0, st>>>(a);
+  });
+  return cudaGetLastError();
+}
+
+}  // namespace nqs

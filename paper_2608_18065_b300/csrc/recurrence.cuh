@@ -1,0 +1,358 @@
+// recurrence.cuh -- fused GRU recurrences of libnqs (sm_103a).
+//
+// One CTA advances a tile of R rows (configurations) through the sites of
+// the zig-zag path together.  Per site the gate pre-activations of all rows
+// are one small GEMM [R x dh] x [dh x 3dh] (App. A) with the packed weights
+// resident in shared memory; each thread owns RT rows x UT hidden units of
+// all three gates, so the gate non-linearities, the state update and the
+// partial output-head dot products stay in registers.  The heads are reduced
+// over the 16 unit-group lanes with warp shuffles; the log-softmax, the
+// zero-magnetisation mask and the Philox draw of each row run on one lane.
+#pragma once
+#include "common.cuh"
+
+namespace nqs {
+
+template <int DH> struct Tile {
+  static constexpr int UG = DH >= 16 ? 16 : DH;  // unit groups (lanes)
+  static constexpr int UT = DH / UG;             // hidden units per thread
+};
+
+// acc[i][j] += sum_k At[k*lda + r0 + i] * B[k*ldb + c0 + j]
+template <typename T, int RT, int CT>
+__device__ __forceinline__ void mm_acc(const T *__restrict__ At, int lda, int r0,
+                                       const T *__restrict__ B, int ldb, int c0,
+                                       int K, T (&acc)[RT][CT]) {
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    T a[RT], b[CT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) a[i] = At[k * lda + r0 + i];
+#pragma unroll
+    for (int j = 0; j < CT; ++j) b[j] = B[k * ldb + c0 + j];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+      for (int j = 0; j < CT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
+template <typename T, int UG>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = UG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Zig-zag path helpers (Sec. II.B): column i of path index k, and the path
+// index of the vertical neighbour (i, j-1) = k - 2m - 1 with m = k mod Lx.
+__device__ __forceinline__ int path_col(int k, int Lx) {
+  int j = k / Lx, m = k - j * Lx;
+  return (j & 1) ? (Lx - 1 - m) : m;
+}
+__device__ __forceinline__ bool on_sublattice_A(int k, int Lx) {
+  return ((path_col(k, Lx) + k / Lx) & 1) != 0;
+}
+
+enum { MODE_SAMPLE = 0, MODE_GIVEN = 1, MODE_ELOC = 2 };
+
+template <typename T> struct FwdArgs {
+  const T *pack;           // packed weights (PackOff layout)
+  int N, Lx, cplx, marshall, zmask;
+  int64_t nrows;           // SAMPLE/GIVEN: rows; ELOC: Ns
+  int ntiles;
+  // SAMPLE
+  uint64_t seed, step;
+  // SAMPLE/GIVEN/ELOC spins: SAMPLE writes, others read
+  uint8_t *spins;
+  double *logpsi;          // [rows*2]
+  T *hcache;               // [rows][N][dh]  (SAMPLE/GIVEN write, ELOC read)
+  T *lccache;              // [rows][N][2]
+  // ELOC
+  int tiles_per_op;
+  const int *op_f;         // [n_off*4]: f1, f2, start, pad
+  const int *item_s;       // [n_off*Ns]
+  const double *item_e;    // [n_off*Ns]
+  const int *item_cnt;     // [n_off]
+  double *contrib;         // [n_off*Ns*2]
+  T *colbuf;               // 2D ELOC: [gridDim][R][Lx][dh]
+};
+
+// Shared-memory footprint of k_forward.
+template <typename T, int DH, int DIM, int R>
+inline size_t fwd_smem_bytes(int N) {
+  constexpr int DIN = DIM == 2 ? 4 : 2;
+  size_t t = (size_t)DH * 3 * DH + (size_t)DIN * 3 * DH + (size_t)DH * 4 + 4 * DH + 8;
+  if (DIM == 2) t += 2 * (size_t)DH * DH;
+  t += (size_t)(DIM == 2 ? 4 : 2) * DH * R;
+  size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
+  return (b + 127) & ~size_t(127);
+}
+
+template <typename T, int DH, int DIM, int RT, int RG, int MODE>
+__global__ void __launch_bounds__(Tile<DH>::UG * RG)
+k_forward(const FwdArgs<T> A) {
+  constexpr int UG = Tile<DH>::UG, UT = Tile<DH>::UT;
+  constexpr int R = RT * RG;
+  constexpr int NTH = UG * RG;
+  constexpr int DIN = DIM == 2 ? 4 : 2;
+  constexpr int C3 = 3 * DH;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sWgT = reinterpret_cast<T *>(smraw);
+  T *sxw = sWgT + DH * C3;
+  T *sbias = sxw + DIN * C3;
+  T *shead = sbias + DH * 4;
+  T *shc = shead + 4 * DH;
+  T *sU12T = shc + 8;
+  T *sh0 = sU12T + (DIM == 2 ? 2 * DH * DH : 0);
+  T *sh1 = sh0 + DH * R;
+  T *shv = sh1 + DH * R;                    // 2D: vertical neighbour states
+  T *shp = shv + (DIM == 2 ? DH * R : 0);   // 2D: h'
+  const int NP = (A.N + 15) & ~15;
+  uint8_t *ssp = reinterpret_cast<uint8_t *>(shp + (DIM == 2 ? DH * R : 0));
+  int *srow = reinterpret_cast<int *>(ssp + R * NP);  // sample id or -1
+
+  const int tid = threadIdx.x;
+  const int ug = tid % UG, rg = tid / UG;
+  const int r0 = rg * RT, a0 = ug * UT;
+  const int N = A.N, Lx = A.Lx;
+
+  // stage the packed weights once per CTA
+  {
+    const T *p = A.pack;
+    // offsets follow pack_offsets(): recomputed here for the compile-time dh
+    auto al = [](int x) { return (x + 31) & ~31; };
+    int oWgT = 0, oWg = al(oWgT + DH * C3), oxw = al(oWg + C3 * DH);
+    int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
+    int oU12T = al(ohc + 4);
+    for (int e = tid; e < DH * C3; e += NTH) sWgT[e] = p[oWgT + e];
+    for (int e = tid; e < DIN * C3; e += NTH) sxw[e] = p[oxw + e];
+    for (int e = tid; e < DH * 4; e += NTH) sbias[e] = p[obias + e];
+    for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
+    if (tid < 4) shc[tid] = p[ohc + tid];
+    if (DIM == 2)
+      for (int e = tid; e < 2 * DH * DH; e += NTH) sU12T[e] = p[oU12T + e];
+  }
+
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    // ------------------------------------------------------- tile setup
+    int kstart = 0, op = 0, f1 = -1, f2 = -1, base = 0, cnt = 0;
+    if (MODE == MODE_ELOC) {
+      op = tile / A.tiles_per_op;
+      base = (tile - op * A.tiles_per_op) * R;
+      cnt = A.item_cnt[op];
+      if (base >= cnt) continue;  // uniform over the CTA
+      f1 = A.op_f[4 * op + 0];
+      f2 = A.op_f[4 * op + 1];
+      kstart = A.op_f[4 * op + 2];
+    }
+    __syncthreads();  // previous tile finished with smem
+    for (int r = tid; r < R; r += NTH) {
+      int s = -1;
+      if (MODE == MODE_ELOC) {
+        if (base + r < cnt) s = A.item_s[(int64_t)op * A.nrows + base + r];
+      } else {
+        int64_t g = (int64_t)tile * R + r;
+        if (g < A.nrows) s = (int)g;
+      }
+      srow[r] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < R * N; e += NTH) {
+      int r = e / N, k = e - r * N;
+      int s = srow[r];
+      uint8_t v = 0;
+      if (MODE != MODE_SAMPLE && s >= 0) {
+        v = A.spins[(int64_t)s * N + k];
+        if (MODE == MODE_ELOC && (k == f1 || k == f2)) v ^= 1;
+      }
+      ssp[r * NP + k] = v;
+    }
+    // initial state h_{kstart-1} (zero at the chain start)
+    for (int e = tid; e < R * DH; e += NTH) {
+      int r = e / DH, a = e - r * DH;
+      int s = srow[r];
+      T v = T(0);
+      if (MODE == MODE_ELOC && kstart > 0 && s >= 0)
+        v = A.hcache[((int64_t)s * N + (kstart - 1)) * DH + a];
+      sh0[a * R + r] = v;
+    }
+    __syncthreads();
+
+    // per-row scalar state lives on lane ug == i of each row group
+    double acc_re = 0.0, acc_im = 0.0;
+    int n_up = 0, n_dn = 0, nA = 0;
+    const int my_i = ug;  // row handled by this lane (if ug < RT)
+    const int my_r = r0 + (my_i < RT ? my_i : 0);
+    const int my_s = my_i < RT ? srow[my_r] : -1;
+    if (MODE == MODE_ELOC && my_s >= 0) {
+      for (int k = 0; k < kstart; ++k) {
+        if (ssp[my_r * NP + k] == 0) ++n_up; else ++n_dn;
+      }
+    }
+
+    T *hcur = sh0, *hnxt = sh1;
+    for (int k = kstart; k < N; ++k) {
+      const T *Ag = hcur;  // A operand of the gate GEMM: h_{k-1} or h'
+      int hor_ok = k > 0, ver = -1, col = 0;
+      if (DIM == 2) {
+        int j = k / Lx, m = k - j * Lx;
+        col = (j & 1) ? (Lx - 1 - m) : m;
+        hor_ok = m != 0;
+        ver = (k >= Lx) ? k - 2 * m - 1 : -1;
+        // vertical neighbour states into shv[a][r]
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          int r = r0 + i, s = srow[r];
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) {
+            int a = a0 + uu;
+            T v = T(0);
+            if (ver >= 0 && s >= 0) {
+              if (MODE == MODE_ELOC && ver >= kstart)
+                v = A.colbuf[(((int64_t)blockIdx.x * R + r) * Lx + col) * DH + a];
+              else
+                v = A.hcache[((int64_t)s * N + ver) * DH + a];
+            }
+            shv[a * R + r] = v;
+          }
+        }
+        __syncthreads();
+        T acc1[RT][UT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int j2 = 0; j2 < UT; ++j2) acc1[i][j2] = T(0);
+        if (hor_ok) mm_acc<T, RT, UT>(hcur, R, r0, sU12T, DH, a0, DH, acc1);
+        if (ver >= 0) mm_acc<T, RT, UT>(shv, R, r0, sU12T + DH * DH, DH, a0, DH, acc1);
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu) shp[(a0 + uu) * R + r0 + i] = acc1[i][uu];
+        __syncthreads();
+        Ag = shp;
+      }
+      T acc[RT][3 * UT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j2 = 0; j2 < 3 * UT; ++j2) acc[i][j2] = T(0);
+      if (DIM == 2 || k > 0) mm_acc<T, RT, 3 * UT>(Ag, R, r0, sWgT, C3, 3 * a0, DH, acc);
+
+      // epilogue: GRU cell (App. A), partial heads, then the row's head on
+      // lane ug == i (log-softmax, mask, draw, accumulate)
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int r = r0 + i;
+        const int s = srow[r];
+        int d0 = -1, d1 = -1;
+        if (DIM == 1) {
+          if (k > 0) d0 = ssp[r * NP + k - 1];
+        } else {
+          if (hor_ok) d0 = ssp[r * NP + k - 1];
+          if (ver >= 0) d1 = 2 + ssp[r * NP + ver];
+        }
+        T z0 = T(0), z1 = T(0), z2 = T(0), z3 = T(0);
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) {
+          const int a = a0 + uu;
+          T au = acc[i][3 * uu + 0] + sbias[4 * a + 0];
+          T ar = acc[i][3 * uu + 1] + sbias[4 * a + 1];
+          T gg = acc[i][3 * uu + 2] + sbias[4 * a + 2];
+          T ai = sbias[4 * a + 3];
+          if (d0 >= 0) {
+            au += sxw[d0 * C3 + 3 * a + 0];
+            ar += sxw[d0 * C3 + 3 * a + 1];
+            ai += sxw[d0 * C3 + 3 * a + 2];
+          }
+          if (d1 >= 0) {
+            au += sxw[d1 * C3 + 3 * a + 0];
+            ar += sxw[d1 * C3 + 3 * a + 1];
+            ai += sxw[d1 * C3 + 3 * a + 2];
+          }
+          const T u = sigm(au), rr = sigm(ar);
+          const T c = tnh(rr * gg + ai);
+          const T hp = (DIM == 2 || k > 0) ? Ag[a * R + r] : T(0);
+          const T hn = (T(1) - u) * hp + u * c;
+          hnxt[a * R + r] = hn;
+          if (s >= 0) {
+            if (MODE != MODE_ELOC && A.hcache)
+              A.hcache[((int64_t)s * N + k) * DH + a] = hn;
+            if (DIM == 2 && MODE == MODE_ELOC)
+              A.colbuf[(((int64_t)blockIdx.x * R + r) * Lx + col) * DH + a] = hn;
+          }
+          z0 += shead[0 * DH + a] * hn;
+          z1 += shead[1 * DH + a] * hn;
+          if (A.cplx) {
+            z2 += shead[2 * DH + a] * hn;
+            z3 += shead[3 * DH + a] * hn;
+          }
+        }
+        z0 = group_sum<T, UG>(z0);
+        z1 = group_sum<T, UG>(z1);
+        if (A.cplx) {
+          z2 = group_sum<T, UG>(z2);
+          z3 = group_sum<T, UG>(z3);
+        }
+        if (i != my_i || my_s < 0) continue;
+        T lp0, lp1;
+        log_softmax2<T>(z0 + shc[0], z1 + shc[1], lp0, lp1);
+        int forced = -1;  // value forced by the mask, or -1
+        if (A.zmask) {
+          if (n_up >= N / 2) forced = 1;
+          else if (n_dn >= N / 2) forced = 0;
+        }
+        int sg;
+        if (MODE == MODE_SAMPLE) {
+          double p0 = forced == 0 ? 1.0 : (forced == 1 ? 0.0 : (double)ex(lp0));
+          double uu = uniform53(A.seed, A.step, (uint32_t)my_s, (uint32_t)k);
+          sg = uu < p0 ? 0 : 1;
+          ssp[r * NP + k] = (uint8_t)sg;
+          A.spins[(int64_t)my_s * N + k] = (uint8_t)sg;
+        } else {
+          sg = ssp[r * NP + k];
+        }
+        double lps;
+        if (forced >= 0) lps = (sg == forced) ? 0.0 : -INFINITY;
+        else lps = (double)(sg == 0 ? lp0 : lp1);
+        double ph = 0.0;
+        if (A.cplx) {
+          T y = (sg == 0 ? z2 : z3) + shc[2 + sg];
+          ph = NQS_PI * (double)softsign(y);
+        }
+        if (MODE == MODE_ELOC) {
+          const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+          acc_re += 0.5 * lps - (double)lc[0];
+          acc_im += ph - (double)lc[1];
+        } else {
+          acc_re += 0.5 * lps;
+          acc_im += ph;
+          if (A.lccache) {
+            T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+            lc[0] = (T)(0.5 * lps);
+            lc[1] = (T)ph;
+          }
+        }
+        if (sg == 0) ++n_up; else ++n_dn;
+        if (A.marshall && sg == 1 && on_sublattice_A(k, Lx)) ++nA;
+      }
+      __syncthreads();
+      T *t = hcur; hcur = hnxt; hnxt = t;
+    }
+    // row outputs
+    if (my_i < RT && my_s >= 0) {
+      if (MODE == MODE_ELOC) {
+        double e = A.item_e[(int64_t)op * A.nrows + base + my_i + r0];
+        double mag = exp(acc_re);
+        double* c = A.contrib + ((int64_t)op * A.nrows + my_s) * 2;
+        c[0] = e * mag * cos(acc_im);
+        c[1] = e * mag * sin(acc_im);
+      } else {
+        A.logpsi[2 * (int64_t)my_s] = acc_re;
+        A.logpsi[2 * (int64_t)my_s + 1] = acc_im + (A.marshall ? NQS_PI * (double)(nA & 1) : 0.0);
+      }
+    }
+  }
+}
+
+}  // namespace nqs

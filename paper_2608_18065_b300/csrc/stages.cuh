@@ -1,0 +1,487 @@
+// stages.cuh -- the non-recurrent stages of one minSR step (sm_103a):
+// parameter packing, connected-configuration lists and local-energy
+// reduction (Sec. II.C), FP64 energy statistics (Eq. energy, Eq. vscore),
+// centring and real representation (Algorithm 1 lines 5-6), the FP64
+// blocked Cholesky solve (Eq. minsrR) and the update with momentum (App. B).
+#pragma once
+#include "common.cuh"
+
+namespace nqs {
+
+// ----------------------------------------------------------- packing
+template <typename T>
+__global__ void k_pack(const double *__restrict__ th, T *__restrict__ pk, Layout L, PackOff P) {
+  const int dh = L.dh, din = L.din, w = dh + din;
+  const int64_t tot = P.total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (e >= P.WgT && e < P.WgT + (int64_t)dh * 3 * dh) {
+      int64_t q = e - P.WgT; int k = q / (3 * dh), n = q % (3 * dh), a = n / 3, g = n % 3;
+      int64_t base = g == 0 ? L.Wu : (g == 1 ? L.Wr : L.Wh);
+      v = th[base + (int64_t)a * (g == 2 ? dh : w) + k];
+    } else if (e >= P.Wg && e < P.Wg + (int64_t)3 * dh * dh) {
+      int64_t q = e - P.Wg; int n = q / dh, b = q % dh, a = n / 3, g = n % 3;
+      int64_t base = g == 0 ? L.Wu : (g == 1 ? L.Wr : L.Wh);
+      v = th[base + (int64_t)a * (g == 2 ? dh : w) + b];
+    } else if (e >= P.xw && e < P.xw + (int64_t)din * 3 * dh) {
+      int64_t q = e - P.xw; int d = q / (3 * dh), n = q % (3 * dh), a = n / 3, g = n % 3;
+      v = g == 0 ? th[L.Wu + (int64_t)a * w + dh + d]
+        : (g == 1 ? th[L.Wr + (int64_t)a * w + dh + d] : th[L.Win + (int64_t)a * din + d]);
+    } else if (e >= P.bias && e < P.bias + (int64_t)dh * 4) {
+      int64_t q = e - P.bias; int a = q / 4, g = q % 4;
+      v = th[(g == 0 ? L.bu : g == 1 ? L.br : g == 2 ? L.bh : L.bin) + a];
+    } else if (e >= P.head && e < P.head + 4 * dh) {
+      int64_t q = e - P.head; int o = q / dh, b = q % dh;
+      v = o < 2 ? th[L.Uo + o * dh + b] : (L.cplx ? th[L.Up + (o - 2) * dh + b] : 0.0);
+    } else if (e >= P.hc && e < P.hc + 4) {
+      int o = e - P.hc;
+      v = o < 2 ? th[L.co + o] : (L.cplx ? th[L.cp + o - 2] : 0.0);
+    } else if (L.dim == 2 && e >= P.U12T && e < P.U12T + (int64_t)2 * dh * dh) {
+      int64_t q = e - P.U12T; int k = q / dh, a = q % dh;
+      v = k < dh ? th[L.U1 + (int64_t)a * dh + k] : th[L.U2 + (int64_t)a * dh + (k - dh)];
+    } else if (L.dim == 2 && e >= P.U12 && e < P.U12 + (int64_t)2 * dh * dh) {
+      int64_t q = e - P.U12; int a = q / (2 * dh), b = q % (2 * dh);
+      v = b < dh ? th[L.U1 + (int64_t)a * dh + b] : th[L.U2 + (int64_t)a * dh + (b - dh)];
+    }
+    pk[e] = (T)v;
+  }
+}
+
+// ----------------------------------------------- Hamiltonian op tables
+// Off-diagonal operator o: kind 1 = flip f1 (and f2 >= 0) with element
+// coeff * z(z1) * z(z2); kind 2 = exchange of f1, f2 if antiparallel with
+// element coeff.  sign carries the Marshall factor (-1)^{#flips on A}.
+struct OffOp {
+  int kind, f1, f2, z1, z2, start, pad0, pad1;
+  double coeff;
+};
+struct DiagOp {
+  int z1, z2;
+  double coeff;
+};
+
+__device__ __forceinline__ double zval(const uint8_t *sp, int k) {
+  return k < 0 ? 1.0 : (sp[k] ? -1.0 : 1.0);
+}
+
+// One CTA per off-diagonal operator: list the samples it connects
+// (compacted, ascending), their matrix elements, and zero its slots of the
+// per-(operator, sample) contribution matrix.
+__global__ void k_eloc_gen(const OffOp *__restrict__ ops, const uint8_t *__restrict__ spins,
+                           int N, int64_t ns, int *item_s, double *item_e, int *item_cnt,
+                           double *contrib) {
+  const int o = blockIdx.x;
+  const OffOp op = ops[o];
+  __shared__ int warp_tot[32];
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t s0 = 0; s0 < ns; s0 += blockDim.x) {
+    const int64_t s = s0 + threadIdx.x;
+    int conn = 0;
+    double el = 0.0;
+    if (s < ns) {
+      const uint8_t *sp = spins + s * N;
+      if (op.kind == 1) {
+        conn = 1;
+        el = op.coeff * zval(sp, op.z1) * zval(sp, op.z2);
+      } else {
+        conn = sp[op.f1] != sp[op.f2];
+        el = op.coeff;
+      }
+      double *c = contrib + ((int64_t)o * ns + s) * 2;
+      c[0] = 0.0; c[1] = 0.0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, conn);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      if (w2 < wid) off += warp_tot[w2];
+      tot += warp_tot[w2];
+    }
+    if (conn) {
+      const int pos = running + off + before;
+      item_s[(int64_t)o * ns + pos] = (int)s;
+      item_e[(int64_t)o * ns + pos] = el;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) running += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) item_cnt[o] = running;
+}
+
+// eps_s = sum of diagonal elements + sum over operators of the connected
+// contributions (already H_ss' Psi(s')/Psi(s)).
+__global__ void k_eloc_reduce(const DiagOp *__restrict__ dops, int n_diag, int n_off,
+                              const uint8_t *__restrict__ spins, int N, int64_t ns,
+                              const double *__restrict__ contrib, double *eloc) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const uint8_t *sp = spins + s * N;
+  double re = 0.0, im = 0.0;
+  for (int d = 0; d < n_diag; ++d) re += dops[d].coeff * zval(sp, dops[d].z1) * zval(sp, dops[d].z2);
+  for (int o = 0; o < n_off; ++o) {
+    const double *c = contrib + ((int64_t)o * ns + s) * 2;
+    re += c[0];
+    im += c[1];
+  }
+  eloc[2 * s] = re;
+  eloc[2 * s + 1] = im;
+}
+
+// ------------------------------------------------------ energy stats
+// One CTA: E = mean eps, var = mean |eps - E|^2, V-score; then
+// eps-bar' = 2 (Re, -Im)(eps - E)^* / sqrt(Ns) = 2 (Re(eps-E), Im(eps-E)) / sqrt(Ns).
+__global__ void k_energy(const double *__restrict__ eloc, int64_t ns, int N, int cplx,
+                         nqs_step_stats *st, double *eps) {
+  __shared__ double sr[1024], si[1024];
+  double r = 0.0, i = 0.0;
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) { r += eloc[2 * s]; i += eloc[2 * s + 1]; }
+  sr[threadIdx.x] = r; si[threadIdx.x] = i;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { sr[threadIdx.x] += sr[threadIdx.x + o]; si[threadIdx.x] += si[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  const double Er = sr[0] / (double)ns, Ei = si[0] / (double)ns;
+  __syncthreads();
+  double v = 0.0;
+  const double isq = 1.0 / sqrt((double)ns);
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+    const double a = eloc[2 * s] - Er, b = eloc[2 * s + 1] - Ei;
+    v += a * a + b * b;
+    eps[s] = 2.0 * a * isq;
+    if (cplx) eps[ns + s] = 2.0 * b * isq;
+  }
+  sr[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sr[threadIdx.x] += sr[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double var = sr[0] / (double)ns;
+    st->E_re = Er; st->E_im = Ei; st->var = var;
+    st->vscore = (double)N * var / (Er * Er);
+    int bad = !(isfinite(Er) && isfinite(Ei) && isfinite(var));
+    st->status = bad ? NQS_ERR_NONFINITE : NQS_OK;
+  }
+}
+
+// ---------------------------------------------------------- centring
+// Column means over the Ns samples of each block (real rows, imaginary
+// rows), accumulated in FP64.  grid.x over column chunks, grid.y = block.
+template <typename T>
+__global__ void k_colmean(const T *__restrict__ O, int64_t ns, int64_t np, double *mean) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const T *B = O + (int64_t)blockIdx.y * ns * np;
+  double acc = 0.0;
+  for (int64_t s = 0; s < ns; ++s) acc += (double)B[s * np + p];
+  mean[(int64_t)blockIdx.y * np + p] = acc / (double)ns;
+}
+
+// O' = (O - mean) / sqrt(Ns), in FP64 arithmetic, stored back in T.
+template <typename T>
+__global__ void k_center(T *__restrict__ O, int64_t ns, int64_t np, int64_t rows,
+                         const double *__restrict__ mean) {
+  const double isq = 1.0 / sqrt((double)ns);
+  const int64_t tot = rows * np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / np, p = e - r * np;
+    const double m = mean[(r / ns) * np + p];
+    O[e] = (T)(((double)O[e] - m) * isq);
+  }
+}
+
+// ------------------------------------------------------------- Gram
+// T = A A^T on CUDA cores, 64x64 output tiles of the upper triangle, K in
+// chunks of 16 through shared memory; accumulation in TA (double for the
+// FP64 path); both triangles written.
+template <typename TI, typename TA>
+__global__ void __launch_bounds__(256) k_gram_simt(const TI *__restrict__ A, int64_t R, int64_t np,
+                                                   double *__restrict__ T) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj < bi) return;
+  __shared__ TA sa[16][64 + 1], sb[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  TA acc[4][4] = {};
+  const int64_t i0 = (int64_t)bi * 64, j0 = (int64_t)bj * 64;
+  for (int64_t k0 = 0; k0 < np; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int r = e / 16, kk = e % 16;
+      const int64_t k = k0 + kk;
+      sa[kk][r] = (i0 + r < R && k < np) ? (TA)A[(i0 + r) * np + k] : TA(0);
+      sb[kk][r] = (j0 + r < R && k < np) ? (TA)A[(j0 + r) * np + k] : TA(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      TA a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = sa[kk][ty + 16 * q]; b[q] = sb[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + ty + 16 * p, j = j0 + tx + 16 * q;
+      if (i < R && j < R && j >= i) {
+        T[i * R + j] = (double)acc[p][q];
+        T[j * R + i] = (double)acc[p][q];
+      }
+    }
+}
+
+// ||T||_F, lambda (constant or coeff*||T||^pow), and the diagonal shift.
+__global__ void k_lambda(double *T, int64_t R, int mode, double lam_c, double coeff, double pw,
+                         nqs_step_stats *st) {
+  __shared__ double s[1024];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < R * R; e += blockDim.x) acc += T[e] * T[e];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double nT = sqrt(s[0]);
+  const double lam = mode == 1 ? coeff * pow(nT, pw) : lam_c;
+  for (int64_t i = threadIdx.x; i < R; i += blockDim.x) T[i * R + i] += lam;
+  if (threadIdx.x == 0) { st->normT = nT; st->lambda = lam; }
+}
+
+// ------------------------------------------------------ FP64 Cholesky
+// Right-looking blocked Cholesky of the lower triangle, panel width 32.
+// k_chol_panel: CTA b (row block p + b) factors the diagonal block in
+// shared memory (every CTA redundantly) and writes L_pp (b = 0) or the
+// panel block L_ip = A_ip L_pp^{-T} (b > 0).
+constexpr int CB = 32;
+
+__global__ void __launch_bounds__(256) k_chol_panel(double *A, int64_t n, int p, int32_t *status) {
+  __shared__ double D[CB][CB + 1];
+  __shared__ double Bk[CB][CB + 1];
+  const int64_t c0 = (int64_t)p * CB;
+  const int nb = (int)min64(CB, n - c0);
+  const int tid = threadIdx.x;
+  if (*status != 0) return;
+  for (int e = tid; e < CB * CB; e += 256) {
+    const int i = e / CB, j = e % CB;
+    D[i][j] = (i < nb && j < nb) ? A[(c0 + i) * n + c0 + j] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // unblocked Cholesky of D (lower), column by column
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double d = D[j][j];
+      D[j][j] = d > 0.0 ? sqrt(d) : -1.0;
+    }
+    __syncthreads();
+    const double djj = D[j][j];
+    if (!(djj > 0.0)) {
+      if (tid == 0 && blockIdx.x == 0) atomicExch(reinterpret_cast<int *>(status), (int)NQS_ERR_NOT_SPD);
+      return;
+    }
+    if (tid > j && tid < nb) D[tid][j] /= djj;
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += 256) {
+      const int i = e / nb, k = e % nb;
+      if (k > j && i >= k) D[i][k] -= D[i][j] * D[k][j];
+    }
+    __syncthreads();
+  }
+  const int b = blockIdx.x;
+  if (b == 0) {
+    for (int e = tid; e < nb * nb; e += 256) {
+      const int i = e / nb, j = e % nb;
+      if (j <= i) A[(c0 + i) * n + c0 + j] = D[i][j];
+    }
+    return;
+  }
+  const int64_t r0 = c0 + (int64_t)b * CB;
+  const int nr = (int)min64(CB, n - r0);
+  for (int e = tid; e < CB * CB; e += 256) {
+    const int i = e / CB, j = e % CB;
+    Bk[i][j] = (i < nr && j < nb) ? A[(r0 + i) * n + c0 + j] : 0.0;
+  }
+  __syncthreads();
+  // row i of L_ip solves L_pp x^T = a^T (forward substitution); one thread per row
+  if (tid < nr) {
+    for (int j = 0; j < nb; ++j) {
+      double v = Bk[tid][j];
+      for (int k = 0; k < j; ++k) v -= Bk[tid][k] * D[j][k];
+      Bk[tid][j] = v / D[j][j];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * nb; e += 256) {
+    const int i = e / nb, j = e % nb;
+    A[(r0 + i) * n + c0 + j] = Bk[i][j];
+  }
+}
+
+// Trailing update A_ij -= L_ip L_jp^T for the lower tiles (64x64) right of
+// panel p.
+__global__ void __launch_bounds__(256) k_chol_update(double *A, int64_t n, int p, const int32_t *status) {
+  if (*status != 0) return;
+  const int64_t c0 = (int64_t)p * CB, t0 = c0 + CB;
+  const int64_t i0 = t0 + (int64_t)blockIdx.y * 64, j0 = t0 + (int64_t)blockIdx.x * 64;
+  if (j0 > i0 + 63 || i0 >= n || j0 >= n) return;
+  __shared__ double La[CB][64 + 1], Lb[CB][64 + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int e = tid; e < 64 * CB; e += 256) {
+    const int r = e / CB, k = e % CB;
+    La[k][r] = (i0 + r < n) ? A[(i0 + r) * n + c0 + k] : 0.0;
+    Lb[k][r] = (j0 + r < n) ? A[(j0 + r) * n + c0 + k] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < CB; ++k) {
+    double a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { a[q] = La[k][ty + 16 * q]; b[q] = Lb[k][tx + 16 * q]; }
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[pp][q] = fma(a[pp], b[q], acc[pp][q]);
+  }
+#pragma unroll
+  for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + ty + 16 * pp, j = j0 + tx + 16 * q;
+      if (i < n && j < n && j <= i) A[i * n + j] -= acc[pp][q];
+    }
+}
+
+// Forward and backward substitution with the factor (lower triangle of A):
+// L y = b, then L^T x = y.  One CTA of 1024 threads; 32-wide blocks, the
+// diagonal block solved by warp 0, the rest updated by all threads.
+__global__ void __launch_bounds__(1024) k_chol_solve(const double *__restrict__ A, int64_t n,
+                                                     const double *__restrict__ b, double *x,
+                                                     const int32_t *status) {
+  extern __shared__ double sx[];  // n
+  if (*status != 0) return;
+  const int tid = threadIdx.x;
+  for (int64_t i = tid; i < n; i += blockDim.x) sx[i] = b[i];
+  __syncthreads();
+  // forward: L y = b
+  for (int64_t c0 = 0; c0 < n; c0 += 32) {
+    const int nb = (int)min64(32, n - c0);
+    if (tid < 32) {
+      double v = tid < nb ? sx[c0 + tid] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        double yj = __shfl_sync(0xffffffffu, v / A[(c0 + j) * n + c0 + j], j);
+        if (tid == j) v = yj;
+        if (tid > j && tid < nb) v -= A[(c0 + tid) * n + c0 + j] * yj;
+      }
+      if (tid < nb) sx[c0 + tid] = v;
+    }
+    __syncthreads();
+    for (int64_t i = c0 + nb + tid; i < n; i += blockDim.x) {
+      double v = 0.0;
+      for (int j = 0; j < nb; ++j) v += A[i * n + c0 + j] * sx[c0 + j];
+      sx[i] -= v;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = y
+  for (int64_t c1 = n; c1 > 0; c1 -= 32) {
+    const int nb = (int)min64(32, c1);
+    const int64_t c0 = c1 - nb;
+    if (tid < 32) {
+      double v = tid < nb ? sx[c0 + tid] : 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        double xj = __shfl_sync(0xffffffffu, v / A[(c0 + j) * n + c0 + j], j);
+        if (tid == j) v = xj;
+        if (tid < j) v -= A[(c0 + j) * n + c0 + tid] * xj;
+      }
+      if (tid < nb) sx[c0 + tid] = v;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < c0; i += blockDim.x) {
+      double v = 0.0;
+      for (int j = 0; j < nb; ++j) v += A[(c0 + j) * n + i] * sx[c0 + j];
+      sx[i] -= v;
+    }
+    __syncthreads();
+  }
+  for (int64_t i = tid; i < n; i += blockDim.x) x[i] = sx[i];
+}
+
+// tau = eps - lambda x (App. F), ||tau||, eta_t = eta0/(1+t/decay_T) and
+// eta* = eta_t/||tau|| in trust-region mode.
+__global__ void k_eta(const double *__restrict__ eps, const double *__restrict__ x, int64_t R,
+                      double eta_t, int trust, nqs_step_stats *st, const int32_t *solve_status) {
+  __shared__ double s[1024];
+  const double lam = st->lambda;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < R; i += blockDim.x) {
+    const double t = eps[i] - lam * x[i];
+    acc += t * t;
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tn = sqrt(s[0]);
+    st->tau_norm = tn;
+    st->eta_eff = trust ? eta_t / tn : eta_t;
+    if (st->status == NQS_OK && *solve_status != 0) st->status = *solve_status;
+  }
+}
+
+// Partial sums of O'x over row chunks: part[c][p] = sum_{r in chunk c} A[r][p] x[r].
+template <typename T>
+__global__ void k_gemv_part(const T *__restrict__ A, int64_t R, int64_t np,
+                            const double *__restrict__ x, int rows_per, double *part) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+  const int64_t r1 = min64(R, r0 + rows_per);
+  double acc = 0.0;
+  for (int64_t r = r0; r < r1; ++r) acc += (double)A[r * np + p] * x[r];
+  part[(int64_t)blockIdx.y * np + p] = acc;
+}
+
+// delta theta = eta_eff * sum of the partials; flags non-finite values.
+__global__ void k_dtheta(const double *__restrict__ part, int nparts, int64_t np,
+                         nqs_step_stats *st, double *dth) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double acc = 0.0;
+  for (int c = 0; c < nparts; ++c) acc += part[(int64_t)c * np + p];
+  const double d = st->eta_eff * acc;
+  dth[p] = d;
+  if (!isfinite(d)) atomicCAS(reinterpret_cast<int *>(&st->status), (int)NQS_OK, (int)NQS_ERR_NONFINITE);
+}
+
+// m <- mu m + (1-mu) dtheta; theta <- theta - m (App. B), only when the
+// step's status is OK.
+__global__ void k_apply(double *theta, double *mom, const double *__restrict__ dth, int64_t np,
+                        double mu, const nqs_step_stats *st) {
+  if (st->status != NQS_OK) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const double m = mu * mom[p] + (1.0 - mu) * dth[p];
+  mom[p] = m;
+  theta[p] -= m;
+}
+
+}  // namespace nqs

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libnqs (include/nqs.h).
+
+Argument marshalling only: every stage runs in the CUDA kernels of
+libnqs.so.  torch supplies device memory (the workspace and the output
+tensors) and streams.  Loading fails loudly if the library is missing.
+"""
+import ctypes as C
+import os
+
+import torch
+
+from .inputs import HamSpec, HParams, ModelSpec
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnqs.so")
+_lib = None
+
+PREC = {"fp64": 0, "mixed": 1}
+FAMILY = {"tfim": 0, "cluster_zxz": 1, "cluster_paper": 2, "j1j2": 3}
+
+
+class NqsError(RuntimeError):
+    pass
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("Lx", C.c_int), ("Ly", C.c_int), ("dh", C.c_int),
+                ("cplx", C.c_int), ("marshall", C.c_int), ("zmask", C.c_int)]
+
+
+class HamDesc(C.Structure):
+    _fields_ = [("family", C.c_int), ("J", C.c_double), ("h", C.c_double),
+                ("J1", C.c_double), ("J2", C.c_double)]
+
+
+class StepHParams(C.Structure):
+    _fields_ = [("eta0", C.c_double), ("decay_T", C.c_double), ("mu", C.c_double),
+                ("lam", C.c_double), ("lambda_coeff", C.c_double),
+                ("lambda_pow", C.c_double), ("lambda_mode", C.c_int32),
+                ("trust_region", C.c_int32), ("step_index", C.c_int64),
+                ("seed", C.c_uint64), ("n_samples", C.c_int64)]
+
+
+STATS_FIELDS = ["E_re", "E_im", "var", "vscore", "lam", "normT", "eta_eff", "tau_norm"]
+STATS_DOUBLES = 9  # 8 doubles + (status, pad) as int32 pair
+
+
+class StepOutputs(C.Structure):
+    _fields_ = [("spins", C.c_void_p), ("logpsi", C.c_void_p), ("eloc", C.c_void_p),
+                ("T", C.c_void_p), ("eps", C.c_void_p), ("x", C.c_void_p),
+                ("dtheta", C.c_void_p)]
+
+
+SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
+           "nqs_set_workspace", "nqs_sample", "nqs_logpsi", "nqs_local_energy",
+           "nqs_jacobian", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
+           "nqs_minsr_step_ex", "nqs_status_string"]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libnqs.so not built ({LIB_PATH}); run "
+                              "python -m paper_2608_18065_b300.build")
+        _lib = C.CDLL(LIB_PATH)
+        _lib.nqs_status_string.restype = C.c_char_p
+        for name in SYMBOLS[:-1]:
+            getattr(_lib, name).restype = C.c_int
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise NqsError(f"libnqs: {lib().nqs_status_string(rc).decode()} ({rc})")
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def model_desc(m: ModelSpec) -> ModelDesc:
+    return ModelDesc(m.dim, m.Lx, m.Ly, m.dh, m.cplx, m.marshall, m.zmask)
+
+
+def ham_desc(h: HamSpec) -> HamDesc:
+    return HamDesc(FAMILY[h.family], h.J, h.h, h.J1, h.J2)
+
+
+def step_hparams(hp: HParams, step_index: int) -> StepHParams:
+    return StepHParams(hp.eta0, hp.decay_T, hp.mu, hp.lam, hp.lambda_coeff, hp.lambda_pow,
+                       hp.lambda_mode, hp.trust_region, step_index, hp.seed, hp.ns)
+
+
+class Context:
+    """A libnqs context plus its torch-owned device workspace."""
+
+    def __init__(self, model: ModelSpec, ham: HamSpec, precision: str, max_samples: int,
+                 device="cuda"):
+        self.model, self.ham, self.precision = model, ham, precision
+        self.max_samples = int(max_samples)
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            h = C.c_void_p()
+            _check(lib().nqs_create(C.byref(model_desc(model)), C.byref(ham_desc(ham)),
+                                    PREC[precision], C.c_int64(self.max_samples), C.byref(h)))
+            self._h = h
+            n = C.c_int64()
+            _check(lib().nqs_param_count(h, C.byref(n)))
+            self.np = n.value
+            b = C.c_size_t()
+            _check(lib().nqs_workspace_size(h, C.byref(b)))
+            self.workspace_bytes = b.value
+            self.workspace = torch.empty(max(b.value, 256) + 256, dtype=torch.uint8,
+                                         device=self.device)
+            base = self.workspace.data_ptr()
+            off = (-base) % 256
+            _check(lib().nqs_set_workspace(h, C.c_void_p(base + off), C.c_size_t(b.value)))
+        self.odtype = torch.float32 if precision == "mixed" else torch.float64
+        self.rows_per_sample = 2 if model.cplx else 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nqs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- stages
+    def sample(self, theta, ns, seed, step, stream=None):
+        spins = torch.empty((ns, self.model.N), dtype=torch.uint8, device=self.device)
+        lp = torch.empty((ns, 2), dtype=torch.float64, device=self.device)
+        _check(lib().nqs_sample(self._h, _ptr(theta), C.c_int64(ns), C.c_uint64(seed),
+                                C.c_uint64(step), _ptr(spins), _ptr(lp), _stream(stream)))
+        return spins, lp
+
+    def logpsi(self, theta, spins, stream=None):
+        spins = spins.contiguous()
+        n = spins.shape[0]
+        lp = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        _check(lib().nqs_logpsi(self._h, _ptr(theta), _ptr(spins), C.c_int64(n), _ptr(lp),
+                                _stream(stream)))
+        return lp
+
+    def local_energy(self, theta, spins, stream=None):
+        spins = spins.contiguous()
+        n = spins.shape[0]
+        el = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        _check(lib().nqs_local_energy(self._h, _ptr(theta), _ptr(spins), C.c_int64(n),
+                                      _ptr(el), _stream(stream)))
+        return el
+
+    def jacobian(self, theta, spins, stream=None):
+        spins = spins.contiguous()
+        n = spins.shape[0]
+        O = torch.empty((n * self.rows_per_sample, self.np), dtype=self.odtype,
+                        device=self.device)
+        _check(lib().nqs_jacobian(self._h, _ptr(theta), _ptr(spins), C.c_int64(n), _ptr(O),
+                                  _stream(stream)))
+        return O
+
+    def gram(self, A, stream=None):
+        A = A.contiguous()
+        R, np_ = A.shape
+        T = torch.empty((R, R), dtype=torch.float64, device=self.device)
+        _check(lib().nqs_gram(self._h, _ptr(A), C.c_int64(R), C.c_int64(np_), _ptr(T),
+                              _stream(stream)))
+        return T
+
+    def regularized_solve(self, T, lam, b, stream=None):
+        """Returns (x, device status); T is overwritten by its factor."""
+        R = T.shape[0]
+        x = torch.empty(R, dtype=torch.float64, device=self.device)
+        status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        _check(lib().nqs_regularized_solve(self._h, _ptr(T), C.c_int64(R), C.c_double(lam),
+                                           _ptr(b), _ptr(x), _ptr(status), _stream(stream)))
+        return x, status
+
+    def new_stats(self):
+        return torch.zeros(STATS_DOUBLES, dtype=torch.float64, device=self.device)
+
+    def minsr_step(self, theta, mom, hp: HParams, step_index, stats=None, outputs=None,
+                   stream=None):
+        """One step of Algorithm 1 in place on theta/mom (device FP64)."""
+        if stats is None:
+            stats = self.new_stats()
+        hps = step_hparams(hp, step_index)
+        if outputs is None:
+            _check(lib().nqs_minsr_step(self._h, _ptr(theta), _ptr(mom), C.byref(hps),
+                                        _ptr(stats), _stream(stream)))
+        else:
+            o = StepOutputs(*[(outputs[k].data_ptr() if k in outputs else None)
+                              for k in ("spins", "logpsi", "eloc", "T", "eps", "x", "dtheta")])
+            _check(lib().nqs_minsr_step_ex(self._h, _ptr(theta), _ptr(mom), C.byref(hps),
+                                           _ptr(stats), C.byref(o), _stream(stream)))
+        return stats
+
+    def step_outputs(self, ns):
+        R = ns * self.rows_per_sample
+        d = self.device
+        return dict(spins=torch.empty((ns, self.model.N), dtype=torch.uint8, device=d),
+                    logpsi=torch.empty((ns, 2), dtype=torch.float64, device=d),
+                    eloc=torch.empty((ns, 2), dtype=torch.float64, device=d),
+                    T=torch.empty((R, R), dtype=torch.float64, device=d),
+                    eps=torch.empty(R, dtype=torch.float64, device=d),
+                    x=torch.empty(R, dtype=torch.float64, device=d),
+                    dtheta=torch.empty(self.np, dtype=torch.float64, device=d))
+
+
+def decode_stats(stats: torch.Tensor) -> dict:
+    v = stats.detach().cpu()
+    d = {k: float(v[i]) for i, k in enumerate(STATS_FIELDS)}
+    d["status"] = int(v[8:9].view(torch.int32)[0])
+    return d

@@ -1,0 +1,52 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the
+C-ABI binding and the oracle on the same seeded inputs."""
+import numpy as np
+import torch
+
+from oracle import oracle as O
+from paper_2608_18065_b300 import nqs
+from paper_2608_18065_b300.inputs import init_theta
+
+# Tolerances.
+#  FP64 path: 1e-10 relative (the bound stated for the plain GPU path); the
+#  kernels differ from the oracle only in summation order and libm ulps.
+#  Mixed path: the recurrence runs in FP32 (unit roundoff u = 6e-8).  A
+#  per-site error of a few u, accumulated over N <= 100 sites and amplified
+#  by the recurrence Jacobian (O(1) for these initialisations), bounds the
+#  error of log Psi at ~N * 10 u ~ 6e-5 absolute; local energies inherit it
+#  through exp(log Psi' - log Psi) -> 1e-4 relative; O is a sum over N sites
+#  of FP32 products -> 1e-4 relative in norm.
+RTOL64 = 1e-10
+TOL_MIXED_LOGPSI = 1e-4
+TOL_MIXED_ELOC = 2e-4
+TOL_MIXED_JAC = 2e-4
+
+
+def ctx(model, ham, precision, max_samples):
+    return nqs.Context(model, ham, precision, max_samples)
+
+
+def theta_dev(model, seed=1234, scale=1.0):
+    th = init_theta(model, seed) * scale
+    return th, torch.tensor(th, dtype=torch.float64, device="cuda")
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def cplx(t):
+    a = t.detach().cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def near_ties(model, theta, spins, seed, step, tol):
+    """Sites where |u - p_k(0)| < tol along each oracle configuration."""
+    out = 0
+    for s in range(spins.shape[0]):
+        p0 = O.conditionals(model, theta, spins[s])
+        u = np.array([O.uniform(seed, step, s, k) for k in range(model.N)])
+        out += int(np.sum(np.abs(u - p0) < tol))
+    return out

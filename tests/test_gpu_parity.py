@@ -1,0 +1,198 @@
+"""GPU parity of every stage of the minSR step against the FP64 oracle,
+through the C-ABI (libnqs.so).  Sizes span several CTA tiles with ragged
+tails; the FP64 path is held to 1e-10 relative and bit-exact samples, the
+mixed path to the FP32-derived tolerances of gpu_helpers."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2608_18065_b300.inputs import HamSpec, HParams, ModelSpec, random_spins
+from tests.gpu_helpers import (RTOL64, TOL_MIXED_ELOC, TOL_MIXED_JAC, TOL_MIXED_LOGPSI,
+                               cplx, ctx, near_ties, rel_err, theta_dev)
+
+pytestmark = pytest.mark.gpu
+
+MODELS = [
+    (ModelSpec(1, 13, 1, 8), HamSpec("tfim", J=1.0, h=0.9)),
+    (ModelSpec(1, 12, 1, 16, cplx=1), HamSpec("cluster_zxz")),
+    (ModelSpec(1, 11, 1, 8, cplx=1), HamSpec("cluster_paper")),
+    (ModelSpec(2, 4, 4, 8, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5)),
+    (ModelSpec(2, 3, 4, 16, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.0)),
+    (ModelSpec(2, 5, 2, 8), HamSpec("j1j2", J1=1.0, J2=0.0)),
+]
+IDS = [f"{m.dim}d_{m.Lx}x{m.Ly}_dh{m.dh}_{h.family}" for m, h in MODELS]
+
+
+@pytest.mark.parametrize("model,ham", MODELS, ids=IDS)
+def test_sampler_fp64_bit_exact(model, ham):
+    ns = 77
+    c = ctx(model, ham, "fp64", ns)
+    th, thd = theta_dev(model, 3, scale=1.5)
+    spins, lp = c.sample(thd, ns, seed=42, step=5)
+    torch.cuda.synchronize()
+    sp_o, lp_o = O.sample(model, th, ns, 42, 5)
+    assert near_ties(model, th, sp_o, 42, 5, 1e-12) == 0
+    assert np.array_equal(spins.cpu().numpy(), sp_o)
+    np.testing.assert_allclose(cplx(lp), lp_o, rtol=RTOL64, atol=RTOL64)
+
+
+@pytest.mark.parametrize("model,ham", MODELS, ids=IDS)
+def test_logpsi_eloc_jacobian_fp64(model, ham):
+    ns = 70
+    c = ctx(model, ham, "fp64", ns)
+    th, thd = theta_dev(model, 4)
+    sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    lp = cplx(c.logpsi(thd, spd))
+    np.testing.assert_allclose(lp, O.logpsi(model, th, sp), rtol=RTOL64, atol=RTOL64)
+    el = cplx(c.local_energy(thd, spd))
+    el_o = O.local_energy(model, ham, th, sp)
+    assert rel_err(el, el_o) < RTOL64
+    J = c.jacobian(thd, spd).cpu().numpy()
+    J_o = O.jacobian(model, th, sp)
+    assert J.shape == J_o.shape
+    assert rel_err(J, J_o) < RTOL64
+    assert np.max(np.abs(J - J_o)) < RTOL64 * np.max(np.abs(J_o))
+
+
+@pytest.mark.parametrize("model,ham", MODELS, ids=IDS)
+def test_logpsi_eloc_jacobian_mixed(model, ham):
+    ns = 70
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 4)
+    sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    lp = cplx(c.logpsi(thd, spd))
+    lp_o = O.logpsi(model, th, sp)
+    assert np.max(np.abs(lp - lp_o)) < TOL_MIXED_LOGPSI
+    el = cplx(c.local_energy(thd, spd))
+    assert rel_err(el, O.local_energy(model, ham, th, sp)) < TOL_MIXED_ELOC
+    J = c.jacobian(thd, spd).cpu().numpy().astype(np.float64)
+    assert rel_err(J, O.jacobian(model, th, sp)) < TOL_MIXED_JAC
+
+
+def test_sampler_mixed_decisions_valid():
+    """FP32 conditionals decide the spins: every decision must agree with the
+    oracle's p_k(0) unless u lies within 1e-5 of it; log Psi as mixed."""
+    model = ModelSpec(2, 4, 4, 16, cplx=1, marshall=1, zmask=1)
+    ns = 100
+    c = ctx(model, HamSpec("j1j2"), "mixed", ns)
+    th, thd = theta_dev(model, 6, scale=1.5)
+    spins, lp = c.sample(thd, ns, seed=11, step=2)
+    sp = spins.cpu().numpy()
+    assert np.all(sp.sum(1) == model.N // 2)
+    bad = 0
+    for s in range(ns):
+        p0 = O.conditionals(model, th, sp[s])
+        u = np.array([O.uniform(11, 2, s, k) for k in range(model.N)])
+        dec = np.where(u < p0, 0, 1)
+        bad += int(np.sum((dec != sp[s]) & (np.abs(u - p0) > 1e-5)))
+    assert bad == 0
+    assert np.max(np.abs(cplx(lp) - O.logpsi(model, th, sp))) < TOL_MIXED_LOGPSI
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("R,np_", [(1, 7), (70, 300), (130, 1001), (256, 4097)])
+def test_gram(prec, R, np_):
+    model, ham = ModelSpec(1, 8, 1, 64), HamSpec("tfim")  # Np = 13058 >= np_
+    c = ctx(model, ham, prec, 256)
+    rng = np.random.default_rng(R)
+    A = rng.standard_normal((R, np_)) / np.sqrt(np_)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Ad = torch.tensor(A, dtype=dt, device="cuda")
+    T = c.gram(Ad).cpu().numpy()
+    Aref = Ad.double().cpu().numpy()
+    Tref = Aref @ Aref.T
+    tol = RTOL64 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(T - Tref)) < tol * np.max(np.abs(Tref))
+    assert np.array_equal(T, T.T)
+
+
+@pytest.mark.parametrize("R", [1, 31, 64, 200, 513])
+def test_regularized_solve(R):
+    model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
+    c = ctx(model, ham, "fp64", 8)
+    rng = np.random.default_rng(R)
+    M = rng.standard_normal((R, R + 5))
+    T = M @ M.T
+    b = rng.standard_normal(R)
+    lam = 1e-2
+    Td = torch.tensor(T, device="cuda")
+    x, st = c.regularized_solve(Td, lam, torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 0
+    xr = np.linalg.solve(T + lam * np.eye(R), b)
+    assert rel_err(x.cpu().numpy(), xr) < 1e-9
+    # an indefinite matrix reports NOT_SPD (5)
+    Td = torch.tensor(-T - np.eye(R), device="cuda")
+    x, st = c.regularized_solve(Td, 0.0, torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 5
+
+
+STEP_CASES = [
+    (ModelSpec(1, 16, 1, 16), HamSpec("tfim"), HParams(0.5, 1e3, 0.7, lam=1e-3, ns=128)),
+    (ModelSpec(1, 12, 1, 8, cplx=1), HamSpec("cluster_zxz"),
+     HParams(5e-3, 5e3, 0.1, lam=1e-3, ns=60)),
+    (ModelSpec(2, 4, 4, 8, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.0),
+     HParams(6e-2, 1e4, 0.75, lambda_mode=1, lambda_coeff=3e-4, lambda_pow=2 / 3, ns=50)),
+    (ModelSpec(2, 4, 4, 8, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.5),
+     HParams(0.1, 1e4, 0.1, lam=0.1, trust_region=1, ns=50)),
+]
+STEP_IDS = ["tfim16", "cluster12", "heis4x4", "j1j2_4x4"]
+
+
+@pytest.mark.parametrize("model,ham,hp", STEP_CASES, ids=STEP_IDS)
+def test_minsr_step_fp64(model, ham, hp):
+    """Two consecutive steps: samples bit-exact; E, T, x, delta theta,
+    theta and momentum to 1e-10 relative (kappa * eps64 << 1e-10 here)."""
+    c = ctx(model, ham, "fp64", hp.ns)
+    th, thd = theta_dev(model, 1234)
+    mom = np.zeros_like(th)
+    momd = torch.zeros_like(thd)
+    for t in range(2):
+        outs = c.step_outputs(hp.ns)
+        stats = c.minsr_step(thd, momd, hp, t, outputs=outs)
+        torch.cuda.synchronize()
+        th, mom, st_o, b = O.minsr_step(model, ham, th, mom, hp, t,
+                                        want=("spins", "eloc", "T", "eps", "x", "dtheta"))
+        from paper_2608_18065_b300.nqs import decode_stats
+        st = decode_stats(stats)
+        assert st["status"] == 0 and st_o["status"] == 0
+        assert np.array_equal(outs["spins"].cpu().numpy(), b["spins"])
+        assert rel_err(cplx(outs["eloc"]), b["eloc"]) < RTOL64
+        for k in ("E_re", "var", "lam", "normT", "eta_eff", "tau_norm"):
+            assert abs(st[k] - st_o[k]) <= RTOL64 * max(abs(st_o[k]), 1e-300), k
+        assert rel_err(outs["T"].cpu().numpy(), b["T"]) < RTOL64
+        assert rel_err(outs["eps"].cpu().numpy(), b["eps"]) < RTOL64
+        Tm = b["T"] + st_o["lam"] * np.eye(len(b["eps"]))
+        kappa = np.linalg.cond(Tm)
+        tol = max(RTOL64, 100 * kappa * 2.2e-16)
+        assert rel_err(outs["x"].cpu().numpy(), b["x"]) < tol
+        assert rel_err(outs["dtheta"].cpu().numpy(), b["dtheta"]) < tol
+        assert rel_err(thd.cpu().numpy(), th) < tol
+        assert rel_err(momd.cpu().numpy(), mom) < tol
+
+
+@pytest.mark.parametrize("model,ham,hp", STEP_CASES[:3], ids=STEP_IDS[:3])
+def test_minsr_step_mixed_error_report(model, ham, hp):
+    """Mixed step against the FP64 oracle from the same state: samples agree
+    except near-ties; E, T and delta theta errors stay within FP32-derived
+    bounds (T: BF16x3/FP32 product error ~1e-5 of max|T|)."""
+    c = ctx(model, ham, "mixed", hp.ns)
+    th, thd = theta_dev(model, 1234)
+    momd = torch.zeros_like(thd)
+    outs = c.step_outputs(hp.ns)
+    stats = c.minsr_step(thd, momd, hp, 0, outputs=outs)
+    torch.cuda.synchronize()
+    from paper_2608_18065_b300.nqs import decode_stats
+    st = decode_stats(stats)
+    _, _, st_o, b = O.minsr_step(model, ham, th, np.zeros_like(th), hp, 0,
+                                 want=("spins", "eloc", "T", "eps", "x", "dtheta"))
+    assert st["status"] == 0
+    sp = outs["spins"].cpu().numpy()
+    if not np.array_equal(sp, b["spins"]):
+        pytest.skip("a near-tie changed a mixed-precision sample")
+    assert abs(st["E_re"] - st_o["E_re"]) < TOL_MIXED_ELOC * abs(st_o["E_re"])
+    T = outs["T"].cpu().numpy()
+    assert np.max(np.abs(T - b["T"])) < 1e-3 * np.max(np.abs(b["T"]))
+    assert rel_err(outs["dtheta"].cpu().numpy(), b["dtheta"]) < 5e-2
