@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark: regularized minSR steps/s on one B300 (and N replicas).
+
+Workload (default): 1D transverse-field Ising open chain, N = 100, h = J = 1,
+GRU hidden size 64 (Np = 13058), Ns = 1024 samples, mixed precision (FP32
+recurrence and Jacobian, BF16x3 tensor-core Gram, FP64 centring and solve),
+Tab. I TFIM hyper-parameters.  One step = one iteration of Algorithm 1
+(sampling, local energies, O, centring, T, regularized solve, momentum,
+update) through nqs_minsr_step.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(bounded per-step sample of the same workload, scaled to steps/s).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "minSR steps/s & Gram TFLOP/s vs plain FP64 GPU path at matched energy error"
+UNIT = "steps/s"
+FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="tfim100")
+    p.add_argument("--matched-steps", type=int, default=40,
+                   help="steps of the mixed and FP64 paths for the matched-energy check (0: skip)")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- algorithmic
+def site_flops(model):
+    """FMA-pipe flops of one site of one configuration (x2 per FMA): the
+    gate products 3dh x dh, the 2D state mix 2 dh x dh, the output heads."""
+    dh = model.dh
+    f = 2 * 3 * dh * dh + 2 * 2 * dh * (2 if model.cplx else 1)
+    if model.dim == 2:
+        f += 2 * 2 * dh * dh
+    return f
+
+
+def eloc_suffix_sites(w):
+    """Sites recomputed per step by the connected-configuration engine for
+    Hamiltonians whose connectivity does not depend on the sample."""
+    N, ns = w.model.N, w.hp.ns
+    if w.ham.family == "tfim":
+        return ns * sum(N - j for j in range(N))
+    if w.ham.family == "cluster_zxz":
+        return ns * sum(N - i for i in range(1, N - 1))
+    return None
+
+
+def src_sha(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        h.update(open(os.path.join(ROOT, r), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, sha, workload):
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel)
+    except (ValueError, OSError):
+        return None
+    if d and d.get("src_sha") == sha and d.get("workload") == workload:
+        return d.get("bytes_per_launch")
+    return None
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_bounded(w, budget_s, seed_step=0):
+    """Time oracle steps on a sample of Ns_sub configurations sized to the
+    budget; returns (steps/s scaled to the full Ns, Ns_sub, seconds, threads)."""
+    import copy
+    from oracle import oracle as O
+    from paper_2608_18065_b300.inputs import init_theta
+    th = init_theta(w.model, w.theta_seed)
+    hp = copy.copy(w.hp)
+    hp.ns = 8
+    t0 = time.perf_counter()
+    O.minsr_step(w.model, w.ham, th, np.zeros_like(th), hp, seed_step)
+    per_sample = (time.perf_counter() - t0) / 8
+    ns_sub = int(max(8, min(w.hp.ns, budget_s / max(per_sample, 1e-9))))
+    hp.ns = ns_sub
+    t0 = time.perf_counter()
+    O.minsr_step(w.model, w.ham, th, np.zeros_like(th), hp, seed_step)
+    dt = time.perf_counter() - t0
+    scale = w.hp.ns / ns_sub
+    return 1.0 / (dt * scale), ns_sub, dt, O.num_threads()
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2608_18065_b300.inputs import workloads
+    w = workloads()[args.workload]
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for t in range(args.warmup):
+        oracle_bounded(w, budget, t)
+    vals, subs, secs, thr = [], [], [], 1
+    for t in range(args.steps):
+        v, sub, dt, thr = oracle_bounded(w, budget, args.warmup + t)
+        vals.append(v); subs.append(sub); secs.append(dt)
+    value = float(np.mean(vals))
+    sample = (f"one oracle step per timed step on Ns_sub={min(subs)}..{max(subs)} of the "
+              f"{w.hp.ns} samples (same model, Hamiltonian, theta_0), time scaled by "
+              f"{w.hp.ns}/Ns_sub (sampling, local energies and O are linear in Ns)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": w.describe(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import init_theta, workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads()[args.workload]
+    hp = w.hp
+    K, Wu = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # replica r: its own Philox key (seed + r), same theta_0
+    import copy
+    hp = copy.copy(hp)
+    hp.seed = hp.seed + rank
+    ctx = nqs.Context(w.model, w.ham, w.precision, hp.ns, device=dev)
+    th0 = init_theta(w.model, w.theta_seed)
+    thd = torch.tensor(th0, device=dev)
+    momd = torch.zeros_like(thd)
+    stats = ctx.new_stats()
+    for t in range(Wu):
+        ctx.minsr_step(thd, momd, hp, t, stats)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.timing_begin(K)
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record()
+    for t in range(Wu, Wu + K):
+        ctx.minsr_step(thd, momd, hp, t, stats)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    stage_ms, nt = ctx.timing_end()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t_ = torch.tensor([ms], device=dev)
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms = float(t_.item())
+    st = nqs.decode_stats(stats)
+    value = world * K / (ms / 1000.0)
+    ms_step = ms / K
+
+    # Gram throughput (symmetric algorithmic count R(R+1)Np)
+    R = hp.ns * (2 if w.model.cplx else 1)
+    gram_ms = stage_ms["gram"] / max(nt, 1)
+    gram_tflops = R * (R + 1) * ctx.np / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
+
+    # dominant kernel and its roofline
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    dom_ms = stage_ms[dom] / max(nt, 1)
+    roof = None
+    if dom == "eloc_suffix":
+        sites = eloc_suffix_sites(w)
+        if sites is not None:
+            fl = sites * site_flops(w.model)
+            ach = fl / (dom_ms * 1e-3) / 1e12
+            sha = src_sha("paper_2608_18065_b300/csrc/recurrence.cuh",
+                          "paper_2608_18065_b300/csrc/recur_impl.cuh")
+            roof = {"kernel": "k_forward<MODE_ELOC> (eloc_suffix)", "bound": "alu",
+                    "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_ALU_PEAK_TFLOPS,
+                    "traffic": load_traffic("eloc_suffix", sha, w.name),
+                    "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
+                    "flops_per_launch": fl, "ms_per_launch": dom_ms}
+    if roof is None:
+        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None, "ms_per_launch": dom_ms}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        th_h = thd.cpu().pin_memory()
+        m_h = momd.cpu().pin_memory()
+        st_h = torch.empty_like(stats, device="cpu").pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for t in range(Wu + K, Wu + 2 * K):
+            thd.copy_(th_h, non_blocking=True)
+            momd.copy_(m_h, non_blocking=True)
+            ctx.minsr_step(thd, momd, hp, t, stats)
+            th_h.copy_(thd, non_blocking=True)
+            m_h.copy_(momd, non_blocking=True)
+            st_h.copy_(stats, non_blocking=True)
+        a1.record()
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t_ = torch.tensor([ems], device=dev)
+            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+            ems = float(t_.item())
+        e2e = {"value": world * K / (ems / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * ctx.np * 8,
+               "d2h_bytes_per_step": 2 * ctx.np * 8 + stats.numel() * 8}
+
+    # plain FP64 GPU path on the same workload
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64 = nqs.Context(w.model, w.ham, "fp64", hp.ns, device=dev)
+        t64 = torch.tensor(th0, device=dev)
+        m64 = torch.zeros_like(t64)
+        s64 = c64.new_stats()
+        c64.minsr_step(t64, m64, hp, 0, s64)
+        torch.cuda.synchronize()
+        c64.timing_begin(args.fp64_steps)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for t in range(1, 1 + args.fp64_steps):
+            c64.minsr_step(t64, m64, hp, t, s64)
+        b1.record()
+        torch.cuda.synchronize()
+        sm64, n64 = c64.timing_end()
+        f_ms = b0.elapsed_time(b1) / args.fp64_steps
+        g64 = sm64["gram"] / max(n64, 1)
+        fp64 = {"steps_per_s": 1000.0 / f_ms, "ms_per_step": f_ms,
+                "gram_tflops": R * (R + 1) * ctx.np / (g64 * 1e-3) / 1e12 if g64 > 0 else None,
+                "stage_ms": {k: v / max(n64, 1) for k, v in sm64.items()},
+                "speedup_mixed_over_fp64": (1000.0 / ms_step) / (1000.0 / f_ms)}
+        del c64
+
+    # matched energy error: both paths from theta_0 with the same seeds
+    matched = None
+    if args.matched_steps > 0 and rank == 0:
+        matched = matched_energy(w, hp, args.matched_steps, dev)
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        v, sub, dt, thr = oracle_bounded(w, 20.0)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": (f"one FP64 oracle step on Ns_sub={sub} of the {hp.ns} samples "
+                          f"({dt:.1f} s), scaled by {hp.ns}/{sub}"), "cpu": cpu_model()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": Wu, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3+f64",
+                "data": "synthetic",
+                "config": dict(w.describe(), l2="step working set > 126 MB L2 (O, caches, adjoints)",
+                               replicas=world),
+                "gram_tflops": gram_tflops,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "fp64_path": fp64, "matched_energy": matched,
+                "stage_ms": {k: v / max(nt, 1) for k, v in stage_ms.items()},
+                "final_stats": st}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def matched_energy(w, hp, steps, dev):
+    """Run the mixed and the FP64 GPU paths for `steps` steps from theta_0
+    with the same Philox seeds; report the mean relative error of E over the
+    last 10 steps against the exact energy (Jordan-Wigner for the TFIM)."""
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import init_theta
+    if w.ham.family != "tfim":
+        return None
+    N = w.model.N
+    B = np.diag(np.full(N, w.ham.h)) + np.diag(np.full(N - 1, w.ham.J), 1)
+    E0 = -float(np.sum(np.linalg.svd(B, compute_uv=False)))
+    out = {"E_exact": E0, "steps": steps}
+    for prec in ("mixed", "fp64"):
+        c = nqs.Context(w.model, w.ham, prec, hp.ns, device=dev)
+        th = torch.tensor(init_theta(w.model, w.theta_seed), device=dev)
+        m = torch.zeros_like(th)
+        es, se = [], []
+        s = c.new_stats()
+        for t in range(steps):
+            c.minsr_step(th, m, hp, t, s)
+            d = nqs.decode_stats(s)
+            es.append(d["E_re"])
+            se.append(np.sqrt(d["var"] / hp.ns))
+        last = np.array(es[-10:])
+        rel = (last - E0) / abs(E0)
+        out[prec] = {"rel_err_last10": float(rel.mean()),
+                     "stderr": float(np.mean(se[-10:]) / abs(E0) / np.sqrt(10)),
+                     "E_first": es[0], "E_last": es[-1]}
+        del c
+    d = abs(out["mixed"]["rel_err_last10"] - out["fp64"]["rel_err_last10"])
+    out["matched"] = bool(d <= max(out["mixed"]["stderr"], out["fp64"]["stderr"]))
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

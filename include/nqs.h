@@ -205,6 +205,29 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
                              nqs_step_stats *dev_stats,
                              const nqs_step_outputs *out, void *stream);
 
+/* ------------------------------------------------------- instrumentation */
+
+/* Stages timed by the step instrumentation, in step order. */
+#define NQS_N_STAGES 14
+/* Name of stage i (static storage), NULL if out of range:
+ * pack, sample, eloc_gen, eloc_suffix, eloc_reduce, energy, jac_bwd,
+ * jac_grad, center, gram, lambda, cholesky, solve, update. */
+const char *nqs_stage_name(int i);
+
+/* Start per-stage CUDA-event timing of the next max_steps calls of
+ * nqs_minsr_step[_ex] on this context (events are recorded on the step's
+ * stream, no host synchronisation is added).  Replaces an earlier timing
+ * window. */
+nqs_status nqs_timing_begin(nqs_ctx *ctx, int max_steps);
+
+/* End the timing window: synchronises the recorded events and writes the
+ * summed milliseconds of each stage to stage_ms[0..NQS_N_STAGES-1] and the
+ * number of timed steps to *n_steps. */
+nqs_status nqs_timing_end(nqs_ctx *ctx, double *stage_ms, int *n_steps);
+
+/* Number of kernels this context has launched since it was created. */
+nqs_status nqs_launch_count(const nqs_ctx *ctx, int64_t *n);
+
 /* Short text for a status code (static storage). */
 const char *nqs_status_string(int status);
 

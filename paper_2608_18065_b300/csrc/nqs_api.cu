@@ -41,6 +41,10 @@ struct nqs_ctx {
   char *ws = nullptr;
   size_t ws_bytes = 0;
   int nsplit = 1;
+  // instrumentation: (NQS_N_STAGES + 1) boundary events per timed step
+  std::vector<cudaEvent_t> tev;
+  int tmax = 0, tstep = 0;
+  int64_t launches = 0;
 };
 
 namespace {
@@ -152,10 +156,16 @@ template <typename T> T *W(nqs_ctx *c, size_t off) { return reinterpret_cast<T *
 
 nqs_status need_ws(nqs_ctx *c) { return c->ws ? NQS_OK : NQS_ERR_WORKSPACE; }
 
+// Record stage boundary i of the current step when a timing window is open.
+void mark(nqs_ctx *c, int i, cudaStream_t st) {
+  if (c->tstep < c->tmax) cudaEventRecord(c->tev[(size_t)c->tstep * (NQS_N_STAGES + 1) + i], st);
+}
+
 template <typename T> nqs_status pack_theta(nqs_ctx *c, const double *theta, cudaStream_t st) {
   const int64_t tot = c->P.total;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
   k_pack<T><<<blocks, 256, 0, st>>>(theta, W<T>(c, c->off.pack), c->L, c->P);
+  c->launches += 1;
   return cu(cudaGetLastError());
 }
 
@@ -174,6 +184,7 @@ nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t st
                      double *logpsi, cudaStream_t st) {
   FwdArgs<T> a = fwd_args<T>(c);
   a.nrows = n; a.seed = seed; a.step = step; a.spins = spins; a.logpsi = logpsi;
+  c->launches += 1;
   return cu(run_forward<T>(c->rd, mode, a, 0, st));
 }
 
@@ -193,7 +204,9 @@ nqs_status pack_any(nqs_ctx *c, const double *theta, cudaStream_t st) {
 // Local energies of the ns configurations whose hidden states are cached.
 template <typename T>
 nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cudaStream_t st) {
+  mark(c, 2, st);
   if (c->n_off > 0) {
+    c->launches += 2;
     k_eloc_gen<<<c->n_off, 256, 0, st>>>(c->d_off, spins, c->L.N, ns, W<int>(c, c->off.item_s),
                                          W<double>(c, c->off.item_e), W<int>(c, c->off.item_cnt),
                                          W<double>(c, c->off.contrib));
@@ -209,8 +222,13 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
     a.item_cnt = W<int>(c, c->off.item_cnt);
     a.contrib = W<double>(c, c->off.contrib);
     a.colbuf = W<T>(c, c->off.colbuf);
+    mark(c, 3, st);
     CU(run_forward<T>(c->rd, MODE_ELOC, a, c->eloc_grid, st));
+  } else {
+    mark(c, 3, st);
   }
+  mark(c, 4, st);
+  c->launches += 1;
   k_eloc_reduce<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(
       c->d_diag, c->n_diag, c->n_off, spins, c->L.N, ns, W<double>(c, c->off.contrib), eloc);
   return cu(cudaGetLastError());
@@ -233,7 +251,10 @@ nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_
   b.adj = W<T>(c, c->off.adj);
   b.adjw = c->adjw;
   b.adjcol = W<T>(c, c->off.adjcol);
+  mark(c, 6, st);
   CU(run_bwd<T>(c->rd, b, st));
+  mark(c, 7, st);
+  c->launches += 2;
   GradArgs<T, T> g{};
   g.N = c->L.N; g.Lx = c->L.Lx; g.cplx = c->L.cplx; g.dim = c->L.dim;
   g.ns = ns; g.nrows = R; g.spins = spins; g.hcache = b.hcache; g.adj = b.adj; g.adjw = c->adjw;
@@ -246,6 +267,7 @@ nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_
 
 // T = A A^T in FP64 (see nqs_gram).
 nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T, cudaStream_t st) {
+  c->launches += gram_tc_available() && f32(c) ? gram_tc_launches() : 1;
   if (f32(c)) {
     if (gram_tc_available())
       return cu(gram_tc_bf16x3(reinterpret_cast<const float *>(A), R, np, T,
@@ -296,9 +318,10 @@ __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int np
 }
 
 // Cholesky of the shifted T in place, then x = (T + lambda I)^{-1} b.
-nqs_status chol_solve(double *T, int64_t R, const double *b, double *x, int32_t *status,
-                      cudaStream_t st) {
+nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double *x,
+                      int32_t *status, cudaStream_t st) {
   const int np_ = (int)((R + CB - 1) / CB);
+  c->launches += 2 * np_;  // panels, trailing updates (np_ - 1) and the solve
   for (int p = 0; p < np_; ++p) {
     const int rows = np_ - p;
     k_chol_panel<<<rows, 256, 0, st>>>(T, R, p, status);
@@ -313,6 +336,7 @@ nqs_status chol_solve(double *T, int64_t R, const double *b, double *x, int32_t 
   const size_t smem = (size_t)R * 8;
   if (smem > 48 * 1024)
     CU(cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  mark(c, 12, st);
   k_chol_solve<<<1, 1024, smem, st>>>(T, R, b, x, status);
   return cu(cudaGetLastError());
 }
@@ -330,17 +354,23 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   double *eps = W<double>(c, c->off.eps);
   double *x = W<double>(c, c->off.x);
   int32_t *sstat = W<int32_t>(c, c->off.sstat);
+  mark(c, 0, st);
   CU(cudaMemsetAsync(sstat, 0, 64, st));
   // line 3: sample (also fills the hidden-state caches)
   ST(pack_theta<T>(c, theta, st));
+  mark(c, 1, st);
   ST(forward_T<T>(c, MODE_SAMPLE, ns, hp->seed, (uint64_t)hp->step_index, spins, logpsi, st));
   // line 4: local energies, E, variance; eps-bar'
   ST(eloc_T<T>(c, ns, spins, eloc, st));
+  mark(c, 5, st);
   k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
+  c->launches += 1;
   CU(cudaGetLastError());
   // line 5: O, centred over samples per block, / sqrt(Ns)
   ST(jac_T<T>(c, ns, spins, O, st));
+  mark(c, 8, st);
   {
+    c->launches += 2;
     dim3 g((unsigned)((np + 255) / 256), c->L.cplx ? 2u : 1u);
     k_colmean<T><<<g, 256, 0, st>>>(O, ns, np, W<double>(c, c->off.mean));
     CU(cudaGetLastError());
@@ -350,24 +380,30 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     CU(cudaGetLastError());
   }
   // line 6: T = O'^T O'
+  mark(c, 9, st);
   ST(gram_any(c, O, R, np, Tm, st));
+  mark(c, 10, st);
   if (out && out->T) CU(cudaMemcpyAsync(out->T, Tm, R * R * 8, cudaMemcpyDeviceToDevice, st));
   // lambda and shift
   {
     const int nparts = 256;
+    c->launches += 2;
     k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
     k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts, hp->lambda_mode,
                                         hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats);
     CU(cudaGetLastError());
   }
   // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
-  ST(chol_solve(Tm, R, eps, x, sstat, st));
+  mark(c, 11, st);
+  ST(chol_solve(c, Tm, R, eps, x, sstat, st));
+  mark(c, 13, st);
   double eta_t = hp->eta0;
   if (hp->decay_T > 0.0 && std::isfinite(hp->decay_T))
     eta_t = hp->eta0 / (1.0 + (double)hp->step_index / hp->decay_T);
   k_eta<<<1, 1024, 0, st>>>(eps, x, R, eta_t, hp->trust_region, stats, sstat);
   CU(cudaGetLastError());
   {
+    c->launches += 4;
     const int rows_per = 64;
     const int nparts = (int)((R + rows_per - 1) / rows_per);
     dim3 g((unsigned)((np + 255) / 256), (unsigned)nparts);
@@ -379,6 +415,8 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
                                                          np, hp->mu, stats);
     CU(cudaGetLastError());
   }
+  mark(c, 14, st);
+  if (c->tstep < c->tmax) ++c->tstep;
   if (out) {
     if (out->spins) CU(cudaMemcpyAsync(out->spins, spins, ns * N, cudaMemcpyDeviceToDevice, st));
     if (out->logpsi) CU(cudaMemcpyAsync(out->logpsi, logpsi, ns * 16, cudaMemcpyDeviceToDevice, st));
@@ -392,6 +430,12 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
 }
 
 }  // namespace
+
+static void timing_free(nqs_ctx *c) {
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
+  c->tmax = c->tstep = 0;
+}
 
 // ===================================================================== ABI
 extern "C" {
@@ -454,6 +498,7 @@ nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int 
 nqs_status nqs_destroy(nqs_ctx *c) {
   if (!c) return NQS_ERR_ARG;
   cudaDeviceSynchronize();
+  timing_free(c);
   if (c->d_off) cudaFree(c->d_off);
   if (c->d_diag) cudaFree(c->d_diag);
   if (c->d_opf) cudaFree(c->d_opf);
@@ -538,7 +583,7 @@ nqs_status nqs_regularized_solve(nqs_ctx *c, double *T, int64_t R, double lambda
     k_shift<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(T, R, lambda);
     CU(cudaGetLastError());
   }
-  return chol_solve(T, R, b, x, dev_status, st);
+  return chol_solve(c, T, R, b, x, dev_status, st);
 }
 
 nqs_status nqs_minsr_step_ex(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
@@ -555,6 +600,48 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *c, double *theta, double *mom, const nqs_s
 nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
                           nqs_step_stats *stats, void *stream) {
   return nqs_minsr_step_ex(c, theta, mom, hp, stats, nullptr, stream);
+}
+
+const char *nqs_stage_name(int i) {
+  static const char *names[NQS_N_STAGES] = {"pack", "sample", "eloc_gen", "eloc_suffix",
+                                            "eloc_reduce", "energy", "jac_bwd", "jac_grad",
+                                            "center", "gram", "lambda", "cholesky", "solve",
+                                            "update"};
+  return (i >= 0 && i < NQS_N_STAGES) ? names[i] : nullptr;
+}
+
+nqs_status nqs_timing_begin(nqs_ctx *c, int max_steps) {
+  if (!c || max_steps <= 0 || max_steps > 100000) return NQS_ERR_ARG;
+  timing_free(c);
+  c->tev.resize((size_t)max_steps * (NQS_N_STAGES + 1));
+  for (auto &e : c->tev)
+    if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; timing_free(c); return NQS_ERR_CUDA; }
+  c->tmax = max_steps;
+  c->tstep = 0;
+  return NQS_OK;
+}
+
+nqs_status nqs_timing_end(nqs_ctx *c, double *stage_ms, int *n_steps) {
+  if (!c || !stage_ms || !n_steps) return NQS_ERR_ARG;
+  for (int i = 0; i < NQS_N_STAGES; ++i) stage_ms[i] = 0.0;
+  *n_steps = c->tstep;
+  for (int t = 0; t < c->tstep; ++t) {
+    cudaEvent_t *e = &c->tev[(size_t)t * (NQS_N_STAGES + 1)];
+    if (cudaEventSynchronize(e[NQS_N_STAGES]) != cudaSuccess) { timing_free(c); return NQS_ERR_CUDA; }
+    for (int i = 0; i < NQS_N_STAGES; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e[i], e[i + 1]) != cudaSuccess) { timing_free(c); return NQS_ERR_CUDA; }
+      stage_ms[i] += ms;
+    }
+  }
+  timing_free(c);
+  return NQS_OK;
+}
+
+nqs_status nqs_launch_count(const nqs_ctx *c, int64_t *n) {
+  if (!c || !n) return NQS_ERR_ARG;
+  *n = c->launches;
+  return NQS_OK;
 }
 
 const char *nqs_status_string(int s) {

@@ -51,10 +51,12 @@ class StepOutputs(C.Structure):
                 ("dtheta", C.c_void_p)]
 
 
+N_STAGES = 14
 SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_set_workspace", "nqs_sample", "nqs_logpsi", "nqs_local_energy",
            "nqs_jacobian", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
-           "nqs_minsr_step_ex", "nqs_status_string"]
+           "nqs_minsr_step_ex", "nqs_timing_begin", "nqs_timing_end", "nqs_launch_count",
+           "nqs_stage_name", "nqs_status_string"]
 
 
 def lib():
@@ -65,7 +67,8 @@ def lib():
                               "python -m paper_2608_18065_b300.build")
         _lib = C.CDLL(LIB_PATH)
         _lib.nqs_status_string.restype = C.c_char_p
-        for name in SYMBOLS[:-1]:
+        _lib.nqs_stage_name.restype = C.c_char_p
+        for name in SYMBOLS[:-2]:
             getattr(_lib, name).restype = C.c_int
     return _lib
 
@@ -203,6 +206,22 @@ class Context:
             _check(lib().nqs_minsr_step_ex(self._h, _ptr(theta), _ptr(mom), C.byref(hps),
                                            _ptr(stats), C.byref(o), _stream(stream)))
         return stats
+
+    # ------------------------------------------------------ instrumentation
+    def timing_begin(self, max_steps):
+        _check(lib().nqs_timing_begin(self._h, int(max_steps)))
+
+    def timing_end(self):
+        """{stage name: summed ms}, number of timed steps."""
+        ms = (C.c_double * N_STAGES)()
+        n = C.c_int()
+        _check(lib().nqs_timing_end(self._h, ms, C.byref(n)))
+        return {lib().nqs_stage_name(i).decode(): ms[i] for i in range(N_STAGES)}, n.value
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(lib().nqs_launch_count(self._h, C.byref(n)))
+        return n.value
 
     def step_outputs(self, ns):
         R = ns * self.rows_per_sample
