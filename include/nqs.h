@@ -205,6 +205,33 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
                              nqs_step_stats *dev_stats,
                              const nqs_step_outputs *out, void *stream);
 
+/* ------------------------------------------------- allocation-free log Psi */
+
+/* Size of the static device scratch array behind nqs_logpsi_noalloc. */
+#define NQS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* log Psi of n given configurations in FP64 without allocating any device
+ * memory and without a context -- the paper has no counterpart to this
+ * call; it exists for callers that cannot call cudaMalloc where they
+ * evaluate the wave function (a host framework whose pool owns the device,
+ * a plug-in limited to the memory it is handed, a loop where allocation and
+ * its implicit synchronisation are not allowed).
+ * model: as for nqs_create; theta: device [Np] FP64; spins: device [n*N]
+ * uint8; logpsi: device [n*2] FP64 (re, im), same values as nqs_logpsi of an
+ * NQS_PREC_FP64 context.  Scratch (the packed theta and the hidden-state
+ * cache, 8*(n*N*dh) bytes plus the packed weights) comes from one file-scope
+ * device array of NQS_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library reserves until the process exits; larger n returns
+ * NQS_ERR_WORKSPACE without launching anything (split the batch).  The first
+ * call on each device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array and leave their data in it: calls that
+ * overlap on the GPU (different streams, or graphs replayed concurrently)
+ * race on it and must be serialised by the caller. */
+nqs_status nqs_logpsi_noalloc(const nqs_model_desc *model, const double *theta,
+                              const uint8_t *spins, int64_t n, double *logpsi,
+                              void *stream);
+
 /* ------------------------------------------------------- instrumentation */
 
 /* Stages timed by the step instrumentation, in step order. */
