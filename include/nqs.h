@@ -238,7 +238,8 @@ nqs_status nqs_logpsi_noalloc(const nqs_model_desc *model, const double *theta,
 #define NQS_N_STAGES 14
 /* Name of stage i (static storage), NULL if out of range:
  * pack, sample, eloc_gen, eloc_suffix, eloc_reduce, energy, jac_bwd,
- * jac_grad, center, gram, lambda, cholesky, solve, update. */
+ * jac_grad, center, gram, lambda, cholesky (factorisation and both
+ * substitutions), solve (empty since they were fused), update. */
 const char *nqs_stage_name(int i);
 
 /* Start per-stage CUDA-event timing of the next max_steps calls of

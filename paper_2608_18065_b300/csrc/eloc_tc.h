@@ -1,0 +1,29 @@
+// eloc_tc.h -- tensor-core engine for the connected-configuration suffixes
+// (mixed precision, 1D chains, hidden size 64).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nqs {
+
+struct ElocTcArgs {
+  const float *pack;      // packed FP32 weights
+  int oWgT, oxw, obias, ohead, ohc;  // their offsets (PackOff)
+  const uint8_t *spins;   // [ns][N] samples
+  const float *hcache;    // [ns][N][64]
+  const float *lccache;   // [ns][N][2]
+  int N, cplx, zmask;
+  int64_t ns;
+  int tiles_per_op, ntiles;  // 128-row tiles per operator, total tiles
+  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site
+  const int *item_s;      // [n_off][ns] connected samples
+  const double *item_e;   // [n_off][ns] matrix elements
+  const int *item_cnt;    // [n_off]
+  double *contrib;        // [n_off][ns][2]
+  int *err;               // device status word
+};
+
+bool eloc_tc_supported(int dim, int dh);
+cudaError_t eloc_tc_run(const ElocTcArgs &args, int sm_count, cudaStream_t st);
+
+}  // namespace nqs

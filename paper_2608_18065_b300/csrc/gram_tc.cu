@@ -1,11 +1,377 @@
-// gram_tc.cu -- placeholder until the tcgen05 kernel is in.
+// gram_tc.cu -- T = A A^T (Algorithm 1 line 6, Eq. minsrR) for FP32 A with
+// split BF16x3 products on the 5th-generation tensor cores (sm_103a).
+//
+// A = hi + lo with hi = bf16(A), lo = bf16(A - hi); T ~ hi hi^T + hi lo^T +
+// lo hi^T with FP32 accumulation (the lo lo^T term is below the FP32
+// accumulation error).  Each CTA owns one 128x128 tile of the upper triangle
+// of T and one slice of the K = Np reduction:
+//   warp 0 lane 0  TMA producer: 4 operand tiles (hi/lo of the row block and
+//                  of the column block, 128 x 64 bf16 each, 128B swizzle)
+//                  per k-block into a 3-stage shared-memory ring;
+//   warp 1 lane 0  MMA issuer: 4 k-steps x 3 tcgen05.mma (M=N=128, K=16)
+//                  per k-block into one FP32 accumulator in tensor memory;
+//   warps 0-3      epilogue: tcgen05.ld of the accumulator rows, FP32
+//                  partial tile to global memory.
+// A second kernel sums the K-slices in FP64 and writes both triangles, so T
+// is deterministic and exactly symmetric.  Every mbarrier wait has an
+// iteration limit; on expiry the CTA raises an error flag, drains its own
+// copies and MMAs (again with a limit), frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
 #include "gram_tc.h"
+#include "tc_common.cuh"
 
 namespace nqs {
-bool gram_tc_available() { return false; }
-int gram_tc_launches() { return 0; }
-size_t gram_tc_split_bytes(int64_t, int64_t) { return 0; }
-cudaError_t gram_tc_bf16x3(const float *, int64_t, int64_t, double *, void *, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128;                    // tile edge (M = N)
+constexpr int BK = 64;                     // bf16 per k-block = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;    // 16 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;
+constexpr int THREADS = 128;
+constexpr int TMEM_COLS = 128;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+struct GramArgs {
+  int R, kblocks, splits, nT;
+  float *part;  // [tiles*splits][128][128]
+  int *err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_gram_bf16x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+              GramArgs g) {
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  unsigned char *gsm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + STAGES * STAGE_BYTES);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: done
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x / g.splits, split = blockIdx.x % g.splits;
+  // tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
+  int bi = 0, rem = t;
+  while (rem >= g.nT - bi) { rem -= g.nT - bi; ++bi; }
+  const int bj = bi + rem;
+  const int kb0 = (int)((int64_t)split * g.kblocks / g.splits);
+  const int kb1 = (int)((int64_t)(split + 1) * g.kblocks / g.splits);
+  const int nk = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------ TMA producer
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      if (!mbar_wait(smem_u32(&bars[STAGES + s]), ((i / STAGES) & 1) ^ 1)) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int *>(abort_flag)) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, STAGE_BYTES);
+      const uint32_t base = smem_u32(gsm + (size_t)s * STAGE_BYTES);
+      const int x = (kb0 + i) * BK;
+      tma_load_2d(base + 0 * TILE_BYTES, &tm_hi, full, x, bi * BM);
+      tma_load_2d(base + 1 * TILE_BYTES, &tm_lo, full, x, bi * BM);
+      tma_load_2d(base + 2 * TILE_BYTES, &tm_hi, full, x, bj * BM);
+      tma_load_2d(base + 3 * TILE_BYTES, &tm_lo, full, x, bj * BM);
+      ++issued;
+    }
+    // drain: every issued stage's copies have landed before the CTA may exit
+    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
+      if (!mbar_wait(smem_u32(&bars[i % STAGES]), (i / STAGES) & 1)) atomicExch(abort_flag, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------- MMA issuer
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      if (!mbar_wait(smem_u32(&bars[s]), (i / STAGES) & 1)) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int *>(abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(gsm + (size_t)s * STAGE_BYTES);
+      const uint64_t ah = sw128_desc(base), al = sw128_desc(base + TILE_BYTES);
+      const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES), bl = sw128_desc(base + 3 * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
+        constexpr uint32_t idesc = idesc_bf16(BM, BM);
+        mma_bf16(tmem, ah + adv, bh + adv, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, ah + adv, bl + adv, idesc, 1u);
+        mma_bf16(tmem, al + adv, bh + adv, idesc, 1u);
+      }
+      mma_commit(smem_u32(&bars[STAGES + s]));  // stage free once these MMAs finish
+    }
+    mma_commit(smem_u32(&bars[2 * STAGES]));    // accumulator complete
+  }
+  __syncwarp();
+  // ------------------------------------------------------------ epilogue
+  const bool done = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool ok = done && *reinterpret_cast<volatile int *>(abort_flag) == 0;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(g.err, (int)NQS_ERR_TIMEOUT);
+  } else {
+    const int row = warp * 32 + lane;
+    float *dst = g.part + ((size_t)t * g.splits + split) * BM * BM + (size_t)row * BM;
+#pragma unroll 1
+    for (int c = 0; c < BM / 16; ++c) {
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16);
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float4 *d4 = reinterpret_cast<float4 *>(dst + c * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        d4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
 }
+
+// Sum of the K-slices in FP64; T[i][j] and T[j][i] for i <= j.
+__global__ void k_gram_reduce(const float *__restrict__ part, int R, int splits, int nT,
+                              double *__restrict__ T) {
+  const int t = blockIdx.y;
+  int bi = 0, rem = t;
+  while (rem >= nT - bi) { rem -= nT - bi; ++bi; }
+  const int bj = bi + rem;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < BM * BM; e += gridDim.x * blockDim.x) {
+    const int r = e / BM, c = e % BM;
+    const int i = bi * BM + r, j = bj * BM + c;
+    if (i >= R || j >= R || j < i) continue;
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += (double)part[((size_t)t * splits + s) * BM * BM + e];
+    T[(size_t)i * R + j] = acc;
+    T[(size_t)j * R + i] = acc;
+  }
+}
+
+// hi = bf16(A), lo = bf16(A - hi); columns np..Kpad-1 are zero.
+__global__ void k_split_bf16(const float *__restrict__ A, int64_t R, int64_t np, int64_t Kpad,
+                             __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+  const int64_t tot = R * Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kpad, k = e - r * Kpad;
+    const float v = k < np ? A[r * np + k] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// Centring and split in one pass (Algorithm 1 line 5): v = (O - mean)/sqrt(Ns)
+// in FP64, hi = bf16(v), lo = bf16(v - hi); zero columns up to Kpad.
+__global__ void k_center_split(const float *__restrict__ O, int64_t ns, int64_t np, int64_t R,
+                               int64_t Kpad, const double *__restrict__ mean, __nv_bfloat16 *hi,
+                               __nv_bfloat16 *lo) {
+  const double isq = 1.0 / sqrt((double)ns);
+  const int64_t tot = R * Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kpad, k = e - r * Kpad;
+    double v = 0.0;
+    if (k < np) v = ((double)O[r * np + k] - mean[(r / ns) * np + k]) * isq;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi[e] = h;
+    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+// Partial sums of O'x from the split planes: part[c][p] = sum_{r in chunk c}
+// (hi + lo)[r][p] x[r], FP64 accumulation.
+__global__ void k_gemv_split_part(const __nv_bfloat16 *__restrict__ hi,
+                                  const __nv_bfloat16 *__restrict__ lo, int64_t R, int64_t np,
+                                  int64_t Kpad, const double *__restrict__ x, int rows_per,
+                                  double *part) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+  const int64_t r1 = min64(R, r0 + rows_per);
+  double acc = 0.0;
+  for (int64_t r = r0; r < r1; ++r)
+    acc += ((double)__bfloat162float(hi[r * Kpad + p]) + (double)__bfloat162float(lo[r * Kpad + p])) * x[r];
+  part[(int64_t)blockIdx.y * np + p] = acc;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int64_t R, int64_t Kpad) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)R};
+  cuuint64_t strides[1] = {(cuuint64_t)Kpad * 2};
+  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t kpad_of(int64_t np) { return (np + BK - 1) / BK * BK; }
+
+void plan(int64_t R, int64_t np, int sms, int *nT, int *tiles, int *kblocks, int *splits) {
+  *nT = (int)((R + BM - 1) / BM);
+  *tiles = *nT * (*nT + 1) / 2;
+  *kblocks = (int)(kpad_of(np) / BK);
+  int s = (2 * sms + *tiles - 1) / *tiles;  // about two CTAs per SM
+  if (s > *kblocks / 4) s = *kblocks / 4;
+  if (s < 1) s = 1;
+  *splits = s;
+}
+
+int g_sms = 0;
+int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 148;
+  }
+  return g_sms;
+}
+
+}  // namespace
+
+bool gram_tc_available() {
+  static int avail = -1;
+  if (avail < 0) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return avail == 1;
+}
+
+int gram_tc_launches() { return 3; }
+
+size_t gram_tc_split_bytes(int64_t R, int64_t np) {
+  // any plan with R' <= R, np' <= np has tiles' * splits' <= tiles + 2 * SMs
+  int nT, tiles, kb, splits;
+  plan(R, np, sm_count(), &nT, &tiles, &kb, &splits);
+  const size_t hl = 2 * (size_t)R * kpad_of(np) * 2;
+  const size_t part = ((size_t)tiles + 2 * (size_t)sm_count()) * BM * BM * 4;
+  return ((hl + 255) & ~size_t(255)) + part + 256;
+}
+
+int64_t gram_tc_kpad(int64_t np) { return kpad_of(np); }
+
+cudaError_t gram_tc_from_split(const void *hi, const void *lo, int64_t R, int64_t np, double *T,
+                               void *scratch_part, int *err, cudaStream_t st) {
+  int nT, tiles, kb, splits;
+  plan(R, np, sm_count(), &nT, &tiles, &kb, &splits);
+  const int64_t Kpad = kpad_of(np);
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, hi, R, Kpad) || !make_map(&ml, lo, R, Kpad)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  GramArgs g{(int)R, kb, splits, nT, static_cast<float *>(scratch_part), err};
+  k_gram_bf16x3<<<tiles * splits, THREADS, SMEM_BYTES, st>>>(mh, ml, g);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gram_reduce<<<dim3(16, tiles), 256, 0, st>>>(static_cast<float *>(scratch_part), (int)R, splits,
+                                                 nT, T);
+  return cudaGetLastError();
+}
+
+cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const double *mean,
+                         void *scratch, cudaStream_t st) {
+  const int64_t Kpad = kpad_of(np);
+  __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(scratch);
+  __nv_bfloat16 *lo = hi + R * Kpad;
+  const int blocks = (int)min64((R * Kpad + 255) / 256, 148 * 32);
+  k_center_split<<<blocks, 256, 0, st>>>(O, ns, np, R, Kpad, mean, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_split(const void *scratch, int64_t R, int64_t np, const double *x, int rows_per,
+                       double *part, cudaStream_t st) {
+  const int64_t Kpad = kpad_of(np);
+  const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(scratch);
+  const __nv_bfloat16 *lo = hi + R * Kpad;
+  dim3 g((unsigned)((np + 255) / 256), (unsigned)((R + rows_per - 1) / rows_per));
+  k_gemv_split_part<<<g, 256, 0, st>>>(hi, lo, R, np, Kpad, x, rows_per, part);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_from_center_split(const void *scratch, int64_t R, int64_t np, double *T, int *err,
+                                   cudaStream_t st) {
+  const int64_t Kpad = kpad_of(np);
+  const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(scratch);
+  const __nv_bfloat16 *lo = hi + R * Kpad;
+  const size_t hl = 2 * (size_t)R * Kpad * 2;
+  void *part = static_cast<char *>(const_cast<void *>(scratch)) + ((hl + 255) & ~size_t(255));
+  return gram_tc_from_split(hi, lo, R, np, T, part, err, st);
+}
+
+cudaError_t gram_tc_bf16x3(const float *A, int64_t R, int64_t np, double *T, void *scratch,
+                           int *err, cudaStream_t st) {
+  const int64_t Kpad = kpad_of(np);
+  __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(scratch);
+  __nv_bfloat16 *lo = hi + R * Kpad;
+  const size_t hl = 2 * (size_t)R * Kpad * 2;
+  void *part = static_cast<char *>(scratch) + ((hl + 255) & ~size_t(255));
+  const int64_t tot = R * Kpad;
+  const int blocks = (int)min64((tot + 255) / 256, 148 * 32);
+  k_split_bf16<<<blocks, 256, 0, st>>>(A, R, np, Kpad, hi, lo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return gram_tc_from_split(hi, lo, R, np, T, part, err, st);
+}
+
 }  // namespace nqs

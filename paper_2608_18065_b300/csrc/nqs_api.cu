@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include "chol_coop.cuh"
+#include "eloc_tc.h"
 #include "gram_tc.h"
 #include "launch.h"
 #include "stages.cuh"
@@ -17,7 +19,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, total;
 };
 
 }  // namespace
@@ -149,6 +151,10 @@ void carve(nqs_ctx *c) {
   o.frob = take(1024 * 8);
   o.sstat = take(64);
   o.split = take(gram_tc_split_bytes(R, np));
+  o.crhs = take(R * 8);
+  o.cy = take(R * 8);
+  o.cpart = take((size_t)2 * c->rd.sm_count * CC_B * 8);
+  o.cbar = take(64);
   o.total = p;
 }
 
@@ -223,7 +229,25 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
     a.contrib = W<double>(c, c->off.contrib);
     a.colbuf = W<T>(c, c->off.colbuf);
     mark(c, 3, st);
-    CU(run_forward<T>(c->rd, MODE_ELOC, a, c->eloc_grid, st));
+    if (f32(c) && gram_tc_available() && eloc_tc_supported(c->L.dim, c->L.dh)) {
+      // tensor-core engine: 128-row tiles
+      ElocTcArgs e{};
+      e.pack = reinterpret_cast<const float *>(a.pack);
+      e.oWgT = (int)c->P.WgT; e.oxw = (int)c->P.xw; e.obias = (int)c->P.bias;
+      e.ohead = (int)c->P.head; e.ohc = (int)c->P.hc;
+      e.spins = spins;
+      e.hcache = reinterpret_cast<const float *>(a.hcache);
+      e.lccache = reinterpret_cast<const float *>(a.lccache);
+      e.N = c->L.N; e.cplx = c->L.cplx; e.zmask = c->L.zmask; e.ns = ns;
+      e.tiles_per_op = (int)((ns + 127) / 128);
+      e.ntiles = e.tiles_per_op * c->n_off;
+      e.op_f = c->d_opf; e.item_s = a.item_s; e.item_e = a.item_e; e.item_cnt = a.item_cnt;
+      e.contrib = a.contrib;
+      e.err = W<int>(c, c->off.sstat);
+      CU(eloc_tc_run(e, c->rd.sm_count, st));
+    } else {
+      CU(run_forward<T>(c->rd, MODE_ELOC, a, c->eloc_grid, st));
+    }
   } else {
     mark(c, 3, st);
   }
@@ -271,7 +295,7 @@ nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
   if (f32(c)) {
     if (gram_tc_available())
       return cu(gram_tc_bf16x3(reinterpret_cast<const float *>(A), R, np, T,
-                               c->ws + c->off.split, st));
+                               c->ws + c->off.split, W<int>(c, c->off.sstat) + 1, st));
     dim3 g((unsigned)((R + 63) / 64), (unsigned)((R + 63) / 64));
     k_gram_simt<float, float><<<g, 256, 0, st>>>(reinterpret_cast<const float *>(A), R, np, T);
   } else {
@@ -317,28 +341,29 @@ __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int np
   for (int64_t i = threadIdx.x; i < R; i += blockDim.x) T[i * R + i] += lam_s;
 }
 
-// Cholesky of the shifted T in place, then x = (T + lambda I)^{-1} b.
+// Cholesky of the shifted T in place, then x = (T + lambda I)^{-1} b: one
+// cooperative launch over all SMs (chol_coop.cuh).
 nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double *x,
                       int32_t *status, cudaStream_t st) {
-  const int np_ = (int)((R + CB - 1) / CB);
-  c->launches += 2 * np_;  // panels, trailing updates (np_ - 1) and the solve
-  for (int p = 0; p < np_; ++p) {
-    const int rows = np_ - p;
-    k_chol_panel<<<rows, 256, 0, st>>>(T, R, p, status);
-    CU(cudaGetLastError());
-    const int64_t trail = R - (int64_t)(p + 1) * CB;
-    if (trail > 0) {
-      const unsigned t = (unsigned)((trail + 63) / 64);
-      k_chol_update<<<dim3(t, t), 256, 0, st>>>(T, R, p, status);
-      CU(cudaGetLastError());
-    }
-  }
-  const size_t smem = (size_t)R * 8;
-  if (smem > 48 * 1024)
-    CU(cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CholCoopArgs a;
+  a.A = T; a.n = R; a.b = b; a.x = x;
+  a.rhs = W<double>(c, c->off.crhs);
+  a.y = W<double>(c, c->off.cy);
+  a.part = W<double>(c, c->off.cpart);
+  a.bar = W<unsigned>(c, c->off.cbar);
+  a.status = status;
+  CU(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st));
+  const size_t smem = chol_coop_smem(R);
+  CU(cudaFuncSetAttribute(k_chol_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop, CC_THREADS, smem));
+  if (per < 1) return NQS_ERR_UNSUPPORTED;
+  const int G = c->rd.sm_count;
+  void *args[] = {&a};
+  c->launches += 1;
+  CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
   mark(c, 12, st);
-  k_chol_solve<<<1, 1024, smem, st>>>(T, R, b, x, status);
-  return cu(cudaGetLastError());
+  return NQS_OK;
 }
 
 template <typename T>
@@ -369,19 +394,32 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   // line 5: O, centred over samples per block, / sqrt(Ns)
   ST(jac_T<T>(c, ns, spins, O, st));
   mark(c, 8, st);
+  // tensor-core route of the mixed path: centring writes the BF16 hi/lo
+  // planes that the Gram and O'x read; otherwise O is centred in place
+  const bool tc = f32(c) && gram_tc_available();
   {
     c->launches += 2;
     dim3 g((unsigned)((np + 255) / 256), c->L.cplx ? 2u : 1u);
     k_colmean<T><<<g, 256, 0, st>>>(O, ns, np, W<double>(c, c->off.mean));
     CU(cudaGetLastError());
-    const int64_t tot = R * np;
-    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
-    k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
-    CU(cudaGetLastError());
+    if (tc) {
+      CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<double>(c, c->off.mean),
+                      c->ws + c->off.split, st));
+    } else {
+      const int64_t tot = R * np;
+      const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+      k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
+      CU(cudaGetLastError());
+    }
   }
   // line 6: T = O'^T O'
   mark(c, 9, st);
-  ST(gram_any(c, O, R, np, Tm, st));
+  if (tc) {
+    c->launches += 2;
+    CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, sstat, st));
+  } else {
+    ST(gram_any(c, O, R, np, Tm, st));
+  }
   mark(c, 10, st);
   if (out && out->T) CU(cudaMemcpyAsync(out->T, Tm, R * R * 8, cudaMemcpyDeviceToDevice, st));
   // lambda and shift
@@ -407,7 +445,10 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     const int rows_per = 64;
     const int nparts = (int)((R + rows_per - 1) / rows_per);
     dim3 g((unsigned)((np + 255) / 256), (unsigned)nparts);
-    k_gemv_part<T><<<g, 256, 0, st>>>(O, R, np, x, rows_per, W<double>(c, c->off.part));
+    if (tc)
+      CU(gemv_split(c->ws + c->off.split, R, np, x, rows_per, W<double>(c, c->off.part), st));
+    else
+      k_gemv_part<T><<<g, 256, 0, st>>>(O, R, np, x, rows_per, W<double>(c, c->off.part));
     k_dtheta<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts, np,
                                                           stats, W<double>(c, c->off.dth));
     // lines 8-9: momentum and update (skipped unless status is OK)
@@ -577,6 +618,8 @@ nqs_status nqs_gram(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
 nqs_status nqs_regularized_solve(nqs_ctx *c, double *T, int64_t R, double lambda, const double *b,
                                  double *x, int32_t *dev_status, void *stream) {
   if (!c || !T || !b || !x || !dev_status || R <= 0 || !(lambda >= 0.0)) return NQS_ERR_ARG;
+  if (R > (c->L.cplx ? 2 * c->max_ns : c->max_ns)) return NQS_ERR_ARG;
+  ST(need_ws(c));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), st));
   if (lambda != 0.0) {

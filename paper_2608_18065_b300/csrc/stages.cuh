@@ -224,165 +224,6 @@ __global__ void k_lambda(double *T, int64_t R, int mode, double lam_c, double co
   if (threadIdx.x == 0) { st->normT = nT; st->lambda = lam; }
 }
 
-// ------------------------------------------------------ FP64 Cholesky
-// Right-looking blocked Cholesky of the lower triangle, panel width 32.
-// k_chol_panel: CTA b (row block p + b) factors the diagonal block in
-// shared memory (every CTA redundantly) and writes L_pp (b = 0) or the
-// panel block L_ip = A_ip L_pp^{-T} (b > 0).
-constexpr int CB = 32;
-
-__global__ void __launch_bounds__(256) k_chol_panel(double *A, int64_t n, int p, int32_t *status) {
-  __shared__ double D[CB][CB + 1];
-  __shared__ double Bk[CB][CB + 1];
-  const int64_t c0 = (int64_t)p * CB;
-  const int nb = (int)min64(CB, n - c0);
-  const int tid = threadIdx.x;
-  if (*status != 0) return;
-  for (int e = tid; e < CB * CB; e += 256) {
-    const int i = e / CB, j = e % CB;
-    D[i][j] = (i < nb && j < nb) ? A[(c0 + i) * n + c0 + j] : (i == j ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  // unblocked Cholesky of D (lower), column by column
-  for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      double d = D[j][j];
-      D[j][j] = d > 0.0 ? sqrt(d) : -1.0;
-    }
-    __syncthreads();
-    const double djj = D[j][j];
-    if (!(djj > 0.0)) {
-      if (tid == 0 && blockIdx.x == 0) atomicExch(reinterpret_cast<int *>(status), (int)NQS_ERR_NOT_SPD);
-      return;
-    }
-    if (tid > j && tid < nb) D[tid][j] /= djj;
-    __syncthreads();
-    for (int e = tid; e < nb * nb; e += 256) {
-      const int i = e / nb, k = e % nb;
-      if (k > j && i >= k) D[i][k] -= D[i][j] * D[k][j];
-    }
-    __syncthreads();
-  }
-  const int b = blockIdx.x;
-  if (b == 0) {
-    for (int e = tid; e < nb * nb; e += 256) {
-      const int i = e / nb, j = e % nb;
-      if (j <= i) A[(c0 + i) * n + c0 + j] = D[i][j];
-    }
-    return;
-  }
-  const int64_t r0 = c0 + (int64_t)b * CB;
-  const int nr = (int)min64(CB, n - r0);
-  for (int e = tid; e < CB * CB; e += 256) {
-    const int i = e / CB, j = e % CB;
-    Bk[i][j] = (i < nr && j < nb) ? A[(r0 + i) * n + c0 + j] : 0.0;
-  }
-  __syncthreads();
-  // row i of L_ip solves L_pp x^T = a^T (forward substitution); one thread per row
-  if (tid < nr) {
-    for (int j = 0; j < nb; ++j) {
-      double v = Bk[tid][j];
-      for (int k = 0; k < j; ++k) v -= Bk[tid][k] * D[j][k];
-      Bk[tid][j] = v / D[j][j];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < nr * nb; e += 256) {
-    const int i = e / nb, j = e % nb;
-    A[(r0 + i) * n + c0 + j] = Bk[i][j];
-  }
-}
-
-// Trailing update A_ij -= L_ip L_jp^T for the lower tiles (64x64) right of
-// panel p.
-__global__ void __launch_bounds__(256) k_chol_update(double *A, int64_t n, int p, const int32_t *status) {
-  if (*status != 0) return;
-  const int64_t c0 = (int64_t)p * CB, t0 = c0 + CB;
-  const int64_t i0 = t0 + (int64_t)blockIdx.y * 64, j0 = t0 + (int64_t)blockIdx.x * 64;
-  if (j0 > i0 + 63 || i0 >= n || j0 >= n) return;
-  __shared__ double La[CB][64 + 1], Lb[CB][64 + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  for (int e = tid; e < 64 * CB; e += 256) {
-    const int r = e / CB, k = e % CB;
-    La[k][r] = (i0 + r < n) ? A[(i0 + r) * n + c0 + k] : 0.0;
-    Lb[k][r] = (j0 + r < n) ? A[(j0 + r) * n + c0 + k] : 0.0;
-  }
-  __syncthreads();
-  double acc[4][4] = {};
-#pragma unroll 4
-  for (int k = 0; k < CB; ++k) {
-    double a[4], b[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { a[q] = La[k][ty + 16 * q]; b[q] = Lb[k][tx + 16 * q]; }
-#pragma unroll
-    for (int pp = 0; pp < 4; ++pp)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[pp][q] = fma(a[pp], b[q], acc[pp][q]);
-  }
-#pragma unroll
-  for (int pp = 0; pp < 4; ++pp)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = i0 + ty + 16 * pp, j = j0 + tx + 16 * q;
-      if (i < n && j < n && j <= i) A[i * n + j] -= acc[pp][q];
-    }
-}
-
-// Forward and backward substitution with the factor (lower triangle of A):
-// L y = b, then L^T x = y.  One CTA of 1024 threads; 32-wide blocks, the
-// diagonal block solved by warp 0, the rest updated by all threads.
-__global__ void __launch_bounds__(1024) k_chol_solve(const double *__restrict__ A, int64_t n,
-                                                     const double *__restrict__ b, double *x,
-                                                     const int32_t *status) {
-  extern __shared__ double sx[];  // n
-  if (*status != 0) return;
-  const int tid = threadIdx.x;
-  for (int64_t i = tid; i < n; i += blockDim.x) sx[i] = b[i];
-  __syncthreads();
-  // forward: L y = b
-  for (int64_t c0 = 0; c0 < n; c0 += 32) {
-    const int nb = (int)min64(32, n - c0);
-    if (tid < 32) {
-      double v = tid < nb ? sx[c0 + tid] : 0.0;
-      for (int j = 0; j < nb; ++j) {
-        double yj = __shfl_sync(0xffffffffu, v / A[(c0 + j) * n + c0 + j], j);
-        if (tid == j) v = yj;
-        if (tid > j && tid < nb) v -= A[(c0 + tid) * n + c0 + j] * yj;
-      }
-      if (tid < nb) sx[c0 + tid] = v;
-    }
-    __syncthreads();
-    for (int64_t i = c0 + nb + tid; i < n; i += blockDim.x) {
-      double v = 0.0;
-      for (int j = 0; j < nb; ++j) v += A[i * n + c0 + j] * sx[c0 + j];
-      sx[i] -= v;
-    }
-    __syncthreads();
-  }
-  // backward: L^T x = y
-  for (int64_t c1 = n; c1 > 0; c1 -= 32) {
-    const int nb = (int)min64(32, c1);
-    const int64_t c0 = c1 - nb;
-    if (tid < 32) {
-      double v = tid < nb ? sx[c0 + tid] : 0.0;
-      for (int j = nb - 1; j >= 0; --j) {
-        double xj = __shfl_sync(0xffffffffu, v / A[(c0 + j) * n + c0 + j], j);
-        if (tid == j) v = xj;
-        if (tid < j) v -= A[(c0 + j) * n + c0 + tid] * xj;
-      }
-      if (tid < nb) sx[c0 + tid] = v;
-    }
-    __syncthreads();
-    for (int64_t i = tid; i < c0; i += blockDim.x) {
-      double v = 0.0;
-      for (int j = 0; j < nb; ++j) v += A[(c0 + j) * n + i] * sx[c0 + j];
-      sx[i] -= v;
-    }
-    __syncthreads();
-  }
-  for (int64_t i = tid; i < n; i += blockDim.x) x[i] = sx[i];
-}
-
 // tau = eps - lambda x (App. F), ||tau||, eta_t = eta0/(1+t/decay_T) and
 // eta* = eta_t/||tau|| in trust-region mode.
 __global__ void k_eta(const double *__restrict__ eps, const double *__restrict__ x, int64_t R,

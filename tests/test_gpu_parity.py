@@ -109,10 +109,10 @@ def test_gram(prec, R, np_):
     assert np.array_equal(T, T.T)
 
 
-@pytest.mark.parametrize("R", [1, 31, 64, 200, 513])
+@pytest.mark.parametrize("R", [1, 31, 64, 200, 513, 600])
 def test_regularized_solve(R):
     model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
-    c = ctx(model, ham, "fp64", 8)
+    c = ctx(model, ham, "fp64", 600)
     rng = np.random.default_rng(R)
     M = rng.standard_normal((R, R + 5))
     T = M @ M.T
@@ -196,3 +196,27 @@ def test_minsr_step_mixed_error_report(model, ham, hp):
     T = outs["T"].cpu().numpy()
     assert np.max(np.abs(T - b["T"])) < 1e-3 * np.max(np.abs(b["T"]))
     assert rel_err(outs["dtheta"].cpu().numpy(), b["dtheta"]) < 5e-2
+
+
+# hidden size 64 on 1D chains takes the tensor-core connected-configuration
+# engine in the mixed path; 300 samples = two full 128-row tiles + a ragged one
+TC_MODELS = [
+    (ModelSpec(1, 24, 1, 64), HamSpec("tfim", J=1.0, h=0.8)),
+    (ModelSpec(1, 20, 1, 64, cplx=1), HamSpec("cluster_zxz")),
+    (ModelSpec(1, 18, 1, 64, cplx=1), HamSpec("cluster_paper")),
+    (ModelSpec(1, 16, 1, 64, zmask=1), HamSpec("tfim")),
+]
+
+
+@pytest.mark.parametrize("model,ham", TC_MODELS, ids=["tfim24", "zxz20", "xzx18", "tfim16mask"])
+def test_eloc_tensor_core_engine_mixed(model, ham):
+    ns = 300
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 4)
+    sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    el = cplx(c.local_energy(thd, spd))
+    assert rel_err(el, O.local_energy(model, ham, th, sp)) < TOL_MIXED_ELOC
+    # the FP64 context (SIMT engine) agrees with the oracle to 1e-10
+    c64 = ctx(model, ham, "fp64", ns)
+    assert rel_err(cplx(c64.local_energy(thd, spd)), O.local_energy(model, ham, th, sp)) < RTOL64
