@@ -106,7 +106,9 @@ typedef struct {
   double eta_eff;      /* eta_t or eta* */
   double tau_norm;     /* ||tau|| */
   int32_t status;      /* nqs_status of the device-side checks */
-  int32_t pad;
+  int32_t solve_fp64;  /* 1: x came from the FP64 Cholesky factorisation (FP64
+                          context, or fallback of the mixed context); 0: from
+                          FP64 iterative refinement on an FP32 factor */
 } nqs_step_stats;
 
 /* Optional device outputs of nqs_minsr_step_ex (any pointer may be NULL). */
@@ -184,9 +186,14 @@ nqs_status nqs_jacobian(nqs_ctx *ctx, const double *theta, const uint8_t *spins,
 nqs_status nqs_gram(nqs_ctx *ctx, const void *A, int64_t R, int64_t np,
                     double *T, void *stream);
 
-/* Solve (T + lambda I) x = b by FP64 Cholesky (Eq. minsrR).  T device
- * [R*R] FP64 is overwritten by its factor; b, x device [R].  *dev_status
- * (device int32) receives 0 or NQS_ERR_NOT_SPD. */
+/* Solve (T + lambda I) x = b (Eq. minsrR) to FP64 accuracy.  FP64 context:
+ * FP64 Cholesky and substitutions.  Mixed context: FP32 Cholesky factor and
+ * FP64 iterative refinement until ||r||_inf <= sqrt(R) u64 ||A||_inf
+ * ||x||_inf, falling back to the FP64 Cholesky if the FP32 factorisation
+ * breaks down or the refinement does not converge in 12 sweeps.  T device
+ * [R*R] FP64 (both triangles) may be overwritten; b, x device [R].
+ * *dev_status (device int32) receives 0, NQS_ERR_NOT_SPD or
+ * NQS_ERR_TIMEOUT.  R <= the context's largest R. */
 nqs_status nqs_regularized_solve(nqs_ctx *ctx, double *T, int64_t R,
                                  double lambda, const double *b, double *x,
                                  int32_t *dev_status, void *stream);

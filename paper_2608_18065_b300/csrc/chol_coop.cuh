@@ -37,6 +37,7 @@ struct CholCoopArgs {
   double *part;       // [2][gridDim][32] scratch: backward partial sums
   unsigned *bar;      // [2] barrier counter and generation (zeroed before launch)
   int32_t *status;    // 0, NQS_ERR_NOT_SPD or NQS_ERR_TIMEOUT
+  const int32_t *gate;// optional: run only when *gate != 0
 };
 
 // Grid-wide barrier with a bounded spin.  Returns false if any CTA failed.
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
   double *tb = ta + CC_T * TS;                       // [16][33] update tile rows j
   double *xs = tb + CC_T * TS;                       // [n] backward solution copy
 
+  if (a.gate && *a.gate == 0) return;  // the refinement already produced x
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x, g = blockIdx.x;
   const int64_t n = a.n;
@@ -93,34 +95,41 @@ __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
   for (int p = 0; p < nb; ++p) {
     const int64_t c0 = (int64_t)p * CC_B;
     const int m = (int)min64(CC_B, n - c0);
-    // (1) diagonal block: load, factor (right-looking, in shared memory)
-    for (int e = tid; e < CC_B * CC_B; e += CC_THREADS) {
-      const int i = e / CC_B, j = e % CC_B;
-      D[i][j] = (i < m && j <= i) ? A[(c0 + i) * n + c0 + j] : 0.0;
+    // (1) diagonal block, factored by warp 0 in registers: lane i holds row i;
+    //     per pivot one rsqrt on its own lane, the rank-1 update by shuffles.
+    __shared__ int bad_s;
+    if (warp == 0) {
+      double r[CC_B];
+#pragma unroll
+      for (int k = 0; k < CC_B; ++k)
+        r[k] = (lane < m && k < m && k <= lane) ? A[(c0 + lane) * n + c0 + k]
+                                                : (k == lane ? 1.0 : 0.0);
+      int bad = 0;
+#pragma unroll
+      for (int j = 0; j < CC_B; ++j) {
+        if (j < m) {
+          const double dj = __shfl_sync(0xffffffffu, r[j], j);
+          bad |= !(dj > 0.0);
+          double inv = 0.0;
+          if (lane == j && dj > 0.0) inv = rsqrt(dj);
+          inv = __shfl_sync(0xffffffffu, inv, j);
+          if (lane == j) { r[j] = dj * inv; rinv[j] = inv; }
+          else if (lane > j) r[j] *= inv;
+#pragma unroll
+          for (int k = j + 1; k < CC_B; ++k) {
+            const double lkj = __shfl_sync(0xffffffffu, r[j], k);
+            if (lane >= k) r[k] -= r[j] * lkj;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < CC_B; ++k) D[lane][k] = (k <= lane) ? r[k] : 0.0;
+      if (lane == 0) bad_s = bad;
     }
     __syncthreads();
-    // FP64 sqrt and division are multi-instruction sequences on a slow unit:
-    // one thread computes them, the others read the result.
-    for (int j = 0; j < m; ++j) {
-      if (tid == 0) {
-        const double d = D[j][j];
-        const double s = d > 0.0 ? sqrt(d) : 0.0;
-        D[j][j] = s;
-        rinv[j] = d > 0.0 ? 1.0 / s : 0.0;
-      }
-      __syncthreads();
-      if (!(D[j][j] > 0.0)) {  // identical in every CTA
-        if (g == 0 && tid == 0) atomicExch(reinterpret_cast<int *>(a.status), (int)NQS_ERR_NOT_SPD);
-        return;
-      }
-      if (tid > j && tid < m) D[tid][j] *= rinv[j];
-      __syncthreads();
-      const int w = m - j - 1;  // trailing size
-      for (int e = tid; e < w * w; e += CC_THREADS) {
-        const int i = j + 1 + e / w, k = j + 1 + e % w;
-        if (k <= i) D[i][k] -= D[i][j] * D[k][j];
-      }
-      __syncthreads();
+    if (bad_s) {  // identical in every CTA
+      if (g == 0 && tid == 0) atomicExch(reinterpret_cast<int *>(a.status), (int)NQS_ERR_NOT_SPD);
+      return;
     }
     // forward substitution of the block: L_pp y_p = rhs_p (warp 0)
     if (warp == 0) {
@@ -163,8 +172,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
       const int nt = (int)((tr + CC_T - 1) / CC_T);
       const int ntiles = nt * (nt + 1) / 2;
       for (int t = g; t < ntiles; t += G) {
-        // t -> (ti, tj), tj <= ti, row-major over the lower triangle
-        int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        // t -> (ti, tj), tj <= ti, row-major over the lower triangle (FP32
+        // estimate, integer correction: no FP64 on this path)
+        int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
         while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
         while (ti * (ti + 1) / 2 > t) --ti;
         const int tj = t - ti * (ti + 1) / 2;
@@ -206,15 +216,21 @@ __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
       part[(size_t)g * CC_B + tid] = s;
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
+    // diagonal block of L into shared memory for the substitution
+    for (int e = tid; e < CC_B * CC_B; e += CC_THREADS) {
+      const int i = e / CC_B, j = e % CC_B;
+      D[i][j] = (i < m && j <= i) ? A[(c0 + i) * n + c0 + j] : 0.0;
+    }
+    __syncthreads();
     if (warp == 0) {
       double s = 0.0;
       for (int q = 0; q < G; ++q) s += part[(size_t)q * CC_B + lane];
       double v = lane < m ? a.y[c0 + lane] - s : 0.0;
-      const double dinv = lane < m ? 1.0 / A[(c0 + lane) * n + c0 + lane] : 0.0;
+      const double dinv = lane < m ? 1.0 / D[lane][lane] : 0.0;
       for (int k = m - 1; k >= 0; --k) {
         if (lane == k) v *= dinv;
         const double xk = __shfl_sync(0xffffffffu, v, k);
-        if (lane < k) v -= A[(c0 + k) * n + c0 + lane] * xk;
+        if (lane < k) v -= D[k][lane] * xk;
       }
       if (lane < m) {
         xs[c0 + lane] = v;

@@ -1,0 +1,331 @@
+// chol_ir.cuh -- (T + lambda I) x = eps' (Eq. minsrR) to FP64 accuracy by
+// iterative refinement on an FP32 Cholesky factor, one cooperative launch
+// (sm_103a).
+//
+// B300's FP64 unit retires two lane-FMAs per clock per SM, 64x below FP32,
+// and a Cholesky of this size is a chain of n dependent pivots; so the
+// factor is computed in FP32 (same right-looking panel scheme as the FP64
+// kernel: redundant warp-level diagonal blocks, grid-wide panel rows,
+// trailing update in 32x32 tiles) and the solution is refined in FP64:
+//   x_0 = 0, r_0 = b;  d = L^{-T} (L^{-1} r) (FP32);  x += d;
+//   r = b - A x in FP64 on all SMs;  stop when the backward error satisfies
+//   ||r||_inf <= sqrt(n) u64 ||A||_inf ||x||_inf  (LAPACK's dsposv test).
+// Substitutions are a chain of dependent steps; instead the inverse L^{-1}
+// is formed once by recursive doubling (32x32 diagonal blocks inverted in
+// parallel, then per level X21 = -L22^{-1} (L21 L11^{-1}) as two tiled
+// products over all SMs), and each sweep is two distributed products.
+// A non-positive FP32 pivot, or no convergence within maxit sweeps, sets
+// *need_fp64 and leaves x to the FP64 Cholesky that the host launches next
+// (it returns at once when *need_fp64 is 0).  Grid barriers are bounded.
+#pragma once
+#include "chol_coop.cuh"
+
+namespace nqs {
+
+constexpr int IR_B = 32;
+constexpr int IR_THREADS = 256;
+
+struct CholIrArgs {
+  const double *A;   // [n][n], both triangles: T + lambda I (not modified)
+  int64_t n;
+  const double *b;   // [n]
+  double *x;         // [n] out
+  float *L;          // [n][n] scratch: FP32 factor (lower triangle)
+  float *Li;         // [n][n] scratch: FP32 inverse of the factor (lower)
+  float *Tm;         // [n][n] scratch: products of the inversion levels
+  float *wv;         // [n] scratch: L^{-1} r
+  float *dpart;      // [chunks][n] scratch: partial sums of L^{-T} w
+  double *r;         // [n] scratch: FP64 residual
+  double *part;      // [gridDim][4] scratch: partial norms
+  unsigned *bar;     // [2] barrier words (zeroed before launch)
+  int32_t *status;   // NQS_ERR_TIMEOUT on a barrier timeout
+  int32_t *need_fp64;// out: 1 when the FP64 factorisation must run
+  int maxit;
+};
+
+__global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
+  extern __shared__ float ir_smem[];
+  float (*D)[IR_B + 1] = reinterpret_cast<float (*)[IR_B + 1]>(ir_smem);  // [32][33]
+  float *rinv = ir_smem + IR_B * (IR_B + 1);          // [32]
+  constexpr int TS = IR_B + 1;
+  float *ta = rinv + IR_B;                             // [32][33] tile rows i
+  float *tb = ta + IR_B * TS;                          // [32][33] tile rows j
+  __shared__ int flag_s;
+  __shared__ double red_s[IR_THREADS / 32][3];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int64_t n = a.n;
+  const int nb = (int)((n + IR_B - 1) / IR_B);
+  float *L = a.L;
+
+  // (0) FP32 copy of the lower triangle
+  for (int64_t e = (int64_t)g * IR_THREADS + tid; e < n * n; e += (int64_t)G * IR_THREADS) {
+    const int64_t i = e / n, j = e - i * n;
+    if (j <= i) L[e] = (float)a.A[e];
+  }
+  if (!cc_grid_sync(a.bar, a.status)) return;
+
+  // (1) FP32 right-looking Cholesky
+  for (int p = 0; p < nb; ++p) {
+    const int64_t c0 = (int64_t)p * IR_B;
+    const int m = (int)min64(IR_B, n - c0);
+    if (warp == 0) {
+      float rr[IR_B];
+#pragma unroll
+      for (int k = 0; k < IR_B; ++k)
+        rr[k] = (lane < m && k < m && k <= lane) ? L[(c0 + lane) * n + c0 + k]
+                                                 : (k == lane ? 1.f : 0.f);
+      int bad = 0;
+#pragma unroll
+      for (int j = 0; j < IR_B; ++j) {
+        if (j < m) {
+          const float dj = __shfl_sync(0xffffffffu, rr[j], j);
+          bad |= !(dj > 0.f);
+          const float inv = dj > 0.f ? rsqrtf(dj) : 0.f;
+          if (lane == j) { rr[j] = dj * inv; rinv[j] = inv; }
+          else if (lane > j) rr[j] *= inv;
+#pragma unroll
+          for (int k = j + 1; k < IR_B; ++k) {
+            const float lkj = __shfl_sync(0xffffffffu, rr[j], k);
+            if (lane >= k) rr[k] -= rr[j] * lkj;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < IR_B; ++k) D[lane][k] = (k <= lane) ? rr[k] : 0.f;
+      if (lane == 0) flag_s = bad;
+    }
+    __syncthreads();
+    if (flag_s) {  // identical in every CTA: the FP64 factorisation takes over
+      if (g == 0 && tid == 0) *a.need_fp64 = 1;
+      return;
+    }
+    const int64_t r0 = c0 + m;
+    for (int64_t r = r0 + (int64_t)g * (IR_THREADS / 32) + warp; r < n;
+         r += (int64_t)G * (IR_THREADS / 32)) {
+      float v = lane < m ? L[r * n + c0 + lane] : 0.f;
+      for (int k = 0; k < m; ++k) {
+        if (lane == k) v *= rinv[k];
+        const float lk = __shfl_sync(0xffffffffu, v, k);
+        if (lane > k && lane < m) v -= D[lane][k] * lk;
+      }
+      if (lane < m) L[r * n + c0 + lane] = v;
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (g == 0)
+      for (int e = tid; e < m * m; e += IR_THREADS) {
+        const int i = e / m, j = e % m;
+        if (j <= i) L[(c0 + i) * n + c0 + j] = D[i][j];
+      }
+    const int64_t tr = n - r0;
+    if (tr > 0) {
+      const int nt = (int)((tr + IR_B - 1) / IR_B);
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int t = g; t < ntiles; t += G) {
+        int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        const int tj = t - ti * (ti + 1) / 2;
+        const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+        __syncthreads();
+        for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+          const int rr = e / IR_B, k = e % IR_B;
+          ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
+          tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+        }
+        __syncthreads();
+        // 4 outputs per thread: rows ty + 8q, column tx
+        const int tx = tid % 32, ty = tid / 32;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int k = 0; k < IR_B; ++k) {
+          const float bv = tb[tx * TS + k];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+          if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+        }
+      }
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+  }
+
+  // (2) explicit inverse of the FP32 factor by recursive doubling:
+  //     diagonal 32x32 blocks first, then per level, for every pair of
+  //     inverted s x s blocks, X21 = -L22^{-1} (L21 L11^{-1}).
+  float *Li = a.Li;
+  for (int64_t e = (int64_t)g * IR_THREADS + tid; e < n * n; e += (int64_t)G * IR_THREADS)
+    Li[e] = 0.f;
+  if (!cc_grid_sync(a.bar, a.status)) return;
+  for (int blk = g; blk < nb; blk += G) {
+    const int64_t c0 = (int64_t)blk * IR_B;
+    const int m = (int)min64(IR_B, n - c0);
+    for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+      const int i = e / IR_B, j = e % IR_B;
+      D[i][j] = (i < m && j <= i) ? L[(c0 + i) * n + c0 + j] : (i == j ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (warp == 0) {  // lane j: column j of the inverse, top to bottom
+      const int j = lane;
+      float xc[IR_B];
+#pragma unroll
+      for (int i = 0; i < IR_B; ++i) {
+        float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc -= D[i][k] * xc[k];
+        xc[i] = (i >= j) ? acc / D[i][i] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < IR_B; ++i)
+        if (i < m && j < m && i >= j) Li[(c0 + i) * n + c0 + j] = xc[i];
+    }
+    __syncthreads();
+  }
+  if (!cc_grid_sync(a.bar, a.status)) return;
+  for (int64_t sz = IR_B; sz < n; sz *= 2) {
+    // Tm[pair block] = L21 Li11 ; then Li21 = -Li22 Tm
+    for (int phase = 0; phase < 2; ++phase) {
+      const int64_t pairs = (n + 2 * sz - 1) / (2 * sz);
+      const int64_t tps = (sz + IR_B - 1) / IR_B;  // tiles per side of a pair block
+      const int64_t ntile = pairs * tps * tps;
+      for (int64_t t = g; t < ntile; t += G) {
+        const int64_t pr = t / (tps * tps), tt = t % (tps * tps);
+        const int64_t ti = tt / tps, tj = tt % tps;
+        const int64_t base = pr * 2 * sz;
+        const int64_t i0 = base + sz + ti * IR_B;   // rows of the lower-left block
+        const int64_t j0 = base + tj * IR_B;        // columns
+        if (i0 >= n) continue;                      // uniform over the CTA
+        const float *Aop; const float *Bop;
+        int64_t arow0, acol0, brow0, kmax;
+        if (phase == 0) {  // Tm = L21 * Li11: A = L rows i, cols base..; B = Li11
+          Aop = L; arow0 = i0; acol0 = base; Bop = Li; brow0 = base; kmax = sz;
+        } else {           // Li21 = -Li22 * Tm: A = Li22 rows i, cols base+sz..; B = Tm
+          Aop = Li; arow0 = i0; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz; kmax = sz;
+        }
+        const int tx = tid % 32, ty = tid / 32;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t k0 = 0; k0 < kmax; k0 += IR_B) {
+          __syncthreads();
+          for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+            const int rr = e / IR_B, kk = e % IR_B;
+            const int64_t ar = arow0 + rr, ac = acol0 + k0 + kk;
+            ta[rr * TS + kk] = (ar < n && ac < n) ? Aop[ar * n + ac] : 0.f;
+            const int64_t br = brow0 + k0 + rr, bc = j0 + kk;
+            tb[rr * TS + kk] = (br < n && bc < n) ? Bop[br * n + bc] : 0.f;
+          }
+          __syncthreads();
+#pragma unroll 8
+          for (int kk = 0; kk < IR_B; ++kk) {
+            const float bv = tb[kk * TS + tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + kk], bv, acc[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+          if (i < n && j < n && j < base + sz) {
+            if (phase == 0) a.Tm[i * n + j] = acc[q];
+            else Li[i * n + j] = -acc[q];
+          }
+        }
+      }
+      if (!cc_grid_sync(a.bar, a.status)) return;
+    }
+  }
+
+  // (3) refinement: d = Li^T (Li r) on all SMs, residual in FP64
+  for (int64_t i = (int64_t)g * IR_THREADS + tid; i < n; i += (int64_t)G * IR_THREADS) {
+    a.r[i] = a.b[i];
+    a.x[i] = 0.0;
+  }
+  if (!cc_grid_sync(a.bar, a.status)) return;
+  const int64_t nwarps = (int64_t)G * (IR_THREADS / 32);
+  const int64_t gw = (int64_t)g * (IR_THREADS / 32) + warp;
+  constexpr int CH = 64;  // rows per partial sum of the transposed product
+  const int64_t nch = (n + CH - 1) / CH;
+  double normA = 0.0;
+  int converged = 0;
+  for (int it = 0; it < a.maxit && !converged; ++it) {
+    // w = Li r (one warp per row)
+    for (int64_t i = gw; i < n; i += nwarps) {
+      const float *row = Li + i * n;
+      float sacc = 0.f;
+      for (int64_t j = lane; j <= i; j += 32) sacc = fmaf(row[j], (float)a.r[j], sacc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) a.wv[i] = sacc;
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+    // partial sums of Li^T w over 64-row chunks: (chunk, 32-column block) per warp
+    const int64_t ncb = (n + 31) / 32;
+    for (int64_t u = gw; u < nch * ncb; u += nwarps) {
+      const int64_t ch = u / ncb, cb = u % ncb;
+      const int64_t j = cb * 32 + lane;
+      float sacc = 0.f;
+      const int64_t r1 = min64(n, (ch + 1) * CH);
+      for (int64_t i = ch * CH; i < r1; ++i)
+        if (j < n && i >= j) sacc = fmaf(Li[i * n + j], a.wv[i], sacc);
+      if (j < n) a.dpart[ch * n + j] = sacc;
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+    for (int64_t j = (int64_t)g * IR_THREADS + tid; j < n; j += (int64_t)G * IR_THREADS) {
+      float d = 0.f;
+      for (int64_t ch = j / CH; ch < nch; ++ch) d += a.dpart[ch * n + j];
+      a.x[j] += (double)d;
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+    // r = b - A x in FP64; partial max |r_i|, max |x_i| and (first sweep) max
+    // row sum |A|
+    double rmax = 0.0, xmax = 0.0, amax = 0.0;
+    for (int64_t i = gw; i < n; i += nwarps) {
+      const double *Ai = a.A + i * n;
+      double sacc = 0.0, sa = 0.0;
+      for (int64_t j = lane; j < n; j += 32) {
+        const double aij = Ai[j];
+        sacc = fma(aij, a.x[j], sacc);
+        if (it == 0) sa += fabs(aij);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      }
+      const double ri = a.b[i] - sacc;
+      if (lane == 0) a.r[i] = ri;
+      rmax = fmax(rmax, fabs(ri));
+      xmax = fmax(xmax, fabs(a.x[i]));
+      amax = fmax(amax, sa);
+    }
+    if (lane == 0) { red_s[warp][0] = rmax; red_s[warp][1] = xmax; red_s[warp][2] = amax; }
+    __syncthreads();
+    if (tid == 0) {
+      double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+      for (int q = 0; q < IR_THREADS / 32; ++q) {
+        m0 = fmax(m0, red_s[q][0]); m1 = fmax(m1, red_s[q][1]); m2 = fmax(m2, red_s[q][2]);
+      }
+      a.part[(size_t)g * 4 + 0] = m0; a.part[(size_t)g * 4 + 1] = m1; a.part[(size_t)g * 4 + 2] = m2;
+    }
+    if (!cc_grid_sync(a.bar, a.status)) return;
+    double rn = 0.0, xn = 0.0, an = 0.0;
+    for (int q = 0; q < G; ++q) {
+      rn = fmax(rn, a.part[(size_t)q * 4]); xn = fmax(xn, a.part[(size_t)q * 4 + 1]);
+      an = fmax(an, a.part[(size_t)q * 4 + 2]);
+    }
+    if (it == 0) normA = an;
+    converged = rn <= sqrt((double)n) * 1.1102230246251565e-16 * normA * xn;
+    // every CTA has read part[] before anyone overwrites it in the next sweep
+    if (!cc_grid_sync(a.bar, a.status)) return;
+  }
+  if (!converged && g == 0 && tid == 0) *a.need_fp64 = 1;
+}
+
+inline size_t chol_ir_smem(int64_t) {
+  return sizeof(float) * ((size_t)IR_B * (IR_B + 1) + IR_B + 2 * (size_t)IR_B * (IR_B + 1));
+}
+
+}  // namespace nqs

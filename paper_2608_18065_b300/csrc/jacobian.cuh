@@ -21,10 +21,12 @@ template <typename T> struct BwdArgs {
   int ntiles;
   const uint8_t *spins;     // [ns][N]
   const T *hcache;          // [ns][N][dh]
+  const T *gcache;          // [ns][N][gw] gate activations of the forward pass
+  int gw;
+  const T *lccache;         // [ns][N][2]: 1/2 log p(sigma_k), phi_k
   T *adj;                   // [nrows][N][adjw]
   int adjw;
   T *adjcol;                // 2D: [nrows][Lx][dh] pending vertical adjoints
-  int wg_in_smem;           // 1: backward weights staged in shared memory
 };
 
 // adjoint record of one site: dau | dar | dg | dac (4 dh) | dz0 dz1 dy0 dy1 |
@@ -34,42 +36,43 @@ template <int DH, int DIM> struct Adj {
   static constexpr int DZ = 4 * DH, DHP = 4 * DH + 4, HP = 5 * DH + 4;
 };
 
+// Unit groups of the reverse sweep: two units per thread at dh >= 64.
+template <int DH> struct BTile {
+  static constexpr int UG = DH >= 32 ? 32 : DH;
+  static constexpr int UT = DH / UG;
+};
+
 template <typename T, int DH, int DIM, int R>
-inline size_t bwd_smem_bytes(int N, bool wg_in_smem) {
-  constexpr int DIN = DIM == 2 ? 4 : 2;
-  size_t t = (size_t)DH * 3 * DH + (size_t)DIN * 3 * DH + (size_t)DH * 4 + 4 * DH + 8;
-  if (DIM == 2) t += 2 * (size_t)DH * DH;               // U12T
-  if (wg_in_smem) t += 3 * (size_t)DH * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);
-  t += (size_t)DH * R * (DIM == 2 ? 4 : 1) + 3 * (size_t)DH * R;  // shh shv shp sdp + sda
+inline size_t bwd_smem_bytes(int N) {
+  size_t t = 3 * (size_t)DH * DH + 4 * DH + 8;           // Wg, head, hc
+  if (DIM == 2) t += 2 * (size_t)DH * DH + (size_t)DH * R;  // U12, sdp
+  t += 3 * (size_t)DH * R;                                // sda
   size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
   return (b + 127) & ~size_t(127);
 }
 
+// Reverse sweep of one row (sample, seed) through the GRU (App. A).  The
+// forward pass stored u, r, c, W_h h' + b_h (and h' in 2D) per site, and the
+// log-conditional of sigma_k, so per site only the adjoint of h',
+// W^T (dau, dar, dg) -- one GEMM [R x 3dh] x [3dh x dh] -- is computed.  The
+// head adjoint follows from the stored terms: p(sigma_k) = exp(2 lc_0),
+// p(other) = 1 - p(sigma_k) (a site fixed by the mask has p = 1 and no
+// gradient), and the softsign slope pi (1 - |phi_k/pi|)^2.
 template <typename T, int DH, int DIM, int RT, int RG>
-__global__ void __launch_bounds__(Tile<DH>::UG * RG)
+__global__ void __launch_bounds__(BTile<DH>::UG * RG)
 k_jac_bwd(const BwdArgs<T> A) {
-  constexpr int UG = Tile<DH>::UG, UT = Tile<DH>::UT;
+  constexpr int UG = BTile<DH>::UG, UT = BTile<DH>::UT;
   constexpr int R = RT * RG;
   constexpr int NTH = UG * RG;
-  constexpr int DIN = DIM == 2 ? 4 : 2;
   constexpr int C3 = 3 * DH;
   using AJ = Adj<DH, DIM>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *sWgT = reinterpret_cast<T *>(smraw);
-  T *sxw = sWgT + DH * C3;
-  T *sbias = sxw + DIN * C3;
-  T *shead = sbias + DH * 4;
+  T *sWg = reinterpret_cast<T *>(smraw);   // [3dh][dh]: Wg[3a+g][b]
+  T *shead = sWg + C3 * DH;                // [4][dh]
   T *shc = shead + 4 * DH;
-  T *sU12T = shc + 8;
-  T *sp = sU12T + (DIM == 2 ? 2 * DH * DH : 0);
-  T *sWg = sp;
-  T *sU12 = sWg + (A.wg_in_smem ? C3 * DH : 0);
-  sp = sU12 + (A.wg_in_smem && DIM == 2 ? 2 * DH * DH : 0);
-  T *shh = sp;                               // h_{k-1} (1D) / h_hor (2D)
-  T *shv = shh + DH * R;                     // 2D: h_ver
-  T *shp = shv + (DIM == 2 ? DH * R : 0);    // 2D: h'
-  T *sdp = shp + (DIM == 2 ? DH * R : 0);    // 2D: adjoint of h'
-  T *sda = sdp + (DIM == 2 ? DH * R : 0);    // gate adjoints [3dh][R]
+  T *sU12 = shc + 8;                       // 2D: [dh][2dh]
+  T *sdp = sU12 + (DIM == 2 ? 2 * DH * DH : 0);  // 2D: adjoint of h' [dh][R]
+  T *sda = sdp + (DIM == 2 ? DH * R : 0);  // gate adjoints [3dh][R]
   const int NP = (A.N + 15) & ~15;
   uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * R);
   int *srow = reinterpret_cast<int *>(ssp + R * NP);
@@ -78,27 +81,20 @@ k_jac_bwd(const BwdArgs<T> A) {
   const int ug = tid % UG, rg = tid / UG;
   const int r0 = rg * RT, a0 = ug * UT;
   const int N = A.N, Lx = A.Lx;
-  const int lane = tid & 31;
 
-  const T *p = A.pack;
-  auto al = [](int x) { return (x + 31) & ~31; };
-  const int oWgT = 0, oWg = al(oWgT + DH * C3), oxw = al(oWg + C3 * DH);
-  const int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
-  const int oU12T = al(ohc + 4), oU12 = al(oU12T + 2 * DH * DH);
-  for (int e = tid; e < DH * C3; e += NTH) sWgT[e] = p[oWgT + e];
-  for (int e = tid; e < DIN * C3; e += NTH) sxw[e] = p[oxw + e];
-  for (int e = tid; e < DH * 4; e += NTH) sbias[e] = p[obias + e];
-  for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
-  if (tid < 4) shc[tid] = p[ohc + tid];
-  if (DIM == 2)
-    for (int e = tid; e < 2 * DH * DH; e += NTH) sU12T[e] = p[oU12T + e];
-  if (A.wg_in_smem) {
+  {
+    const T *p = A.pack;
+    auto al = [](int x) { return (x + 31) & ~31; };
+    constexpr int DIN = DIM == 2 ? 4 : 2;
+    const int oWg = al(DH * C3), oxw = al(oWg + C3 * DH);
+    const int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
+    const int oU12T = al(ohc + 4), oU12 = al(oU12T + 2 * DH * DH);
     for (int e = tid; e < C3 * DH; e += NTH) sWg[e] = p[oWg + e];
+    for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
+    if (tid < 4) shc[tid] = p[ohc + tid];
     if (DIM == 2)
       for (int e = tid; e < 2 * DH * DH; e += NTH) sU12[e] = p[oU12 + e];
   }
-  const T *Wg = A.wg_in_smem ? sWg : p + oWg;
-  const T *U12 = A.wg_in_smem ? sU12 : p + oU12;
 
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
     __syncthreads();
@@ -113,14 +109,6 @@ k_jac_bwd(const BwdArgs<T> A) {
       ssp[r * NP + k] = g >= 0 ? A.spins[(g % A.ns) * (int64_t)N + k] : 0;
     }
     __syncthreads();
-    // per-row mask counters (lane ug == i): counts over [0, k] before site k
-    const int my_i = ug;
-    const int my_r = r0 + (my_i < RT ? my_i : 0);
-    int cnt_up = 0, cnt_dn = 0;
-    if (my_i < RT && A.zmask)
-      for (int k = 0; k < N; ++k) {
-        if (ssp[my_r * NP + k] == 0) ++cnt_up; else ++cnt_dn;
-      }
     if (DIM == 2) {
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
@@ -138,6 +126,29 @@ k_jac_bwd(const BwdArgs<T> A) {
 #pragma unroll
       for (int uu = 0; uu < UT; ++uu) carry[i][uu] = T(0);
 
+    // forward-pass values of site k for this thread's rows and units,
+    // loaded one site ahead of their use
+    T gu[RT][UT], gr[RT][UT], gc[RT][UT], gg[RT][UT], ghp[RT][UT], lc0[RT], lc1[RT];
+    auto load_site = [&](int k) {
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int g = srow[r0 + i];
+        const int64_t s = g >= 0 ? g % A.ns : 0;
+        const T *G = A.gcache + (s * N + k) * A.gw;
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) {
+          const int a = a0 + uu;
+          gu[i][uu] = G[a]; gr[i][uu] = G[DH + a]; gc[i][uu] = G[2 * DH + a];
+          gg[i][uu] = G[3 * DH + a];
+          if (DIM == 2) ghp[i][uu] = G[4 * DH + a];
+          else ghp[i][uu] = k > 0 ? A.hcache[(s * N + k - 1) * DH + a] : T(0);
+        }
+        lc0[i] = A.lccache[(s * N + k) * 2];
+        lc1[i] = A.lccache[(s * N + k) * 2 + 1];
+      }
+    };
+    load_site(N - 1);
+
     for (int k = N - 1; k >= 0; --k) {
       int hor_ok = k > 0, ver = -1, col = 0;
       if (DIM == 2) {
@@ -146,104 +157,23 @@ k_jac_bwd(const BwdArgs<T> A) {
         hor_ok = m != 0;
         ver = (k >= Lx) ? k - 2 * m - 1 : -1;
       }
-      // input states of site k
-#pragma unroll
-      for (int i = 0; i < RT; ++i) {
-        int r = r0 + i, g = srow[r];
-        int64_t s = g >= 0 ? g % A.ns : 0;
-#pragma unroll
-        for (int uu = 0; uu < UT; ++uu) {
-          int a = a0 + uu;
-          shh[a * R + r] = (g >= 0 && hor_ok) ? A.hcache[(s * N + k - 1) * DH + a] : T(0);
-          if (DIM == 2)
-            shv[a * R + r] = (g >= 0 && ver >= 0) ? A.hcache[(s * N + ver) * DH + a] : T(0);
-        }
-      }
-      __syncthreads();
-      const T *Ag = shh;
-      if (DIM == 2) {
-        T acc1[RT][UT];
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-          for (int uu = 0; uu < UT; ++uu) acc1[i][uu] = T(0);
-        if (hor_ok) mm_acc<T, RT, UT>(shh, R, r0, sU12T, DH, a0, DH, acc1);
-        if (ver >= 0) mm_acc<T, RT, UT>(shv, R, r0, sU12T + DH * DH, DH, a0, DH, acc1);
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-          for (int uu = 0; uu < UT; ++uu) shp[(a0 + uu) * R + r0 + i] = acc1[i][uu];
-        __syncthreads();
-        Ag = shp;
-      }
-      T acc[RT][3 * UT];
-#pragma unroll
-      for (int i = 0; i < RT; ++i)
-#pragma unroll
-        for (int j2 = 0; j2 < 3 * UT; ++j2) acc[i][j2] = T(0);
-      if (DIM == 2 || k > 0) mm_acc<T, RT, 3 * UT>(Ag, R, r0, sWgT, C3, 3 * a0, DH, acc);
-
       T dpd[RT][UT];  // (1-u) dh: the direct path of dh into h'
+      T hpv[RT][UT];
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
         const int r = r0 + i, g = srow[r];
         const int which = g >= 0 ? (int)(g / A.ns) : 0;
         const int sk = ssp[r * NP + k];
-        int d0 = -1, d1 = -1;
-        if (DIM == 1) {
-          if (k > 0) d0 = ssp[r * NP + k - 1];
-        } else {
-          if (hor_ok) d0 = ssp[r * NP + k - 1];
-          if (ver >= 0) d1 = 2 + ssp[r * NP + ver];
-        }
-        T uv[UT], rv[UT], cv[UT], gv[UT], hv[UT], hpv[UT];
-        T z0 = T(0), z1 = T(0), y = T(0);
-#pragma unroll
-        for (int uu = 0; uu < UT; ++uu) {
-          const int a = a0 + uu;
-          T au = acc[i][3 * uu + 0] + sbias[4 * a + 0];
-          T ar = acc[i][3 * uu + 1] + sbias[4 * a + 1];
-          T gg = acc[i][3 * uu + 2] + sbias[4 * a + 2];
-          T ai = sbias[4 * a + 3];
-          if (d0 >= 0) {
-            au += sxw[d0 * C3 + 3 * a + 0]; ar += sxw[d0 * C3 + 3 * a + 1];
-            ai += sxw[d0 * C3 + 3 * a + 2];
-          }
-          if (d1 >= 0) {
-            au += sxw[d1 * C3 + 3 * a + 0]; ar += sxw[d1 * C3 + 3 * a + 1];
-            ai += sxw[d1 * C3 + 3 * a + 2];
-          }
-          uv[uu] = sigm(au); rv[uu] = sigm(ar); gv[uu] = gg;
-          cv[uu] = tnh(rv[uu] * gg + ai);
-          hpv[uu] = (DIM == 2 || k > 0) ? Ag[a * R + r] : T(0);
-          hv[uu] = (T(1) - uv[uu]) * hpv[uu] + uv[uu] * cv[uu];
-          z0 += shead[a] * hv[uu];
-          z1 += shead[DH + a] * hv[uu];
-          if (A.cplx) y += shead[(2 + sk) * DH + a] * hv[uu];
-        }
-        z0 = group_sum<T, UG>(z0);
-        z1 = group_sum<T, UG>(z1);
-        if (A.cplx) y = group_sum<T, UG>(y);
-        // mask state of this row before site k, broadcast from lane ug == i
-        int forced_l = 0;
-        if (my_i == i) {
-          if (sk == 0) --cnt_up; else --cnt_dn;
-          forced_l = A.zmask && (cnt_up >= N / 2 || cnt_dn >= N / 2);
-        }
-        const int src = (lane & ~(UG - 1)) | i;
-        const int forced = __shfl_sync(0xffffffffu, forced_l, src, 32);
+        // head adjoint from the stored log-conditional and phase of sigma_k
         T dz0 = T(0), dz1 = T(0), dy = T(0);
         if (which == 0) {
-          if (!forced) {
-            T lp0, lp1;
-            log_softmax2<T>(z0 + shc[0], z1 + shc[1], lp0, lp1);
-            dz0 = T(0.5) * ((sk == 0 ? T(1) : T(0)) - ex(lp0));
-            dz1 = T(0.5) * ((sk == 1 ? T(1) : T(0)) - ex(lp1));
-          }
+          const T ps = ex(T(2) * lc0[i]);
+          dz0 = sk == 0 ? T(0.5) * (T(1) - ps) : T(-0.5) * (T(1) - ps);
+          dz1 = -dz0;
         } else {
-          T yy = y + shc[2 + sk];
-          T den = T(1) + (yy < T(0) ? -yy : yy);
-          dy = T(NQS_PI) / (den * den);
+          const T q = lc1[i] / T(NQS_PI);
+          const T om = T(1) - (q < T(0) ? -q : q);
+          dy = T(NQS_PI) * om * om;
         }
         T *rec = A.adj + ((int64_t)(g >= 0 ? g : 0) * N + k) * A.adjw;
         if (g >= 0 && ug == 0) {
@@ -257,30 +187,34 @@ k_jac_bwd(const BwdArgs<T> A) {
           T dh = carry[i][uu] + shead[a] * dz0 + shead[DH + a] * dz1;
           if (A.cplx) dh += shead[(2 + sk) * DH + a] * dy;
           if (DIM == 2 && g >= 0) dh += A.adjcol[((int64_t)g * Lx + col) * DH + a];
-          const T dc = dh * uv[uu];
-          const T du = dh * (cv[uu] - hpv[uu]);
-          dpd[i][uu] = dh * (T(1) - uv[uu]);
-          const T dac = dc * (T(1) - cv[uu] * cv[uu]);
-          const T dr = dac * gv[uu];
-          const T dg = dac * rv[uu];
-          const T dar = dr * rv[uu] * (T(1) - rv[uu]);
-          const T dau = du * uv[uu] * (T(1) - uv[uu]);
+          const T u = gu[i][uu], rr = gr[i][uu], c = gc[i][uu], gv = gg[i][uu];
+          const T hp = ghp[i][uu];
+          hpv[i][uu] = hp;
+          const T dc = dh * u;
+          const T du = dh * (c - hp);
+          dpd[i][uu] = dh * (T(1) - u);
+          const T dac = dc * (T(1) - c * c);
+          const T dr = dac * gv;
+          const T dg = dac * rr;
+          const T dar = dr * rr * (T(1) - rr);
+          const T dau = du * u * (T(1) - u);
           sda[(3 * a + 0) * R + r] = dau;
           sda[(3 * a + 1) * R + r] = dar;
           sda[(3 * a + 2) * R + r] = dg;
           if (g >= 0) {
             rec[a] = dau; rec[DH + a] = dar; rec[2 * DH + a] = dg; rec[3 * DH + a] = dac;
-            if (DIM == 2) rec[AJ::HP + a] = hpv[uu];
+            if (DIM == 2) rec[AJ::HP + a] = hp;
           }
         }
       }
+      if (k > 0) load_site(k - 1);  // in flight during the GEMM below
       __syncthreads();
       T dh1[RT][UT];
 #pragma unroll
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int uu = 0; uu < UT; ++uu) dh1[i][uu] = dpd[i][uu];
-      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, R, r0, Wg, DH, a0, C3, dh1);
+      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, R, r0, sWg, DH, a0, C3, dh1);
       if (DIM == 1) {
 #pragma unroll
         for (int i = 0; i < RT; ++i)
@@ -303,8 +237,8 @@ k_jac_bwd(const BwdArgs<T> A) {
         for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int uu = 0; uu < UT; ++uu) { dhh[i][uu] = T(0); dhv[i][uu] = T(0); }
-        mm_acc<T, RT, UT>(sdp, R, r0, U12, 2 * DH, a0, DH, dhh);
-        mm_acc<T, RT, UT>(sdp, R, r0, U12 + DH, 2 * DH, a0, DH, dhv);
+        mm_acc<T, RT, UT>(sdp, R, r0, sU12, 2 * DH, a0, DH, dhh);
+        mm_acc<T, RT, UT>(sdp, R, r0, sU12 + DH, 2 * DH, a0, DH, dhv);
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
           const int g = srow[r0 + i];
@@ -316,6 +250,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           }
         }
       }
+      (void)hpv;
       __syncthreads();
     }
   }

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "chol_coop.cuh"
+#include "chol_ir.cuh"
 #include "eloc_tc.h"
 #include "gram_tc.h"
 #include "launch.h"
@@ -19,7 +20,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, total;
 };
 
 }  // namespace
@@ -38,6 +39,7 @@ struct nqs_ctx {
   int *d_opf = nullptr;
   int eloc_grid = 0, eloc_R = 0;
   int adjw = 0;
+  int gw = 0;  // gate-cache record width: 4 dh (+ dh in 2D)
   size_t es = 8;  // element size of the recurrence precision
   WsOff off{};
   char *ws = nullptr;
@@ -145,7 +147,7 @@ void carve(nqs_ctx *c) {
   o.T = take(R * R * 8);
   o.eps = take(R * 8);
   o.x = take(R * 8);
-  c->nsplit = (int)((R + 63) / 64);
+  c->nsplit = (int)((R + 63) / 64) + 2;  // also holds the column-sum chunks
   o.part = take((size_t)c->nsplit * np * 8);
   o.dth = take(np * 8);
   o.frob = take(1024 * 8);
@@ -155,6 +157,12 @@ void carve(nqs_ctx *c) {
   o.cy = take(R * 8);
   o.cpart = take((size_t)2 * c->rd.sm_count * CC_B * 8);
   o.cbar = take(64);
+  o.gcache = take(ns * N * c->gw * es);
+  o.L32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
+  o.Li32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
+  o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
+  o.wv32 = take(R * 4);
+  o.dpart32 = take(((R + 63) / 64) * R * 4);
   o.total = p;
 }
 
@@ -185,19 +193,24 @@ FwdArgs<T> fwd_args(nqs_ctx *c) {
   return a;
 }
 
+// with_gates: also store the gate activations the reverse sweep reads.
 template <typename T>
 nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t step, uint8_t *spins,
-                     double *logpsi, cudaStream_t st) {
+                     double *logpsi, cudaStream_t st, bool with_gates = false) {
   FwdArgs<T> a = fwd_args<T>(c);
   a.nrows = n; a.seed = seed; a.step = step; a.spins = spins; a.logpsi = logpsi;
+  if (with_gates) {
+    a.gcache = W<T>(c, c->off.gcache);
+    a.gw = c->gw;
+  }
   c->launches += 1;
   return cu(run_forward<T>(c->rd, mode, a, 0, st));
 }
 
 nqs_status forward(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t step, uint8_t *spins,
-                   double *logpsi, cudaStream_t st) {
-  return f32(c) ? forward_T<float>(c, mode, n, seed, step, spins, logpsi, st)
-                : forward_T<double>(c, mode, n, seed, step, spins, logpsi, st);
+                   double *logpsi, cudaStream_t st, bool with_gates = false) {
+  return f32(c) ? forward_T<float>(c, mode, n, seed, step, spins, logpsi, st, with_gates)
+                : forward_T<double>(c, mode, n, seed, step, spins, logpsi, st, with_gates);
 }
 
 template <typename T> nqs_status pack(nqs_ctx *c, const double *theta, cudaStream_t st) {
@@ -272,6 +285,9 @@ nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_
   b.ns = ns; b.nrows = R;
   b.spins = spins;
   b.hcache = W<T>(c, c->off.hcache);
+  b.gcache = W<T>(c, c->off.gcache);
+  b.gw = c->gw;
+  b.lccache = W<T>(c, c->off.lccache);
   b.adj = W<T>(c, c->off.adj);
   b.adjw = c->adjw;
   b.adjcol = W<T>(c, c->off.adjcol);
@@ -304,6 +320,8 @@ nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
   }
   return cu(cudaGetLastError());
 }
+
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
 __global__ void k_shift(double *T, int64_t R, double lam) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -341,24 +359,55 @@ __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int np
   for (int64_t i = threadIdx.x; i < R; i += blockDim.x) T[i * R + i] += lam_s;
 }
 
-// Cholesky of the shifted T in place, then x = (T + lambda I)^{-1} b: one
-// cooperative launch over all SMs (chol_coop.cuh).
+// x = (T + lambda I)^{-1} b for the shifted T.  FP64 context: FP64 Cholesky
+// and both substitutions in one cooperative launch (chol_coop.cuh).  Mixed
+// context: FP32 factor and FP64 iterative refinement (chol_ir.cuh); the FP64
+// kernel follows on the stream and runs only if the refinement reports that
+// it must (non-positive FP32 pivot or no convergence).  *need_fp64 (device)
+// ends as 0 (refined) or 1 (FP64 factorisation).
 nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double *x,
                       int32_t *status, cudaStream_t st) {
+  unsigned *bar = W<unsigned>(c, c->off.cbar);
+  int32_t *need = reinterpret_cast<int32_t *>(bar + 4);
+  const int G = c->rd.sm_count;
+  CU(cudaMemsetAsync(bar, 0, 32, st));
+  if (f32(c)) {
+    CholIrArgs ir;
+    ir.A = T; ir.n = R; ir.b = b; ir.x = x;
+    ir.L = W<float>(c, c->off.L32);
+    ir.Li = W<float>(c, c->off.Li32);
+    ir.Tm = W<float>(c, c->off.Tm32);
+    ir.wv = W<float>(c, c->off.wv32);
+    ir.dpart = W<float>(c, c->off.dpart32);
+    ir.r = W<double>(c, c->off.crhs);
+    ir.part = W<double>(c, c->off.cpart);
+    ir.bar = bar + 2;
+    ir.status = status;
+    ir.need_fp64 = need;
+    ir.maxit = 12;
+    const size_t smem = chol_ir_smem(R);
+    CU(cudaFuncSetAttribute(k_chol_ir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void *args[] = {&ir};
+    c->launches += 1;
+    CU(cudaLaunchCooperativeKernel((void *)k_chol_ir, dim3(G), dim3(IR_THREADS), args, smem, st));
+  } else {
+    k_set_i32<<<1, 1, 0, st>>>(need, 1);
+    c->launches += 1;
+    CU(cudaGetLastError());
+  }
   CholCoopArgs a;
   a.A = T; a.n = R; a.b = b; a.x = x;
   a.rhs = W<double>(c, c->off.crhs);
   a.y = W<double>(c, c->off.cy);
   a.part = W<double>(c, c->off.cpart);
-  a.bar = W<unsigned>(c, c->off.cbar);
+  a.bar = bar;
   a.status = status;
-  CU(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st));
+  a.gate = need;
   const size_t smem = chol_coop_smem(R);
   CU(cudaFuncSetAttribute(k_chol_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop, CC_THREADS, smem));
   if (per < 1) return NQS_ERR_UNSUPPORTED;
-  const int G = c->rd.sm_count;
   void *args[] = {&a};
   c->launches += 1;
   CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
@@ -384,7 +433,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   // line 3: sample (also fills the hidden-state caches)
   ST(pack_theta<T>(c, theta, st));
   mark(c, 1, st);
-  ST(forward_T<T>(c, MODE_SAMPLE, ns, hp->seed, (uint64_t)hp->step_index, spins, logpsi, st));
+  ST(forward_T<T>(c, MODE_SAMPLE, ns, hp->seed, (uint64_t)hp->step_index, spins, logpsi, st, true));
   // line 4: local energies, E, variance; eps-bar'
   ST(eloc_T<T>(c, ns, spins, eloc, st));
   mark(c, 5, st);
@@ -398,9 +447,13 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   // planes that the Gram and O'x read; otherwise O is centred in place
   const bool tc = f32(c) && gram_tc_available();
   {
-    c->launches += 2;
-    dim3 g((unsigned)((np + 255) / 256), c->L.cplx ? 2u : 1u);
-    k_colmean<T><<<g, 256, 0, st>>>(O, ns, np, W<double>(c, c->off.mean));
+    c->launches += 3;
+    const int chunks = (int)((ns + COL_ROWS - 1) / COL_ROWS);
+    const unsigned nblk = c->L.cplx ? 2u : 1u;
+    dim3 g((unsigned)((np + 255) / 256), nblk * chunks);
+    k_colsum_part<T><<<g, 256, 0, st>>>(O, ns, np, chunks, W<double>(c, c->off.part));
+    k_colmean_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
+        W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean));
     CU(cudaGetLastError());
     if (tc) {
       CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<double>(c, c->off.mean),
@@ -438,7 +491,8 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   double eta_t = hp->eta0;
   if (hp->decay_T > 0.0 && std::isfinite(hp->decay_T))
     eta_t = hp->eta0 / (1.0 + (double)hp->step_index / hp->decay_T);
-  k_eta<<<1, 1024, 0, st>>>(eps, x, R, eta_t, hp->trust_region, stats, sstat);
+  k_eta<<<1, 1024, 0, st>>>(eps, x, R, eta_t, hp->trust_region, stats, sstat,
+                            reinterpret_cast<int32_t *>(W<unsigned>(c, c->off.cbar) + 4));
   CU(cudaGetLastError());
   {
     c->launches += 4;
@@ -510,6 +564,7 @@ nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int 
   }
   c->rd = RecDesc{m.dim, m.dh, N, m.Lx, m.cplx, m.marshall, m.zmask, sms};
   c->adjw = 4 * m.dh + 4 + (m.dim == 2 ? 2 * m.dh : 0);
+  c->gw = 4 * m.dh + (m.dim == 2 ? m.dh : 0);
   c->eloc_R = eloc_rows(c->rd, precision == NQS_PREC_MIXED);
   c->eloc_grid = precision == NQS_PREC_MIXED ? eloc_max_grid<float>(c->rd) : eloc_max_grid<double>(c->rd);
   if (c->eloc_grid <= 0) { delete c; return NQS_ERR_CUDA; }
@@ -602,7 +657,8 @@ nqs_status nqs_jacobian(nqs_ctx *c, const double *theta, const uint8_t *spins, i
   ST(need_ws(c));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ST(pack_any(c, theta, st));
-  ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st));
+  ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st,
+             true));
   return f32(c) ? jac_T<float>(c, ns, spins, static_cast<float *>(O), st)
                 : jac_T<double>(c, ns, spins, static_cast<double *>(O), st);
 }

@@ -77,17 +77,12 @@ template <typename T, int DH, int DIM>
 static cudaError_t bwd_dim(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
   constexpr int RT = Rows<T>::BWD_RT, RG = Rows<T>::BWD_RG, R = RT * RG;
   auto kern = k_jac_bwd<T, DH, DIM, RT, RG>;
-  size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, true);
-  a.wg_in_smem = 1;
-  if (smem > 200 * 1024) {
-    smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
-    a.wg_in_smem = 0;
-  }
+  const size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   a.ntiles = (int)((a.nrows + R - 1) / R);
   if (a.ntiles <= 0) return cudaSuccess;
-  kern<<<a.ntiles, Tile<DH>::UG * RG, smem, st>>>(a);
+  kern<<<a.ntiles, BTile<DH>::UG * RG, smem, st>>>(a);
   return cudaGetLastError();
 }
 

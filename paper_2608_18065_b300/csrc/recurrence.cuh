@@ -68,6 +68,8 @@ template <typename T> struct FwdArgs {
   double *logpsi;          // [rows*2]
   T *hcache;               // [rows][N][dh]  (SAMPLE/GIVEN write, ELOC read)
   T *lccache;              // [rows][N][2]
+  T *gcache;               // optional [rows][N][gw]: u | r | c | W_h h'+b_h (| h' in 2D)
+  int gw;
   // ELOC
   int tiles_per_op;
   const int *op_f;         // [n_off*4]: f1, f2, start, pad
@@ -278,6 +280,11 @@ k_forward(const FwdArgs<T> A) {
           if (s >= 0) {
             if (MODE != MODE_ELOC && A.hcache)
               A.hcache[((int64_t)s * N + k) * DH + a] = hn;
+            if (MODE != MODE_ELOC && A.gcache) {
+              T *gr = A.gcache + ((int64_t)s * N + k) * A.gw;
+              gr[a] = u; gr[DH + a] = rr; gr[2 * DH + a] = c; gr[3 * DH + a] = gg;
+              if (DIM == 2) gr[4 * DH + a] = hp;
+            }
             if (DIM == 2 && MODE == MODE_ELOC)
               A.colbuf[(((int64_t)blockIdx.x * R + r) * Lx + col) * DH + a] = hn;
           }

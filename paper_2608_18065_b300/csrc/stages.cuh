@@ -136,15 +136,30 @@ __global__ void k_energy(const double *__restrict__ eloc, int64_t ns, int N, int
 
 // ---------------------------------------------------------- centring
 // Column means over the Ns samples of each block (real rows, imaginary
-// rows), accumulated in FP64.  grid.x over column chunks, grid.y = block.
+// rows), accumulated in FP64: partial sums over 64-row chunks (grid.y =
+// block * chunks + chunk), then one pass that adds the chunks.
+constexpr int COL_ROWS = 64;
 template <typename T>
-__global__ void k_colmean(const T *__restrict__ O, int64_t ns, int64_t np, double *mean) {
+__global__ void k_colsum_part(const T *__restrict__ O, int64_t ns, int64_t np, int chunks,
+                              double *part) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const T *B = O + (int64_t)blockIdx.y * ns * np;
+  const int blk = blockIdx.y / chunks, ch = blockIdx.y % chunks;
+  const int64_t r0 = (int64_t)ch * COL_ROWS, r1 = min64(ns, r0 + COL_ROWS);
+  const T *B = O + (int64_t)blk * ns * np;
   double acc = 0.0;
-  for (int64_t s = 0; s < ns; ++s) acc += (double)B[s * np + p];
-  mean[(int64_t)blockIdx.y * np + p] = acc / (double)ns;
+  for (int64_t s = r0; s < r1; ++s) acc += (double)B[s * np + p];
+  part[(int64_t)blockIdx.y * np + p] = acc;
+}
+
+__global__ void k_colmean_fin(const double *__restrict__ part, int64_t ns, int64_t np, int chunks,
+                              double *mean) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int blk = blockIdx.y;
+  double acc = 0.0;
+  for (int c = 0; c < chunks; ++c) acc += part[((int64_t)blk * chunks + c) * np + p];
+  mean[(int64_t)blk * np + p] = acc / (double)ns;
 }
 
 // O' = (O - mean) / sqrt(Ns), in FP64 arithmetic, stored back in T.
@@ -227,7 +242,8 @@ __global__ void k_lambda(double *T, int64_t R, int mode, double lam_c, double co
 // tau = eps - lambda x (App. F), ||tau||, eta_t = eta0/(1+t/decay_T) and
 // eta* = eta_t/||tau|| in trust-region mode.
 __global__ void k_eta(const double *__restrict__ eps, const double *__restrict__ x, int64_t R,
-                      double eta_t, int trust, nqs_step_stats *st, const int32_t *solve_status) {
+                      double eta_t, int trust, nqs_step_stats *st, const int32_t *solve_status,
+                      const int32_t *solve_fp64) {
   __shared__ double s[1024];
   const double lam = st->lambda;
   double acc = 0.0;
@@ -246,6 +262,7 @@ __global__ void k_eta(const double *__restrict__ eps, const double *__restrict__
     st->tau_norm = tn;
     st->eta_eff = trust ? eta_t / tn : eta_t;
     if (st->status == NQS_OK && *solve_status != 0) st->status = *solve_status;
+    st->solve_fp64 = *solve_fp64;
   }
 }
 

@@ -239,4 +239,5 @@ def decode_stats(stats: torch.Tensor) -> dict:
     v = stats.detach().cpu()
     d = {k: float(v[i]) for i, k in enumerate(STATS_FIELDS)}
     d["status"] = int(v[8:9].view(torch.int32)[0])
+    d["solve_fp64"] = int(v[8:9].view(torch.int32)[1])
     return d

@@ -109,10 +109,13 @@ def test_gram(prec, R, np_):
     assert np.array_equal(T, T.T)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("R", [1, 31, 64, 200, 513, 600])
-def test_regularized_solve(R):
+def test_regularized_solve(R, prec):
+    """FP64 Cholesky (FP64 context) and FP32-factor + FP64 refinement (mixed
+    context) both reach the FP64 solution."""
     model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
-    c = ctx(model, ham, "fp64", 600)
+    c = ctx(model, ham, prec, 600)
     rng = np.random.default_rng(R)
     M = rng.standard_normal((R, R + 5))
     T = M @ M.T
@@ -122,7 +125,8 @@ def test_regularized_solve(R):
     x, st = c.regularized_solve(Td, lam, torch.tensor(b, device="cuda"))
     assert int(st.item()) == 0
     xr = np.linalg.solve(T + lam * np.eye(R), b)
-    assert rel_err(x.cpu().numpy(), xr) < 1e-9
+    kappa = np.linalg.cond(T + lam * np.eye(R))
+    assert rel_err(x.cpu().numpy(), xr) < max(1e-10, 100 * kappa * 2.2e-16)
     # an indefinite matrix reports NOT_SPD (5)
     Td = torch.tensor(-T - np.eye(R), device="cuda")
     x, st = c.regularized_solve(Td, 0.0, torch.tensor(b, device="cuda"))
@@ -220,3 +224,23 @@ def test_eloc_tensor_core_engine_mixed(model, ham):
     # the FP64 context (SIMT engine) agrees with the oracle to 1e-10
     c64 = ctx(model, ham, "fp64", ns)
     assert rel_err(cplx(c64.local_energy(thd, spd)), O.local_energy(model, ham, th, sp)) < RTOL64
+
+
+def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
+    """A matrix whose FP32 Cholesky breaks down (kappa ~ 1e12) but is SPD in
+    FP64: the mixed context must still return the FP64 solution."""
+    model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
+    c = ctx(model, ham, "mixed", 64)
+    R = 64
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((R, R)))
+    ev = np.logspace(0, -12, R)
+    T = (Q * ev) @ Q.T
+    T = 0.5 * (T + T.T)
+    b = rng.standard_normal(R)
+    x, st = c.regularized_solve(torch.tensor(T, device="cuda"), 0.0,
+                                torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 0
+    xr = np.linalg.solve(T, b)
+    kappa = np.linalg.cond(T)
+    assert rel_err(x.cpu().numpy(), xr) < 100 * kappa * 2.2e-16
