@@ -178,6 +178,15 @@ nqs_status nqs_local_energy(nqs_ctx *ctx, const double *theta,
 nqs_status nqs_jacobian(nqs_ctx *ctx, const double *theta, const uint8_t *spins,
                         int64_t ns, void *O, void *stream);
 
+/* Vector-Jacobian product of log Psi (the backward of log Psi as a
+ * differentiable function of theta): grad_theta[k] = sum_s ( g_s^re
+ * d Re log Psi(sigma_s)/d theta_k + g_s^im d Im log Psi(sigma_s)/d theta_k ),
+ * with the log-derivatives of nqs_jacobian.  grad_logpsi: device [ns*2]
+ * FP64 (re, im) cotangents; grad_theta: device [Np] FP64 (overwritten). */
+nqs_status nqs_logpsi_vjp(nqs_ctx *ctx, const double *theta, const uint8_t *spins,
+                          int64_t ns, const double *grad_logpsi, double *grad_theta,
+                          void *stream);
+
 /* T = A A^T (Algorithm 1 line 6) for a row-major A [R x np] of centred,
  * scaled log-derivatives (rows = samples): FP64 A -> FP64 T on CUDA cores
  * for the FP64 context; FP32 A -> FP64 T via BF16x3 tcgen05 products with

@@ -323,6 +323,22 @@ nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
+// Cotangents (re, im) interleaved -> [re block; im block].
+__global__ void k_split_cot(const double *__restrict__ g, int64_t ns, int cplx, double *v) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  v[s] = g[2 * s];
+  if (cplx) v[ns + s] = g[2 * s + 1];
+}
+
+__global__ void k_sum_parts(const double *__restrict__ part, int nparts, int64_t np, double *out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double acc = 0.0;
+  for (int c = 0; c < nparts; ++c) acc += part[(int64_t)c * np + p];
+  out[p] = acc;
+}
+
 __global__ void k_shift(double *T, int64_t R, double lam) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < R) T[i * R + i] += lam;
@@ -532,6 +548,26 @@ static void timing_free(nqs_ctx *c) {
   c->tmax = c->tstep = 0;
 }
 
+namespace {
+template <typename T>
+nqs_status vjp_T(nqs_ctx *c, const uint8_t *spins, int64_t ns, const double *g, double *out,
+                 cudaStream_t st) {
+  const int64_t R = c->L.cplx ? 2 * ns : ns, np = c->L.np;
+  T *O = W<T>(c, c->off.O);
+  ST(jac_T<T>(c, ns, spins, O, st));
+  double *v = W<double>(c, c->off.eps);
+  k_split_cot<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(g, ns, c->L.cplx, v);
+  const int rows_per = 64;
+  const int nparts = (int)((R + rows_per - 1) / rows_per);
+  dim3 gr((unsigned)((np + 255) / 256), (unsigned)nparts);
+  k_gemv_part<T><<<gr, 256, 0, st>>>(O, R, np, v, rows_per, W<double>(c, c->off.part));
+  k_sum_parts<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts, np, out);
+  c->launches += 3;
+  return cu(cudaGetLastError());
+}
+
+}  // namespace
+
 // ===================================================================== ABI
 extern "C" {
 
@@ -661,6 +697,19 @@ nqs_status nqs_jacobian(nqs_ctx *c, const double *theta, const uint8_t *spins, i
              true));
   return f32(c) ? jac_T<float>(c, ns, spins, static_cast<float *>(O), st)
                 : jac_T<double>(c, ns, spins, static_cast<double *>(O), st);
+}
+
+nqs_status nqs_logpsi_vjp(nqs_ctx *c, const double *theta, const uint8_t *spins, int64_t ns,
+                          const double *grad_logpsi, double *grad_theta, void *stream) {
+  if (!c || !theta || !spins || !grad_logpsi || !grad_theta || ns <= 0 || ns > c->max_ns)
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ST(pack_any(c, theta, st));
+  ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st,
+             true));
+  return f32(c) ? vjp_T<float>(c, spins, ns, grad_logpsi, grad_theta, st)
+                : vjp_T<double>(c, spins, ns, grad_logpsi, grad_theta, st);
 }
 
 nqs_status nqs_gram(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T, void *stream) {

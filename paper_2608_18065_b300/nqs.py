@@ -54,7 +54,7 @@ class StepOutputs(C.Structure):
 N_STAGES = 14
 SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_set_workspace", "nqs_sample", "nqs_logpsi", "nqs_local_energy",
-           "nqs_jacobian", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
+           "nqs_jacobian", "nqs_logpsi_vjp", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
            "nqs_minsr_step_ex", "nqs_timing_begin", "nqs_timing_end", "nqs_launch_count",
            "nqs_stage_name", "nqs_status_string"]
 
@@ -171,6 +171,14 @@ class Context:
                                   _stream(stream)))
         return O
 
+    def logpsi_vjp(self, theta, spins, grad_logpsi, stream=None):
+        spins = spins.contiguous()
+        g = grad_logpsi.to(torch.float64).contiguous()
+        out = torch.empty(self.np, dtype=torch.float64, device=self.device)
+        _check(lib().nqs_logpsi_vjp(self._h, _ptr(theta), _ptr(spins), C.c_int64(spins.shape[0]),
+                                    _ptr(g), _ptr(out), _stream(stream)))
+        return out
+
     def gram(self, A, stream=None):
         A = A.contiguous()
         R, np_ = A.shape
@@ -241,3 +249,28 @@ def decode_stats(stats: torch.Tensor) -> dict:
     d["status"] = int(v[8:9].view(torch.int32)[0])
     d["solve_fp64"] = int(v[8:9].view(torch.int32)[1])
     return d
+
+
+class LogPsi(torch.autograd.Function):
+    """log Psi(sigma; theta) as a differentiable torch function.
+
+    forward: nqs_logpsi -> (n, 2) FP64 tensor (Re, Im of log Psi).
+    backward: nqs_logpsi_vjp, the hand-written reverse-mode Jacobian kernels
+    contracted with the incoming cotangent on the device.  Gradients flow to
+    theta only (spins are discrete)."""
+
+    @staticmethod
+    def forward(fctx, theta, spins, context):
+        fctx.context = context
+        fctx.save_for_backward(theta, spins)
+        return context.logpsi(theta, spins)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        theta, spins = fctx.saved_tensors
+        g = fctx.context.logpsi_vjp(theta, spins, grad_out)
+        return g, None, None
+
+
+def logpsi(theta, spins, context):
+    return LogPsi.apply(theta, spins, context)
