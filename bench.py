@@ -38,11 +38,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="tfim100")
-    p.add_argument("--matched-steps", type=int, default=40,
+    p.add_argument("--matched-steps", type=int, default=60,
                    help="steps of the mixed and FP64 paths for the matched-energy check (0: skip)")
+    p.add_argument("--matched-eta0", type=float, default=0.1,
+                   help="eta0 of the matched-energy runs (Tab. I's 0.5 collapses this model "
+                        "onto the product state within ~30 steps for both paths)")
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="launch every kernel eagerly")
     return p.parse_args()
 
 
@@ -227,6 +231,7 @@ def run_ours(args):
     hp = copy.copy(hp)
     hp.seed = hp.seed + rank
     ctx = nqs.Context(w.model, w.ham, w.precision, hp.ns, device=dev)
+    ctx.use_graph(not args.no_graph)
     th0 = init_theta(w.model, w.theta_seed)
     thd = torch.tensor(th0, device=dev)
     momd = torch.zeros_like(thd)
@@ -237,7 +242,6 @@ def run_ours(args):
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ctx.timing_begin(K)
     l0 = ctx.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -249,7 +253,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    launches = ctx.launch_count() - l0
+    graph_used = ctx.graph_active()
+    # kernels per step, counted by the library on the eager path (a graph
+    # replay launches the same kernels as one graph)
+    ctx.timing_begin(min(K, 10))
+    lt0 = ctx.launch_count()
+    for t in range(Wu + K, Wu + K + min(K, 10)):
+        ctx.minsr_step(thd, momd, hp, t, stats)
+    torch.cuda.synchronize()
+    per_step = (ctx.launch_count() - lt0) / min(K, 10)
+    launches = int(round(per_step * K))
     stage_ms, nt = ctx.timing_end()
     ms = e0.elapsed_time(e1)
     if world > 1:
@@ -296,7 +309,7 @@ def run_ours(args):
         barrier()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        for t in range(Wu + K, Wu + 2 * K):
+        for t in range(Wu + K + 10, Wu + 2 * K + 10):
             thd.copy_(th_h, non_blocking=True)
             momd.copy_(m_h, non_blocking=True)
             ctx.minsr_step(thd, momd, hp, t, stats)
@@ -342,7 +355,9 @@ def run_ours(args):
     # matched energy error: both paths from theta_0 with the same seeds
     matched = None
     if args.matched_steps > 0 and rank == 0:
-        matched = matched_energy(w, hp, args.matched_steps, dev)
+        hpm = copy.copy(hp)
+        hpm.eta0 = args.matched_eta0
+        matched = matched_energy(w, hpm, args.matched_steps, dev)
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -360,7 +375,8 @@ def run_ours(args):
                                replicas=world),
                 "gram_tflops": gram_tflops,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "fp64_path": fp64, "matched_energy": matched,
+                "clocks": clk, "cuda_graph": graph_used, "fp64_path": fp64,
+                "matched_energy": matched,
                 "stage_ms": {k: v / max(nt, 1) for k, v in stage_ms.items()},
                 "final_stats": st}
         print(json.dumps(line))
@@ -381,7 +397,7 @@ def matched_energy(w, hp, steps, dev):
     N = w.model.N
     B = np.diag(np.full(N, w.ham.h)) + np.diag(np.full(N - 1, w.ham.J), 1)
     E0 = -float(np.sum(np.linalg.svd(B, compute_uv=False)))
-    out = {"E_exact": E0, "steps": steps}
+    out = {"E_exact": E0, "steps": steps, "eta0": hp.eta0}
     for prec in ("mixed", "fp64"):
         c = nqs.Context(w.model, w.ham, prec, hp.ns, device=dev)
         th = torch.tensor(init_theta(w.model, w.theta_seed), device=dev)

@@ -272,6 +272,20 @@ nqs_status nqs_timing_end(nqs_ctx *ctx, double *stage_ms, int *n_steps);
 /* Number of kernels this context has launched since it was created. */
 nqs_status nqs_launch_count(const nqs_ctx *ctx, int64_t *n);
 
+/* --------------------------------------------------------- CUDA graphs */
+
+/* Enable (1) or disable (0) replay of nqs_minsr_step as a CUDA graph.  When
+ * enabled, the first call captures the whole step (on a stream private to
+ * the context) and later calls replay it on the caller's stream; the step
+ * counter lives on the device and advances with every step, so consecutive
+ * step_index values cost one graph launch, any other value one extra tiny
+ * kernel.  A different theta/momentum/stats pointer or any other
+ * hyper-parameter re-captures the graph; nqs_minsr_step_ex with outputs and
+ * steps inside a timing window always launch eagerly.  If capture fails the
+ * context silently keeps launching eagerly (nqs_graph_active reports it). */
+nqs_status nqs_set_graph(nqs_ctx *ctx, int enable);
+nqs_status nqs_graph_active(const nqs_ctx *ctx, int *active);
+
 /* Short text for a status code (static storage). */
 const char *nqs_status_string(int status);
 

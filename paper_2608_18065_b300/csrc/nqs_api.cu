@@ -20,7 +20,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, total;
 };
 
 }  // namespace
@@ -49,6 +49,15 @@ struct nqs_ctx {
   std::vector<cudaEvent_t> tev;
   int tmax = 0, tstep = 0;
   int64_t launches = 0;
+  // CUDA graph of the step (optional)
+  int graph_enabled = 0, graph_broken = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct Key {
+    const void *theta, *mom, *stats;
+    nqs_step_hparams hp;  // step_index ignored
+  } gkey{};
+  int64_t gnext = -1;
 };
 
 namespace {
@@ -163,6 +172,7 @@ void carve(nqs_ctx *c) {
   o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.wv32 = take(R * 4);
   o.dpart32 = take(((R + 63) / 64) * R * 4);
+  o.dstep = take(64);
   o.total = p;
 }
 
@@ -322,6 +332,8 @@ nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
 }
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+__global__ void k_inc_i64(int64_t *p) { *p += 1; }
 
 // Cotangents (re, im) interleaved -> [re block; im block].
 __global__ void k_split_cot(const double *__restrict__ g, int64_t ns, int cplx, double *v) {
@@ -449,7 +461,16 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   // line 3: sample (also fills the hidden-state caches)
   ST(pack_theta<T>(c, theta, st));
   mark(c, 1, st);
-  ST(forward_T<T>(c, MODE_SAMPLE, ns, hp->seed, (uint64_t)hp->step_index, spins, logpsi, st, true));
+  {
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = ns; a.seed = hp->seed; a.step = (uint64_t)hp->step_index;
+    a.step_dev = W<int64_t>(c, c->off.dstep);
+    a.spins = spins; a.logpsi = logpsi;
+    a.gcache = W<T>(c, c->off.gcache);
+    a.gw = c->gw;
+    c->launches += 1;
+    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+  }
   // line 4: local energies, E, variance; eps-bar'
   ST(eloc_T<T>(c, ns, spins, eloc, st));
   mark(c, 5, st);
@@ -504,10 +525,8 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   mark(c, 11, st);
   ST(chol_solve(c, Tm, R, eps, x, sstat, st));
   mark(c, 13, st);
-  double eta_t = hp->eta0;
-  if (hp->decay_T > 0.0 && std::isfinite(hp->decay_T))
-    eta_t = hp->eta0 / (1.0 + (double)hp->step_index / hp->decay_T);
-  k_eta<<<1, 1024, 0, st>>>(eps, x, R, eta_t, hp->trust_region, stats, sstat,
+  k_eta<<<1, 1024, 0, st>>>(eps, x, R, hp->eta0, hp->decay_T, hp->trust_region,
+                            W<int64_t>(c, c->off.dstep), stats, sstat,
                             reinterpret_cast<int32_t *>(W<unsigned>(c, c->off.cbar) + 4));
   CU(cudaGetLastError());
   {
@@ -526,6 +545,9 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
                                                          np, hp->mu, stats);
     CU(cudaGetLastError());
   }
+  k_inc_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep));  // next step's counter
+  c->launches += 1;
+  CU(cudaGetLastError());
   mark(c, 14, st);
   if (c->tstep < c->tmax) ++c->tstep;
   if (out) {
@@ -631,6 +653,8 @@ nqs_status nqs_destroy(nqs_ctx *c) {
   if (!c) return NQS_ERR_ARG;
   cudaDeviceSynchronize();
   timing_free(c);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->d_off) cudaFree(c->d_off);
   if (c->d_diag) cudaFree(c->d_diag);
   if (c->d_opf) cudaFree(c->d_opf);
@@ -734,6 +758,19 @@ nqs_status nqs_regularized_solve(nqs_ctx *c, double *T, int64_t R, double lambda
   return chol_solve(c, T, R, b, x, dev_status, st);
 }
 
+static nqs_status step_body(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
+                            nqs_step_stats *stats, const nqs_step_outputs *out, cudaStream_t st) {
+  return f32(c) ? step_T<float>(c, theta, mom, hp, stats, out, st)
+                : step_T<double>(c, theta, mom, hp, stats, out, st);
+}
+
+static bool same_key(const nqs_ctx::Key &k, const void *th, const void *mo, const void *sts,
+                     const nqs_step_hparams *hp) {
+  nqs_step_hparams a = k.hp, b = *hp;
+  a.step_index = b.step_index = 0;
+  return k.theta == th && k.mom == mo && k.stats == sts && std::memcmp(&a, &b, sizeof(a)) == 0;
+}
+
 nqs_status nqs_minsr_step_ex(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
                              nqs_step_stats *stats, const nqs_step_outputs *out, void *stream) {
   if (!c || !theta || !mom || !hp || !stats) return NQS_ERR_ARG;
@@ -741,8 +778,58 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *c, double *theta, double *mom, const nqs_s
   if (hp->lambda_mode != 0 && hp->lambda_mode != 1) return NQS_ERR_ARG;
   ST(need_ws(c));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return f32(c) ? step_T<float>(c, theta, mom, hp, stats, out, st)
-                : step_T<double>(c, theta, mom, hp, stats, out, st);
+  int64_t *dstep = W<int64_t>(c, c->off.dstep);
+  const bool graph = c->graph_enabled && !c->graph_broken && !out && c->tstep >= c->tmax;
+  if (graph) {
+    if (!c->gexec || !same_key(c->gkey, theta, mom, stats, hp)) {
+      if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+      if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return NQS_ERR_CUDA;
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      nqs_status s = NQS_OK;
+      if (ok) s = step_body(c, theta, mom, hp, stats, nullptr, c->cap_stream);
+      const bool ended = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess;
+      ok = ok && ended && s == NQS_OK && g;
+      if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();  // clear a failed capture's sticky-free error
+      if (!ok) {
+        c->gexec = nullptr;
+        c->graph_broken = 1;  // eager launches from now on
+      } else {
+        c->gkey = nqs_ctx::Key{theta, mom, stats, *hp};
+        c->gnext = -1;
+      }
+    }
+    if (c->gexec) {
+      if (hp->step_index != c->gnext) {
+        k_set_i64<<<1, 1, 0, st>>>(dstep, hp->step_index);
+        c->launches += 1;
+        CU(cudaGetLastError());
+      }
+      CU(cudaGraphLaunch(c->gexec, st));
+      c->gnext = hp->step_index + 1;
+      return NQS_OK;
+    }
+  }
+  k_set_i64<<<1, 1, 0, st>>>(dstep, hp->step_index);
+  c->launches += 1;
+  CU(cudaGetLastError());
+  c->gnext = -1;
+  return step_body(c, theta, mom, hp, stats, out, st);
+}
+
+nqs_status nqs_set_graph(nqs_ctx *c, int enable) {
+  if (!c) return NQS_ERR_ARG;
+  c->graph_enabled = enable != 0;
+  return NQS_OK;
+}
+
+nqs_status nqs_graph_active(const nqs_ctx *c, int *active) {
+  if (!c || !active) return NQS_ERR_ARG;
+  *active = c->gexec != nullptr && !c->graph_broken;
+  return NQS_OK;
 }
 
 nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,

@@ -63,6 +63,7 @@ template <typename T> struct FwdArgs {
   int ntiles;
   // SAMPLE
   uint64_t seed, step;
+  const int64_t *step_dev; // optional: step counter on the device (overrides step)
   // SAMPLE/GIVEN/ELOC spins: SAMPLE writes, others read
   uint8_t *spins;
   double *logpsi;          // [rows*2]
@@ -312,7 +313,8 @@ k_forward(const FwdArgs<T> A) {
         int sg;
         if (MODE == MODE_SAMPLE) {
           double p0 = forced == 0 ? 1.0 : (forced == 1 ? 0.0 : (double)ex(lp0));
-          double uu = uniform53(A.seed, A.step, (uint32_t)my_s, (uint32_t)k);
+          const uint64_t stp = A.step_dev ? (uint64_t)*A.step_dev : A.step;
+          double uu = uniform53(A.seed, stp, (uint32_t)my_s, (uint32_t)k);
           sg = uu < p0 ? 0 : 1;
           ssp[r * NP + k] = (uint8_t)sg;
           A.spins[(int64_t)my_s * N + k] = (uint8_t)sg;

@@ -239,11 +239,12 @@ __global__ void k_lambda(double *T, int64_t R, int mode, double lam_c, double co
   if (threadIdx.x == 0) { st->normT = nT; st->lambda = lam; }
 }
 
-// tau = eps - lambda x (App. F), ||tau||, eta_t = eta0/(1+t/decay_T) and
-// eta* = eta_t/||tau|| in trust-region mode.
+// tau = eps - lambda x (App. F), ||tau||, eta_t = eta0/(1+t/decay_T) with
+// the step t read from the device, and eta* = eta_t/||tau|| in trust-region
+// mode.
 __global__ void k_eta(const double *__restrict__ eps, const double *__restrict__ x, int64_t R,
-                      double eta_t, int trust, nqs_step_stats *st, const int32_t *solve_status,
-                      const int32_t *solve_fp64) {
+                      double eta0, double decay_T, int trust, const int64_t *step_dev,
+                      nqs_step_stats *st, const int32_t *solve_status, const int32_t *solve_fp64) {
   __shared__ double s[1024];
   const double lam = st->lambda;
   double acc = 0.0;
@@ -259,6 +260,8 @@ __global__ void k_eta(const double *__restrict__ eps, const double *__restrict__
   }
   if (threadIdx.x == 0) {
     const double tn = sqrt(s[0]);
+    double eta_t = eta0;
+    if (decay_T > 0.0 && isfinite(decay_T)) eta_t = eta0 / (1.0 + (double)*step_dev / decay_T);
     st->tau_norm = tn;
     st->eta_eff = trust ? eta_t / tn : eta_t;
     if (st->status == NQS_OK && *solve_status != 0) st->status = *solve_status;

@@ -55,7 +55,7 @@ N_STAGES = 14
 SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_set_workspace", "nqs_sample", "nqs_logpsi", "nqs_local_energy",
            "nqs_jacobian", "nqs_logpsi_vjp", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
-           "nqs_minsr_step_ex", "nqs_timing_begin", "nqs_timing_end", "nqs_launch_count",
+           "nqs_minsr_step_ex", "nqs_set_graph", "nqs_graph_active", "nqs_timing_begin", "nqs_timing_end", "nqs_launch_count",
            "nqs_stage_name", "nqs_status_string"]
 
 
@@ -214,6 +214,14 @@ class Context:
             _check(lib().nqs_minsr_step_ex(self._h, _ptr(theta), _ptr(mom), C.byref(hps),
                                            _ptr(stats), C.byref(o), _stream(stream)))
         return stats
+
+    def use_graph(self, enable=True):
+        _check(lib().nqs_set_graph(self._h, 1 if enable else 0))
+
+    def graph_active(self):
+        v = C.c_int()
+        _check(lib().nqs_graph_active(self._h, C.byref(v)))
+        return bool(v.value)
 
     # ------------------------------------------------------ instrumentation
     def timing_begin(self, max_steps):
