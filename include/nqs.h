@@ -71,7 +71,7 @@ typedef enum {
 typedef struct {
   int dim;      /* 1 or 2 */
   int Lx, Ly;   /* N = Lx*Ly; Ly = 1 for dim 1 */
-  int dh;       /* hidden size: 8, 16, 32 or 64 in this build */
+  int dh;       /* hidden size: 8, 16, 32, 64, 96 or 128 in this build */
   int cplx;     /* 1: softsign phase head (cRNN), 0: positive (pRNN) */
   int marshall; /* 1: Marshall sign (-1)^{sigma_A} (Sec. III.C) */
   int zmask;    /* 1: zero-magnetisation mask during sampling (N even) */

@@ -27,6 +27,7 @@ template <typename T> struct BwdArgs {
   T *adj;                   // [nrows][N][adjw]
   int adjw;
   T *adjcol;                // 2D: [nrows][Lx][dh] pending vertical adjoints
+  int wsmem;                // 1: W and [U1|U2] staged in shared memory
 };
 
 // adjoint record of one site: dau | dar | dg | dac (4 dh) | dz0 dz1 dy0 dy1 |
@@ -43,9 +44,10 @@ template <int DH> struct BTile {
 };
 
 template <typename T, int DH, int DIM, int R>
-inline size_t bwd_smem_bytes(int N) {
-  size_t t = 3 * (size_t)DH * DH + 4 * DH + 8;           // Wg, head, hc
-  if (DIM == 2) t += 2 * (size_t)DH * DH + (size_t)DH * R;  // U12, sdp
+inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
+  size_t t = 4 * DH + 8;                                   // head, hc
+  if (wsmem) t += 3 * (size_t)DH * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);  // Wg, U12
+  if (DIM == 2) t += (size_t)DH * R;                       // sdp
   t += 3 * (size_t)DH * R;                                // sda
   size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
   return (b + 127) & ~size_t(127);
@@ -67,11 +69,12 @@ k_jac_bwd(const BwdArgs<T> A) {
   constexpr int C3 = 3 * DH;
   using AJ = Adj<DH, DIM>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *sWg = reinterpret_cast<T *>(smraw);   // [3dh][dh]: Wg[3a+g][b]
-  T *shead = sWg + C3 * DH;                // [4][dh]
+  T *shead = reinterpret_cast<T *>(smraw);  // [4][dh]
   T *shc = shead + 4 * DH;
-  T *sU12 = shc + 8;                       // 2D: [dh][2dh]
-  T *sdp = sU12 + (DIM == 2 ? 2 * DH * DH : 0);  // 2D: adjoint of h' [dh][R]
+  T *swb = shc + 8;                        // staged Wg [3dh][dh] and U12 [dh][2dh] (wsmem)
+  const T *sWg = swb;
+  const T *sU12 = swb + C3 * DH;
+  T *sdp = swb + (A.wsmem ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][R]
   T *sda = sdp + (DIM == 2 ? DH * R : 0);  // gate adjoints [3dh][R]
   const int NP = (A.N + 15) & ~15;
   uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * R);
@@ -89,11 +92,16 @@ k_jac_bwd(const BwdArgs<T> A) {
     const int oWg = al(DH * C3), oxw = al(oWg + C3 * DH);
     const int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
     const int oU12T = al(ohc + 4), oU12 = al(oU12T + 2 * DH * DH);
-    for (int e = tid; e < C3 * DH; e += NTH) sWg[e] = p[oWg + e];
     for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
     if (tid < 4) shc[tid] = p[ohc + tid];
-    if (DIM == 2)
-      for (int e = tid; e < 2 * DH * DH; e += NTH) sU12[e] = p[oU12 + e];
+    if (A.wsmem) {
+      for (int e = tid; e < C3 * DH; e += NTH) swb[e] = p[oWg + e];
+      if (DIM == 2)
+        for (int e = tid; e < 2 * DH * DH; e += NTH) swb[C3 * DH + e] = p[oU12 + e];
+    } else {
+      sWg = p + oWg;
+      sU12 = p + oU12;
+    }
   }
 
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
@@ -275,12 +283,21 @@ template <int DH> struct GTile {
   static constexpr int GT = DH / TA;                       // threads per edge
 };
 
+// Sites per shared-memory chunk of k_jac_grad: static shared memory <= ~45 KB.
+template <typename T, int DH, int DIM> __host__ __device__ constexpr int grad_kc() {
+  return (16 * (Adj<DH, DIM>::W + 4 * DH) * (int)sizeof(T) <= 45000) ? 16
+       : (8 * (Adj<DH, DIM>::W + 4 * DH) * (int)sizeof(T) <= 45000) ? 8 : 4;
+}
+
 template <typename T, typename TO, int DH, int DIM>
 __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
   constexpr int TA = GTile<DH>::TA, GT = GTile<DH>::GT;
-  constexpr int KC = (sizeof(T) == 8 && DH >= 64) ? 8 : 16;  // static smem <= 48 KB
+  constexpr int KC = grad_kc<T, DH, DIM>();
   constexpr int DIN = DIM == 2 ? 4 : 2;
   constexpr int NB = DIM == 2 ? 5 : 3;  // big blocks: Wu_h Wr_h Wh (U1 U2)
+  // above dh = 64 the big blocks are accumulated one per pass (registers)
+  constexpr int BPP = TA <= 4 ? NB : 1;
+  constexpr int NPASS = (NB + BPP - 1) / BPP;
   using AJ = Adj<DH, DIM>;
   const int row = blockIdx.x;
   const int64_t s = row % A.ns;
@@ -295,13 +312,6 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
 
   const bool big = tid < GT * GT;
   const int ta = (tid / GT) * TA, tb = (tid % GT) * TA;
-  T accB[NB][TA][TA];
-#pragma unroll
-  for (int q = 0; q < NB; ++q)
-#pragma unroll
-    for (int i = 0; i < TA; ++i)
-#pragma unroll
-      for (int j = 0; j < TA; ++j) accB[q][i][j] = T(0);
   // small entries: heads (4 dh), x-columns (3 dh din), biases (4 dh + 4)
   const int nsmall = 4 * DH + 3 * DH * DIN + 4 * DH + 4;
   constexpr int SPT = (4 * DH + 3 * DH * DIN + 4 * DH + 4 + 255) / 256;
@@ -312,110 +322,119 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
   const T *adjrow = A.adj + (int64_t)row * N * A.adjw;
   const T *hrow = A.hcache + s * N * DH;
   const uint8_t *sprow = A.spins + s * N;
-  for (int k0 = 0; k0 < N; k0 += KC) {
-    const int kc = min(KC, N - k0);
-    __syncthreads();
-    for (int e = tid; e < kc * AJ::W; e += 256) {
-      int kk = e / AJ::W, w = e - kk * AJ::W;
-      sadj[kk][w] = adjrow[(int64_t)(k0 + kk) * A.adjw + w];
-    }
-    for (int e = tid; e < kc * DH; e += 256) {
-      int kk = e / DH, a = e - kk * DH, k = k0 + kk;
-      sH[kk][a] = hrow[(int64_t)k * DH + a];
-      if (DIM == 1) {
-        sQ[kk][a] = k > 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
-      } else {
-        int j = k / Lx, m = k - j * Lx;
-        int ver = k >= Lx ? k - 2 * m - 1 : -1;
-        sHh[kk][a] = m != 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
-        sHv[kk][a] = ver >= 0 ? hrow[(int64_t)ver * DH + a] : T(0);
-        sQ[kk][a] = adjrow[(int64_t)k * A.adjw + AJ::HP + a];
+  TO *Orow = A.O + (int64_t)row * A.np;
+  const int w = DH + DIN;
+  // big block qb: 0 Wu_h, 1 Wr_h, 2 Wh (adjoint x h'), 3 U1, 4 U2 (adjoint of h' x h_hor/h_ver)
+  auto adj_off = [&](int qb) { return qb == 0 ? 0 : qb == 1 ? DH : qb == 2 ? 2 * DH : AJ::DHP; };
+  for (int pass = 0; pass < NPASS; ++pass) {
+    T accB[BPP][TA][TA];
+#pragma unroll
+    for (int q = 0; q < BPP; ++q)
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < TA; ++j) accB[q][i][j] = T(0);
+    for (int k0 = 0; k0 < N; k0 += KC) {
+      const int kc = min(KC, N - k0);
+      __syncthreads();
+      for (int e = tid; e < kc * AJ::W; e += 256) {
+        int kk = e / AJ::W, wi = e - kk * AJ::W;
+        sadj[kk][wi] = adjrow[(int64_t)(k0 + kk) * A.adjw + wi];
       }
-    }
-    for (int kk = tid; kk < kc; kk += 256) {
-      int k = k0 + kk;
-      if (DIM == 1) {
-        sx[kk][0] = k > 0 ? sprow[k - 1] : -1;
-        sx[kk][1] = -1;
-      } else {
-        int j = k / Lx, m = k - j * Lx;
-        int ver = k >= Lx ? k - 2 * m - 1 : -1;
-        sx[kk][0] = m != 0 ? sprow[k - 1] : -1;
-        sx[kk][1] = ver >= 0 ? 2 + sprow[ver] : -1;
-      }
-    }
-    __syncthreads();
-    if (big) {
-      for (int kk = 0; kk < kc; ++kk) {
-        T q[TA];
-#pragma unroll
-        for (int j = 0; j < TA; ++j) q[j] = sQ[kk][tb + j];
-#pragma unroll
-        for (int i = 0; i < TA; ++i) {
-          const T pu = sadj[kk][ta + i], pr = sadj[kk][DH + ta + i], pg = sadj[kk][2 * DH + ta + i];
-#pragma unroll
-          for (int j = 0; j < TA; ++j) {
-            accB[0][i][j] = fma(pu, q[j], accB[0][i][j]);
-            accB[1][i][j] = fma(pr, q[j], accB[1][i][j]);
-            accB[2][i][j] = fma(pg, q[j], accB[2][i][j]);
-          }
+      for (int e = tid; e < kc * DH; e += 256) {
+        int kk = e / DH, a = e - kk * DH, k = k0 + kk;
+        sH[kk][a] = hrow[(int64_t)k * DH + a];
+        if (DIM == 1) {
+          sQ[kk][a] = k > 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
+        } else {
+          int j = k / Lx, m = k - j * Lx;
+          int ver = k >= Lx ? k - 2 * m - 1 : -1;
+          sHh[kk][a] = m != 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
+          sHv[kk][a] = ver >= 0 ? hrow[(int64_t)ver * DH + a] : T(0);
+          sQ[kk][a] = adjrow[(int64_t)k * A.adjw + AJ::HP + a];
         }
-        if (DIM == 2) {
+      }
+      for (int kk = tid; kk < kc; kk += 256) {
+        int k = k0 + kk;
+        if (DIM == 1) {
+          sx[kk][0] = k > 0 ? sprow[k - 1] : -1;
+          sx[kk][1] = -1;
+        } else {
+          int j = k / Lx, m = k - j * Lx;
+          int ver = k >= Lx ? k - 2 * m - 1 : -1;
+          sx[kk][0] = m != 0 ? sprow[k - 1] : -1;
+          sx[kk][1] = ver >= 0 ? 2 + sprow[ver] : -1;
+        }
+      }
+      __syncthreads();
+      if (big) {
+        for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
-          for (int i = 0; i < TA; ++i) {
-            const T pd = sadj[kk][AJ::DHP + ta + i];
+          for (int q = 0; q < BPP; ++q) {
+            const int qb = pass * BPP + q;
+            if (qb >= NB) break;
+            const T *Qv = qb < 3 ? sQ[kk] : (qb == 3 ? sHh[kk] : sHv[kk]);
+            const int po = adj_off(qb);
+            T qv[TA];
 #pragma unroll
-            for (int j = 0; j < TA; ++j) {
-              accB[NB - 2][i][j] = fma(pd, sHh[kk][tb + j], accB[NB - 2][i][j]);
-              accB[NB - 1][i][j] = fma(pd, sHv[kk][tb + j], accB[NB - 1][i][j]);
+            for (int j = 0; j < TA; ++j) qv[j] = Qv[tb + j];
+#pragma unroll
+            for (int i = 0; i < TA; ++i) {
+              const T pv = sadj[kk][po + ta + i];
+#pragma unroll
+              for (int j = 0; j < TA; ++j) accB[q][i][j] = fma(pv, qv[j], accB[q][i][j]);
             }
           }
         }
       }
-    }
+      if (pass == 0) {
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) {
-      const int e = tid + 256 * q;
-      if (e >= nsmall) continue;
-      T v = accS[q];
-      if (e < 4 * DH) {  // heads: U (o<2) and Uphi (o>=2): sum_k dz/dy[k][o] h_k[b]
-        const int o = e / DH, b = e - o * DH;
-        for (int kk = 0; kk < kc; ++kk) v = fma(sadj[kk][AJ::DZ + o], sH[kk][b], v);
-      } else if (e < 4 * DH + 3 * DH * DIN) {  // x-columns of Wu, Wr, Win
-        const int e2 = e - 4 * DH;
-        const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;
-        const int a = rem / DIN, d = rem - a * DIN;
-        const int off = gsel == 0 ? 0 : (gsel == 1 ? DH : 3 * DH);  // dau, dar, dac
-        for (int kk = 0; kk < kc; ++kk)
-          if (sx[kk][0] == d || sx[kk][1] == d) v += sadj[kk][off + a];
-      } else {  // biases: bu br bh bin (sum of dau dar dg dac), then c, cphi
-        const int e2 = e - 4 * DH - 3 * DH * DIN;
-        if (e2 < 4 * DH) {
-          for (int kk = 0; kk < kc; ++kk) v += sadj[kk][e2];
-        } else {
-          for (int kk = 0; kk < kc; ++kk) v += sadj[kk][AJ::DZ + (e2 - 4 * DH)];
+        for (int q = 0; q < SPT; ++q) {
+          const int e = tid + 256 * q;
+          if (e >= nsmall) continue;
+          T v = accS[q];
+          if (e < 4 * DH) {  // heads: U (o<2) and Uphi (o>=2): sum_k dz/dy[k][o] h_k[b]
+            const int o = e / DH, b2 = e - o * DH;
+            for (int kk = 0; kk < kc; ++kk) v = fma(sadj[kk][AJ::DZ + o], sH[kk][b2], v);
+          } else if (e < 4 * DH + 3 * DH * DIN) {  // x-columns of Wu, Wr, Win
+            const int e2 = e - 4 * DH;
+            const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;
+            const int a = rem / DIN, d = rem - a * DIN;
+            const int off = gsel == 0 ? 0 : (gsel == 1 ? DH : 3 * DH);  // dau, dar, dac
+            for (int kk = 0; kk < kc; ++kk)
+              if (sx[kk][0] == d || sx[kk][1] == d) v += sadj[kk][off + a];
+          } else {  // biases: bu br bh bin (sum of dau dar dg dac), then c, cphi
+            const int e2 = e - 4 * DH - 3 * DH * DIN;
+            if (e2 < 4 * DH) {
+              for (int kk = 0; kk < kc; ++kk) v += sadj[kk][e2];
+            } else {
+              for (int kk = 0; kk < kc; ++kk) v += sadj[kk][AJ::DZ + (e2 - 4 * DH)];
+            }
+          }
+          accS[q] = v;
         }
       }
-      accS[q] = v;
     }
-  }
-  // write the row of O
-  TO *Orow = A.O + (int64_t)row * A.np;
-  const int w = DH + DIN;
-  if (big) {
+    // write this pass's big blocks into the row of O
+    if (big) {
 #pragma unroll
-    for (int i = 0; i < TA; ++i)
+      for (int q = 0; q < BPP; ++q) {
+        const int qb = pass * BPP + q;
+        if (qb >= NB) break;
 #pragma unroll
-      for (int j = 0; j < TA; ++j) {
-        const int a = ta + i, b = tb + j;
-        Orow[A.Wu + (int64_t)a * w + b] = (TO)accB[0][i][j];
-        Orow[A.Wr + (int64_t)a * w + b] = (TO)accB[1][i][j];
-        Orow[A.Wh + (int64_t)a * DH + b] = (TO)accB[2][i][j];
-        if (DIM == 2) {
-          Orow[A.U1 + (int64_t)a * DH + b] = (TO)accB[NB - 2][i][j];
-          Orow[A.U2 + (int64_t)a * DH + b] = (TO)accB[NB - 1][i][j];
-        }
+        for (int i = 0; i < TA; ++i)
+#pragma unroll
+          for (int j = 0; j < TA; ++j) {
+            const int a = ta + i, b2 = tb + j;
+            const TO v = (TO)accB[q][i][j];
+            if (qb == 0) Orow[A.Wu + (int64_t)a * w + b2] = v;
+            else if (qb == 1) Orow[A.Wr + (int64_t)a * w + b2] = v;
+            else if (qb == 2) Orow[A.Wh + (int64_t)a * DH + b2] = v;
+            else if (qb == 3) Orow[A.U1 + (int64_t)a * DH + b2] = v;
+            else Orow[A.U2 + (int64_t)a * DH + b2] = v;
+          }
       }
+    }
   }
 #pragma unroll
   for (int q = 0; q < SPT; ++q) {
@@ -423,9 +442,9 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
     if (e >= nsmall) continue;
     const TO v = (TO)accS[q];
     if (e < 4 * DH) {
-      const int o = e / DH, b = e - o * DH;
-      if (o < 2) Orow[A.Uo + o * DH + b] = v;
-      else if (A.cplx) Orow[A.Up + (o - 2) * DH + b] = v;
+      const int o = e / DH, b2 = e - o * DH;
+      if (o < 2) Orow[A.Uo + o * DH + b2] = v;
+      else if (A.cplx) Orow[A.Up + (o - 2) * DH + b2] = v;
     } else if (e < 4 * DH + 3 * DH * DIN) {
       const int e2 = e - 4 * DH;
       const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;

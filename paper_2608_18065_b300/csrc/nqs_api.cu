@@ -896,5 +896,7 @@ const char *nqs_status_string(int s) {
 }  // extern "C"
 
 namespace nqs {
-bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32 || dh == 64; }
+bool dh_supported(int dh) {
+  return dh == 8 || dh == 16 || dh == 32 || dh == 64 || dh == 96 || dh == 128;
+}
 }  // namespace nqs

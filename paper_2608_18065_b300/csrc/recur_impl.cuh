@@ -12,6 +12,8 @@ namespace nqs {
     case 16: { constexpr int DH = 16; __VA_ARGS__; } break;  \
     case 32: { constexpr int DH = 32; __VA_ARGS__; } break;  \
     case 64: { constexpr int DH = 64; __VA_ARGS__; } break;  \
+    case 96: { constexpr int DH = 96; __VA_ARGS__; } break;  \
+    case 128: { constexpr int DH = 128; __VA_ARGS__; } break;  \
     default: return cudaErrorInvalidValue;                \
   }
 
@@ -19,7 +21,12 @@ template <typename T, int DH, int DIM, int RT, int RG, int MODE>
 static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStream_t st) {
   constexpr int R = RT * RG;
   auto kern = k_forward<T, DH, DIM, RT, RG, MODE>;
-  const size_t smem = fwd_smem_bytes<T, DH, DIM, R>(d.N);
+  size_t smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, true);
+  a.wsmem = 1;
+  if (smem > 200 * 1024) {
+    smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+    a.wsmem = 0;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (MODE != MODE_ELOC) a.ntiles = (int)((a.nrows + R - 1) / R);
@@ -54,7 +61,8 @@ static int eloc_grid_dim(const RecDesc &d) {
   constexpr int RT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
   constexpr int RG = Rows<T>::ELOC_RG;
   auto kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC>;
-  const size_t smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N);
+  size_t smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, true);
+  if (smem > 200 * 1024) smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, false);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int per = 0;
@@ -69,6 +77,8 @@ template <typename T> int eloc_max_grid(const RecDesc &d) {
     case 16: return d.dim == 1 ? eloc_grid_dim<T, 16, 1>(d) : eloc_grid_dim<T, 16, 2>(d);
     case 32: return d.dim == 1 ? eloc_grid_dim<T, 32, 1>(d) : eloc_grid_dim<T, 32, 2>(d);
     case 64: return d.dim == 1 ? eloc_grid_dim<T, 64, 1>(d) : eloc_grid_dim<T, 64, 2>(d);
+    case 96: return d.dim == 1 ? eloc_grid_dim<T, 96, 1>(d) : eloc_grid_dim<T, 96, 2>(d);
+    case 128: return d.dim == 1 ? eloc_grid_dim<T, 128, 1>(d) : eloc_grid_dim<T, 128, 2>(d);
   }
   return 0;
 }
@@ -77,7 +87,12 @@ template <typename T, int DH, int DIM>
 static cudaError_t bwd_dim(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
   constexpr int RT = Rows<T>::BWD_RT, RG = Rows<T>::BWD_RG, R = RT * RG;
   auto kern = k_jac_bwd<T, DH, DIM, RT, RG>;
-  const size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N);
+  size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, true);
+  a.wsmem = 1;
+  if (smem > 200 * 1024) {
+    smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+    a.wsmem = 0;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   a.ntiles = (int)((a.nrows + R - 1) / R);

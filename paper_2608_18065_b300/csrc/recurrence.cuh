@@ -71,6 +71,7 @@ template <typename T> struct FwdArgs {
   T *lccache;              // [rows][N][2]
   T *gcache;               // optional [rows][N][gw]: u | r | c | W_h h'+b_h (| h' in 2D)
   int gw;
+  int wsmem;               // 1: large weight blocks staged in shared memory
   // ELOC
   int tiles_per_op;
   const int *op_f;         // [n_off*4]: f1, f2, start, pad
@@ -81,12 +82,14 @@ template <typename T> struct FwdArgs {
   T *colbuf;               // 2D ELOC: [gridDim][R][Lx][dh]
 };
 
-// Shared-memory footprint of k_forward.
+// Shared-memory footprint of k_forward; wsmem = 0 leaves the two large
+// weight blocks (W^T and, in 2D, [U1 | U2]^T) in global memory (read
+// through L1), for hidden sizes whose weights exceed shared memory.
 template <typename T, int DH, int DIM, int R>
-inline size_t fwd_smem_bytes(int N) {
+inline size_t fwd_smem_bytes(int N, bool wsmem = true) {
   constexpr int DIN = DIM == 2 ? 4 : 2;
-  size_t t = (size_t)DH * 3 * DH + (size_t)DIN * 3 * DH + (size_t)DH * 4 + 4 * DH + 8;
-  if (DIM == 2) t += 2 * (size_t)DH * DH;
+  size_t t = (size_t)DIN * 3 * DH + (size_t)DH * 4 + 4 * DH + 8;
+  if (wsmem) t += (size_t)DH * 3 * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);
   t += (size_t)(DIM == 2 ? 4 : 2) * DH * R;
   size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
   return (b + 127) & ~size_t(127);
@@ -101,13 +104,14 @@ k_forward(const FwdArgs<T> A) {
   constexpr int DIN = DIM == 2 ? 4 : 2;
   constexpr int C3 = 3 * DH;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *sWgT = reinterpret_cast<T *>(smraw);
-  T *sxw = sWgT + DH * C3;
+  T *sxw = reinterpret_cast<T *>(smraw);
   T *sbias = sxw + DIN * C3;
   T *shead = sbias + DH * 4;
   T *shc = shead + 4 * DH;
-  T *sU12T = shc + 8;
-  T *sh0 = sU12T + (DIM == 2 ? 2 * DH * DH : 0);
+  T *sw = shc + 8;                         // staged W^T and [U1|U2]^T (wsmem)
+  const T *sWgT = sw;
+  const T *sU12T = sw + DH * C3;
+  T *sh0 = sw + (A.wsmem ? DH * C3 + (DIM == 2 ? 2 * DH * DH : 0) : 0);
   T *sh1 = sh0 + DH * R;
   T *shv = sh1 + DH * R;                    // 2D: vertical neighbour states
   T *shp = shv + (DIM == 2 ? DH * R : 0);   // 2D: h'
@@ -128,13 +132,18 @@ k_forward(const FwdArgs<T> A) {
     int oWgT = 0, oWg = al(oWgT + DH * C3), oxw = al(oWg + C3 * DH);
     int obias = al(oxw + DIN * C3), ohead = al(obias + DH * 4), ohc = al(ohead + 4 * DH);
     int oU12T = al(ohc + 4);
-    for (int e = tid; e < DH * C3; e += NTH) sWgT[e] = p[oWgT + e];
     for (int e = tid; e < DIN * C3; e += NTH) sxw[e] = p[oxw + e];
     for (int e = tid; e < DH * 4; e += NTH) sbias[e] = p[obias + e];
     for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
     if (tid < 4) shc[tid] = p[ohc + tid];
-    if (DIM == 2)
-      for (int e = tid; e < 2 * DH * DH; e += NTH) sU12T[e] = p[oU12T + e];
+    if (A.wsmem) {
+      for (int e = tid; e < DH * C3; e += NTH) sw[e] = p[oWgT + e];
+      if (DIM == 2)
+        for (int e = tid; e < 2 * DH * DH; e += NTH) sw[DH * C3 + e] = p[oU12T + e];
+    } else {
+      sWgT = p + oWgT;
+      sU12T = p + oU12T;
+    }
   }
 
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {

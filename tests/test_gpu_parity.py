@@ -244,3 +244,49 @@ def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
     xr = np.linalg.solve(T, b)
     kappa = np.linalg.cond(T)
     assert rel_err(x.cpu().numpy(), xr) < 100 * kappa * 2.2e-16
+
+
+# hidden sizes whose weights do not fit shared memory (read through L1)
+BIG = [
+    (ModelSpec(1, 10, 1, 96), HamSpec("tfim")),
+    (ModelSpec(1, 9, 1, 128, cplx=1), HamSpec("cluster_zxz")),
+    (ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.25)),
+    (ModelSpec(2, 4, 3, 96, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.6)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model,ham", BIG, ids=["1d96", "1d128", "2d128", "2d96"])
+def test_large_hidden_sizes(model, ham, prec):
+    ns = 37
+    c = ctx(model, ham, prec, ns)
+    th, thd = theta_dev(model, 8)
+    sp = random_spins(model, ns, seed=2, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    lp = cplx(c.logpsi(thd, spd))
+    el = cplx(c.local_energy(thd, spd))
+    J = c.jacobian(thd, spd).cpu().numpy().astype(np.float64)
+    lp_o, el_o, J_o = O.logpsi(model, th, sp), O.local_energy(model, ham, th, sp), O.jacobian(model, th, sp)
+    if prec == "fp64":
+        np.testing.assert_allclose(lp, lp_o, rtol=RTOL64, atol=RTOL64)
+        assert rel_err(el, el_o) < RTOL64
+        assert rel_err(J, J_o) < RTOL64
+    else:
+        assert np.max(np.abs(lp - lp_o)) < TOL_MIXED_LOGPSI
+        assert rel_err(el, el_o) < TOL_MIXED_ELOC
+        assert rel_err(J, J_o) < TOL_MIXED_JAC
+
+
+def test_large_hidden_size_step_fp64():
+    model, ham = ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.5)
+    hp = HParams(0.1, 1e4, 0.1, lam=0.1, trust_region=1, ns=48)
+    c = ctx(model, ham, "fp64", hp.ns)
+    th, thd = theta_dev(model, 1234)
+    momd = torch.zeros_like(thd)
+    outs = c.step_outputs(hp.ns)
+    c.minsr_step(thd, momd, hp, 0, outputs=outs)
+    torch.cuda.synchronize()
+    th1, _, st_o, b = O.minsr_step(model, ham, th, np.zeros_like(th), hp, 0, want=("spins", "dtheta"))
+    assert np.array_equal(outs["spins"].cpu().numpy(), b["spins"])
+    assert rel_err(outs["dtheta"].cpu().numpy(), b["dtheta"]) < 1e-9
+    assert rel_err(thd.cpu().numpy(), th1) < 1e-9
