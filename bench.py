@@ -143,6 +143,59 @@ def load_traffic(kernel, sha, workload):
     return None
 
 
+def measured_peak(key, fallback):
+    """A peak from the measured MEASURED_PEAKS.json beside this file,
+    else the stated fallback; returns (value, source)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = json.load(open(p)).get(key)
+        if v:
+            return float(v), f"measured ({key})"
+    except (ValueError, OSError):
+        pass
+    return fallback, "fallback"
+
+
+def eloc_tc_used(model, precision):
+    """The connected-configuration engine runs on tcgen05 for mixed 1D, dh=64."""
+    return precision == "mixed" and model.dim == 1 and model.dh == 64
+
+
+def eloc_roofline(w, ms):
+    """Roofline of the connected-configuration engine for one launch.
+
+    Tensor-core engine: per recomputed site of one connected configuration
+    the gate product [1 x dh] x [dh x 3dh] is issued as three BF16 MMAs
+    (hi.hi + hi.lo + lo.hi), 3 * 2 * dh * 3dh tensor-pipe flops; bound by
+    the measured sustained BF16 rate.  SIMT engine: FP32 FMA-pipe flops of
+    the recurrence against the derived FP32 peak."""
+    sites = eloc_suffix_sites(w)
+    if sites is None:
+        return None
+    dh = w.model.dh
+    alg = sites * site_flops(w.model)
+    if eloc_tc_used(w.model, w.precision):
+        fl = sites * 3 * 2 * dh * 3 * dh
+        peak, src = measured_peak("bf16_tflops_sustained", 1400.0)
+        ach = fl / (ms * 1e-3) / 1e12
+        sha = src_sha("paper_2608_18065_b300/csrc/eloc_tc.cu", "paper_2608_18065_b300/csrc/tc_common.cuh")
+        return {"kernel": "k_eloc_tc (eloc_suffix)", "bound": "tensor", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": load_traffic("k_eloc_tc", sha, w.name),
+                "peak_source": src + ", BF16 dense, sustained",
+                "flops_per_launch": fl, "fp32_equiv_flops_per_launch": alg,
+                "fp32_equiv_tflops": alg / (ms * 1e-3) / 1e12, "ms_per_launch": ms}
+    ach = alg / (ms * 1e-3) / 1e12
+    sha = src_sha("paper_2608_18065_b300/csrc/recurrence.cuh",
+                  "paper_2608_18065_b300/csrc/recur_impl.cuh")
+    return {"kernel": "k_forward<MODE_ELOC> (eloc_suffix)", "bound": "alu",
+            "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_ALU_PEAK_TFLOPS,
+            "traffic": load_traffic("k_forward_eloc", sha, w.name),
+            "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
+            "flops_per_launch": alg, "ms_per_launch": ms}
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_bounded(w, budget_s, seed_step=0):
     """Time oracle steps on a sample of Ns_sub configurations sized to the
@@ -179,7 +232,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_2608_18065_b300.inputs import workloads
+    from paper_2608_18065_b300.inputs import batched_instances, workloads
+    if args.workload == "batched16":
+        return run_reference_batched(args)
     w = workloads()[args.workload]
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     for t in range(args.warmup):
@@ -200,6 +255,40 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_batched(args):
+    """Oracle arm of the batched workload: per timed step one bounded oracle
+    step of every instance, each scaled to its full Ns, summed."""
+    from paper_2608_18065_b300.inputs import batched_instances
+    insts = batched_instances()
+    budget = max(0.3, 150.0 / max(1, args.steps + args.warmup) / len(insts))
+    vals, thr, subs = [], 1, []
+    for t in range(args.warmup + args.steps):
+        tot = 0.0
+        for w in insts:
+            v, sub, dt, thr = oracle_bounded(w, budget, t)
+            tot += 1.0 / v
+            subs.append(sub)
+        if t >= args.warmup:
+            vals.append(1.0 / tot)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "batched steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched16_j1j2", "instances": [w.name for w in insts],
+                       "n_instances": len(insts), "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "batched steps/s", "cores": thr,
+                             "kind": "oracle",
+                             "sample": (f"one oracle step per instance per timed step on "
+                                        f"Ns_sub={min(subs)}..{max(subs)} samples, each scaled "
+                                        "to its full Ns, summed over the 16 instances"),
+                             "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": "batched steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -277,24 +366,21 @@ def run_ours(args):
     R = hp.ns * (2 if w.model.cplx else 1)
     gram_ms = stage_ms["gram"] / max(nt, 1)
     gram_tflops = R * (R + 1) * ctx.np / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
+    gram = None
+    if gram_tflops:
+        pk, src = measured_peak("bf16_tflops_sustained", 1400.0)
+        tc = w.precision == "mixed"
+        gram = {"tflops_symmetric": gram_tflops, "ms": gram_ms,
+                "mma_tflops": 3 * gram_tflops if tc else None,
+                "frac_of_bf16": 3 * gram_tflops / pk if tc else None,
+                "peak_source": src if tc else None}
 
     # dominant kernel and its roofline
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     dom_ms = stage_ms[dom] / max(nt, 1)
     roof = None
     if dom == "eloc_suffix":
-        sites = eloc_suffix_sites(w)
-        if sites is not None:
-            fl = sites * site_flops(w.model)
-            ach = fl / (dom_ms * 1e-3) / 1e12
-            sha = src_sha("paper_2608_18065_b300/csrc/recurrence.cuh",
-                          "paper_2608_18065_b300/csrc/recur_impl.cuh")
-            roof = {"kernel": "k_forward<MODE_ELOC> (eloc_suffix)", "bound": "alu",
-                    "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_ALU_PEAK_TFLOPS,
-                    "traffic": load_traffic("eloc_suffix", sha, w.name),
-                    "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
-                    "flops_per_launch": fl, "ms_per_launch": dom_ms}
+        roof = eloc_roofline(w, dom_ms)
     if roof is None:
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None, "ms_per_launch": dom_ms}
@@ -372,13 +458,202 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3+f64",
                 "data": "synthetic",
                 "config": dict(w.describe(), l2="step working set > 126 MB L2 (O, caches, adjoints)",
-                               replicas=world),
-                "gram_tflops": gram_tflops,
+                               replicas=world, workspace_mb=ctx.workspace_bytes / 2**20),
+                "gram_tflops": gram_tflops, "gram": gram,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "cuda_graph": graph_used, "fp64_path": fp64,
                 "matched_energy": matched,
                 "stage_ms": {k: v / max(nt, 1) for k, v in stage_ms.items()},
                 "final_stats": st}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args):
+    """Batched J1-J2 workload: 16 heterogeneous 2D instances (L in {6..12},
+    J2 in {0, .25, .5, .6}, Ns in {256..4096}, dh in {32..128}) stepped
+    together by nqs_minsr_step_batched (one graph per batched step, launch
+    shapes from the autotuner); value = batched steps/s (x16 instance steps)."""
+    import copy
+    import torch
+    import torch.distributed as dist
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import batched_instances, init_theta, param_count
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = batched_instances()
+    n = len(insts)
+    K, Wu = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ctxs = [nqs.Context(w.model, w.ham, "mixed", w.hp.ns, device=dev) for w in insts]
+    th0 = [init_theta(w.model, w.theta_seed) for w in insts]
+    thd = [torch.tensor(t, device=dev) for t in th0]
+    mod = [torch.zeros_like(t) for t in thd]
+    hps = []
+    for w in insts:
+        h = copy.copy(w.hp)
+        h.seed = h.seed + rank
+        hps.append(h)
+    b = nqs.Batch(ctxs)
+    b.use_graph(not args.no_graph)
+    t0 = time.perf_counter()
+    tune_ms = b.autotune(thd, hps, 0)
+    tune_s = time.perf_counter() - t0
+    tuning = [c.tuning() for c in ctxs]
+    stats = b.new_stats()
+    for t in range(Wu):
+        b.step(thd, mod, hps, t, stats)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record()
+    for t in range(Wu, Wu + K):
+        b.step(thd, mod, hps, t, stats)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t_ = torch.tensor([ms], device=dev)
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms = float(t_.item())
+    value = world * K / (ms / 1000.0)
+    st = [nqs.decode_stats(stats[i]) for i in range(n)]
+
+    # per-instance stage times: every instance alone, eager, one step
+    solo = []
+    tot_stage = {}
+    eloc_ms = eloc_flops = gram_ms = gram_fl = 0.0
+    launches = 0
+    for i, (c, w) in enumerate(zip(ctxs, insts)):
+        c.timing_begin(1)
+        l0 = c.launch_count()
+        s1 = c.new_stats()
+        c.minsr_step(thd[i], mod[i], hps[i], Wu + K, s1)
+        torch.cuda.synchronize()
+        launches += c.launch_count() - l0
+        sm, nt = c.timing_end()
+        cfg, sites = c.eloc_work()
+        R = w.hp.ns * (2 if w.model.cplx else 1)
+        np_ = param_count(w.model)
+        for k, v in sm.items():
+            tot_stage[k] = tot_stage.get(k, 0.0) + v
+        eloc_ms += sm["eloc_suffix"]
+        eloc_flops += sites * site_flops(w.model)
+        gram_ms += sm["gram"]
+        gram_fl += R * (R + 1) * np_
+        solo.append({"instance": w.name, "ms": sum(sm.values()), "eloc_configs": cfg,
+                     "workspace_mb": round(c.workspace_bytes / 2**20, 1),
+                     "eloc_sites": sites, "E_re": st[i]["E_re"], "status": st[i]["status"],
+                     "tuning": {k: tuning[i][k] for k in ("eloc_grid", "gram_splits", "solve_grid")}})
+    solo_ms = sum(x["ms"] for x in solo)
+    dom = max(tot_stage, key=lambda k: tot_stage[k])
+    roof = None
+    if dom == "eloc_suffix" and eloc_ms > 0:
+        ach = eloc_flops / (eloc_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_forward<MODE_ELOC> 2D (eloc_suffix, all instances)", "bound": "alu",
+                "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
+                "flops_per_batch": eloc_flops, "ms_per_batch": eloc_ms}
+    if roof is None:
+        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "ms_per_batch": tot_stage[dom]}
+
+    # end to end: every instance's theta and momentum from and back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        th_h = [t.cpu().pin_memory() for t in thd]
+        m_h = [m.cpu().pin_memory() for m in mod]
+        st_h = torch.empty_like(stats, device="cpu").pin_memory()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for t in range(Wu + K + 1, Wu + 2 * K + 1):
+            for i in range(n):
+                thd[i].copy_(th_h[i], non_blocking=True)
+                mod[i].copy_(m_h[i], non_blocking=True)
+            b.step(thd, mod, hps, t, stats)
+            for i in range(n):
+                th_h[i].copy_(thd[i], non_blocking=True)
+                m_h[i].copy_(mod[i], non_blocking=True)
+            st_h.copy_(stats, non_blocking=True)
+        a1.record()
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        nbytes = sum(t.numel() * 8 for t in thd) * 2
+        e2e = {"value": world * K / (ems / 1000.0), "unit": "batched steps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + stats.numel() * 8}
+
+    # the same instances one at a time on the plain FP64 GPU path
+    fp64 = None
+    if args.fp64_steps > 0:
+        f_ms = 0.0
+        per = []
+        for i, w in enumerate(insts):
+            c64 = nqs.Context(w.model, w.ham, "fp64", w.hp.ns, device=dev)
+            t64 = torch.tensor(th0[i], device=dev)
+            m64 = torch.zeros_like(t64)
+            s64 = c64.new_stats()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record()
+            for t in range(args.fp64_steps):
+                c64.minsr_step(t64, m64, hps[i], t, s64)
+            b1.record()
+            torch.cuda.synchronize()
+            d = b0.elapsed_time(b1) / args.fp64_steps
+            f_ms += d
+            per.append(round(d, 3))
+            del c64
+        fp64 = {"batched_steps_per_s": 1000.0 / f_ms, "ms_per_batched_step": f_ms,
+                "instance_ms": per, "steps_per_instance": args.fp64_steps,
+                "speedup_mixed_batched_over_fp64": (1000.0 * K / ms) / (1000.0 / f_ms)}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        tot_s, subs, thr = 0.0, [], 1
+        for w in insts:
+            v, sub, dt, thr = oracle_bounded(w, 1.5)
+            tot_s += 1.0 / v
+            subs.append(sub)
+        cpu = {"value": 1.0 / tot_s, "unit": "batched steps/s", "cores": thr, "kind": "oracle",
+               "sample": (f"one FP64 oracle step per instance on Ns_sub={min(subs)}..{max(subs)} "
+                          "samples, each scaled to its full Ns, summed over the 16 instances"),
+               "cpu": cpu_model()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "batched steps/s", "n_gpus": world,
+                "steps": K, "warmup": Wu, "ms_per_step": ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3+f64",
+                "data": "synthetic",
+                "config": {"workload": "batched16_j1j2", "instances": [w.name for w in insts],
+                           "n_instances": n, "precision": "mixed",
+                           "l2": "step working set > 126 MB L2", "replicas": world},
+                "instance_steps_per_s": n * value,
+                "solo_sum_ms": solo_ms, "concurrency_gain": solo_ms / (ms / K),
+                "gram_tflops": gram_fl / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches * K), "clocks": clk,
+                "cuda_graph": b.graph_active(), "concurrency": b.concurrency(),
+                "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
+                "fp64_path": fp64,
+                "stage_ms_solo_sum": tot_stage, "instances": solo}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -424,6 +699,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched16":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -221,6 +221,95 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
                              nqs_step_stats *dev_stats,
                              const nqs_step_outputs *out, void *stream);
 
+/* ------------------------------------------------------------ autotuner */
+
+/* Launch shapes the autotuner chose for one context (0 = built-in choice). */
+typedef struct {
+  int64_t n_samples;  /* sample count they were measured for (0: not tuned) */
+  int eloc_grid;      /* CTAs of the connected-configuration engine */
+  int gram_splits;    /* K-slices per 128x128 tile of the tensor-core Gram */
+  int solve_grid;     /* CTAs of the cooperative Cholesky / refinement */
+  double ms[3];         /* time of the chosen shape: eloc, gram, solve */
+  double ms_default[3]; /* time of the built-in shape */
+} nqs_tuning;
+
+/* Re-measure even if the process-wide cache holds this problem shape. */
+#define NQS_TUNE_FORCE 1
+
+/* Choose the launch shapes of the step's three largest stages for
+ * hp->n_samples samples by timing candidates on the device: the grid of the
+ * connected-configuration engine (local energies, Sec. II.C), the K-split
+ * of the Gram T (Eq. minsrT) and the grid of the regularized solve.  Runs
+ * one eager step on copies of theta kept in the workspace (theta itself is
+ * not modified), then times every candidate (best of two) with CUDA events;
+ * synchronises `stream`; must not be called during stream capture.  The
+ * choice is kept in the context (used by every later step with the same
+ * sample count, and it invalidates the context's captured graph) and in a
+ * process-wide cache keyed by device, model, Hamiltonian family, precision
+ * and sample count; a later call on a matching context takes the cached
+ * shapes without measuring unless flags has NQS_TUNE_FORCE.  A shape changes
+ * only how the work is spread over CTAs; where that regroups a sum (the
+ * K-slices of T, the row partials of the substitutions) results differ from
+ * the built-in shapes by rounding only, and two contexts with the same
+ * shapes give bit-identical results. */
+nqs_status nqs_autotune(nqs_ctx *ctx, const double *theta,
+                        const nqs_step_hparams *hp, int flags, void *stream);
+nqs_status nqs_get_tuning(const nqs_ctx *ctx, nqs_tuning *out);
+/* Back to the built-in shapes. */
+nqs_status nqs_clear_tuning(nqs_ctx *ctx);
+
+/* ------------------------------------------------------ batched instances */
+
+/* A batch steps n independent contexts (different lattices, hidden sizes,
+ * couplings and sample counts) together.  The paper runs one instance per
+ * GPU; a batch fills one B300 with many.  The batch owns one stream per
+ * instance, the events that fork them from and join them to the caller's
+ * stream, and optionally one CUDA graph of the whole batched step.  The
+ * contexts stay owned by the caller, must outlive the batch, must each have
+ * their own workspace and must not be stepped elsewhere while a batched step
+ * is in flight. */
+typedef struct nqs_batch nqs_batch;
+
+/* ctxs: host array of n distinct contexts (1 <= n <= 4096). */
+nqs_status nqs_batch_create(int n, nqs_ctx *const *ctxs, nqs_batch **out);
+/* Synchronises the device, then frees the batch (not the contexts). */
+nqs_status nqs_batch_destroy(nqs_batch *b);
+
+/* One minSR step of every instance (Algorithm 1 lines 3-9 each, exactly as
+ * nqs_minsr_step of that context would compute it: the results are
+ * bit-identical).  thetas, moms: host arrays of n device pointers [Np_i]
+ * FP64, updated in place; hps: host array of n hyper-parameter sets;
+ * dev_stats: device array of n nqs_step_stats.  The instances run
+ * concurrently on the batch's streams, ordered after the work already on
+ * `stream`, and `stream` waits for all of them; the cooperative solves of
+ * the instances run one after another in instance order, since each of them
+ * spreads over every SM.  Device-side failures of one instance leave only
+ * that instance's theta and momentum unchanged. */
+nqs_status nqs_minsr_step_batched(nqs_batch *b, double *const *thetas,
+                                  double *const *moms,
+                                  const nqs_step_hparams *hps,
+                                  nqs_step_stats *dev_stats, void *stream);
+
+/* Replay the batched step as one CUDA graph (captured on the first call and
+ * again when a pointer, a hyper-parameter other than step_index or the
+ * concurrency changes).  As for nqs_set_graph, failed capture falls back
+ * to eager launches. */
+nqs_status nqs_batch_set_graph(nqs_batch *b, int enable);
+nqs_status nqs_batch_graph_active(const nqs_batch *b, int *active);
+
+/* Number of instance streams (0 or >= n: one per instance; 1: the
+ * instances run back to back). */
+nqs_status nqs_batch_set_concurrency(nqs_batch *b, int streams);
+nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams);
+
+/* nqs_autotune for every instance, then the concurrency, chosen by timing
+ * whole batched steps (best of two) on the workspace copies of theta; the
+ * fastest batched step time goes to *step_ms (may be NULL).  Synchronous;
+ * the callers' thetas are not modified. */
+nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,
+                              const nqs_step_hparams *hps, int flags,
+                              double *step_ms, void *stream);
+
 /* ------------------------------------------------- allocation-free log Psi */
 
 /* Size of the static device scratch array behind nqs_logpsi_noalloc. */
@@ -268,6 +357,14 @@ nqs_status nqs_timing_begin(nqs_ctx *ctx, int max_steps);
  * summed milliseconds of each stage to stage_ms[0..NQS_N_STAGES-1] and the
  * number of timed steps to *n_steps. */
 nqs_status nqs_timing_end(nqs_ctx *ctx, double *stage_ms, int *n_steps);
+
+/* Work of the connected-configuration engine in the last local-energy pass
+ * (nqs_local_energy or a step) of this context: *configs = number of
+ * connected configurations sigma' with H_{sigma sigma'} != 0 off the
+ * diagonal, *sites = sites recomputed for them (sum of N - j over sigma',
+ * j its first changed site).  Synchronous: waits for the device copy of the
+ * per-operator counts, so call it after that pass has completed. */
+nqs_status nqs_eloc_work(const nqs_ctx *ctx, int64_t *configs, int64_t *sites);
 
 /* Number of kernels this context has launched since it was created. */
 nqs_status nqs_launch_count(const nqs_ctx *ctx, int64_t *n);

@@ -3,18 +3,27 @@
 //
 // A connected configuration sigma' differs from its sample sigma from site j
 // on, so its suffix k = j..N-1 is recomputed from the cached state h_{j-1}.
-// Rows of one operator share j; 128 of them form a tile.  Per site the gate
-// pre-activations of the tile are one product [128 x 64] x [64 x 192] (App. A):
-// the FP32 states are split h = hi + lo into BF16 planes in shared memory and
-// tcgen05.mma accumulates hi W_hi + hi W_lo + lo W_hi in FP32 in tensor memory
-// (the weights are split once per CTA).  Each epilogue thread owns one row:
-// it reads its 192 accumulator columns with tcgen05.ld, applies the GRU cell
-// and the heads in FP32 registers, accumulates the change of log Psi in FP64
-// and writes the next BF16 planes.  Two tiles per CTA (two epilogue
-// warpgroups, two accumulators) alternate so that the tensor core works on
-// one tile while the other runs its epilogue; one extra warp issues the MMAs.
-// Every mbarrier wait is bounded; on expiry the CTA flags NQS_ERR_TIMEOUT,
-// drains its MMAs, frees its tensor memory and exits.
+// Rows of one operator share j; 128 of them form a tile.  Per round the tile's
+// FP32 states are split h = hi + lo into BF16 planes in shared memory and one
+// product [128 x 80] x [80 x 208] is accumulated in FP32 in tensor memory as
+// hi W_hi + hi W_lo + lo W_hi (App. A).  K = 64 state columns plus a 16-wide
+// block holding (1, one-hot of sigma'_{k-1}) exactly in BF16, so the gate
+// biases and the one-hot input weights of W_u, W_r and the bias of W_h come
+// out of the MMA too.  Output columns 0..191 are the gate pre-activations of
+// the next site (n = 3a + g: [W_u|W_r][h;x] + b, W_h h + b_h), columns
+// 192..195 the output heads U h, U_phi h of the state itself (Sec. II.A):
+// round r yields the gates of site j + r and the conditional of site
+// j + r - 1, and one extra round after the last site reads the last head.
+// Only W_in x + b_in (outside the reset gate) comes from a small table.
+// The 64 units of a row are split over two warps that read the same
+// tensor-memory lanes, so 16 warps (two tiles x two halves x four lane
+// quarters) share the epilogue; the tensor core alternates between the two
+// tiles.  After a named barrier of its 256 threads one thread of each tile
+// issues the tile's MMAs and commits them to the tile's mbarrier.  Every
+// mbarrier wait is bounded and its outcome is OR-reduced over the tile at
+// the next barrier, so all threads of a tile leave together; on expiry the
+// CTA flags NQS_ERR_TIMEOUT, drains its MMAs, frees its tensor memory and
+// exits.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -26,16 +35,25 @@ namespace {
 
 constexpr int DH = 64;
 constexpr int NG = 3 * DH;                   // gate columns, n = 3a + g
+constexpr int NHD = 16;                      // head columns (4 used)
+constexpr int NB = NG + NHD;                 // MMA N
 constexpr int TR = 128;                      // rows per tile (MMA M)
 constexpr int SLOTS = 2;
-constexpr int EPI = TR * SLOTS;              // epilogue threads
-constexpr int THREADS = EPI + 32;            // + MMA warp
+constexpr int HALVES = 2;                    // warps sharing one row's units
+constexpr int UH = DH / HALVES;              // units per thread
+constexpr int THREADS = TR * SLOTS * HALVES;  // 16 warps
 constexpr int TMEM_COLS = 512;
 constexpr int ACC_STRIDE = 256;              // tensor-memory columns per slot
-constexpr int ATILE = TR * DH * 2;           // one BF16 plane of a row tile (16 KB)
-constexpr int BTILE = NG * DH * 2;           // one BF16 plane of the weights (24 KB)
-constexpr size_t SMEM_BYTES = 1024 + 2 * (size_t)BTILE + 2 * SLOTS * (size_t)ATILE +
-                              sizeof(float) * (DH * 4 + 2 * NG + 4 * DH + 8) + 128;
+constexpr int ATILE = TR * 64 * 2;           // one 128-byte-swizzle atom column of A (16 KB)
+constexpr int BTILE = NB * 64 * 2;           // one atom column of B (26 KB)
+constexpr int XS = DH + 1;                   // padded stride of the W_in x + b_in table
+// B: [hi | lo] x [state atom | augmented atom];  A per slot: hi, lo, augmented
+constexpr size_t SMEM_BYTES = 1024 + 4 * (size_t)BTILE + 3 * SLOTS * (size_t)ATILE + 4 * 8 +
+                              2 * 4 + sizeof(float) * (3 * XS + 4) + 64;
+static_assert(BTILE % 1024 == 0 && ATILE % 1024 == 0, "swizzle atoms stay 1024-aligned");
+static_assert(SMEM_BYTES <= 227 * 1024, "fits one CTA per SM");
+
+constexpr uint16_t BF16_ONE = 0x3F80;
 
 // Two floats rounded to BF16 and packed, x0 in the low half (lower address).
 __device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1) {
@@ -47,49 +65,125 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1) {
 __device__ __forceinline__ float sigm_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float tanh_f(float x) { return 2.0f * sigm_f(2.0f * x) - 1.0f; }
 
+// BF16 hi/lo planes of this thread's UH units of row `row`.
+__device__ __forceinline__ void write_planes(unsigned char *Ahi, unsigned char *Alo, int row,
+                                             int half, const float (&h)[UH]) {
+#pragma unroll
+  for (int c = 0; c < UH / 8; ++c) {
+    uint32_t hp[4], lp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x0 = h[8 * c + 2 * q], x1 = h[8 * c + 2 * q + 1];
+      hp[q] = pack_bf16x2(x0, x1);
+      const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
+      lp[q] = pack_bf16x2(x0 - h0, x1 - h1);
+    }
+    const uint32_t off = sw128_off(row, UH * half + 8 * c);
+    *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+    *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+  }
+}
+
+// Augmented columns of row `row`: (1, [d == 0], [d == 1], 0 ...); d = 2: no input.
+__device__ __forceinline__ void write_aug(unsigned char *Aaug, int row, int d) {
+  const uint32_t w0 = BF16_ONE | ((d == 0 ? (uint32_t)BF16_ONE : 0u) << 16);
+  const uint32_t w1 = d == 1 ? (uint32_t)BF16_ONE : 0u;
+  *reinterpret_cast<uint4 *>(Aaug + sw128_off(row, 0)) = make_uint4(w0, w1, 0u, 0u);
+}
+
+// Named barrier of n threads whose result is the OR of pred over them.
+__device__ __forceinline__ bool bar_any(int id, int n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// One round of the tile's product into tensor memory d, committed to bar.
+// a0: shared address of the tile's A atoms (hi, lo, augmented); b0: of the
+// B atoms (hi, lo, augmented hi, augmented lo).
+__device__ __forceinline__ void issue_round(uint32_t d, uint32_t a0, uint32_t b0, uint32_t bar) {
+  constexpr uint32_t idesc = idesc_bf16(TR, NB);
+  const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + ATILE), ax = sw128_desc(a0 + 2 * ATILE);
+  const uint64_t bh = sw128_desc(b0), bl = sw128_desc(b0 + BTILE);
+  tc_fence_after();
+#pragma unroll
+  for (int kk = 0; kk < DH / 16; ++kk) {
+    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+    mma_bf16(d, ah + adv, bh + adv, idesc, kk > 0 ? 1u : 0u);
+    mma_bf16(d, ah + adv, bl + adv, idesc, 1u);
+    mma_bf16(d, al + adv, bh + adv, idesc, 1u);
+  }
+  // augmented block: exact in BF16, so two products suffice
+  mma_bf16(d, ax, sw128_desc(b0 + 2 * BTILE), idesc, 1u);
+  mma_bf16(d, ax, sw128_desc(b0 + 3 * BTILE), idesc, 1u);
+  mma_commit(bar);
+}
+
+__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, int n, int k,
+                                          float w) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+  *reinterpret_cast<__nv_bfloat16 *>(hi + sw128_off(n, k)) = h;
+  *reinterpret_cast<__nv_bfloat16 *>(lo + sw128_off(n, k)) =
+      __float2bfloat16_rn(w - __bfloat162float(h));
+}
+
 __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(eraw) + 1023) & ~uintptr_t(1023));
-  unsigned char *Bhi = sm, *Blo = sm + BTILE;
-  unsigned char *Abase = sm + 2 * BTILE;     // A(slot, plane) = Abase + (2 slot + plane) ATILE
-  float *sbias = reinterpret_cast<float *>(Abase + 2 * SLOTS * ATILE);  // [DH][4]
-  float *sxw = sbias + DH * 4;               // [2][NG]
-  float *shead = sxw + 2 * NG;               // [4][DH]
-  float *shc = shead + 4 * DH;               // [4]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(shc + 8);  // hready[2] accfull[2] drain
-  int *cmd = reinterpret_cast<int *>(bars + 5);            // [2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cmd + 2);
-  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  unsigned char *Bhi = sm, *Blo = sm + BTILE, *Bxh = sm + 2 * BTILE, *Bxl = sm + 3 * BTILE;
+  unsigned char *Abase = sm + 4 * BTILE;     // A(slot, plane) = Abase + (3 slot + plane) ATILE
+  // mbarriers first: they need 8-byte alignment (this address is 1024-aligned)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(Abase + 3 * SLOTS * ATILE);  // accfull[2] drain[2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+  float *sxi = reinterpret_cast<float *>(tmem_slot + 2);  // [3][XS]
+  float *shc = sxi + 3 * XS;                 // [4]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.N;
+  const int nh = a.cplx ? 4 : 2;
 
-  // weights B[n][k] = W_g[a][k] (n = 3a+g) split into BF16 planes, 128B swizzle
-  for (int e = tid; e < NG * DH; e += THREADS) {
+  // zero the augmented atoms (only their first 16 columns are read)
+  for (int e = tid; e < 2 * BTILE / 16; e += THREADS)
+    reinterpret_cast<uint4 *>(Bxh)[e] = make_uint4(0u, 0u, 0u, 0u);
+  for (int t = 0; t < SLOTS; ++t)
+    for (int e = tid; e < ATILE / 16; e += THREADS)
+      reinterpret_cast<uint4 *>(Abase + (3 * t + 2) * ATILE)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  // weights B[n][k], split into BF16 planes with the 128-byte swizzle:
+  // n < 192: W_g[a][k] (n = 3a + g); 192 + j: head row j; rest zero
+  for (int e = tid; e < NB * DH; e += THREADS) {
     const int n = e / DH, k = e % DH;
-    const float w = a.pack[a.oWgT + k * NG + n];
-    const __nv_bfloat16 h = __float2bfloat16_rn(w);
-    *reinterpret_cast<__nv_bfloat16 *>(Bhi + sw128_off(n, k)) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(Blo + sw128_off(n, k)) =
-        __float2bfloat16_rn(w - __bfloat162float(h));
+    float w = 0.f;
+    if (n < NG) w = a.pack[a.oWgT + k * NG + n];
+    else if (n - NG < nh) w = a.pack[a.ohead + (n - NG) * DH + k];
+    put_split(Bhi, Blo, n, k, w);
   }
-  for (int e = tid; e < DH * 4; e += THREADS) sbias[e] = a.pack[a.obias + e];
-  for (int e = tid; e < 2 * NG; e += THREADS) sxw[e] = a.pack[a.oxw + e];
-  for (int e = tid; e < 4 * DH; e += THREADS) shead[e] = a.pack[a.ohead + e];
+  // augmented rows: column 0 the bias of gate n, columns 1, 2 the one-hot
+  // input weights of the update and reset gates
+  for (int n = tid; n < NG; n += THREADS) {
+    const int q = n / 3, g = n % 3;
+    put_split(Bxh, Bxl, n, 0, a.pack[a.obias + 4 * q + g]);
+    put_split(Bxh, Bxl, n, 1, g < 2 ? a.pack[a.oxw + n] : 0.f);
+    put_split(Bxh, Bxl, n, 2, g < 2 ? a.pack[a.oxw + NG + n] : 0.f);
+  }
+  // W_in x + b_in per previous spin d (0, 1; 2 = none at site 0)
+  for (int e = tid; e < 3 * DH; e += THREADS) {
+    const int d = e / DH, q = e % DH;
+    sxi[d * XS + q] = a.pack[a.obias + 4 * q + 3] + (d < 2 ? a.pack[a.oxw + d * NG + 3 * q + 2] : 0.f);
+  }
   if (tid < 4) shc[tid] = a.pack[a.ohc + tid];
   if (tid == 0) {
-    for (int t = 0; t < SLOTS; ++t) {
-      mbar_init(smem_u32(&bars[t]), TR);       // hready[t]: all rows of the tile
-      mbar_init(smem_u32(&bars[2 + t]), 1);    // accfull[t]: one commit
-      cmd[t] = 1;
-    }
-    mbar_init(smem_u32(&bars[4]), 1);          // drain
-    *abort_flag = 0;
+    for (int t = 0; t < 2 * SLOTS; ++t) mbar_init(smem_u32(&bars[t]), 1);  // one commit each
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_async_smem();
-  if (warp == SLOTS * 4) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(TMEM_COLS)
@@ -101,150 +195,125 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == SLOTS * 4) {
-    // ------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      int alive[SLOTS] = {1, 1};
-      uint32_t ph[SLOTS] = {0, 0};
-      constexpr uint32_t idesc = idesc_bf16(TR, NG);
-      const uint64_t bh = sw128_desc(smem_u32(Bhi)), bl = sw128_desc(smem_u32(Blo));
-      bool ok = true;
-      while (ok && (alive[0] || alive[1])) {
-        for (int t = 0; t < SLOTS && ok; ++t) {
-          if (!alive[t]) continue;
-          if (!mbar_wait(smem_u32(&bars[t]), ph[t])) { ok = false; break; }
-          ph[t] ^= 1;
-          if (*reinterpret_cast<volatile int *>(&cmd[t]) == 0) { alive[t] = 0; continue; }
-          if (*reinterpret_cast<volatile int *>(abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          const uint64_t ah = sw128_desc(smem_u32(Abase + (2 * t) * ATILE));
-          const uint64_t al = sw128_desc(smem_u32(Abase + (2 * t + 1) * ATILE));
-          const uint32_t d = tmem + (uint32_t)(t * ACC_STRIDE);
-#pragma unroll
-          for (int kk = 0; kk < DH / 16; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            mma_bf16(d, ah + adv, bh + adv, idesc, kk > 0 ? 1u : 0u);
-            mma_bf16(d, ah + adv, bl + adv, idesc, 1u);
-            mma_bf16(d, al + adv, bh + adv, idesc, 1u);
-          }
-          mma_commit(smem_u32(&bars[2 + t]));
-        }
-      }
-      if (!ok) {
-        atomicExch(abort_flag, 1);
-        atomicExch(a.err, (int)NQS_ERR_TIMEOUT);
-      }
-      mma_commit(smem_u32(&bars[4]));   // all MMAs issued so far
-      mbar_wait(smem_u32(&bars[4]), 0);
-    }
-  } else {
-    // ---------------------------------------------------------- epilogue
-    const int t = warp / 4;
-    const int row = (warp % 4) * 32 + lane;
-    unsigned char *Ahi = Abase + (2 * t) * ATILE, *Alo = Abase + (2 * t + 1) * ATILE;
-    const uint32_t dcol = tmem + ((uint32_t)((warp % 4) * 32) << 16) + (uint32_t)(t * ACC_STRIDE);
+  {
+    const int t = warp / 8, half = (warp / 4) & 1, quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const bool issuer = (warp & 7) == 0 && lane == 0;
+    unsigned char *Ahi = Abase + (3 * t) * ATILE, *Alo = Ahi + ATILE, *Aaug = Ahi + 2 * ATILE;
+    const uint32_t a0 = smem_u32(Ahi), b0 = smem_u32(Bhi);
+    const uint32_t dacc = tmem + (uint32_t)(t * ACC_STRIDE);
+    const uint32_t accbar = smem_u32(&bars[t]);
+    const uint32_t dcol = dacc + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t gcol = dcol + (uint32_t)(3 * UH * half);  // this half's gate columns
     uint32_t acc_ph = 0;
     bool ok = true;
     for (int tile = blockIdx.x * SLOTS + t; tile < a.ntiles && ok; tile += gridDim.x * SLOTS) {
       const int op = tile / a.tiles_per_op;
       const int base = (tile - op * a.tiles_per_op) * TR;
       const int cnt = a.item_cnt[op];
-      if (base >= cnt) continue;  // uniform over the warpgroup
+      if (base >= cnt) continue;  // uniform over the tile's 256 threads
       const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], j0 = a.op_f[4 * op + 2];
       const bool valid = base + row < cnt;
       const int64_t item = (int64_t)op * a.ns + base + row;
       const int s = valid ? a.item_s[item] : 0;
       const uint8_t *sp = a.spins + (int64_t)s * N;
-      float h[DH];
+      const float *lcrow = a.lccache + (int64_t)s * N * 2;
+      auto spin_at = [&](int k) { return (int)sp[k] ^ ((k == f1 || k == f2) ? 1 : 0); };
+      float h[UH];
+      if (valid && j0 > 0) {
+        const float4 *src =
+            reinterpret_cast<const float4 *>(a.hcache + ((int64_t)s * N + j0 - 1) * DH + UH * half);
 #pragma unroll
-      for (int q = 0; q < DH; ++q)
-        h[q] = (valid && j0 > 0) ? a.hcache[((int64_t)s * N + j0 - 1) * DH + q] : 0.f;
-      int n_up = 0, n_dn = 0;
-      if (a.zmask)
-        for (int k = 0; k < j0; ++k) { if (sp[k] == 0) ++n_up; else ++n_dn; }
-      double dre = 0.0, dimg = 0.0;
-      for (int k = j0; k < N; ++k) {
-        // BF16 planes of h_{k-1} for this row, then hand the tile to the MMA warp
-#pragma unroll
-        for (int c = 0; c < DH / 8; ++c) {
-          uint32_t hp[4], lp[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float x0 = h[8 * c + 2 * q], x1 = h[8 * c + 2 * q + 1];
-            hp[q] = pack_bf16x2(x0, x1);
-            const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
-            lp[q] = pack_bf16x2(x0 - h0, x1 - h1);
-          }
-          const uint32_t off = sw128_off(row, 8 * c);
-          *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-          *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+        for (int c = 0; c < UH / 4; ++c) {
+          const float4 v = src[c];
+          h[4 * c] = v.x; h[4 * c + 1] = v.y; h[4 * c + 2] = v.z; h[4 * c + 3] = v.w;
         }
-        fence_async_smem();
-        tc_fence_before();
-        mbar_arrive(smem_u32(&bars[t]));
-        if (!mbar_wait(smem_u32(&bars[2 + t]), acc_ph)) { ok = false; break; }
+      } else {
+#pragma unroll
+        for (int q = 0; q < UH; ++q) h[q] = 0.f;
+      }
+      int n_up = 0, n_dn = 0;
+      if (a.zmask && half == 0)
+        for (int k = 0; k < j0; ++k) { if (sp[k] == 0) ++n_up; else ++n_dn; }
+      // round 0: planes of h_{j-1} and the input of site j
+      int sprev = j0 > 0 ? spin_at(j0 - 1) : 2;
+      write_planes(Ahi, Alo, row, half, h);
+      if (half == 0) write_aug(Aaug, row, sprev);
+      fence_async_smem();
+      tc_fence_before();
+      if (bar_any(1 + t, 2 * TR, !ok)) { ok = false; break; }
+      if (issuer) issue_round(dacc, a0, b0, accbar);
+      double dre = 0.0, dimg = 0.0;
+      const int L = N - j0;
+      for (int r = 0; r <= L; ++r) {
+        const int k = j0 + r;  // gates of site k (r < L), head of site k - 1 (r > 0)
+        // loads for after the wait: sigma'_k and sigma's cached terms at k - 1
+        const int scur = k < N ? spin_at(k) : 0;
+        float2 lc = make_float2(0.f, 0.f);
+        if (half == 0 && r > 0 && valid) lc = *reinterpret_cast<const float2 *>(lcrow + 2 * (k - 1));
+        if (!mbar_wait(accbar, acc_ph)) ok = false;
         acc_ph ^= 1;
         tc_fence_after();
-        const int d0 = k > 0 ? (sp[k - 1] ^ ((k - 1 == f1 || k - 1 == f2) ? 1 : 0)) : -1;
-        const int sk = sp[k] ^ ((k == f1 || k == f2) ? 1 : 0);
-        float z0 = shc[0], z1 = shc[1], y0 = shc[2], y1 = shc[3];
-#pragma unroll
-        for (int ch = 0; ch < DH / 8; ++ch) {
-          float v0[8], v1[8], v2[8];  // columns 24 ch .. 24 ch + 23 = units 8 ch .. 8 ch + 7
-          tmem_ld8(dcol + (uint32_t)(ch * 24), v0);
-          tmem_ld8(dcol + (uint32_t)(ch * 24 + 8), v1);
-          tmem_ld8(dcol + (uint32_t)(ch * 24 + 16), v2);
+        if (half == 0 && r > 0) {
+          // conditional of site k - 1 from U h_{k-1} (Sec. II.A); sprev = sigma'_{k-1}
+          float hv[8];
+          tmem_ld8(dcol + (uint32_t)NG, hv);
           tmem_wait_ld();
+          float lp0, lp1;
+          log_softmax2<float>(hv[0] + shc[0], hv[1] + shc[1], lp0, lp1);
+          int forced = -1;
+          if (a.zmask) {
+            if (n_up >= N / 2) forced = 1;
+            else if (n_dn >= N / 2) forced = 0;
+          }
+          double lps;
+          if (forced >= 0) lps = (sprev == forced) ? 0.0 : -INFINITY;
+          else lps = (double)(sprev == 0 ? lp0 : lp1);
+          double ph = 0.0;
+          if (a.cplx) ph = NQS_PI * (double)softsign(sprev == 0 ? hv[2] + shc[2] : hv[3] + shc[3]);
+          if (valid) {
+            dre += 0.5 * lps - (double)lc.x;
+            dimg += ph - (double)lc.y;
+          }
+          if (sprev == 0) ++n_up; else ++n_dn;
+        }
+        if (r < L) {
+          // GRU cell of site k (App. A) on this half's units
+          const float *xi = sxi + (k > 0 ? sprev : 2) * XS + UH * half;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int q = ch * 8 + u;
-            const int c0 = 3 * u, c1 = 3 * u + 1, c2 = 3 * u + 2;
-            const float pu = c0 < 8 ? v0[c0] : (c0 < 16 ? v1[c0 - 8] : v2[c0 - 16]);
-            const float pr = c1 < 8 ? v0[c1] : (c1 < 16 ? v1[c1 - 8] : v2[c1 - 16]);
-            const float pg = c2 < 8 ? v0[c2] : (c2 < 16 ? v1[c2 - 8] : v2[c2 - 16]);
-            float au = pu + sbias[4 * q];
-            float ar = pr + sbias[4 * q + 1];
-            const float gg = pg + sbias[4 * q + 2];
-            float ai = sbias[4 * q + 3];
-            if (d0 >= 0) {
-              au += sxw[d0 * NG + 3 * q];
-              ar += sxw[d0 * NG + 3 * q + 1];
-              ai += sxw[d0 * NG + 3 * q + 2];
-            }
-            const float uu = sigm_f(au), rr = sigm_f(ar);
-            const float cc = tanh_f(rr * gg + ai);
-            const float hn = (1.0f - uu) * h[q] + uu * cc;
-            h[q] = hn;
-            z0 = fmaf(shead[q], hn, z0);
-            z1 = fmaf(shead[DH + q], hn, z1);
-            if (a.cplx) {
-              y0 = fmaf(shead[2 * DH + q], hn, y0);
-              y1 = fmaf(shead[3 * DH + q], hn, y1);
+          for (int ch = 0; ch < UH / 4; ++ch) {
+            // columns 3q + g of units 4 ch .. 4 ch + 3; every load starts at a
+            // multiple of its width
+            float v0[4], v1[4], v2[4];
+            tmem_ld4(gcol + (uint32_t)(ch * 12), v0);
+            tmem_ld4(gcol + (uint32_t)(ch * 12 + 4), v1);
+            tmem_ld4(gcol + (uint32_t)(ch * 12 + 8), v2);
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = ch * 4 + u;
+              const int c0 = 3 * u, c1 = 3 * u + 1, c2 = 3 * u + 2;
+              const float pu = c0 < 4 ? v0[c0] : (c0 < 8 ? v1[c0 - 4] : v2[c0 - 8]);
+              const float pr = c1 < 4 ? v0[c1] : (c1 < 8 ? v1[c1 - 4] : v2[c1 - 8]);
+              const float pg = c2 < 4 ? v0[c2] : (c2 < 8 ? v1[c2 - 4] : v2[c2 - 8]);
+              const float uu = sigm_f(pu), rr = sigm_f(pr);
+              const float cc = tanh_f(fmaf(rr, pg, xi[q]));
+              h[q] = fmaf(uu, cc - h[q], h[q]);
             }
           }
+          sprev = scur;
+          write_planes(Ahi, Alo, row, half, h);
+          if (half == 0) write_aug(Aaug, row, sprev);
+          fence_async_smem();
+          tc_fence_before();
+          if (bar_any(1 + t, 2 * TR, !ok)) { ok = false; break; }
+          if (issuer) issue_round(dacc, a0, b0, accbar);
+        } else {
+          tc_fence_before();
+          if (bar_any(1 + t, 2 * TR, !ok)) { ok = false; break; }
         }
-        tc_fence_before();
-        // head of site k (Sec. II.A) and the change against sigma's cached term
-        float lp0, lp1;
-        log_softmax2<float>(z0, z1, lp0, lp1);
-        int forced = -1;
-        if (a.zmask) {
-          if (n_up >= N / 2) forced = 1;
-          else if (n_dn >= N / 2) forced = 0;
-        }
-        double lps;
-        if (forced >= 0) lps = (sk == forced) ? 0.0 : -INFINITY;
-        else lps = (double)(sk == 0 ? lp0 : lp1);
-        double ph = 0.0;
-        if (a.cplx) ph = NQS_PI * (double)softsign(sk == 0 ? y0 : y1);
-        if (valid) {
-          const float *lc = a.lccache + ((int64_t)s * N + k) * 2;
-          dre += 0.5 * lps - (double)lc[0];
-          dimg += ph - (double)lc[1];
-        }
-        if (sk == 0) ++n_up; else ++n_dn;
       }
-      if (ok && valid) {
+      if (ok && valid && half == 0) {
         const double e = a.item_e[item];
         const double mag = exp(dre);
         double *c = a.contrib + ((int64_t)op * a.ns + s) * 2;
@@ -252,15 +321,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
         c[1] = e * mag * sin(dimg);
       }
     }
-    // slot finished (or failed): tell the MMA warp
-    if (row == 0) cmd[t] = 0;
-    if (!ok) atomicExch(abort_flag, 1);
-    mbar_arrive(smem_u32(&bars[t]));
+    // drain this tile's MMAs before the tensor memory is freed
+    if (issuer) {
+      mma_commit(smem_u32(&bars[SLOTS + t]));
+      if (!mbar_wait(smem_u32(&bars[SLOTS + t]), 0)) ok = false;
+    }
+    if (!ok) atomicExch(a.err, (int)NQS_ERR_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == SLOTS * 4)
+  if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS)
                  : "memory");

@@ -18,6 +18,8 @@
 // copies and MMAs (again with a limit), frees its tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <algorithm>
+#include <cmath>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -200,37 +202,66 @@ __global__ void k_split_bf16(const float *__restrict__ A, int64_t R, int64_t np,
 }
 
 // Centring and split in one pass (Algorithm 1 line 5): v = (O - mean)/sqrt(Ns)
-// in FP64, hi = bf16(v), lo = bf16(v - hi); zero columns up to Kpad.
-__global__ void k_center_split(const float *__restrict__ O, int64_t ns, int64_t np, int64_t R,
-                               int64_t Kpad, const double *__restrict__ mean, __nv_bfloat16 *hi,
-                               __nv_bfloat16 *lo) {
-  const double isq = 1.0 / sqrt((double)ns);
-  const int64_t tot = R * Kpad;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / Kpad, k = e - r * Kpad;
-    double v = 0.0;
-    if (k < np) v = ((double)O[r * np + k] - mean[(r / ns) * np + k]) * isq;
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(v - (double)__bfloat162float(h));
-  }
+// with the difference O - mean taken in FP64 (the column means are FP64), then
+// hi = bf16(v), lo = bf16(v - hi) (v - hi is exact in FP32); columns up to
+// Kpad are zero.  Grid (column chunks, rows); each thread owns 8 consecutive
+// columns of one row and writes them as one 16-byte store per plane.
+constexpr int CS_THREADS = 256, CS_COLS = 8;
+
+__device__ __forceinline__ uint32_t bf16x2_rn(float x0, float x1) {
+  uint32_t u;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(x1), "f"(x0));
+  return u;
 }
 
-// Partial sums of O'x from the split planes: part[c][p] = sum_{r in chunk c}
-// (hi + lo)[r][p] x[r], FP64 accumulation.
-__global__ void k_gemv_split_part(const __nv_bfloat16 *__restrict__ hi,
-                                  const __nv_bfloat16 *__restrict__ lo, int64_t R, int64_t np,
-                                  int64_t Kpad, const double *__restrict__ x, int rows_per,
-                                  double *part) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(CS_THREADS) k_center_split(
+    const float *__restrict__ O, int64_t ns, int64_t np, int64_t Kpad,
+    const double *__restrict__ mean, float isq, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+  const int64_t r = blockIdx.y;
+  const int64_t k0 = ((int64_t)blockIdx.x * CS_THREADS + threadIdx.x) * CS_COLS;
+  if (k0 >= Kpad) return;
+  const float *orow = O + r * np;
+  const double *mrow = mean + (r / ns) * np;
+  float v[CS_COLS];
+#pragma unroll
+  for (int j = 0; j < CS_COLS; ++j) {
+    const int64_t k = k0 + j;
+    v[j] = k < np ? (float)((double)orow[k] - mrow[k]) * isq : 0.f;
+  }
+  uint32_t hp[4], lp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hp[q] = bf16x2_rn(v[2 * q], v[2 * q + 1]);
+    const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
+    lp[q] = bf16x2_rn(v[2 * q] - h0, v[2 * q + 1] - h1);
+  }
+  *reinterpret_cast<uint4 *>(hi + r * Kpad + k0) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+  *reinterpret_cast<uint4 *>(lo + r * Kpad + k0) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+}
+
+// Partial sums of O'x from the split planes: part[c][p] = sum over the rows r
+// of chunk c of (hi + lo)[r][p] x[r].  hi + lo is exact in FP32; the products
+// are accumulated in FP32 within a chunk of rows_per rows (x rounded to FP32)
+// and the chunks are summed in FP64 by the caller.  Each thread owns 2
+// adjacent columns (one 4-byte load per plane and row).
+__global__ void __launch_bounds__(256) k_gemv_split_part(
+    const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *__restrict__ lo, int64_t R,
+    int64_t np, int64_t Kpad, const double *__restrict__ x, int rows_per, double *part) {
+  const int64_t p = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (p >= np) return;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
   const int64_t r1 = min64(R, r0 + rows_per);
-  double acc = 0.0;
-  for (int64_t r = r0; r < r1; ++r)
-    acc += ((double)__bfloat162float(hi[r * Kpad + p]) + (double)__bfloat162float(lo[r * Kpad + p])) * x[r];
-  part[(int64_t)blockIdx.y * np + p] = acc;
+  float a0 = 0.f, a1 = 0.f;
+  for (int64_t r = r0; r < r1; ++r) {
+    const uint32_t h = *reinterpret_cast<const uint32_t *>(hi + r * Kpad + p);
+    const uint32_t l = *reinterpret_cast<const uint32_t *>(lo + r * Kpad + p);
+    const float xr = (float)x[r];
+    a0 = fmaf(__uint_as_float(h << 16) + __uint_as_float(l << 16), xr, a0);
+    a1 = fmaf(__uint_as_float(h & 0xffff0000u) + __uint_as_float(l & 0xffff0000u), xr, a1);
+  }
+  double *out = part + (int64_t)blockIdx.y * np + p;
+  out[0] = a0;
+  if (p + 1 < np) out[1] = a1;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -310,10 +341,24 @@ size_t gram_tc_split_bytes(int64_t R, int64_t np) {
 
 int64_t gram_tc_kpad(int64_t np) { return kpad_of(np); }
 
-cudaError_t gram_tc_from_split(const void *hi, const void *lo, int64_t R, int64_t np, double *T,
-                               void *scratch_part, int *err, cudaStream_t st) {
+int gram_tc_max_splits(int64_t R, int64_t np) {
   int nT, tiles, kb, splits;
   plan(R, np, sm_count(), &nT, &tiles, &kb, &splits);
+  const int cap = (tiles + 2 * sm_count()) / tiles;  // partials the scratch holds
+  return std::max(1, std::min(cap, kb));
+}
+
+int gram_tc_default_splits(int64_t R, int64_t np) {
+  int nT, tiles, kb, splits;
+  plan(R, np, sm_count(), &nT, &tiles, &kb, &splits);
+  return splits;
+}
+
+cudaError_t gram_tc_from_split(const void *hi, const void *lo, int64_t R, int64_t np, double *T,
+                               void *scratch_part, int *err, cudaStream_t st, int want_splits = 0) {
+  int nT, tiles, kb, splits;
+  plan(R, np, sm_count(), &nT, &tiles, &kb, &splits);
+  if (want_splits > 0) splits = std::min(want_splits, gram_tc_max_splits(R, np));
   const int64_t Kpad = kpad_of(np);
   CUtensorMap mh, ml;
   if (!make_map(&mh, hi, R, Kpad) || !make_map(&ml, lo, R, Kpad)) return cudaErrorInvalidValue;
@@ -334,8 +379,9 @@ cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, cons
   const int64_t Kpad = kpad_of(np);
   __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(scratch);
   __nv_bfloat16 *lo = hi + R * Kpad;
-  const int blocks = (int)min64((R * Kpad + 255) / 256, 148 * 32);
-  k_center_split<<<blocks, 256, 0, st>>>(O, ns, np, R, Kpad, mean, hi, lo);
+  dim3 g((unsigned)((Kpad + CS_THREADS * CS_COLS - 1) / (CS_THREADS * CS_COLS)), (unsigned)R);
+  k_center_split<<<g, CS_THREADS, 0, st>>>(O, ns, np, Kpad, mean, (float)(1.0 / std::sqrt((double)ns)),
+                                            hi, lo);
   return cudaGetLastError();
 }
 
@@ -344,19 +390,19 @@ cudaError_t gemv_split(const void *scratch, int64_t R, int64_t np, const double 
   const int64_t Kpad = kpad_of(np);
   const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(scratch);
   const __nv_bfloat16 *lo = hi + R * Kpad;
-  dim3 g((unsigned)((np + 255) / 256), (unsigned)((R + rows_per - 1) / rows_per));
+  dim3 g((unsigned)((np + 511) / 512), (unsigned)((R + rows_per - 1) / rows_per));
   k_gemv_split_part<<<g, 256, 0, st>>>(hi, lo, R, np, Kpad, x, rows_per, part);
   return cudaGetLastError();
 }
 
 cudaError_t gram_from_center_split(const void *scratch, int64_t R, int64_t np, double *T, int *err,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int splits) {
   const int64_t Kpad = kpad_of(np);
   const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(scratch);
   const __nv_bfloat16 *lo = hi + R * Kpad;
   const size_t hl = 2 * (size_t)R * Kpad * 2;
   void *part = static_cast<char *>(const_cast<void *>(scratch)) + ((hl + 255) & ~size_t(255));
-  return gram_tc_from_split(hi, lo, R, np, T, part, err, st);
+  return gram_tc_from_split(hi, lo, R, np, T, part, err, st, splits);
 }
 
 cudaError_t gram_tc_bf16x3(const float *A, int64_t R, int64_t np, double *T, void *scratch,

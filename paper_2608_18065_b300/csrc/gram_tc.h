@@ -20,9 +20,14 @@ cudaError_t gram_tc_bf16x3(const float *A, int64_t R, int64_t np, double *T, voi
 // FP64 column means, scale by 1/sqrt(ns), split into the scratch planes ...
 cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const double *mean,
                          void *scratch, cudaStream_t st);
-// ... T from those planes ...
+// ... T from those planes (splits: K-slices per output tile, 0 = built-in
+// plan, capped at gram_tc_max_splits) ...
 cudaError_t gram_from_center_split(const void *scratch, int64_t R, int64_t np, double *T, int *err,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int splits = 0);
+// Largest K-split the scratch of gram_tc_split_bytes(R, np) holds, and the
+// built-in plan's choice.
+int gram_tc_max_splits(int64_t R, int64_t np);
+int gram_tc_default_splits(int64_t R, int64_t np);
 // ... and partial sums of O'x from the same planes.
 cudaError_t gemv_split(const void *scratch, int64_t R, int64_t np, const double *x, int rows_per,
                        double *part, cudaStream_t st);

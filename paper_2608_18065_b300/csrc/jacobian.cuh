@@ -27,7 +27,6 @@ template <typename T> struct BwdArgs {
   T *adj;                   // [nrows][N][adjw]
   int adjw;
   T *adjcol;                // 2D: [nrows][Lx][dh] pending vertical adjoints
-  int wsmem;                // 1: W and [U1|U2] staged in shared memory
 };
 
 // adjoint record of one site: dau | dar | dg | dac (4 dh) | dz0 dz1 dy0 dy1 |
@@ -60,7 +59,8 @@ inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
 // head adjoint follows from the stored terms: p(sigma_k) = exp(2 lc_0),
 // p(other) = 1 - p(sigma_k) (a site fixed by the mask has p = 1 and no
 // gradient), and the softsign slope pi (1 - |phi_k/pi|)^2.
-template <typename T, int DH, int DIM, int RT, int RG>
+// WS: W and [U1|U2] staged in shared memory (otherwise read through L1).
+template <typename T, int DH, int DIM, int RT, int RG, bool WS = true>
 __global__ void __launch_bounds__(BTile<DH>::UG * RG)
 k_jac_bwd(const BwdArgs<T> A) {
   constexpr int UG = BTile<DH>::UG, UT = BTile<DH>::UT;
@@ -74,7 +74,7 @@ k_jac_bwd(const BwdArgs<T> A) {
   T *swb = shc + 8;                        // staged Wg [3dh][dh] and U12 [dh][2dh] (wsmem)
   const T *sWg = swb;
   const T *sU12 = swb + C3 * DH;
-  T *sdp = swb + (A.wsmem ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][R]
+  T *sdp = swb + (WS ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][R]
   T *sda = sdp + (DIM == 2 ? DH * R : 0);  // gate adjoints [3dh][R]
   const int NP = (A.N + 15) & ~15;
   uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * R);
@@ -94,7 +94,7 @@ k_jac_bwd(const BwdArgs<T> A) {
     const int oU12T = al(ohc + 4), oU12 = al(oU12T + 2 * DH * DH);
     for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
     if (tid < 4) shc[tid] = p[ohc + tid];
-    if (A.wsmem) {
+    if constexpr (WS) {
       for (int e = tid; e < C3 * DH; e += NTH) swb[e] = p[oWg + e];
       if (DIM == 2)
         for (int e = tid; e < 2 * DH * DH; e += NTH) swb[C3 * DH + e] = p[oU12 + e];

@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "chol_coop.cuh"
@@ -20,7 +23,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, total;
 };
 
 }  // namespace
@@ -34,6 +37,7 @@ struct nqs_ctx {
   PackOff P;
   RecDesc rd;
   int n_off = 0, n_diag = 0;
+  std::vector<int> op_start;  // first changed site of each off-diagonal operator
   OffOp *d_off = nullptr;
   DiagOp *d_diag = nullptr;
   int *d_opf = nullptr;
@@ -58,6 +62,13 @@ struct nqs_ctx {
     nqs_step_hparams hp;  // step_index ignored
   } gkey{};
   int64_t gnext = -1;
+  // launch shapes chosen by nqs_autotune for tuned_ns samples (0 = built-in)
+  int64_t tuned_ns = 0;
+  int t_eloc_grid = 0, t_gram_splits = 0, t_solve_grid = 0;
+  double t_ms[3] = {0, 0, 0}, t_ms_default[3] = {0, 0, 0};
+  int64_t cur_ns = 0;  // sample count of the step being issued
+  // batched steps: order this context's cooperative solve after another's
+  cudaEvent_t solve_wait = nullptr, solve_rec = nullptr;
 };
 
 namespace {
@@ -173,12 +184,26 @@ void carve(nqs_ctx *c) {
   o.wv32 = take(R * 4);
   o.dpart32 = take(((R + 63) / 64) * R * 4);
   o.dstep = take(64);
+  o.tth = take(np * 8);
+  o.tmo = take(np * 8);
+  o.tstats = take(256);
   o.total = p;
 }
 
 template <typename T> T *W(nqs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
 
 nqs_status need_ws(nqs_ctx *c) { return c->ws ? NQS_OK : NQS_ERR_WORKSPACE; }
+
+// Tuned launch shapes apply to the sample count they were measured for.
+bool tuned(const nqs_ctx *c) { return c->tuned_ns > 0 && c->tuned_ns == c->cur_ns; }
+int eloc_grid_cap(const nqs_ctx *c, int dflt) {
+  return tuned(c) && c->t_eloc_grid > 0 ? std::min(c->t_eloc_grid, dflt) : dflt;
+}
+int gram_splits(const nqs_ctx *c) { return tuned(c) ? c->t_gram_splits : 0; }
+int solve_grid(const nqs_ctx *c) {
+  return tuned(c) && c->t_solve_grid > 0 ? std::min(c->t_solve_grid, c->rd.sm_count)
+                                         : c->rd.sm_count;
+}
 
 // Record stage boundary i of the current step when a timing window is open.
 void mark(nqs_ctx *c, int i, cudaStream_t st) {
@@ -267,9 +292,9 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.op_f = c->d_opf; e.item_s = a.item_s; e.item_e = a.item_e; e.item_cnt = a.item_cnt;
       e.contrib = a.contrib;
       e.err = W<int>(c, c->off.sstat);
-      CU(eloc_tc_run(e, c->rd.sm_count, st));
+      CU(eloc_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
-      CU(run_forward<T>(c->rd, MODE_ELOC, a, c->eloc_grid, st));
+      CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
     }
   } else {
     mark(c, 3, st);
@@ -397,7 +422,7 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
                       int32_t *status, cudaStream_t st) {
   unsigned *bar = W<unsigned>(c, c->off.cbar);
   int32_t *need = reinterpret_cast<int32_t *>(bar + 4);
-  const int G = c->rd.sm_count;
+  const int G = solve_grid(c);
   CU(cudaMemsetAsync(bar, 0, 32, st));
   if (f32(c)) {
     CholIrArgs ir;
@@ -456,6 +481,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   double *eps = W<double>(c, c->off.eps);
   double *x = W<double>(c, c->off.x);
   int32_t *sstat = W<int32_t>(c, c->off.sstat);
+  c->cur_ns = ns;
   mark(c, 0, st);
   CU(cudaMemsetAsync(sstat, 0, 64, st));
   // line 3: sample (also fills the hidden-state caches)
@@ -506,7 +532,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   mark(c, 9, st);
   if (tc) {
     c->launches += 2;
-    CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, sstat, st));
+    CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, sstat, st, gram_splits(c)));
   } else {
     ST(gram_any(c, O, R, np, Tm, st));
   }
@@ -523,7 +549,9 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   }
   // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
   mark(c, 11, st);
+  if (c->solve_wait) CU(cudaStreamWaitEvent(st, c->solve_wait, 0));
   ST(chol_solve(c, Tm, R, eps, x, sstat, st));
+  if (c->solve_rec) CU(cudaEventRecord(c->solve_rec, st));
   mark(c, 13, st);
   k_eta<<<1, 1024, 0, st>>>(eps, x, R, hp->eta0, hp->decay_T, hp->trust_region,
                             W<int64_t>(c, c->off.dstep), stats, sstat,
@@ -631,6 +659,7 @@ nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int 
   build_hamiltonian(m, *ham, off, dg);
   c->n_off = (int)off.size();
   c->n_diag = (int)dg.size();
+  for (const OffOp &o : off) c->op_start.push_back(o.start);
   std::vector<int> opf(4 * std::max<size_t>(off.size(), 1));
   for (size_t i = 0; i < off.size(); ++i) {
     opf[4 * i] = off[i].f1; opf[4 * i + 1] = off[i].f2; opf[4 * i + 2] = off[i].start; opf[4 * i + 3] = 0;
@@ -706,6 +735,7 @@ nqs_status nqs_local_energy(nqs_ctx *c, const double *theta, const uint8_t *spin
   if (!c || !theta || !spins || !eloc || ns <= 0 || ns > c->max_ns) return NQS_ERR_ARG;
   ST(need_ws(c));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  c->cur_ns = ns;
   ST(pack_any(c, theta, st));
   ST(forward(c, MODE_GIVEN, ns, 0, 0, const_cast<uint8_t *>(spins), W<double>(c, c->off.logpsi), st));
   return eloc_any(c, ns, spins, eloc, st);
@@ -750,6 +780,7 @@ nqs_status nqs_regularized_solve(nqs_ctx *c, double *T, int64_t R, double lambda
   if (R > (c->L.cplx ? 2 * c->max_ns : c->max_ns)) return NQS_ERR_ARG;
   ST(need_ws(c));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  c->cur_ns = c->L.cplx ? R / 2 : R;
   CU(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), st));
   if (lambda != 0.0) {
     k_shift<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(T, R, lambda);
@@ -835,6 +866,492 @@ nqs_status nqs_graph_active(const nqs_ctx *c, int *active) {
 nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams *hp,
                           nqs_step_stats *stats, void *stream) {
   return nqs_minsr_step_ex(c, theta, mom, hp, stats, nullptr, stream);
+}
+
+// ------------------------------------------------------------- autotuner
+
+}  // extern "C"
+
+namespace {
+
+struct Tuned {
+  int eloc_grid, gram_splits, solve_grid;
+  double ms[3], ms_default[3];
+};
+std::mutex g_tune_mu;
+std::map<std::string, Tuned> g_tune_cache;  // process-wide, keyed by problem shape
+
+std::string tune_key(const nqs_ctx *c, int64_t ns) {
+  char b[256];
+  const int dev = [] { int d = 0; cudaGetDevice(&d); return d; }();
+  std::snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%lld", dev, c->m.dim, c->m.Lx,
+                c->m.Ly, c->m.dh, c->m.cplx, c->m.zmask, c->h.family, c->prec,
+                c->n_off, (long long)ns);
+  return b;
+}
+
+struct EvPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool ok() {
+    return cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+  }
+  ~EvPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// Best of `reps` timings of body(); pre() runs untimed before each.
+template <class Pre, class Body>
+nqs_status best_ms(cudaStream_t st, int reps, Pre pre, Body body, double *out) {
+  EvPair ev;
+  if (!ev.ok()) return NQS_ERR_CUDA;
+  double best = 1e300;
+  for (int r = 0; r < reps; ++r) {
+    ST(pre());
+    CU(cudaEventRecord(ev.a, st));
+    ST(body());
+    CU(cudaEventRecord(ev.b, st));
+    CU(cudaEventSynchronize(ev.b));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    best = std::min(best, (double)ms);
+  }
+  *out = best;
+  return NQS_OK;
+}
+
+// T from the current centred O (untimed part of the solve measurement).
+template <typename T>
+nqs_status regram(nqs_ctx *c, int64_t ns, const nqs_step_hparams &h, nqs_step_stats *stats,
+                  cudaStream_t st) {
+  const int64_t R = c->L.cplx ? 2 * ns : ns, np = c->L.np;
+  double *Tm = W<double>(c, c->off.T);
+  if (f32(c) && gram_tc_available())
+    CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, W<int>(c, c->off.sstat), st, 0));
+  else
+    ST(gram_any(c, W<T>(c, c->off.O), R, np, Tm, st));
+  k_frob_part<<<256, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
+  k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), 256, h.lambda_mode,
+                                      h.lambda, h.lambda_coeff, h.lambda_pow, stats);
+  return cu(cudaGetLastError());
+}
+
+void uniq_push(std::vector<int> &v, int x) {
+  if (x >= 1 && std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+}
+
+template <typename T>
+nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *hp, cudaStream_t st) {
+  const int64_t ns = hp->n_samples, np = c->L.np;
+  const int64_t R = c->L.cplx ? 2 * ns : ns;
+  double *tth = W<double>(c, c->off.tth), *tmo = W<double>(c, c->off.tmo);
+  nqs_step_stats *tstats = W<nqs_step_stats>(c, c->off.tstats);
+  // one eager step on scratch copies fills the caches, O, the split planes and T
+  c->tuned_ns = 0;
+  CU(cudaMemcpyAsync(tth, theta, np * 8, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemsetAsync(tmo, 0, np * 8, st));
+  k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hp->step_index);
+  ST(step_T<T>(c, tth, tmo, hp, tstats, nullptr, st));
+  CU(cudaStreamSynchronize(st));
+  c->tuned_ns = ns;
+  c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
+  const int reps = 2;
+  auto none = [] { return NQS_OK; };
+  uint8_t *spins = W<uint8_t>(c, c->off.spins);
+  double *eloc = W<double>(c, c->off.eloc);
+  // (1) grid of the connected-configuration engine
+  {
+    const bool tce = f32(c) && gram_tc_available() && eloc_tc_supported(c->L.dim, c->L.dh);
+    const int emax = tce ? c->rd.sm_count : c->eloc_grid;
+    std::vector<int> cand;
+    for (int d : {1, 2, 4}) uniq_push(cand, emax / d);
+    uniq_push(cand, emax * 3 / 4);
+    double best = 1e300;
+    int pick = emax;
+    for (int g : cand) {
+      c->t_eloc_grid = g;
+      double ms = 0;
+      ST(best_ms(st, reps, none, [&] { return eloc_T<T>(c, ns, spins, eloc, st); }, &ms));
+      if (g == emax) c->t_ms_default[0] = ms;
+      if (ms < best) { best = ms; pick = g; }
+    }
+    c->t_eloc_grid = pick;
+    c->t_ms[0] = best;
+  }
+  // (2) K-split of the tensor-core Gram
+  if (f32(c) && gram_tc_available()) {
+    const int smax = gram_tc_max_splits(R, np), sdef = gram_tc_default_splits(R, np);
+    std::vector<int> cand;
+    uniq_push(cand, sdef);
+    for (int q : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+      if (q <= smax) uniq_push(cand, q);
+    double best = 1e300;
+    int pick = sdef;
+    double *Tm = W<double>(c, c->off.T);
+    for (int q : cand) {
+      double ms = 0;
+      ST(best_ms(st, reps, none, [&] {
+        return cu(gram_from_center_split(c->ws + c->off.split, R, np, Tm,
+                                         W<int>(c, c->off.sstat), st, q));
+      }, &ms));
+      if (q == sdef) c->t_ms_default[1] = ms;
+      if (ms < best) { best = ms; pick = q; }
+    }
+    c->t_gram_splits = pick;
+    c->t_ms[1] = best;
+  }
+  // (3) grid of the cooperative solve (T rebuilt before every timed solve)
+  {
+    const int G0 = c->rd.sm_count;
+    std::vector<int> cand;
+    for (int d : {1, 2, 4, 8}) uniq_push(cand, G0 / d);
+    double best = 1e300;
+    int pick = G0;
+    double *Tm = W<double>(c, c->off.T);
+    for (int g : cand) {
+      c->t_solve_grid = g;
+      double ms = 0;
+      ST(best_ms(st, reps, [&] { return regram<T>(c, ns, *hp, tstats, st); },
+                 [&] {
+                   return chol_solve(c, Tm, R, W<double>(c, c->off.eps), W<double>(c, c->off.x),
+                                     W<int32_t>(c, c->off.sstat), st);
+                 }, &ms));
+      if (g == G0) c->t_ms_default[2] = ms;
+      if (ms < best) { best = ms; pick = g; }
+    }
+    c->t_solve_grid = pick;
+    c->t_ms[2] = best;
+  }
+  return NQS_OK;
+}
+
+void drop_graph(nqs_ctx *c) {
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+}
+
+}  // namespace
+
+extern "C" {
+
+nqs_status nqs_autotune(nqs_ctx *c, const double *theta, const nqs_step_hparams *hp, int flags,
+                        void *stream) {
+  if (!c || !theta || !hp) return NQS_ERR_ARG;
+  if (hp->n_samples < 2 || hp->n_samples > c->max_ns) return NQS_ERR_ARG;
+  if (hp->lambda_mode != 0 && hp->lambda_mode != 1) return NQS_ERR_ARG;
+  if (flags & ~NQS_TUNE_FORCE) return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const std::string key = tune_key(c, hp->n_samples);
+  drop_graph(c);
+  if (!(flags & NQS_TUNE_FORCE)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const Tuned &t = it->second;
+      c->tuned_ns = hp->n_samples;
+      c->t_eloc_grid = t.eloc_grid; c->t_gram_splits = t.gram_splits; c->t_solve_grid = t.solve_grid;
+      std::memcpy(c->t_ms, t.ms, sizeof t.ms);
+      std::memcpy(c->t_ms_default, t.ms_default, sizeof t.ms_default);
+      return NQS_OK;
+    }
+  }
+  const int64_t saved_tmax = c->tmax;
+  c->tmax = c->tstep;  // no timing marks while tuning
+  nqs_status s = f32(c) ? autotune_T<float>(c, theta, hp, st) : autotune_T<double>(c, theta, hp, st);
+  c->tmax = (int)saved_tmax;
+  if (s != NQS_OK) {
+    c->tuned_ns = 0;
+    return s;
+  }
+  Tuned t{c->t_eloc_grid, c->t_gram_splits, c->t_solve_grid, {}, {}};
+  std::memcpy(t.ms, c->t_ms, sizeof t.ms);
+  std::memcpy(t.ms_default, c->t_ms_default, sizeof t.ms_default);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = t;
+  return NQS_OK;
+}
+
+nqs_status nqs_get_tuning(const nqs_ctx *c, nqs_tuning *out) {
+  if (!c || !out) return NQS_ERR_ARG;
+  out->n_samples = c->tuned_ns;
+  out->eloc_grid = c->t_eloc_grid;
+  out->gram_splits = c->t_gram_splits;
+  out->solve_grid = c->t_solve_grid;
+  for (int i = 0; i < 3; ++i) { out->ms[i] = c->t_ms[i]; out->ms_default[i] = c->t_ms_default[i]; }
+  return NQS_OK;
+}
+
+nqs_status nqs_clear_tuning(nqs_ctx *c) {
+  if (!c) return NQS_ERR_ARG;
+  drop_graph(c);
+  c->tuned_ns = 0;
+  c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
+  return NQS_OK;
+}
+
+// ------------------------------------------------------------ batched step
+
+}  // extern "C"
+
+struct nqs_batch {
+  std::vector<nqs_ctx *> ctx;
+  int conc = 0;  // instance streams in use (0: one per instance)
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> done, solved;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_enabled = 0, graph_broken = 0;
+  struct Key {
+    std::vector<const void *> ptr;  // theta, momentum, stats of every instance
+    std::vector<nqs_step_hparams> hp;
+    int conc;
+  } key;
+  std::vector<int64_t> gnext;
+};
+
+namespace {
+
+void batch_free(nqs_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaStream_t s : b->st) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->solved) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+int batch_conc(const nqs_batch *b) {
+  const int n = (int)b->ctx.size();
+  return b->conc > 0 && b->conc < n ? b->conc : n;
+}
+
+// Fork the instances' steps from `origin` onto the instance streams and join
+// them back; cooperative solves run one after another (instance order).
+nqs_status batch_issue(nqs_batch *b, double *const *th, double *const *mo,
+                       const nqs_step_hparams *hps, nqs_step_stats *const *stats, bool set_steps,
+                       cudaStream_t origin) {
+  const int n = (int)b->ctx.size(), q = batch_conc(b);
+  CU(cudaEventRecord(b->fork, origin));
+  for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+  nqs_status s = NQS_OK;
+  for (int i = 0; i < n && s == NQS_OK; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    cudaStream_t st = b->st[i % q];
+    if (set_steps) {
+      k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
+      c->launches += 1;
+    }
+    c->solve_wait = i > 0 ? b->solved[i - 1] : nullptr;
+    c->solve_rec = b->solved[i];
+    s = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, st);
+    c->solve_wait = c->solve_rec = nullptr;
+  }
+  for (int j = 0; j < q; ++j) {
+    CU(cudaEventRecord(b->done[j], b->st[j]));
+    CU(cudaStreamWaitEvent(origin, b->done[j], 0));
+  }
+  return s;
+}
+
+nqs_status batch_check(nqs_batch *b, double *const *th, double *const *mo,
+                       const nqs_step_hparams *hps) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    nqs_ctx *c = b->ctx[i];
+    if (!th[i] || !mo[i]) return NQS_ERR_ARG;
+    if (hps[i].n_samples < 2 || hps[i].n_samples > c->max_ns) return NQS_ERR_ARG;
+    if (hps[i].lambda_mode != 0 && hps[i].lambda_mode != 1) return NQS_ERR_ARG;
+    ST(need_ws(c));
+  }
+  return NQS_OK;
+}
+
+nqs_status batch_step(nqs_batch *b, double *const *th, double *const *mo,
+                      const nqs_step_hparams *hps, nqs_step_stats *const *stats, cudaStream_t st) {
+  const int n = (int)b->ctx.size();
+  bool timing = false;
+  for (nqs_ctx *c : b->ctx) timing |= c->tstep < c->tmax;
+  if (b->graph_enabled && !b->graph_broken && !timing) {
+    nqs_batch::Key k;
+    for (int i = 0; i < n; ++i) {
+      k.ptr.push_back(th[i]); k.ptr.push_back(mo[i]); k.ptr.push_back(stats[i]);
+      nqs_step_hparams h = hps[i];
+      h.step_index = 0;
+      k.hp.push_back(h);
+    }
+    k.conc = batch_conc(b);
+    bool same = b->gexec && k.ptr == b->key.ptr && k.conc == b->key.conc;
+    for (int i = 0; same && i < n; ++i)
+      same = std::memcmp(&k.hp[i], &b->key.hp[i], sizeof(nqs_step_hparams)) == 0;
+    if (!same) {
+      if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      nqs_status s = NQS_OK;
+      if (ok) s = batch_issue(b, th, mo, hps, stats, false, b->cap);
+      const bool ended = cudaStreamEndCapture(b->cap, &g) == cudaSuccess;
+      ok = ok && ended && s == NQS_OK && g;
+      if (ok) ok = cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (!ok) {
+        b->gexec = nullptr;
+        b->graph_broken = 1;
+      } else {
+        b->key = k;
+        b->gnext.assign(n, -1);
+      }
+    }
+    if (b->gexec) {
+      for (int i = 0; i < n; ++i)
+        if (hps[i].step_index != b->gnext[i]) {
+          nqs_ctx *c = b->ctx[i];
+          k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
+          c->launches += 1;
+          CU(cudaGetLastError());
+        }
+      CU(cudaGraphLaunch(b->gexec, st));
+      for (int i = 0; i < n; ++i) b->gnext[i] = hps[i].step_index + 1;
+      return NQS_OK;
+    }
+  }
+  b->gnext.assign(n, -1);
+  return batch_issue(b, th, mo, hps, stats, true, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+nqs_status nqs_batch_create(int n, nqs_ctx *const *ctxs, nqs_batch **out) {
+  if (!out || n <= 0 || n > 4096 || !ctxs) return NQS_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return NQS_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return NQS_ERR_ARG;  // one workspace per instance
+  }
+  nqs_batch *b = new (std::nothrow) nqs_batch();
+  if (!b) return NQS_ERR_ARG;
+  b->ctx.assign(ctxs, ctxs + n);
+  b->st.assign(n, nullptr);
+  b->done.assign(n, nullptr);
+  b->solved.assign(n, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; ok && i < n; ++i)
+    ok = cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->solved[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) { batch_free(b); return NQS_ERR_CUDA; }
+  *out = b;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_destroy(nqs_batch *b) {
+  if (!b) return NQS_ERR_ARG;
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_set_graph(nqs_batch *b, int enable) {
+  if (!b) return NQS_ERR_ARG;
+  b->graph_enabled = enable != 0;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_graph_active(const nqs_batch *b, int *active) {
+  if (!b || !active) return NQS_ERR_ARG;
+  *active = b->gexec != nullptr && !b->graph_broken;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_set_concurrency(nqs_batch *b, int streams) {
+  if (!b || streams < 0) return NQS_ERR_ARG;
+  b->conc = streams;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams) {
+  if (!b || !streams) return NQS_ERR_ARG;
+  *streams = batch_conc(b);
+  return NQS_OK;
+}
+
+nqs_status nqs_minsr_step_batched(nqs_batch *b, double *const *thetas, double *const *moms,
+                                  const nqs_step_hparams *hps, nqs_step_stats *dev_stats,
+                                  void *stream) {
+  if (!b || !thetas || !moms || !hps || !dev_stats) return NQS_ERR_ARG;
+  ST(batch_check(b, thetas, moms, hps));
+  std::vector<nqs_step_stats *> sp(b->ctx.size());
+  for (size_t i = 0; i < sp.size(); ++i) sp[i] = dev_stats + i;
+  return batch_step(b, thetas, moms, hps, sp.data(), static_cast<cudaStream_t>(stream));
+}
+
+nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_step_hparams *hps,
+                              int flags, double *step_ms, void *stream) {
+  if (!b || !thetas || !hps) return NQS_ERR_ARG;
+  const int n = (int)b->ctx.size();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // (1) every instance alone
+  for (int i = 0; i < n; ++i) ST(nqs_autotune(b->ctx[i], thetas[i], &hps[i], flags, stream));
+  // (2) instance streams: whole batched steps on scratch copies of theta
+  std::vector<double *> th(n), mo(n);
+  std::vector<nqs_step_stats *> sp(n);
+  for (int i = 0; i < n; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    th[i] = W<double>(c, c->off.tth);
+    mo[i] = W<double>(c, c->off.tmo);
+    sp[i] = W<nqs_step_stats>(c, c->off.tstats);
+  }
+  std::vector<int> cand;
+  for (int q : {1, 2, 4, 8, 16}) if (q < n) uniq_push(cand, q);
+  uniq_push(cand, n);
+  const int saved_graph = b->graph_enabled;
+  b->graph_enabled = 0;
+  double best = 1e300;
+  int pick = n;
+  nqs_status s = NQS_OK;
+  for (int q : cand) {
+    b->conc = q;
+    double ms = 0;
+    s = best_ms(st, 2, [&] {
+      for (int i = 0; i < n; ++i) {
+        const int64_t np = b->ctx[i]->L.np;
+        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
+      }
+      return NQS_OK;
+    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
+    if (s != NQS_OK) break;
+    if (ms < best) { best = ms; pick = q; }
+  }
+  b->graph_enabled = saved_graph;
+  b->conc = pick;
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  if (step_ms) *step_ms = best;
+  return s;
+}
+
+nqs_status nqs_eloc_work(const nqs_ctx *c, int64_t *configs, int64_t *sites) {
+  if (!c || !configs || !sites) return NQS_ERR_ARG;
+  if (!c->ws) return NQS_ERR_WORKSPACE;
+  std::vector<int> cnt(std::max(c->n_off, 1));
+  if (c->n_off > 0 &&
+      cudaMemcpy(cnt.data(), c->ws + c->off.item_cnt, sizeof(int) * c->n_off,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NQS_ERR_CUDA;
+  int64_t nc = 0, ns = 0;
+  for (int i = 0; i < c->n_off; ++i) {
+    nc += cnt[i];
+    ns += (int64_t)cnt[i] * (c->L.N - c->op_start[i]);
+  }
+  *configs = nc;
+  *sites = ns;
+  return NQS_OK;
 }
 
 const char *nqs_stage_name(int i) {

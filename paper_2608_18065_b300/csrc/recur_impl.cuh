@@ -17,15 +17,19 @@ namespace nqs {
     default: return cudaErrorInvalidValue;                \
   }
 
+// Shared memory above this leaves the large weight blocks in global memory.
+constexpr size_t SMEM_STAGE_LIMIT = 200 * 1024;
+
 template <typename T, int DH, int DIM, int RT, int RG, int MODE>
 static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStream_t st) {
   constexpr int R = RT * RG;
-  auto kern = k_forward<T, DH, DIM, RT, RG, MODE>;
+  auto kern = k_forward<T, DH, DIM, RT, RG, MODE, true>;
   size_t smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, true);
-  a.wsmem = 1;
-  if (smem > 200 * 1024) {
-    smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, false);
-    a.wsmem = 0;
+  if constexpr (DH >= 96) {
+    if (smem > SMEM_STAGE_LIMIT) {
+      smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+      kern = k_forward<T, DH, DIM, RT, RG, MODE, false>;
+    }
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -60,9 +64,14 @@ template <typename T, int DH, int DIM>
 static int eloc_grid_dim(const RecDesc &d) {
   constexpr int RT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
   constexpr int RG = Rows<T>::ELOC_RG;
-  auto kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC>;
+  auto kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC, true>;
   size_t smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, true);
-  if (smem > 200 * 1024) smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, false);
+  if constexpr (DH >= 96) {
+    if (smem > SMEM_STAGE_LIMIT) {
+      smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, false);
+      kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC, false>;
+    }
+  }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int per = 0;
@@ -86,12 +95,13 @@ template <typename T> int eloc_max_grid(const RecDesc &d) {
 template <typename T, int DH, int DIM>
 static cudaError_t bwd_dim(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
   constexpr int RT = Rows<T>::BWD_RT, RG = Rows<T>::BWD_RG, R = RT * RG;
-  auto kern = k_jac_bwd<T, DH, DIM, RT, RG>;
+  auto kern = k_jac_bwd<T, DH, DIM, RT, RG, true>;
   size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, true);
-  a.wsmem = 1;
-  if (smem > 200 * 1024) {
-    smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
-    a.wsmem = 0;
+  if constexpr (DH >= 96) {
+    if (smem > SMEM_STAGE_LIMIT) {
+      smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+      kern = k_jac_bwd<T, DH, DIM, RT, RG, false>;
+    }
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -71,7 +71,6 @@ template <typename T> struct FwdArgs {
   T *lccache;              // [rows][N][2]
   T *gcache;               // optional [rows][N][gw]: u | r | c | W_h h'+b_h (| h' in 2D)
   int gw;
-  int wsmem;               // 1: large weight blocks staged in shared memory
   // ELOC
   int tiles_per_op;
   const int *op_f;         // [n_off*4]: f1, f2, start, pad
@@ -95,7 +94,9 @@ inline size_t fwd_smem_bytes(int N, bool wsmem = true) {
   return (b + 127) & ~size_t(127);
 }
 
-template <typename T, int DH, int DIM, int RT, int RG, int MODE>
+// WS: the two large weight blocks are staged in shared memory (otherwise they
+// are read through L1 from the packed copy in global memory).
+template <typename T, int DH, int DIM, int RT, int RG, int MODE, bool WS = true>
 __global__ void __launch_bounds__(Tile<DH>::UG * RG)
 k_forward(const FwdArgs<T> A) {
   constexpr int UG = Tile<DH>::UG, UT = Tile<DH>::UT;
@@ -108,10 +109,10 @@ k_forward(const FwdArgs<T> A) {
   T *sbias = sxw + DIN * C3;
   T *shead = sbias + DH * 4;
   T *shc = shead + 4 * DH;
-  T *sw = shc + 8;                         // staged W^T and [U1|U2]^T (wsmem)
+  T *sw = shc + 8;                         // staged W^T and [U1|U2]^T (WS)
   const T *sWgT = sw;
   const T *sU12T = sw + DH * C3;
-  T *sh0 = sw + (A.wsmem ? DH * C3 + (DIM == 2 ? 2 * DH * DH : 0) : 0);
+  T *sh0 = sw + (WS ? DH * C3 + (DIM == 2 ? 2 * DH * DH : 0) : 0);
   T *sh1 = sh0 + DH * R;
   T *shv = sh1 + DH * R;                    // 2D: vertical neighbour states
   T *shp = shv + (DIM == 2 ? DH * R : 0);   // 2D: h'
@@ -136,7 +137,7 @@ k_forward(const FwdArgs<T> A) {
     for (int e = tid; e < DH * 4; e += NTH) sbias[e] = p[obias + e];
     for (int e = tid; e < 4 * DH; e += NTH) shead[e] = p[ohead + e];
     if (tid < 4) shc[tid] = p[ohc + tid];
-    if (A.wsmem) {
+    if constexpr (WS) {
       for (int e = tid; e < DH * C3; e += NTH) sw[e] = p[oWgT + e];
       if (DIM == 2)
         for (int e = tid; e < 2 * DH * DH; e += NTH) sw[DH * C3 + e] = p[oU12T + e];

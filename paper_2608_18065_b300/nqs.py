@@ -56,7 +56,17 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_set_workspace", "nqs_sample", "nqs_logpsi", "nqs_local_energy",
            "nqs_jacobian", "nqs_logpsi_vjp", "nqs_gram", "nqs_regularized_solve", "nqs_minsr_step",
            "nqs_minsr_step_ex", "nqs_set_graph", "nqs_graph_active", "nqs_timing_begin", "nqs_timing_end", "nqs_launch_count",
+           "nqs_autotune", "nqs_get_tuning", "nqs_clear_tuning", "nqs_batch_create",
+           "nqs_batch_destroy", "nqs_minsr_step_batched", "nqs_batch_set_graph",
+           "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
+           "nqs_batch_autotune", "nqs_eloc_work",
            "nqs_stage_name", "nqs_status_string"]
+TUNE_FORCE = 1
+
+
+class Tuning(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("eloc_grid", C.c_int), ("gram_splits", C.c_int),
+                ("solve_grid", C.c_int), ("ms", C.c_double * 3), ("ms_default", C.c_double * 3)]
 
 
 def lib():
@@ -234,10 +244,37 @@ class Context:
         _check(lib().nqs_timing_end(self._h, ms, C.byref(n)))
         return {lib().nqs_stage_name(i).decode(): ms[i] for i in range(N_STAGES)}, n.value
 
+    def eloc_work(self):
+        """(connected configurations, recomputed sites) of the last E_loc pass."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().nqs_eloc_work(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def launch_count(self):
         n = C.c_int64()
         _check(lib().nqs_launch_count(self._h, C.byref(n)))
         return n.value
+
+    # ------------------------------------------------------------ autotuner
+    def autotune(self, theta, hp: HParams, step_index=0, force=False, stream=None):
+        """Measure and keep the launch shapes for hp.ns samples (synchronous;
+        theta is not modified)."""
+        hps = step_hparams(hp, step_index)
+        _check(lib().nqs_autotune(self._h, _ptr(theta), C.byref(hps),
+                                  TUNE_FORCE if force else 0, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().nqs_get_tuning(self._h, C.byref(t)))
+        names = ("eloc", "gram", "solve")
+        return {"n_samples": t.n_samples, "eloc_grid": t.eloc_grid,
+                "gram_splits": t.gram_splits, "solve_grid": t.solve_grid,
+                "ms": dict(zip(names, list(t.ms))),
+                "ms_default": dict(zip(names, list(t.ms_default)))}
+
+    def clear_tuning(self):
+        _check(lib().nqs_clear_tuning(self._h))
 
     def step_outputs(self, ns):
         R = ns * self.rows_per_sample
@@ -249,6 +286,77 @@ class Context:
                     eps=torch.empty(R, dtype=torch.float64, device=d),
                     x=torch.empty(R, dtype=torch.float64, device=d),
                     dtheta=torch.empty(self.np, dtype=torch.float64, device=d))
+
+
+class Batch:
+    """n independent contexts stepped together (nqs_minsr_step_batched)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        n = len(self.contexts)
+        arr = (C.c_void_p * n)(*[c._h for c in self.contexts])
+        h = C.c_void_p()
+        _check(lib().nqs_batch_create(n, arr, C.byref(h)))
+        self._h = h
+        self.device = self.contexts[0].device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nqs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_stats(self):
+        return torch.zeros((len(self.contexts), STATS_DOUBLES), dtype=torch.float64,
+                           device=self.device)
+
+    def _arrays(self, thetas, hps, step_index):
+        n = len(self.contexts)
+        if len(thetas) != n or len(hps) != n:
+            raise ValueError("one theta and one HParams per instance")
+        steps = step_index if isinstance(step_index, (list, tuple)) else [step_index] * n
+        th = (C.c_void_p * n)(*[t.data_ptr() for t in thetas])
+        hp = (StepHParams * n)(*[step_hparams(h, int(s)) for h, s in zip(hps, steps)])
+        return th, hp
+
+    def step(self, thetas, moms, hps, step_index, stats=None, stream=None):
+        """One step of every instance; stats: device [n, 9] doubles."""
+        if stats is None:
+            stats = self.new_stats()
+        th, hp = self._arrays(thetas, hps, step_index)
+        mo = (C.c_void_p * len(moms))(*[m.data_ptr() for m in moms])
+        _check(lib().nqs_minsr_step_batched(self._h, th, mo, hp, _ptr(stats), _stream(stream)))
+        return stats
+
+    def autotune(self, thetas, hps, step_index=0, force=False, stream=None):
+        """Tune every instance, then the concurrency; returns the best batched
+        step time in ms (thetas are not modified)."""
+        th, hp = self._arrays(thetas, hps, step_index)
+        ms = C.c_double()
+        _check(lib().nqs_batch_autotune(self._h, th, hp, TUNE_FORCE if force else 0,
+                                        C.byref(ms), _stream(stream)))
+        return ms.value
+
+    def use_graph(self, enable=True):
+        _check(lib().nqs_batch_set_graph(self._h, 1 if enable else 0))
+
+    def graph_active(self):
+        v = C.c_int()
+        _check(lib().nqs_batch_graph_active(self._h, C.byref(v)))
+        return bool(v.value)
+
+    def set_concurrency(self, streams):
+        _check(lib().nqs_batch_set_concurrency(self._h, int(streams)))
+
+    def concurrency(self):
+        v = C.c_int()
+        _check(lib().nqs_batch_get_concurrency(self._h, C.byref(v)))
+        return v.value
 
 
 def decode_stats(stats: torch.Tensor) -> dict:
