@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "minSR steps/s & Gram TFLOP/s vs plain FP64 GPU path at matched energy error"
 UNIT = "steps/s"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 x max SM clock
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12    # SMs x FP64 lane-FMAs x 2 x max SM clock
 
 
 def parse():
@@ -161,7 +162,7 @@ def eloc_tc_used(model, precision):
     return precision == "mixed" and model.dim == 1 and model.dh == 64
 
 
-def eloc_roofline(w, ms):
+def eloc_roofline(w, ms, sites=None):
     """Roofline of the connected-configuration engine for one launch.
 
     Tensor-core engine: per recomputed site of one connected configuration
@@ -169,7 +170,8 @@ def eloc_roofline(w, ms):
     (hi.hi + hi.lo + lo.hi), 3 * 2 * dh * 3dh tensor-pipe flops; bound by
     the measured sustained BF16 rate.  SIMT engine: FP32 FMA-pipe flops of
     the recurrence against the derived FP32 peak."""
-    sites = eloc_suffix_sites(w)
+    if sites is None:
+        sites = eloc_suffix_sites(w)
     if sites is None:
         return None
     dh = w.model.dh
@@ -194,6 +196,67 @@ def eloc_roofline(w, ms):
             "traffic": load_traffic("k_forward_eloc", sha, w.name),
             "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
             "flops_per_launch": alg, "ms_per_launch": ms}
+
+
+def stage_rooflines(w, ms, sites, R, np_):
+    """Per-stage rooflines of one step (ms: stage -> ms per step).
+
+    eloc_suffix: see eloc_roofline (sites = recomputed sites counted by the
+    library).  sample, jac_bwd, jac_grad: FP32 (FP64) FMA-pipe work of the
+    recurrence, N_s N (sample) or R N (reverse sweep, O assembly) sites of
+    site_flops each.  cholesky: n^3/3 factor + n^3/3 triangular inverse
+    (n = R) in FP32 for the mixed path (refinement sweeps: 2n^2 each, not
+    counted).  gram: BF16x3 tensor work 3 R(R+1) Np.  center: HBM bytes of
+    the column sums and the split (read O twice, write hi and lo)."""
+    out = {}
+    f32 = w.precision == "mixed"
+    alu_peak = FP32_ALU_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    alu_src = ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)" if f32 else
+               "148 SMs x 2 FP64 lane-FMAs x 2 flop x 2032 MHz (derived; 0.94 measured)")
+    sf = site_flops(w.model)
+    N = w.model.N
+
+    def alu(name, kernel, flops):
+        t = ms.get(name, 0.0)
+        if t <= 0:
+            return
+        a = flops / (t * 1e-3) / 1e12
+        out[name] = {"kernel": kernel, "bound": "alu", "achieved": a, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": a / alu_peak, "traffic": None,
+                     "peak_source": alu_src, "flops_per_launch": flops, "ms_per_launch": t}
+
+    if ms.get("eloc_suffix", 0) > 0 and sites:
+        if eloc_tc_used(w.model, w.precision):
+            out["eloc_suffix"] = eloc_roofline(w, ms["eloc_suffix"], sites)
+        else:
+            alu("eloc_suffix", "k_forward<MODE_ELOC>", sites * sf)
+    alu("sample", "k_forward<MODE_SAMPLE>", w.hp.ns * N * sf)
+    alu("jac_bwd", "k_jac_bwd", R * N * sf)
+    alu("jac_grad", "k_jac_grad", R * N * sf)
+    alu("cholesky", "k_chol_ir" if f32 else "k_chol_coop", 2 * R ** 3 / 3)
+    if ms.get("gram", 0) > 0:
+        t = ms["gram"]
+        if f32:
+            pk, src = measured_peak("bf16_tflops_sustained", 1400.0)
+            a = 3 * R * (R + 1) * np_ / (t * 1e-3) / 1e12
+            out["gram"] = {"kernel": "k_gram_bf16x3 + k_gram_reduce", "bound": "tensor",
+                           "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                           "traffic": None, "peak_source": src + ", BF16 dense, sustained",
+                           "ms_per_launch": t}
+        else:
+            alu("gram", "k_gram_simt<double>", R * (R + 1) * np_)
+    if ms.get("center", 0) > 0:
+        t = ms["center"]
+        kpad = (np_ + 63) // 64 * 64
+        byts = R * np_ * (4 if f32 else 8) * 2 + (R * kpad * 4 if f32 else R * np_ * 8)
+        pk, src = measured_peak("hbm_gbs", 6400.0)
+        a = byts / (t * 1e-3) / 1e9
+        out["center"] = {"kernel": "k_colsum_part + k_colmean_fin + " +
+                         ("k_center_split" if f32 else "k_center"), "bound": "hbm",
+                         "achieved": a, "peak": pk, "unit": "GB/s", "frac": a / pk,
+                         "traffic": None, "peak_source": src, "bytes_per_launch": byts,
+                         "ms_per_launch": t}
+    return out
 
 
 # ------------------------------------------------------------------ oracle
@@ -375,15 +438,14 @@ def run_ours(args):
                 "frac_of_bf16": 3 * gram_tflops / pk if tc else None,
                 "peak_source": src if tc else None}
 
-    # dominant kernel and its roofline
+    # roofline of every large stage; the dominant one is the headline
+    cfg, sites = ctx.eloc_work()
+    kernels = stage_rooflines(w, {k: v / max(nt, 1) for k, v in stage_ms.items()}, sites, R,
+                              ctx.np)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
-    dom_ms = stage_ms[dom] / max(nt, 1)
-    roof = None
-    if dom == "eloc_suffix":
-        roof = eloc_roofline(w, dom_ms)
-    if roof is None:
-        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None, "ms_per_launch": dom_ms}
+    roof = kernels.get(dom) or {"kernel": dom, "bound": None, "achieved": None, "peak": None,
+                                "unit": None, "frac": None, "traffic": None,
+                                "ms_per_launch": stage_ms[dom] / max(nt, 1)}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -460,7 +522,8 @@ def run_ours(args):
                 "config": dict(w.describe(), l2="step working set > 126 MB L2 (O, caches, adjoints)",
                                replicas=world, workspace_mb=ctx.workspace_bytes / 2**20),
                 "gram_tflops": gram_tflops, "gram": gram,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "clocks": clk, "cuda_graph": graph_used, "fp64_path": fp64,
                 "matched_energy": matched,
                 "stage_ms": {k: v / max(nt, 1) for k, v in stage_ms.items()},

@@ -135,6 +135,28 @@ typedef struct nqs_ctx nqs_ctx;
 nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham,
                       int precision, int64_t max_samples, nqs_ctx **out);
 
+/* Options of nqs_create_ex. */
+typedef struct {
+  /* Hidden-state checkpoints for the per-sample Jacobian (1D chains only):
+   * 0 caches every h_k (the default of nqs_create); c > 0 keeps h_k only for
+   * k = c-1, 2c-1, ... and the reverse sweep recomputes each segment of c
+   * sites from its checkpoint (and the local energies restart from the
+   * last checkpoint before their first changed site); -1 takes
+   * c = ceil(sqrt(N)).  Memory of the hidden-state, gate and adjoint caches
+   * drops from O(Ns N dh) to O(Ns (N/c + c) dh) for about one extra forward
+   * pass.  NQS_ERR_UNSUPPORTED for 2D lattices (the zig-zag vertical
+   * neighbour reaches a full row back). */
+  int checkpoint_stride;
+} nqs_options;
+
+/* nqs_create with options (opt may be NULL: all defaults). */
+nqs_status nqs_create_ex(const nqs_model_desc *model, const nqs_ham_desc *ham,
+                         int precision, int64_t max_samples,
+                         const nqs_options *opt, nqs_ctx **out);
+
+/* The checkpoint stride in use (0: every state cached). */
+nqs_status nqs_checkpoint_stride(const nqs_ctx *ctx, int *stride);
+
 /* Release the context (host memory and its device tables).  Synchronises
  * the device first. */
 nqs_status nqs_destroy(nqs_ctx *ctx);
@@ -229,6 +251,7 @@ typedef struct {
   int eloc_grid;      /* CTAs of the connected-configuration engine */
   int gram_splits;    /* K-slices per 128x128 tile of the tensor-core Gram */
   int solve_grid;     /* CTAs of the cooperative Cholesky / refinement */
+  int solve_tiles_per_warp; /* refinement tiles: 1 per warp, 0 per CTA, -1 built-in */
   double ms[3];         /* time of the chosen shape: eloc, gram, solve */
   double ms_default[3]; /* time of the built-in shape */
 } nqs_tuning;

@@ -37,19 +37,70 @@ struct CholIrArgs {
   float *dpart;      // [chunks][n] scratch: partial sums of L^{-T} w
   double *r;         // [n] scratch: FP64 residual
   double *part;      // [gridDim][4] scratch: partial norms
-  unsigned *bar;     // [2] barrier words (zeroed before launch)
+  unsigned *bar;     // barrier arrival counter (zeroed before launch)
   int32_t *status;   // NQS_ERR_TIMEOUT on a barrier timeout
   int32_t *need_fp64;// out: 1 when the FP64 factorisation must run
   int maxit;
 };
 
+// Per-warp 32x32 tile product in shared memory (row stride WS floats, a
+// multiple of 4 so rows are 16-byte aligned): lane j owns column j of the
+// tile, acc[i] += sum_k sA[i][k] * B(k, j) with B(k, j) = sB[j][k] (nt) or
+// sB[k][j] (nn).  Row reads of sA are warp-wide broadcasts of 16 bytes.
+constexpr int WS = IR_B + 4;
+template <bool NT>
+__device__ __forceinline__ void warp_tile_fma(const float *sA, const float *sB, int lane,
+                                              float (&acc)[IR_B]) {
+#pragma unroll 2
+  for (int k = 0; k < IR_B; k += 4) {
+    float b0, b1, b2, b3;
+    if (NT) {
+      const float4 bv = *reinterpret_cast<const float4 *>(sB + lane * WS + k);
+      b0 = bv.x; b1 = bv.y; b2 = bv.z; b3 = bv.w;
+    } else {
+      b0 = sB[(k + 0) * WS + lane]; b1 = sB[(k + 1) * WS + lane];
+      b2 = sB[(k + 2) * WS + lane]; b3 = sB[(k + 3) * WS + lane];
+    }
+#pragma unroll
+    for (int i = 0; i < IR_B; ++i) {
+      const float4 av = *reinterpret_cast<const float4 *>(sA + i * WS + k);
+      acc[i] = fmaf(av.x, b0, acc[i]);
+      acc[i] = fmaf(av.y, b1, acc[i]);
+      acc[i] = fmaf(av.z, b2, acc[i]);
+      acc[i] = fmaf(av.w, b3, acc[i]);
+    }
+  }
+}
+
+// Stage rows r0.. r0+31, columns c0.. c0+31 of M (row stride ld, nrow x ncol
+// valid) into a warp's tile; zeros outside, and columns >= cmax.
+__device__ __forceinline__ void warp_stage(float *sT, const float *M, int64_t ld, int64_t r0,
+                                           int64_t c0, int64_t nrow, int64_t ncol, int64_t cmax,
+                                           int lane) {
+  const int64_t c = c0 + lane;
+  const bool cok = c < ncol && c < cmax;
+  float v[IR_B];  // all 32 row loads in flight before the first store
+#pragma unroll
+  for (int r = 0; r < IR_B; ++r) {
+    const int64_t rr = r0 + r;
+    v[r] = (cok && rr < nrow) ? M[rr * ld + c] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < IR_B; ++r) sT[r * WS + lane] = v[r];
+}
+
+// WT: 32x32 tiles of the trailing update and of the inversion products are
+// spread one per warp (more tiles in flight; better at large n), else one
+// per CTA with four outputs per thread (shorter per-tile latency; better at
+// small n).  The launch picks the variant (or the autotuner does).
+template <bool WT>
 __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   extern __shared__ float ir_smem[];
   float (*D)[IR_B + 1] = reinterpret_cast<float (*)[IR_B + 1]>(ir_smem);  // [32][33]
   float *rinv = ir_smem + IR_B * (IR_B + 1);          // [32]
-  constexpr int TS = IR_B + 1;
-  float *ta = rinv + IR_B;                             // [32][33] tile rows i
-  float *tb = ta + IR_B * TS;                          // [32][33] tile rows j
+  float *wtile = rinv + IR_B;                          // [8 warps][2][32][WS]
+  constexpr int TS = IR_B + 1;                         // CTA tiles: [32][33] each
+  float *ta = wtile, *tb = wtile + IR_B * TS;
   __shared__ int flag_s;
   __shared__ double red_s[IR_THREADS / 32][3];
 
@@ -122,33 +173,62 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     if (tr > 0) {
       const int nt = (int)((tr + IR_B - 1) / IR_B);
       const int ntiles = nt * (nt + 1) / 2;
-      for (int t = g; t < ntiles; t += G) {
+      if constexpr (!WT) {
+        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA
+        for (int t = g; t < ntiles; t += G) {
+          int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+          while (ti * (ti + 1) / 2 > t) --ti;
+          const int tj = t - ti * (ti + 1) / 2;
+          const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+          __syncthreads();
+          for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+            const int rr = e / IR_B, k = e % IR_B;
+            ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
+            tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+          }
+          __syncthreads();
+          // 4 outputs per thread: rows ty + 8q, column tx
+          const int tx = tid % 32, ty = tid / 32;
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+          for (int k = 0; k < IR_B; ++k) {
+            const float bv = tb[tx * TS + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+            if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+          }
+        }
+      } else {
+      // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile of the lower
+      // triangle per warp over the whole grid
+      float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
+      const int64_t gwarp = (int64_t)g * (IR_THREADS / 32) + warp;
+      for (int64_t t = gwarp; t < ntiles; t += (int64_t)G * (IR_THREADS / 32)) {
         int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
         while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
         while (ti * (ti + 1) / 2 > t) --ti;
-        const int tj = t - ti * (ti + 1) / 2;
+        const int tj = (int)(t - ti * (ti + 1) / 2);
         const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
-        __syncthreads();
-        for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-          const int rr = e / IR_B, k = e % IR_B;
-          ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
-          tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
-        }
-        __syncthreads();
-        // 4 outputs per thread: rows ty + 8q, column tx
-        const int tx = tid % 32, ty = tid / 32;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-        for (int k = 0; k < IR_B; ++k) {
-          const float bv = tb[tx * TS + k];
+        __syncwarp();
+        warp_stage(sA, L, n, i0, c0, n, n, c0 + m, lane);
+        warp_stage(sB, L, n, j0, c0, n, n, c0 + m, lane);
+        __syncwarp();
+        float acc[IR_B];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
-        }
+        for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
+        warp_tile_fma<true>(sA, sB, lane, acc);
+        const int64_t j = j0 + lane;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
-          if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+        for (int i = 0; i < IR_B; ++i) {
+          const int64_t ii = i0 + i;
+          if (ii < n && j < n && j <= ii) L[ii * n + j] -= acc[i];
         }
+      }
       }
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
@@ -192,47 +272,83 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       const int64_t pairs = (n + 2 * sz - 1) / (2 * sz);
       const int64_t tps = (sz + IR_B - 1) / IR_B;  // tiles per side of a pair block
       const int64_t ntile = pairs * tps * tps;
-      for (int64_t t = g; t < ntile; t += G) {
+      if constexpr (!WT) {
+        for (int64_t t = g; t < ntile; t += G) {
+          const int64_t pr = t / (tps * tps), tt = t % (tps * tps);
+          const int64_t ti = tt / tps, tj = tt % tps;
+          const int64_t base = pr * 2 * sz;
+          const int64_t i0 = base + sz + ti * IR_B;   // rows of the lower-left block
+          const int64_t j0 = base + tj * IR_B;        // columns
+          if (i0 >= n) continue;                      // uniform over the CTA
+          const float *Aop; const float *Bop;
+          int64_t acol0, brow0;
+          if (phase == 0) { Aop = L; acol0 = base; Bop = Li; brow0 = base; }
+          else { Aop = Li; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz; }
+          const int tx = tid % 32, ty = tid / 32;
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int64_t k0 = 0; k0 < sz; k0 += IR_B) {
+            __syncthreads();
+            for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+              const int rr = e / IR_B, kk = e % IR_B;
+              const int64_t ar = i0 + rr, ac = acol0 + k0 + kk;
+              ta[rr * TS + kk] = (ar < n && ac < n) ? Aop[ar * n + ac] : 0.f;
+              const int64_t br = brow0 + k0 + rr, bc = j0 + kk;
+              tb[rr * TS + kk] = (br < n && bc < n) ? Bop[br * n + bc] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < IR_B; ++kk) {
+              const float bv = tb[kk * TS + tx];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + kk], bv, acc[q]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+            if (i < n && j < n && j < base + sz) {
+              if (phase == 0) a.Tm[i * n + j] = acc[q];
+              else Li[i * n + j] = -acc[q];
+            }
+          }
+        }
+      } else {
+      float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
+      const int64_t gwarp = (int64_t)g * (IR_THREADS / 32) + warp;
+      for (int64_t t = gwarp; t < ntile; t += (int64_t)G * (IR_THREADS / 32)) {
         const int64_t pr = t / (tps * tps), tt = t % (tps * tps);
         const int64_t ti = tt / tps, tj = tt % tps;
         const int64_t base = pr * 2 * sz;
         const int64_t i0 = base + sz + ti * IR_B;   // rows of the lower-left block
         const int64_t j0 = base + tj * IR_B;        // columns
-        if (i0 >= n) continue;                      // uniform over the CTA
+        if (i0 >= n) continue;                      // uniform over the warp
         const float *Aop; const float *Bop;
-        int64_t arow0, acol0, brow0, kmax;
+        int64_t acol0, brow0;
         if (phase == 0) {  // Tm = L21 * Li11: A = L rows i, cols base..; B = Li11
-          Aop = L; arow0 = i0; acol0 = base; Bop = Li; brow0 = base; kmax = sz;
+          Aop = L; acol0 = base; Bop = Li; brow0 = base;
         } else {           // Li21 = -Li22 * Tm: A = Li22 rows i, cols base+sz..; B = Tm
-          Aop = Li; arow0 = i0; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz; kmax = sz;
+          Aop = Li; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz;
         }
-        const int tx = tid % 32, ty = tid / 32;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t k0 = 0; k0 < kmax; k0 += IR_B) {
-          __syncthreads();
-          for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-            const int rr = e / IR_B, kk = e % IR_B;
-            const int64_t ar = arow0 + rr, ac = acol0 + k0 + kk;
-            ta[rr * TS + kk] = (ar < n && ac < n) ? Aop[ar * n + ac] : 0.f;
-            const int64_t br = brow0 + k0 + rr, bc = j0 + kk;
-            tb[rr * TS + kk] = (br < n && bc < n) ? Bop[br * n + bc] : 0.f;
-          }
-          __syncthreads();
-#pragma unroll 8
-          for (int kk = 0; kk < IR_B; ++kk) {
-            const float bv = tb[kk * TS + tx];
+        float acc[IR_B];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + kk], bv, acc[q]);
-          }
+        for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
+        for (int64_t k0 = 0; k0 < sz; k0 += IR_B) {
+          __syncwarp();
+          warp_stage(sA, Aop, n, i0, acol0 + k0, n, n, n, lane);
+          warp_stage(sB, Bop, n, brow0 + k0, j0, n, n, n, lane);
+          __syncwarp();
+          warp_tile_fma<false>(sA, sB, lane, acc);
         }
+        const int64_t j = j0 + lane;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
-          if (i < n && j < n && j < base + sz) {
-            if (phase == 0) a.Tm[i * n + j] = acc[q];
-            else Li[i * n + j] = -acc[q];
+        for (int i = 0; i < IR_B; ++i) {
+          const int64_t ii = i0 + i;
+          if (ii < n && j < n && j < base + sz) {
+            if (phase == 0) a.Tm[ii * n + j] = acc[i];
+            else Li[ii * n + j] = -acc[i];
           }
         }
+      }
       }
       if (!cc_grid_sync(a.bar, a.status)) return;
     }
@@ -325,7 +441,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
 }
 
 inline size_t chol_ir_smem(int64_t) {
-  return sizeof(float) * ((size_t)IR_B * (IR_B + 1) + IR_B + 2 * (size_t)IR_B * (IR_B + 1));
+  return sizeof(float) * ((size_t)IR_B * (IR_B + 1) + IR_B + (IR_THREADS / 32) * 2 * (size_t)IR_B * WS);
 }
 
 }  // namespace nqs

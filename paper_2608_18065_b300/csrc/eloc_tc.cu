@@ -215,17 +215,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], j0 = a.op_f[4 * op + 2];
       const bool valid = base + row < cnt;
       const int64_t item = (int64_t)op * a.ns + base + row;
-      const int s = valid ? a.item_s[item] : 0;
+      const int s = valid ? __ldcg(a.item_s + item) : 0;
       const uint8_t *sp = a.spins + (int64_t)s * N;
       const float *lcrow = a.lccache + (int64_t)s * N * 2;
-      auto spin_at = [&](int k) { return (int)sp[k] ^ ((k == f1 || k == f2) ? 1 : 0); };
+      // streamed operands bypass L1 (ld.global.cg), which keeps the small L1
+      // left beside the 202 KB of shared memory for register spills
+      auto spin_at = [&](int k) { return (int)__ldcg(sp + k) ^ ((k == f1 || k == f2) ? 1 : 0); };
+      // first recomputed site: j0, or with checkpoints the site after the
+      // last checkpoint before it (its sites up to j0 - 1 add nothing)
+      const int kr = a.ck > 0 ? (j0 / a.ck) * a.ck : j0;
       float h[UH];
-      if (valid && j0 > 0) {
-        const float4 *src =
-            reinterpret_cast<const float4 *>(a.hcache + ((int64_t)s * N + j0 - 1) * DH + UH * half);
+      if (valid && kr > 0) {
+        const int64_t slot = a.ck > 0 ? (int64_t)s * a.nck + (kr / a.ck - 1) : (int64_t)s * N + kr - 1;
+        const float4 *src = reinterpret_cast<const float4 *>(a.hcache + slot * DH + UH * half);
 #pragma unroll
         for (int c = 0; c < UH / 4; ++c) {
-          const float4 v = src[c];
+          const float4 v = __ldcg(src + c);
           h[4 * c] = v.x; h[4 * c + 1] = v.y; h[4 * c + 2] = v.z; h[4 * c + 3] = v.w;
         }
       } else {
@@ -234,9 +239,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       }
       int n_up = 0, n_dn = 0;
       if (a.zmask && half == 0)
-        for (int k = 0; k < j0; ++k) { if (sp[k] == 0) ++n_up; else ++n_dn; }
-      // round 0: planes of h_{j-1} and the input of site j
-      int sprev = j0 > 0 ? spin_at(j0 - 1) : 2;
+        for (int k = 0; k < kr; ++k) { if (__ldcg(sp + k) == 0) ++n_up; else ++n_dn; }
+      // round 0: planes of h_{kr-1} and the input of site kr
+      int sprev = kr > 0 ? spin_at(kr - 1) : 2;
       write_planes(Ahi, Alo, row, half, h);
       if (half == 0) write_aug(Aaug, row, sprev);
       fence_async_smem();
@@ -244,13 +249,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       if (bar_any(1 + t, 2 * TR, !ok)) { ok = false; break; }
       if (issuer) issue_round(dacc, a0, b0, accbar);
       double dre = 0.0, dimg = 0.0;
-      const int L = N - j0;
+      const int L = N - kr;
       for (int r = 0; r <= L; ++r) {
-        const int k = j0 + r;  // gates of site k (r < L), head of site k - 1 (r > 0)
+        const int k = kr + r;  // gates of site k (r < L), head of site k - 1 (r > 0)
         // loads for after the wait: sigma'_k and sigma's cached terms at k - 1
         const int scur = k < N ? spin_at(k) : 0;
         float2 lc = make_float2(0.f, 0.f);
-        if (half == 0 && r > 0 && valid) lc = *reinterpret_cast<const float2 *>(lcrow + 2 * (k - 1));
+        if (half == 0 && r > 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * (k - 1)));
         if (!mbar_wait(accbar, acc_ph)) ok = false;
         acc_ph ^= 1;
         tc_fence_after();
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
           else lps = (double)(sprev == 0 ? lp0 : lp1);
           double ph = 0.0;
           if (a.cplx) ph = NQS_PI * (double)softsign(sprev == 0 ? hv[2] + shc[2] : hv[3] + shc[3]);
-          if (valid) {
+          if (valid && k - 1 >= j0) {
             dre += 0.5 * lps - (double)lc.x;
             dimg += ph - (double)lc.y;
           }

@@ -10,7 +10,7 @@ struct ElocTcArgs {
   const float *pack;      // packed FP32 weights
   int oWgT, oxw, obias, ohead, ohc;  // their offsets (PackOff)
   const uint8_t *spins;   // [ns][N] samples
-  const float *hcache;    // [ns][N][64]
+  const float *hcache;    // [ns][N][64], or [ns][nck][64] checkpoints
   const float *lccache;   // [ns][N][2]
   int N, cplx, zmask;
   int64_t ns;
@@ -21,6 +21,7 @@ struct ElocTcArgs {
   const int *item_cnt;    // [n_off]
   double *contrib;        // [n_off][ns][2]
   int *err;               // device status word
+  int ck, nck;            // checkpoints: hcache holds h_{m ck - 1} in slot m - 1 (ck > 0)
 };
 
 bool eloc_tc_supported(int dim, int dh);

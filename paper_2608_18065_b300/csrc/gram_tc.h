@@ -12,7 +12,8 @@ bool gram_tc_available();
 int gram_tc_launches();
 // Bytes of scratch: the hi/lo planes [2][R][Kpad] bf16 and the K-slice partials.
 size_t gram_tc_split_bytes(int64_t R, int64_t np);
-// T[R x R] (FP64, both triangles) = A A^T, A row-major [R x np] FP32.  *err
+// T[R x R] (FP64, both triangles) = A A^T, A row-major [R x np] FP32, from
+// the four BF16 products of the split with compensated FP32 chunk sums.  *err
 // (device int) receives NQS_ERR_TIMEOUT if a bounded device wait ran out.
 cudaError_t gram_tc_bf16x3(const float *A, int64_t R, int64_t np, double *T, void *scratch,
                            int *err, cudaStream_t st);
@@ -28,6 +29,11 @@ cudaError_t gram_from_center_split(const void *scratch, int64_t R, int64_t np, d
 // built-in plan's choice.
 int gram_tc_max_splits(int64_t R, int64_t np);
 int gram_tc_default_splits(int64_t R, int64_t np);
+// T in FP64 from the same planes (exact products, FP64 sums), only when
+// *gate (device) is non-zero: the fallback when T + lambda I from the
+// tensor cores is not positive definite at the requested lambda.
+cudaError_t gram_split_f64(const void *scratch, int64_t R, int64_t np, double *T,
+                           const int32_t *gate, cudaStream_t st);
 // ... and partial sums of O'x from the same planes.
 cudaError_t gemv_split(const void *scratch, int64_t R, int64_t np, const double *x, int rows_per,
                        double *part, cudaStream_t st);

@@ -27,6 +27,11 @@ template <typename T> struct BwdArgs {
   T *adj;                   // [nrows][N][adjw]
   int adjw;
   T *adjcol;                // 2D: [nrows][Lx][dh] pending vertical adjoints
+  // sites of this pass, [k_lo, k_hi) (0, N: the whole chain), and where
+  // their inputs live: h_{k-1} at hcache[(s hN + k - 1 - hoff) dh], gates at
+  // gcache[(s gN + k - goff) gw], records at adj[(row aN + k - aoff) adjw]
+  int k_lo, k_hi, hN, hoff, gN, goff, aN, aoff;
+  T *carry;                 // optional [nrows][dh]: adjoint of h_{k_hi-1} in, of h_{k_lo-1} out
 };
 
 // adjoint record of one site: dau | dar | dg | dac (4 dh) | dz0 dz1 dy0 dy1 |
@@ -130,9 +135,12 @@ k_jac_bwd(const BwdArgs<T> A) {
     }
     T carry[RT][UT];
 #pragma unroll
-    for (int i = 0; i < RT; ++i)
+    for (int i = 0; i < RT; ++i) {
+      const int g = srow[r0 + i];
 #pragma unroll
-      for (int uu = 0; uu < UT; ++uu) carry[i][uu] = T(0);
+      for (int uu = 0; uu < UT; ++uu)
+        carry[i][uu] = (A.carry && g >= 0) ? A.carry[(int64_t)g * DH + a0 + uu] : T(0);
+    }
 
     // forward-pass values of site k for this thread's rows and units,
     // loaded one site ahead of their use
@@ -142,22 +150,22 @@ k_jac_bwd(const BwdArgs<T> A) {
       for (int i = 0; i < RT; ++i) {
         const int g = srow[r0 + i];
         const int64_t s = g >= 0 ? g % A.ns : 0;
-        const T *G = A.gcache + (s * N + k) * A.gw;
+        const T *G = A.gcache + (s * A.gN + k - A.goff) * A.gw;
 #pragma unroll
         for (int uu = 0; uu < UT; ++uu) {
           const int a = a0 + uu;
           gu[i][uu] = G[a]; gr[i][uu] = G[DH + a]; gc[i][uu] = G[2 * DH + a];
           gg[i][uu] = G[3 * DH + a];
           if (DIM == 2) ghp[i][uu] = G[4 * DH + a];
-          else ghp[i][uu] = k > 0 ? A.hcache[(s * N + k - 1) * DH + a] : T(0);
+          else ghp[i][uu] = k > 0 ? A.hcache[(s * A.hN + k - 1 - A.hoff) * DH + a] : T(0);
         }
         lc0[i] = A.lccache[(s * N + k) * 2];
         lc1[i] = A.lccache[(s * N + k) * 2 + 1];
       }
     };
-    load_site(N - 1);
+    load_site(A.k_hi - 1);
 
-    for (int k = N - 1; k >= 0; --k) {
+    for (int k = A.k_hi - 1; k >= A.k_lo; --k) {
       int hor_ok = k > 0, ver = -1, col = 0;
       if (DIM == 2) {
         int j = k / Lx, m = k - j * Lx;
@@ -183,7 +191,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           const T om = T(1) - (q < T(0) ? -q : q);
           dy = T(NQS_PI) * om * om;
         }
-        T *rec = A.adj + ((int64_t)(g >= 0 ? g : 0) * N + k) * A.adjw;
+        T *rec = A.adj + ((int64_t)(g >= 0 ? g : 0) * A.aN + k - A.aoff) * A.adjw;
         if (g >= 0 && ug == 0) {
           rec[AJ::DZ + 0] = dz0; rec[AJ::DZ + 1] = dz1;
           rec[AJ::DZ + 2] = sk == 0 ? dy : T(0);
@@ -215,7 +223,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           }
         }
       }
-      if (k > 0) load_site(k - 1);  // in flight during the GEMM below
+      if (k > A.k_lo) load_site(k - 1);  // in flight during the GEMM below
       __syncthreads();
       T dh1[RT][UT];
 #pragma unroll
@@ -236,7 +244,7 @@ k_jac_bwd(const BwdArgs<T> A) {
 #pragma unroll
           for (int uu = 0; uu < UT; ++uu) {
             sdp[(a0 + uu) * R + r] = dh1[i][uu];
-            if (g >= 0) A.adj[((int64_t)g * N + k) * A.adjw + AJ::DHP + a0 + uu] = dh1[i][uu];
+            if (g >= 0) A.adj[((int64_t)g * A.aN + k - A.aoff) * A.adjw + AJ::DHP + a0 + uu] = dh1[i][uu];
           }
         }
         __syncthreads();
@@ -261,6 +269,15 @@ k_jac_bwd(const BwdArgs<T> A) {
       (void)hpv;
       __syncthreads();
     }
+    if (A.carry) {
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        const int g = srow[r0 + i];
+        if (g < 0) continue;
+#pragma unroll
+        for (int uu = 0; uu < UT; ++uu) A.carry[(int64_t)g * DH + a0 + uu] = carry[i][uu];
+      }
+    }
   }
 }
 
@@ -274,6 +291,9 @@ template <typename T, typename TO> struct GradArgs {
   int adjw;
   TO *O;                    // [nrows][np]
   int64_t np;
+  // sites [k_lo, k_hi) of this pass; h_k at hcache[(s hN + k - hoff) dh],
+  // records at adj[(row aN + k - aoff) adjw]; accumulate: O += (else O =)
+  int k_lo, k_hi, hN, hoff, aN, aoff, accumulate;
   // layout offsets
   int64_t U1, U2, Wu, bu, Wr, br, Wh, bh, Win, bin, Uo, co, Up, cp;
 };
@@ -319,10 +339,12 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
 #pragma unroll
   for (int q = 0; q < SPT; ++q) accS[q] = T(0);
 
-  const T *adjrow = A.adj + (int64_t)row * N * A.adjw;
-  const T *hrow = A.hcache + s * N * DH;
+  // record of site k, state h_k (k >= hoff) of this row
+  auto adj_at = [&](int k) { return A.adj + ((int64_t)row * A.aN + (k - A.aoff)) * A.adjw; };
+  auto h_at = [&](int k) { return A.hcache + (s * A.hN + (k - A.hoff)) * DH; };
   const uint8_t *sprow = A.spins + s * N;
   TO *Orow = A.O + (int64_t)row * A.np;
+  auto put = [&](int64_t idx, TO v) { Orow[idx] = A.accumulate ? Orow[idx] + v : v; };
   const int w = DH + DIN;
   // big block qb: 0 Wu_h, 1 Wr_h, 2 Wh (adjoint x h'), 3 U1, 4 U2 (adjoint of h' x h_hor/h_ver)
   auto adj_off = [&](int qb) { return qb == 0 ? 0 : qb == 1 ? DH : qb == 2 ? 2 * DH : AJ::DHP; };
@@ -334,24 +356,24 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
       for (int i = 0; i < TA; ++i)
 #pragma unroll
         for (int j = 0; j < TA; ++j) accB[q][i][j] = T(0);
-    for (int k0 = 0; k0 < N; k0 += KC) {
-      const int kc = min(KC, N - k0);
+    for (int k0 = A.k_lo; k0 < A.k_hi; k0 += KC) {
+      const int kc = min(KC, A.k_hi - k0);
       __syncthreads();
       for (int e = tid; e < kc * AJ::W; e += 256) {
         int kk = e / AJ::W, wi = e - kk * AJ::W;
-        sadj[kk][wi] = adjrow[(int64_t)(k0 + kk) * A.adjw + wi];
+        sadj[kk][wi] = adj_at(k0 + kk)[wi];
       }
       for (int e = tid; e < kc * DH; e += 256) {
         int kk = e / DH, a = e - kk * DH, k = k0 + kk;
-        sH[kk][a] = hrow[(int64_t)k * DH + a];
+        sH[kk][a] = h_at(k)[a];
         if (DIM == 1) {
-          sQ[kk][a] = k > 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
+          sQ[kk][a] = k > 0 ? h_at(k - 1)[a] : T(0);
         } else {
           int j = k / Lx, m = k - j * Lx;
           int ver = k >= Lx ? k - 2 * m - 1 : -1;
-          sHh[kk][a] = m != 0 ? hrow[(int64_t)(k - 1) * DH + a] : T(0);
-          sHv[kk][a] = ver >= 0 ? hrow[(int64_t)ver * DH + a] : T(0);
-          sQ[kk][a] = adjrow[(int64_t)k * A.adjw + AJ::HP + a];
+          sHh[kk][a] = m != 0 ? h_at(k - 1)[a] : T(0);
+          sHv[kk][a] = ver >= 0 ? h_at(ver)[a] : T(0);
+          sQ[kk][a] = adj_at(k)[AJ::HP + a];
         }
       }
       for (int kk = tid; kk < kc; kk += 256) {
@@ -427,11 +449,11 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
           for (int j = 0; j < TA; ++j) {
             const int a = ta + i, b2 = tb + j;
             const TO v = (TO)accB[q][i][j];
-            if (qb == 0) Orow[A.Wu + (int64_t)a * w + b2] = v;
-            else if (qb == 1) Orow[A.Wr + (int64_t)a * w + b2] = v;
-            else if (qb == 2) Orow[A.Wh + (int64_t)a * DH + b2] = v;
-            else if (qb == 3) Orow[A.U1 + (int64_t)a * DH + b2] = v;
-            else Orow[A.U2 + (int64_t)a * DH + b2] = v;
+            if (qb == 0) put(A.Wu + (int64_t)a * w + b2, v);
+            else if (qb == 1) put(A.Wr + (int64_t)a * w + b2, v);
+            else if (qb == 2) put(A.Wh + (int64_t)a * DH + b2, v);
+            else if (qb == 3) put(A.U1 + (int64_t)a * DH + b2, v);
+            else put(A.U2 + (int64_t)a * DH + b2, v);
           }
       }
     }
@@ -443,23 +465,23 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
     const TO v = (TO)accS[q];
     if (e < 4 * DH) {
       const int o = e / DH, b2 = e - o * DH;
-      if (o < 2) Orow[A.Uo + o * DH + b2] = v;
-      else if (A.cplx) Orow[A.Up + (o - 2) * DH + b2] = v;
+      if (o < 2) put(A.Uo + o * DH + b2, v);
+      else if (A.cplx) put(A.Up + (o - 2) * DH + b2, v);
     } else if (e < 4 * DH + 3 * DH * DIN) {
       const int e2 = e - 4 * DH;
       const int gsel = e2 / (DH * DIN), rem = e2 - gsel * DH * DIN;
       const int a = rem / DIN, d = rem - a * DIN;
-      if (gsel == 0) Orow[A.Wu + (int64_t)a * w + DH + d] = v;
-      else if (gsel == 1) Orow[A.Wr + (int64_t)a * w + DH + d] = v;
-      else Orow[A.Win + (int64_t)a * DIN + d] = v;
+      if (gsel == 0) put(A.Wu + (int64_t)a * w + DH + d, v);
+      else if (gsel == 1) put(A.Wr + (int64_t)a * w + DH + d, v);
+      else put(A.Win + (int64_t)a * DIN + d, v);
     } else {
       const int e2 = e - 4 * DH - 3 * DH * DIN;
-      if (e2 < DH) Orow[A.bu + e2] = v;
-      else if (e2 < 2 * DH) Orow[A.br + e2 - DH] = v;
-      else if (e2 < 3 * DH) Orow[A.bh + e2 - 2 * DH] = v;
-      else if (e2 < 4 * DH) Orow[A.bin + e2 - 3 * DH] = v;
-      else if (e2 < 4 * DH + 2) Orow[A.co + e2 - 4 * DH] = v;
-      else if (A.cplx) Orow[A.cp + e2 - 4 * DH - 2] = v;
+      if (e2 < DH) put(A.bu + e2, v);
+      else if (e2 < 2 * DH) put(A.br + e2 - DH, v);
+      else if (e2 < 3 * DH) put(A.bh + e2 - 2 * DH, v);
+      else if (e2 < 4 * DH) put(A.bin + e2 - 3 * DH, v);
+      else if (e2 < 4 * DH + 2) put(A.co + e2 - 4 * DH, v);
+      else if (A.cplx) put(A.cp + e2 - 4 * DH - 2, v);
     }
   }
 }

@@ -23,7 +23,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, hseg, carry, total;
 };
 
 }  // namespace
@@ -45,6 +45,9 @@ struct nqs_ctx {
   int adjw = 0;
   int gw = 0;  // gate-cache record width: 4 dh (+ dh in 2D)
   size_t es = 8;  // element size of the recurrence precision
+  // hidden-state checkpoints (1D): stride ck (0 = every state cached), nck
+  // checkpoint slots, nseg segments of the reverse sweep
+  int ck = 0, nck = 0, nseg = 1;
   WsOff off{};
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -64,7 +67,7 @@ struct nqs_ctx {
   int64_t gnext = -1;
   // launch shapes chosen by nqs_autotune for tuned_ns samples (0 = built-in)
   int64_t tuned_ns = 0;
-  int t_eloc_grid = 0, t_gram_splits = 0, t_solve_grid = 0;
+  int t_eloc_grid = 0, t_gram_splits = 0, t_solve_grid = 0, t_chol_var = -1;
   double t_ms[3] = {0, 0, 0}, t_ms_default[3] = {0, 0, 0};
   int64_t cur_ns = 0;  // sample count of the step being issued
   // batched steps: order this context's cooperative solve after another's
@@ -152,7 +155,7 @@ void carve(nqs_ctx *c) {
   o.pack = take(c->P.total * es);
   o.spins = take(ns * N);
   o.logpsi = take(ns * 2 * 8);
-  o.hcache = take(ns * N * dh * es);
+  o.hcache = take(c->ck ? ns * std::max(c->nck, 1) * dh * es : ns * N * dh * es);
   o.lccache = take(ns * N * 2 * es);
   o.eloc = take(ns * 2 * 8);
   o.item_s = take((size_t)c->n_off * ns * 4);
@@ -160,7 +163,7 @@ void carve(nqs_ctx *c) {
   o.item_cnt = take((size_t)c->n_off * 4);
   o.contrib = take((size_t)c->n_off * ns * 16);
   o.colbuf = take(c->L.dim == 2 ? (size_t)c->eloc_grid * c->eloc_R * c->L.Lx * dh * es : 0);
-  o.adj = take(R * N * c->adjw * es);
+  o.adj = take(R * (c->ck ? c->ck : N) * c->adjw * es);
   o.adjcol = take(c->L.dim == 2 ? R * c->L.Lx * dh * es : 0);
   o.O = take(R * np * es);
   o.mean = take(2 * np * 8);
@@ -177,7 +180,9 @@ void carve(nqs_ctx *c) {
   o.cy = take(R * 8);
   o.cpart = take((size_t)2 * c->rd.sm_count * CC_B * 8);
   o.cbar = take(64);
-  o.gcache = take(ns * N * c->gw * es);
+  o.gcache = take(ns * (c->ck ? c->ck : N) * c->gw * es);
+  o.hseg = take(c->ck ? ns * (c->ck + 1) * dh * es : 0);
+  o.carry = take(c->ck ? R * dh * es : 0);
   o.L32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Li32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
@@ -225,6 +230,8 @@ FwdArgs<T> fwd_args(nqs_ctx *c) {
   a.N = c->L.N; a.Lx = c->L.Lx; a.cplx = c->L.cplx; a.marshall = c->L.marshall; a.zmask = c->L.zmask;
   a.hcache = W<T>(c, c->off.hcache);
   a.lccache = W<T>(c, c->off.lccache);
+  a.ck = c->ck;
+  a.nck = c->nck;
   return a;
 }
 
@@ -234,7 +241,7 @@ nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t st
                      double *logpsi, cudaStream_t st, bool with_gates = false) {
   FwdArgs<T> a = fwd_args<T>(c);
   a.nrows = n; a.seed = seed; a.step = step; a.spins = spins; a.logpsi = logpsi;
-  if (with_gates) {
+  if (with_gates && c->ck == 0) {
     a.gcache = W<T>(c, c->off.gcache);
     a.gw = c->gw;
   }
@@ -292,6 +299,8 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.op_f = c->d_opf; e.item_s = a.item_s; e.item_e = a.item_e; e.item_cnt = a.item_cnt;
       e.contrib = a.contrib;
       e.err = W<int>(c, c->off.sstat);
+      e.ck = c->ck;
+      e.nck = c->nck;
       CU(eloc_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
@@ -310,34 +319,76 @@ nqs_status eloc_any(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, 
   return f32(c) ? eloc_T<float>(c, ns, spins, eloc, st) : eloc_T<double>(c, ns, spins, eloc, st);
 }
 
-// Jacobian rows of the ns cached configurations into O (precision T).
+// Jacobian rows of the ns cached configurations into O (precision T).  With
+// checkpoints, the reverse sweep runs segment by segment from the last: the
+// segment's states and gates are recomputed from its checkpoint, the sweep
+// carries the adjoint of the state into the previous segment, and the
+// segment's contributions are added into O.
 template <typename T>
 nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_t st) {
   const int64_t R = c->L.cplx ? 2 * ns : ns;
+  const int N = c->L.N;
   BwdArgs<T> b{};
   b.pack = W<T>(c, c->off.pack);
-  b.N = c->L.N; b.Lx = c->L.Lx; b.cplx = c->L.cplx; b.zmask = c->L.zmask;
+  b.N = N; b.Lx = c->L.Lx; b.cplx = c->L.cplx; b.zmask = c->L.zmask;
   b.ns = ns; b.nrows = R;
   b.spins = spins;
-  b.hcache = W<T>(c, c->off.hcache);
   b.gcache = W<T>(c, c->off.gcache);
   b.gw = c->gw;
   b.lccache = W<T>(c, c->off.lccache);
   b.adj = W<T>(c, c->off.adj);
   b.adjw = c->adjw;
   b.adjcol = W<T>(c, c->off.adjcol);
-  mark(c, 6, st);
-  CU(run_bwd<T>(c->rd, b, st));
-  mark(c, 7, st);
-  c->launches += 2;
   GradArgs<T, T> g{};
-  g.N = c->L.N; g.Lx = c->L.Lx; g.cplx = c->L.cplx; g.dim = c->L.dim;
-  g.ns = ns; g.nrows = R; g.spins = spins; g.hcache = b.hcache; g.adj = b.adj; g.adjw = c->adjw;
+  g.N = N; g.Lx = c->L.Lx; g.cplx = c->L.cplx; g.dim = c->L.dim;
+  g.ns = ns; g.nrows = R; g.spins = spins; g.adj = b.adj; g.adjw = c->adjw;
   g.O = O; g.np = c->L.np;
   g.U1 = c->L.U1; g.U2 = c->L.U2; g.Wu = c->L.Wu; g.bu = c->L.bu; g.Wr = c->L.Wr; g.br = c->L.br;
   g.Wh = c->L.Wh; g.bh = c->L.bh; g.Win = c->L.Win; g.bin = c->L.bin; g.Uo = c->L.Uo;
   g.co = c->L.co; g.Up = c->L.Up; g.cp = c->L.cp;
-  return cu(run_grad<T>(c->rd, g, st));
+  if (c->ck == 0) {
+    b.hcache = W<T>(c, c->off.hcache);
+    b.k_lo = 0; b.k_hi = N; b.hN = N; b.hoff = 0; b.gN = N; b.goff = 0; b.aN = N; b.aoff = 0;
+    mark(c, 6, st);
+    CU(run_bwd<T>(c->rd, b, st));
+    mark(c, 7, st);
+    c->launches += 2;
+    g.hcache = b.hcache;
+    g.k_lo = 0; g.k_hi = N; g.hN = N; g.hoff = 0; g.aN = N; g.aoff = 0; g.accumulate = 0;
+    return cu(run_grad<T>(c->rd, g, st));
+  }
+  const int ck = c->ck;
+  T *hseg = W<T>(c, c->off.hseg);
+  T *carry = W<T>(c, c->off.carry);
+  mark(c, 6, st);
+  CU(cudaMemsetAsync(carry, 0, (size_t)R * c->L.dh * sizeof(T), st));
+  for (int m = c->nseg - 1; m >= 0; --m) {
+    const int k_lo = m * ck, k_hi = std::min(N, k_lo + ck);
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = ns;
+    a.spins = const_cast<uint8_t *>(spins);
+    a.gcache = W<T>(c, c->off.gcache);
+    a.gw = c->gw;
+    a.hseg = hseg;
+    a.k_lo = k_lo; a.k_hi = k_hi;
+    CU(run_forward<T>(c->rd, MODE_GIVEN, a, 0, st));
+    b.hcache = hseg;
+    b.k_lo = k_lo; b.k_hi = k_hi;
+    b.hN = ck + 1; b.hoff = k_lo - 1;
+    b.gN = ck; b.goff = k_lo;
+    b.aN = ck; b.aoff = k_lo;
+    b.carry = carry;
+    CU(run_bwd<T>(c->rd, b, st));
+    g.hcache = hseg;
+    g.k_lo = k_lo; g.k_hi = k_hi;
+    g.hN = ck + 1; g.hoff = k_lo - 1;
+    g.aN = ck; g.aoff = k_lo;
+    g.accumulate = m != c->nseg - 1;
+    CU(run_grad<T>(c->rd, g, st));
+    c->launches += 3;
+  }
+  mark(c, 7, st);
+  return NQS_OK;
 }
 
 // T = A A^T in FP64 (see nqs_gram).
@@ -357,6 +408,17 @@ nqs_status gram_any(nqs_ctx *c, const void *A, int64_t R, int64_t np, double *T,
 }
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+
+// After the FP64 Cholesky of the tensor-core T: a non-positive pivot arms the
+// FP64-Gram retry (status cleared, need_fp64 = 2), anything else disarms it.
+__global__ void k_retry_arm(int32_t *status, int32_t *retry, int32_t *need_fp64) {
+  const bool arm = *status == (int32_t)NQS_ERR_NOT_SPD;
+  *retry = arm ? 1 : 0;
+  if (arm) {
+    *status = 0;
+    *need_fp64 = 2;
+  }
+}
 __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 __global__ void k_inc_i64(int64_t *p) { *p += 1; }
 
@@ -381,7 +443,9 @@ __global__ void k_shift(double *T, int64_t R, double lam) {
   if (i < R) T[i * R + i] += lam;
 }
 
-__global__ void k_frob_part(const double *__restrict__ T, int64_t n2, double *part) {
+__global__ void k_frob_part(const double *__restrict__ T, int64_t n2, double *part,
+                            const int32_t *gate = nullptr) {
+  if (gate && *gate == 0) return;
   __shared__ double s[256];
   double acc = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2;
@@ -397,7 +461,9 @@ __global__ void k_frob_part(const double *__restrict__ T, int64_t n2, double *pa
 }
 
 __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int nparts, int mode,
-                                double lam_c, double coeff, double pw, nqs_step_stats *st) {
+                                double lam_c, double coeff, double pw, nqs_step_stats *st,
+                                const int32_t *gate = nullptr) {
+  if (gate && *gate == 0) return;
   __shared__ double lam_s;
   if (threadIdx.x == 0) {
     double acc = 0.0;
@@ -418,8 +484,13 @@ __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int np
 // kernel follows on the stream and runs only if the refinement reports that
 // it must (non-positive FP32 pivot or no convergence).  *need_fp64 (device)
 // ends as 0 (refined) or 1 (FP64 factorisation).
+struct RetryInfo {
+  const nqs_step_hparams *hp;  // lambda of the step
+  nqs_step_stats *stats;
+};
+
 nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double *x,
-                      int32_t *status, cudaStream_t st) {
+                      int32_t *status, cudaStream_t st, const RetryInfo *retry = nullptr) {
   unsigned *bar = W<unsigned>(c, c->off.cbar);
   int32_t *need = reinterpret_cast<int32_t *>(bar + 4);
   const int G = solve_grid(c);
@@ -439,10 +510,14 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     ir.need_fp64 = need;
     ir.maxit = 12;
     const size_t smem = chol_ir_smem(R);
-    CU(cudaFuncSetAttribute(k_chol_ir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // tiles per warp pay off once n is large (measured: 16.5 vs 19.8 ms at
+    // n = 4096, 1.71 vs 0.93 ms at n = 1024)
+    const bool wt = tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var == 1 : R >= 2048;
+    const void *kern = wt ? (const void *)k_chol_ir<true> : (const void *)k_chol_ir<false>;
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void *args[] = {&ir};
     c->launches += 1;
-    CU(cudaLaunchCooperativeKernel((void *)k_chol_ir, dim3(G), dim3(IR_THREADS), args, smem, st));
+    CU(cudaLaunchCooperativeKernel(kern, dim3(G), dim3(IR_THREADS), args, smem, st));
   } else {
     k_set_i32<<<1, 1, 0, st>>>(need, 1);
     c->launches += 1;
@@ -464,6 +539,26 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
   void *args[] = {&a};
   c->launches += 1;
   CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
+  if (retry && f32(c) && gram_tc_available()) {
+    // T from the tensor cores can miss positive definiteness by its rounding
+    // when lambda is tiny against ||T||: then rebuild T in FP64 from the same
+    // split planes, recompute lambda and factor again in FP64 (all gated on
+    // the device, so the sequence is graph-capturable)
+    int32_t *rflag = need + 1;
+    k_retry_arm<<<1, 1, 0, st>>>(status, rflag, need);
+    const int64_t np = c->L.np;
+    CU(gram_split_f64(c->ws + c->off.split, R, np, T, rflag, st));
+    const int nparts = 256;
+    k_frob_part<<<nparts, 256, 0, st>>>(T, R * R, W<double>(c, c->off.frob), rflag);
+    k_lambda_finish<<<1, 1024, 0, st>>>(T, R, W<double>(c, c->off.frob), nparts,
+                                        retry->hp->lambda_mode, retry->hp->lambda,
+                                        retry->hp->lambda_coeff, retry->hp->lambda_pow,
+                                        retry->stats, rflag);
+    CU(cudaMemsetAsync(bar, 0, 4, st));
+    a.gate = rflag;
+    c->launches += 5;
+    CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
+  }
   mark(c, 12, st);
   return NQS_OK;
 }
@@ -492,8 +587,10 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     a.nrows = ns; a.seed = hp->seed; a.step = (uint64_t)hp->step_index;
     a.step_dev = W<int64_t>(c, c->off.dstep);
     a.spins = spins; a.logpsi = logpsi;
-    a.gcache = W<T>(c, c->off.gcache);
-    a.gw = c->gw;
+    if (c->ck == 0) {  // gates for the reverse sweep (recomputed per segment otherwise)
+      a.gcache = W<T>(c, c->off.gcache);
+      a.gw = c->gw;
+    }
     c->launches += 1;
     CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
   }
@@ -550,7 +647,8 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
   mark(c, 11, st);
   if (c->solve_wait) CU(cudaStreamWaitEvent(st, c->solve_wait, 0));
-  ST(chol_solve(c, Tm, R, eps, x, sstat, st));
+  const RetryInfo rinfo{hp, stats};
+  ST(chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo));
   if (c->solve_rec) CU(cudaEventRecord(c->solve_rec, st));
   mark(c, 13, st);
   k_eta<<<1, 1024, 0, st>>>(eps, x, R, hp->eta0, hp->decay_T, hp->trust_region,
@@ -623,6 +721,11 @@ extern "C" {
 
 nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int precision,
                       int64_t max_samples, nqs_ctx **out) {
+  return nqs_create_ex(model, ham, precision, max_samples, nullptr, out);
+}
+
+nqs_status nqs_create_ex(const nqs_model_desc *model, const nqs_ham_desc *ham, int precision,
+                         int64_t max_samples, const nqs_options *opt, nqs_ctx **out) {
   if (!model || !ham || !out || max_samples <= 0) return NQS_ERR_ARG;
   *out = nullptr;
   const nqs_model_desc &m = *model;
@@ -639,6 +742,19 @@ nqs_status nqs_create(const nqs_model_desc *model, const nqs_ham_desc *ham, int 
   nqs_ctx *c = new (std::nothrow) nqs_ctx();
   if (!c) return NQS_ERR_ARG;
   c->m = m; c->h = *ham; c->prec = precision; c->max_ns = max_samples;
+  if (opt && opt->checkpoint_stride != 0) {
+    int ck = opt->checkpoint_stride;
+    if (ck < -1) { delete c; return NQS_ERR_ARG; }
+    if (m.dim != 1) { delete c; return NQS_ERR_UNSUPPORTED; }
+    if (ck == -1) {
+      ck = 1;
+      while (ck * ck < N) ++ck;  // ceil(sqrt(N))
+    }
+    ck = std::min(ck, N);
+    c->ck = ck;
+    c->nseg = (N + ck - 1) / ck;
+    c->nck = c->nseg - 1;
+  }
   c->L = make_layout(m);
   c->P = pack_offsets(c->L);
   c->es = precision == NQS_PREC_MIXED ? 4 : 8;
@@ -688,6 +804,12 @@ nqs_status nqs_destroy(nqs_ctx *c) {
   if (c->d_diag) cudaFree(c->d_diag);
   if (c->d_opf) cudaFree(c->d_opf);
   delete c;
+  return NQS_OK;
+}
+
+nqs_status nqs_checkpoint_stride(const nqs_ctx *c, int *stride) {
+  if (!c || !stride) return NQS_ERR_ARG;
+  *stride = c->ck;
   return NQS_OK;
 }
 
@@ -875,7 +997,7 @@ nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step
 namespace {
 
 struct Tuned {
-  int eloc_grid, gram_splits, solve_grid;
+  int eloc_grid, gram_splits, solve_grid, chol_var;
   double ms[3], ms_default[3];
 };
 std::mutex g_tune_mu;
@@ -956,6 +1078,7 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
   CU(cudaStreamSynchronize(st));
   c->tuned_ns = ns;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
+  c->t_chol_var = -1;
   const int reps = 2;
   auto none = [] { return NQS_OK; };
   uint8_t *spins = W<uint8_t>(c, c->off.spins);
@@ -1001,26 +1124,33 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
     c->t_gram_splits = pick;
     c->t_ms[1] = best;
   }
-  // (3) grid of the cooperative solve (T rebuilt before every timed solve)
+  // (3) grid and tile mapping of the cooperative solve (T rebuilt before
+  //     every timed solve)
   {
     const int G0 = c->rd.sm_count;
     std::vector<int> cand;
     for (int d : {1, 2, 4, 8}) uniq_push(cand, G0 / d);
+    const int var0 = R >= 2048 ? 1 : 0;
     double best = 1e300;
-    int pick = G0;
+    int pick = G0, pvar = var0;
     double *Tm = W<double>(c, c->off.T);
-    for (int g : cand) {
-      c->t_solve_grid = g;
-      double ms = 0;
-      ST(best_ms(st, reps, [&] { return regram<T>(c, ns, *hp, tstats, st); },
-                 [&] {
-                   return chol_solve(c, Tm, R, W<double>(c, c->off.eps), W<double>(c, c->off.x),
-                                     W<int32_t>(c, c->off.sstat), st);
-                 }, &ms));
-      if (g == G0) c->t_ms_default[2] = ms;
-      if (ms < best) { best = ms; pick = g; }
+    for (int var : {0, 1}) {
+      if (!f32(c) && var == 1) continue;  // the FP64 path has one variant
+      for (int g : cand) {
+        c->t_solve_grid = g;
+        c->t_chol_var = var;
+        double ms = 0;
+        ST(best_ms(st, reps, [&] { return regram<T>(c, ns, *hp, tstats, st); },
+                   [&] {
+                     return chol_solve(c, Tm, R, W<double>(c, c->off.eps), W<double>(c, c->off.x),
+                                       W<int32_t>(c, c->off.sstat), st);
+                   }, &ms));
+        if (g == G0 && var == var0) c->t_ms_default[2] = ms;
+        if (ms < best) { best = ms; pick = g; pvar = var; }
+      }
     }
     c->t_solve_grid = pick;
+    c->t_chol_var = pvar;
     c->t_ms[2] = best;
   }
   return NQS_OK;
@@ -1051,6 +1181,7 @@ nqs_status nqs_autotune(nqs_ctx *c, const double *theta, const nqs_step_hparams 
       const Tuned &t = it->second;
       c->tuned_ns = hp->n_samples;
       c->t_eloc_grid = t.eloc_grid; c->t_gram_splits = t.gram_splits; c->t_solve_grid = t.solve_grid;
+      c->t_chol_var = t.chol_var;
       std::memcpy(c->t_ms, t.ms, sizeof t.ms);
       std::memcpy(c->t_ms_default, t.ms_default, sizeof t.ms_default);
       return NQS_OK;
@@ -1064,7 +1195,7 @@ nqs_status nqs_autotune(nqs_ctx *c, const double *theta, const nqs_step_hparams 
     c->tuned_ns = 0;
     return s;
   }
-  Tuned t{c->t_eloc_grid, c->t_gram_splits, c->t_solve_grid, {}, {}};
+  Tuned t{c->t_eloc_grid, c->t_gram_splits, c->t_solve_grid, c->t_chol_var, {}, {}};
   std::memcpy(t.ms, c->t_ms, sizeof t.ms);
   std::memcpy(t.ms_default, c->t_ms_default, sizeof t.ms_default);
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1078,6 +1209,7 @@ nqs_status nqs_get_tuning(const nqs_ctx *c, nqs_tuning *out) {
   out->eloc_grid = c->t_eloc_grid;
   out->gram_splits = c->t_gram_splits;
   out->solve_grid = c->t_solve_grid;
+  out->solve_tiles_per_warp = c->t_chol_var;
   for (int i = 0; i < 3; ++i) { out->ms[i] = c->t_ms[i]; out->ms_default[i] = c->t_ms_default[i]; }
   return NQS_OK;
 }
@@ -1087,6 +1219,7 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   drop_graph(c);
   c->tuned_ns = 0;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
+  c->t_chol_var = -1;
   return NQS_OK;
 }
 

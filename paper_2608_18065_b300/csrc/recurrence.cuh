@@ -18,6 +18,30 @@ template <int DH> struct Tile {
   static constexpr int UT = DH / UG;             // hidden units per thread
 };
 
+// n consecutive values from shared or global memory, as 16-byte vectors when
+// the element offset is a multiple of the vector width (callers guarantee
+// it: row/column offsets and leading dimensions are multiples of 4 floats
+// or 2 doubles whenever n is)
+template <typename T, int n>
+__device__ __forceinline__ void load_run(const T *__restrict__ p, T (&v)[n]) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  if constexpr (n % VW == 0) {
+#pragma unroll
+    for (int q = 0; q < n / VW; ++q) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 t = reinterpret_cast<const float4 *>(p)[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+      } else {
+        const double2 t = reinterpret_cast<const double2 *>(p)[q];
+        v[2 * q] = t.x; v[2 * q + 1] = t.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < n; ++i) v[i] = p[i];
+  }
+}
+
 // acc[i][j] += sum_k At[k*lda + r0 + i] * B[k*ldb + c0 + j]
 template <typename T, int RT, int CT>
 __device__ __forceinline__ void mm_acc(const T *__restrict__ At, int lda, int r0,
@@ -26,10 +50,8 @@ __device__ __forceinline__ void mm_acc(const T *__restrict__ At, int lda, int r0
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
     T a[RT], b[CT];
-#pragma unroll
-    for (int i = 0; i < RT; ++i) a[i] = At[k * lda + r0 + i];
-#pragma unroll
-    for (int j = 0; j < CT; ++j) b[j] = B[k * ldb + c0 + j];
+    load_run<T, RT>(At + k * lda + r0, a);
+    load_run<T, CT>(B + k * ldb + c0, b);
 #pragma unroll
     for (int i = 0; i < RT; ++i)
 #pragma unroll
@@ -79,6 +101,15 @@ template <typename T> struct FwdArgs {
   const int *item_cnt;     // [n_off]
   double *contrib;         // [n_off*Ns*2]
   T *colbuf;               // 2D ELOC: [gridDim][R][Lx][dh]
+  // hidden-state checkpoints (1D): ck > 0 keeps h_k only for k = m ck - 1
+  // (m = 1..nck), in slot m - 1 of hcache rows of nck slots; ck = 0 keeps
+  // every h_k (hcache rows of N sites)
+  int ck, nck;
+  // segment recompute (MODE_GIVEN, ck > 0): sites [k_lo, k_hi) from the
+  // checkpoint h_{k_lo-1}; states to hseg [rows][ck+1][dh] (slot 0 =
+  // h_{k_lo-1}), gates to gcache [rows][ck][gw]; log Psi is not written
+  int k_lo, k_hi;
+  T *hseg;
 };
 
 // Shared-memory footprint of k_forward; wsmem = 0 leaves the two large
@@ -181,14 +212,24 @@ k_forward(const FwdArgs<T> A) {
       }
       ssp[r * NP + k] = v;
     }
-    // initial state h_{kstart-1} (zero at the chain start)
+    // first recomputed site: the op's first changed site, or with
+    // checkpoints the site after the last checkpoint before it (sites in
+    // between are recomputed but add nothing to log Psi(sigma') - log Psi)
+    const bool seg = MODE == MODE_GIVEN && A.hseg != nullptr;
+    int krec = 0, kend = N;
+    if (MODE == MODE_ELOC) krec = A.ck > 0 ? (kstart / A.ck) * A.ck : kstart;
+    if (seg) { krec = A.k_lo; kend = A.k_hi; }
+    // initial state h_{krec-1} (zero at the chain start)
     for (int e = tid; e < R * DH; e += NTH) {
       int r = e / DH, a = e - r * DH;
       int s = srow[r];
       T v = T(0);
-      if (MODE == MODE_ELOC && kstart > 0 && s >= 0)
-        v = A.hcache[((int64_t)s * N + (kstart - 1)) * DH + a];
+      if (krec > 0 && s >= 0) {
+        if (A.ck > 0) v = A.hcache[((int64_t)s * A.nck + (krec / A.ck - 1)) * DH + a];
+        else v = A.hcache[((int64_t)s * N + (krec - 1)) * DH + a];
+      }
       sh0[a * R + r] = v;
+      if (seg && s >= 0) A.hseg[((int64_t)s * (A.ck + 1)) * DH + a] = v;
     }
     __syncthreads();
 
@@ -198,14 +239,14 @@ k_forward(const FwdArgs<T> A) {
     const int my_i = ug;  // row handled by this lane (if ug < RT)
     const int my_r = r0 + (my_i < RT ? my_i : 0);
     const int my_s = my_i < RT ? srow[my_r] : -1;
-    if (MODE == MODE_ELOC && my_s >= 0) {
-      for (int k = 0; k < kstart; ++k) {
+    if ((MODE == MODE_ELOC || seg) && my_s >= 0) {
+      for (int k = 0; k < krec; ++k) {
         if (ssp[my_r * NP + k] == 0) ++n_up; else ++n_dn;
       }
     }
 
     T *hcur = sh0, *hnxt = sh1;
-    for (int k = kstart; k < N; ++k) {
+    for (int k = krec; k < kend; ++k) {
       const T *Ag = hcur;  // A operand of the gate GEMM: h_{k-1} or h'
       int hor_ok = k > 0, ver = -1, col = 0;
       if (DIM == 2) {
@@ -289,10 +330,16 @@ k_forward(const FwdArgs<T> A) {
           const T hn = (T(1) - u) * hp + u * c;
           hnxt[a * R + r] = hn;
           if (s >= 0) {
-            if (MODE != MODE_ELOC && A.hcache)
-              A.hcache[((int64_t)s * N + k) * DH + a] = hn;
+            if (seg) {
+              A.hseg[((int64_t)s * (A.ck + 1) + (k - krec + 1)) * DH + a] = hn;
+            } else if (MODE != MODE_ELOC && A.hcache) {
+              if (A.ck == 0) A.hcache[((int64_t)s * N + k) * DH + a] = hn;
+              else if ((k + 1) % A.ck == 0 && (k + 1) / A.ck <= A.nck)
+                A.hcache[((int64_t)s * A.nck + ((k + 1) / A.ck - 1)) * DH + a] = hn;
+            }
             if (MODE != MODE_ELOC && A.gcache) {
-              T *gr = A.gcache + ((int64_t)s * N + k) * A.gw;
+              T *gr = seg ? A.gcache + ((int64_t)s * A.ck + (k - krec)) * A.gw
+                          : A.gcache + ((int64_t)s * N + k) * A.gw;
               gr[a] = u; gr[DH + a] = rr; gr[2 * DH + a] = c; gr[3 * DH + a] = gg;
               if (DIM == 2) gr[4 * DH + a] = hp;
             }
@@ -340,10 +387,12 @@ k_forward(const FwdArgs<T> A) {
           ph = NQS_PI * (double)softsign(y);
         }
         if (MODE == MODE_ELOC) {
-          const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
-          acc_re += 0.5 * lps - (double)lc[0];
-          acc_im += ph - (double)lc[1];
-        } else {
+          if (k >= kstart) {
+            const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+            acc_re += 0.5 * lps - (double)lc[0];
+            acc_im += ph - (double)lc[1];
+          }
+        } else if (!seg) {
           acc_re += 0.5 * lps;
           acc_im += ph;
           if (A.lccache) {
@@ -366,7 +415,7 @@ k_forward(const FwdArgs<T> A) {
         double* c = A.contrib + ((int64_t)op * A.nrows + my_s) * 2;
         c[0] = e * mag * cos(acc_im);
         c[1] = e * mag * sin(acc_im);
-      } else {
+      } else if (!seg) {
         A.logpsi[2 * (int64_t)my_s] = acc_re;
         A.logpsi[2 * (int64_t)my_s + 1] = acc_im + (A.marshall ? NQS_PI * (double)(nA & 1) : 0.0);
       }

@@ -45,6 +45,10 @@ STATS_FIELDS = ["E_re", "E_im", "var", "vscore", "lam", "normT", "eta_eff", "tau
 STATS_DOUBLES = 9  # 8 doubles + (status, pad) as int32 pair
 
 
+class Options(C.Structure):
+    _fields_ = [("checkpoint_stride", C.c_int)]
+
+
 class StepOutputs(C.Structure):
     _fields_ = [("spins", C.c_void_p), ("logpsi", C.c_void_p), ("eloc", C.c_void_p),
                 ("T", C.c_void_p), ("eps", C.c_void_p), ("x", C.c_void_p),
@@ -59,14 +63,15 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_autotune", "nqs_get_tuning", "nqs_clear_tuning", "nqs_batch_create",
            "nqs_batch_destroy", "nqs_minsr_step_batched", "nqs_batch_set_graph",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
-           "nqs_batch_autotune", "nqs_eloc_work",
+           "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_stage_name", "nqs_status_string"]
 TUNE_FORCE = 1
 
 
 class Tuning(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("eloc_grid", C.c_int), ("gram_splits", C.c_int),
-                ("solve_grid", C.c_int), ("ms", C.c_double * 3), ("ms_default", C.c_double * 3)]
+                ("solve_grid", C.c_int), ("solve_tiles_per_warp", C.c_int),
+                ("ms", C.c_double * 3), ("ms_default", C.c_double * 3)]
 
 
 def lib():
@@ -114,14 +119,18 @@ class Context:
     """A libnqs context plus its torch-owned device workspace."""
 
     def __init__(self, model: ModelSpec, ham: HamSpec, precision: str, max_samples: int,
-                 device="cuda"):
+                 device="cuda", checkpoint_stride: int = 0):
+        """checkpoint_stride: 0 caches every hidden state; c > 0 (or -1 for
+        ceil(sqrt(N))) keeps every c-th and recomputes the rest (1D)."""
         self.model, self.ham, self.precision = model, ham, precision
         self.max_samples = int(max_samples)
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
             h = C.c_void_p()
-            _check(lib().nqs_create(C.byref(model_desc(model)), C.byref(ham_desc(ham)),
-                                    PREC[precision], C.c_int64(self.max_samples), C.byref(h)))
+            opt = Options(int(checkpoint_stride))
+            _check(lib().nqs_create_ex(C.byref(model_desc(model)), C.byref(ham_desc(ham)),
+                                       PREC[precision], C.c_int64(self.max_samples),
+                                       C.byref(opt), C.byref(h)))
             self._h = h
             n = C.c_int64()
             _check(lib().nqs_param_count(h, C.byref(n)))
@@ -136,6 +145,11 @@ class Context:
             _check(lib().nqs_set_workspace(h, C.c_void_p(base + off), C.c_size_t(b.value)))
         self.odtype = torch.float32 if precision == "mixed" else torch.float64
         self.rows_per_sample = 2 if model.cplx else 1
+
+    def checkpoint_stride(self):
+        v = C.c_int()
+        _check(lib().nqs_checkpoint_stride(self._h, C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -270,6 +284,7 @@ class Context:
         names = ("eloc", "gram", "solve")
         return {"n_samples": t.n_samples, "eloc_grid": t.eloc_grid,
                 "gram_splits": t.gram_splits, "solve_grid": t.solve_grid,
+                "solve_tiles_per_warp": t.solve_tiles_per_warp,
                 "ms": dict(zip(names, list(t.ms))),
                 "ms_default": dict(zip(names, list(t.ms_default)))}
 

@@ -103,3 +103,74 @@ def test_full_size_step(key, prec):
     d_ref = stats["eta_eff"] * (A.T @ x)
     d = outs["dtheta"].cpu().numpy()
     assert rel_err(d, d_ref) < (1e-9 if f64 else 5e-4)
+
+
+def _fp64_gram_of(ctx, model, th, spins, ns):
+    """T from the context's own FP32 Jacobian, centred and multiplied in FP64."""
+    O = ctx.jacobian(th, spins).double()
+    blocks = [O[:ns]] + ([O[ns:]] if model.cplx else [])
+    Oc = torch.cat([(b - b.mean(0)) / np.sqrt(ns) for b in blocks], 0)
+    return Oc @ Oc.T
+
+
+def test_tensor_core_gram_keeps_positive_semidefinite():
+    """The tensor-core T (four split products, compensated chunk sums) stays
+    within FP32-split accuracy of the FP64 Gram of the same FP32 Jacobian and
+    loses positive semi-definiteness only at the level of its own rounding
+    (dropping lo lo^T or summing long K ranges in one FP32 accumulator made
+    its smallest eigenvalue about -1e-4 ||T|| on this 10 x 10 lattice)."""
+    w = workloads()["heis10"]
+    model, ham, hp = w.model, w.ham, w.hp
+    ns = hp.ns
+    c = nqs.Context(model, ham, "mixed", ns)
+    th = torch.tensor(init_theta(model, w.theta_seed), device="cuda")
+    outs = c.step_outputs(ns)
+    s = c.new_stats()
+    c.minsr_step(th.clone(), torch.zeros_like(th), hp, 0, s, outputs=outs)
+    torch.cuda.synchronize()
+    T = outs["T"]
+    Tx = _fp64_gram_of(c, model, th, outs["spins"], ns)
+    scale = Tx.abs().max().item()
+    assert (T - Tx).abs().max().item() <= 2e-5 * scale
+    ev = torch.linalg.eigvalsh(T)
+    assert ev.min().item() >= -1e-7 * ev.max().item(), (ev.min().item(), ev.max().item())
+    st = nqs.decode_stats(s)
+    assert st["status"] == 0 and st["solve_fp64"] == 0, st
+
+
+def test_mixed_steps_accepted_where_fp64_is():
+    """Tab. I Heisenberg steps on the 10 x 10 lattice: every mixed step is
+    accepted (status 0), as on the FP64 path."""
+    w = workloads()["heis10"]
+    c = nqs.Context(w.model, w.ham, "mixed", w.hp.ns)
+    th = torch.tensor(init_theta(w.model, w.theta_seed), device="cuda")
+    mo = torch.zeros_like(th)
+    s = c.new_stats()
+    for t in range(4):
+        c.minsr_step(th, mo, w.hp, t, s)
+        torch.cuda.synchronize()
+        st = nqs.decode_stats(s)
+        assert st["status"] == 0, (t, st)
+
+
+def test_fp64_gram_retry_when_lambda_is_below_tensor_core_rounding():
+    """A 12 x 12 J1-J2 instance (dh 32, Ns 256, lambda = 0.1) whose ||T||
+    reaches 1e8-1e9: T + lambda I from the tensor cores is indefinite by its
+    rounding, the step rebuilds T in FP64 from the split planes and solves
+    again (solve_fp64 = 2) instead of being rejected; the FP64 path accepts
+    the same steps."""
+    from paper_2608_18065_b300.inputs import batched_instances
+    w = batched_instances()[11]
+    c = nqs.Context(w.model, w.ham, "mixed", w.hp.ns)
+    th = torch.tensor(init_theta(w.model, w.theta_seed), device="cuda")
+    mo = torch.zeros_like(th)
+    s = c.new_stats()
+    seen = set()
+    for t in range(5):
+        c.minsr_step(th, mo, w.hp, t, s)
+        torch.cuda.synchronize()
+        st = nqs.decode_stats(s)
+        assert st["status"] == 0, (t, st)
+        seen.add(st["solve_fp64"])
+    assert 2 in seen, seen
+    assert torch.isfinite(th).all()
