@@ -252,6 +252,8 @@ typedef struct {
   int gram_splits;    /* K-slices per 128x128 tile of the tensor-core Gram */
   int solve_grid;     /* CTAs of the cooperative Cholesky / refinement */
   int solve_tiles_per_warp; /* refinement tiles: 1 per warp, 0 per CTA, -1 built-in */
+  int solve_substitution;   /* refinement sweeps: 1 block substitution, 0 explicit inverse, -1 built-in */
+  int reserved;
   double ms[3];         /* time of the chosen shape: eloc, gram, solve */
   double ms_default[3]; /* time of the built-in shape */
 } nqs_tuning;

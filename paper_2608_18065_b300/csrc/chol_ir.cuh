@@ -41,6 +41,10 @@ struct CholIrArgs {
   int32_t *status;   // NQS_ERR_TIMEOUT on a barrier timeout
   int32_t *need_fp64;// out: 1 when the FP64 factorisation must run
   int maxit;
+  float *dv;         // [n] scratch: L^{-T} w (substitution sweeps)
+  int subst;         // 1: sweeps by block substitution with the inverted
+                     // 32x32 diagonal blocks (no full inverse); 0: two
+                     // products with the explicit inverse
 };
 
 // Per-warp 32x32 tile product in shared memory (row stride WS floats, a
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     __syncthreads();
   }
   if (!cc_grid_sync(a.bar, a.status)) return;
-  for (int64_t sz = IR_B; sz < n; sz *= 2) {
+  for (int64_t sz = IR_B; sz < n && !a.subst; sz *= 2) {
     // Tm[pair block] = L21 Li11 ; then Li21 = -Li22 Tm
     for (int phase = 0; phase < 2; ++phase) {
       const int64_t pairs = (n + 2 * sz - 1) / (2 * sz);
@@ -366,7 +370,56 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   const int64_t nch = (n + CH - 1) / CH;
   double normA = 0.0;
   int converged = 0;
+  __shared__ float sw_s[IR_B];
   for (int it = 0; it < a.maxit && !converged; ++it) {
+    if (a.subst) {
+      // d = L^{-T} L^{-1} r by block substitution: per 32-block one grid
+      // barrier; every CTA forms the block's solution from the inverted
+      // diagonal block, CTA 0 stores it, all warps fold it into the rows
+      // (forward) or columns (backward) still to come.
+      for (int64_t i = (int64_t)g * IR_THREADS + tid; i < n; i += (int64_t)G * IR_THREADS)
+        a.wv[i] = (float)a.r[i];
+      if (!cc_grid_sync(a.bar, a.status)) return;
+      for (int p = 0; p < nb; ++p) {  // forward: L w = r
+        const int64_t c0 = (int64_t)p * IR_B;
+        const int m = (int)min64(IR_B, n - c0);
+        if (warp == 0) {
+          float acc = 0.f;
+          if (lane < m)
+            for (int j = 0; j <= lane; ++j) acc = fmaf(Li[(c0 + lane) * n + c0 + j], a.wv[c0 + j], acc);
+          sw_s[lane] = acc;
+        }
+        __syncthreads();
+        if (g == 0 && tid < m) a.dv[c0 + tid] = sw_s[tid];
+        for (int64_t i = c0 + m + gw; i < n; i += nwarps) {
+          float t = lane < m ? L[i * n + c0 + lane] * sw_s[lane] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == 0) a.wv[i] -= t;
+        }
+        if (!cc_grid_sync(a.bar, a.status)) return;
+      }
+      for (int p = nb - 1; p >= 0; --p) {  // backward: L^T d = w (w in dv)
+        const int64_t c0 = (int64_t)p * IR_B;
+        const int m = (int)min64(IR_B, n - c0);
+        if (warp == 0) {
+          float acc = 0.f;
+          if (lane < m)
+            for (int k = lane; k < m; ++k) acc = fmaf(Li[(c0 + k) * n + c0 + lane], a.dv[c0 + k], acc);
+          sw_s[lane] = acc;
+        }
+        __syncthreads();
+        // the block's correction goes straight into x (dv of this block is
+        // not read again)
+        if (g == 0 && tid < m) a.x[c0 + tid] += (double)sw_s[tid];
+        for (int64_t j = (int64_t)g * IR_THREADS + tid; j < c0; j += (int64_t)G * IR_THREADS) {
+          float t = 0.f;
+          for (int i = 0; i < m; ++i) t = fmaf(L[(c0 + i) * n + j], sw_s[i], t);
+          a.dv[j] -= t;
+        }
+        if (!cc_grid_sync(a.bar, a.status)) return;
+      }
+    } else {
     // w = Li r (one warp per row)
     for (int64_t i = gw; i < n; i += nwarps) {
       const float *row = Li + i * n;
@@ -395,6 +448,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       a.x[j] += (double)d;
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
+    }
     // r = b - A x in FP64; partial max |r_i|, max |x_i| and (first sweep) max
     // row sum |A|
     double rmax = 0.0, xmax = 0.0, amax = 0.0;

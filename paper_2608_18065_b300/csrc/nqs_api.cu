@@ -67,7 +67,7 @@ struct nqs_ctx {
   int64_t gnext = -1;
   // launch shapes chosen by nqs_autotune for tuned_ns samples (0 = built-in)
   int64_t tuned_ns = 0;
-  int t_eloc_grid = 0, t_gram_splits = 0, t_solve_grid = 0, t_chol_var = -1;
+  int t_eloc_grid = 0, t_gram_splits = 0, t_solve_grid = 0, t_chol_var = -1, t_chol_subst = -1;
   double t_ms[3] = {0, 0, 0}, t_ms_default[3] = {0, 0, 0};
   int64_t cur_ns = 0;  // sample count of the step being issued
   // batched steps: order this context's cooperative solve after another's
@@ -509,6 +509,10 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     ir.status = status;
     ir.need_fp64 = need;
     ir.maxit = 12;
+    // large systems: block substitution instead of the explicit inverse
+    // (measured at n = 4096: the inversion levels took 9 of 16.5 ms)
+    ir.subst = tuned(c) && c->t_chol_subst >= 0 ? c->t_chol_subst : (R >= 2048 ? 1 : 0);
+    ir.dv = ir.dpart;
     const size_t smem = chol_ir_smem(R);
     // tiles per warp pay off once n is large (measured: 16.5 vs 19.8 ms at
     // n = 4096, 1.71 vs 0.93 ms at n = 1024)
@@ -997,7 +1001,7 @@ nqs_status nqs_minsr_step(nqs_ctx *c, double *theta, double *mom, const nqs_step
 namespace {
 
 struct Tuned {
-  int eloc_grid, gram_splits, solve_grid, chol_var;
+  int eloc_grid, gram_splits, solve_grid, chol_var, chol_subst;
   double ms[3], ms_default[3];
 };
 std::mutex g_tune_mu;
@@ -1078,7 +1082,7 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
   CU(cudaStreamSynchronize(st));
   c->tuned_ns = ns;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
-  c->t_chol_var = -1;
+  c->t_chol_var = c->t_chol_subst = -1;
   const int reps = 2;
   auto none = [] { return NQS_OK; };
   uint8_t *spins = W<uint8_t>(c, c->off.spins);
@@ -1124,33 +1128,43 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
     c->t_gram_splits = pick;
     c->t_ms[1] = best;
   }
-  // (3) grid and tile mapping of the cooperative solve (T rebuilt before
-  //     every timed solve)
+  // (3) tile mapping, sweep form and grid of the cooperative solve (T
+  //     rebuilt before every timed solve)
   {
     const int G0 = c->rd.sm_count;
-    std::vector<int> cand;
-    for (int d : {1, 2, 4, 8}) uniq_push(cand, G0 / d);
-    const int var0 = R >= 2048 ? 1 : 0;
-    double best = 1e300;
-    int pick = G0, pvar = var0;
     double *Tm = W<double>(c, c->off.T);
-    for (int var : {0, 1}) {
-      if (!f32(c) && var == 1) continue;  // the FP64 path has one variant
-      for (int g : cand) {
-        c->t_solve_grid = g;
+    auto time_solve = [&](double *ms) {
+      return best_ms(st, reps, [&] { return regram<T>(c, ns, *hp, tstats, st); },
+                     [&] {
+                       return chol_solve(c, Tm, R, W<double>(c, c->off.eps),
+                                         W<double>(c, c->off.x), W<int32_t>(c, c->off.sstat), st);
+                     }, ms);
+    };
+    const int var0 = R >= 2048 ? 1 : 0, sub0 = R >= 2048 ? 1 : 0;
+    double best = 1e300;
+    int pvar = var0, psub = sub0, pick = G0;
+    c->t_solve_grid = G0;
+    for (int var : {0, 1})
+      for (int sub : {0, 1}) {
+        if (!f32(c) && (var != var0 || sub != sub0)) continue;  // FP64 path: one form
         c->t_chol_var = var;
+        c->t_chol_subst = sub;
         double ms = 0;
-        ST(best_ms(st, reps, [&] { return regram<T>(c, ns, *hp, tstats, st); },
-                   [&] {
-                     return chol_solve(c, Tm, R, W<double>(c, c->off.eps), W<double>(c, c->off.x),
-                                       W<int32_t>(c, c->off.sstat), st);
-                   }, &ms));
-        if (g == G0 && var == var0) c->t_ms_default[2] = ms;
-        if (ms < best) { best = ms; pick = g; pvar = var; }
+        ST(time_solve(&ms));
+        if (var == var0 && sub == sub0) c->t_ms_default[2] = ms;
+        if (ms < best) { best = ms; pvar = var; psub = sub; }
       }
+    c->t_chol_var = pvar;
+    c->t_chol_subst = psub;
+    for (int d : {2, 4, 8}) {
+      const int g = G0 / d;
+      if (g < 1) continue;
+      c->t_solve_grid = g;
+      double ms = 0;
+      ST(time_solve(&ms));
+      if (ms < best) { best = ms; pick = g; }
     }
     c->t_solve_grid = pick;
-    c->t_chol_var = pvar;
     c->t_ms[2] = best;
   }
   return NQS_OK;
@@ -1182,6 +1196,7 @@ nqs_status nqs_autotune(nqs_ctx *c, const double *theta, const nqs_step_hparams 
       c->tuned_ns = hp->n_samples;
       c->t_eloc_grid = t.eloc_grid; c->t_gram_splits = t.gram_splits; c->t_solve_grid = t.solve_grid;
       c->t_chol_var = t.chol_var;
+      c->t_chol_subst = t.chol_subst;
       std::memcpy(c->t_ms, t.ms, sizeof t.ms);
       std::memcpy(c->t_ms_default, t.ms_default, sizeof t.ms_default);
       return NQS_OK;
@@ -1195,7 +1210,8 @@ nqs_status nqs_autotune(nqs_ctx *c, const double *theta, const nqs_step_hparams 
     c->tuned_ns = 0;
     return s;
   }
-  Tuned t{c->t_eloc_grid, c->t_gram_splits, c->t_solve_grid, c->t_chol_var, {}, {}};
+  Tuned t{c->t_eloc_grid, c->t_gram_splits, c->t_solve_grid, c->t_chol_var, c->t_chol_subst,
+          {}, {}};
   std::memcpy(t.ms, c->t_ms, sizeof t.ms);
   std::memcpy(t.ms_default, c->t_ms_default, sizeof t.ms_default);
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1210,6 +1226,7 @@ nqs_status nqs_get_tuning(const nqs_ctx *c, nqs_tuning *out) {
   out->gram_splits = c->t_gram_splits;
   out->solve_grid = c->t_solve_grid;
   out->solve_tiles_per_warp = c->t_chol_var;
+  out->solve_substitution = c->t_chol_subst;
   for (int i = 0; i < 3; ++i) { out->ms[i] = c->t_ms[i]; out->ms_default[i] = c->t_ms_default[i]; }
   return NQS_OK;
 }
@@ -1219,7 +1236,7 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   drop_graph(c);
   c->tuned_ns = 0;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
-  c->t_chol_var = -1;
+  c->t_chol_var = c->t_chol_subst = -1;
   return NQS_OK;
 }
 

@@ -59,6 +59,35 @@ __device__ __forceinline__ void mm_acc(const T *__restrict__ At, int lda, int r0
   }
 }
 
+// Shared-memory state arrays are unit-major, [a][r] for R rows, with the row
+// index XOR-swizzled by the unit's lane group (a / UT) in steps of RT rows:
+// the unit-group lanes of a warp that store or load the same rows of
+// different units then fall in different banks, while every thread's RT
+// consecutive rows stay contiguous for vector loads.
+template <int R, int RT, int UT>
+__device__ __forceinline__ int ssw(int a, int r) {
+  static_assert((R & (R - 1)) == 0, "R is a power of two");
+  constexpr int G = (R / RT) < 8 ? (R / RT) : 8;
+  return a * R + (r ^ (((a / UT) & (G - 1)) * RT));
+}
+
+// mm_acc with the A operand in the swizzled [k][r] layout.
+template <typename T, int RT, int CT, int R, int UT>
+__device__ __forceinline__ void mm_acc_s(const T *__restrict__ At, int r0,
+                                         const T *__restrict__ B, int ldb, int c0,
+                                         int K, T (&acc)[RT][CT]) {
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    T a[RT], b[CT];
+    load_run<T, RT>(At + ssw<R, RT, UT>(k, r0), a);
+    load_run<T, CT>(B + k * ldb + c0, b);
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+      for (int j = 0; j < CT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
 template <typename T, int UG>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -228,7 +257,7 @@ k_forward(const FwdArgs<T> A) {
         if (A.ck > 0) v = A.hcache[((int64_t)s * A.nck + (krec / A.ck - 1)) * DH + a];
         else v = A.hcache[((int64_t)s * N + (krec - 1)) * DH + a];
       }
-      sh0[a * R + r] = v;
+      sh0[ssw<R, RT, UT>(a, r)] = v;
       if (seg && s >= 0) A.hseg[((int64_t)s * (A.ck + 1)) * DH + a] = v;
     }
     __syncthreads();
@@ -268,7 +297,7 @@ k_forward(const FwdArgs<T> A) {
               else
                 v = A.hcache[((int64_t)s * N + ver) * DH + a];
             }
-            shv[a * R + r] = v;
+            shv[ssw<R, RT, UT>(a, r)] = v;
           }
         }
         __syncthreads();
@@ -277,12 +306,12 @@ k_forward(const FwdArgs<T> A) {
         for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int j2 = 0; j2 < UT; ++j2) acc1[i][j2] = T(0);
-        if (hor_ok) mm_acc<T, RT, UT>(hcur, R, r0, sU12T, DH, a0, DH, acc1);
-        if (ver >= 0) mm_acc<T, RT, UT>(shv, R, r0, sU12T + DH * DH, DH, a0, DH, acc1);
+        if (hor_ok) mm_acc_s<T, RT, UT, R, UT>(hcur, r0, sU12T, DH, a0, DH, acc1);
+        if (ver >= 0) mm_acc_s<T, RT, UT, R, UT>(shv, r0, sU12T + DH * DH, DH, a0, DH, acc1);
 #pragma unroll
         for (int i = 0; i < RT; ++i)
 #pragma unroll
-          for (int uu = 0; uu < UT; ++uu) shp[(a0 + uu) * R + r0 + i] = acc1[i][uu];
+          for (int uu = 0; uu < UT; ++uu) shp[ssw<R, RT, UT>(a0 + uu, r0 + i)] = acc1[i][uu];
         __syncthreads();
         Ag = shp;
       }
@@ -291,7 +320,7 @@ k_forward(const FwdArgs<T> A) {
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int j2 = 0; j2 < 3 * UT; ++j2) acc[i][j2] = T(0);
-      if (DIM == 2 || k > 0) mm_acc<T, RT, 3 * UT>(Ag, R, r0, sWgT, C3, 3 * a0, DH, acc);
+      if (DIM == 2 || k > 0) mm_acc_s<T, RT, 3 * UT, R, UT>(Ag, r0, sWgT, C3, 3 * a0, DH, acc);
 
       // epilogue: GRU cell (App. A), partial heads, then the row's head on
       // lane ug == i (log-softmax, mask, draw, accumulate)
@@ -326,9 +355,9 @@ k_forward(const FwdArgs<T> A) {
           }
           const T u = sigm(au), rr = sigm(ar);
           const T c = tnh(rr * gg + ai);
-          const T hp = (DIM == 2 || k > 0) ? Ag[a * R + r] : T(0);
+          const T hp = (DIM == 2 || k > 0) ? Ag[ssw<R, RT, UT>(a, r)] : T(0);
           const T hn = (T(1) - u) * hp + u * c;
-          hnxt[a * R + r] = hn;
+          hnxt[ssw<R, RT, UT>(a, r)] = hn;
           if (s >= 0) {
             if (seg) {
               A.hseg[((int64_t)s * (A.ck + 1) + (k - krec + 1)) * DH + a] = hn;

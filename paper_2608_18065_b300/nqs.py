@@ -71,6 +71,7 @@ TUNE_FORCE = 1
 class Tuning(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("eloc_grid", C.c_int), ("gram_splits", C.c_int),
                 ("solve_grid", C.c_int), ("solve_tiles_per_warp", C.c_int),
+                ("solve_substitution", C.c_int), ("reserved", C.c_int),
                 ("ms", C.c_double * 3), ("ms_default", C.c_double * 3)]
 
 
@@ -285,6 +286,7 @@ class Context:
         return {"n_samples": t.n_samples, "eloc_grid": t.eloc_grid,
                 "gram_splits": t.gram_splits, "solve_grid": t.solve_grid,
                 "solve_tiles_per_warp": t.solve_tiles_per_warp,
+                "solve_substitution": t.solve_substitution,
                 "ms": dict(zip(names, list(t.ms))),
                 "ms_default": dict(zip(names, list(t.ms_default)))}
 

@@ -290,3 +290,26 @@ def test_large_hidden_size_step_fp64():
     assert np.array_equal(outs["spins"].cpu().numpy(), b["spins"])
     assert rel_err(outs["dtheta"].cpu().numpy(), b["dtheta"]) < 1e-9
     assert rel_err(thd.cpu().numpy(), th1) < 1e-9
+
+
+@pytest.mark.parametrize("R", [2090, 2304])
+def test_regularized_solve_block_substitution(R):
+    """Mixed context, R >= 2048: refinement sweeps by block substitution with
+    the inverted 32 x 32 diagonal blocks (ragged last block for R = 2090)
+    reach the FP64 solution; an indefinite matrix still reports NOT_SPD."""
+    model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
+    c = ctx(model, ham, "mixed", R)
+    rng = np.random.default_rng(R)
+    M = rng.standard_normal((R, R + 5))
+    T = M @ M.T / R
+    b = rng.standard_normal(R)
+    lam = 1e-2
+    x, st = c.regularized_solve(torch.tensor(T, device="cuda"), lam, torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 0
+    A = T + lam * np.eye(R)
+    xr = np.linalg.solve(A, b)
+    kappa = np.linalg.cond(A)
+    xg = x.cpu().numpy()
+    assert rel_err(xg, xr) < max(1e-10, 100 * kappa * 2.2e-16)
+    berr = np.max(np.abs(A @ xg - b)) / (np.max(np.abs(A).sum(1)) * np.max(np.abs(xg)))
+    assert berr < 100 * np.sqrt(R) * 1.11e-16
