@@ -380,8 +380,8 @@ def run_ours(args):
 
     # replica r: its own Philox key (seed + r), same theta_0
     import copy
-    hp = copy.copy(hp)
-    hp.seed = hp.seed + rank
+    from paper_2608_18065_b300.replicas import aggregate_rate, max_over_ranks, replica_hparams
+    hp = replica_hparams(hp, rank)
     ctx = nqs.Context(w.model, w.ham, w.precision, hp.ns, device=dev)
     ctx.use_graph(not args.no_graph)
     th0 = init_theta(w.model, w.theta_seed)
@@ -416,13 +416,9 @@ def run_ours(args):
     per_step = (ctx.launch_count() - lt0) / min(K, 10)
     launches = int(round(per_step * K))
     stage_ms, nt = ctx.timing_end()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        ms = float(t_.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     st = nqs.decode_stats(stats)
-    value = world * K / (ms / 1000.0)
+    value = aggregate_rate(world, K, ms)
     ms_step = ms / K
 
     # Gram throughput (symmetric algorithmic count R(R+1)Np)
@@ -466,12 +462,8 @@ def run_ours(args):
             st_h.copy_(stats, non_blocking=True)
         a1.record()
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if world > 1:
-            t_ = torch.tensor([ems], device=dev)
-            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-            ems = float(t_.item())
-        e2e = {"value": world * K / (ems / 1000.0), "unit": UNIT,
+        ems = max_over_ranks(a0.elapsed_time(a1), dist, dev)
+        e2e = {"value": aggregate_rate(world, K, ems), "unit": UNIT,
                "h2d_bytes_per_step": 2 * ctx.np * 8,
                "d2h_bytes_per_step": 2 * ctx.np * 8 + stats.numel() * 8}
 
@@ -563,11 +555,8 @@ def run_batched(args):
     th0 = [init_theta(w.model, w.theta_seed) for w in insts]
     thd = [torch.tensor(t, device=dev) for t in th0]
     mod = [torch.zeros_like(t) for t in thd]
-    hps = []
-    for w in insts:
-        h = copy.copy(w.hp)
-        h.seed = h.seed + rank
-        hps.append(h)
+    from paper_2608_18065_b300.replicas import aggregate_rate, max_over_ranks, replica_hparams
+    hps = [replica_hparams(w.hp, rank) for w in insts]
     b = nqs.Batch(ctxs)
     b.use_graph(not args.no_graph)
     t0 = time.perf_counter()
@@ -591,12 +580,8 @@ def run_batched(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        ms = float(t_.item())
-    value = world * K / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    value = aggregate_rate(world, K, ms)
     st = [nqs.decode_stats(stats[i]) for i in range(n)]
 
     # per-instance stage times: every instance alone, eager, one step
@@ -659,9 +644,9 @@ def run_batched(args):
             st_h.copy_(stats, non_blocking=True)
         a1.record()
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
+        ems = max_over_ranks(a0.elapsed_time(a1), dist, dev)
         nbytes = sum(t.numel() * 8 for t in thd) * 2
-        e2e = {"value": world * K / (ems / 1000.0), "unit": "batched steps/s",
+        e2e = {"value": aggregate_rate(world, K, ems), "unit": "batched steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + stats.numel() * 8}
 
     # the same instances one at a time on the plain FP64 GPU path
