@@ -80,12 +80,21 @@ typedef struct {
   int64_t step_index;         /* t, for eta_t = eta0/(1+t/decay_T) */
   uint64_t seed;              /* Philox key */
   int64_t ns;                 /* number of samples */
+  double lm_omega;            /* > 1: Levenberg-Marquardt damping (App. G) */
 } or_hparams;
 
 typedef struct {
   double E_re, E_im, var, vscore, lambda, normT, eta_eff, tau_norm;
   int status; /* 0 ok, 4 non-finite, 5 not SPD */
+  double rho;          /* Levenberg-Marquardt gain ratio (0 when off) */
+  double lambda_next;  /* damping for the next step (lambda when off) */
 } or_stats;
+
+/* Philox key of the samples that estimate E(theta + delta theta) for the
+ * damping ratio: the step's key plus this odd constant (2^64 / golden
+ * ratio), same counter layout, so they are independent of the step's own
+ * samples. */
+#define OR_LM_KEY_OFFSET 0x9E3779B97F4A7C15ULL
 
 /* ------------------------------------------------------- Philox4x32-10 */
 
@@ -784,6 +793,39 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
   for (int64_t k = 0; k < np && finite; ++k) finite = isfinite(dth[k]);
   if (status == 0 && !finite) status = 4;
   st->status = status;
+  /* Levenberg-Marquardt damping (App. G): gain ratio of the step against
+   * its quadratic model.  The model's predicted decrease for the step
+   * delta theta (theta -> theta - delta theta) is
+   *   g^T dtheta - 1/2 dtheta^T S dtheta,  g = O'^T eps', S = O'^T O',
+   * and with dtheta = eta O'^T x, T x = tau this is
+   *   eta eps'^T tau - 1/2 eta^2 ||tau||^2
+   * (= eta* eps'^T tau - 1/2 eta_t^2 in the trust-region mode, App. G).
+   * The actual decrease uses E at theta - delta theta, estimated from Ns
+   * fresh samples (key seed + OR_LM_KEY_OFFSET, counter step t). */
+  st->rho = 0.0;
+  st->lambda_next = lam;
+  if (hp->lm_omega > 1.0) {
+    double et = 0.0;
+    for (int64_t i = 0; i < R; ++i) et += eps[i] * (eps[i] - lam * x[i]);
+    const double pred = eta * et - 0.5 * eta * eta * tn * tn;
+    double *th2 = (double *)malloc(sizeof(double) * (size_t)np);
+    uint8_t *sp2 = (uint8_t *)malloc((size_t)(ns * N));
+    double *lp2 = (double *)malloc(sizeof(double) * (size_t)(2 * ns));
+    double *el2 = (double *)malloc(sizeof(double) * (size_t)(2 * ns));
+    if (!th2 || !sp2 || !lp2 || !el2) return -2;
+    for (int64_t k = 0; k < np; ++k) th2[k] = status == 0 ? theta[k] - dth[k] : theta[k];
+    or_sample(m, th2, ns, hp->seed + OR_LM_KEY_OFFSET, (uint64_t)hp->step_index, sp2, lp2);
+    or_local_energy(m, H, th2, sp2, ns, el2);
+    double E2 = 0.0;
+    for (int64_t s = 0; s < ns; ++s) E2 += el2[2 * s];
+    E2 /= (double)ns;
+    const double rho = (Er - E2) / pred;
+    st->rho = rho;
+    /* a rejected step or an undefined ratio counts as a poor step */
+    if (status != 0 || !(rho >= 0.25)) st->lambda_next = hp->lm_omega * lam;
+    else if (rho > 0.75) st->lambda_next = lam / hp->lm_omega;
+    free(th2); free(sp2); free(lp2); free(el2);
+  }
   /* lines 8-9: momentum and update, only for an accepted step */
   if (status == 0) {
     for (int64_t k = 0; k < np; ++k) {

@@ -40,14 +40,14 @@ class OrHParams(C.Structure):
                 ("lam", C.c_double), ("lambda_coeff", C.c_double),
                 ("lambda_pow", C.c_double), ("lambda_mode", C.c_int),
                 ("trust_region", C.c_int), ("step_index", C.c_int64),
-                ("seed", C.c_uint64), ("ns", C.c_int64)]
+                ("seed", C.c_uint64), ("ns", C.c_int64), ("lm_omega", C.c_double)]
 
 
 class OrStats(C.Structure):
     _fields_ = [("E_re", C.c_double), ("E_im", C.c_double), ("var", C.c_double),
                 ("vscore", C.c_double), ("lam", C.c_double), ("normT", C.c_double),
                 ("eta_eff", C.c_double), ("tau_norm", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("rho", C.c_double), ("lambda_next", C.c_double)]
 
 
 class OrStepOut(C.Structure):
@@ -238,7 +238,7 @@ def cholesky_solve(A, b):
 def hparams_struct(hp, step_index) -> OrHParams:
     return OrHParams(hp.eta0, hp.decay_T, hp.mu, hp.lam, hp.lambda_coeff,
                      hp.lambda_pow, hp.lambda_mode, hp.trust_region,
-                     step_index, hp.seed, hp.ns)
+                     step_index, hp.seed, hp.ns, getattr(hp, "lm_omega", 0.0))
 
 
 def minsr_step(spec, hamspec, theta, mom, hp, step_index, want=()):

@@ -52,6 +52,7 @@ class HParams:
     trust_region: int = 0
     seed: int = 42
     ns: int = 128
+    lm_omega: float = 0.0         # > 1: Levenberg-Marquardt damping factor (App. G)
 
 
 def param_blocks(spec: ModelSpec) -> List[Tuple[str, int, int, int]]:

@@ -141,3 +141,50 @@ def test_small_tfim_training_approaches_exact_energy():
     late = np.mean(Es[-10:])
     assert (late - E0) / abs(E0) < 2e-3
     assert late > E0 - 5 * np.mean(errs[-10:]) / np.sqrt(10)
+
+
+LM_KEY_OFFSET = 0x9E3779B97F4A7C15
+LM_CASES = [
+    (ModelSpec(1, 8, 1, 4), HamSpec("tfim"),
+     HParams(0.5, 1e3, 0.7, lam=1e-3, ns=24, lm_omega=1.5)),
+    (ModelSpec(2, 4, 3, 3, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.5),
+     HParams(0.1, 1e4, 0.1, lam=0.1, trust_region=1, ns=20, lm_omega=1.5)),
+]
+
+
+@pytest.mark.parametrize("spec,ham,hp", LM_CASES, ids=["tfim8", "j1j2_4x3_tr"])
+def test_levenberg_marquardt_gain_ratio(spec, ham, hp):
+    """App. G: rho = (E(theta) - E(theta - dtheta)) / predicted decrease, the
+    prediction taken from the quadratic model with the gradient g = O'^T eps'
+    and the metric S = O'^T O' built here from the oracle's own Jacobian (not
+    from the simplified eta eps'^T tau form the step uses); E(theta - dtheta)
+    from fresh samples of the shifted key; lambda grows by omega below 1/4 and
+    shrinks above 3/4."""
+    th = init_theta(spec, 21)
+    t = 3
+    th1, _, st, b = O.minsr_step(spec, ham, th, np.zeros_like(th), hp, t, want=WANT)
+    assert st["status"] == 0
+    A = _centred(spec, th, b["spins"])
+    d = b["dtheta"]
+    g = A.T @ b["eps"]
+    pred = g @ d - 0.5 * np.sum((A @ d) ** 2)
+    th2 = th - d
+    sp2, _ = O.sample(spec, th2, hp.ns, (hp.seed + LM_KEY_OFFSET) % 2**64, t)
+    E2 = O.local_energy(spec, ham, th2, sp2).real.mean()
+    rho = (st["E_re"] - E2) / pred
+    assert st["rho"] == pytest.approx(rho, rel=1e-9)
+    if hp.trust_region:
+        # App. G's closed form: dtheta^T S dtheta = eta_t^2 on the trust region
+        eta_t = hp.eta0 / (1 + t / hp.decay_T)
+        tau = b["eps"] - st["lam"] * b["x"]
+        assert pred == pytest.approx(st["eta_eff"] * b["eps"] @ tau - 0.5 * eta_t ** 2, rel=1e-9)
+    lam = st["lam"]
+    want_next = lam * 1.5 if rho < 0.25 else (lam / 1.5 if rho > 0.75 else lam)
+    assert st["lambda_next"] == pytest.approx(want_next, rel=1e-15)
+
+
+def test_levenberg_marquardt_off():
+    spec, ham, hp = CASES[0]
+    th = init_theta(spec, 21)
+    _, _, st, _ = O.minsr_step(spec, ham, th, np.zeros_like(th), hp, 0)
+    assert st["rho"] == 0.0 and st["lambda_next"] == st["lam"]
