@@ -108,7 +108,11 @@ typedef struct {
   int32_t status;      /* nqs_status of the device-side checks */
   int32_t solve_fp64;  /* 1: x came from the FP64 Cholesky factorisation (FP64
                           context, or fallback of the mixed context); 0: from
-                          FP64 iterative refinement on an FP32 factor */
+                          FP64 iterative refinement on an FP32 factor; 2: T
+                          rebuilt in FP64 and factored in FP64 (mixed context,
+                          lambda below the tensor-core T's rounding) */
+  double rho;          /* Levenberg-Marquardt gain ratio (0 when damping is off) */
+  double lambda_next;  /* damping of the next step (= lambda when off) */
 } nqs_step_stats;
 
 /* Optional device outputs of nqs_minsr_step_ex (any pointer may be NULL). */
@@ -242,6 +246,27 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
                              const nqs_step_hparams *hp,
                              nqs_step_stats *dev_stats,
                              const nqs_step_outputs *out, void *stream);
+
+/* ------------------------------------------------ adaptive damping (LM) */
+
+/* Levenberg-Marquardt damping (App. G).  omega > 1 switches it on with
+ * lambda0 as the damping of the next step; omega <= 1 switches it off (the
+ * steps use nqs_step_hparams' lambda again).  While on, every step:
+ *  - uses the damping held on the device (hp->lambda and lambda_mode are
+ *    ignored) and reports it in stats.lambda;
+ *  - after the update, estimates E at theta - delta theta (the SR step
+ *    itself, without momentum) from n_samples fresh samples drawn with the
+ *    Philox key seed + 0x9E3779B97F4A7C15 and the step's counter;
+ *  - forms rho = (E - E(theta - delta theta)) / (eta eps'^T tau -
+ *    1/2 eta^2 ||tau||^2), the decrease predicted by the quadratic model
+ *    with metric S (App. G; eta* eps'^T tau - 1/2 eta_t^2 in the trust-region
+ *    mode), and multiplies the damping by omega if rho < 1/4 (or the step
+ *    was rejected), divides it by omega if rho > 3/4 (stats.rho,
+ *    stats.lambda_next).
+ * The extra sampling and local-energy pass roughly doubles the forward
+ * work of a step.  Synchronous (copies lambda0 to the device); call it
+ * outside stream capture.  Invalidates the context's captured graph. */
+nqs_status nqs_set_damping(nqs_ctx *ctx, double omega, double lambda0);
 
 /* ------------------------------------------------------------ autotuner */
 

@@ -23,7 +23,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, hseg, carry, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, hseg, carry, dlm, total;
 };
 
 }  // namespace
@@ -48,6 +48,8 @@ struct nqs_ctx {
   // hidden-state checkpoints (1D): stride ck (0 = every state cached), nck
   // checkpoint slots, nseg segments of the reverse sweep
   int ck = 0, nck = 0, nseg = 1;
+  // Levenberg-Marquardt damping factor (0: off); the damping lives on the device
+  double lm_omega = 0.0;
   WsOff off{};
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -183,6 +185,7 @@ void carve(nqs_ctx *c) {
   o.gcache = take(ns * (c->ck ? c->ck : N) * c->gw * es);
   o.hseg = take(c->ck ? ns * (c->ck + 1) * dh * es : 0);
   o.carry = take(c->ck ? R * dh * es : 0);
+  o.dlm = take(64);
   o.L32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Li32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
@@ -460,22 +463,74 @@ __global__ void k_frob_part(const double *__restrict__ T, int64_t n2, double *pa
   if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
+// lam_dev (optional): the damping held on the device (Levenberg-Marquardt
+// mode) instead of mode / lam_c.
 __global__ void k_lambda_finish(double *T, int64_t R, const double *part, int nparts, int mode,
                                 double lam_c, double coeff, double pw, nqs_step_stats *st,
-                                const int32_t *gate = nullptr) {
+                                const int32_t *gate = nullptr, const double *lam_dev = nullptr) {
   if (gate && *gate == 0) return;
   __shared__ double lam_s;
   if (threadIdx.x == 0) {
     double acc = 0.0;
     for (int i = 0; i < nparts; ++i) acc += part[i];
     const double nT = sqrt(acc);
-    const double lam = mode == 1 ? coeff * pow(nT, pw) : lam_c;
+    const double lam = lam_dev ? *lam_dev : (mode == 1 ? coeff * pow(nT, pw) : lam_c);
     st->normT = nT;
     st->lambda = lam;
+    st->rho = 0.0;
+    st->lambda_next = lam;
     lam_s = lam;
   }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < R; i += blockDim.x) T[i * R + i] += lam_s;
+}
+
+// Philox key offset of the samples that estimate E(theta - delta theta) for
+// the damping ratio (the step's key plus 2^64 / golden ratio).
+constexpr uint64_t LM_KEY_OFFSET = 0x9E3779B97F4A7C15ull;
+
+// The point of the damping ratio: theta - delta theta before momentum, i.e.
+// theta' + m' - delta theta after an accepted update; theta if rejected.
+__global__ void k_lm_point(const double *__restrict__ theta, const double *__restrict__ mom,
+                           const double *__restrict__ dth, int64_t np, const nqs_step_stats *st,
+                           double *out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  out[k] = st->status == NQS_OK ? theta[k] + mom[k] - dth[k] : theta[k];
+}
+
+// Gain ratio and next damping (App. G): rho = (E - E2) / (eta eps'^T tau -
+// 1/2 eta^2 ||tau||^2) with tau = eps' - lambda x; one block.
+__global__ void k_lm_update(const double *__restrict__ eloc2, int64_t ns,
+                            const double *__restrict__ eps, const double *__restrict__ x, int64_t R,
+                            nqs_step_stats *st, double *lam_dev, double omega) {
+  __shared__ double s1[1024], s2[1024];
+  const double lam = st->lambda;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) a += eloc2[2 * i];
+  for (int64_t i = threadIdx.x; i < R; i += blockDim.x) b += eps[i] * (eps[i] - lam * x[i]);
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double E2 = s1[0] / (double)ns;
+    const double eta = st->eta_eff, tn = st->tau_norm;
+    const double pred = eta * s2[0] - 0.5 * eta * eta * tn * tn;
+    const double rho = (st->E_re - E2) / pred;
+    double ln = lam;
+    if (st->status != NQS_OK || !(rho >= 0.25)) ln = omega * lam;
+    else if (rho > 0.75) ln = lam / omega;
+    st->rho = rho;
+    st->lambda_next = ln;
+    *lam_dev = ln;
+  }
 }
 
 // x = (T + lambda I)^{-1} b for the shifted T.  FP64 context: FP64 Cholesky
@@ -557,7 +612,8 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     k_lambda_finish<<<1, 1024, 0, st>>>(T, R, W<double>(c, c->off.frob), nparts,
                                         retry->hp->lambda_mode, retry->hp->lambda,
                                         retry->hp->lambda_coeff, retry->hp->lambda_pow,
-                                        retry->stats, rflag);
+                                        retry->stats, rflag,
+                                        c->lm_omega > 1.0 ? W<double>(c, c->off.dlm) : nullptr);
     CU(cudaMemsetAsync(bar, 0, 4, st));
     a.gate = rflag;
     c->launches += 5;
@@ -645,7 +701,9 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     c->launches += 2;
     k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
     k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts, hp->lambda_mode,
-                                        hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats);
+                                        hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats,
+                                        nullptr,
+                                        c->lm_omega > 1.0 ? W<double>(c, c->off.dlm) : nullptr);
     CU(cudaGetLastError());
   }
   // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
@@ -675,11 +733,6 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
                                                          np, hp->mu, stats);
     CU(cudaGetLastError());
   }
-  k_inc_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep));  // next step's counter
-  c->launches += 1;
-  CU(cudaGetLastError());
-  mark(c, 14, st);
-  if (c->tstep < c->tmax) ++c->tstep;
   if (out) {
     if (out->spins) CU(cudaMemcpyAsync(out->spins, spins, ns * N, cudaMemcpyDeviceToDevice, st));
     if (out->logpsi) CU(cudaMemcpyAsync(out->logpsi, logpsi, ns * 16, cudaMemcpyDeviceToDevice, st));
@@ -689,6 +742,34 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     if (out->dtheta)
       CU(cudaMemcpyAsync(out->dtheta, W<double>(c, c->off.dth), np * 8, cudaMemcpyDeviceToDevice, st));
   }
+  if (c->lm_omega > 1.0) {
+    // damping ratio (App. G): E at theta - delta theta from fresh samples;
+    // the pass reuses the step's caches, so it runs after the outputs are
+    // copied, and it records no stage events
+    const int saved_tmax = c->tmax;
+    c->tmax = c->tstep;
+    double *tth = W<double>(c, c->off.tth);
+    k_lm_point<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(theta, mom, W<double>(c, c->off.dth),
+                                                            np, stats, tth);
+    CU(cudaGetLastError());
+    ST(pack_theta<T>(c, tth, st));
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = ns; a.seed = hp->seed + LM_KEY_OFFSET; a.step = (uint64_t)hp->step_index;
+    a.step_dev = W<int64_t>(c, c->off.dstep);
+    a.spins = spins; a.logpsi = logpsi;
+    c->launches += 3;
+    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+    ST(eloc_T<T>(c, ns, spins, eloc, st));
+    k_lm_update<<<1, 1024, 0, st>>>(eloc, ns, eps, x, R, stats, W<double>(c, c->off.dlm),
+                                    c->lm_omega);
+    CU(cudaGetLastError());
+    c->tmax = saved_tmax;
+  }
+  k_inc_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep));  // next step's counter
+  c->launches += 1;
+  CU(cudaGetLastError());
+  mark(c, 14, st);
+  if (c->tstep < c->tmax) ++c->tstep;
   return NQS_OK;
 }
 
@@ -1237,6 +1318,20 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   c->tuned_ns = 0;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
   c->t_chol_var = c->t_chol_subst = -1;
+  return NQS_OK;
+}
+
+nqs_status nqs_set_damping(nqs_ctx *c, double omega, double lambda0) {
+  if (!c || !(omega == omega) || !(lambda0 == lambda0)) return NQS_ERR_ARG;
+  if (omega > 1.0) {
+    if (!(lambda0 > 0.0) || !std::isfinite(omega) || !std::isfinite(lambda0)) return NQS_ERR_ARG;
+    ST(need_ws(c));
+    CU(cudaMemcpy(c->ws + c->off.dlm, &lambda0, sizeof(double), cudaMemcpyHostToDevice));
+    c->lm_omega = omega;
+  } else {
+    c->lm_omega = 0.0;
+  }
+  drop_graph(c);
   return NQS_OK;
 }
 

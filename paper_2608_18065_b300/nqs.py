@@ -42,7 +42,7 @@ class StepHParams(C.Structure):
 
 
 STATS_FIELDS = ["E_re", "E_im", "var", "vscore", "lam", "normT", "eta_eff", "tau_norm"]
-STATS_DOUBLES = 9  # 8 doubles + (status, pad) as int32 pair
+STATS_DOUBLES = 11  # 8 doubles, (status, solve_fp64) as an int32 pair, rho, lambda_next
 
 
 class Options(C.Structure):
@@ -64,6 +64,7 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_destroy", "nqs_minsr_step_batched", "nqs_batch_set_graph",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
+           "nqs_set_damping",
            "nqs_stage_name", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -240,6 +241,10 @@ class Context:
                                            _ptr(stats), C.byref(o), _stream(stream)))
         return stats
 
+    def set_damping(self, omega, lambda0):
+        """Levenberg-Marquardt damping (App. G): omega > 1 on, else off."""
+        _check(lib().nqs_set_damping(self._h, C.c_double(omega), C.c_double(lambda0)))
+
     def use_graph(self, enable=True):
         _check(lib().nqs_set_graph(self._h, 1 if enable else 0))
 
@@ -381,6 +386,8 @@ def decode_stats(stats: torch.Tensor) -> dict:
     d = {k: float(v[i]) for i, k in enumerate(STATS_FIELDS)}
     d["status"] = int(v[8:9].view(torch.int32)[0])
     d["solve_fp64"] = int(v[8:9].view(torch.int32)[1])
+    d["rho"] = float(v[9])
+    d["lambda_next"] = float(v[10])
     return d
 
 
