@@ -46,12 +46,40 @@ constexpr int TMEM_COLS = 512;
 constexpr int ACC_STRIDE = 256;              // tensor-memory columns per slot
 constexpr int ATILE = TR * 64 * 2;           // one 128-byte-swizzle atom column of A (16 KB)
 constexpr int BTILE = NB * 64 * 2;           // one atom column of B (26 KB)
+// the augmented K = 16 block in the non-swizzled K-major layout: core
+// matrices of 8 rows x 16 bytes, the two K halves 128 bytes apart, 8-row
+// groups 256 bytes apart
+constexpr int XLBO = 128, XSBO = 256;
+constexpr int XTILE_B = (NB / 8) * XSBO;     // 6.5 KB
+constexpr int XTILE_A = (TR / 8) * XSBO;     // 4 KB
+constexpr int SLOT_BYTES = 2 * ATILE + XTILE_A;
+constexpr int HSTATE = TR * DH;              // FP32 states of one tile
 constexpr int XS = DH + 1;                   // padded stride of the W_in x + b_in table
-// B: [hi | lo] x [state atom | augmented atom];  A per slot: hi, lo, augmented
-constexpr size_t SMEM_BYTES = 1024 + 4 * (size_t)BTILE + 3 * SLOTS * (size_t)ATILE + 4 * 8 +
+// B: hi, lo (128-byte swizzle), augmented hi, lo; per slot A: hi, lo,
+// augmented; per slot the FP32 states; barriers and small tables
+constexpr size_t SMEM_BYTES = 1024 + 2 * (size_t)BTILE + 2 * (size_t)XTILE_B +
+                              SLOTS * (size_t)SLOT_BYTES + SLOTS * (size_t)HSTATE * 4 + 4 * 8 +
                               2 * 4 + sizeof(float) * (3 * XS + 4) + 64;
 static_assert(BTILE % 1024 == 0 && ATILE % 1024 == 0, "swizzle atoms stay 1024-aligned");
+static_assert((2 * BTILE + 2 * XTILE_B) % 1024 == 0 && SLOT_BYTES % 1024 == 0,
+              "the A atoms of every slot stay 1024-aligned");
 static_assert(SMEM_BYTES <= 227 * 1024, "fits one CTA per SM");
+
+// Byte offset of element k (< 16) of row r in the augmented block.
+__device__ __forceinline__ uint32_t xoff(int r, int k) {
+  return (uint32_t)(r >> 3) * XSBO + (uint32_t)(k >> 3) * XLBO + (uint32_t)(r & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+// Shared-memory matrix descriptor of a K-major bf16 tile without swizzle.
+__device__ __forceinline__ uint64_t noswz_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)(XLBO >> 4) << 16;             // leading byte offset: next core matrix in K
+  d |= (uint64_t)(XSBO >> 4) << 32;             // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                       // descriptor version (tcgen05)
+  return d;                                     // layout 0: no swizzle
+}
 
 constexpr uint16_t BF16_ONE = 0x3F80;
 
@@ -65,30 +93,34 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1) {
 __device__ __forceinline__ float sigm_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float tanh_f(float x) { return 2.0f * sigm_f(2.0f * x) - 1.0f; }
 
-// BF16 hi/lo planes of this thread's UH units of row `row`.
-__device__ __forceinline__ void write_planes(unsigned char *Ahi, unsigned char *Alo, int row,
-                                             int half, const float (&h)[UH]) {
+// BF16 hi/lo planes of units k0 .. k0 + 7 of row `row`.
+__device__ __forceinline__ void write_planes8(unsigned char *Ahi, unsigned char *Alo, int row,
+                                              int k0, const float (&h)[8]) {
+  uint32_t hp[4], lp[4];
 #pragma unroll
-  for (int c = 0; c < UH / 8; ++c) {
-    uint32_t hp[4], lp[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float x0 = h[8 * c + 2 * q], x1 = h[8 * c + 2 * q + 1];
-      hp[q] = pack_bf16x2(x0, x1);
-      const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
-      lp[q] = pack_bf16x2(x0 - h0, x1 - h1);
-    }
-    const uint32_t off = sw128_off(row, UH * half + 8 * c);
-    *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-    *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = h[2 * q], x1 = h[2 * q + 1];
+    hp[q] = pack_bf16x2(x0, x1);
+    const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
+    lp[q] = pack_bf16x2(x0 - h0, x1 - h1);
   }
+  const uint32_t off = sw128_off(row, k0);
+  *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+  *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+}
+
+// The FP32 state of a row lives in shared memory, 64 floats in 16 chunks of
+// 4; chunk c of row r sits at position c ^ (r mod 8) (within its half), so
+// the 8 rows a quarter-warp reads with one 16-byte load hit distinct banks.
+__device__ __forceinline__ float4 *hchunk(float *hrow, int row, int c) {
+  return reinterpret_cast<float4 *>(hrow) + (c ^ (row & 7));
 }
 
 // Augmented columns of row `row`: (1, [d == 0], [d == 1], 0 ...); d = 2: no input.
 __device__ __forceinline__ void write_aug(unsigned char *Aaug, int row, int d) {
   const uint32_t w0 = BF16_ONE | ((d == 0 ? (uint32_t)BF16_ONE : 0u) << 16);
   const uint32_t w1 = d == 1 ? (uint32_t)BF16_ONE : 0u;
-  *reinterpret_cast<uint4 *>(Aaug + sw128_off(row, 0)) = make_uint4(w0, w1, 0u, 0u);
+  *reinterpret_cast<uint4 *>(Aaug + xoff(row, 0)) = make_uint4(w0, w1, 0u, 0u);
 }
 
 // Named barrier of n threads whose result is the OR of pred over them.
@@ -108,7 +140,7 @@ __device__ __forceinline__ bool bar_any(int id, int n, bool pred) {
 // B atoms (hi, lo, augmented hi, augmented lo).
 __device__ __forceinline__ void issue_round(uint32_t d, uint32_t a0, uint32_t b0, uint32_t bar) {
   constexpr uint32_t idesc = idesc_bf16(TR, NB);
-  const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + ATILE), ax = sw128_desc(a0 + 2 * ATILE);
+  const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + ATILE), ax = noswz_desc(a0 + 2 * ATILE);
   const uint64_t bh = sw128_desc(b0), bl = sw128_desc(b0 + BTILE);
   tc_fence_after();
 #pragma unroll
@@ -119,27 +151,28 @@ __device__ __forceinline__ void issue_round(uint32_t d, uint32_t a0, uint32_t b0
     mma_bf16(d, al + adv, bh + adv, idesc, 1u);
   }
   // augmented block: exact in BF16, so two products suffice
-  mma_bf16(d, ax, sw128_desc(b0 + 2 * BTILE), idesc, 1u);
-  mma_bf16(d, ax, sw128_desc(b0 + 3 * BTILE), idesc, 1u);
+  mma_bf16(d, ax, noswz_desc(b0 + 2 * BTILE), idesc, 1u);
+  mma_bf16(d, ax, noswz_desc(b0 + 2 * BTILE + XTILE_B), idesc, 1u);
   mma_commit(bar);
 }
 
-__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, int n, int k,
+// w split into BF16 hi + lo at byte offset off of the two planes.
+__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, uint32_t off,
                                           float w) {
   const __nv_bfloat16 h = __float2bfloat16_rn(w);
-  *reinterpret_cast<__nv_bfloat16 *>(hi + sw128_off(n, k)) = h;
-  *reinterpret_cast<__nv_bfloat16 *>(lo + sw128_off(n, k)) =
-      __float2bfloat16_rn(w - __bfloat162float(h));
+  *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
+  *reinterpret_cast<__nv_bfloat16 *>(lo + off) = __float2bfloat16_rn(w - __bfloat162float(h));
 }
 
 __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(eraw) + 1023) & ~uintptr_t(1023));
-  unsigned char *Bhi = sm, *Blo = sm + BTILE, *Bxh = sm + 2 * BTILE, *Bxl = sm + 3 * BTILE;
-  unsigned char *Abase = sm + 4 * BTILE;     // A(slot, plane) = Abase + (3 slot + plane) ATILE
-  // mbarriers first: they need 8-byte alignment (this address is 1024-aligned)
-  uint64_t *bars = reinterpret_cast<uint64_t *>(Abase + 3 * SLOTS * ATILE);  // accfull[2] drain[2]
+  unsigned char *Bhi = sm, *Blo = sm + BTILE, *Bxh = sm + 2 * BTILE, *Bxl = Bxh + XTILE_B;
+  unsigned char *Abase = Bxl + XTILE_B;      // slot t: Abase + t SLOT_BYTES: hi, lo, augmented
+  float *hstate = reinterpret_cast<float *>(Abase + SLOTS * SLOT_BYTES);  // [SLOTS][TR][DH]
+  // mbarriers next: they need 8-byte alignment (this address is 1024-aligned)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(hstate + SLOTS * HSTATE);  // accfull[2] drain[2]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
   float *sxi = reinterpret_cast<float *>(tmem_slot + 2);  // [3][XS]
   float *shc = sxi + 3 * XS;                 // [4]
@@ -148,12 +181,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   const int N = a.N;
   const int nh = a.cplx ? 4 : 2;
 
-  // zero the augmented atoms (only their first 16 columns are read)
-  for (int e = tid; e < 2 * BTILE / 16; e += THREADS)
+  // zero the augmented blocks (columns 3..15 stay zero)
+  for (int e = tid; e < 2 * XTILE_B / 16; e += THREADS)
     reinterpret_cast<uint4 *>(Bxh)[e] = make_uint4(0u, 0u, 0u, 0u);
   for (int t = 0; t < SLOTS; ++t)
-    for (int e = tid; e < ATILE / 16; e += THREADS)
-      reinterpret_cast<uint4 *>(Abase + (3 * t + 2) * ATILE)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < XTILE_A / 16; e += THREADS)
+      reinterpret_cast<uint4 *>(Abase + t * SLOT_BYTES + 2 * ATILE)[e] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   // weights B[n][k], split into BF16 planes with the 128-byte swizzle:
   // n < 192: W_g[a][k] (n = 3a + g); 192 + j: head row j; rest zero
@@ -162,15 +195,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
     float w = 0.f;
     if (n < NG) w = a.pack[a.oWgT + k * NG + n];
     else if (n - NG < nh) w = a.pack[a.ohead + (n - NG) * DH + k];
-    put_split(Bhi, Blo, n, k, w);
+    put_split(Bhi, Blo, sw128_off(n, k), w);
   }
   // augmented rows: column 0 the bias of gate n, columns 1, 2 the one-hot
   // input weights of the update and reset gates
   for (int n = tid; n < NG; n += THREADS) {
     const int q = n / 3, g = n % 3;
-    put_split(Bxh, Bxl, n, 0, a.pack[a.obias + 4 * q + g]);
-    put_split(Bxh, Bxl, n, 1, g < 2 ? a.pack[a.oxw + n] : 0.f);
-    put_split(Bxh, Bxl, n, 2, g < 2 ? a.pack[a.oxw + NG + n] : 0.f);
+    put_split(Bxh, Bxl, xoff(n, 0), a.pack[a.obias + 4 * q + g]);
+    put_split(Bxh, Bxl, xoff(n, 1), g < 2 ? a.pack[a.oxw + n] : 0.f);
+    put_split(Bxh, Bxl, xoff(n, 2), g < 2 ? a.pack[a.oxw + NG + n] : 0.f);
   }
   // W_in x + b_in per previous spin d (0, 1; 2 = none at site 0)
   for (int e = tid; e < 3 * DH; e += THREADS) {
@@ -199,7 +232,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
     const int t = warp / 8, half = (warp / 4) & 1, quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const bool issuer = (warp & 7) == 0 && lane == 0;
-    unsigned char *Ahi = Abase + (3 * t) * ATILE, *Alo = Ahi + ATILE, *Aaug = Ahi + 2 * ATILE;
+    unsigned char *Ahi = Abase + t * SLOT_BYTES, *Alo = Ahi + ATILE, *Aaug = Ahi + 2 * ATILE;
+    float *hrow = hstate + (t * TR + row) * DH;
     const uint32_t a0 = smem_u32(Ahi), b0 = smem_u32(Bhi);
     const uint32_t dacc = tmem + (uint32_t)(t * ACC_STRIDE);
     const uint32_t accbar = smem_u32(&bars[t]);
@@ -224,25 +258,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       // first recomputed site: j0, or with checkpoints the site after the
       // last checkpoint before it (its sites up to j0 - 1 add nothing)
       const int kr = a.ck > 0 ? (j0 / a.ck) * a.ck : j0;
-      float h[UH];
-      if (valid && kr > 0) {
-        const int64_t slot = a.ck > 0 ? (int64_t)s * a.nck + (kr / a.ck - 1) : (int64_t)s * N + kr - 1;
-        const float4 *src = reinterpret_cast<const float4 *>(a.hcache + slot * DH + UH * half);
-#pragma unroll
-        for (int c = 0; c < UH / 4; ++c) {
-          const float4 v = __ldcg(src + c);
-          h[4 * c] = v.x; h[4 * c + 1] = v.y; h[4 * c + 2] = v.z; h[4 * c + 3] = v.w;
+      // h_{kr-1}: this half's 32 units into the shared state and the planes
+      {
+        const float4 *src = nullptr;
+        if (valid && kr > 0) {
+          const int64_t slot =
+              a.ck > 0 ? (int64_t)s * a.nck + (kr / a.ck - 1) : (int64_t)s * N + kr - 1;
+          src = reinterpret_cast<const float4 *>(a.hcache + slot * DH + UH * half);
         }
-      } else {
 #pragma unroll
-        for (int q = 0; q < UH; ++q) h[q] = 0.f;
+        for (int g8 = 0; g8 < UH / 8; ++g8) {
+          float h8[8];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float4 v = src ? __ldcg(src + 2 * g8 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            *hchunk(hrow, row, (UH / 4) * half + 2 * g8 + q) = v;
+            h8[4 * q] = v.x; h8[4 * q + 1] = v.y; h8[4 * q + 2] = v.z; h8[4 * q + 3] = v.w;
+          }
+          write_planes8(Ahi, Alo, row, UH * half + 8 * g8, h8);
+        }
       }
       int n_up = 0, n_dn = 0;
       if (a.zmask && half == 0)
         for (int k = 0; k < kr; ++k) { if (__ldcg(sp + k) == 0) ++n_up; else ++n_dn; }
       // round 0: planes of h_{kr-1} and the input of site kr
       int sprev = kr > 0 ? spin_at(kr - 1) : 2;
-      write_planes(Ahi, Alo, row, half, h);
       if (half == 0) write_aug(Aaug, row, sprev);
       fence_async_smem();
       tc_fence_before();
@@ -283,31 +323,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
           if (sprev == 0) ++n_up; else ++n_dn;
         }
         if (r < L) {
-          // GRU cell of site k (App. A) on this half's units
+          // GRU cell of site k (App. A) on this half's units, 8 at a time:
+          // state from shared memory, gate pre-activations from tensor memory
           const float *xi = sxi + (k > 0 ? sprev : 2) * XS + UH * half;
 #pragma unroll
-          for (int ch = 0; ch < UH / 4; ++ch) {
-            // columns 3q + g of units 4 ch .. 4 ch + 3; every load starts at a
-            // multiple of its width
-            float v0[4], v1[4], v2[4];
-            tmem_ld4(gcol + (uint32_t)(ch * 12), v0);
-            tmem_ld4(gcol + (uint32_t)(ch * 12 + 4), v1);
-            tmem_ld4(gcol + (uint32_t)(ch * 12 + 8), v2);
+          for (int g8 = 0; g8 < UH / 8; ++g8) {
+            // columns 3q + g of units 8 g8 .. 8 g8 + 7: 24 columns, loads of 4
+            // starting at multiples of 4
+            float v[24];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              float t4[4];
+              tmem_ld4(gcol + (uint32_t)(g8 * 24 + 4 * q), t4);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) v[4 * q + e] = t4[e];
+            }
+            float h8[8];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const float4 c4 = *hchunk(hrow, row, (UH / 4) * half + 2 * g8 + q);
+              h8[4 * q] = c4.x; h8[4 * q + 1] = c4.y; h8[4 * q + 2] = c4.z; h8[4 * q + 3] = c4.w;
+            }
             tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = ch * 4 + u;
-              const int c0 = 3 * u, c1 = 3 * u + 1, c2 = 3 * u + 2;
-              const float pu = c0 < 4 ? v0[c0] : (c0 < 8 ? v1[c0 - 4] : v2[c0 - 8]);
-              const float pr = c1 < 4 ? v0[c1] : (c1 < 8 ? v1[c1 - 4] : v2[c1 - 8]);
-              const float pg = c2 < 4 ? v0[c2] : (c2 < 8 ? v1[c2 - 4] : v2[c2 - 8]);
-              const float uu = sigm_f(pu), rr = sigm_f(pr);
-              const float cc = tanh_f(fmaf(rr, pg, xi[q]));
-              h[q] = fmaf(uu, cc - h[q], h[q]);
+            for (int u = 0; u < 8; ++u) {
+              const float uu = sigm_f(v[3 * u]), rr = sigm_f(v[3 * u + 1]);
+              const float cc = tanh_f(fmaf(rr, v[3 * u + 2], xi[8 * g8 + u]));
+              h8[u] = fmaf(uu, cc - h8[u], h8[u]);
             }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+              *hchunk(hrow, row, (UH / 4) * half + 2 * g8 + q) =
+                  make_float4(h8[4 * q], h8[4 * q + 1], h8[4 * q + 2], h8[4 * q + 3]);
+            write_planes8(Ahi, Alo, row, UH * half + 8 * g8, h8);
           }
           sprev = scur;
-          write_planes(Ahi, Alo, row, half, h);
           if (half == 0) write_aug(Aaug, row, sprev);
           fence_async_smem();
           tc_fence_before();
