@@ -49,10 +49,11 @@ template <int DH> struct BTile {
 
 template <typename T, int DH, int DIM, int R>
 inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
+  constexpr int RP = R == 8 ? R + 1 : R;                   // padded row stride (see k_jac_bwd)
   size_t t = 4 * DH + 8;                                   // head, hc
   if (wsmem) t += 3 * (size_t)DH * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);  // Wg, U12
-  if (DIM == 2) t += (size_t)DH * R;                       // sdp
-  t += 3 * (size_t)DH * R;                                // sda
+  if (DIM == 2) t += (size_t)DH * RP;                      // sdp
+  t += 3 * (size_t)DH * RP;                               // sda
   size_t b = t * sizeof(T) + (size_t)R * ((N + 15) & ~15) + R * 16;
   return (b + 127) & ~size_t(127);
 }
@@ -79,10 +80,13 @@ k_jac_bwd(const BwdArgs<T> A) {
   T *swb = shc + 8;                        // staged Wg [3dh][dh] and U12 [dh][2dh] (wsmem)
   const T *sWg = swb;
   const T *sU12 = swb + C3 * DH;
-  T *sdp = swb + (WS ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][R]
-  T *sda = sdp + (DIM == 2 ? DH * R : 0);  // gate adjoints [3dh][R]
+  // the 8 rows of a unit are stored 9 floats apart, so the lanes of a warp
+  // (one row, consecutive units) spread over the banks
+  constexpr int RP = R == 8 ? R + 1 : R;
+  T *sdp = swb + (WS ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][RP]
+  T *sda = sdp + (DIM == 2 ? DH * RP : 0);  // gate adjoints [3dh][RP]
   const int NP = (A.N + 15) & ~15;
-  uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * R);
+  uint8_t *ssp = reinterpret_cast<uint8_t *>(sda + C3 * RP);
   int *srow = reinterpret_cast<int *>(ssp + R * NP);
 
   const int tid = threadIdx.x;
@@ -214,9 +218,9 @@ k_jac_bwd(const BwdArgs<T> A) {
           const T dg = dac * rr;
           const T dar = dr * rr * (T(1) - rr);
           const T dau = du * u * (T(1) - u);
-          sda[(3 * a + 0) * R + r] = dau;
-          sda[(3 * a + 1) * R + r] = dar;
-          sda[(3 * a + 2) * R + r] = dg;
+          sda[(3 * a + 0) * RP + r] = dau;
+          sda[(3 * a + 1) * RP + r] = dar;
+          sda[(3 * a + 2) * RP + r] = dg;
           if (g >= 0) {
             rec[a] = dau; rec[DH + a] = dar; rec[2 * DH + a] = dg; rec[3 * DH + a] = dac;
             if (DIM == 2) rec[AJ::HP + a] = hp;
@@ -230,7 +234,7 @@ k_jac_bwd(const BwdArgs<T> A) {
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int uu = 0; uu < UT; ++uu) dh1[i][uu] = dpd[i][uu];
-      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, R, r0, sWg, DH, a0, C3, dh1);
+      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, RP, r0, sWg, DH, a0, C3, dh1);
       if (DIM == 1) {
 #pragma unroll
         for (int i = 0; i < RT; ++i)
@@ -243,7 +247,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           const int r = r0 + i, g = srow[r];
 #pragma unroll
           for (int uu = 0; uu < UT; ++uu) {
-            sdp[(a0 + uu) * R + r] = dh1[i][uu];
+            sdp[(a0 + uu) * RP + r] = dh1[i][uu];
             if (g >= 0) A.adj[((int64_t)g * A.aN + k - A.aoff) * A.adjw + AJ::DHP + a0 + uu] = dh1[i][uu];
           }
         }
@@ -253,8 +257,8 @@ k_jac_bwd(const BwdArgs<T> A) {
         for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int uu = 0; uu < UT; ++uu) { dhh[i][uu] = T(0); dhv[i][uu] = T(0); }
-        mm_acc<T, RT, UT>(sdp, R, r0, sU12, 2 * DH, a0, DH, dhh);
-        mm_acc<T, RT, UT>(sdp, R, r0, sU12 + DH, 2 * DH, a0, DH, dhv);
+        mm_acc<T, RT, UT>(sdp, RP, r0, sU12, 2 * DH, a0, DH, dhh);
+        mm_acc<T, RT, UT>(sdp, RP, r0, sU12 + DH, 2 * DH, a0, DH, dhv);
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
           const int g = srow[r0 + i];
@@ -331,6 +335,8 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
   __shared__ int sx[KC][2];     // active one-hot input columns of site k (-1: none)
 
   const bool big = tid < GT * GT;
+  constexpr int NA = (KC * AJ::W + 255) / 256;   // adjoint values per thread and chunk
+  constexpr int NH = (KC * DH + 255) / 256;      // state values per thread and chunk
   const int ta = (tid / GT) * TA, tb = (tid % GT) * TA;
   // small entries: heads (4 dh), x-columns (3 dh din), biases (4 dh + 4)
   const int nsmall = 4 * DH + 3 * DH * DIN + 4 * DH + 4;
@@ -356,39 +362,82 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
       for (int i = 0; i < TA; ++i)
 #pragma unroll
         for (int j = 0; j < TA; ++j) accB[q][i][j] = T(0);
+    // chunks of KC sites through shared memory; the next chunk's values are
+    // fetched into registers while the current one is multiplied
+    T ra[NA], rh[NH], rq[NH], rhh[DIM == 2 ? NH : 1], rhv[DIM == 2 ? NH : 1];
+    int rx0 = -1, rx1 = -1;
+    auto fetch = [&](int k0) {
+      const int kc = min(KC, A.k_hi - k0);
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        const int e = tid + 256 * q;
+        if (e < kc * AJ::W) {
+          const int kk = e / AJ::W, wi = e - kk * AJ::W;
+          ra[q] = adj_at(k0 + kk)[wi];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        const int e = tid + 256 * q;
+        if (e < kc * DH) {
+          const int kk = e / DH, a = e - kk * DH, k = k0 + kk;
+          rh[q] = h_at(k)[a];
+          if (DIM == 1) {
+            rq[q] = k > 0 ? h_at(k - 1)[a] : T(0);
+          } else {
+            const int j = k / Lx, m = k - j * Lx;
+            const int ver = k >= Lx ? k - 2 * m - 1 : -1;
+            rhh[DIM == 2 ? q : 0] = m != 0 ? h_at(k - 1)[a] : T(0);
+            rhv[DIM == 2 ? q : 0] = ver >= 0 ? h_at(ver)[a] : T(0);
+            rq[q] = adj_at(k)[AJ::HP + a];
+          }
+        }
+      }
+      if (tid < kc) {
+        const int k = k0 + tid;
+        if (DIM == 1) {
+          rx0 = k > 0 ? sprow[k - 1] : -1;
+          rx1 = -1;
+        } else {
+          const int j = k / Lx, m = k - j * Lx;
+          const int ver = k >= Lx ? k - 2 * m - 1 : -1;
+          rx0 = m != 0 ? sprow[k - 1] : -1;
+          rx1 = ver >= 0 ? 2 + sprow[ver] : -1;
+        }
+      }
+    };
+    auto commit = [&](int k0) {
+      const int kc = min(KC, A.k_hi - k0);
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        const int e = tid + 256 * q;
+        if (e < kc * AJ::W) {
+          const int kk = e / AJ::W, wi = e - kk * AJ::W;
+          sadj[kk][wi] = ra[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        const int e = tid + 256 * q;
+        if (e < kc * DH) {
+          const int kk = e / DH, a = e - kk * DH;
+          sH[kk][a] = rh[q];
+          sQ[kk][a] = rq[q];
+          if (DIM == 2) {
+            sHh[kk][a] = rhh[DIM == 2 ? q : 0];
+            sHv[kk][a] = rhv[DIM == 2 ? q : 0];
+          }
+        }
+      }
+      if (tid < kc) { sx[tid][0] = rx0; sx[tid][1] = rx1; }
+    };
+    fetch(A.k_lo);
     for (int k0 = A.k_lo; k0 < A.k_hi; k0 += KC) {
       const int kc = min(KC, A.k_hi - k0);
+      __syncthreads();  // the previous chunk is no longer read
+      commit(k0);
       __syncthreads();
-      for (int e = tid; e < kc * AJ::W; e += 256) {
-        int kk = e / AJ::W, wi = e - kk * AJ::W;
-        sadj[kk][wi] = adj_at(k0 + kk)[wi];
-      }
-      for (int e = tid; e < kc * DH; e += 256) {
-        int kk = e / DH, a = e - kk * DH, k = k0 + kk;
-        sH[kk][a] = h_at(k)[a];
-        if (DIM == 1) {
-          sQ[kk][a] = k > 0 ? h_at(k - 1)[a] : T(0);
-        } else {
-          int j = k / Lx, m = k - j * Lx;
-          int ver = k >= Lx ? k - 2 * m - 1 : -1;
-          sHh[kk][a] = m != 0 ? h_at(k - 1)[a] : T(0);
-          sHv[kk][a] = ver >= 0 ? h_at(ver)[a] : T(0);
-          sQ[kk][a] = adj_at(k)[AJ::HP + a];
-        }
-      }
-      for (int kk = tid; kk < kc; kk += 256) {
-        int k = k0 + kk;
-        if (DIM == 1) {
-          sx[kk][0] = k > 0 ? sprow[k - 1] : -1;
-          sx[kk][1] = -1;
-        } else {
-          int j = k / Lx, m = k - j * Lx;
-          int ver = k >= Lx ? k - 2 * m - 1 : -1;
-          sx[kk][0] = m != 0 ? sprow[k - 1] : -1;
-          sx[kk][1] = ver >= 0 ? 2 + sprow[ver] : -1;
-        }
-      }
-      __syncthreads();
+      if (k0 + KC < A.k_hi) fetch(k0 + KC);
       if (big) {
         for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
