@@ -221,10 +221,16 @@ __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
       const int i = e / CC_B, j = e % CC_B;
       D[i][j] = (i < m && j <= i) ? A[(c0 + i) * n + c0 + j] : 0.0;
     }
+    {  // the CTAs' partial sums, eight strided groups in flight
+      double s = 0.0;
+#pragma unroll 4
+      for (int q = warp; q < G; q += 8) s += part[(size_t)q * CC_B + lane];
+      red[warp * CC_B + lane] = s;
+    }
     __syncthreads();
     if (warp == 0) {
       double s = 0.0;
-      for (int q = 0; q < G; ++q) s += part[(size_t)q * CC_B + lane];
+      for (int w = 0; w < 8; ++w) s += red[w * CC_B + lane];
       double v = lane < m ? a.y[c0 + lane] - s : 0.0;
       const double dinv = lane < m ? 1.0 / D[lane][lane] : 0.0;
       for (int k = m - 1; k >= 0; --k) {

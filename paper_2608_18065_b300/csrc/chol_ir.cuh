@@ -45,7 +45,13 @@ struct CholIrArgs {
   int subst;         // 1: sweeps by block substitution with the inverted
                      // 32x32 diagonal blocks (no full inverse); 0: two
                      // products with the explicit inverse
+  float *dg;         // [2][IR_DG] scratch: the next panel's factored
+                     // diagonal block, 1/L_jj and its pivot flag
 };
+
+// published diagonal block: [32][32] factor (zero upper triangle), [32]
+// reciprocal pivots, one pivot flag; padded to 128-byte rows
+constexpr int IR_DG = IR_B * IR_B + 2 * IR_B;
 
 // Per-warp 32x32 tile product in shared memory (row stride WS floats, a
 // multiple of 4 so rows are 16-byte aligned): lane j owns column j of the
@@ -93,6 +99,141 @@ __device__ __forceinline__ void warp_stage(float *sT, const float *M, int64_t ld
   for (int r = 0; r < IR_B; ++r) sT[r * WS + lane] = v[r];
 }
 
+// Cholesky of one 32x32 diagonal block by one warp; lane i holds row i
+// (identity outside the valid m x m block).  Column j is published through
+// shared memory (one store per lane, broadcast reads; two buffers so one
+// __syncwarp per column suffices) and every lane takes the pivot itself, so
+// the dependent chain per column is one store/load round trip, a reciprocal
+// square root and one FMA.  Returns nonzero (uniform over the warp) for a
+// pivot that is not positive; lane j's rinv is 1/L_jj.
+__device__ __forceinline__ int warp_chol32(float (&rr)[IR_B], float *colb, int lane,
+                                           float &rinv) {
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < IR_B; ++j) {
+    float *cb = colb + (j & 1) * IR_B;
+    cb[lane] = rr[j];
+    __syncwarp();
+    const float dj = cb[j];
+    bad |= !(dj > 0.f);
+    const float inv = dj > 0.f ? rsqrtf(dj) : 0.f;
+    const float lij = rr[j] * inv;  // L_ij for lane i > j
+    const float t = lij * inv;      // L_ij / L_jj
+#pragma unroll
+    for (int k = j + 1; k < IR_B; ++k)
+      if (lane >= k) rr[k] = fmaf(-t, cb[k], rr[k]);
+    rr[j] = lane == j ? dj * inv : (lane > j ? lij : 0.f);
+    if (lane == j) rinv = inv;
+  }
+  return bad;
+}
+
+// Factor the diagonal block staged in S ([32][33], lower triangle valid for
+// the first m rows and columns) and publish it: the factor into L (rows and
+// columns c0..c0+m), the block with zero upper triangle, 1/L_jj and the pivot
+// flag into dg.  One warp; S is overwritten.
+__device__ __noinline__ void warp_factor_publish(float *S, int m, float *colb, float *L,
+                                                    int64_t n, int64_t c0, float *dg, int lane) {
+  constexpr int SS = IR_B + 1;
+  float rr[IR_B];
+#pragma unroll
+  for (int k = 0; k < IR_B; ++k)
+    rr[k] = (lane < m && k < m && k <= lane) ? S[lane * SS + k] : (k == lane ? 1.f : 0.f);
+  float rinv = 1.f;
+  const int bad = warp_chol32(rr, colb, lane, rinv);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < IR_B; ++k) S[lane * SS + k] = rr[k];
+  __syncwarp();
+#pragma unroll 8
+  for (int r = 0; r < IR_B; ++r) {
+    const float v = S[r * SS + lane];
+    dg[r * IR_B + lane] = v;
+    if (r < m && lane <= r) L[(c0 + r) * n + c0 + lane] = v;
+  }
+  dg[IR_B * IR_B + lane] = rinv;
+  if (lane == 0) dg[IR_B * IR_B + IR_B] = __int_as_float(bad);
+}
+
+// Inverse of the unit-padded lower-triangular block D ([32][33]) into the
+// diagonal block of Li at c0 (m x m valid); lane j forms column j.
+__device__ __noinline__ void warp_tri_inverse(const float (*D)[IR_B + 1], int m, float *Li,
+                                                 int64_t n, int64_t c0, int lane) {
+  const int j = lane;
+  float xc[IR_B];
+#pragma unroll
+  for (int i = 0; i < IR_B; ++i) {
+    float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+    for (int k = 0; k < i; ++k) acc -= D[i][k] * xc[k];
+    xc[i] = (i >= j) ? acc / D[i][i] : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < IR_B; ++i)
+    if (i < m && j < m && i >= j) Li[(c0 + i) * n + c0 + j] = xc[i];
+}
+
+// Asynchronous global -> shared copies (cp.async, completion by groups);
+// src_bytes < size fills the rest with zeros (0: nothing is read).
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// K pieces of the inversion-level products staged whole in shared memory:
+// A rows [32][LV_KP + 4], B rows [LV_KP][36], two pieces in flight.
+constexpr int LV_KP = 256;
+constexpr int LV_AS = LV_KP + 4, LV_BS = IR_B + 4;
+constexpr int LV_STAGE = IR_B * LV_AS + LV_KP * LV_BS;  // floats per piece
+
+// Stage rows i0..i0+31, columns ac..ac+klen of Aop and rows br..br+klen,
+// columns j0..j0+31 of Bop (n x n, row-major; zeros outside) into one piece.
+// vec: n % 4 == 0, so every 16-byte chunk is aligned and wholly in or out.
+__device__ __forceinline__ void lv_stage(float *sA, float *sB, const float *Aop, const float *Bop,
+                                         int64_t n, int64_t i0, int64_t ac, int64_t br, int64_t j0,
+                                         int klen, bool vec, int tid) {
+  if (vec) {
+    const int qa = klen / 4;
+    for (int c = tid; c < IR_B * qa; c += IR_THREADS) {
+      const int r = c / qa, q = c - r * qa;
+      const int64_t row = i0 + r, col = ac + 4 * q;
+      const bool ok = row < n && col < n;
+      cp_async16(sA + r * LV_AS + 4 * q, ok ? Aop + row * n + col : Aop, ok ? 16 : 0);
+    }
+    for (int c = tid; c < klen * (IR_B / 4); c += IR_THREADS) {
+      const int r = c >> 3, q = c & 7;
+      const int64_t row = br + r, col = j0 + 4 * q;
+      const bool ok = row < n && col < n;
+      cp_async16(sB + r * LV_BS + 4 * q, ok ? Bop + row * n + col : Bop, ok ? 16 : 0);
+    }
+  } else {
+    for (int c = tid; c < IR_B * klen; c += IR_THREADS) {
+      const int r = c / klen, q = c - r * klen;
+      const int64_t row = i0 + r, col = ac + q;
+      const bool ok = row < n && col < n;
+      cp_async4(sA + r * LV_AS + q, ok ? Aop + row * n + col : Aop, ok ? 4 : 0);
+    }
+    for (int c = tid; c < klen * IR_B; c += IR_THREADS) {
+      const int r = c >> 5, q = c & 31;
+      const int64_t row = br + r, col = j0 + q;
+      const bool ok = row < n && col < n;
+      cp_async4(sB + r * LV_BS + q, ok ? Bop + row * n + col : Bop, ok ? 4 : 0);
+    }
+  }
+  cp_async_commit();
+}
+
 // WT: 32x32 tiles of the trailing update and of the inversion products are
 // spread one per warp (more tiles in flight; better at large n), else one
 // per CTA with four outputs per thread (shorter per-tile latency; better at
@@ -114,52 +255,55 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   const int nb = (int)((n + IR_B - 1) / IR_B);
   float *L = a.L;
 
-  // (0) FP32 copy of the lower triangle
+  // (0) FP32 copy of the lower triangle (diagonal block 0 excepted) and
+  // Li cleared; CTA 0 factors diagonal block 0 straight from A and publishes
+  // it.  From here on the factor is right-looking with look-ahead: while the
+  // other CTAs update the trailing matrix of panel p, CTA 0 updates the
+  // next diagonal block alone, factors and publishes it, so the factor of a
+  // diagonal block is never on the path between the two grid barriers of a
+  // panel.
+  __shared__ __align__(16) float colb_s[2 * IR_B];
+  float *S = wtile + 2 * IR_B * TS;  // [32][33] staging of a diagonal block
+  const int m0 = (int)min64(IR_B, n);
   for (int64_t e = (int64_t)g * IR_THREADS + tid; e < n * n; e += (int64_t)G * IR_THREADS) {
     const int64_t i = e / n, j = e - i * n;
-    if (j <= i) L[e] = (float)a.A[e];
+    a.Li[e] = 0.f;
+    if (j <= i && i >= m0) L[e] = (float)a.A[e];
+  }
+  if (g == 0 && warp == 0) {
+    float v[IR_B];
+#pragma unroll
+    for (int r = 0; r < IR_B; ++r) v[r] = (r < m0 && lane <= r) ? (float)a.A[r * n + lane] : 0.f;
+#pragma unroll
+    for (int r = 0; r < IR_B; ++r) S[r * TS + lane] = v[r];
+    __syncwarp();
+    warp_factor_publish(S, m0, colb_s, L, n, 0, a.dg, lane);
   }
   if (!cc_grid_sync(a.bar, a.status)) return;
 
   // (1) FP32 right-looking Cholesky
+  const bool la = G > 1;  // CTA 0 keeps the next diagonal block to itself
   for (int p = 0; p < nb; ++p) {
     const int64_t c0 = (int64_t)p * IR_B;
     const int m = (int)min64(IR_B, n - c0);
-    if (warp == 0) {
-      float rr[IR_B];
-#pragma unroll
-      for (int k = 0; k < IR_B; ++k)
-        rr[k] = (lane < m && k < m && k <= lane) ? L[(c0 + lane) * n + c0 + k]
-                                                 : (k == lane ? 1.f : 0.f);
-      int bad = 0;
-#pragma unroll
-      for (int j = 0; j < IR_B; ++j) {
-        if (j < m) {
-          const float dj = __shfl_sync(0xffffffffu, rr[j], j);
-          bad |= !(dj > 0.f);
-          const float inv = dj > 0.f ? rsqrtf(dj) : 0.f;
-          if (lane == j) { rr[j] = dj * inv; rinv[j] = inv; }
-          else if (lane > j) rr[j] *= inv;
-#pragma unroll
-          for (int k = j + 1; k < IR_B; ++k) {
-            const float lkj = __shfl_sync(0xffffffffu, rr[j], k);
-            if (lane >= k) rr[k] -= rr[j] * lkj;
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < IR_B; ++k) D[lane][k] = (k <= lane) ? rr[k] : 0.f;
-      if (lane == 0) flag_s = bad;
+    const int64_t r0 = c0 + m;
+    // this warp's first panel row is requested before the published block
+    const int64_t rfirst = r0 + (int64_t)g * (IR_THREADS / 32) + warp;
+    const float vfirst = (rfirst < n && lane < m) ? L[rfirst * n + c0 + lane] : 0.f;
+    {
+      const float *dgp = a.dg + (p & 1) * IR_DG;
+      for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) D[e >> 5][e & 31] = __ldcg(dgp + e);
+      if (tid < IR_B) rinv[tid] = __ldcg(dgp + IR_B * IR_B + tid);
+      if (tid == 0) flag_s = __float_as_int(__ldcg(dgp + IR_B * IR_B + IR_B));
     }
     __syncthreads();
     if (flag_s) {  // identical in every CTA: the FP64 factorisation takes over
       if (g == 0 && tid == 0) *a.need_fp64 = 1;
       return;
     }
-    const int64_t r0 = c0 + m;
-    for (int64_t r = r0 + (int64_t)g * (IR_THREADS / 32) + warp; r < n;
-         r += (int64_t)G * (IR_THREADS / 32)) {
-      float v = lane < m ? L[r * n + c0 + lane] : 0.f;
+    // panel rows below the diagonal block: L_rp = A_rp L_pp^{-T}
+    for (int64_t r = rfirst; r < n; r += (int64_t)G * (IR_THREADS / 32)) {
+      float v = r == rfirst ? vfirst : (lane < m ? L[r * n + c0 + lane] : 0.f);
       for (int k = 0; k < m; ++k) {
         if (lane == k) v *= rinv[k];
         const float lk = __shfl_sync(0xffffffffu, v, k);
@@ -168,18 +312,43 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       if (lane < m) L[r * n + c0 + lane] = v;
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
-    if (g == 0)
-      for (int e = tid; e < m * m; e += IR_THREADS) {
-        const int i = e / m, j = e % m;
-        if (j <= i) L[(c0 + i) * n + c0 + j] = D[i][j];
-      }
     const int64_t tr = n - r0;
+    const int m1 = (int)min64(IR_B, tr);  // size of the next diagonal block
     if (tr > 0) {
       const int nt = (int)((tr + IR_B - 1) / IR_B);
       const int ntiles = nt * (nt + 1) / 2;
-      if constexpr (!WT) {
-        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA
-        for (int t = g; t < ntiles; t += G) {
+      if (la && g == 0) {
+        // tile (0, 0) of the trailing matrix (the next diagonal block),
+        // CTA-wide, its result also staged in S
+        for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+          const int rr = e / IR_B, k = e % IR_B;
+          ta[rr * TS + k] = (rr < m1 && k < m) ? L[(r0 + rr) * n + c0 + k] : 0.f;
+        }
+        const int tx = tid % 32, ty = tid / 32;
+        float old[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = ty + 8 * q;
+          old[q] = (i < m1 && tx <= i) ? L[(r0 + i) * n + r0 + tx] : 0.f;
+        }
+        __syncthreads();
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int k = 0; k < IR_B; ++k) {
+          const float bv = ta[tx * TS + k];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = ty + 8 * q;
+          S[i * TS + tx] = old[q] - acc[q];  // the factor writes the block back to L
+        }
+      } else if constexpr (!WT) {
+        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA (with
+        // look-ahead, tiles 1.. over CTAs 1..)
+        const int cta0 = la ? 1 : 0;
+        for (int t = g; t < ntiles; t += G - cta0) {
           int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
           while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
           while (ti * (ti + 1) / 2 > t) --ti;
@@ -208,68 +377,69 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
           }
         }
       } else {
-      // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile of the lower
-      // triangle per warp over the whole grid
-      float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
-      const int64_t gwarp = (int64_t)g * (IR_THREADS / 32) + warp;
-      for (int64_t t = gwarp; t < ntiles; t += (int64_t)G * (IR_THREADS / 32)) {
-        int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-        while (ti * (ti + 1) / 2 > t) --ti;
-        const int tj = (int)(t - ti * (ti + 1) / 2);
-        const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
-        __syncwarp();
-        warp_stage(sA, L, n, i0, c0, n, n, c0 + m, lane);
-        warp_stage(sB, L, n, j0, c0, n, n, c0 + m, lane);
-        __syncwarp();
-        float acc[IR_B];
+        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile of the lower
+        // triangle per warp (with look-ahead, tiles 1.. over CTAs 1..)
+        float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
+        const int cta0 = la ? 1 : 0;
+        const int64_t gwarp = (int64_t)(g - cta0) * (IR_THREADS / 32) + warp + cta0;
+        for (int64_t t = gwarp; t < ntiles; t += (int64_t)(G - cta0) * (IR_THREADS / 32)) {
+          int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+          while (ti * (ti + 1) / 2 > t) --ti;
+          const int tj = (int)(t - ti * (ti + 1) / 2);
+          const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+          __syncwarp();
+          warp_stage(sA, L, n, i0, c0, n, n, c0 + m, lane);
+          warp_stage(sB, L, n, j0, c0, n, n, c0 + m, lane);
+          __syncwarp();
+          float acc[IR_B];
 #pragma unroll
-        for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
-        warp_tile_fma<true>(sA, sB, lane, acc);
-        const int64_t j = j0 + lane;
+          for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
+          warp_tile_fma<true>(sA, sB, lane, acc);
+          const int64_t j = j0 + lane;
 #pragma unroll
-        for (int i = 0; i < IR_B; ++i) {
-          const int64_t ii = i0 + i;
-          if (ii < n && j < n && j <= ii) L[ii * n + j] -= acc[i];
+          for (int i = 0; i < IR_B; ++i) {
+            const int64_t ii = i0 + i;
+            if (ii < n && j < n && j <= ii) L[ii * n + j] -= acc[i];
+          }
         }
       }
+    }
+    if (g == 0) {
+      __syncthreads();
+      if (warp == 0 && tr > 0) {
+        if (!la) {  // CTA 0 updated the block among all the others: stage it
+          float v[IR_B];
+#pragma unroll
+          for (int r = 0; r < IR_B; ++r)
+            v[r] = (r < m1 && lane <= r) ? L[(r0 + r) * n + r0 + lane] : 0.f;
+#pragma unroll
+          for (int r = 0; r < IR_B; ++r) S[r * TS + lane] = v[r];
+          __syncwarp();
+        }
+        warp_factor_publish(S, m1, colb_s, L, n, r0, a.dg + ((p + 1) & 1) * IR_DG, lane);
       }
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
   }
-
-  // (2) explicit inverse of the FP32 factor by recursive doubling:
-  //     diagonal 32x32 blocks first, then per level, for every pair of
-  //     inverted s x s blocks, X21 = -L22^{-1} (L21 L11^{-1}).
-  float *Li = a.Li;
-  for (int64_t e = (int64_t)g * IR_THREADS + tid; e < n * n; e += (int64_t)G * IR_THREADS)
-    Li[e] = 0.f;
-  if (!cc_grid_sync(a.bar, a.status)) return;
+  // diagonal blocks of the inverse, one block per CTA
   for (int blk = g; blk < nb; blk += G) {
     const int64_t c0 = (int64_t)blk * IR_B;
     const int m = (int)min64(IR_B, n - c0);
+    __syncthreads();
     for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
       const int i = e / IR_B, j = e % IR_B;
       D[i][j] = (i < m && j <= i) ? L[(c0 + i) * n + c0 + j] : (i == j ? 1.f : 0.f);
     }
     __syncthreads();
-    if (warp == 0) {  // lane j: column j of the inverse, top to bottom
-      const int j = lane;
-      float xc[IR_B];
-#pragma unroll
-      for (int i = 0; i < IR_B; ++i) {
-        float acc = (i == j) ? 1.f : 0.f;
-#pragma unroll
-        for (int k = 0; k < i; ++k) acc -= D[i][k] * xc[k];
-        xc[i] = (i >= j) ? acc / D[i][i] : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < IR_B; ++i)
-        if (i < m && j < m && i >= j) Li[(c0 + i) * n + c0 + j] = xc[i];
-    }
-    __syncthreads();
+    if (warp == 0) warp_tri_inverse(D, m, a.Li, n, c0, lane);
   }
   if (!cc_grid_sync(a.bar, a.status)) return;
+
+  // (2) explicit inverse of the FP32 factor by recursive doubling: the
+  //     diagonal 32x32 blocks are inverted above; per level, for every pair
+  //     of inverted s x s blocks, X21 = -L22^{-1} (L21 L11^{-1}).
+  float *Li = a.Li;
   for (int64_t sz = IR_B; sz < n && !a.subst; sz *= 2) {
     // Tm[pair block] = L21 Li11 ; then Li21 = -Li22 Tm
     for (int phase = 0; phase < 2; ++phase) {
@@ -277,34 +447,66 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       const int64_t tps = (sz + IR_B - 1) / IR_B;  // tiles per side of a pair block
       const int64_t ntile = pairs * tps * tps;
       if constexpr (!WT) {
-        for (int64_t t = g; t < ntile; t += G) {
-          const int64_t pr = t / (tps * tps), tt = t % (tps * tps);
-          const int64_t ti = tt / tps, tj = tt % tps;
+        // one 32x32 output tile per CTA; the triangular operand (Li11 in
+        // phase 0, Li22 in phase 1) makes leading or trailing K chunks zero,
+        // which are skipped (each output still sums its nonzero terms in
+        // ascending k).  Tiles go out by decreasing K length, round-robin
+        // in alternating directions, to balance the CTAs.
+        const bool vec = (n & 3) == 0;
+        float *stg = wtile;  // two pieces of LV_STAGE floats
+        for (int64_t rnd = 0; rnd * G < ntile; ++rnd) {
+          const int64_t t = rnd * G + ((rnd & 1) ? (G - 1 - g) : g);
+          if (t >= ntile) continue;                   // uniform over the CTA
+          const int64_t pr = t % pairs, u = t / pairs;
+          const int64_t ti = phase == 0 ? u % tps : tps - 1 - u / tps;
+          const int64_t tj = phase == 0 ? u / tps : u % tps;
           const int64_t base = pr * 2 * sz;
           const int64_t i0 = base + sz + ti * IR_B;   // rows of the lower-left block
           const int64_t j0 = base + tj * IR_B;        // columns
           if (i0 >= n) continue;                      // uniform over the CTA
           const float *Aop; const float *Bop;
-          int64_t acol0, brow0;
-          if (phase == 0) { Aop = L; acol0 = base; Bop = Li; brow0 = base; }
-          else { Aop = Li; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz; }
+          int64_t acol0, brow0, kb, ke;
+          if (phase == 0) {  // Tm = L21 Li11: Li11 rows below j0 only
+            Aop = L; acol0 = base; Bop = Li; brow0 = base; kb = tj * IR_B; ke = sz;
+          } else {           // Li21 = -Li22 Tm: Li22 columns up to row i0 + 31
+            Aop = Li; acol0 = base + sz; Bop = a.Tm; brow0 = base + sz; kb = 0;
+            ke = (ti + 1) * IR_B;
+          }
           const int tx = tid % 32, ty = tid / 32;
           float acc[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int64_t k0 = 0; k0 < sz; k0 += IR_B) {
+          const int np = (int)((ke - kb + LV_KP - 1) / LV_KP);
+          __syncthreads();  // the previous tile's pieces are no longer read
+          for (int q = 0; q < np && q < 2; ++q) {
+            const int64_t k0 = kb + (int64_t)q * LV_KP;
+            float *sA = stg + q * LV_STAGE;
+            lv_stage(sA, sA + IR_B * LV_AS, Aop, Bop, n, i0, acol0 + k0, brow0 + k0, j0,
+                     (int)min64(LV_KP, ke - k0), vec, tid);
+          }
+          for (int q = 0; q < np; ++q) {
+            if (q + 1 < np) cp_async_wait_all_but_one(); else cp_async_wait_all();
             __syncthreads();
-            for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-              const int rr = e / IR_B, kk = e % IR_B;
-              const int64_t ar = i0 + rr, ac = acol0 + k0 + kk;
-              ta[rr * TS + kk] = (ar < n && ac < n) ? Aop[ar * n + ac] : 0.f;
-              const int64_t br = brow0 + k0 + rr, bc = j0 + kk;
-              tb[rr * TS + kk] = (br < n && bc < n) ? Bop[br * n + bc] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < IR_B; ++kk) {
-              const float bv = tb[kk * TS + tx];
+            const int64_t k0 = kb + (int64_t)q * LV_KP;
+            const int klen = (int)min64(LV_KP, ke - k0);
+            const float *sA = stg + (q & 1) * LV_STAGE, *sB = sA + IR_B * LV_AS;
+#pragma unroll 2
+            for (int kk = 0; kk < klen; kk += 4) {
+              const float b0 = sB[(kk + 0) * LV_BS + tx], b1 = sB[(kk + 1) * LV_BS + tx];
+              const float b2 = sB[(kk + 2) * LV_BS + tx], b3 = sB[(kk + 3) * LV_BS + tx];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + kk], bv, acc[q]);
+              for (int r = 0; r < 4; ++r) {
+                const float4 av = *reinterpret_cast<const float4 *>(sA + (ty + 8 * r) * LV_AS + kk);
+                acc[r] = fmaf(av.x, b0, acc[r]);
+                acc[r] = fmaf(av.y, b1, acc[r]);
+                acc[r] = fmaf(av.z, b2, acc[r]);
+                acc[r] = fmaf(av.w, b3, acc[r]);
+              }
+            }
+            if (q + 2 < np) {
+              __syncthreads();  // piece q is no longer read
+              const int64_t k2 = kb + (int64_t)(q + 2) * LV_KP;
+              float *sA2 = stg + (q & 1) * LV_STAGE;
+              lv_stage(sA2, sA2 + IR_B * LV_AS, Aop, Bop, n, i0, acol0 + k2, brow0 + k2, j0,
+                       (int)min64(LV_KP, ke - k2), vec, tid);
             }
           }
 #pragma unroll
@@ -424,6 +626,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     for (int64_t i = gw; i < n; i += nwarps) {
       const float *row = Li + i * n;
       float sacc = 0.f;
+#pragma unroll 8
       for (int64_t j = lane; j <= i; j += 32) sacc = fmaf(row[j], (float)a.r[j], sacc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
@@ -437,13 +640,17 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       const int64_t j = cb * 32 + lane;
       float sacc = 0.f;
       const int64_t r1 = min64(n, (ch + 1) * CH);
-      for (int64_t i = ch * CH; i < r1; ++i)
-        if (j < n && i >= j) sacc = fmaf(Li[i * n + j], a.wv[i], sacc);
+      if (j < n) {
+        const int64_t i1 = max64(ch * CH, j);
+#pragma unroll 16
+        for (int64_t i = i1; i < r1; ++i) sacc = fmaf(Li[i * n + j], a.wv[i], sacc);
+      }
       if (j < n) a.dpart[ch * n + j] = sacc;
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
     for (int64_t j = (int64_t)g * IR_THREADS + tid; j < n; j += (int64_t)G * IR_THREADS) {
       float d = 0.f;
+#pragma unroll 8
       for (int64_t ch = j / CH; ch < nch; ++ch) d += a.dpart[ch * n + j];
       a.x[j] += (double)d;
     }
@@ -455,6 +662,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     for (int64_t i = gw; i < n; i += nwarps) {
       const double *Ai = a.A + i * n;
       double sacc = 0.0, sa = 0.0;
+#pragma unroll 8
       for (int64_t j = lane; j < n; j += 32) {
         const double aij = Ai[j];
         sacc = fma(aij, a.x[j], sacc);
@@ -481,10 +689,28 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       a.part[(size_t)g * 4 + 0] = m0; a.part[(size_t)g * 4 + 1] = m1; a.part[(size_t)g * 4 + 2] = m2;
     }
     if (!cc_grid_sync(a.bar, a.status)) return;
+    // maxima over the CTAs' partials: all loads in flight at once (max is
+    // exact, so the grouping does not matter)
+    {
+      double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+      for (int q = tid; q < G; q += IR_THREADS) {
+        q0 = fmax(q0, a.part[(size_t)q * 4]); q1 = fmax(q1, a.part[(size_t)q * 4 + 1]);
+        q2 = fmax(q2, a.part[(size_t)q * 4 + 2]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        q0 = fmax(q0, __shfl_xor_sync(0xffffffffu, q0, o));
+        q1 = fmax(q1, __shfl_xor_sync(0xffffffffu, q1, o));
+        q2 = fmax(q2, __shfl_xor_sync(0xffffffffu, q2, o));
+      }
+      __syncthreads();  // red_s of the sweep's own maxima has been read
+      if (lane == 0) { red_s[warp][0] = q0; red_s[warp][1] = q1; red_s[warp][2] = q2; }
+      __syncthreads();
+    }
     double rn = 0.0, xn = 0.0, an = 0.0;
-    for (int q = 0; q < G; ++q) {
-      rn = fmax(rn, a.part[(size_t)q * 4]); xn = fmax(xn, a.part[(size_t)q * 4 + 1]);
-      an = fmax(an, a.part[(size_t)q * 4 + 2]);
+#pragma unroll
+    for (int q = 0; q < IR_THREADS / 32; ++q) {
+      rn = fmax(rn, red_s[q][0]); xn = fmax(xn, red_s[q][1]); an = fmax(an, red_s[q][2]);
     }
     if (it == 0) normA = an;
     converged = rn <= sqrt((double)n) * 1.1102230246251565e-16 * normA * xn;
@@ -495,7 +721,9 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
 }
 
 inline size_t chol_ir_smem(int64_t) {
-  return sizeof(float) * ((size_t)IR_B * (IR_B + 1) + IR_B + (IR_THREADS / 32) * 2 * (size_t)IR_B * WS);
+  const size_t tiles = (IR_THREADS / 32) * 2 * (size_t)IR_B * WS;  // warp tiles
+  const size_t pieces = 2 * (size_t)LV_STAGE;                      // level pieces
+  return sizeof(float) * ((size_t)IR_B * (IR_B + 1) + IR_B + (tiles > pieces ? tiles : pieces));
 }
 
 }  // namespace nqs

@@ -12,6 +12,7 @@
 namespace nqs {
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 of Salmon et al. (SC'11): ten rounds of two 32x32->64-bit

@@ -23,7 +23,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dstep, tth, tmo, tstats, hseg, carry, dlm, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dg32, dstep, tth, tmo, tstats, hseg, carry, dlm, total;
 };
 
 }  // namespace
@@ -191,6 +191,7 @@ void carve(nqs_ctx *c) {
   o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.wv32 = take(R * 4);
   o.dpart32 = take(((R + 63) / 64) * R * 4);
+  o.dg32 = take(c->prec == NQS_PREC_MIXED ? 2 * IR_DG * 4 : 0);
   o.dstep = take(64);
   o.tth = take(np * 8);
   o.tmo = take(np * 8);
@@ -568,6 +569,7 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     // (measured at n = 4096: the inversion levels took 9 of 16.5 ms)
     ir.subst = tuned(c) && c->t_chol_subst >= 0 ? c->t_chol_subst : (R >= 2048 ? 1 : 0);
     ir.dv = ir.dpart;
+    ir.dg = W<float>(c, c->off.dg32);
     const size_t smem = chol_ir_smem(R);
     // tiles per warp pay off once n is large (measured: 16.5 vs 19.8 ms at
     // n = 4096, 1.71 vs 0.93 ms at n = 1024)
