@@ -70,6 +70,39 @@ __device__ __forceinline__ bool cc_grid_sync(unsigned *bar, int32_t *status) {
   return ok_s != 0;
 }
 
+// Grid barrier with an explicit instance count, for kernels in which a CTA
+// may join an instance without waiting for it: instance e (0-based) is
+// complete once the counter reaches (e + 1) G, whatever the order of the
+// arrivals.  cc_arrive joins an instance and returns at once (the caller
+// must not read what the other CTAs write before that instance);
+// cc_sync_ep joins one and waits for it, which implies every earlier one.
+// The same bounded acquire polling as cc_grid_sync.
+__device__ __forceinline__ void cc_arrive(unsigned *bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool cc_sync_ep(unsigned *bar, int32_t *status, unsigned target) {
+  __shared__ int oke_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned v;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+    v += 1;
+    unsigned long long it = 0;
+    while ((int)(v - target) < 0) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (++it > (1ull << 23)) {
+        atomicCAS(reinterpret_cast<int *>(status), 0, (int)NQS_ERR_TIMEOUT);
+        break;
+      }
+    }
+    oke_s = *reinterpret_cast<volatile int32_t *>(status) == 0;
+  }
+  __syncthreads();
+  return oke_s != 0;
+}
+
 __global__ void __launch_bounds__(CC_THREADS) k_chol_coop(CholCoopArgs a) {
   extern __shared__ double cc_smem[];
   double (*D)[CC_B + 1] = reinterpret_cast<double (*)[CC_B + 1]>(cc_smem);  // [32][33]

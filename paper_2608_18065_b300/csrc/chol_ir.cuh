@@ -101,11 +101,13 @@ __device__ __forceinline__ void warp_stage(float *sT, const float *M, int64_t ld
 
 // Cholesky of one 32x32 diagonal block by one warp; lane i holds row i
 // (identity outside the valid m x m block).  Column j is published through
-// shared memory (one store per lane, broadcast reads; two buffers so one
-// __syncwarp per column suffices) and every lane takes the pivot itself, so
-// the dependent chain per column is one store/load round trip, a reciprocal
-// square root and one FMA.  Returns nonzero (uniform over the warp) for a
-// pivot that is not positive; lane j's rinv is 1/L_jj.
+// shared memory (one store per lane, read back as broadcast float4s; two
+// buffers so one __syncwarp per column suffices) and every lane takes the
+// pivot itself, so the dependent chain per column is one store/load round
+// trip, a reciprocal square root and one FMA.  The updates run on every lane
+// unconditionally: lanes i < k only touch the upper triangle, which is
+// scratch and cleared column by column.  Returns nonzero (uniform over the
+// warp) for a pivot that is not positive; lane j's rinv is 1/L_jj.
 __device__ __forceinline__ int warp_chol32(float (&rr)[IR_B], float *colb, int lane,
                                            float &rinv) {
   int bad = 0;
@@ -114,18 +116,41 @@ __device__ __forceinline__ int warp_chol32(float (&rr)[IR_B], float *colb, int l
     float *cb = colb + (j & 1) * IR_B;
     cb[lane] = rr[j];
     __syncwarp();
-    const float dj = cb[j];
+    float c[IR_B];
+#pragma unroll
+    for (int q = j / 4; q < IR_B / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4 *>(cb)[q];
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+    const float dj = c[j];
     bad |= !(dj > 0.f);
     const float inv = dj > 0.f ? rsqrtf(dj) : 0.f;
     const float lij = rr[j] * inv;  // L_ij for lane i > j
     const float t = lij * inv;      // L_ij / L_jj
 #pragma unroll
-    for (int k = j + 1; k < IR_B; ++k)
-      if (lane >= k) rr[k] = fmaf(-t, cb[k], rr[k]);
+    for (int k = j + 1; k < IR_B; ++k) rr[k] = fmaf(-t, c[k], rr[k]);
     rr[j] = lane == j ? dj * inv : (lane > j ? lij : 0.f);
     if (lane == j) rinv = inv;
   }
   return bad;
+}
+
+// Panel rows L_rp = A_rp L_pp^{-T} by substitution, NR rows per warp at
+// once (lane k holds entry k of each row; the same operations per row
+// whatever NR, so every CTA that solves a row gets the same values).
+template <int NR>
+__device__ __forceinline__ void panel_row_solve(float (&v)[NR], const float (*D)[IR_B + 1],
+                                                const float *rinv, int m, int lane) {
+  for (int k = 0; k < m; ++k) {
+    const float rk = rinv[k], dk = D[lane][k];
+    const bool upd = lane > k && lane < m;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (lane == k) v[r] = v[r] * rk;
+      const float lk = __shfl_sync(0xffffffffu, v[r], k);
+      if (upd) v[r] = fmaf(-dk, lk, v[r]);
+    }
+  }
 }
 
 // Factor the diagonal block staged in S ([32][33], lower triangle valid for
@@ -254,6 +279,9 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   const int64_t n = a.n;
   const int nb = (int)((n + IR_B - 1) / IR_B);
   float *L = a.L;
+  // grid barrier instances passed (the same sequence in every CTA)
+  unsigned ep = 0;
+  auto gsync = [&]() -> bool { ++ep; return cc_sync_ep(a.bar, a.status, ep * (unsigned)G); };
 
   // (0) FP32 copy of the lower triangle (diagonal block 0 excepted) and
   // Li cleared; CTA 0 factors diagonal block 0 straight from A and publishes
@@ -279,17 +307,36 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     __syncwarp();
     warp_factor_publish(S, m0, colb_s, L, n, 0, a.dg, lane);
   }
-  if (!cc_grid_sync(a.bar, a.status)) return;
+  if (!gsync()) return;
 
-  // (1) FP32 right-looking Cholesky
-  const bool la = G > 1;  // CTA 0 keeps the next diagonal block to itself
+  // (1) FP32 right-looking Cholesky.  With look-ahead CTA 0 solves the
+  // panel rows of the next diagonal block itself, joins the first barrier
+  // of the panel without waiting at it, updates and factors that block and
+  // publishes it before the second barrier; the other CTAs solve the panel
+  // rows (the same arithmetic, so the same values) and update the rest of
+  // the trailing matrix.
+  const bool la = G > 1;
+  const int Gr = la ? G - 1 : G;               // CTAs that solve panel rows
+  const int gr = la ? g - 1 : g;
   for (int p = 0; p < nb; ++p) {
     const int64_t c0 = (int64_t)p * IR_B;
     const int m = (int)min64(IR_B, n - c0);
     const int64_t r0 = c0 + m;
-    // this warp's first panel row is requested before the published block
-    const int64_t rfirst = r0 + (int64_t)g * (IR_THREADS / 32) + warp;
-    const float vfirst = (rfirst < n && lane < m) ? L[rfirst * n + c0 + lane] : 0.f;
+    const int64_t tr = n - r0;
+    const int m1 = (int)min64(IR_B, tr);     // size of the next diagonal block
+    const bool look = la && g == 0;
+    // panel rows are requested before the published block
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t rfirst = r0 + (int64_t)gr * (IR_THREADS / 32) + warp;
+    if (look) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = warp + 8 * q;
+        v[q] = (row < m1 && lane < m) ? L[(r0 + row) * n + c0 + lane] : 0.f;
+      }
+    } else {
+      v[0] = (rfirst < n && lane < m) ? L[rfirst * n + c0 + lane] : 0.f;
+    }
     {
       const float *dgp = a.dg + (p & 1) * IR_DG;
       for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) D[e >> 5][e & 31] = __ldcg(dgp + e);
@@ -301,37 +348,23 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       if (g == 0 && tid == 0) *a.need_fp64 = 1;
       return;
     }
-    // panel rows below the diagonal block: L_rp = A_rp L_pp^{-T}
-    for (int64_t r = rfirst; r < n; r += (int64_t)G * (IR_THREADS / 32)) {
-      float v = r == rfirst ? vfirst : (lane < m ? L[r * n + c0 + lane] : 0.f);
-      for (int k = 0; k < m; ++k) {
-        if (lane == k) v *= rinv[k];
-        const float lk = __shfl_sync(0xffffffffu, v, k);
-        if (lane > k && lane < m) v -= D[lane][k] * lk;
-      }
-      if (lane < m) L[r * n + c0 + lane] = v;
-    }
-    if (!cc_grid_sync(a.bar, a.status)) return;
-    const int64_t tr = n - r0;
-    const int m1 = (int)min64(IR_B, tr);  // size of the next diagonal block
-    if (tr > 0) {
-      const int nt = (int)((tr + IR_B - 1) / IR_B);
-      const int ntiles = nt * (nt + 1) / 2;
-      if (la && g == 0) {
-        // tile (0, 0) of the trailing matrix (the next diagonal block),
-        // CTA-wide, its result also staged in S
-        for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-          const int rr = e / IR_B, k = e % IR_B;
-          ta[rr * TS + k] = (rr < m1 && k < m) ? L[(r0 + rr) * n + c0 + k] : 0.f;
-        }
-        const int tx = tid % 32, ty = tid / 32;
-        float old[4];
+    if (look) {
+      const int tx = tid % 32, ty = tid / 32;
+      float old[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = ty + 8 * q;
-          old[q] = (i < m1 && tx <= i) ? L[(r0 + i) * n + r0 + tx] : 0.f;
-        }
-        __syncthreads();
+      for (int q = 0; q < 4; ++q) {
+        const int i = ty + 8 * q;
+        old[q] = (i < m1 && tx <= i) ? L[(r0 + i) * n + r0 + tx] : 0.f;
+      }
+      if (tr > 0) {
+        panel_row_solve<4>(v, D, rinv, m, lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ta[(warp + 8 * q) * TS + lane] = v[q];
+      }
+      ++ep;
+      cc_arrive(a.bar);  // first barrier of the panel, not awaited
+      if (tr > 0) {
+        // tile (0, 0) of the trailing matrix from the rows just solved
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
         for (int k = 0; k < IR_B; ++k) {
@@ -340,87 +373,96 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
           for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = ty + 8 * q;
-          S[i * TS + tx] = old[q] - acc[q];  // the factor writes the block back to L
-        }
-      } else if constexpr (!WT) {
-        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA (with
-        // look-ahead, tiles 1.. over CTAs 1..)
-        const int cta0 = la ? 1 : 0;
-        for (int t = g; t < ntiles; t += G - cta0) {
-          int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-          while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-          while (ti * (ti + 1) / 2 > t) --ti;
-          const int tj = t - ti * (ti + 1) / 2;
-          const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
-          __syncthreads();
-          for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-            const int rr = e / IR_B, k = e % IR_B;
-            ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
-            tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
-          }
-          __syncthreads();
-          // 4 outputs per thread: rows ty + 8q, column tx
-          const int tx = tid % 32, ty = tid / 32;
-          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < 4; ++q) S[(ty + 8 * q) * TS + tx] = old[q] - acc[q];
+        __syncthreads();
+        if (warp == 0)
+          warp_factor_publish(S, m1, colb_s, L, n, r0, a.dg + ((p + 1) & 1) * IR_DG, lane);
+      }
+    } else {
+      // panel rows below the diagonal block: L_rp = A_rp L_pp^{-T}
+      for (int64_t r = rfirst; r < n; r += (int64_t)Gr * (IR_THREADS / 32)) {
+        float w[1] = {r == rfirst ? v[0] : (lane < m ? L[r * n + c0 + lane] : 0.f)};
+        panel_row_solve<1>(w, D, rinv, m, lane);
+        if (lane < m) L[r * n + c0 + lane] = w[0];
+      }
+      if (!gsync()) return;
+      if (tr > 0) {
+        const int nt = (int)((tr + IR_B - 1) / IR_B);
+        const int ntiles = nt * (nt + 1) / 2;
+        const int cta0 = la ? 1 : 0;  // with look-ahead tile 0 is CTA 0's
+        if constexpr (!WT) {
+          // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA
+          for (int t = gr + cta0; t < ntiles; t += Gr) {
+            int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while (ti * (ti + 1) / 2 > t) --ti;
+            const int tj = t - ti * (ti + 1) / 2;
+            const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+            __syncthreads();
+            for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
+              const int rr = e / IR_B, k = e % IR_B;
+              ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
+              tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+            }
+            __syncthreads();
+            // 4 outputs per thread: rows ty + 8q, column tx
+            const int tx = tid % 32, ty = tid / 32;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-          for (int k = 0; k < IR_B; ++k) {
-            const float bv = tb[tx * TS + k];
+            for (int k = 0; k < IR_B; ++k) {
+              const float bv = tb[tx * TS + k];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
+              for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+              if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+            }
           }
+        } else {
+          // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile of the lower
+          // triangle per warp
+          float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
+          const int64_t gwarp = (int64_t)gr * (IR_THREADS / 32) + warp + cta0;
+          for (int64_t t = gwarp; t < ntiles; t += (int64_t)Gr * (IR_THREADS / 32)) {
+            int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while (ti * (ti + 1) / 2 > t) --ti;
+            const int tj = (int)(t - ti * (ti + 1) / 2);
+            const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+            __syncwarp();
+            warp_stage(sA, L, n, i0, c0, n, n, c0 + m, lane);
+            warp_stage(sB, L, n, j0, c0, n, n, c0 + m, lane);
+            __syncwarp();
+            float acc[IR_B];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
-            if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+            for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
+            warp_tile_fma<true>(sA, sB, lane, acc);
+            const int64_t j = j0 + lane;
+#pragma unroll
+            for (int i = 0; i < IR_B; ++i) {
+              const int64_t ii = i0 + i;
+              if (ii < n && j < n && j <= ii) L[ii * n + j] -= acc[i];
+            }
           }
         }
-      } else {
-        // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile of the lower
-        // triangle per warp (with look-ahead, tiles 1.. over CTAs 1..)
-        float *sA = wtile + warp * 2 * IR_B * WS, *sB = sA + IR_B * WS;
-        const int cta0 = la ? 1 : 0;
-        const int64_t gwarp = (int64_t)(g - cta0) * (IR_THREADS / 32) + warp + cta0;
-        for (int64_t t = gwarp; t < ntiles; t += (int64_t)(G - cta0) * (IR_THREADS / 32)) {
-          int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-          while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-          while (ti * (ti + 1) / 2 > t) --ti;
-          const int tj = (int)(t - ti * (ti + 1) / 2);
-          const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
-          __syncwarp();
-          warp_stage(sA, L, n, i0, c0, n, n, c0 + m, lane);
-          warp_stage(sB, L, n, j0, c0, n, n, c0 + m, lane);
-          __syncwarp();
-          float acc[IR_B];
+        if (!la) {  // one CTA: it updated the next diagonal block itself
+          __syncthreads();
+          if (warp == 0) {
+            float st[IR_B];
 #pragma unroll
-          for (int i = 0; i < IR_B; ++i) acc[i] = 0.f;
-          warp_tile_fma<true>(sA, sB, lane, acc);
-          const int64_t j = j0 + lane;
+            for (int r = 0; r < IR_B; ++r)
+              st[r] = (r < m1 && lane <= r) ? L[(r0 + r) * n + r0 + lane] : 0.f;
 #pragma unroll
-          for (int i = 0; i < IR_B; ++i) {
-            const int64_t ii = i0 + i;
-            if (ii < n && j < n && j <= ii) L[ii * n + j] -= acc[i];
+            for (int r = 0; r < IR_B; ++r) S[r * TS + lane] = st[r];
+            __syncwarp();
+            warp_factor_publish(S, m1, colb_s, L, n, r0, a.dg + ((p + 1) & 1) * IR_DG, lane);
           }
         }
       }
     }
-    if (g == 0) {
-      __syncthreads();
-      if (warp == 0 && tr > 0) {
-        if (!la) {  // CTA 0 updated the block among all the others: stage it
-          float v[IR_B];
-#pragma unroll
-          for (int r = 0; r < IR_B; ++r)
-            v[r] = (r < m1 && lane <= r) ? L[(r0 + r) * n + r0 + lane] : 0.f;
-#pragma unroll
-          for (int r = 0; r < IR_B; ++r) S[r * TS + lane] = v[r];
-          __syncwarp();
-        }
-        warp_factor_publish(S, m1, colb_s, L, n, r0, a.dg + ((p + 1) & 1) * IR_DG, lane);
-      }
-    }
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
   }
   // diagonal blocks of the inverse, one block per CTA
   for (int blk = g; blk < nb; blk += G) {
@@ -434,7 +476,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     __syncthreads();
     if (warp == 0) warp_tri_inverse(D, m, a.Li, n, c0, lane);
   }
-  if (!cc_grid_sync(a.bar, a.status)) return;
+  if (!gsync()) return;
 
   // (2) explicit inverse of the FP32 factor by recursive doubling: the
   //     diagonal 32x32 blocks are inverted above; per level, for every pair
@@ -556,7 +598,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
         }
       }
       }
-      if (!cc_grid_sync(a.bar, a.status)) return;
+      if (!gsync()) return;
     }
   }
 
@@ -565,7 +607,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     a.r[i] = a.b[i];
     a.x[i] = 0.0;
   }
-  if (!cc_grid_sync(a.bar, a.status)) return;
+  if (!gsync()) return;
   const int64_t nwarps = (int64_t)G * (IR_THREADS / 32);
   const int64_t gw = (int64_t)g * (IR_THREADS / 32) + warp;
   constexpr int CH = 64;  // rows per partial sum of the transposed product
@@ -581,7 +623,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       // (forward) or columns (backward) still to come.
       for (int64_t i = (int64_t)g * IR_THREADS + tid; i < n; i += (int64_t)G * IR_THREADS)
         a.wv[i] = (float)a.r[i];
-      if (!cc_grid_sync(a.bar, a.status)) return;
+      if (!gsync()) return;
       for (int p = 0; p < nb; ++p) {  // forward: L w = r
         const int64_t c0 = (int64_t)p * IR_B;
         const int m = (int)min64(IR_B, n - c0);
@@ -599,7 +641,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
           if (lane == 0) a.wv[i] -= t;
         }
-        if (!cc_grid_sync(a.bar, a.status)) return;
+        if (!gsync()) return;
       }
       for (int p = nb - 1; p >= 0; --p) {  // backward: L^T d = w (w in dv)
         const int64_t c0 = (int64_t)p * IR_B;
@@ -619,7 +661,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
           for (int i = 0; i < m; ++i) t = fmaf(L[(c0 + i) * n + j], sw_s[i], t);
           a.dv[j] -= t;
         }
-        if (!cc_grid_sync(a.bar, a.status)) return;
+        if (!gsync()) return;
       }
     } else {
     // w = Li r (one warp per row)
@@ -632,7 +674,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
       if (lane == 0) a.wv[i] = sacc;
     }
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
     // partial sums of Li^T w over 64-row chunks: (chunk, 32-column block) per warp
     const int64_t ncb = (n + 31) / 32;
     for (int64_t u = gw; u < nch * ncb; u += nwarps) {
@@ -647,14 +689,14 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       }
       if (j < n) a.dpart[ch * n + j] = sacc;
     }
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
     for (int64_t j = (int64_t)g * IR_THREADS + tid; j < n; j += (int64_t)G * IR_THREADS) {
       float d = 0.f;
 #pragma unroll 8
       for (int64_t ch = j / CH; ch < nch; ++ch) d += a.dpart[ch * n + j];
       a.x[j] += (double)d;
     }
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
     }
     // r = b - A x in FP64; partial max |r_i|, max |x_i| and (first sweep) max
     // row sum |A|
@@ -688,7 +730,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       }
       a.part[(size_t)g * 4 + 0] = m0; a.part[(size_t)g * 4 + 1] = m1; a.part[(size_t)g * 4 + 2] = m2;
     }
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
     // maxima over the CTAs' partials: all loads in flight at once (max is
     // exact, so the grouping does not matter)
     {
@@ -715,7 +757,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     if (it == 0) normA = an;
     converged = rn <= sqrt((double)n) * 1.1102230246251565e-16 * normA * xn;
     // every CTA has read part[] before anyone overwrites it in the next sweep
-    if (!cc_grid_sync(a.bar, a.status)) return;
+    if (!gsync()) return;
   }
   if (!converged && g == 0 && tid == 0) *a.need_fp64 = 1;
 }
