@@ -293,10 +293,15 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   __shared__ __align__(16) float colb_s[2 * IR_B];
   float *S = wtile + 2 * IR_B * TS;  // [32][33] staging of a diagonal block
   const int m0 = (int)min64(IR_B, n);
-  for (int64_t e = (int64_t)g * IR_THREADS + tid; e < n * n; e += (int64_t)G * IR_THREADS) {
-    const int64_t i = e / n, j = e - i * n;
-    a.Li[e] = 0.f;
-    if (j <= i && i >= m0) L[e] = (float)a.A[e];
+  for (int64_t i = g; i < n; i += G) {  // one row per CTA at a time, no division
+    const double *Ai = a.A + i * n;
+    float *Lr = L + i * n, *Lir = a.Li + i * n;
+    if (i >= m0) {
+#pragma unroll 4
+      for (int64_t j = tid; j <= i; j += IR_THREADS) Lr[j] = (float)Ai[j];
+    }
+#pragma unroll 4
+    for (int64_t j = tid; j < n; j += IR_THREADS) Lir[j] = 0.f;
   }
   if (g == 0 && warp == 0) {
     float v[IR_B];
@@ -339,9 +344,18 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     }
     {
       const float *dgp = a.dg + (p & 1) * IR_DG;
-      for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) D[e >> 5][e & 31] = __ldcg(dgp + e);
-      if (tid < IR_B) rinv[tid] = __ldcg(dgp + IR_B * IR_B + tid);
-      if (tid == 0) flag_s = __float_as_int(__ldcg(dgp + IR_B * IR_B + IR_B));
+      float dv[IR_B * IR_B / IR_THREADS];
+#pragma unroll
+      for (int q = 0; q < IR_B * IR_B / IR_THREADS; ++q) dv[q] = __ldcg(dgp + tid + q * IR_THREADS);
+      const float rv = tid < IR_B ? __ldcg(dgp + IR_B * IR_B + tid) : 0.f;
+      const float fv = tid == 0 ? __ldcg(dgp + IR_B * IR_B + IR_B) : 0.f;
+#pragma unroll
+      for (int q = 0; q < IR_B * IR_B / IR_THREADS; ++q) {
+        const int e = tid + q * IR_THREADS;
+        D[e >> 5][e & 31] = dv[q];
+      }
+      if (tid < IR_B) rinv[tid] = rv;
+      if (tid == 0) flag_s = __float_as_int(fv);
     }
     __syncthreads();
     if (flag_s) {  // identical in every CTA: the FP64 factorisation takes over
@@ -398,11 +412,20 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
             while (ti * (ti + 1) / 2 > t) --ti;
             const int tj = t - ti * (ti + 1) / 2;
             const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+            // all eight loads of a thread in flight before the first store
+            float va[4], vb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = (tid >> 5) + 8 * q, k = tid & 31;
+              va[q] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
+              vb[q] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+            }
             __syncthreads();
-            for (int e = tid; e < IR_B * IR_B; e += IR_THREADS) {
-              const int rr = e / IR_B, k = e % IR_B;
-              ta[rr * TS + k] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
-              tb[rr * TS + k] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = (tid >> 5) + 8 * q, k = tid & 31;
+              ta[rr * TS + k] = va[q];
+              tb[rr * TS + k] = vb[q];
             }
             __syncthreads();
             // 4 outputs per thread: rows ty + 8q, column tx
