@@ -72,14 +72,36 @@ __device__ __forceinline__ bool cc_grid_sync(unsigned *bar, int32_t *status) {
 
 // Grid barrier with an explicit instance count, for kernels in which a CTA
 // may join an instance without waiting for it: instance e (0-based) is
-// complete once the counter reaches (e + 1) G, whatever the order of the
-// arrivals.  cc_arrive joins an instance and returns at once (the caller
-// must not read what the other CTAs write before that instance);
-// cc_sync_ep joins one and waits for it, which implies every earlier one.
+// complete once the counter reaches (e + 1) G.  cc_arrive joins an instance
+// and returns at once (the caller must not read what the other CTAs write
+// before that instance); cc_wait_ep waits for an instance already joined;
+// cc_sync_ep joins one and waits for it.  A CTA must see an instance
+// complete before it joins the next one: otherwise its arrival at the next
+// instance would count in place of a CTA still missing from the current one.
 // The same bounded acquire polling as cc_grid_sync.
 __device__ __forceinline__ void cc_arrive(unsigned *bar) {
   __syncthreads();
   if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool cc_wait_ep(unsigned *bar, int32_t *status, unsigned target) {
+  __shared__ int okw_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+    unsigned long long it = 0;
+    while ((int)(v - target) < 0) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (++it > (1ull << 23)) {
+        atomicCAS(reinterpret_cast<int *>(status), 0, (int)NQS_ERR_TIMEOUT);
+        break;
+      }
+    }
+    okw_s = *reinterpret_cast<volatile int32_t *>(status) == 0;
+  }
+  __syncthreads();
+  return okw_s != 0;
 }
 
 __device__ __forceinline__ bool cc_sync_ep(unsigned *bar, int32_t *status, unsigned target) {

@@ -392,6 +392,8 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
         if (warp == 0)
           warp_factor_publish(S, m1, colb_s, L, n, r0, a.dg + ((p + 1) & 1) * IR_DG, lane);
       }
+      // the first barrier must be complete before CTA 0 joins the second
+      if (!cc_wait_ep(a.bar, a.status, ep * (unsigned)G)) return;
     } else {
       // panel rows below the diagonal block: L_rp = A_rp L_pp^{-T}
       for (int64_t r = rfirst; r < n; r += (int64_t)Gr * (IR_THREADS / 32)) {
@@ -405,42 +407,65 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
         const int ntiles = nt * (nt + 1) / 2;
         const int cta0 = la ? 1 : 0;  // with look-ahead tile 0 is CTA 0's
         if constexpr (!WT) {
-          // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA
-          for (int t = gr + cta0; t < ntiles; t += Gr) {
-            int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-            while (ti * (ti + 1) / 2 > t) --ti;
-            const int tj = t - ti * (ti + 1) / 2;
-            const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
-            // all eight loads of a thread in flight before the first store
-            float va[4], vb[4];
+          // trailing update A_ij -= L_ip L_jp^T, one 32x32 tile per CTA at a
+          // time; a CTA's tiles go in batches of TB whose loads (operands
+          // and the outputs' old values) are all in flight together, then
+          // are multiplied back to back
+          constexpr int TB = 4;
+          const int tx = tid % 32, ty = tid / 32;
+          for (int tb0 = gr + cta0; tb0 < ntiles; tb0 += TB * Gr) {
+            float va[TB][4], vb[TB][4], vc[TB][4];
+            int64_t i0s[TB], j0s[TB];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = (tid >> 5) + 8 * q, k = tid & 31;
-              va[q] = (i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
-              vb[q] = (j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+            for (int b = 0; b < TB; ++b) {
+              const int t = tb0 + b * Gr;
+              int ti = 0, tj = 0;
+              if (t < ntiles) {
+                ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+                while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+                while (ti * (ti + 1) / 2 > t) --ti;
+                tj = t - ti * (ti + 1) / 2;
+              }
+              const int64_t i0 = r0 + (int64_t)ti * IR_B, j0 = r0 + (int64_t)tj * IR_B;
+              i0s[b] = t < ntiles ? i0 : n;  // n: nothing to do
+              j0s[b] = j0;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int rr = ty + 8 * q, k = tx;
+                va[b][q] = (t < ntiles && i0 + rr < n && k < m) ? L[(i0 + rr) * n + c0 + k] : 0.f;
+                vb[b][q] = (t < ntiles && j0 + rr < n && k < m) ? L[(j0 + rr) * n + c0 + k] : 0.f;
+                const int64_t i = i0 + rr, j = j0 + k;
+                vc[b][q] = (t < ntiles && i < n && j < n && j <= i) ? L[i * n + j] : 0.f;
+              }
+            }
+            __syncthreads();  // the previous batch is no longer read
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+              float *sa = wtile + b * 2 * IR_B * TS, *sb = sa + IR_B * TS;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                sa[(ty + 8 * q) * TS + tx] = va[b][q];
+                sb[(ty + 8 * q) * TS + tx] = vb[b][q];
+              }
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = (tid >> 5) + 8 * q, k = tid & 31;
-              ta[rr * TS + k] = va[q];
-              tb[rr * TS + k] = vb[q];
-            }
-            __syncthreads();
-            // 4 outputs per thread: rows ty + 8q, column tx
-            const int tx = tid % 32, ty = tid / 32;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int b = 0; b < TB; ++b) {
+              if (i0s[b] >= n) continue;  // uniform over the CTA
+              const float *sa = wtile + b * 2 * IR_B * TS, *sb = sa + IR_B * TS;
+              // 4 outputs per thread: rows ty + 8q, column tx
+              float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-            for (int k = 0; k < IR_B; ++k) {
-              const float bv = tb[tx * TS + k];
+              for (int k = 0; k < IR_B; ++k) {
+                const float bv = sb[tx * TS + k];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc[q] = fmaf(ta[(ty + 8 * q) * TS + k], bv, acc[q]);
-            }
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(sa[(ty + 8 * q) * TS + k], bv, acc[q]);
+              }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
-              if (i < n && j < n && j <= i) L[i * n + j] -= acc[q];
+              for (int q = 0; q < 4; ++q) {
+                const int64_t i = i0s[b] + ty + 8 * q, j = j0s[b] + tx;
+                if (i < n && j < n && j <= i) L[i * n + j] = vc[b][q] - acc[q];
+              }
             }
           }
         } else {
