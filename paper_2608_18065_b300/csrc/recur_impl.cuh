@@ -17,18 +17,26 @@ namespace nqs {
     default: return cudaErrorInvalidValue;                \
   }
 
+// Unit groups of the sampling / given-configuration sweeps: the FP32 d_h = 64
+// sweep runs two hidden units per thread (eight warps per CTA) instead of
+// four, the others the default tile.
+template <typename T, int DH> constexpr int sample_groups() {
+  return (sizeof(T) == 4 && DH == 64) ? 32 : 0;
+}
+
 // Shared memory above this leaves the large weight blocks in global memory.
 constexpr size_t SMEM_STAGE_LIMIT = 200 * 1024;
 
-template <typename T, int DH, int DIM, int RT, int RG, int MODE>
+template <typename T, int DH, int DIM, int RT, int RG, int MODE, int UGX = 0>
 static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStream_t st) {
   constexpr int R = RT * RG;
-  auto kern = k_forward<T, DH, DIM, RT, RG, MODE, true>;
+  constexpr int UG = UGX ? UGX : Tile<DH>::UG;
+  auto kern = k_forward<T, DH, DIM, RT, RG, MODE, true, UGX>;
   size_t smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, true);
   if constexpr (DH >= 96) {
     if (smem > SMEM_STAGE_LIMIT) {
       smem = fwd_smem_bytes<T, DH, DIM, R>(d.N, false);
-      kern = k_forward<T, DH, DIM, RT, RG, MODE, false>;
+      kern = k_forward<T, DH, DIM, RT, RG, MODE, false, UGX>;
     }
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -37,7 +45,7 @@ static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStr
   int grid = a.ntiles;
   if (MODE == MODE_ELOC) grid = grid < max_grid ? grid : max_grid;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, Tile<DH>::UG * RG, smem, st>>>(a);
+  kern<<<grid, UG * RG, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -45,9 +53,11 @@ template <typename T, int DH, int DIM>
 static cudaError_t fwd_dim(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, cudaStream_t st) {
   constexpr int ERT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
   if (mode == MODE_SAMPLE)
-    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_SAMPLE>(d, a, max_grid, st);
+    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_SAMPLE,
+                   sample_groups<T, DH>()>(d, a, max_grid, st);
   if (mode == MODE_GIVEN)
-    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_GIVEN>(d, a, max_grid, st);
+    return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_GIVEN,
+                   sample_groups<T, DH>()>(d, a, max_grid, st);
   return fwd_one<T, DH, DIM, ERT, Rows<T>::ELOC_RG, MODE_ELOC>(d, a, max_grid, st);
 }
 

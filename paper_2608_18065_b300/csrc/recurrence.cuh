@@ -156,10 +156,13 @@ inline size_t fwd_smem_bytes(int N, bool wsmem = true) {
 
 // WS: the two large weight blocks are staged in shared memory (otherwise they
 // are read through L1 from the packed copy in global memory).
-template <typename T, int DH, int DIM, int RT, int RG, int MODE, bool WS = true>
-__global__ void __launch_bounds__(Tile<DH>::UG * RG)
+// UGX: unit groups (lanes per row) when not Tile<DH>::UG; more groups give
+// each thread fewer hidden units and the CTA more warps per site.
+template <typename T, int DH, int DIM, int RT, int RG, int MODE, bool WS = true, int UGX = 0>
+__global__ void __launch_bounds__((UGX ? UGX : Tile<DH>::UG) * RG)
 k_forward(const FwdArgs<T> A) {
-  constexpr int UG = Tile<DH>::UG, UT = Tile<DH>::UT;
+  constexpr int UG = UGX ? UGX : Tile<DH>::UG, UT = DH / UG;
+  static_assert(UG * UT == DH && UG <= 32 && (UG & (UG - 1)) == 0, "unit groups");
   constexpr int R = RT * RG;
   constexpr int NTH = UG * RG;
   constexpr int DIN = DIM == 2 ? 4 : 2;
