@@ -19,13 +19,20 @@ template <int DH> struct Tile {
 };
 
 // n consecutive values from shared or global memory, as 16-byte vectors when
-// the element offset is a multiple of the vector width (callers guarantee
-// it: row/column offsets and leading dimensions are multiples of 4 floats
-// or 2 doubles whenever n is)
+// the element offset is a multiple of the vector width, else as float pairs
+// when n is even (callers guarantee it: row/column offsets and leading
+// dimensions are multiples of 4 floats or 2 doubles whenever n is, and even
+// whenever n is)
 template <typename T, int n>
 __device__ __forceinline__ void load_run(const T *__restrict__ p, T (&v)[n]) {
   constexpr int VW = 16 / (int)sizeof(T);
-  if constexpr (n % VW == 0) {
+  if constexpr (sizeof(T) == 4 && n % VW != 0 && n % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < n / 2; ++q) {
+      const float2 t = reinterpret_cast<const float2 *>(p)[q];
+      v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+  } else if constexpr (n % VW == 0) {
 #pragma unroll
     for (int q = 0; q < n / VW; ++q) {
       if constexpr (sizeof(T) == 4) {
