@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-spectrum", action="store_true",
+                   help="skip the conditioning diagnostics of T (App. E)")
+    p.add_argument("--spectrum-steps", type=int, default=64,
+                   help="Lanczos steps of the conditioning diagnostics")
     p.add_argument("--no-graph", action="store_true", help="launch every kernel eagerly")
     return p.parse_args()
 
@@ -142,6 +146,45 @@ def load_traffic(kernel, sha, workload):
     if d and d.get("src_sha") == sha and d.get("workload") == workload:
         return d.get("bytes_per_launch")
     return None
+
+
+def spectrum_diagnostics(ctx, w, hp, th0, dev, m=64, reps=5):
+    """kappa_2(T + lambda I), lambda_max(T) and the reliable digits (App. E)
+    of the T of one eager step from theta_0 (nqs_spectrum, m Lanczos steps,
+    the step's own lambda), with the kernel's CUDA-event time over reps
+    back-to-back launches and the rate of its dominant traffic: one product
+    T v per Lanczos step, R^2 FP64 reads each (T stays resident in L2)."""
+    import ctypes as C
+    import torch
+    from paper_2608_18065_b300 import nqs
+    th = torch.tensor(th0, device=dev)
+    outs = ctx.step_outputs(hp.ns)
+    stats = ctx.minsr_step(th, torch.zeros_like(th), hp, 0, outputs=outs)
+    torch.cuda.synchronize()
+    lam = nqs.decode_stats(stats)["lam"]
+    T = outs["T"]
+    R = T.shape[0]
+    st = nqs.spectrum(T, lam, m=m)
+    lib = nqs.lib()
+    wb = lib.nqs_spectrum_workspace(R, m)
+    work = torch.empty(wb, dtype=torch.uint8, device=dev)
+    out = torch.zeros(C.sizeof(nqs.SpectrumStats), dtype=torch.uint8, device=dev)
+    args = (nqs._ptr(T), C.c_int64(R), C.c_double(lam), C.c_int(m), C.c_uint64(1),
+            nqs._ptr(work), C.c_size_t(wb), nqs._ptr(out), nqs._stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        nqs._check(lib.nqs_spectrum(*args))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    byts = st["iterations"] * R * R * 8
+    return {"kernel": "k_lanczos", "R": R, "m": m, "iterations": st["iterations"],
+            "lambda": lam, "lambda_max": st["lambda_max"],
+            "lambda_min_ritz": st["lambda_min_ritz"], "kappa": st["kappa"],
+            "digits_fp32": st["digits_fp32"], "digits_fp64": st["digits_fp64"],
+            "ritz_residual": st["residual"], "status": st["status"],
+            "ms": ms, "tv_bytes": byts, "tv_gbs": byts / (ms * 1e-3) / 1e9}
 
 
 def measured_peak(key, fallback):
@@ -492,6 +535,12 @@ def run_ours(args):
                 "speedup_mixed_over_fp64": (1000.0 / ms_step) / (1000.0 / f_ms)}
         del c64
 
+    # conditioning diagnostics of the step's T (App. E), outside the timed
+    # region: lambda_max by Lanczos, kappa_2 and the reliable digits
+    spec = None
+    if not args.no_spectrum and rank == 0:
+        spec = spectrum_diagnostics(ctx, w, hp, th0, dev, m=args.spectrum_steps)
+
     # matched energy error: both paths from theta_0 with the same seeds
     matched = None
     if args.matched_steps > 0 and rank == 0:
@@ -517,7 +566,7 @@ def run_ours(args):
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
                 "clocks": clk, "cuda_graph": graph_used, "fp64_path": fp64,
-                "matched_energy": matched,
+                "matched_energy": matched, "spectrum": spec,
                 "stage_ms": {k: v / max(nt, 1) for k, v in stage_ms.items()},
                 "final_stats": st}
         print(json.dumps(line))

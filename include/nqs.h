@@ -387,6 +387,47 @@ nqs_status nqs_logpsi_noalloc(const nqs_model_desc *model, const double *theta,
                               const uint8_t *spins, int64_t n, double *logpsi,
                               void *stream);
 
+/* ------------------------------------------------ spectrum diagnostics */
+
+/* Conditioning of the damped minSR system (App. E): T + lambda I has
+ * kappa_2 = (lambda_max(T) + lambda) / (lambda_min(T) + lambda), and
+ * d = -log10(kappa_2 eps) decimal digits survive a solve in a precision of
+ * machine epsilon eps (2^-23 FP32, 2^-52 FP64).  T, centred over the
+ * samples, has the all-ones vector of each real block in its null space, so
+ * lambda_min(T) = 0 and kappa_2 = 1 + lambda_max / lambda. */
+typedef struct {
+  double lambda_max;       /* largest eigenvalue of T (Lanczos Ritz value) */
+  double lambda_min_ritz;  /* smallest Ritz value: an upper bound on lambda_min(T) */
+  double kappa;            /* (lambda_max + lambda) / lambda: lambda_min(T) = 0 */
+  double digits_fp32;      /* -log10(kappa * 2^-23) */
+  double digits_fp64;      /* -log10(kappa * 2^-52) */
+  double residual;         /* |T y - lambda_max y| for the top Ritz pair */
+  int32_t iterations;      /* Lanczos steps taken (fewer than m when the
+                              Krylov space became invariant) */
+  int32_t status;          /* nqs_status of the device-side checks */
+} nqs_spectrum_stats;
+
+/* Bytes of device scratch that nqs_spectrum needs for an R x R matrix and at
+ * most m Lanczos steps. */
+size_t nqs_spectrum_workspace(int64_t R, int m);
+
+/* Extreme eigenvalues of the symmetric R x R FP64 matrix T (device,
+ * row-major, both triangles, e.g. the Gram matrix of nqs_gram or of a step's
+ * outputs; not modified) by m steps of Lanczos with full
+ * reorthogonalisation in FP64 (classical Gram-Schmidt applied twice), from
+ * a start vector of Philox uniforms of `seed`, then bisection on the
+ * tridiagonal matrix; one cooperative launch, deterministic.  lambda >= 0
+ * is the Tikhonov damping of the step.  work: device scratch of at least
+ * nqs_spectrum_workspace(R, m) bytes, 256-byte aligned, owned by the caller;
+ * out: device nqs_spectrum_stats written by the kernel.  Errors:
+ * NQS_ERR_ARG for R < 1, m < 1, m > 512, lambda < 0 or a NULL pointer,
+ * NQS_ERR_WORKSPACE if work_bytes is too small; out->status is
+ * NQS_ERR_NONFINITE if T holds non-finite values and NQS_ERR_TIMEOUT if a
+ * grid barrier timed out. */
+nqs_status nqs_spectrum(const double *T, int64_t R, double lambda, int m, uint64_t seed,
+                        void *work, size_t work_bytes, nqs_spectrum_stats *out,
+                        void *stream);
+
 /* ------------------------------------------------------- instrumentation */
 
 /* Stages timed by the step instrumentation, in step order. */

@@ -64,9 +64,16 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_destroy", "nqs_minsr_step_batched", "nqs_batch_set_graph",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
-           "nqs_set_damping",
+           "nqs_set_damping", "nqs_spectrum",
            "nqs_stage_name", "nqs_status_string"]
 TUNE_FORCE = 1
+
+
+class SpectrumStats(C.Structure):
+    _fields_ = [("lambda_max", C.c_double), ("lambda_min_ritz", C.c_double),
+                ("kappa", C.c_double), ("digits_fp32", C.c_double),
+                ("digits_fp64", C.c_double), ("residual", C.c_double),
+                ("iterations", C.c_int32), ("status", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -87,6 +94,8 @@ def lib():
         _lib.nqs_stage_name.restype = C.c_char_p
         for name in SYMBOLS[:-2]:
             getattr(_lib, name).restype = C.c_int
+        _lib.nqs_spectrum_workspace.restype = C.c_size_t
+        _lib.nqs_spectrum_workspace.argtypes = [C.c_int64, C.c_int]
     return _lib
 
 
@@ -414,3 +423,23 @@ class LogPsi(torch.autograd.Function):
 
 def logpsi(theta, spins, context):
     return LogPsi.apply(theta, spins, context)
+
+
+def spectrum(T, lam, m=64, seed=1, stream=None):
+    """Conditioning diagnostics of T + lam I (App. E) through nqs_spectrum:
+    lambda_max(T), the smallest Ritz value, kappa_2 = (lambda_max + lam)/lam
+    (lambda_min(T) = 0 for the centred Gram matrix), the reliable digits in
+    FP32 and FP64, the Ritz residual, the Lanczos steps and the device
+    status.  T: square contiguous FP64 CUDA tensor (not modified)."""
+    assert T.dtype == torch.float64 and T.is_cuda and T.is_contiguous()
+    R = T.shape[0]
+    wb = lib().nqs_spectrum_workspace(R, m)
+    if wb == 0:
+        raise NqsError("libnqs: invalid argument (spectrum size)")
+    work = torch.empty(wb, dtype=torch.uint8, device=T.device)
+    out = torch.zeros(C.sizeof(SpectrumStats), dtype=torch.uint8, device=T.device)
+    _check(lib().nqs_spectrum(_ptr(T), C.c_int64(R), C.c_double(lam), C.c_int(m),
+                              C.c_uint64(seed), _ptr(work), C.c_size_t(wb), _ptr(out),
+                              _stream(stream)))
+    st = SpectrumStats.from_buffer_copy(out.cpu().numpy().tobytes())
+    return {f: getattr(st, f) for f, _ in SpectrumStats._fields_}
