@@ -252,7 +252,9 @@ __global__ void k_split_bf16(const float *__restrict__ A, int64_t R, int64_t np,
 }
 
 // Centring and split in one pass (Algorithm 1 line 5): v = (O - mean)/sqrt(Ns)
-// with the difference O - mean taken in FP64 (the column means are FP64), then
+// with the difference O - mean formed from the column mean as an FP32 pair
+// (hi, lo) by an error-free TwoSum, i.e. the exact difference rounded to FP32
+// within one unit in the last place, without the FP64 pipe; then
 // hi = bf16(v), lo = bf16(v - hi) (v - hi is exact in FP32); columns up to
 // Kpad are zero.  Grid (column chunks, rows); each thread owns 8 consecutive
 // columns of one row and writes them as one 16-byte store per plane.
@@ -266,17 +268,28 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float x0, float x1) {
 
 __global__ void __launch_bounds__(CS_THREADS) k_center_split(
     const float *__restrict__ O, int64_t ns, int64_t np, int64_t Kpad,
-    const double *__restrict__ mean, float isq, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+    const float2 *__restrict__ mean, float isq, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
   const int64_t r = blockIdx.y;
   const int64_t k0 = ((int64_t)blockIdx.x * CS_THREADS + threadIdx.x) * CS_COLS;
   if (k0 >= Kpad) return;
   const float *orow = O + r * np;
-  const double *mrow = mean + (r / ns) * np;
+  const float2 *mrow = mean + (r / ns) * np;
   float v[CS_COLS];
 #pragma unroll
   for (int j = 0; j < CS_COLS; ++j) {
     const int64_t k = k0 + j;
-    v[j] = k < np ? (float)((double)orow[k] - mrow[k]) * isq : 0.f;
+    float d = 0.f;
+    if (k < np) {
+      // o - (m_hi + m_lo): TwoSum of o and -m_hi (exact error e), then the
+      // low-order terms: the FP32 rounding of the exact difference to within
+      // one unit in the last place, on the FP32 pipe
+      const float o = orow[k];
+      const float2 m = mrow[k];
+      const float s = o - m.x, bb = s - o;
+      const float e = (o - (s - bb)) + (-m.x - bb);
+      d = s + (e - m.y);
+    }
+    v[j] = d * isq;
   }
   uint32_t hp[4], lp[4];
 #pragma unroll
@@ -479,7 +492,7 @@ cudaError_t gram_tc_from_split(const void *hi, const void *lo, int64_t R, int64_
   return cudaGetLastError();
 }
 
-cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const double *mean,
+cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const float2 *mean,
                          void *scratch, cudaStream_t st) {
   const int64_t Kpad = kpad_of(np);
   __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(scratch);

@@ -18,8 +18,9 @@ size_t gram_tc_split_bytes(int64_t R, int64_t np);
 cudaError_t gram_tc_bf16x3(const float *A, int64_t R, int64_t np, double *T, void *scratch,
                            int *err, cudaStream_t st);
 // Step path: centre O (FP32, rows = Re block then Im block of ns samples) with
-// FP64 column means, scale by 1/sqrt(ns), split into the scratch planes ...
-cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const double *mean,
+// the column means as FP32 pairs (hi, lo), scale by 1/sqrt(ns), split into
+// the scratch planes ...
+cudaError_t center_split(const float *O, int64_t ns, int64_t np, int64_t R, const float2 *mean,
                          void *scratch, cudaStream_t st);
 // ... T from those planes (splits: K-slices per output tile, 0 = built-in
 // plan, capped at gram_tc_max_splits) ...

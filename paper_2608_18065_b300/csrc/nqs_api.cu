@@ -675,10 +675,10 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     dim3 g((unsigned)((np + 255) / 256), nblk * chunks);
     k_colsum_part<T><<<g, 256, 0, st>>>(O, ns, np, chunks, W<double>(c, c->off.part));
     k_colmean_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
-        W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean));
+        W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean), tc ? 1 : 0);
     CU(cudaGetLastError());
     if (tc) {
-      CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<double>(c, c->off.mean),
+      CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<float2>(c, c->off.mean),
                       c->ws + c->off.split, st));
     } else {
       const int64_t tot = R * np;

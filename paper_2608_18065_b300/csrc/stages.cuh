@@ -136,8 +136,12 @@ __global__ void k_energy(const double *__restrict__ eloc, int64_t ns, int N, int
 
 // ---------------------------------------------------------- centring
 // Column means over the Ns samples of each block (real rows, imaginary
-// rows), accumulated in FP64: partial sums over 64-row chunks (grid.y =
-// block * chunks + chunk), then one pass that adds the chunks.
+// rows): partial sums over 64-row chunks (grid.y = block * chunks + chunk),
+// then one pass that adds the chunks in FP64.  FP64 data is summed in FP64;
+// FP32 data is summed in FP32 with Knuth's error-free TwoSum on every term
+// (the rounding error of each addition is recovered exactly and carried in
+// a second FP32 word), which keeps the chunk sum to about twice FP32's
+// precision without the FP64 pipe (64 times slower than FP32 on this part).
 constexpr int COL_ROWS = 64;
 template <typename T>
 __global__ void k_colsum_part(const T *__restrict__ O, int64_t ns, int64_t np, int chunks,
@@ -147,19 +151,39 @@ __global__ void k_colsum_part(const T *__restrict__ O, int64_t ns, int64_t np, i
   const int blk = blockIdx.y / chunks, ch = blockIdx.y % chunks;
   const int64_t r0 = (int64_t)ch * COL_ROWS, r1 = min64(ns, r0 + COL_ROWS);
   const T *B = O + (int64_t)blk * ns * np;
-  double acc = 0.0;
-  for (int64_t s = r0; s < r1; ++s) acc += (double)B[s * np + p];
-  part[(int64_t)blockIdx.y * np + p] = acc;
+  if constexpr (sizeof(T) == 4) {
+    float sum = 0.f, err = 0.f;
+#pragma unroll 8
+    for (int64_t s = r0; s < r1; ++s) {
+      const float x = B[s * np + p];
+      const float t = sum + x, z = t - sum;
+      err += (sum - (t - z)) + (x - z);
+      sum = t;
+    }
+    part[(int64_t)blockIdx.y * np + p] = (double)sum + (double)err;
+  } else {
+    double acc = 0.0;
+    for (int64_t s = r0; s < r1; ++s) acc += (double)B[s * np + p];
+    part[(int64_t)blockIdx.y * np + p] = acc;
+  }
 }
 
+// pairs: store each mean as the FP32 pair (hi, lo) with hi + lo = mean to
+// about 2^-48 relative (for the FP32 centring), else as an FP64 value.
 __global__ void k_colmean_fin(const double *__restrict__ part, int64_t ns, int64_t np, int chunks,
-                              double *mean) {
+                              double *mean, int pairs) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= np) return;
   const int blk = blockIdx.y;
   double acc = 0.0;
   for (int c = 0; c < chunks; ++c) acc += part[((int64_t)blk * chunks + c) * np + p];
-  mean[(int64_t)blk * np + p] = acc / (double)ns;
+  const double m = acc / (double)ns;
+  if (pairs) {
+    const float hi = (float)m;
+    reinterpret_cast<float2 *>(mean)[(int64_t)blk * np + p] = make_float2(hi, (float)(m - (double)hi));
+  } else {
+    mean[(int64_t)blk * np + p] = m;
+  }
 }
 
 // O' = (O - mean) / sqrt(Ns), in FP64 arithmetic, stored back in T.
