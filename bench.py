@@ -201,8 +201,10 @@ def measured_peak(key, fallback):
 
 
 def eloc_tc_used(model, precision):
-    """The connected-configuration engine runs on tcgen05 for mixed 1D, dh=64."""
-    return precision == "mixed" and model.dim == 1 and model.dh == 64
+    """The connected-configuration engine runs on tcgen05 for mixed 1D chains
+    of hidden size 64, and 32 (run with its units padded to 64: the issued
+    tensor work per site is that of 64)."""
+    return precision == "mixed" and model.dim == 1 and model.dh in (32, 64)
 
 
 def eloc_roofline(w, ms, sites=None):
@@ -220,7 +222,7 @@ def eloc_roofline(w, ms, sites=None):
     dh = w.model.dh
     alg = sites * site_flops(w.model)
     if eloc_tc_used(w.model, w.precision):
-        fl = sites * 3 * 2 * dh * 3 * dh
+        fl = sites * 3 * 2 * 64 * 3 * 64
         peak, src = measured_peak("bf16_tflops_sustained", 1400.0)
         ach = fl / (ms * 1e-3) / 1e12
         sha = src_sha("paper_2608_18065_b300/csrc/eloc_tc.cu", "paper_2608_18065_b300/csrc/tc_common.cuh")

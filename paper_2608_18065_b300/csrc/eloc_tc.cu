@@ -164,6 +164,8 @@ __device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, 
   *reinterpret_cast<__nv_bfloat16 *>(lo + off) = __float2bfloat16_rn(w - __bfloat162float(h));
 }
 
+// DHM: the model's hidden size (64, or 32 run with zero-padded units)
+template <int DHM>
 __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
@@ -190,25 +192,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   __syncthreads();
   // weights B[n][k], split into BF16 planes with the 128-byte swizzle:
   // n < 192: W_g[a][k] (n = 3a + g); 192 + j: head row j; rest zero
+  // a model of hidden size dhm < 64 runs with its units padded by zero
+  // weights: a padded unit's state stays 0 (c = tanh(0), h' = 0) and adds
+  // nothing to the other units or the heads, so the values are unchanged
+  constexpr int dhm = DHM, ngm = 3 * DHM;
   for (int e = tid; e < NB * DH; e += THREADS) {
     const int n = e / DH, k = e % DH;
     float w = 0.f;
-    if (n < NG) w = a.pack[a.oWgT + k * NG + n];
-    else if (n - NG < nh) w = a.pack[a.ohead + (n - NG) * DH + k];
+    if (n < NG) {
+      if (n / 3 < dhm && k < dhm) w = a.pack[a.oWgT + k * ngm + n];
+    } else if (n - NG < nh && k < dhm) {
+      w = a.pack[a.ohead + (n - NG) * dhm + k];
+    }
     put_split(Bhi, Blo, sw128_off(n, k), w);
   }
   // augmented rows: column 0 the bias of gate n, columns 1, 2 the one-hot
   // input weights of the update and reset gates
   for (int n = tid; n < NG; n += THREADS) {
     const int q = n / 3, g = n % 3;
-    put_split(Bxh, Bxl, xoff(n, 0), a.pack[a.obias + 4 * q + g]);
-    put_split(Bxh, Bxl, xoff(n, 1), g < 2 ? a.pack[a.oxw + n] : 0.f);
-    put_split(Bxh, Bxl, xoff(n, 2), g < 2 ? a.pack[a.oxw + NG + n] : 0.f);
+    const bool u = q < dhm;
+    put_split(Bxh, Bxl, xoff(n, 0), u ? a.pack[a.obias + 4 * q + g] : 0.f);
+    put_split(Bxh, Bxl, xoff(n, 1), u && g < 2 ? a.pack[a.oxw + n] : 0.f);
+    put_split(Bxh, Bxl, xoff(n, 2), u && g < 2 ? a.pack[a.oxw + ngm + n] : 0.f);
   }
   // W_in x + b_in per previous spin d (0, 1; 2 = none at site 0)
   for (int e = tid; e < 3 * DH; e += THREADS) {
     const int d = e / DH, q = e % DH;
-    sxi[d * XS + q] = a.pack[a.obias + 4 * q + 3] + (d < 2 ? a.pack[a.oxw + d * NG + 3 * q + 2] : 0.f);
+    sxi[d * XS + q] = q < dhm ? a.pack[a.obias + 4 * q + 3] +
+                                    (d < 2 ? a.pack[a.oxw + d * ngm + 3 * q + 2] : 0.f)
+                              : 0.f;
   }
   if (tid < 4) shc[tid] = a.pack[a.ohc + tid];
   if (tid == 0) {
@@ -261,10 +273,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       // h_{kr-1}: this half's 32 units into the shared state and the planes
       {
         const float4 *src = nullptr;
-        if (valid && kr > 0) {
+        if (valid && kr > 0 && UH * half < dhm) {
           const int64_t slot =
               a.ck > 0 ? (int64_t)s * a.nck + (kr / a.ck - 1) : (int64_t)s * N + kr - 1;
-          src = reinterpret_cast<const float4 *>(a.hcache + slot * DH + UH * half);
+          src = reinterpret_cast<const float4 *>(a.hcache + slot * dhm + UH * half);
         }
 #pragma unroll
         for (int g8 = 0; g8 < UH / 8; ++g8) {
@@ -394,16 +406,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
 
 }  // namespace
 
-bool eloc_tc_supported(int dim, int dh) { return dim == 1 && dh == DH; }
+// hidden size 64, or 32 padded to 64 (dhm must be a multiple of UH = 32 so
+// that each half's cached units are whole or absent)
+bool eloc_tc_supported(int dim, int dh) { return dim == 1 && (dh == DH || dh == DH / 2); }
 
 cudaError_t eloc_tc_run(const ElocTcArgs &args, int sm_count, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_eloc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (args.dhm != DH && args.dhm != DH / 2) return cudaErrorInvalidValue;
+  const void *kern = args.dhm == DH ? (const void *)k_eloc_tc<DH> : (const void *)k_eloc_tc<DH / 2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int needed = (args.ntiles + SLOTS - 1) / SLOTS;
   const int grid = needed < sm_count ? needed : sm_count;
   if (grid <= 0) return cudaSuccess;
-  k_eloc_tc<<<grid, THREADS, SMEM_BYTES, st>>>(args);
+  if (args.dhm == DH)
+    k_eloc_tc<DH><<<grid, THREADS, SMEM_BYTES, st>>>(args);
+  else
+    k_eloc_tc<DH / 2><<<grid, THREADS, SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // eloc_tc.h -- tensor-core engine for the connected-configuration suffixes
-// (mixed precision, 1D chains, hidden size 64).
+// (mixed precision, 1D chains, hidden size 64, or 32 run with zero-padded
+// units).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -10,7 +11,7 @@ struct ElocTcArgs {
   const float *pack;      // packed FP32 weights
   int oWgT, oxw, obias, ohead, ohc;  // their offsets (PackOff)
   const uint8_t *spins;   // [ns][N] samples
-  const float *hcache;    // [ns][N][64], or [ns][nck][64] checkpoints
+  const float *hcache;    // [ns][N][dhm], or [ns][nck][dhm] checkpoints
   const float *lccache;   // [ns][N][2]
   int N, cplx, zmask;
   int64_t ns;
@@ -22,6 +23,7 @@ struct ElocTcArgs {
   double *contrib;        // [n_off][ns][2]
   int *err;               // device status word
   int ck, nck;            // checkpoints: hcache holds h_{m ck - 1} in slot m - 1 (ck > 0)
+  int dhm;                // the model's hidden size (64, or 32 padded with zero units)
 };
 
 bool eloc_tc_supported(int dim, int dh);

@@ -305,6 +305,7 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.err = W<int>(c, c->off.sstat);
       e.ck = c->ck;
       e.nck = c->nck;
+      e.dhm = c->L.dh;
       CU(eloc_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));

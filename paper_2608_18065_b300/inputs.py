@@ -125,8 +125,9 @@ class Workload:
 
 
 def workloads() -> dict:
-    """The synthetic benchmark workloads (1D TFIM small/large, 1D cluster,
-    2D Heisenberg), each with Tab. I hyper-parameters."""
+    """The synthetic benchmark workloads (1D TFIM small/large and at the
+    paper's own size, 1D cluster, 2D Heisenberg), each with Tab. I
+    hyper-parameters."""
     w = {}
     w["tfim16"] = Workload(
         "tfim_N16_dh16_ns128_fp64", ModelSpec(1, 16, 1, 16),
@@ -134,6 +135,10 @@ def workloads() -> dict:
     w["tfim100"] = Workload(
         "tfim_N100_dh64_ns1024_mixed", ModelSpec(1, 100, 1, 64),
         HamSpec("tfim", J=1.0, h=1.0), HParams(ns=1024, **TAB1["tfim"]), "mixed")
+    # the paper's own 1D TFIM configuration (Sec. III.A, Tab. I)
+    w["tfim200"] = Workload(
+        "tfim_N200_dh32_ns100_mixed", ModelSpec(1, 200, 1, 32),
+        HamSpec("tfim", J=1.0, h=1.0), HParams(ns=100, **TAB1["tfim"]), "mixed")
     w["cluster64"] = Workload(
         "cluster_zxz_N64_dh64_ns512_mixed", ModelSpec(1, 64, 1, 64, cplx=1),
         HamSpec("cluster_zxz"), HParams(ns=512, **TAB1["cluster"]), "mixed")

@@ -41,7 +41,8 @@ def _centred_oracle_rows(model, th, spins):
     return np.concatenate([(b - b.mean(0)) / np.sqrt(ns) for b in blocks], 0)
 
 
-CASES = [("tfim100", "mixed"), ("tfim100", "fp64"), ("cluster64", "mixed"), ("heis10", "mixed")]
+CASES = [("tfim100", "mixed"), ("tfim100", "fp64"), ("tfim200", "mixed"), ("cluster64", "mixed"),
+         ("heis10", "mixed")]
 
 
 @pytest.mark.parametrize("key,prec", CASES, ids=[f"{k}-{p}" for k, p in CASES])

@@ -203,16 +203,20 @@ def test_minsr_step_mixed_error_report(model, ham, hp):
 
 
 # hidden size 64 on 1D chains takes the tensor-core connected-configuration
-# engine in the mixed path; 300 samples = two full 128-row tiles + a ragged one
+# engine in the mixed path, and so does 32 (units padded with zeros); 300
+# samples = two full 128-row tiles + a ragged one
 TC_MODELS = [
     (ModelSpec(1, 24, 1, 64), HamSpec("tfim", J=1.0, h=0.8)),
     (ModelSpec(1, 20, 1, 64, cplx=1), HamSpec("cluster_zxz")),
     (ModelSpec(1, 18, 1, 64, cplx=1), HamSpec("cluster_paper")),
     (ModelSpec(1, 16, 1, 64, zmask=1), HamSpec("tfim")),
+    (ModelSpec(1, 26, 1, 32), HamSpec("tfim", J=1.0, h=1.0)),
+    (ModelSpec(1, 18, 1, 32, cplx=1, zmask=1), HamSpec("cluster_zxz")),
 ]
 
 
-@pytest.mark.parametrize("model,ham", TC_MODELS, ids=["tfim24", "zxz20", "xzx18", "tfim16mask"])
+@pytest.mark.parametrize("model,ham", TC_MODELS,
+                         ids=["tfim24", "zxz20", "xzx18", "tfim16mask", "tfim26dh32", "zxz18dh32mask"])
 def test_eloc_tensor_core_engine_mixed(model, ham):
     ns = 300
     c = ctx(model, ham, "mixed", ns)

@@ -34,7 +34,8 @@ def test_uniform_definition_and_moments():
 
 def test_param_counts_match_layout():
     # counts implied by the layout of App. A for the benchmark models
-    expect = {"tfim16": 962, "tfim100": 13058, "cluster64": 13188, "heis10": 21764}
+    expect = {"tfim16": 962, "tfim100": 13058, "tfim200": 3458, "cluster64": 13188,
+              "heis10": 21764}
     for key, w in workloads().items():
         assert O.param_count(w.model) == param_count(w.model) == expect[key]
     assert O.param_count(ModelSpec(2, 6, 6, 32, cplx=1)) == 5764
