@@ -794,12 +794,72 @@ def matched_energy(w, hp, steps, dev):
     return out
 
 
+def run_lambda_grid(args):
+    """Stability grid of App. E / Fig. 6: a 1D TFIM network (N = 20, d_h = 32,
+    Tab. I's TFIM column) trained for 100 steps from theta_0 for every
+    (lambda, N_s) of the grid, in the mixed and the FP64 contexts.  Per point:
+    steps the library rejected (non-finite E, eps or delta theta; theta left
+    unchanged), solves that fell back from FP32-factor refinement to the FP64
+    factorisation, lambda_max and kappa_2 of the last step's T + lambda I
+    (nqs_spectrum; lambda_max = 0 means every sample was the same
+    configuration and training has stalled), and the final relative energy
+    error against the Jordan-Wigner energy."""
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import HamSpec, HParams, ModelSpec, TAB1, init_theta
+    dev = torch.device("cuda", 0)
+    model, ham = ModelSpec(1, 20, 1, 32), HamSpec("tfim", J=1.0, h=1.0)
+    N = model.N
+    B = np.diag(np.full(N, ham.h)) + np.diag(np.full(N - 1, ham.J), 1)
+    E0 = -float(np.sum(np.linalg.svd(B, compute_uv=False)))
+    lams = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
+    nss = [16, 64, 256, 1024]
+    steps = 100
+    grid = []
+    t0 = time.time()
+    for prec in ("mixed", "fp64"):
+        for ns in nss:
+            c = nqs.Context(model, ham, prec, ns, device=dev)
+            for lam in lams:
+                tab = dict(TAB1["tfim"])
+                tab["lam"] = lam
+                hp = HParams(ns=ns, **tab)
+                th = torch.tensor(init_theta(model, 5), device=dev)
+                m = torch.zeros_like(th)
+                s = c.new_stats()
+                rejected = fallback = 0
+                E = float("nan")
+                for t in range(steps):
+                    outs = c.step_outputs(ns) if t == steps - 1 else None
+                    c.minsr_step(th, m, hp, t, s, outputs=outs)
+                    d = nqs.decode_stats(s)
+                    rejected += int(d["status"] != 0)
+                    fallback += int(d["solve_fp64"] != 0)
+                    if d["status"] == 0:
+                        E = d["E_re"]
+                sp = nqs.spectrum(outs["T"], lam, m=min(64, outs["T"].shape[0]))
+                grid.append({"precision": prec, "ns": ns, "lambda": lam, "rejected": rejected,
+                             # the FP64 context always factors in FP64
+                             "fp64_fallback": fallback if prec == "mixed" else None,
+                             "lambda_max_last": sp["lambda_max"], "kappa_last": sp["kappa"],
+                             "rel_err_final": (E - E0) / abs(E0),
+                             "finite_theta": bool(torch.isfinite(th).all().item())})
+            del c
+    line = {"metric": "minSR stability grid (App. E, Fig. 6)", "workload": "lambda_grid",
+            "model": "tfim_N20_dh32", "steps_per_point": steps, "E_exact": E0,
+            "seconds": time.time() - t0, "grid": grid}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched16":
         return run_batched(args)
+    if args.workload == "lambda_grid":
+        return run_lambda_grid(args)
     return run_ours(args)
 
 
