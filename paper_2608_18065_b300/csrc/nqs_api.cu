@@ -8,11 +8,13 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "chol_coop.cuh"
 #include "chol_ir.cuh"
 #include "eloc_tc.h"
+#include "jac_tc.h"
 #include "gram_tc.h"
 #include "launch.h"
 #include "stages.cuh"
@@ -360,6 +362,21 @@ nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_
     c->launches += 2;
     g.hcache = b.hcache;
     g.k_lo = 0; g.k_hi = N; g.hN = N; g.hoff = 0; g.aN = N; g.aoff = 0; g.accumulate = 0;
+    if constexpr (std::is_same<T, float>::value) {
+      if (gram_tc_available() && jac_tc_supported(c->L.dim, c->L.dh)) {
+        // mixed 1D chains: the rows of O as tensor-core products
+        JacTcArgs j{};
+        j.N = N; j.cplx = c->L.cplx; j.dh = c->L.dh;
+        j.ns = ns; j.nrows = R; j.spins = spins;
+        j.hcache = b.hcache; j.adj = b.adj; j.adjw = c->adjw;
+        j.O = O; j.np = c->L.np;
+        j.Wu = c->L.Wu; j.bu = c->L.bu; j.Wr = c->L.Wr; j.br = c->L.br; j.Wh = c->L.Wh;
+        j.bh = c->L.bh; j.Win = c->L.Win; j.bin = c->L.bin; j.Uo = c->L.Uo; j.co = c->L.co;
+        j.Up = c->L.Up; j.cp = c->L.cp;
+        j.err = W<int>(c, c->off.sstat);
+        return cu(jac_tc_run(j, c->rd.sm_count, st));
+      }
+    }
     return cu(run_grad<T>(c->rd, g, st));
   }
   const int ck = c->ck;
