@@ -85,57 +85,72 @@ __device__ __forceinline__ void put_b(unsigned char *stage, int n, int kk, float
   *reinterpret_cast<__nv_bfloat16 *>(stage + S::A_BYTES + (ks * 2 + 1) * S::BSUB + o) = l;
 }
 
-// Stage chunk c (sites k' = 16 c .. 16 c + 15) of row `row` (sample s): every
-// thread issues all of its global loads before its first shared store.
+// One chunk's values in registers: chunk c (sites k' = 16 c .. 16 c + 15) of
+// row `row` (sample s).  The loads of the next chunk are issued right after
+// the current one is stored, so they overlap the barrier, the products and,
+// at the end of a row, the epilogue.
+template <int DH> struct ChunkRegs {
+  static constexpr int AW = 4 * DH;                   // dau, dar, dg, dac
+  static constexpr int NA = JT_KC * AW / JT_THREADS;  // gate adjoints per thread
+  static constexpr int NH = JT_KC * DH / JT_THREADS;  // states per thread
+  float va[NA], vh[NH], vz;
+  int sp;
+};
+
 template <int DH>
-__device__ __forceinline__ void load_chunk(const JacTcArgs &a, unsigned char *stage, int64_t row,
-                                           int64_t s, int c, int tid) {
-  constexpr int AW = 4 * DH;                          // dau, dar, dg, dac
-  constexpr int NA = JT_KC * AW / JT_THREADS;         // gate adjoints per thread
-  constexpr int NH = JT_KC * DH / JT_THREADS;         // states per thread
+__device__ __forceinline__ void fetch_chunk(const JacTcArgs &a, ChunkRegs<DH> &r, int64_t row,
+                                            int64_t s, int c, int tid) {
+  using CR = ChunkRegs<DH>;
   const int N = a.N;
   const int k0 = c * JT_KC;
   const float *arow = a.adj + row * (int64_t)N * a.adjw;
   const float *hrow = a.hcache + s * (int64_t)N * DH;
-  float va[NA], vh[NH], vz = 0.f;
 #pragma unroll
-  for (int q = 0; q < NA; ++q) {
+  for (int q = 0; q < CR::NA; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / AW, m = e - kk * AW, k = k0 + kk;
-    va[q] = k < N ? __ldcg(arow + (int64_t)k * a.adjw + m) : 0.f;
+    const int kk = e / CR::AW, m = e - kk * CR::AW, k = k0 + kk;
+    r.va[q] = k < N ? __ldcg(arow + (int64_t)k * a.adjw + m) : 0.f;
   }
+  r.vz = 0.f;
   if (tid < 4 * JT_KC) {  // dz of site k' - 1: the heads' shifted index
     const int kk = tid >> 2, o = tid & 3, k = k0 + kk - 1;
-    vz = (k >= 0 && k < N) ? __ldcg(arow + (int64_t)k * a.adjw + AW + o) : 0.f;
+    r.vz = (k >= 0 && k < N) ? __ldcg(arow + (int64_t)k * a.adjw + CR::AW + o) : 0.f;
   }
 #pragma unroll
-  for (int q = 0; q < NH; ++q) {
+  for (int q = 0; q < CR::NH; ++q) {
     const int e = tid + q * JT_THREADS;
     const int kk = e / DH, n = e - kk * DH, k = k0 + kk - 1;
-    vh[q] = (k >= 0 && k < N) ? __ldcg(hrow + (int64_t)k * DH + n) : 0.f;
+    r.vh[q] = (k >= 0 && k < N) ? __ldcg(hrow + (int64_t)k * DH + n) : 0.f;
   }
-  int sp = -1;
+  r.sp = -1;
   if (tid < JT_KC) {
     const int k = k0 + tid - 1;
-    sp = (k >= 0 && k < N) ? (int)__ldcg(a.spins + s * (int64_t)N + k) : -1;
+    r.sp = (k >= 0 && k < N) ? (int)__ldcg(a.spins + s * (int64_t)N + k) : -1;
   }
+}
+
+template <int DH>
+__device__ __forceinline__ void store_chunk(const ChunkRegs<DH> &r, unsigned char *stage, int N,
+                                            int c, int tid) {
+  using CR = ChunkRegs<DH>;
+  const int k0 = c * JT_KC;
 #pragma unroll
-  for (int q = 0; q < NA; ++q) {
+  for (int q = 0; q < CR::NA; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / AW, m = e - kk * AW;
-    put_a<DH>(stage, m / (2 * DH), m % (2 * DH), kk, va[q]);
+    const int kk = e / CR::AW, m = e - kk * CR::AW;
+    put_a<DH>(stage, m / (2 * DH), m % (2 * DH), kk, r.va[q]);
   }
-  if (tid < 4 * JT_KC) put_a<DH>(stage, 2, tid & 3, tid >> 2, vz);
+  if (tid < 4 * JT_KC) put_a<DH>(stage, 2, tid & 3, tid >> 2, r.vz);
 #pragma unroll
-  for (int q = 0; q < NH; ++q) {
+  for (int q = 0; q < CR::NH; ++q) {
     const int e = tid + q * JT_THREADS;
     const int kk = e / DH, n = e - kk * DH;
-    put_b<DH>(stage, n, kk, vh[q]);
+    put_b<DH>(stage, n, kk, r.vh[q]);
   }
   if (tid < JT_KC) {
     put_b<DH>(stage, DH, tid, k0 + tid <= N ? 1.f : 0.f);  // ones over k' = 0..N
-    put_b<DH>(stage, DH + 1, tid, sp == 0 ? 1.f : 0.f);
-    put_b<DH>(stage, DH + 2, tid, sp == 1 ? 1.f : 0.f);
+    put_b<DH>(stage, DH + 1, tid, r.sp == 0 ? 1.f : 0.f);
+    put_b<DH>(stage, DH + 2, tid, r.sp == 1 ? 1.f : 0.f);
   }
 }
 
@@ -221,12 +236,21 @@ __global__ void __launch_bounds__(JT_THREADS, 2) k_jac_tc(const JacTcArgs a) {
     return flag_s == 0;
   };
 
+  ChunkRegs<DH> cr;
+  if ((int64_t)blockIdx.x < a.nrows) fetch_chunk<DH>(a, cr, blockIdx.x, blockIdx.x % a.ns, 0, tid);
   for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
     const int64_t s = row % a.ns;
     for (int c = 0; c < NC; ++c) {
       const int st = c & 1;
       if (pending[st] && !drain(st)) { ok = false; break; }
-      load_chunk<DH>(a, stg[st], row, s, c, tid);
+      store_chunk<DH>(cr, stg[st], a.N, c, tid);
+      // the next chunk's loads, or the next row's first, fly during the rest
+      if (c + 1 < NC) {
+        fetch_chunk<DH>(a, cr, row, s, c + 1, tid);
+      } else if (row + gridDim.x < a.nrows) {
+        const int64_t nrow = row + gridDim.x;
+        fetch_chunk<DH>(a, cr, nrow, nrow % a.ns, 0, tid);
+      }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
