@@ -249,7 +249,8 @@ def stage_rooflines(w, ms, sites, R, np_):
     eloc_suffix: see eloc_roofline (sites = recomputed sites counted by the
     library).  sample, jac_bwd, jac_grad: FP32 (FP64) FMA-pipe work of the
     recurrence, N_s N (sample) or R N (reverse sweep, O assembly) sites of
-    site_flops each.  cholesky: n^3/3 factor + n^3/3 triangular inverse
+    site_flops each (the mixed 1D O assembly on the tensor cores is
+    reported by its HBM bytes).  cholesky: n^3/3 factor + n^3/3 triangular inverse
     (n = R) in FP32 for the mixed path (refinement sweeps: 2n^2 each, not
     counted).  gram: BF16x3 tensor work 3 R(R+1) Np.  center: HBM bytes of
     the column sums and the split (read O twice, write hi and lo)."""
@@ -277,7 +278,19 @@ def stage_rooflines(w, ms, sites, R, np_):
             alu("eloc_suffix", "k_forward<MODE_ELOC>", sites * sf)
     alu("sample", "k_forward<MODE_SAMPLE>", w.hp.ns * N * sf)
     alu("jac_bwd", "k_jac_bwd", R * N * sf)
-    alu("jac_grad", "k_jac_grad", R * N * sf)
+    if f32 and w.model.dim == 1 and w.model.dh in (32, 64) and ms.get("jac_grad", 0) > 0:
+        # tensor-core O assembly: HBM-bound reads of the adjoint records and
+        # states, write of O
+        t = ms["jac_grad"]
+        dh = w.model.dh
+        byts = R * N * (4 * dh + 4) * 4 + w.hp.ns * N * dh * 4 + R * np_ * 4
+        pk, src = measured_peak("hbm_gbs", 6400.0)
+        a = byts / (t * 1e-3) / 1e9
+        out["jac_grad"] = {"kernel": "k_jac_tc", "bound": "hbm", "achieved": a, "peak": pk,
+                           "unit": "GB/s", "frac": a / pk, "traffic": None, "peak_source": src,
+                           "bytes_per_launch": byts, "ms_per_launch": t}
+    else:
+        alu("jac_grad", "k_jac_grad", R * N * sf)
     alu("cholesky", "k_chol_ir" if f32 else "k_chol_coop", 2 * R ** 3 / 3)
     if ms.get("gram", 0) > 0:
         t = ms["gram"]
