@@ -89,13 +89,27 @@ __device__ __forceinline__ void put_b(unsigned char *stage, int n, int kk, float
 // row `row` (sample s).  The loads of the next chunk are issued right after
 // the current one is stored, so they overlap the barrier, the products and,
 // at the end of a row, the epilogue.
+// Each thread owns pairs of consecutive sites (k', k' + 1) of one column m
+// (or unit n), so that the two BF16 values of a plane go out as one 4-byte
+// store.
 template <int DH> struct ChunkRegs {
-  static constexpr int AW = 4 * DH;                   // dau, dar, dg, dac
-  static constexpr int NA = JT_KC * AW / JT_THREADS;  // gate adjoints per thread
-  static constexpr int NH = JT_KC * DH / JT_THREADS;  // states per thread
-  float va[NA], vh[NH], vz;
+  static constexpr int AW = 4 * DH;                        // dau, dar, dg, dac
+  static constexpr int NA = JT_KC * AW / JT_THREADS / 2;   // site pairs of gate adjoints
+  static constexpr int NH = JT_KC * DH / JT_THREADS / 2;   // site pairs of states
+  float va[NA][2], vh[NH][2], vz;
   int sp;
 };
+
+// hi, lo planes of the pair (v0, v1) at sites kk, kk + 1 (kk even) of a row
+__device__ __forceinline__ void put_pair(unsigned char *hi, unsigned char *lo, int r, int kk,
+                                         float v0, float v1) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+  const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+  const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+  const uint32_t o = kmaj_off(r, kk & 15);
+  *reinterpret_cast<__nv_bfloat162 *>(hi + o) = __halves2bfloat162(h0, h1);
+  *reinterpret_cast<__nv_bfloat162 *>(lo + o) = __halves2bfloat162(l0, l1);
+}
 
 template <int DH>
 __device__ __forceinline__ void fetch_chunk(const JacTcArgs &a, ChunkRegs<DH> &r, int64_t row,
@@ -108,8 +122,9 @@ __device__ __forceinline__ void fetch_chunk(const JacTcArgs &a, ChunkRegs<DH> &r
 #pragma unroll
   for (int q = 0; q < CR::NA; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / CR::AW, m = e - kk * CR::AW, k = k0 + kk;
-    r.va[q] = k < N ? __ldcg(arow + (int64_t)k * a.adjw + m) : 0.f;
+    const int kp = e / CR::AW, m = e - kp * CR::AW, k = k0 + 2 * kp;
+    r.va[q][0] = k < N ? __ldcg(arow + (int64_t)k * a.adjw + m) : 0.f;
+    r.va[q][1] = k + 1 < N ? __ldcg(arow + (int64_t)(k + 1) * a.adjw + m) : 0.f;
   }
   r.vz = 0.f;
   if (tid < 4 * JT_KC) {  // dz of site k' - 1: the heads' shifted index
@@ -119,8 +134,9 @@ __device__ __forceinline__ void fetch_chunk(const JacTcArgs &a, ChunkRegs<DH> &r
 #pragma unroll
   for (int q = 0; q < CR::NH; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / DH, n = e - kk * DH, k = k0 + kk - 1;
-    r.vh[q] = (k >= 0 && k < N) ? __ldcg(hrow + (int64_t)k * DH + n) : 0.f;
+    const int kp = e / DH, n = e - kp * DH, k = k0 + 2 * kp - 1;
+    r.vh[q][0] = (k >= 0 && k < N) ? __ldcg(hrow + (int64_t)k * DH + n) : 0.f;
+    r.vh[q][1] = (k + 1 >= 0 && k + 1 < N) ? __ldcg(hrow + (int64_t)(k + 1) * DH + n) : 0.f;
   }
   r.sp = -1;
   if (tid < JT_KC) {
@@ -137,15 +153,20 @@ __device__ __forceinline__ void store_chunk(const ChunkRegs<DH> &r, unsigned cha
 #pragma unroll
   for (int q = 0; q < CR::NA; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / CR::AW, m = e - kk * CR::AW;
-    put_a<DH>(stage, m / (2 * DH), m % (2 * DH), kk, r.va[q]);
+    const int kp = e / CR::AW, m = e - kp * CR::AW, kk = 2 * kp;
+    const int t = m / (2 * DH), ks = kk >> 4;
+    put_pair(stage + ((ks * 2 + 0) * JT_TILES + t) * JT_ASUB,
+             stage + ((ks * 2 + 1) * JT_TILES + t) * JT_ASUB, m % (2 * DH), kk, r.va[q][0],
+             r.va[q][1]);
   }
   if (tid < 4 * JT_KC) put_a<DH>(stage, 2, tid & 3, tid >> 2, r.vz);
 #pragma unroll
   for (int q = 0; q < CR::NH; ++q) {
     const int e = tid + q * JT_THREADS;
-    const int kk = e / DH, n = e - kk * DH;
-    put_b<DH>(stage, n, kk, r.vh[q]);
+    const int kp = e / DH, n = e - kp * DH, kk = 2 * kp, ks = kk >> 4;
+    using S = JtShape<DH>;
+    put_pair(stage + S::A_BYTES + (ks * 2 + 0) * S::BSUB, stage + S::A_BYTES + (ks * 2 + 1) * S::BSUB,
+             n, kk, r.vh[q][0], r.vh[q][1]);
   }
   if (tid < JT_KC) {
     put_b<DH>(stage, DH, tid, k0 + tid <= N ? 1.f : 0.f);  // ones over k' = 0..N
