@@ -36,7 +36,7 @@ struct CholIrArgs {
   float *wv;         // [n] scratch: L^{-1} r
   float *dpart;      // [chunks][n] scratch: partial sums of L^{-T} w
   double *r;         // [n] scratch: FP64 residual
-  double *part;      // [gridDim][4] scratch: partial norms
+  double *part;      // [2][gridDim][4] scratch: partial norms (by sweep parity)
   unsigned *bar;     // barrier arrival counter (zeroed before launch)
   int32_t *status;   // NQS_ERR_TIMEOUT on a barrier timeout
   int32_t *need_fp64;// out: 1 when the FP64 factorisation must run
@@ -776,7 +776,8 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       for (int q = 0; q < IR_THREADS / 32; ++q) {
         m0 = fmax(m0, red_s[q][0]); m1 = fmax(m1, red_s[q][1]); m2 = fmax(m2, red_s[q][2]);
       }
-      a.part[(size_t)g * 4 + 0] = m0; a.part[(size_t)g * 4 + 1] = m1; a.part[(size_t)g * 4 + 2] = m2;
+      double *pt = a.part + (size_t)(it & 1) * G * 4;  // two buffers by sweep parity
+      pt[(size_t)g * 4 + 0] = m0; pt[(size_t)g * 4 + 1] = m1; pt[(size_t)g * 4 + 2] = m2;
     }
     if (!gsync()) return;
     // maxima over the CTAs' partials: all loads in flight at once (max is
@@ -784,8 +785,9 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     {
       double q0 = 0.0, q1 = 0.0, q2 = 0.0;
       for (int q = tid; q < G; q += IR_THREADS) {
-        q0 = fmax(q0, a.part[(size_t)q * 4]); q1 = fmax(q1, a.part[(size_t)q * 4 + 1]);
-        q2 = fmax(q2, a.part[(size_t)q * 4 + 2]);
+        const double *pt = a.part + (size_t)(it & 1) * G * 4;
+        q0 = fmax(q0, pt[(size_t)q * 4]); q1 = fmax(q1, pt[(size_t)q * 4 + 1]);
+        q2 = fmax(q2, pt[(size_t)q * 4 + 2]);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -804,8 +806,8 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     }
     if (it == 0) normA = an;
     converged = rn <= sqrt((double)n) * 1.1102230246251565e-16 * normA * xn;
-    // every CTA has read part[] before anyone overwrites it in the next sweep
-    if (!gsync()) return;
+    // the next sweep writes the other buffer; the one after that comes only
+    // after that sweep's barriers, which every CTA passes after this read
   }
   if (!converged && g == 0 && tid == 0) *a.need_fp64 = 1;
 }
