@@ -38,6 +38,32 @@ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t step, uint32
   return (double)(bits >> 11) * 0x1.0p-53;
 }
 
+// The top 24 of those 53 bits as an FP32 uniform: u24 <= u53 < u24 + 2^-24,
+// so a comparison with a probability differs from the FP64 one only within
+// 2^-24 of a tie.
+__device__ __forceinline__ float uniform24(uint64_t seed, uint64_t step, uint32_t s, uint32_t k) {
+  uint32_t c[4] = {k, s, (uint32_t)step, (uint32_t)(step >> 32)};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return (float)(c[1] >> 8) * 0x1.0p-24f;
+}
+
+// Error-free FP32 accumulation (Knuth's TwoSum): sum + err carries the
+// running sum to about twice FP32's precision without the FP64 pipe (64
+// times slower than FP32 on this part).
+__device__ __forceinline__ void two_add(float &sum, float &err, float x) {
+  const float t = sum + x, z = t - sum;
+  err += (sum - (t - z)) + (x - z);
+  sum = t;
+}
+// pi s as the pair (p, e) with p + e = pi s to about 2^-46 relative: p the
+// rounded product, e its exact error (FMA) plus the error of pi in FP32.
+__device__ __forceinline__ void pi_times(float s, float &p, float &e) {
+  const float pi_hi = 3.14159274101257324f;        // pi rounded to FP32
+  const float pi_lo = -8.742277657347586e-08f;     // pi - pi_hi, rounded to FP32
+  p = pi_hi * s;
+  e = fmaf(pi_hi, s, -p) + pi_lo * s;
+}
+
 // --------------------------------------------------------- activations
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
 __device__ __forceinline__ double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }

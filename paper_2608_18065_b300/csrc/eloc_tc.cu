@@ -300,7 +300,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       tc_fence_before();
       if (bar_any(1 + t, 2 * TR, !ok)) { ok = false; break; }
       if (issuer) issue_round(dacc, a0, b0, accbar);
-      double dre = 0.0, dimg = 0.0;
+      // log |psi(sigma')/psi(sigma)| and the phase difference as error-free
+      // FP32 TwoSum pairs (each term's parts added exactly, off the slow FP64
+      // pipe); dead: the mask forces the amplitude of sigma' to zero
+      float sre = 0.f, cre = 0.f, sim = 0.f, cim = 0.f;
+      bool dead = false;
       const int L = N - kr;
       for (int r = 0; r <= L; ++r) {
         const int k = kr + r;  // gates of site k (r < L), head of site k - 1 (r > 0)
@@ -323,14 +327,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
             if (n_up >= N / 2) forced = 1;
             else if (n_dn >= N / 2) forced = 0;
           }
-          double lps;
-          if (forced >= 0) lps = (sprev == forced) ? 0.0 : -INFINITY;
-          else lps = (double)(sprev == 0 ? lp0 : lp1);
-          double ph = 0.0;
-          if (a.cplx) ph = NQS_PI * (double)softsign(sprev == 0 ? hv[2] + shc[2] : hv[3] + shc[3]);
+          const bool kill = forced >= 0 && sprev != forced;
+          const float hl = forced >= 0 ? 0.f : 0.5f * (sprev == 0 ? lp0 : lp1);
+          float pp = 0.f, pe = 0.f;
+          if (a.cplx) pi_times(softsign(sprev == 0 ? hv[2] + shc[2] : hv[3] + shc[3]), pp, pe);
           if (valid && k - 1 >= j0) {
-            dre += 0.5 * lps - (double)lc.x;
-            dimg += ph - (double)lc.y;
+            dead |= kill;
+            two_add(sre, cre, hl);
+            two_add(sre, cre, -lc.x);
+            two_add(sim, cim, pp);
+            two_add(sim, cim, pe - lc.y);
           }
           if (sprev == 0) ++n_up; else ++n_dn;
         }
@@ -382,7 +388,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       }
       if (ok && valid && half == 0) {
         const double e = a.item_e[item];
-        const double mag = exp(dre);
+        const double dre = (double)sre + (double)cre, dimg = (double)sim + (double)cim;
+        const double mag = dead ? 0.0 : exp(dre);
         double *c = a.contrib + ((int64_t)op * a.ns + s) * 2;
         c[0] = e * mag * cos(dimg);
         c[1] = e * mag * sin(dimg);

@@ -272,8 +272,14 @@ k_forward(const FwdArgs<T> A) {
     }
     __syncthreads();
 
-    // per-row scalar state lives on lane ug == i of each row group
+    // per-row scalar state lives on lane ug == i of each row group; the
+    // log-amplitude sums are FP64 for FP64 data and TwoSum pairs for FP32
+    // data (each term's parts added exactly); dead: an amplitude the mask
+    // forces to zero
     double acc_re = 0.0, acc_im = 0.0;
+    float sre = 0.f, cre = 0.f, sim = 0.f, cim = 0.f;
+    bool dead = false;
+    constexpr bool F32 = sizeof(T) == 4;
     int n_up = 0, n_dn = 0, nA = 0;
     const int my_i = ug;  // row handled by this lane (if ug < RT)
     const int my_r = r0 + (my_i < RT ? my_i : 0);
@@ -408,36 +414,68 @@ k_forward(const FwdArgs<T> A) {
         }
         int sg;
         if (MODE == MODE_SAMPLE) {
-          double p0 = forced == 0 ? 1.0 : (forced == 1 ? 0.0 : (double)ex(lp0));
           const uint64_t stp = A.step_dev ? (uint64_t)*A.step_dev : A.step;
-          double uu = uniform53(A.seed, stp, (uint32_t)my_s, (uint32_t)k);
-          sg = uu < p0 ? 0 : 1;
+          if constexpr (F32) {
+            const float p0 = forced == 0 ? 1.f : (forced == 1 ? 0.f : (float)ex(lp0));
+            sg = uniform24(A.seed, stp, (uint32_t)my_s, (uint32_t)k) < p0 ? 0 : 1;
+          } else {
+            double p0 = forced == 0 ? 1.0 : (forced == 1 ? 0.0 : (double)ex(lp0));
+            double uu = uniform53(A.seed, stp, (uint32_t)my_s, (uint32_t)k);
+            sg = uu < p0 ? 0 : 1;
+          }
           ssp[r * NP + k] = (uint8_t)sg;
           A.spins[(int64_t)my_s * N + k] = (uint8_t)sg;
         } else {
           sg = ssp[r * NP + k];
         }
-        double lps;
-        if (forced >= 0) lps = (sg == forced) ? 0.0 : -INFINITY;
-        else lps = (double)(sg == 0 ? lp0 : lp1);
-        double ph = 0.0;
-        if (A.cplx) {
-          T y = (sg == 0 ? z2 : z3) + shc[2 + sg];
-          ph = NQS_PI * (double)softsign(y);
-        }
-        if (MODE == MODE_ELOC) {
-          if (k >= kstart) {
-            const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
-            acc_re += 0.5 * lps - (double)lc[0];
-            acc_im += ph - (double)lc[1];
+        if constexpr (F32) {
+          const bool kill = forced >= 0 && sg != forced;  // log p = -inf
+          const float hl = forced >= 0 ? 0.f : 0.5f * (float)(sg == 0 ? lp0 : lp1);
+          float pp = 0.f, pe = 0.f;  // pi softsign(y) as a pair
+          if (A.cplx) pi_times((float)softsign((sg == 0 ? z2 : z3) + shc[2 + sg]), pp, pe);
+          if (MODE == MODE_ELOC) {
+            if (k >= kstart) {
+              const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+              dead |= kill;
+              two_add(sre, cre, hl);
+              two_add(sre, cre, -(float)lc[0]);
+              two_add(sim, cim, pp);
+              two_add(sim, cim, pe - (float)lc[1]);
+            }
+          } else if (!seg) {
+            dead |= kill;
+            two_add(sre, cre, hl);
+            two_add(sim, cim, pp);
+            two_add(sim, cim, pe);
+            if (A.lccache) {
+              T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+              lc[0] = kill ? (T)-INFINITY : (T)hl;
+              lc[1] = (T)(pp + pe);
+            }
           }
-        } else if (!seg) {
-          acc_re += 0.5 * lps;
-          acc_im += ph;
-          if (A.lccache) {
-            T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
-            lc[0] = (T)(0.5 * lps);
-            lc[1] = (T)ph;
+        } else {
+          double lps;
+          if (forced >= 0) lps = (sg == forced) ? 0.0 : -INFINITY;
+          else lps = (double)(sg == 0 ? lp0 : lp1);
+          double ph = 0.0;
+          if (A.cplx) {
+            T y = (sg == 0 ? z2 : z3) + shc[2 + sg];
+            ph = NQS_PI * (double)softsign(y);
+          }
+          if (MODE == MODE_ELOC) {
+            if (k >= kstart) {
+              const T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+              acc_re += 0.5 * lps - (double)lc[0];
+              acc_im += ph - (double)lc[1];
+            }
+          } else if (!seg) {
+            acc_re += 0.5 * lps;
+            acc_im += ph;
+            if (A.lccache) {
+              T *lc = A.lccache + ((int64_t)my_s * N + k) * 2;
+              lc[0] = (T)(0.5 * lps);
+              lc[1] = (T)ph;
+            }
           }
         }
         if (sg == 0) ++n_up; else ++n_dn;
@@ -445,6 +483,10 @@ k_forward(const FwdArgs<T> A) {
       }
       __syncthreads();
       T *t = hcur; hcur = hnxt; hnxt = t;
+    }
+    if constexpr (F32) {
+      acc_re = dead ? -INFINITY : (double)sre + (double)cre;
+      acc_im = (double)sim + (double)cim;
     }
     // row outputs
     if (my_i < RT && my_s >= 0) {
