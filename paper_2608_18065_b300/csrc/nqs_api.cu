@@ -317,7 +317,7 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
   }
   mark(c, 4, st);
   c->launches += 1;
-  k_eloc_reduce<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(
+  k_eloc_reduce<<<(unsigned)((eloc_reduce_threads(ns) + 255) / 256), 256, 0, st>>>(
       c->d_diag, c->n_diag, c->n_off, spins, c->L.N, ns, W<double>(c, c->off.contrib), eloc);
   return cu(cudaGetLastError());
 }

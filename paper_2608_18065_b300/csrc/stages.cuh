@@ -78,22 +78,35 @@ __global__ void k_eloc_gen(const OffOp *__restrict__ ops, const uint8_t *__restr
 
 // eps_s = sum of diagonal elements + sum over operators of the connected
 // contributions (already H_ss' Psi(s')/Psi(s)).
+// One warp per sample: the lanes take the diagonal terms and the operators'
+// contributions in strides of 32, then a fixed-order shuffle tree.
 __global__ void k_eloc_reduce(const DiagOp *__restrict__ dops, int n_diag, int n_off,
                               const uint8_t *__restrict__ spins, int N, int64_t ns,
                               const double *__restrict__ contrib, double *eloc) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= ns) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (s >= ns) return;  // uniform over the warp
   const uint8_t *sp = spins + s * N;
   double re = 0.0, im = 0.0;
-  for (int d = 0; d < n_diag; ++d) re += dops[d].coeff * zval(sp, dops[d].z1) * zval(sp, dops[d].z2);
-  for (int o = 0; o < n_off; ++o) {
+  for (int d = lane; d < n_diag; d += 32)
+    re += dops[d].coeff * zval(sp, dops[d].z1) * zval(sp, dops[d].z2);
+  for (int o = lane; o < n_off; o += 32) {
     const double *c = contrib + ((int64_t)o * ns + s) * 2;
     re += c[0];
     im += c[1];
   }
-  eloc[2 * s] = re;
-  eloc[2 * s + 1] = im;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  if (lane == 0) {
+    eloc[2 * s] = re;
+    eloc[2 * s + 1] = im;
+  }
 }
+// threads of k_eloc_reduce for ns samples
+inline int64_t eloc_reduce_threads(int64_t ns) { return ns * 32; }
 
 // ------------------------------------------------------ energy stats
 // One CTA: E = mean eps, var = mean |eps - E|^2, V-score; then
