@@ -72,6 +72,35 @@ def test_logpsi_eloc_jacobian_mixed(model, ham):
     assert rel_err(J, O.jacobian(model, th, sp)) < TOL_MIXED_JAC
 
 
+# hidden size 64 and 32 on 1D chains assemble the rows of O on the tensor
+# cores: chain lengths that end a 16-site chunk exactly (N + 1 = 16), leave
+# one site over (N + 1 = 17) or span two chunks, real and complex heads, the
+# mask, and more rows than the two CTAs per SM (so a CTA walks several rows
+# with the next row's loads in flight)
+JTC_MODELS = [
+    (ModelSpec(1, 21, 1, 64), HamSpec("tfim", J=1.0, h=0.9), 300),
+    (ModelSpec(1, 16, 1, 32, cplx=1, zmask=1), HamSpec("cluster_zxz"), 160),
+    (ModelSpec(1, 15, 1, 64, cplx=1), HamSpec("cluster_zxz"), 40),
+    (ModelSpec(1, 30, 1, 32, zmask=1), HamSpec("tfim"), 333),
+]
+
+
+@pytest.mark.parametrize("model,ham,ns", JTC_MODELS,
+                         ids=["tfim21dh64", "zxz16dh32cmask", "zxz15dh64c", "tfim30dh32mask"])
+def test_tensor_core_jacobian_mixed(model, ham, ns):
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 6)
+    sp = random_spins(model, ns, seed=13, zero_mag=bool(model.zmask))
+    J = c.jacobian(thd, torch.tensor(sp, device="cuda")).cpu().numpy().astype(np.float64)
+    J_o = O.jacobian(model, th, sp)
+    assert J.shape == J_o.shape
+    assert rel_err(J, J_o) < TOL_MIXED_JAC
+    # every entry, including the biases, input columns and heads, within the
+    # same tolerance of the largest entry of its row
+    scale = np.max(np.abs(J_o), axis=1, keepdims=True)
+    assert np.max(np.abs(J - J_o) / scale) < TOL_MIXED_JAC
+
+
 def test_sampler_mixed_decisions_valid():
     """FP32 conditionals decide the spins: every decision must agree with the
     oracle's p_k(0) unless u lies within 1e-5 of it; log Psi as mixed."""
