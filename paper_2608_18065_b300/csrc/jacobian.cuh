@@ -58,6 +58,27 @@ inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
   return (b + 127) & ~size_t(127);
 }
 
+// Two floats rounded to BF16 and packed, x0 in the low half.
+__device__ __forceinline__ uint32_t bf16x2_pack(float x0, float x1) {
+  uint32_t u;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(x1), "f"(x0));
+  return u;
+}
+// hi = bf16(x), lo = bf16(x - hi) of a pair, packed as above.
+__device__ __forceinline__ void bf16x2_split(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  hi = bf16x2_pack(x0, x1);
+  lo = bf16x2_pack(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
+}
+// D += A B on one warp: m16n8k16, BF16 inputs, FP32 accumulation.
+__device__ __forceinline__ void mma_m16n8k16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                             uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 // Reverse sweep of one row (sample, seed) through the GRU (App. A).  The
 // forward pass stored u, r, c, W_h h' + b_h (and h' in 2D) per site, and the
 // log-conditional of sigma_k, so per site only the adjoint of h',
@@ -91,7 +112,17 @@ k_jac_bwd(const BwdArgs<T> A) {
 
   const int tid = threadIdx.x;
   const int ug = tid % UG, rg = tid / UG;
-  const int r0 = rg * RT, a0 = ug * UT;
+  // 1D FP32 d_h = 64: the per-site product dh1 = dpd + W_g^T [dau; dar; dg]
+  // (K = 3 d_h) runs as warp-level MMAs, m16n8k16 with BF16 hi.hi + hi.lo +
+  // lo.hi and FP32 accumulation, 8 of the 16 rows used.  These products are
+  // a dependent chain of N small ones on 8 rows per CTA, which the register
+  // operands of warp MMAs serve with the least latency.  Warp w owns units
+  // 8w .. 8w + 7 of all 8 rows; lane (lane / 4, lane % 4) = (row g, t) owns
+  // units 8w + 2t, 8w + 2t + 1 of row g, where the MMA leaves their sums.
+  constexpr bool WMMA = sizeof(T) == 4 && DIM == 1 && DH == 64 && RT == 1 && RG == 8;
+  const int r0 = WMMA ? (tid & 31) >> 2 : rg * RT;
+  const int a0 = WMMA ? 8 * (tid >> 5) + 2 * (tid & 3) : ug * UT;
+  const bool row_lead = WMMA ? (tid >> 5) == 0 && (tid & 3) == 0 : ug == 0;
   const int N = A.N, Lx = A.Lx;
 
   {
@@ -111,6 +142,22 @@ k_jac_bwd(const BwdArgs<T> A) {
       sWg = p + oWg;
       sU12 = p + oU12;
     }
+  }
+
+  // the MMA's B operand, W_g of this warp's 8 units split into BF16 hi / lo,
+  // stays in registers for the whole sweep: [12 K steps][2 registers]
+  uint32_t wbh[WMMA ? 24 : 1], wbl[WMMA ? 24 : 1];
+  if constexpr (WMMA) {
+    __syncthreads();  // W_g staged
+    const int gq = (tid & 31) >> 2, tq = tid & 3, n = 8 * (tid >> 5) + gq;
+#pragma unroll
+    for (int st = 0; st < 12; ++st)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int k = 16 * st + 2 * tq + 8 * hh;
+        bf16x2_split((float)sWg[k * DH + n], (float)sWg[(k + 1) * DH + n], wbh[2 * st + hh],
+                     wbl[2 * st + hh]);
+      }
   }
 
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
@@ -196,7 +243,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           dy = T(NQS_PI) * om * om;
         }
         T *rec = A.adj + ((int64_t)(g >= 0 ? g : 0) * A.aN + k - A.aoff) * A.adjw;
-        if (g >= 0 && ug == 0) {
+        if (g >= 0 && row_lead) {
           rec[AJ::DZ + 0] = dz0; rec[AJ::DZ + 1] = dz1;
           rec[AJ::DZ + 2] = sk == 0 ? dy : T(0);
           rec[AJ::DZ + 3] = sk == 1 ? dy : T(0);
@@ -234,7 +281,26 @@ k_jac_bwd(const BwdArgs<T> A) {
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int uu = 0; uu < UT; ++uu) dh1[i][uu] = dpd[i][uu];
-      if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, RP, r0, sWg, DH, a0, C3, dh1);
+      if constexpr (WMMA) {
+        if (k > 0) {
+          const int gq = (tid & 31) >> 2, tq = tid & 3;
+          float c[4] = {(float)dh1[0][0], (float)dh1[0][1], 0.f, 0.f};
+#pragma unroll
+          for (int st = 0; st < 12; ++st) {
+            const int kb = 16 * st + 2 * tq;
+            uint32_t h0, l0, h2, l2;
+            bf16x2_split((float)sda[kb * RP + gq], (float)sda[(kb + 1) * RP + gq], h0, l0);
+            bf16x2_split((float)sda[(kb + 8) * RP + gq], (float)sda[(kb + 9) * RP + gq], h2, l2);
+            mma_m16n8k16(c, h0, 0u, h2, 0u, wbh[2 * st], wbh[2 * st + 1]);
+            mma_m16n8k16(c, h0, 0u, h2, 0u, wbl[2 * st], wbl[2 * st + 1]);
+            mma_m16n8k16(c, l0, 0u, l2, 0u, wbh[2 * st], wbh[2 * st + 1]);
+          }
+          dh1[0][0] = (T)c[0];
+          dh1[0][1] = (T)c[1];
+        }
+      } else {
+        if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, RP, r0, sWg, DH, a0, C3, dh1);
+      }
       if (DIM == 1) {
 #pragma unroll
         for (int i = 0; i < RT; ++i)
