@@ -58,27 +58,6 @@ inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
   return (b + 127) & ~size_t(127);
 }
 
-// Two floats rounded to BF16 and packed, x0 in the low half.
-__device__ __forceinline__ uint32_t bf16x2_pack(float x0, float x1) {
-  uint32_t u;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(x1), "f"(x0));
-  return u;
-}
-// hi = bf16(x), lo = bf16(x - hi) of a pair, packed as above.
-__device__ __forceinline__ void bf16x2_split(float x0, float x1, uint32_t &hi, uint32_t &lo) {
-  hi = bf16x2_pack(x0, x1);
-  lo = bf16x2_pack(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
-}
-// D += A B on one warp: m16n8k16, BF16 inputs, FP32 accumulation.
-__device__ __forceinline__ void mma_m16n8k16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                             uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 // Reverse sweep of one row (sample, seed) through the GRU (App. A).  The
 // forward pass stored u, r, c, W_h h' + b_h (and h' in 2D) per site, and the
 // log-conditional of sigma_k, so per site only the adjoint of h',

@@ -217,6 +217,31 @@ k_forward(const FwdArgs<T> A) {
     }
   }
 
+  // 1D FP32 d_h = 64 sampling / given-configuration sweeps: the per-site
+  // gate product [8 rows x 64] x [64 x 192] runs as warp-level MMAs
+  // (m16n8k16, BF16 hi.hi + hi.lo + lo.hi, FP32 accumulation, 8 of the 16
+  // rows used) with W_g in registers: warp w computes gate j of units
+  // 8w .. 8w + 7 for every row, and the results reach the threads that own
+  // them (row = warp, units 2 lane, 2 lane + 1) through shared memory.
+  constexpr bool WMMA = sizeof(T) == 4 && DIM == 1 && DH == 64 && UG == 32 && RT == 1 &&
+                        RG == 8 && MODE != MODE_ELOC;
+  __shared__ float sgate[WMMA ? 8 * DH * 3 : 1];
+  uint32_t wbh[WMMA ? 24 : 1], wbl[WMMA ? 24 : 1];  // [4 K steps][3 gates][2 registers]
+  if constexpr (WMMA) {
+    __syncthreads();  // W_g staged
+    const int gq = (tid & 31) >> 2, tq = tid & 3, w = tid >> 5;
+#pragma unroll
+    for (int st = 0; st < 4; ++st)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int k = 16 * st + 2 * tq + 8 * hh, n = 3 * (8 * w + gq) + j;
+          bf16x2_split((float)sWgT[k * C3 + n], (float)sWgT[(k + 1) * C3 + n],
+                       wbh[(st * 3 + j) * 2 + hh], wbl[(st * 3 + j) * 2 + hh]);
+        }
+  }
+
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
     // ------------------------------------------------------- tile setup
     int kstart = 0, op = 0, f1 = -1, f2 = -1, base = 0, cnt = 0;
@@ -336,7 +361,42 @@ k_forward(const FwdArgs<T> A) {
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int j2 = 0; j2 < 3 * UT; ++j2) acc[i][j2] = T(0);
-      if (DIM == 2 || k > 0) mm_acc_s<T, RT, 3 * UT, R, UT>(Ag, r0, sWgT, C3, 3 * a0, DH, acc);
+      if constexpr (WMMA) {
+        if (k > 0) {
+          const int gq = (tid & 31) >> 2, tq = tid & 3, w = tid >> 5;
+          float c[3][4];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+#pragma unroll
+          for (int st = 0; st < 4; ++st) {
+            const int kb = 16 * st + 2 * tq;
+            uint32_t h0, l0, h2, l2;
+            bf16x2_split((float)Ag[ssw<R, RT, UT>(kb, gq)], (float)Ag[ssw<R, RT, UT>(kb + 1, gq)],
+                         h0, l0);
+            bf16x2_split((float)Ag[ssw<R, RT, UT>(kb + 8, gq)],
+                         (float)Ag[ssw<R, RT, UT>(kb + 9, gq)], h2, l2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const int b = (st * 3 + j) * 2;
+              mma_m16n8k16(c[j], h0, 0u, h2, 0u, wbh[b], wbh[b + 1]);
+              mma_m16n8k16(c[j], h0, 0u, h2, 0u, wbl[b], wbl[b + 1]);
+              mma_m16n8k16(c[j], l0, 0u, l2, 0u, wbh[b], wbh[b + 1]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int uu = 0; uu < 2; ++uu)
+              sgate[(gq * DH + 8 * w + 2 * tq + uu) * 3 + j] = c[j][uu];
+          __syncthreads();
+#pragma unroll
+          for (int uu = 0; uu < UT; ++uu)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[0][3 * uu + j] = (T)sgate[(r0 * DH + a0 + uu) * 3 + j];
+        }
+      } else {
+        if (DIM == 2 || k > 0) mm_acc_s<T, RT, 3 * UT, R, UT>(Ag, r0, sWgT, C3, 3 * a0, DH, acc);
+      }
 
       // epilogue: GRU cell (App. A), partial heads, then the row's head on
       // lane ug == i (log-softmax, mask, draw, accumulate)
