@@ -259,6 +259,31 @@ def test_eloc_tensor_core_engine_mixed(model, ham):
     assert rel_err(cplx(c64.local_energy(thd, spd)), O.local_energy(model, ham, th, sp)) < RTOL64
 
 
+# 2D lattices with hidden size 64 run the warp-MMA engine in the mixed
+# context: 64-row tiles with a ragged tail, more tiles than CTAs (ns = 300 on
+# the 4x4 J1-J2 model gives 42 operators x 5 tiles), an odd row length, two
+# columns (a row turn every other site), real and complex heads, the mask
+E2D_MODELS = [
+    (ModelSpec(2, 4, 4, 64, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 300),
+    (ModelSpec(2, 5, 3, 64), HamSpec("j1j2", J1=1.0, J2=0.0), 130),
+    (ModelSpec(2, 2, 3, 64, cplx=1), HamSpec("j1j2", J1=1.0, J2=0.25), 70),
+]
+
+
+@pytest.mark.parametrize("model,ham,ns", E2D_MODELS, ids=["j1j2_4x4_cmask", "heis_5x3", "j1j2_2x3_c"])
+def test_eloc_2d_warp_mma_engine_mixed(model, ham, ns):
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 4)
+    sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    el = cplx(c.local_energy(thd, spd))
+    el_o = O.local_energy(model, ham, th, sp)
+    assert rel_err(el, el_o) < TOL_MIXED_ELOC
+    # every sample's local energy, not only the vector norm
+    scale = np.max(np.abs(el_o))
+    assert np.max(np.abs(el - el_o)) < TOL_MIXED_ELOC * scale
+
+
 def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
     """A matrix whose FP32 Cholesky breaks down (kappa ~ 1e12) but is SPD in
     FP64: the mixed context must still return the FP64 solution."""
