@@ -1,0 +1,34 @@
+// eloc2d_tc.h -- tensor-core engine for the connected-configuration
+// suffixes of 2D lattices (mixed precision, zig-zag path, hidden size 64,
+// every state cached).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nqs {
+
+struct Eloc2dTcArgs {
+  const float *pack;      // packed FP32 weights
+  int oWgT, oxw, obias, ohead, ohc, oU12T;  // their offsets (PackOff)
+  const uint8_t *spins;   // [ns][N] samples
+  const float *hcache;    // [ns][N][64]: h_k of every sample
+  const float *lccache;   // [ns][N][2]
+  int N, Lx, cplx, zmask;
+  int64_t ns;
+  int tiles_per_op, ntiles;  // 128-row tiles per operator, total tiles
+  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site
+  const int *item_s;      // [n_off][ns] connected samples
+  const double *item_e;   // [n_off][ns] matrix elements
+  const int *item_cnt;    // [n_off]
+  double *contrib;        // [n_off][ns][2]
+  float *colbuf;          // [grid][128][Lx][64]: recomputed states by lattice column
+  int *err;               // device status word (NQS_ERR_TIMEOUT on a wait that ran out)
+};
+
+constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)
+
+bool eloc2d_tc_supported(int dim, int dh);
+// grid <= sm_count; the column buffer must hold grid x 128 rows
+cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st);
+
+}  // namespace nqs

@@ -14,6 +14,7 @@
 #include "chol_coop.cuh"
 #include "chol_ir.cuh"
 #include "eloc_tc.h"
+#include "eloc2d_tc.h"
 #include "jac_tc.h"
 #include "gram_tc.h"
 #include "launch.h"
@@ -166,7 +167,12 @@ void carve(nqs_ctx *c) {
   o.item_e = take((size_t)c->n_off * ns * 8);
   o.item_cnt = take((size_t)c->n_off * 4);
   o.contrib = take((size_t)c->n_off * ns * 16);
-  o.colbuf = take(c->L.dim == 2 ? (size_t)c->eloc_grid * c->eloc_R * c->L.Lx * dh * es : 0);
+  // column buffers of the 2D local-energy engines: the SIMT / warp-MMA
+  // engines' grid x 64 rows, the tensor-core engine's SM count x 128
+  size_t cb_rows = (size_t)c->eloc_grid * c->eloc_R;
+  if (c->L.dim == 2 && c->es == 4 && eloc2d_tc_supported(c->L.dim, (int)dh))
+    cb_rows = std::max(cb_rows, (size_t)c->rd.sm_count * ELOC2D_TC_ROWS);
+  o.colbuf = take(c->L.dim == 2 ? cb_rows * c->L.Lx * dh * es : 0);
   o.adj = take(R * (c->ck ? c->ck : N) * c->adjw * es);
   o.adjcol = take(c->L.dim == 2 ? R * c->L.Lx * dh * es : 0);
   o.O = take(R * np * es);
@@ -309,6 +315,24 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.nck = c->nck;
       e.dhm = c->L.dh;
       CU(eloc_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
+    } else if (f32(c) && c->ck == 0 && gram_tc_available() &&
+               eloc2d_tc_supported(c->L.dim, c->L.dh)) {
+      // 2D tensor-core engine: 128-row tiles, one CTA per SM
+      Eloc2dTcArgs e{};
+      e.pack = reinterpret_cast<const float *>(a.pack);
+      e.oWgT = (int)c->P.WgT; e.oxw = (int)c->P.xw; e.obias = (int)c->P.bias;
+      e.ohead = (int)c->P.head; e.ohc = (int)c->P.hc; e.oU12T = (int)c->P.U12T;
+      e.spins = spins;
+      e.hcache = reinterpret_cast<const float *>(a.hcache);
+      e.lccache = reinterpret_cast<const float *>(a.lccache);
+      e.N = c->L.N; e.Lx = c->L.Lx; e.cplx = c->L.cplx; e.zmask = c->L.zmask; e.ns = ns;
+      e.tiles_per_op = (int)((ns + ELOC2D_TC_ROWS - 1) / ELOC2D_TC_ROWS);
+      e.ntiles = e.tiles_per_op * c->n_off;
+      e.op_f = c->d_opf; e.item_s = a.item_s; e.item_e = a.item_e; e.item_cnt = a.item_cnt;
+      e.contrib = a.contrib;
+      e.colbuf = reinterpret_cast<float *>(a.colbuf);
+      e.err = W<int>(c, c->off.sstat);
+      CU(eloc2d_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
     }

@@ -259,19 +259,19 @@ def test_eloc_tensor_core_engine_mixed(model, ham):
     assert rel_err(cplx(c64.local_energy(thd, spd)), O.local_energy(model, ham, th, sp)) < RTOL64
 
 
-# 2D lattices with hidden size 64 run the warp-MMA engine in the mixed
-# context: 64-row tiles with a ragged tail, more tiles than CTAs (ns = 300 on
-# the 4x4 J1-J2 model gives 42 operators x 5 tiles), an odd row length, two
+# 2D lattices with hidden size 64 run the tensor-core engine in the mixed
+# context: 128-row tiles with a ragged tail, more tiles than CTAs (ns = 700 on
+# the 4x4 J1-J2 model gives 42 operators x 6 tiles), an odd row length, two
 # columns (a row turn every other site), real and complex heads, the mask
 E2D_MODELS = [
-    (ModelSpec(2, 4, 4, 64, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 300),
+    (ModelSpec(2, 4, 4, 64, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 700),
     (ModelSpec(2, 5, 3, 64), HamSpec("j1j2", J1=1.0, J2=0.0), 130),
     (ModelSpec(2, 2, 3, 64, cplx=1), HamSpec("j1j2", J1=1.0, J2=0.25), 70),
 ]
 
 
 @pytest.mark.parametrize("model,ham,ns", E2D_MODELS, ids=["j1j2_4x4_cmask", "heis_5x3", "j1j2_2x3_c"])
-def test_eloc_2d_warp_mma_engine_mixed(model, ham, ns):
+def test_eloc_2d_tensor_core_engine_mixed(model, ham, ns):
     c = ctx(model, ham, "mixed", ns)
     th, thd = theta_dev(model, 4)
     sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
