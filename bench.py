@@ -203,8 +203,19 @@ def measured_peak(key, fallback):
 def eloc_tc_used(model, precision):
     """The connected-configuration engine runs on tcgen05 for mixed 1D chains
     of hidden size 64, and 32 (run with its units padded to 64: the issued
-    tensor work per site is that of 64)."""
-    return precision == "mixed" and model.dim == 1 and model.dh in (32, 64)
+    tensor work per site is that of 64), and for mixed 2D lattices of hidden
+    size 64."""
+    if precision != "mixed":
+        return False
+    return (model.dim == 1 and model.dh in (32, 64)) or (model.dim == 2 and model.dh == 64)
+
+
+def eloc_tc_site_flops(model):
+    """Tensor-pipe flops issued per recomputed site of one configuration:
+    three BF16 products (hi.hi + hi.lo + lo.hi) of the gate product
+    [1 x 64] x [64 x 192], and in 2D also of the state mix [1 x 128] x [128 x 64]."""
+    k = 3 * 64 + (2 * 64 if model.dim == 2 else 0)
+    return 3 * 2 * 64 * k
 
 
 def eloc_roofline(w, ms, sites=None):
@@ -222,13 +233,15 @@ def eloc_roofline(w, ms, sites=None):
     dh = w.model.dh
     alg = sites * site_flops(w.model)
     if eloc_tc_used(w.model, w.precision):
-        fl = sites * 3 * 2 * 64 * 3 * 64
+        fl = sites * eloc_tc_site_flops(w.model)
         peak, src = measured_peak("bf16_tflops_sustained", 1400.0)
         ach = fl / (ms * 1e-3) / 1e12
-        sha = src_sha("paper_2608_18065_b300/csrc/eloc_tc.cu", "paper_2608_18065_b300/csrc/tc_common.cuh")
-        return {"kernel": "k_eloc_tc (eloc_suffix)", "bound": "tensor", "achieved": ach,
+        kern = "k_eloc_tc" if w.model.dim == 1 else "k_eloc2d_tc"
+        sha = src_sha("paper_2608_18065_b300/csrc/%s.cu" % kern[2:],
+                      "paper_2608_18065_b300/csrc/tc_common.cuh")
+        return {"kernel": kern + " (eloc_suffix)", "bound": "tensor", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": load_traffic("k_eloc_tc", sha, w.name),
+                "traffic": load_traffic(kern, sha, w.name),
                 "peak_source": src + ", BF16 dense, sustained",
                 "flops_per_launch": fl, "fp32_equiv_flops_per_launch": alg,
                 "fp32_equiv_tflops": alg / (ms * 1e-3) / 1e12, "ms_per_launch": ms}
@@ -679,7 +692,9 @@ def run_batched(args):
     roof = None
     if dom == "eloc_suffix" and eloc_ms > 0:
         ach = eloc_flops / (eloc_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_forward<MODE_ELOC> 2D (eloc_suffix, all instances)", "bound": "alu",
+        roof = {"kernel": "2D E_loc engines (eloc_suffix, all instances; k_eloc2d_tc for "
+                          "mixed d_h = 64, k_forward<MODE_ELOC> otherwise; FP32-equivalent flops)",
+                "bound": "alu",
                 "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",

@@ -2,9 +2,6 @@
 // dispatching the runtime hidden size and lattice dimension onto the
 // compile-time instantiations.
 #pragma once
-#include <type_traits>
-
-#include "eloc2d_mma.cuh"
 #include "launch.h"
 
 namespace nqs {
@@ -52,30 +49,9 @@ static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStr
   return cudaGetLastError();
 }
 
-// 2D FP32 hidden size 64 local energies with every state cached: the
-// warp-MMA engine (64-row tiles, as the SIMT engine, so the column buffers
-// are sized alike).
-template <typename T, int DH, int DIM> constexpr bool eloc2d_mma_case() {
-  return std::is_same<T, float>::value && DIM == 2 && DH == e2d::DH &&
-         Rows<float>::ELOC_RT_2D * Rows<float>::ELOC_RG == e2d::R;
-}
-
-inline cudaError_t eloc2d_mma_run(const RecDesc &d, FwdArgs<float> a, int max_grid, cudaStream_t st) {
-  const size_t smem = eloc2d_mma_smem_bytes(d.N);
-  cudaError_t e = cudaFuncSetAttribute(k_eloc2d_mma<e2d::DH>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int grid = a.ntiles < max_grid ? a.ntiles : max_grid;
-  if (grid <= 0) return cudaSuccess;
-  k_eloc2d_mma<e2d::DH><<<grid, e2d::NTH, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
 template <typename T, int DH, int DIM>
 static cudaError_t fwd_dim(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, cudaStream_t st) {
   constexpr int ERT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
-  if constexpr (eloc2d_mma_case<T, DH, DIM>())
-    if (mode == MODE_ELOC && a.ck == 0) return eloc2d_mma_run(d, a, max_grid, st);
   if (mode == MODE_SAMPLE)
     return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_SAMPLE,
                    sample_groups<T, DH>()>(d, a, max_grid, st);
@@ -111,17 +87,6 @@ static int eloc_grid_dim(const RecDesc &d) {
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, Tile<DH>::UG * RG, smem) != cudaSuccess)
     return 0;
-  if constexpr (eloc2d_mma_case<T, DH, DIM>()) {
-    // the column buffers serve whichever engine runs: size for the larger grid
-    const size_t s2 = eloc2d_mma_smem_bytes(d.N);
-    int per2 = 0;
-    if (cudaFuncSetAttribute(k_eloc2d_mma<e2d::DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)s2) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_eloc2d_mma<e2d::DH>, e2d::NTH, s2) !=
-            cudaSuccess)
-      return 0;
-    per = per > per2 ? per : per2;
-  }
   return per * d.sm_count;
 }
 
