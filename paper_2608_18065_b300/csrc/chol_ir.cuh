@@ -315,11 +315,12 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
   if (!gsync()) return;
 
   // (1) FP32 right-looking Cholesky.  With look-ahead CTA 0 solves the
-  // panel rows of the next diagonal block itself, joins the first barrier
-  // of the panel without waiting at it, updates and factors that block and
-  // publishes it before the second barrier; the other CTAs solve the panel
-  // rows (the same arithmetic, so the same values) and update the rest of
-  // the trailing matrix.
+  // panel rows of the next diagonal block itself and writes them, joins the
+  // first barrier of the panel without waiting at it, updates and factors
+  // that block and publishes it before the second barrier; the other CTAs
+  // solve the panel rows below that block and update the rest of the
+  // trailing matrix.  (CTA 0 alone writes the rows it reads at the start of
+  // the panel, so no other CTA can overwrite them before it has read them.)
   const bool la = G > 1;
   const int Gr = la ? G - 1 : G;               // CTAs that solve panel rows
   const int gr = la ? g - 1 : g;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
     const bool look = la && g == 0;
     // panel rows are requested before the published block
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t rfirst = r0 + (int64_t)gr * (IR_THREADS / 32) + warp;
+    const int64_t rfirst = r0 + (la ? m1 : 0) + (int64_t)gr * (IR_THREADS / 32) + warp;
     if (look) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -373,10 +374,14 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
       if (tr > 0) {
         panel_row_solve<4>(v, D, rinv, m, lane);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ta[(warp + 8 * q) * TS + lane] = v[q];
+        for (int q = 0; q < 4; ++q) {
+          const int row = warp + 8 * q;
+          ta[row * TS + lane] = v[q];
+          if (row < m1 && lane < m) L[(r0 + row) * n + c0 + lane] = v[q];
+        }
       }
       ++ep;
-      cc_arrive(a.bar);  // first barrier of the panel, not awaited
+      cc_arrive(a.bar);  // first barrier of the panel (publishes those rows), not awaited
       if (tr > 0) {
         // tile (0, 0) of the trailing matrix from the rows just solved
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
