@@ -180,10 +180,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
   const uint32_t aS = smem_u32(Sh), aV = smem_u32(Vh), bW = smem_u32(Wh), bU = smem_u32(Uh);
   uint32_t ph_h = 0, ph_g = 0;
   bool ok = true;
+  // tiles in rank order (longest suffixes first) from the launch's counter,
+  // taken by one thread and published at a barrier that also makes ok uniform
+  __shared__ int s_tile[2];
+  int par = 0;
+  auto grab = [&]() -> int {
+    if (issuer) s_tile[par] = atomicAdd(a.tile_ctr, 1);
+    if (__syncthreads_or(!ok)) ok = false;
+    const int v = s_tile[par];
+    par ^= 1;
+    return v;
+  };
 
-  for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-    const int op = tile / a.tiles_per_op;
-    const int base = (tile - op * a.tiles_per_op) * TR;
+  for (int tile = grab(); tile < a.ntiles && ok; tile = grab()) {
+    const int rk = tile / a.tiles_per_op;
+    const int op = a.op_f[4 * rk + 3];
+    const int base = (tile - rk * a.tiles_per_op) * TR;
     const int cnt = a.item_cnt[op];
     if (base >= cnt) continue;  // uniform over the CTA
     const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], kst = a.op_f[4 * op + 2];

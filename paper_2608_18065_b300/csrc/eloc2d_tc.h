@@ -16,13 +16,15 @@ struct Eloc2dTcArgs {
   int N, Lx, cplx, zmask;
   int64_t ns;
   int tiles_per_op, ntiles;  // 128-row tiles per operator, total tiles
-  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site
+  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site, rank order
   const int *item_s;      // [n_off][ns] connected samples
   const double *item_e;   // [n_off][ns] matrix elements
   const int *item_cnt;    // [n_off]
   double *contrib;        // [n_off][ns][2]
   float *colbuf;          // [grid][128][Lx][64]: recomputed states by lattice column
   int *err;               // device status word (NQS_ERR_TIMEOUT on a wait that ran out)
+  int *tile_ctr;          // zeroed before the launch: tiles handed out in rank order
+                          // (op_f[4 i + 3] = the operator of rank i, longest suffix first)
 };
 
 constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.N;
   const int nh = a.cplx ? 4 : 2;
+  __shared__ int s_tile[SLOTS][2];  // the slot's next tile, double-buffered
 
   // zero the augmented blocks (columns 3..15 stay zero)
   for (int e = tid; e < 2 * XTILE_B / 16; e += THREADS)
@@ -253,9 +254,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
     const uint32_t gcol = dcol + (uint32_t)(3 * UH * half);  // this half's gate columns
     uint32_t acc_ph = 0;
     bool ok = true;
-    for (int tile = blockIdx.x * SLOTS + t; tile < a.ntiles && ok; tile += gridDim.x * SLOTS) {
-      const int op = tile / a.tiles_per_op;
-      const int base = (tile - op * a.tiles_per_op) * TR;
+    // tiles in rank order (longest suffixes first) from the launch's counter:
+    // the slot's issuer takes one and publishes it at a barrier of the slot,
+    // which also makes ok uniform over the slot
+    int par = 0;
+    auto grab = [&]() -> int {
+      if (issuer) s_tile[t][par] = atomicAdd(a.tile_ctr, 1);
+      if (bar_any(1 + t, 2 * TR, !ok)) ok = false;
+      const int v = s_tile[t][par];
+      par ^= 1;
+      return v;
+    };
+    for (int tile = grab(); tile < a.ntiles && ok; tile = grab()) {
+      const int rk = tile / a.tiles_per_op;
+      const int op = a.op_f[4 * rk + 3];
+      const int base = (tile - rk * a.tiles_per_op) * TR;
       const int cnt = a.item_cnt[op];
       if (base >= cnt) continue;  // uniform over the tile's 256 threads
       const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], j0 = a.op_f[4 * op + 2];

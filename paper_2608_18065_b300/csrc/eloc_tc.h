@@ -16,7 +16,7 @@ struct ElocTcArgs {
   int N, cplx, zmask;
   int64_t ns;
   int tiles_per_op, ntiles;  // 128-row tiles per operator, total tiles
-  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site
+  const int *op_f;        // [n_off][4]: flip sites f1, f2, first changed site, rank order
   const int *item_s;      // [n_off][ns] connected samples
   const double *item_e;   // [n_off][ns] matrix elements
   const int *item_cnt;    // [n_off]
@@ -24,6 +24,8 @@ struct ElocTcArgs {
   int *err;               // device status word
   int ck, nck;            // checkpoints: hcache holds h_{m ck - 1} in slot m - 1 (ck > 0)
   int dhm;                // the model's hidden size (64, or 32 padded with zero units)
+  int *tile_ctr;          // zeroed before the launch: tiles handed out in rank order
+                          // (op_f[4 i + 3] = the operator of rank i, longest suffix first)
 };
 
 bool eloc_tc_supported(int dim, int dh);

@@ -26,7 +26,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dg32, dstep, tth, tmo, tstats, hseg, carry, dlm, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dg32, dstep, tth, tmo, tstats, hseg, carry, dlm, tctr, total;
 };
 
 }  // namespace
@@ -185,6 +185,7 @@ void carve(nqs_ctx *c) {
   o.dth = take(np * 8);
   o.frob = take(1024 * 8);
   o.sstat = take(64);
+  o.tctr = take(64);  // tile counter of the tensor-core local-energy engines
   o.split = take(gram_tc_split_bytes(R, np));
   o.crhs = take(R * 8);
   o.cy = take(R * 8);
@@ -314,6 +315,8 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.ck = c->ck;
       e.nck = c->nck;
       e.dhm = c->L.dh;
+      e.tile_ctr = W<int>(c, c->off.tctr);
+      CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
       CU(eloc_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else if (f32(c) && c->ck == 0 && gram_tc_available() &&
                eloc2d_tc_supported(c->L.dim, c->L.dh)) {
@@ -332,6 +335,8 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.contrib = a.contrib;
       e.colbuf = reinterpret_cast<float *>(a.colbuf);
       e.err = W<int>(c, c->off.sstat);
+      e.tile_ctr = W<int>(c, c->off.tctr);
+      CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
       CU(eloc2d_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
@@ -906,8 +911,14 @@ nqs_status nqs_create_ex(const nqs_model_desc *model, const nqs_ham_desc *ham, i
   c->n_diag = (int)dg.size();
   for (const OffOp &o : off) c->op_start.push_back(o.start);
   std::vector<int> opf(4 * std::max<size_t>(off.size(), 1));
+  // field 3 of entry i: the operator of rank i by first changed site, so the
+  // tensor-core engines hand out the longest suffixes first
+  std::vector<int> rank(off.size());
+  for (size_t i = 0; i < off.size(); ++i) rank[i] = (int)i;
+  std::stable_sort(rank.begin(), rank.end(), [&](int x, int y) { return off[x].start < off[y].start; });
   for (size_t i = 0; i < off.size(); ++i) {
-    opf[4 * i] = off[i].f1; opf[4 * i + 1] = off[i].f2; opf[4 * i + 2] = off[i].start; opf[4 * i + 3] = 0;
+    opf[4 * i] = off[i].f1; opf[4 * i + 1] = off[i].f2; opf[4 * i + 2] = off[i].start;
+    opf[4 * i + 3] = rank[i];
   }
   bool ok = cudaMalloc(&c->d_off, sizeof(OffOp) * std::max<size_t>(off.size(), 1)) == cudaSuccess &&
             cudaMalloc(&c->d_diag, sizeof(DiagOp) * std::max<size_t>(dg.size(), 1)) == cudaSuccess &&

@@ -131,7 +131,7 @@ template <typename T> struct FwdArgs {
   int gw;
   // ELOC
   int tiles_per_op;
-  const int *op_f;         // [n_off*4]: f1, f2, start, pad
+  const int *op_f;         // [n_off*4]: f1, f2, start, rank order (unused here)
   const int *item_s;       // [n_off*Ns]
   const double *item_e;    // [n_off*Ns]
   const int *item_cnt;     // [n_off]
