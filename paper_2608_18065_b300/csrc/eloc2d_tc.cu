@@ -42,8 +42,9 @@ constexpr int BU = DH * 128;            // one K atom of [U1 | U2], N = 64 rows
 constexpr int TS = NG + 4;              // stride of the bias / input table rows (floats)
 // B: W hi, lo; U hi (atoms hor, ver), U lo (hor, ver); A: S hi, lo, V hi, lo
 constexpr int OFF_BW = 0, OFF_BU = 2 * BW, OFF_S = OFF_BU + 4 * BU, OFF_V = OFF_S + 2 * ATOM;
-constexpr int OFF_VS = OFF_V + 2 * ATOM;        // float [128][64]: next vertical states (FP32)
-constexpr int OFF_TAB = OFF_VS + TR * DH * 4;   // float [9][TS]: per input pair (d0, d1)
+constexpr int VSS = DH + 4;                     // staging row stride (floats): rows on distinct banks
+constexpr int OFF_VS = OFF_V + 2 * ATOM;        // float [128][VSS]: next vertical states (FP32)
+constexpr int OFF_TAB = OFF_VS + TR * VSS * 4;  // float [9][TS]: per input pair (d0, d1)
 constexpr int OFF_BH = OFF_TAB + 9 * TS * 4;    // float [64]: b_h
 constexpr int OFF_HEAD = OFF_BH + DH * 4;       // float [4][64]: head rows
 constexpr int OFF_HC = OFF_HEAD + 4 * DH * 4;   // float [4]: head biases
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
   float *shead = reinterpret_cast<float *>(sm + OFF_HEAD);
   float *shc = reinterpret_cast<float *>(sm + OFF_HC);
   float4 *zx = reinterpret_cast<float4 *>(sm + OFF_ZX);
-  float *vsrow = reinterpret_cast<float *>(sm + OFF_VS);  // + row * DH + UH * half below
+  float *vsrow = reinterpret_cast<float *>(sm + OFF_VS);  // + row * VSS + UH * half below
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + OFF_BAR);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_TM);
 
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
   const int quarter = warp & 3, half = warp >> 2;
   const int row = 32 * quarter + lane;
   const int N = a.N, Lx = a.Lx;
-  float4 *vs = reinterpret_cast<float4 *>(vsrow + row * DH + UH * half);  // this thread's staging
+  float4 *vs = reinterpret_cast<float4 *>(vsrow + row * VSS + UH * half);  // this thread's staging
 
   // weights as B[n][k] planes: W row n = 64 j + unit (gate j), U atoms
   // B[unit][k] over the horizontal (atom 0) and vertical (atom 1) inputs
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
   const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
   const uint32_t hcol = lanes + (uint32_t)(UH * half);       // h' of this half's units
   const uint32_t gcol = lanes + (uint32_t)(DH + UH * half);  // gate j at + 64 j
-  const bool issuer = tid == 0;
+  const bool issuer = tid == 128;  // a half-1 thread (no row work)
   const uint32_t bar_h = smem_u32(&bars[0]), bar_g = smem_u32(&bars[1]);
   const uint32_t aS = smem_u32(Sh), aV = smem_u32(Vh), bW = smem_u32(Wh), bU = smem_u32(Uh);
   uint32_t ph_h = 0, ph_g = 0;
@@ -313,13 +314,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
       // site's own, at the first site of a lattice row), spins, and this
       // site's cached terms
       bool turn = false;
-      int s_next = 2, s_vnext = 2;
-      if (k + 1 < N) {
+      int r_next = 0, r_vnext = 0, k_v = -1;  // raw spins: flipped at the end of the site,
+      if (k + 1 < N) {                        // when the loads have landed
         const int m1 = (k + 1) % Lx;
         if (m1 == 0) turn = true;
         else fetch_ver(k + 1);
-        s_next = spin_at(k + 1);
-        if (k + 1 >= Lx) s_vnext = spin_at(k + 1 - 2 * m1 - 1);
+        r_next = __ldcg(sp + k + 1);
+        if (k + 1 >= Lx) {
+          k_v = k + 1 - 2 * m1 - 1;
+          r_vnext = __ldcg(sp + k_v);
+        }
       }
       float2 lc = make_float2(0.f, 0.f);
       if (half == 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * k));
@@ -402,8 +406,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
         lcp = lc;
       }
       s_prev = s_cur;
-      s_cur = s_next;
-      s_ver = s_vnext;
+      s_cur = k + 1 < N ? r_next ^ ((k + 1 == f1 || k + 1 == f2) ? 1 : 0) : 2;
+      s_ver = k_v >= 0 ? r_vnext ^ ((k_v == f1 || k_v == f2) ? 1 : 0) : 2;
     }
     // the last site's row work, then the row's contribution
     tc_fence_before();
