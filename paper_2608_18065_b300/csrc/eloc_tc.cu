@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
       for (int r = 0; r <= L; ++r) {
         const int k = kr + r;  // gates of site k (r < L), head of site k - 1 (r > 0)
         // loads for after the wait: sigma'_k and sigma's cached terms at k - 1
-        const int scur = k < N ? spin_at(k) : 0;
+        const int sraw = k < N ? (int)__ldcg(sp + k) : 0;  // flipped when used, after it lands
         float2 lc = make_float2(0.f, 0.f);
         if (half == 0 && r > 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * (k - 1)));
         if (!mbar_wait(accbar, acc_ph)) ok = false;
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc_tc(const ElocTcArgs a) {
                   make_float4(h8[4 * q], h8[4 * q + 1], h8[4 * q + 2], h8[4 * q + 3]);
             write_planes8(Ahi, Alo, row, UH * half + 8 * g8, h8);
           }
-          sprev = scur;
+          sprev = sraw ^ ((k == f1 || k == f2) ? 1 : 0);
           if (half == 0) write_aug(Aaug, row, sprev);
           fence_async_smem();
           tc_fence_before();
