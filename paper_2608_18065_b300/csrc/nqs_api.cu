@@ -612,15 +612,17 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     ir.status = status;
     ir.need_fp64 = need;
     ir.maxit = 12;
-    // large systems: block substitution instead of the explicit inverse
-    // (measured at n = 4096: the inversion levels took 9 of 16.5 ms)
-    ir.subst = tuned(c) && c->t_chol_subst >= 0 ? c->t_chol_subst : (R >= 2048 ? 1 : 0);
+    // sweeps with the explicit inverse at every size (measured at n = 4096,
+    // probe copy of the kernel: inversion levels 1.67 ms + 3 product sweeps
+    // 0.47 ms, against 4.2 ms for 3 block-substitution sweeps)
+    ir.subst = tuned(c) && c->t_chol_subst >= 0 ? c->t_chol_subst : 0;
     ir.dv = ir.dpart;
     ir.dg = W<float>(c, c->off.dg32);
     const size_t smem = chol_ir_smem(R);
-    // tiles per warp pay off once n is large (measured: 16.5 vs 19.8 ms at
-    // n = 4096, 1.71 vs 0.93 ms at n = 1024)
-    const bool wt = tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var == 1 : R >= 2048;
+    // CTA tiles in batches of four at every size (measured: factor 4.7 ms
+    // against 6.6 ms with a tile per warp at n = 4096; 0.26 ms against 0.93
+    // at n = 1024)
+    const bool wt = tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var == 1 : false;
     const void *kern = wt ? (const void *)k_chol_ir<true> : (const void *)k_chol_ir<false>;
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void *args[] = {&ir};
