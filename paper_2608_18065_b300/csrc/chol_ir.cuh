@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
           // and the outputs' old values) are all in flight together, then
           // are multiplied back to back
           constexpr int TB = 4;
+          constexpr int TU = IR_B + 4;  // row stride: 16-byte rows, float4 reads conflict-free
           const int tx = tid % 32, ty = tid / 32;
           for (int tb0 = gr + cta0; tb0 < ntiles; tb0 += TB * Gr) {
             float va[TB][4], vb[TB][4], vc[TB][4];
@@ -446,25 +447,32 @@ __global__ void __launch_bounds__(IR_THREADS) k_chol_ir(CholIrArgs a) {
             __syncthreads();  // the previous batch is no longer read
 #pragma unroll
             for (int b = 0; b < TB; ++b) {
-              float *sa = wtile + b * 2 * IR_B * TS, *sb = sa + IR_B * TS;
+              float *sa = wtile + b * 2 * IR_B * TU, *sb = sa + IR_B * TU;
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                sa[(ty + 8 * q) * TS + tx] = va[b][q];
-                sb[(ty + 8 * q) * TS + tx] = vb[b][q];
+                sa[(ty + 8 * q) * TU + tx] = va[b][q];
+                sb[(ty + 8 * q) * TU + tx] = vb[b][q];
               }
             }
             __syncthreads();
 #pragma unroll
             for (int b = 0; b < TB; ++b) {
               if (i0s[b] >= n) continue;  // uniform over the CTA
-              const float *sa = wtile + b * 2 * IR_B * TS, *sb = sa + IR_B * TS;
-              // 4 outputs per thread: rows ty + 8q, column tx
+              const float *sa = wtile + b * 2 * IR_B * TU, *sb = sa + IR_B * TU;
+              // 4 outputs per thread: rows ty + 8q, column tx; four k per
+              // 16-byte load (the sums still run over k in order)
               float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-              for (int k = 0; k < IR_B; ++k) {
-                const float bv = sb[tx * TS + k];
+#pragma unroll 2
+              for (int k = 0; k < IR_B; k += 4) {
+                const float4 bv = *reinterpret_cast<const float4 *>(sb + tx * TU + k);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(sa[(ty + 8 * q) * TS + k], bv, acc[q]);
+                for (int q = 0; q < 4; ++q) {
+                  const float4 av = *reinterpret_cast<const float4 *>(sa + (ty + 8 * q) * TU + k);
+                  acc[q] = fmaf(av.x, bv.x, acc[q]);
+                  acc[q] = fmaf(av.y, bv.y, acc[q]);
+                  acc[q] = fmaf(av.z, bv.z, acc[q]);
+                  acc[q] = fmaf(av.w, bv.w, acc[q]);
+                }
               }
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
