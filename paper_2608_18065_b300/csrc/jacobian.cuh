@@ -91,14 +91,14 @@ k_jac_bwd(const BwdArgs<T> A) {
 
   const int tid = threadIdx.x;
   const int ug = tid % UG, rg = tid / UG;
-  // 1D FP32 d_h = 64: the per-site product dh1 = dpd + W_g^T [dau; dar; dg]
-  // (K = 3 d_h) runs as warp-level MMAs, m16n8k16 with BF16 hi.hi + hi.lo +
+  // FP32 d_h = 64 (1D and 2D): the per-site product dh1 = dpd + W_g^T
+  // [dau; dar; dg] (K = 3 d_h; in 2D the adjoint of h') runs as warp-level MMAs, m16n8k16 with BF16 hi.hi + hi.lo +
   // lo.hi and FP32 accumulation, 8 of the 16 rows used.  These products are
   // a dependent chain of N small ones on 8 rows per CTA, which the register
   // operands of warp MMAs serve with the least latency.  Warp w owns units
   // 8w .. 8w + 7 of all 8 rows; lane (lane / 4, lane % 4) = (row g, t) owns
   // units 8w + 2t, 8w + 2t + 1 of row g, where the MMA leaves their sums.
-  constexpr bool WMMA = sizeof(T) == 4 && DIM == 1 && DH == 64 && RT == 1 && RG == 8;
+  constexpr bool WMMA = sizeof(T) == 4 && DH == 64 && RT == 1 && RG == 8;
   const int r0 = WMMA ? (tid & 31) >> 2 : rg * RT;
   const int a0 = WMMA ? 8 * (tid >> 5) + 2 * (tid & 3) : ug * UT;
   const bool row_lead = WMMA ? (tid >> 5) == 0 && (tid & 3) == 0 : ug == 0;
@@ -261,7 +261,7 @@ k_jac_bwd(const BwdArgs<T> A) {
 #pragma unroll
         for (int uu = 0; uu < UT; ++uu) dh1[i][uu] = dpd[i][uu];
       if constexpr (WMMA) {
-        if (k > 0) {
+        if (DIM == 2 || k > 0) {
           const int gq = (tid & 31) >> 2, tq = tid & 3;
           float c[4] = {(float)dh1[0][0], (float)dh1[0][1], 0.f, 0.f};
 #pragma unroll

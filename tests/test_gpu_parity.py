@@ -284,6 +284,31 @@ def test_eloc_2d_tensor_core_engine_mixed(model, ham, ns):
     assert np.max(np.abs(el - el_o)) < TOL_MIXED_ELOC * scale
 
 
+# 2D lattices with hidden size 64 run the reverse sweep's gate product
+# W^T [dau; dar; dg] on warp-level MMAs in the mixed context (the adjoint of
+# h', routed on through U1, U2 to the horizontal and vertical neighbours):
+# complex head with mask (two adjoint seeds), an odd row length, two columns
+E2DJ_MODELS = [
+    (ModelSpec(2, 4, 4, 64, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 150),
+    (ModelSpec(2, 5, 3, 64), HamSpec("j1j2", J1=1.0, J2=0.0), 130),
+    (ModelSpec(2, 2, 3, 64, cplx=1), HamSpec("j1j2", J1=1.0, J2=0.25), 70),
+]
+
+
+@pytest.mark.parametrize("model,ham,ns", E2DJ_MODELS, ids=["j1j2_4x4_cmask", "heis_5x3", "j1j2_2x3_c"])
+def test_jacobian_2d_warp_mma_mixed(model, ham, ns):
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 6)
+    sp = random_spins(model, ns, seed=13, zero_mag=bool(model.zmask))
+    J = c.jacobian(thd, torch.tensor(sp, device="cuda")).cpu().numpy().astype(np.float64)
+    J_o = O.jacobian(model, th, sp)
+    assert J.shape == J_o.shape
+    assert rel_err(J, J_o) < TOL_MIXED_JAC
+    # every entry within the tolerance of the largest entry of its row
+    scale = np.max(np.abs(J_o), axis=1, keepdims=True)
+    assert np.max(np.abs(J - J_o) / scale) < TOL_MIXED_JAC
+
+
 def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
     """A matrix whose FP32 Cholesky breaks down (kappa ~ 1e12) but is SPD in
     FP64: the mixed context must still return the FP64 solution."""
