@@ -132,7 +132,15 @@ typedef struct nqs_ctx nqs_ctx;
  * device.  precision: NQS_PREC_FP64 runs every stage in FP64 (the plain GPU
  * path); NQS_PREC_MIXED runs the recurrences and O in FP32, T and O'x as
  * split BF16x3 tensor-core products with FP32 accumulation, and the
- * centring, reductions and the regularized solve in FP64.  max_samples
+ * centring, reductions and the regularized solve in FP64.  In the mixed
+ * context the per-site products of hidden size 64 (32 for 1D local
+ * energies, with zero-padded units) are also split BF16x3 products with
+ * FP32 accumulation:
+ *  - the local-energy recomputations (1D and 2D) and the rows of O (1D) on
+ *    tcgen05;
+ *  - the gate products of the 1D sampler and of the reverse sweep (1D and
+ *    2D) on warp-level MMAs.
+ * Nonlinearities and state updates stay in FP32.  max_samples
  * bounds Ns of every later call.  *out receives the context; release it with
  * nqs_destroy.  Errors: NQS_ERR_ARG for an invalid description,
  * NQS_ERR_UNSUPPORTED for a hidden size not built. */
