@@ -14,6 +14,7 @@ Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -880,6 +881,88 @@ def run_lambda_grid(args):
     return 0
 
 
+def qgt_error_from_gram(G, n_ref, n_sub, cplx):
+    """||S_ref - S_sub||_F / ||S_ref||_F of Fig. 5b from the Gram G = X X^T of
+    the stacked centred rows X = [Re Obar_ref; (Im Obar_ref;) Re Obar_sub;
+    (Im Obar_sub)], without the N_p x N_p metrics: S = Obar^dagger Obar has
+    ||S||_F = ||Obar Obar^dagger||_F and tr(S_ref S_sub) =
+    ||Obar_ref Obar_sub^dagger||_F^2, and each complex Gram block follows from
+    the real ones, (A + iB)(C + iD)^dagger = A C^T + B D^T + i (B C^T - A D^T)."""
+    G = np.asarray(G, dtype=np.float64)
+    k = 2 if cplx else 1
+    r0, s0 = 0, k * n_ref
+    def blk(i0, ni, j0, nj):
+        a = G[i0:i0 + ni, j0:j0 + nj]
+        if not cplx:
+            return a.astype(np.complex128)
+        ar, br = i0, i0 + ni
+        ac, bc = j0, j0 + nj
+        re = G[ar:ar + ni, ac:ac + nj] + G[br:br + ni, bc:bc + nj]
+        im = G[br:br + ni, ac:ac + nj] - G[ar:ar + ni, bc:bc + nj]
+        return re + 1j * im
+    rr = blk(r0, n_ref, r0, n_ref)
+    ss = blk(s0, n_sub, s0, n_sub)
+    rs = blk(r0, n_ref, s0, n_sub)
+    nr2 = float(np.sum(np.abs(rr) ** 2))
+    d2 = nr2 + float(np.sum(np.abs(ss) ** 2)) - 2.0 * float(np.sum(np.abs(rs) ** 2))
+    return float(np.sqrt(max(d2, 0.0) / nr2))
+
+
+def qgt_subsample_errors(ctx, theta, sp_ref, sp_subs):
+    """Fig. 5b errors of the subsampled SR metric for each spin set of
+    sp_subs against the reference spins sp_ref: Jacobian rows from the
+    library (nqs_jacobian), centred and scaled, stacked, and one FP64 Gram
+    (nqs_gram) per subsample."""
+    import torch
+    cplx = bool(ctx.model.cplx)
+
+    def rows(sp):
+        n = sp.shape[0]
+        J = ctx.jacobian(theta, sp)
+        blocks = [J[:n]] + ([J[n:2 * n]] if cplx else [])
+        return [(b - b.mean(0)) / math.sqrt(n) for b in blocks]
+
+    ref = rows(sp_ref)
+    out = []
+    for sp in sp_subs:
+        X = torch.cat(ref + rows(sp), 0).contiguous()
+        G = ctx.gram(X).cpu().numpy()
+        out.append(qgt_error_from_gram(G, sp_ref.shape[0], sp.shape[0], cplx))
+    return out
+
+
+def run_qgt_subsample(args):
+    """Fig. 5b: relative error ||S - S~||_F / ||S||_F of the SR metric from
+    N_s samples against a reference from 4096 samples (>= N_p), for the 6 x 6
+    J1-J2 model (J2 = 0.5, complex head, Marshall sign, zero magnetisation)
+    at theta_0, versus alpha = sqrt(N_s) / N_p.  The paper uses d_h = 10;
+    the library builds hidden sizes 8, 16, 32, ..., and this run takes 16.
+    FP64 context: exact samples, FP64 Jacobian and Gram.  Reports the fitted
+    slope of log(error) against log(alpha) (Eq. UB predicts -1 for the
+    bound)."""
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import HamSpec, ModelSpec, init_theta
+    dev = torch.device("cuda", 0)
+    model, ham = ModelSpec(2, 6, 6, 16, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5)
+    n_ref, subs = 4096, [16, 32, 64, 128, 256, 512, 1024, 2048]
+    t0 = time.time()
+    c = nqs.Context(model, ham, "fp64", n_ref, device=dev)
+    th = torch.tensor(init_theta(model, 7), device=dev)
+    sp_ref, _ = c.sample(th, n_ref, seed=101, step=0)
+    sp_all, _ = c.sample(th, max(subs), seed=202, step=0)
+    errs = qgt_subsample_errors(c, th, sp_ref, [sp_all[:n] for n in subs])
+    npar = c.np
+    alphas = [math.sqrt(n) / npar for n in subs]
+    slope = float(np.polyfit(np.log(alphas), np.log(errs), 1)[0])
+    line = {"metric": "subsampled SR-metric error (Sec. III, Fig. 5b)", "workload": "qgt_subsample",
+            "model": "j1j2_6x6_dh16_cplx", "n_params": npar, "n_ref": n_ref,
+            "points": [{"ns": n, "alpha": a, "rel_err": e} for n, a, e in zip(subs, alphas, errs)],
+            "loglog_slope": slope, "seconds": time.time() - t0}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -888,6 +971,8 @@ def main():
         return run_batched(args)
     if args.workload == "lambda_grid":
         return run_lambda_grid(args)
+    if args.workload == "qgt_subsample":
+        return run_qgt_subsample(args)
     return run_ours(args)
 
 

@@ -107,3 +107,27 @@ def test_nonfinite_and_arguments():
         nqs.spectrum(_dev(np.eye(4)), -1.0)
     with pytest.raises(nqs.NqsError):
         nqs.spectrum(_dev(np.eye(4)), 0.1, m=0)
+
+
+def test_subsampled_sr_metric_error_matches_oracle():
+    """Fig. 5b: ||S - S~||_F / ||S||_F from the library's Jacobian rows and
+    one FP64 Gram of the stacked centred rows (bench.py) against the oracle's
+    explicit N_p x N_p metrics built from the oracle's Jacobian."""
+    import bench
+    from oracle import oracle as O
+    from oracle import qgt
+    from paper_2608_18065_b300.inputs import random_spins
+    model, ham = ModelSpec(2, 3, 3, 8, cplx=1, marshall=1), HamSpec("j1j2", J2=0.5)
+    n_ref, subs = 200, [20, 60]
+    c = ctx(model, ham, "fp64", n_ref)
+    th, thd = theta_dev(model, 3)
+    sp_ref = random_spins(model, n_ref, seed=1)
+    sp_sub = random_spins(model, max(subs), seed=2)
+    dev = thd.device
+    errs = bench.qgt_subsample_errors(c, thd, torch.tensor(sp_ref, device=dev),
+                                      [torch.tensor(sp_sub[:n], device=dev) for n in subs])
+    J_ref = O.jacobian(model, th, sp_ref)
+    for n, e in zip(subs, errs):
+        e_o = qgt.subsampled_error(J_ref, n_ref, O.jacobian(model, th, sp_sub[:n]), n, True)
+        assert e_o > 0
+        assert abs(e - e_o) < 1e-9 * e_o
