@@ -18,10 +18,15 @@
 // finished reading it before the next value is written), a second pair
 // holds the vertical neighbour.  Thread (quarter q, half f) of the 8 warps
 // owns row 32 q + lane (its tensor-memory lane) and units 32 f .. 32 f + 31:
-// it splits its own states into the planes, keeps h' in registers for the
-// update, and writes h_k to the column buffer.  The output heads run in FP32
-// on the SIMT side; a row's log-softmax, mask and log-amplitude sums of site
-// k run on its half-0 thread during the next site's first product.  Every
+// it splits its own states into the planes, reads h' back from tensor
+// memory for the update (the columns hold it until the next site's first
+// product), and writes h_k to the column buffer.  The next site's vertical
+// states are staged by cp.async into a per-thread FP32 area while a site
+// runs.  Tiles come from a per-launch counter, longest suffixes first.  The
+// MMAs are issued by a half-1 thread, which has no row work.  The output
+// heads run in FP32 on the SIMT side; a row's log-softmax, mask and
+// log-amplitude sums of site k run on its half-0 thread during the next
+// site's first product.  Every
 // mbarrier wait is bounded and its outcome OR-reduced at the next barrier;
 // on expiry the CTA flags NQS_ERR_TIMEOUT, drains its MMAs, frees its tensor
 // memory and exits.
