@@ -184,7 +184,7 @@ nqs_status nqs_workspace_size(const nqs_ctx *ctx, size_t *bytes);
  * are in flight; calls on one context must not overlap on the device. */
 nqs_status nqs_set_workspace(nqs_ctx *ctx, void *dev_ptr, size_t bytes);
 
-/* Exact autoregressive sampling (Sec. II.A, Algorithm 1 line 3).
+/* Exact autoregressive sampling (Sec. II.A, Algorithm 1, sampling step).
  * theta: device [Np] FP64.  Writes spins (device [ns*N] uint8) and logpsi
  * (device [ns*2] FP64) using u(seed, step, s, k).  Also fills the context's
  * hidden-state cache used by later stages of a step. */
@@ -221,7 +221,7 @@ nqs_status nqs_logpsi_vjp(nqs_ctx *ctx, const double *theta, const uint8_t *spin
                           int64_t ns, const double *grad_logpsi, double *grad_theta,
                           void *stream);
 
-/* T = A A^T (Algorithm 1 line 6) for a row-major A [R x np] of centred,
+/* T = A A^T (Algorithm 1, Gram step) for a row-major A [R x np] of centred,
  * scaled log-derivatives (rows = samples): FP64 A -> FP64 T on CUDA cores
  * for the FP64 context; FP32 A -> FP64 T via BF16x3 tcgen05 products with
  * FP32 accumulation for the mixed context.  T: device [R*R], both
@@ -241,7 +241,7 @@ nqs_status nqs_regularized_solve(nqs_ctx *ctx, double *T, int64_t R,
                                  double lambda, const double *b, double *x,
                                  int32_t *dev_status, void *stream);
 
-/* One minSR step (Algorithm 1 lines 3-9).  theta, momentum: device [Np]
+/* One minSR step (Algorithm 1, all steps).  theta, momentum: device [Np]
  * FP64, updated in place unless the device-side checks fail, in which case
  * both are left unchanged.  dev_stats: device nqs_step_stats. */
 nqs_status nqs_minsr_step(nqs_ctx *ctx, double *theta, double *momentum,
@@ -272,8 +272,10 @@ nqs_status nqs_minsr_step_ex(nqs_ctx *ctx, double *theta, double *momentum,
  *    was rejected), divides it by omega if rho > 3/4 (stats.rho,
  *    stats.lambda_next).
  * The extra sampling and local-energy pass roughly doubles the forward
- * work of a step.  Synchronous (copies lambda0 to the device); call it
- * outside stream capture.  Invalidates the context's captured graph. */
+ * work of a step.  Synchronous: waits for all work on the device (so a
+ * step in flight on any stream finishes before the damping it reads or
+ * writes is replaced), then copies lambda0 to the device; call it outside
+ * stream capture.  Invalidates the context's captured graph. */
 nqs_status nqs_set_damping(nqs_ctx *ctx, double omega, double lambda0);
 
 /* ------------------------------------------------------------ autotuner */
@@ -333,7 +335,7 @@ nqs_status nqs_batch_create(int n, nqs_ctx *const *ctxs, nqs_batch **out);
 /* Synchronises the device, then frees the batch (not the contexts). */
 nqs_status nqs_batch_destroy(nqs_batch *b);
 
-/* One minSR step of every instance (Algorithm 1 lines 3-9 each, exactly as
+/* One minSR step of every instance (Algorithm 1, all steps each, exactly as
  * nqs_minsr_step of that context would compute it: the results are
  * bit-identical).  thetas, moms: host arrays of n device pointers [Np_i]
  * FP64, updated in place; hps: host array of n hyper-parameter sets;
@@ -381,11 +383,13 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,
  * its implicit synchronisation are not allowed).
  * model: as for nqs_create; theta: device [Np] FP64; spins: device [n*N]
  * uint8; logpsi: device [n*2] FP64 (re, im), same values as nqs_logpsi of an
- * NQS_PREC_FP64 context.  Scratch (the packed theta and the hidden-state
- * cache, 8*(n*N*dh) bytes plus the packed weights) comes from one file-scope
- * device array of NQS_NOALLOC_SCRATCH_BYTES that every GPU loading the
- * library reserves until the process exits; larger n returns
- * NQS_ERR_WORKSPACE without launching anything (split the batch).  The first
+ * NQS_PREC_FP64 context.  Scratch (the packed theta and, for 2D lattices,
+ * the hidden-state cache of 8*(n*N*dh) bytes that the vertical neighbours
+ * read back; a 1D chain needs the packed weights only) comes from one
+ * file-scope device array of NQS_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library reserves until the process exits; a 2D batch whose
+ * cache does not fit, or n > 2^31 - 1, returns NQS_ERR_WORKSPACE without
+ * launching anything (split the batch).  The first
  * call on each device looks up the array's address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
  * All calls share the one array and leave their data in it: calls that

@@ -718,9 +718,9 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
   double *dth = (double *)malloc(sizeof(double) * (size_t)np);
   if (!spins || !lp || !el || !O || !T || !eps || !x || !dth) return -2;
 
-  /* line 3: draw Ns configurations */
+  /* Alg. 1, sampling: draw Ns configurations */
   or_sample(m, theta, ns, hp->seed, (uint64_t)hp->step_index, spins, lp);
-  /* line 4: local energies and E */
+  /* Alg. 1, energy: local energies and E */
   or_local_energy(m, H, theta, spins, ns, el);
   double Er = 0.0, Ei = 0.0;
   for (int64_t s = 0; s < ns; ++s) { Er += el[2 * s]; Ei += el[2 * s + 1]; }
@@ -734,7 +734,7 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
   st->E_re = Er; st->E_im = Ei; st->var = var;
   st->vscore = (double)N * var / (Er * Er);
 
-  /* line 5: O_ks = d log Psi / d theta_k / sqrt(Ns), centred over samples,
+  /* Alg. 1, log-derivatives: O_ks = d log Psi / d theta_k / sqrt(Ns), centred over samples,
    * separately for the real and the imaginary rows */
   or_jacobian(m, theta, spins, ns, O);
   double isq = 1.0 / sqrt((double)ns);
@@ -754,7 +754,7 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
     eps[s] = 2.0 * (el[2 * s] - Er) * isq;
     if (m->cplx) eps[ns + s] = 2.0 * (el[2 * s + 1] - Ei) * isq;
   }
-  /* line 6: T = O'^T O' */
+  /* Alg. 1, Gram: T = O'^T O' */
   or_gram(O, R, np, T);
   double nT = 0.0;
   for (int64_t i = 0; i < R * R; ++i) nT += T[i] * T[i];
@@ -764,7 +764,7 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
   st->normT = nT;
   st->lambda = lam;
   if (out && out->T) memcpy(out->T, T, sizeof(double) * (size_t)(R * R));
-  /* line 7: x = (T + lambda I)^{-1} eps-bar' */
+  /* Alg. 1, solve: x = (T + lambda I)^{-1} eps-bar' */
   for (int64_t i = 0; i < R; ++i) T[i * R + i] += lam;
   int ok = or_cholesky_solve(T, R, eps, x);
   int status = 0;
@@ -826,7 +826,7 @@ int or_minsr_step(const or_model *m, const or_ham *H, double *theta, double *mom
     else if (rho > 0.75) st->lambda_next = lam / hp->lm_omega;
     free(th2); free(sp2); free(lp2); free(el2);
   }
-  /* lines 8-9: momentum and update, only for an accepted step */
+  /* Alg. 1, momentum and update, only for an accepted step */
   if (status == 0) {
     for (int64_t k = 0; k < np; ++k) {
       mom[k] = hp->mu * mom[k] + (1.0 - hp->mu) * dth[k];

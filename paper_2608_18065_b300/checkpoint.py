@@ -28,13 +28,15 @@ def save(path, theta, mom, next_step, hp: HParams, stats, damping_omega=0.0):
 
 
 def load(path, ctx):
-    """theta and m on ctx's device, the index of the next step and hp; turns
-    the context's damping on at the saved damping when it was on."""
+    """theta and m on ctx's device, the index of the next step and hp; sets
+    the context's damping to the saved state (on at the saved damping, or
+    off)."""
     z = np.load(path)
     hp = HParams(**json.loads(str(z["hp"])))
     theta = torch.tensor(z["theta"], dtype=torch.float64, device=ctx.device)
     mom = torch.tensor(z["mom"], dtype=torch.float64, device=ctx.device)
     omega = float(z["damping_omega"])
-    if omega > 1.0:
-        ctx.set_damping(omega, float(z["lambda_next"]))
+    # always set: a saved run without damping switches off damping the
+    # target context may have on (omega <= 1 turns it off)
+    ctx.set_damping(omega, float(z["lambda_next"]) if omega > 1.0 else 0.0)
     return theta, mom, int(z["next_step"]), hp

@@ -1,4 +1,4 @@
-// gram_tc.cu -- T = A A^T (Algorithm 1 line 6, Eq. minsrR) for FP32 A with
+// gram_tc.cu -- T = A A^T (Algorithm 1, Gram step, Eq. minsrR) for FP32 A with
 // split BF16 products on the 5th-generation tensor cores (sm_103a).
 //
 // A = hi + lo with hi = bf16(A), lo = bf16(A - hi), so hi + lo carries 16
@@ -251,7 +251,7 @@ __global__ void k_split_bf16(const float *__restrict__ A, int64_t R, int64_t np,
   }
 }
 
-// Centring and split in one pass (Algorithm 1 line 5): v = (O - mean)/sqrt(Ns)
+// Centring and split in one pass (Algorithm 1, log-derivative step): v = (O - mean)/sqrt(Ns)
 // with the difference O - mean formed from the column mean as an FP32 pair
 // (hi, lo) by an error-free TwoSum, i.e. the exact difference rounded to FP32
 // within one unit in the last place, without the FP64 pipe; then

@@ -1,4 +1,4 @@
-// jac_tc.cu -- the rows of O (Alg. 1 line 5, App. A) on the tensor cores.
+// jac_tc.cu -- the rows of O (Alg. 1, log-derivative step, App. A) on the tensor cores.
 //
 // For one row (sample, adjoint seed) every entry of O is a sum over the
 // sites k of an adjoint component times a state component:

@@ -68,17 +68,26 @@ extern "C" nqs_status nqs_logpsi_noalloc(const nqs_model_desc *model, const doub
   if (!dh_supported(m.dh)) return NQS_ERR_UNSUPPORTED;
   const Layout L = make_layout(m);
   const PackOff P = pack_offsets(L);
-  // scratch: packed theta (FP64), then the hidden-state cache [n][N][dh] (FP64)
+  // scratch: packed theta (FP64), then, for 2D lattices only, the hidden-
+  // state cache [n][N][dh] (FP64) that the vertical neighbours read back; a
+  // 1D chain reads no earlier state, so it needs the packed weights alone
+  const size_t cap = (size_t)NQS_NOALLOC_SCRATCH_BYTES;
   const size_t pack_bytes = al256((size_t)P.total * sizeof(double));
-  const size_t need = pack_bytes + (size_t)n * N * m.dh * sizeof(double);
-  if (need > (size_t)NQS_NOALLOC_SCRATCH_BYTES) return NQS_ERR_WORKSPACE;
+  if (pack_bytes > cap) return NQS_ERR_WORKSPACE;
+  const size_t row_bytes = (size_t)N * m.dh * sizeof(double);
+  const bool need_cache = m.dim == 2;
+  // n is compared before it is multiplied, so the product cannot wrap
+  if (need_cache && (size_t)n > (cap - pack_bytes) / row_bytes) return NQS_ERR_WORKSPACE;
+  if ((size_t)n > (size_t)INT32_MAX) return NQS_ERR_WORKSPACE;
   void *scratch = nullptr;
   int sms = 0;
   nqs_status s = scratch_for_current_device(&scratch, &sms);
   if (s != NQS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double *pack = static_cast<double *>(scratch);
-  double *hcache = reinterpret_cast<double *>(static_cast<unsigned char *>(scratch) + pack_bytes);
+  double *hcache = need_cache
+      ? reinterpret_cast<double *>(static_cast<unsigned char *>(scratch) + pack_bytes)
+      : nullptr;
   // Every scratch element a kernel reads is written earlier in the same call
   // (the pack first, each cached state before its vertical neighbour reads
   // it), so nothing has to be cleared between calls.

@@ -690,7 +690,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   c->cur_ns = ns;
   mark(c, 0, st);
   CU(cudaMemsetAsync(sstat, 0, 64, st));
-  // line 3: sample (also fills the hidden-state caches)
+  // Alg. 1, sampling: sample (also fills the hidden-state caches)
   ST(pack_theta<T>(c, theta, st));
   mark(c, 1, st);
   {
@@ -705,13 +705,13 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     c->launches += 1;
     CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
   }
-  // line 4: local energies, E, variance; eps-bar'
+  // Alg. 1, energy: local energies, E, variance; eps-bar'
   ST(eloc_T<T>(c, ns, spins, eloc, st));
   mark(c, 5, st);
   k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
   c->launches += 1;
   CU(cudaGetLastError());
-  // line 5: O, centred over samples per block, / sqrt(Ns)
+  // Alg. 1, log-derivatives: O, centred over samples per block, / sqrt(Ns)
   ST(jac_T<T>(c, ns, spins, O, st));
   mark(c, 8, st);
   // tensor-core route of the mixed path: centring writes the BF16 hi/lo
@@ -736,7 +736,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
       CU(cudaGetLastError());
     }
   }
-  // line 6: T = O'^T O'
+  // Alg. 1, Gram: T = O'^T O'
   mark(c, 9, st);
   if (tc) {
     c->launches += 2;
@@ -757,7 +757,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
                                         c->lm_omega > 1.0 ? W<double>(c, c->off.dlm) : nullptr);
     CU(cudaGetLastError());
   }
-  // line 7: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
+  // Alg. 1, solve: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
   mark(c, 11, st);
   if (c->solve_wait) CU(cudaStreamWaitEvent(st, c->solve_wait, 0));
   const RetryInfo rinfo{hp, stats};
@@ -779,7 +779,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
       k_gemv_part<T><<<g, 256, 0, st>>>(O, R, np, x, rows_per, W<double>(c, c->off.part));
     k_dtheta<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts, np,
                                                           stats, W<double>(c, c->off.dth));
-    // lines 8-9: momentum and update (skipped unless status is OK)
+    // Alg. 1, momentum and update (skipped unless status is OK)
     k_apply<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(theta, mom, W<double>(c, c->off.dth),
                                                          np, hp->mu, stats);
     CU(cudaGetLastError());
@@ -1383,6 +1383,9 @@ nqs_status nqs_set_damping(nqs_ctx *c, double omega, double lambda0) {
   if (omega > 1.0) {
     if (!(lambda0 > 0.0) || !std::isfinite(omega) || !std::isfinite(lambda0)) return NQS_ERR_ARG;
     ST(need_ws(c));
+    // a step still running on any stream may read or rewrite the device-held
+    // damping; the device is drained first so the new value is not raced
+    CU(cudaDeviceSynchronize());
     CU(cudaMemcpy(c->ws + c->off.dlm, &lambda0, sizeof(double), cudaMemcpyHostToDevice));
     c->lm_omega = omega;
   } else {

@@ -1,7 +1,7 @@
 // stages.cuh -- the non-recurrent stages of one minSR step (sm_103a):
 // parameter packing, connected-configuration lists and local-energy
 // reduction (Sec. II.C), FP64 energy statistics (Eq. energy, Eq. vscore),
-// centring and real representation (Algorithm 1 lines 5-6), the FP64
+// centring and real representation (Algorithm 1, log-derivative and Gram steps), the FP64
 // blocked Cholesky solve (Eq. minsrR) and the update with momentum (App. B).
 #pragma once
 #include "common.cuh"

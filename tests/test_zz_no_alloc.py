@@ -50,11 +50,35 @@ def test_noalloc_logpsi_matches_context_path_twice(model, ham):
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
-    model = ModelSpec(1, 100, 1, 64)  # 51200 bytes of cache per configuration
-    n = 400                           # > 16 MiB in total
+    # 2D: the hidden-state cache (here 8 * 64 * 64 bytes per configuration)
+    # must fit beside the packed weights
+    model = ModelSpec(2, 8, 8, 64, cplx=1, marshall=1, zmask=1)
     th = torch.tensor(init_theta(model, 1), device="cuda")
-    sp = torch.zeros((n, model.N), dtype=torch.uint8, device="cuda")
-    out = torch.full((n, 2), float("nan"), dtype=torch.float64, device="cuda")
-    assert _noalloc(model, th, sp, out) == 7  # NQS_ERR_WORKSPACE, nothing launched
+    for n in (1000, 1 << 40):  # too large; so large that n * N * dh * 8 would wrap
+        m = min(n, 1000)
+        sp = torch.zeros((m, model.N), dtype=torch.uint8, device="cuda")
+        out = torch.full((m, 2), float("nan"), dtype=torch.float64, device="cuda")
+        L = nqs.lib()
+        L.nqs_logpsi_noalloc.restype = C.c_int
+        md = nqs.model_desc(model)
+        rc = L.nqs_logpsi_noalloc(C.byref(md), C.c_void_p(th.data_ptr()),
+                                  C.c_void_p(sp.data_ptr()), C.c_int64(n),
+                                  C.c_void_p(out.data_ptr()),
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 7  # NQS_ERR_WORKSPACE, nothing launched
+        torch.cuda.synchronize()
+        assert torch.isnan(out).all()
+
+
+def test_noalloc_1d_needs_no_state_cache():
+    # a 1D chain keeps no scratch beyond the packed weights, so a batch whose
+    # state cache alone would exceed the array (400 * 100 * 64 * 8 bytes) runs
+    model = ModelSpec(1, 100, 1, 64)
+    ctx = nqs.Context(model, HamSpec("tfim"), "fp64", 400)
+    th = torch.tensor(init_theta(model, 3), device="cuda")
+    sp = torch.tensor(random_spins(model, 400, seed=5), device="cuda")
+    out = torch.full((400, 2), float("nan"), dtype=torch.float64, device="cuda")
+    assert _noalloc(model, th, sp, out) == 0
+    ref = ctx.logpsi(th, sp)
     torch.cuda.synchronize()
-    assert torch.isnan(out).all()
+    np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=RTOL64, atol=RTOL64)
