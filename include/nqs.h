@@ -489,6 +489,11 @@ nqs_status nqs_graph_active(const nqs_ctx *ctx, int *active);
 /* Short text for a status code (static storage). */
 const char *nqs_status_string(int status);
 
+/* Text of the CUDA error behind the last NQS_ERR_CUDA that a call made on
+ * the calling host thread returned (static storage; "no CUDA error" if
+ * none).  Not cleared by later successful calls. */
+const char *nqs_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

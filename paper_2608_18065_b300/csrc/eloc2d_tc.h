@@ -1,6 +1,8 @@
-// eloc2d_tc.h -- tensor-core engine for the connected-configuration
-// suffixes of 2D lattices (mixed precision, zig-zag path, hidden size 64,
-// every state cached).
+// eloc2d_tc.h -- tensor-core engines for the connected-configuration
+// suffixes of 2D lattices (mixed precision, zig-zag path, every state
+// cached): weights resident in shared memory for hidden size 64
+// (eloc2d_tc.cu), streamed from L2 for hidden sizes 96 and 128
+// (eloc2d_tcs.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,6 +27,8 @@ struct Eloc2dTcArgs {
   int *err;               // device status word (NQS_ERR_TIMEOUT on a wait that ran out)
   int *tile_ctr;          // zeroed before the launch: tiles handed out in rank order
                           // (op_f[4 i + 3] = the operator of rank i, longest suffix first)
+  const unsigned char *wimg;  // streamed engine: its weight image (eloc2d_tcs_image_bytes),
+                              // written from pack by eloc2d_tcs_run before the engine runs
 };
 
 constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)
@@ -32,5 +36,11 @@ constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)
 bool eloc2d_tc_supported(int dim, int dh);
 // grid <= sm_count; the column buffer must hold grid x 128 rows
 cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st);
+
+// Streamed-weight engine, hidden sizes 96 and 128: column buffer [grid][128]
+// [Lx][dh] of U2 h (FP32); grid <= sm_count.
+bool eloc2d_tcs_supported(int dim, int dh);
+size_t eloc2d_tcs_image_bytes(int dh);
+cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st);
 
 }  // namespace nqs

@@ -1,0 +1,647 @@
+// eloc2d_tcs.cu -- log Psi of every connected configuration (Sec. II.C) for
+// 2D lattices on the zig-zag path (Sec. II.B) with hidden size 96 or 128,
+// mixed precision, on the tensor cores (sm_103a), with the weights streamed
+// from L2.
+//
+// At these sizes the BF16 hi/lo planes of the weights (240 KB at d_h = 96,
+// 320 KB at 128) do not fit in shared memory beside a tile's states, so they
+// are kept in global memory as ready-swizzled K atoms (an image written once
+// per step from the packed weights) and streamed through a ring of shared-
+// memory slots by cp.async.bulk; they stay resident in L2.
+//
+// The vertical input of the 2D cell (App. A) enters as U2 h_ver.  Instead of
+// staging h_ver as a second operand, each site's first product also forms
+// U2 h_{k-1}, which is kept (FP32) in a per-CTA column buffer until the site
+// above k-1 reads it.  So per site k, with M = 128 connected configurations
+// of one operator (a tile, sharing the first changed site kst) and the BF16x3
+// split (hi.hi + lo.hi + hi.lo) of both operands, FP32 accumulation:
+//   D1 = [U1; U2] h_{k-1}   N = 2 d_h, K = d_h     (X = U1 h_{k-1}, Y = U2 h_{k-1})
+//   h' = X [if a horizontal neighbour] + (Y at a row start | U2 h_ver from the
+//        column buffer | 0)
+//   D2 = W h'               N = 3 d_h in chunks of units (u, r, c gate
+//                           columns of a chunk's units side by side), K = d_h
+// Before a tile's first site, one D1 pass per cached state of the row
+// frontier (the last cached state of each lattice column: not simply the last
+// Lx sites, since the path visits a column twice in a row where it turns)
+// puts U2 h of those states into the column buffer.  K is padded to two 64-wide atoms; the
+// padded k-steps are not issued.
+//
+// Warp roles: 4 d_h / 32 compute warps (thread (quarter q, part p) owns row
+// 32 q + lane, its tensor-memory lane, and units 32 p .. 32 p + 31), one MMA
+// warp (one thread issues every tcgen05.mma and commit) and one producer warp
+// (one thread hands out tiles and streams the weight stages).  The producer
+// takes tiles from the launch's counter, longest suffixes first, and
+// publishes them in a two-slot queue; all three roles derive the same stage
+// schedule from the tile.  Every wait is bounded; a wait that runs out sets a
+// CTA-wide abort flag that ends every role's loop, the MMAs are drained, the
+// producer waits for its copies in flight, the tensor memory is freed and
+// NQS_ERR_TIMEOUT goes to the status word.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "eloc2d_tc.h"
+#include "tc_common.cuh"
+
+namespace nqs {
+namespace {
+
+template <int DH>
+struct Tcs {
+  static constexpr int TR = ELOC2D_TC_ROWS;         // rows per tile (the MMA's M)
+  static constexpr int P = DH / 32;                 // unit parts per row
+  static constexpr int NCW = 4 * P;                 // compute warps
+  static constexpr int NCT = 32 * NCW;              // compute threads
+  static constexpr int THREADS = NCT + 64;          // + MMA warp + producer warp
+  // registers per thread: each of the 4 SM sub-partitions holds 16 K of
+  // them and ceil(warps / 4) of the CTA's warps
+  static constexpr int REGS = (16384 / (32 * ((THREADS / 32 + 3) / 4))) & ~7;
+  static constexpr int NA = 2;                      // 64-wide K atoms (K padded to 128)
+  static constexpr int KS_LAST = (DH - 64) / 16;    // k-steps issued in the last atom
+  static constexpr int CU = DH == 128 ? 64 : 32;    // units per gate chunk
+  static constexpr int NCH = DH / CU;               // gate chunks
+  static constexpr int N1 = 2 * DH;                 // first product: [U1; U2]
+  static constexpr int N2 = 3 * CU;                 // second product, per chunk
+  static constexpr int SB1 = N1 * 128, SB2 = N2 * 128;    // stage bytes (one atom, one plane)
+  static constexpr int NS1 = 2 * NA, NS2 = NCH * 2 * NA;  // stages per product
+  static constexpr int SLOT = SB1 > SB2 ? SB1 : SB2;
+  static constexpr int NSLOT = DH == 128 ? 4 : 5;
+  static constexpr int ATOM = TR * 128;             // one K atom of the 128-row A tile
+  static constexpr int TS = 3 * DH + 4;             // bias / input table row stride (floats)
+  static constexpr int OFF_S = 0;                   // A planes: hi atoms, then lo atoms
+  static constexpr int OFF_RING = OFF_S + 2 * NA * ATOM;
+  static constexpr int OFF_TAB = OFF_RING + NSLOT * SLOT;  // float [9][TS]
+  static constexpr int OFF_BH = OFF_TAB + 9 * TS * 4;      // float [DH]: b_h
+  static constexpr int OFF_HEAD = OFF_BH + DH * 4;         // float [4][DH]: head rows
+  static constexpr int OFF_HC = OFF_HEAD + 4 * DH * 4;     // float [4]: head biases
+  static constexpr int OFF_ZX = OFF_HC + 16;               // float4 [P-1][TR]: head partials
+  static constexpr int OFF_BAR = OFF_ZX + (P - 1) * TR * 16;
+  // mbarriers: full[NSLOT], empty[NSLOT], a, d1, d2[NCH], z, tfull[2], tempty[2], drain
+  static constexpr int B_FULL = 0, B_EMPTY = NSLOT, B_A = 2 * NSLOT, B_D1 = B_A + 1,
+                       B_D2 = B_D1 + 1, B_Z = B_D2 + NCH, B_TF = B_Z + 1, B_TE = B_TF + 2,
+                       B_DRAIN = B_TE + 2, NBAR = B_DRAIN + 1;
+  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;      // int tile[2], abort, tmem base
+  static constexpr size_t SMEM = 1024 + OFF_MISC + 32;
+  static constexpr int IMG = NS1 * SB1 + NS2 * SB2;        // weight image bytes
+  static_assert(OFF_RING % 1024 == 0 && SLOT % 1024 == 0 && ATOM % 1024 == 0, "atom alignment");
+  static_assert(OFF_ZX % 16 == 0 && OFF_BAR % 8 == 0, "vector and barrier alignment");
+  static_assert(SMEM <= 227 * 1024, "one CTA per SM");
+  static_assert(3 * DH <= 512 && N1 <= 256 && N2 <= 256 && N2 % 16 == 0, "MMA shapes, TMEM");
+};
+
+__device__ __forceinline__ uint32_t pack2(float x0, float x1) {
+  uint32_t u;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(x1), "f"(x0));
+  return u;
+}
+__device__ __forceinline__ float sigm_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+__device__ __forceinline__ float tanh_f(float x) { return 2.0f * sigm_f(2.0f * x) - 1.0f; }
+
+// BF16 hi/lo planes of units k0 .. k0 + 7 of row `row`; k0 is the unit index,
+// which lands in K atom k0 / 64 (the lo plane sits NA atoms after the hi one).
+template <int DH>
+__device__ __forceinline__ void planes8(unsigned char *hi, int row, int k0, const float *h) {
+  uint32_t hp[4], lp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = h[2 * q], x1 = h[2 * q + 1];
+    hp[q] = pack2(x0, x1);
+    lp[q] = pack2(x0 - __uint_as_float(hp[q] << 16), x1 - __uint_as_float(hp[q] & 0xffff0000u));
+  }
+  const uint32_t off = (uint32_t)(k0 >> 6) * Tcs<DH>::ATOM + sw128_off(row, k0 & 63);
+  *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+  *reinterpret_cast<uint4 *>(hi + Tcs<DH>::NA * Tcs<DH>::ATOM + off) =
+      make_uint4(lp[0], lp[1], lp[2], lp[3]);
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait that also gives up once another role of the CTA has aborted;
+// running out sets the abort flag.
+__device__ __forceinline__ bool wait_ab(uint32_t bar, uint32_t parity, volatile int *abort) {
+  for (unsigned long long it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    __nanosleep(20);
+  }
+  *abort = 1;
+  return false;
+}
+
+// Stage schedule of a tile: F frontier passes (first product only) and S
+// sites (both products); zero for a tile past its operator's row count.
+__device__ __forceinline__ void tile_sched(const Eloc2dTcArgs &a, int tile, int &F, int &S) {
+  const int rk = tile / a.tiles_per_op;
+  const int op = a.op_f[4 * rk + 3];
+  const int base = (tile - rk * a.tiles_per_op) * ELOC2D_TC_ROWS;
+  if (base >= a.item_cnt[op]) { F = S = 0; return; }
+  const int kst = a.op_f[4 * op + 2];
+  F = kst >= 1 ? min(a.Lx, kst) - 1 : 0;
+  S = a.N - kst;
+}
+
+template <int DH>
+__global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k_eloc2d_tcs(const Eloc2dTcArgs a) {
+  using C = Tcs<DH>;
+  extern __shared__ __align__(1024) unsigned char eraw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(eraw) + 1023) & ~uintptr_t(1023));
+  unsigned char *Sh = sm + C::OFF_S;
+  unsigned char *ring = sm + C::OFF_RING;
+  float *tab = reinterpret_cast<float *>(sm + C::OFF_TAB);
+  float *sbh = reinterpret_cast<float *>(sm + C::OFF_BH);
+  float *shead = reinterpret_cast<float *>(sm + C::OFF_HEAD);
+  float *shc = reinterpret_cast<float *>(sm + C::OFF_HC);
+  float4 *zx = reinterpret_cast<float4 *>(sm + C::OFF_ZX);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
+  int *s_tile = reinterpret_cast<int *>(sm + C::OFF_MISC);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(sm + C::OFF_MISC + 8);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + C::OFF_MISC + 16);
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NG = 3 * DH;
+  // additive terms per input pair (d0, d1), 2 = no input: update and reset
+  // gates b + W_x x, candidate input W_in x + b_in (outside the reset gate)
+  for (int e = tid; e < 9 * NG; e += C::THREADS) {
+    const int c = e / NG, r = e % NG, j = r / DH, q = r % DH, d0 = c / 3, d1 = c % 3;
+    float v = a.pack[a.obias + 4 * q + (j == 2 ? 3 : j)];
+    if (d0 < 2) v += a.pack[a.oxw + d0 * NG + 3 * q + j];
+    if (d1 < 2) v += a.pack[a.oxw + (2 + d1) * NG + 3 * q + j];
+    tab[c * C::TS + r] = v;
+  }
+  for (int e = tid; e < DH; e += C::THREADS) sbh[e] = a.pack[a.obias + 4 * e + 2];
+  for (int e = tid; e < 4 * DH; e += C::THREADS) shead[e] = a.pack[a.ohead + e];
+  if (tid < 4) shc[tid] = a.pack[a.ohc + tid];
+  if (tid == 0) {
+    for (int i = 0; i < C::NSLOT; ++i) {
+      mbar_init(bar(C::B_FULL + i), 1);   // the producer's expect_tx arrive
+      mbar_init(bar(C::B_EMPTY + i), 1);  // the MMA thread's commit
+    }
+    mbar_init(bar(C::B_A), C::NCT);       // every compute thread: operand written
+    mbar_init(bar(C::B_D1), 1);
+    for (int c = 0; c < C::NCH; ++c) mbar_init(bar(C::B_D2 + c), 1);
+    mbar_init(bar(C::B_Z), C::NCT);       // end of a tile: head partials written
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(C::B_TF + i), 1);             // the producer publishes a tile
+      mbar_init(bar(C::B_TE + i), C::NCW + 1);    // compute warps and the MMA warp are done
+    }
+    mbar_init(bar(C::B_DRAIN), 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int N = a.N, Lx = a.Lx;
+
+  if (warp == C::NCW + 1) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t q = 0;  // stages issued so far
+      for (int it = 0;; ++it) {
+        const int slot = it & 1;
+        if (it >= 2 && !wait_ab(bar(C::B_TE + slot), ((it >> 1) - 1) & 1, s_abort)) break;
+        const int tile = *s_abort ? a.ntiles : atomicAdd(a.tile_ctr, 1);
+        s_tile[slot] = tile;
+        mbar_arrive(bar(C::B_TF + slot));
+        if (tile >= a.ntiles) break;
+        int F, S;
+        tile_sched(a, tile, F, S);
+        bool stop = false;
+        for (int f = 0; f < F + S && !stop; ++f) {
+          const int len = f < F ? C::NS1 : C::NS1 + C::NS2;
+          for (int si = 0; si < len; ++si, ++q) {
+            const uint32_t sl = q % C::NSLOT, round = q / C::NSLOT;
+            if (round > 0 && !wait_ab(bar(C::B_EMPTY + sl), (round - 1) & 1, s_abort)) {
+              stop = true;
+              break;
+            }
+            const uint32_t bytes = si < C::NS1 ? C::SB1 : C::SB2;
+            const uint32_t off = si < C::NS1 ? si * C::SB1 : C::NS1 * C::SB1 + (si - C::NS1) * C::SB2;
+            mbar_expect_tx(bar(C::B_FULL + sl), bytes);
+            bulk_g2s(smem_u32(ring + sl * C::SLOT), a.wimg + off, bytes, bar(C::B_FULL + sl));
+          }
+        }
+        if (stop) break;
+      }
+      // no copy outlives the kernel: wait for the last one issued into each slot
+      const uint32_t q0 = q > (uint32_t)C::NSLOT ? q - C::NSLOT : 0;
+      for (uint32_t r = q0; r < q; ++r) {
+        volatile int never = 0;
+        wait_ab(bar(C::B_FULL + r % C::NSLOT), (r / C::NSLOT) & 1, &never);
+      }
+    }
+    __syncwarp();
+  } else if (warp == C::NCW) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t id1 = idesc_bf16(C::TR, C::N1), id2 = idesc_bf16(C::TR, C::N2);
+      const uint32_t aH = smem_u32(Sh), aL = aH + C::NA * C::ATOM;
+      uint32_t q = 0, pa = 0;
+      bool stop = false;
+      for (int it = 0; !stop; ++it) {
+        const int slot = it & 1;
+        if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort)) break;
+        const int tile = s_tile[slot];
+        if (tile >= a.ntiles) break;
+        int F, S;
+        tile_sched(a, tile, F, S);
+        for (int f = 0; f < F + S && !stop; ++f) {
+          for (int prod = 0; prod < (f < F ? 1 : 2) && !stop; ++prod) {
+            if (!wait_ab(bar(C::B_A), pa & 1, s_abort)) { stop = true; break; }
+            ++pa;
+            tc_fence_after();
+            const int nst = prod == 0 ? C::NS1 : C::NS2;
+            for (int si = 0; si < nst; ++si, ++q) {
+              const uint32_t sl = q % C::NSLOT;
+              if (!wait_ab(bar(C::B_FULL + sl), (q / C::NSLOT) & 1, s_abort)) { stop = true; break; }
+              tc_fence_after();
+              const int at = (si >> 1) % C::NA, plane = si & 1, chunk = si / (2 * C::NA);
+              const uint64_t bd = sw128_desc(smem_u32(ring + sl * C::SLOT));
+              const uint64_t ah = sw128_desc(aH + at * C::ATOM), al = sw128_desc(aL + at * C::ATOM);
+              const uint32_t d = prod == 0 ? tmem : tmem + (uint32_t)(chunk * C::N2);
+              const uint32_t idn = prod == 0 ? id1 : id2;
+              const int ks = at == C::NA - 1 ? C::KS_LAST : 4;
+              for (int kk = 0; kk < ks; ++kk) {
+                const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                if (plane == 0) {
+                  mma_bf16(d, ah + adv, bd + adv, idn, (at == 0 && kk == 0) ? 0u : 1u);
+                  mma_bf16(d, al + adv, bd + adv, idn, 1u);
+                } else {
+                  mma_bf16(d, ah + adv, bd + adv, idn, 1u);
+                }
+              }
+              mma_commit(bar(C::B_EMPTY + sl));
+              if (prod == 1 && si % (2 * C::NA) == 2 * C::NA - 1) mma_commit(bar(C::B_D2 + chunk));
+            }
+            if (prod == 0 && !stop) mma_commit(bar(C::B_D1));
+          }
+        }
+        if (!stop) mbar_arrive(bar(C::B_TE + slot));
+      }
+      // drain the MMAs before the tensor memory is freed
+      mma_commit(bar(C::B_DRAIN));
+      volatile int never = 0;
+      if (!wait_ab(bar(C::B_DRAIN), 0, &never)) *s_abort = 1;
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------ compute warps
+    const int quarter = warp & 3, part = warp >> 2;
+    const int row = 32 * quarter + lane, u0 = 32 * part;
+    const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
+    const int chunk = u0 / C::CU, uo = u0 - chunk * C::CU;
+    const uint32_t gcol = lanes + (uint32_t)(chunk * C::N2 + uo);  // gate j at + CU j
+    uint32_t na = 0, pd1 = 0, pd2 = 0, pz = 0;  // arrivals on a; phases of d1, d2, z waited
+    bool ok = true;
+    auto arrive_a = [&]() {
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(bar(C::B_A));
+      ++na;
+    };
+    for (int it = 0; ok; ++it) {
+      const int slot = it & 1;
+      if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort)) { ok = false; break; }
+      const int tile = s_tile[slot];
+      if (tile >= a.ntiles) break;
+      const int rk = tile / a.tiles_per_op;
+      const int op = a.op_f[4 * rk + 3];
+      const int base = (tile - rk * a.tiles_per_op) * C::TR;
+      const int cnt = a.item_cnt[op];
+      if (base >= cnt) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(C::B_TE + slot));
+        continue;
+      }
+      const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], kst = a.op_f[4 * op + 2];
+      const bool valid = base + row < cnt;
+      const int64_t item = (int64_t)op * a.ns + base + row;
+      const int s = valid ? __ldcg(a.item_s + item) : 0;
+      const uint8_t *sp = a.spins + (int64_t)s * N;
+      const float *lcrow = a.lccache + (int64_t)s * N * 2;
+      const float *hrow = a.hcache + (int64_t)s * N * DH + u0;
+      float *cb = a.colbuf + ((int64_t)blockIdx.x * C::TR + row) * Lx * DH + u0;
+      auto colof = [&](int k) {
+        const int jr = k / Lx, m = k - jr * Lx;
+        return (jr & 1) ? (Lx - 1 - m) : m;
+      };
+      auto spin_at = [&](int k) { return (int)__ldcg(sp + k) ^ ((k == f1 || k == f2) ? 1 : 0); };
+      // cached state h_k (this thread's units) into the A planes, zero if k < 0
+      auto cached_planes = [&](int k) {
+        const float4 *src = reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          float h8[8];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float4 v = (valid && k >= 0) ? __ldcg(src + 2 * g8 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            h8[4 * q] = v.x; h8[4 * q + 1] = v.y; h8[4 * q + 2] = v.z; h8[4 * q + 3] = v.w;
+          }
+          planes8<DH>(Sh, row, u0 + 8 * g8, h8);
+        }
+      };
+      // Y = U2 h (columns DH + units) of the last first product into the
+      // column buffer at lattice column col
+      auto store_y = [&](int col) {
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          float y[8];
+          tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
+          tmem_wait_ld();
+          if (valid) {
+            float4 *dst = reinterpret_cast<float4 *>(cb + col * DH + 8 * g8);
+            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+          }
+        }
+      };
+
+      // frontier passes: U2 h of the last cached state of every lattice
+      // column but that of kst - 1 (the first site's product forms it).  With
+      // kst at position m0 of row j0 these are row j0 - 1's first Lx - m0
+      // sites (its others lie below row j0's first m0 sites, in the same
+      // columns) and row j0's sites before kst - 1.
+      const int F = kst >= 1 ? min(Lx, kst) - 1 : 0;
+      const int j0 = kst / Lx, m0 = kst - j0 * Lx;
+      for (int fi = 0; fi < F && ok; ++fi) {
+        const int f = j0 == 0 ? fi : (fi < Lx - m0 ? (j0 - 1) * Lx + fi : kst - m0 + fi - (Lx - m0));
+        cached_planes(f);
+        arrive_a();
+        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort)) { ok = false; break; }
+        ++pd1;
+        tc_fence_after();
+        store_y(colof(f));
+      }
+      if (!ok) break;
+      cached_planes(kst - 1);
+
+      // spins of the first site: sigma'_{k-1} (horizontal input), sigma'_k, vertical input
+      int s_prev = kst > 0 ? spin_at(kst - 1) : 2;
+      int s_cur = spin_at(kst);
+      int s_ver;
+      {
+        const int m = kst % Lx;
+        s_ver = kst >= Lx ? spin_at(kst - 2 * m - 1) : 2;
+      }
+      int n_up = 0, n_dn = 0;
+      if (a.zmask && part == 0)
+        for (int k = 0; k < kst; ++k) { if (__ldcg(sp + k) == 0) ++n_up; else ++n_dn; }
+      // log |psi(sigma')/psi(sigma)| and the phase difference as error-free
+      // FP32 TwoSum pairs; dead: the mask forces the amplitude of sigma' to zero
+      float sre = 0.f, cre = 0.f, sim = 0.f, cim = 0.f;
+      bool dead = false;
+      float zp[4] = {0.f, 0.f, 0.f, 0.f};
+      int sgp = -1;
+      float2 lcp = make_float2(0.f, 0.f);
+      auto row_work = [&]() {
+        float4 zo = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < C::P - 1; ++p) {
+          const float4 v = zx[p * C::TR + row];
+          zo.x += v.x; zo.y += v.y; zo.z += v.z; zo.w += v.w;
+        }
+        float lp0, lp1;
+        log_softmax2<float>(zp[0] + zo.x + shc[0], zp[1] + zo.y + shc[1], lp0, lp1);
+        int forced = -1;  // value forced by the mask, or -1
+        if (a.zmask) {
+          if (n_up >= N / 2) forced = 1;
+          else if (n_dn >= N / 2) forced = 0;
+        }
+        const bool kill = forced >= 0 && sgp != forced;
+        const float hl = forced >= 0 ? 0.f : 0.5f * (sgp == 0 ? lp0 : lp1);
+        float pp = 0.f, pe = 0.f;
+        if (a.cplx)
+          pi_times(softsign(sgp == 0 ? zp[2] + zo.z + shc[2] : zp[3] + zo.w + shc[3]), pp, pe);
+        dead |= kill;
+        two_add(sre, cre, hl);
+        two_add(sre, cre, -lcp.x);
+        two_add(sim, cim, pp);
+        two_add(sim, cim, pe - lcp.y);
+        if (sgp == 0) ++n_up; else ++n_dn;
+      };
+
+      for (int k = kst; k < N; ++k) {
+        const int jr = k / Lx, m = k - jr * Lx;
+        const int col = (jr & 1) ? (Lx - 1 - m) : m;
+        const bool hor = m != 0;
+        const int ver = k >= Lx ? k - 2 * m - 1 : -1;
+        const int d0 = hor ? s_prev : 2, d1 = ver >= 0 ? s_ver : 2;
+        arrive_a();  // A = h_{k-1}
+        // the vertical term from the column buffer (in flight during the product)
+        float hp[32];
+        const bool vbuf = valid && ver >= 0 && ver != k - 1;
+        {
+          const float4 *src = reinterpret_cast<const float4 *>(cb + col * DH);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 v = vbuf ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            hp[4 * q] = v.x; hp[4 * q + 1] = v.y; hp[4 * q + 2] = v.z; hp[4 * q + 3] = v.w;
+          }
+        }
+        // next site's raw spins (flipped when used) and this site's cached terms
+        int r_next = 0, r_vnext = 0, k_v = -1;
+        if (k + 1 < N) {
+          const int m1 = (k + 1) % Lx;
+          r_next = __ldcg(sp + k + 1);
+          if (k + 1 >= Lx) {
+            k_v = k + 1 - 2 * m1 - 1;
+            r_vnext = __ldcg(sp + k_v);
+          }
+        }
+        float2 lc = make_float2(0.f, 0.f);
+        if (part == 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * k));
+        // the previous site's row work overlaps the first product (the other
+        // parts' head partials are published by their arrival on a)
+        if (part == 0 && sgp >= 0) {
+          if (!wait_ab(bar(C::B_A), (na - 1) & 1, s_abort)) { ok = false; break; }
+          row_work();
+        }
+        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort)) { ok = false; break; }
+        ++pd1;
+        tc_fence_after();
+        // h' = X [horizontal] + (Y at a row start | U2 h_ver | 0); Y to the
+        // buffer; h' to the planes, 8 units at a time
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          float x[8], y[8];
+          tmem_ld8(lanes + (uint32_t)(u0 + 8 * g8), x);
+          tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float v = ver == k - 1 ? y[i] : hp[8 * g8 + i];
+            hp[8 * g8 + i] = hor ? x[i] + v : v;
+          }
+          if (valid && k >= 1) {
+            float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + 8 * g8);
+            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+          }
+          planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
+        }
+        arrive_a();  // A = h'
+        if (!wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort)) { ok = false; break; }
+        tc_fence_after();
+        // GRU cell (App. A) on this thread's units, 8 at a time; h_k overwrites
+        // h' in registers and goes to the planes once every chunk is done
+        const float *tb = tab + (d0 * 3 + d1) * C::TS + u0;
+        float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          float gu[8], gr[8], gg[8];
+          tmem_ld8(gcol + (uint32_t)(8 * g8), gu);
+          tmem_ld8(gcol + (uint32_t)(C::CU + 8 * g8), gr);
+          tmem_ld8(gcol + (uint32_t)(2 * C::CU + 8 * g8), gg);
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = 8 * g8 + u, un = u0 + i;
+            const float uu = sigm_f(gu[u] + tb[i]), rr = sigm_f(gr[u] + tb[DH + i]);
+            const float cc = tanh_f(fmaf(rr, gg[u] + sbh[un], tb[2 * DH + i]));
+            const float hn = fmaf(uu, cc - hp[i], hp[i]);
+            hp[i] = hn;
+            z0 = fmaf(shead[un], hn, z0);
+            z1 = fmaf(shead[DH + un], hn, z1);
+            if (a.cplx) {
+              z2 = fmaf(shead[2 * DH + un], hn, z2);
+              z3 = fmaf(shead[3 * DH + un], hn, z3);
+            }
+          }
+        }
+        if (chunk != C::NCH - 1 &&
+            !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort)) { ok = false; break; }
+        ++pd2;
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
+        if (part > 0) {
+          zx[(part - 1) * C::TR + row] = make_float4(z0, z1, z2, z3);
+        } else {
+          zp[0] = z0; zp[1] = z1; zp[2] = z2; zp[3] = z3;
+          sgp = s_cur;
+          lcp = lc;
+        }
+        s_prev = s_cur;
+        s_cur = k + 1 < N ? r_next ^ ((k + 1 == f1 || k + 1 == f2) ? 1 : 0) : 2;
+        s_ver = k_v >= 0 ? r_vnext ^ ((k_v == f1 || k_v == f2) ? 1 : 0) : 2;
+      }
+      if (!ok) break;
+      // the last site's row work, then the row's contribution
+      tc_fence_before();
+      mbar_arrive(bar(C::B_Z));
+      if (!wait_ab(bar(C::B_Z), pz & 1, s_abort)) { ok = false; break; }
+      ++pz;
+      if (part == 0) {
+        if (sgp >= 0) row_work();
+        if (valid) {
+          const double e = a.item_e[item];
+          const double dre = (double)sre + (double)cre, dimg = (double)sim + (double)cim;
+          const double mag = dead ? 0.0 : exp(dre);
+          double *c = a.contrib + ((int64_t)op * a.ns + s) * 2;
+          c[0] = e * mag * cos(dimg);
+          c[1] = e * mag * sin(dimg);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(C::B_TE + slot));
+    }
+    if (!ok) *s_abort = 1;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0 && *s_abort) atomicExch(a.err, (int)NQS_ERR_TIMEOUT);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+}
+
+// The weight image: every stage of the two products as a K atom (64 k, 128 B
+// rows, 128-byte swizzle) of BF16 hi then lo, in the order the MMAs use them:
+// [U1; U2] atom 0 hi, lo, atom 1 hi, lo; then per gate chunk the same four.
+// Row n of a chunk is gate n / CU of unit chunk * CU + n % CU.
+template <int DH>
+__global__ void k_eloc2d_tcs_image(const float *__restrict__ pack, int oWgT, int oU12T,
+                                   unsigned char *__restrict__ img) {
+  using C = Tcs<DH>;
+  const int e1 = C::NA * C::N1 * 64, e2 = C::NCH * C::NA * C::N2 * 64;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < e1 + e2; e += gridDim.x * blockDim.x) {
+    float w = 0.f;
+    unsigned char *hi;
+    int n, kk;
+    if (e < e1) {
+      const int at = e / (C::N1 * 64), r = e % (C::N1 * 64);
+      n = r / 64; kk = r % 64;
+      const int k = 64 * at + kk;
+      if (k < DH) w = n < DH ? pack[oU12T + k * DH + n] : pack[oU12T + (DH + k) * DH + (n - DH)];
+      hi = img + (2 * at) * C::SB1;
+    } else {
+      const int f = e - e1, c = f / (C::NA * C::N2 * 64), r = f % (C::NA * C::N2 * 64);
+      const int at = r / (C::N2 * 64), r2 = r % (C::N2 * 64);
+      n = r2 / 64; kk = r2 % 64;
+      const int k = 64 * at + kk, j = n / C::CU, q = c * C::CU + n % C::CU;
+      if (k < DH) w = pack[oWgT + k * 3 * DH + 3 * q + j];
+      hi = img + C::NS1 * C::SB1 + ((c * C::NA + at) * 2) * C::SB2;
+    }
+    const int sb = e < e1 ? C::SB1 : C::SB2;
+    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+    const uint32_t off = sw128_off(n, kk);
+    *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(hi + sb + off) = __float2bfloat16_rn(w - __bfloat162float(h));
+  }
+}
+
+template <int DH>
+cudaError_t run_dh(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st) {
+  using C = Tcs<DH>;
+  k_eloc2d_tcs_image<DH><<<C::IMG / 2 / 256 / 4 + 1, 256, 0, st>>>(
+      args.pack, args.oWgT, args.oU12T, const_cast<unsigned char *>(args.wimg));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_eloc2d_tcs<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  const int grid = args.ntiles < sm_count ? args.ntiles : sm_count;
+  if (grid <= 0) return cudaSuccess;
+  k_eloc2d_tcs<DH><<<grid, C::THREADS, C::SMEM, st>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool eloc2d_tcs_supported(int dim, int dh) { return dim == 2 && (dh == 96 || dh == 128); }
+
+size_t eloc2d_tcs_image_bytes(int dh) {
+  return dh == 128 ? (size_t)Tcs<128>::IMG : dh == 96 ? (size_t)Tcs<96>::IMG : 0;
+}
+
+cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st) {
+  if (dh == 128) return run_dh<128>(args, sm_count, st);
+  if (dh == 96) return run_dh<96>(args, sm_count, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nqs

@@ -26,7 +26,7 @@ namespace {
 
 struct WsOff {
   size_t pack, spins, logpsi, hcache, lccache, eloc, item_s, item_e, item_cnt, contrib, colbuf,
-      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dg32, dstep, tth, tmo, tstats, hseg, carry, dlm, tctr, total;
+      adj, adjcol, O, mean, T, eps, x, part, dth, frob, sstat, split, crhs, cy, cpart, cbar, gcache, L32, Li32, Tm32, wv32, dpart32, dg32, dstep, tth, tmo, tstats, hseg, carry, dlm, wimg, tctr, total;
 };
 
 }  // namespace
@@ -146,8 +146,14 @@ void build_hamiltonian(const nqs_model_desc &m, const nqs_ham_desc &h, std::vect
                    [](const OffOp &a, const OffOp &b) { return a.start < b.start; });
 }
 
-nqs_status cu(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ERR_CUDA; }
-#define CU(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return NQS_ERR_CUDA; } while (0)
+// the last CUDA error a call of this thread returned as NQS_ERR_CUDA
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+nqs_status cu(cudaError_t e) {
+  if (e == cudaSuccess) return NQS_OK;
+  g_last_cuda = e;
+  return NQS_ERR_CUDA;
+}
+#define CU(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) { g_last_cuda = _e; return NQS_ERR_CUDA; } } while (0)
 #define ST(x) do { nqs_status _s = (x); if (_s != NQS_OK) return _s; } while (0)
 
 void carve(nqs_ctx *c) {
@@ -170,7 +176,8 @@ void carve(nqs_ctx *c) {
   // column buffers of the 2D local-energy engines: the SIMT / warp-MMA
   // engines' grid x 64 rows, the tensor-core engine's SM count x 128
   size_t cb_rows = (size_t)c->eloc_grid * c->eloc_R;
-  if (c->L.dim == 2 && c->es == 4 && eloc2d_tc_supported(c->L.dim, (int)dh))
+  if (c->L.dim == 2 && c->es == 4 &&
+      (eloc2d_tc_supported(c->L.dim, (int)dh) || eloc2d_tcs_supported(c->L.dim, (int)dh)))
     cb_rows = std::max(cb_rows, (size_t)c->rd.sm_count * ELOC2D_TC_ROWS);
   o.colbuf = take(c->L.dim == 2 ? cb_rows * c->L.Lx * dh * es : 0);
   o.adj = take(R * (c->ck ? c->ck : N) * c->adjw * es);
@@ -195,6 +202,7 @@ void carve(nqs_ctx *c) {
   o.hseg = take(c->ck ? ns * (c->ck + 1) * dh * es : 0);
   o.carry = take(c->ck ? R * dh * es : 0);
   o.dlm = take(64);
+  o.wimg = take(c->L.dim == 2 && c->es == 4 ? eloc2d_tcs_image_bytes((int)dh) : 0);
   o.L32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Li32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
   o.Tm32 = take(c->prec == NQS_PREC_MIXED ? R * R * 4 : 0);
@@ -338,6 +346,28 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.tile_ctr = W<int>(c, c->off.tctr);
       CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
       CU(eloc2d_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
+    } else if (f32(c) && c->ck == 0 && gram_tc_available() &&
+               eloc2d_tcs_supported(c->L.dim, c->L.dh)) {
+      // 2D tensor-core engine with the weights streamed from L2 (d_h 96, 128)
+      Eloc2dTcArgs e{};
+      e.pack = reinterpret_cast<const float *>(a.pack);
+      e.oWgT = (int)c->P.WgT; e.oxw = (int)c->P.xw; e.obias = (int)c->P.bias;
+      e.ohead = (int)c->P.head; e.ohc = (int)c->P.hc; e.oU12T = (int)c->P.U12T;
+      e.spins = spins;
+      e.hcache = reinterpret_cast<const float *>(a.hcache);
+      e.lccache = reinterpret_cast<const float *>(a.lccache);
+      e.N = c->L.N; e.Lx = c->L.Lx; e.cplx = c->L.cplx; e.zmask = c->L.zmask; e.ns = ns;
+      e.tiles_per_op = (int)((ns + ELOC2D_TC_ROWS - 1) / ELOC2D_TC_ROWS);
+      e.ntiles = e.tiles_per_op * c->n_off;
+      e.op_f = c->d_opf; e.item_s = a.item_s; e.item_e = a.item_e; e.item_cnt = a.item_cnt;
+      e.contrib = a.contrib;
+      e.colbuf = reinterpret_cast<float *>(a.colbuf);
+      e.err = W<int>(c, c->off.sstat);
+      e.tile_ctr = W<int>(c, c->off.tctr);
+      e.wimg = reinterpret_cast<const unsigned char *>(c->ws + c->off.wimg);
+      c->launches += 1;
+      CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
+      CU(eloc2d_tcs_run(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
     }
@@ -1699,6 +1729,10 @@ nqs_status nqs_launch_count(const nqs_ctx *c, int64_t *n) {
   if (!c || !n) return NQS_ERR_ARG;
   *n = c->launches;
   return NQS_OK;
+}
+
+const char *nqs_last_cuda_error(void) {
+  return g_last_cuda == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda);
 }
 
 const char *nqs_status_string(int s) {

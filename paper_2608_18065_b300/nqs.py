@@ -65,7 +65,7 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_set_damping", "nqs_spectrum",
-           "nqs_stage_name", "nqs_status_string"]
+           "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
 
@@ -92,7 +92,8 @@ def lib():
         _lib = C.CDLL(LIB_PATH)
         _lib.nqs_status_string.restype = C.c_char_p
         _lib.nqs_stage_name.restype = C.c_char_p
-        for name in SYMBOLS[:-2]:
+        _lib.nqs_last_cuda_error.restype = C.c_char_p
+        for name in SYMBOLS[:-3]:
             getattr(_lib, name).restype = C.c_int
         _lib.nqs_spectrum_workspace.restype = C.c_size_t
         _lib.nqs_spectrum_workspace.argtypes = [C.c_int64, C.c_int]
@@ -101,7 +102,10 @@ def lib():
 
 def _check(rc):
     if rc != 0:
-        raise NqsError(f"libnqs: {lib().nqs_status_string(rc).decode()} ({rc})")
+        msg = f"libnqs: {lib().nqs_status_string(rc).decode()} ({rc})"
+        if rc == 2:  # NQS_ERR_CUDA
+            msg += ": " + lib().nqs_last_cuda_error().decode()
+        raise NqsError(msg)
 
 
 def _ptr(t):

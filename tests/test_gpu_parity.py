@@ -291,6 +291,34 @@ def test_eloc_2d_tensor_core_engine_mixed(model, ham, ns):
     assert np.max(np.abs(el - el_o)) < TOL_MIXED_ELOC * scale
 
 
+# 2D lattices with hidden size 96 or 128 run the streamed-weight tensor-core
+# engine in the mixed context: the frontier passes (U2 h of the cached row
+# frontier), row starts taking U2 h_{k-1} from the same product, several
+# 128-row tiles per operator with a ragged tail, odd row lengths, real and
+# complex heads, the mask
+E2DS_MODELS = [
+    (ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 300),
+    (ModelSpec(2, 5, 3, 96), HamSpec("j1j2", J1=1.0, J2=0.0), 130),
+    (ModelSpec(2, 3, 4, 128, cplx=1), HamSpec("j1j2", J1=1.0, J2=0.25), 200),
+    (ModelSpec(2, 4, 3, 96, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.6), 260),
+]
+
+
+@pytest.mark.parametrize("model,ham,ns", E2DS_MODELS,
+                         ids=["j1j2_4x4_dh128_cmask", "heis_5x3_dh96", "j1j2_3x4_dh128_c",
+                              "j1j2_4x3_dh96_cmask"])
+def test_eloc_2d_tensor_core_streamed_mixed(model, ham, ns):
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 4)
+    sp = random_spins(model, ns, seed=9, zero_mag=bool(model.zmask))
+    spd = torch.tensor(sp, device="cuda")
+    el = cplx(c.local_energy(thd, spd))
+    el_o = O.local_energy(model, ham, th, sp)
+    assert rel_err(el, el_o) < TOL_MIXED_ELOC
+    scale = np.max(np.abs(el_o))
+    assert np.max(np.abs(el - el_o)) < TOL_MIXED_ELOC * scale
+
+
 # 2D lattices with hidden size 64 run the reverse sweep's gate product
 # W^T [dau; dar; dg] on warp-level MMAs in the mixed context (the adjoint of
 # h', routed on through U1, U2 to the horizontal and vertical neighbours):
