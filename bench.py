@@ -1,12 +1,17 @@
 #!/usr/bin/env python
 """Benchmark: regularized minSR steps/s on one B300 (and N replicas).
 
-Workload (default): 1D transverse-field Ising open chain, N = 100, h = J = 1,
-GRU hidden size 64 (Np = 13058), Ns = 1024 samples, mixed precision (FP32
-recurrence and Jacobian, BF16x3 tensor-core Gram, FP64 centring and solve),
-Tab. I TFIM hyper-parameters.  One step = one iteration of Algorithm 1
-(sampling, local energies, O, centring, T, regularized solve, momentum,
-update) through nqs_minsr_step.
+Workload (default, `batched16`): 16 independent 2D J1-J2 instances on open
+L x L lattices (L in {6, 8, 10, 12}, J2/J1 in {0, .25, .5, .6}, Ns in
+{256 .. 4096}, GRU hidden size 32 .. 128, complex head, Marshall sign,
+zero-magnetisation mask), mixed precision (FP32 recurrence and Jacobian,
+BF16x3 tensor-core local energies and Gram, FP64 centring and solve), each
+with Tab. I's hyper-parameters, stepped together: one batched step = one
+iteration of Algorithm 1 (sampling, local energies, O, centring, T,
+regularized solve, momentum, update) of every instance, one CUDA graph.
+Beside it: the same instances one at a time on the plain FP64 GPU path,
+matched energies, and a summary of each single-instance workload.
+Other workloads by --workload (tfim100, heis10, ...).
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (bounded per-step sample of the same workload, scaled to steps/s).
@@ -39,13 +44,18 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="tfim100")
-    p.add_argument("--matched-steps", type=int, default=60,
+    p.add_argument("--workload", default="batched16",
+                   help="batched16 (the headline: 16 J1-J2 instances), tfim16, tfim100, "
+                        "tfim200, cluster64, heis10, lambda_grid, qgt_subsample")
+    p.add_argument("--matched-steps", type=int, default=50,
                    help="steps of the mixed and FP64 paths for the matched-energy check (0: skip)")
     p.add_argument("--matched-eta0", type=float, default=0.1,
                    help="eta0 of the matched-energy runs (Tab. I's 0.5 collapses this model "
                         "onto the product state within ~30 steps for both paths)")
-    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=1,
+                   help="timed steps of the plain FP64 GPU path (per instance)")
+    p.add_argument("--no-per-config", action="store_true",
+                   help="batched16: skip the summary lines of the other workloads")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-spectrum", action="store_true",
@@ -203,20 +213,33 @@ def measured_peak(key, fallback):
 
 def eloc_tc_used(model, precision):
     """The connected-configuration engine runs on tcgen05 for mixed 1D chains
-    of hidden size 64, and 32 (run with its units padded to 64: the issued
-    tensor work per site is that of 64), and for mixed 2D lattices of hidden
-    size 64."""
+    of hidden size 64 and 32 (units padded to 64), and for mixed 2D lattices
+    of hidden size 64 (weights in shared memory; 32 padded to 64) and 96 or
+    128 (weights streamed from L2)."""
     if precision != "mixed":
         return False
-    return (model.dim == 1 and model.dh in (32, 64)) or (model.dim == 2 and model.dh == 64)
+    return ((model.dim == 1 and model.dh in (32, 64)) or
+            (model.dim == 2 and model.dh in ENGINE2D_DH))
+
+
+# 2D hidden sizes served by the tensor-core engines
+ENGINE2D_DH = (32, 64, 96, 128)
 
 
 def eloc_tc_site_flops(model):
-    """Tensor-pipe flops issued per recomputed site of one configuration:
-    three BF16 products (hi.hi + hi.lo + lo.hi) of the gate product
-    [1 x 64] x [64 x 192], and in 2D also of the state mix [1 x 128] x [128 x 64]."""
-    k = 3 * 64 + (2 * 64 if model.dim == 2 else 0)
-    return 3 * 2 * 64 * k
+    """Tensor-pipe flops issued per recomputed site of one configuration
+    (three BF16 products hi.hi + hi.lo + lo.hi of each product):
+    1D: the gate product [1 x 64] x [64 x 192];
+    2D, d_h 64 (32 padded): the state mix [1 x 128] x [128 x 64] and the
+    gates [1 x 64] x [64 x 192];
+    2D, d_h 96 / 128: [U1; U2] h_{k-1}, [1 x dh] x [dh x 2dh], and the gates
+    [1 x dh] x [dh x 3dh] (the padded k-steps are not issued)."""
+    if model.dim == 1:
+        return 3 * 2 * 64 * 3 * 64
+    if model.dh in (32, 64):
+        return 3 * 2 * 64 * (3 * 64 + 2 * 64)
+    dh = model.dh
+    return 3 * 2 * dh * (2 * dh + 3 * dh)
 
 
 def eloc_roofline(w, ms, sites=None):
@@ -237,7 +260,8 @@ def eloc_roofline(w, ms, sites=None):
         fl = sites * eloc_tc_site_flops(w.model)
         peak, src = measured_peak("bf16_tflops_sustained", 1400.0)
         ach = fl / (ms * 1e-3) / 1e12
-        kern = "k_eloc_tc" if w.model.dim == 1 else "k_eloc2d_tc"
+        kern = ("k_eloc_tc" if w.model.dim == 1 else
+                "k_eloc2d_tc" if w.model.dh in (32, 64) else "k_eloc2d_tcs")
         sha = src_sha("paper_2608_18065_b300/csrc/%s.cu" % kern[2:],
                       "paper_2608_18065_b300/csrc/tc_common.cuh")
         return {"kernel": kern + " (eloc_suffix)", "bound": "tensor", "achieved": ach,
@@ -332,27 +356,6 @@ def stage_rooflines(w, ms, sites, R, np_):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_bounded(w, budget_s, seed_step=0):
-    """Time oracle steps on a sample of Ns_sub configurations sized to the
-    budget; returns (steps/s scaled to the full Ns, Ns_sub, seconds, threads)."""
-    import copy
-    from oracle import oracle as O
-    from paper_2608_18065_b300.inputs import init_theta
-    th = init_theta(w.model, w.theta_seed)
-    hp = copy.copy(w.hp)
-    hp.ns = 8
-    t0 = time.perf_counter()
-    O.minsr_step(w.model, w.ham, th, np.zeros_like(th), hp, seed_step)
-    per_sample = (time.perf_counter() - t0) / 8
-    ns_sub = int(max(8, min(w.hp.ns, budget_s / max(per_sample, 1e-9))))
-    hp.ns = ns_sub
-    t0 = time.perf_counter()
-    O.minsr_step(w.model, w.ham, th, np.zeros_like(th), hp, seed_step)
-    dt = time.perf_counter() - t0
-    scale = w.hp.ns / ns_sub
-    return 1.0 / (dt * scale), ns_sub, dt, O.num_threads()
-
-
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -363,70 +366,136 @@ def cpu_model():
     return "unknown"
 
 
+L2_NOTE = "working set > 126 MB L2 per step (O, caches, adjoints); no flush"
+
+
+def workload_config(args, w=None, insts=None):
+    """The config dict of a bench line: the same for the repo arm and the
+    reference arm (precision and buffer sizes are reported beside it)."""
+    if insts is not None:
+        return {"workload": "batched16_j1j2", "n_instances": len(insts),
+                "instances": [x.name for x in insts],
+                "draw": "PCG64(7): L in {6,8,10,12}, J2 in {0,.25,.5,.6}, "
+                        "Ns in {256..4096}, dh in {32,64,96,128}; theta_0 seed 1000+i",
+                "l2": L2_NOTE, "replicas": args.gpus}
+    d = w.describe()
+    d.pop("precision", None)
+    d.update(l2=L2_NOTE, replicas=args.gpus)
+    return d
+
+
+def oracle_instance_step(w, ns_sub, step):
+    """One FP64 oracle step of instance w on ns_sub of its samples; returns
+    (measured seconds, seconds scaled to its full Ns)."""
+    import copy
+    from oracle import oracle as O
+    from paper_2608_18065_b300.inputs import init_theta
+    th = init_theta(w.model, w.theta_seed)
+    hp = copy.copy(w.hp)
+    hp.ns = ns_sub
+    t0 = time.perf_counter()
+    O.minsr_step(w.model, w.ham, th, np.zeros_like(th), hp, step)
+    dt = time.perf_counter() - t0
+    return dt, dt * w.hp.ns / ns_sub
+
+
+def oracle_sample_size(w, budget_s):
+    """Samples of a bounded oracle step of w: at least as many as the oracle
+    has threads (every core works), else as many as fit budget_s by a probe
+    at that size, at most Ns."""
+    from oracle import oracle as O
+    nmin = min(w.hp.ns, max(4, O.num_threads()))
+    dt, _ = oracle_instance_step(w, nmin, 0)
+    return int(min(w.hp.ns, max(nmin, nmin * budget_s / max(dt, 1e-9))))
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores, on the same
+    workload.  Every timed step is one oracle step on a bounded sample of
+    configurations: for the batched workload, instance t mod 16 (so that the
+    timed steps walk through the instances) on as many samples as the oracle
+    has threads; for one instance, as many samples as fit about
+    150 s / (W + K).  ms_per_step is the measured time of that bounded step;
+    value is the rate of whole steps, each instance's time scaled to its
+    full Ns (sampling, local energies and O are linear in Ns and dominate
+    the oracle's time; its Gram and solve grow faster, so the scaling
+    flatters the oracle)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as O
     from paper_2608_18065_b300.inputs import batched_instances, workloads
     if args.workload == "batched16":
-        return run_reference_batched(args)
-    w = workloads()[args.workload]
-    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+        insts = batched_instances()
+        cfg = workload_config(args, insts=insts)
+        unit = "batched steps/s"
+        nsub = [min(w.hp.ns, max(4, O.num_threads())) for w in insts]
+    else:
+        w = workloads()[args.workload]
+        insts = [w]
+        cfg = workload_config(args, w=w)
+        unit = UNIT
+        nsub = [oracle_sample_size(w, max(1.0, 150.0 / max(1, args.steps + args.warmup)))]
+    n = len(insts)
     for t in range(args.warmup):
-        oracle_bounded(w, budget, t)
-    vals, subs, secs, thr = [], [], [], 1
-    for t in range(args.steps):
-        v, sub, dt, thr = oracle_bounded(w, budget, args.warmup + t)
-        vals.append(v); subs.append(sub); secs.append(dt)
-    value = float(np.mean(vals))
-    sample = (f"one oracle step per timed step on Ns_sub={min(subs)}..{max(subs)} of the "
-              f"{w.hp.ns} samples (same model, Hamiltonian, theta_0), time scaled by "
-              f"{w.hp.ns}/Ns_sub (sampling, local energies and O are linear in Ns)")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        oracle_instance_step(insts[t % n], nsub[t % n], t)
+    meas = []
+    full = [[] for _ in range(n)]
+    for t in range(args.warmup, args.warmup + args.steps):
+        m, f = oracle_instance_step(insts[t % n], nsub[t % n], t)
+        meas.append(m)
+        full[t % n].append(f)
+    for i in range(n):  # fewer timed steps than instances: the rest once, untimed
+        if not full[i]:
+            full[i].append(oracle_instance_step(insts[i], nsub[i], 0)[1])
+    per_full = sum(float(np.mean(x)) for x in full)
+    value = 1.0 / per_full
+    whole = all(ns == w.hp.ns for ns, w in zip(nsub, insts))
+    sample = ("one whole FP64 oracle step per timed step" if whole and n == 1 else
+              (f"one FP64 oracle step per timed step of instance t mod {n} on "
+               f"{min(nsub)}..{max(nsub)} of its samples (same models, Hamiltonians, "
+               "theta_0); each instance's time scaled to its full Ns and summed"
+               if n > 1 else
+               f"one FP64 oracle step per timed step on {nsub[0]} of the {insts[0].hp.ns} "
+               "samples, time scaled to the full Ns"))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": w.describe(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": sample, "cpu": cpu_model()},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "ms_per_step": 1000.0 * float(np.mean(meas)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "precision": "fp64",
+            "data": "synthetic", "config": cfg,
+            "ms_per_full_step_scaled": 1000.0 * per_full,
+            "samples_per_instance": nsub,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def run_reference_batched(args):
-    """Oracle arm of the batched workload: per timed step one bounded oracle
-    step of every instance, each scaled to its full Ns, summed."""
-    from paper_2608_18065_b300.inputs import batched_instances
-    insts = batched_instances()
-    budget = max(0.3, 150.0 / max(1, args.steps + args.warmup) / len(insts))
-    vals, thr, subs = [], 1, []
-    for t in range(args.warmup + args.steps):
-        tot = 0.0
-        for w in insts:
-            v, sub, dt, thr = oracle_bounded(w, budget, t)
-            tot += 1.0 / v
-            subs.append(sub)
-        if t >= args.warmup:
-            vals.append(1.0 / tot)
-    value = float(np.mean(vals))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "batched steps/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched16_j1j2", "instances": [w.name for w in insts],
-                       "n_instances": len(insts), "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": "batched steps/s", "cores": thr,
-                             "kind": "oracle",
-                             "sample": (f"one oracle step per instance per timed step on "
-                                        f"Ns_sub={min(subs)}..{max(subs)} samples, each scaled "
-                                        "to its full Ns, summed over the 16 instances"),
-                             "cpu": cpu_model()},
-            "e2e": {"value": value, "unit": "batched steps/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-    return 0
+def cpu_baseline_leg(insts, unit, budget_s=20.0):
+    """cpu_baseline of the repo arm: one bounded FP64 oracle step of every
+    instance on the host cores (as many samples as the oracle has threads
+    for the batched workload; as many as fit budget_s for one instance),
+    each scaled to its full Ns, summed."""
+    from oracle import oracle as O
+    if len(insts) > 1:
+        nsub = [min(w.hp.ns, max(4, O.num_threads())) for w in insts]
+    else:
+        nsub = [oracle_sample_size(insts[0], budget_s)]
+    meas = full = 0.0
+    for w, ns in zip(insts, nsub):
+        m, f = oracle_instance_step(w, ns, 0)
+        meas += m
+        full += f
+    return {"value": 1.0 / full, "unit": unit, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"one FP64 oracle step of each of the {len(insts)} instances on "
+                       f"{min(nsub)}..{max(nsub)} of its samples, {meas:.1f} s measured, "
+                       "each scaled to its full Ns and summed"
+                       if len(insts) > 1 else
+                       f"one FP64 oracle step on {nsub[0]} of the {insts[0].hp.ns} samples "
+                       f"({meas:.1f} s), scaled to the full Ns"),
+            "cpu": cpu_model()}
 
 
 # -------------------------------------------------------------------- ours
@@ -574,23 +643,22 @@ def run_ours(args):
     matched = None
     if args.matched_steps > 0 and rank == 0:
         hpm = copy.copy(hp)
-        hpm.eta0 = args.matched_eta0
-        matched = matched_energy(w, hpm, args.matched_steps, dev)
+        if w.ham.family == "tfim":
+            hpm.eta0 = args.matched_eta0
+        matched = matched_energy(w, hpm, args.matched_steps, dev, reference_energy(w))
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        v, sub, dt, thr = oracle_bounded(w, 20.0)
-        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": (f"one FP64 oracle step on Ns_sub={sub} of the {hp.ns} samples "
-                          f"({dt:.1f} s), scaled by {hp.ns}/{sub}"), "cpu": cpu_model()}
+        cpu = cpu_baseline_leg([w], UNIT, 20.0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": Wu, "ms_per_step": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3+f64",
-                "data": "synthetic",
-                "config": dict(w.describe(), l2="step working set > 126 MB L2 (O, caches, adjoints)",
-                               replicas=world, workspace_mb=ctx.workspace_bytes / 2**20),
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+bf16x3+f64" if w.precision == "mixed" else "f64",
+                "precision": w.precision, "data": "synthetic",
+                "config": workload_config(args, w=w),
+                "workspace_mb": ctx.workspace_bytes / 2**20,
                 "gram_tflops": gram_tflops, "gram": gram,
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
@@ -604,12 +672,77 @@ def run_ours(args):
     return 0
 
 
+MATCHED_SUBSET = ("j1j2_L6_J20.6_dh64_ns256", "j1j2_L6_J20.25_dh128_ns512",
+                  "j1j2_L8_J20.0_dh96_ns256", "j1j2_L8_J20.25_dh32_ns512")
+
+
+def instance_roofline(insts, stage_ms_list, sites_list):
+    """Roofline of the batch's dominant stage, summed over the instances:
+    the local-energy engines by issued tensor flops against the sustained
+    BF16 peak when every instance runs on tcgen05 (else FP32-equivalent
+    flops against the derived FP32 peak), other stages by the per-stage
+    counts of stage_rooflines."""
+    tot = {}
+    for sm in stage_ms_list:
+        for k, v in sm.items():
+            tot[k] = tot.get(k, 0.0) + v
+    dom = max(tot, key=lambda k: tot[k])
+    if dom == "eloc_suffix":
+        ms = tot[dom]
+        alg = sum(n * site_flops(w.model) for w, n in zip(insts, sites_list))
+        if all(eloc_tc_used(w.model, w.precision) for w in insts):
+            fl = sum(n * eloc_tc_site_flops(w.model) for w, n in zip(insts, sites_list))
+            peak, src = measured_peak("bf16_tflops_sustained", 1400.0)
+            ach = fl / (ms * 1e-3) / 1e12
+            return dom, {"kernel": "k_eloc2d_tc (d_h 32, 64) + k_eloc2d_tcs (d_h 96, 128), "
+                                   "all instances (eloc_suffix)",
+                         "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None,
+                         "peak_source": src + ", BF16 dense, sustained",
+                         "flops_per_batch": fl, "fp32_equiv_flops_per_batch": alg,
+                         "fp32_equiv_tflops": alg / (ms * 1e-3) / 1e12, "ms_per_batch": ms}
+        ach = alg / (ms * 1e-3) / 1e12
+        return dom, {"kernel": "2D E_loc engines, all instances (eloc_suffix; FP32-equivalent)",
+                     "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
+                     "flops_per_batch": alg, "ms_per_batch": ms}
+    # other stages: sum the per-instance work of the stage's own count
+    work = ms = 0.0
+    first = None
+    for w, sm, n in zip(insts, stage_ms_list, sites_list):
+        R = w.hp.ns * (2 if w.model.cplx else 1)
+        from paper_2608_18065_b300.inputs import param_count
+        k = stage_rooflines(w, sm, n, R, param_count(w.model)).get(dom)
+        if not k:
+            continue
+        first = first or k
+        t = k["ms_per_launch"]
+        ms += t
+        work += k["achieved"] * t
+    if not first:
+        return dom, {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
+                     "frac": None, "traffic": None, "ms_per_batch": tot[dom]}
+    ach = work / ms
+    out = dict(first)
+    out.update(kernel=first["kernel"] + ", all instances", achieved=ach,
+               frac=ach / first["peak"], ms_per_batch=ms)
+    out.pop("ms_per_launch", None)
+    out.pop("flops_per_launch", None)
+    out.pop("bytes_per_launch", None)
+    return dom, out
+
+
 def run_batched(args):
-    """Batched J1-J2 workload: 16 heterogeneous 2D instances (L in {6..12},
-    J2 in {0, .25, .5, .6}, Ns in {256..4096}, dh in {32..128}) stepped
-    together by nqs_minsr_step_batched (one graph per batched step, launch
-    shapes from the autotuner); value = batched steps/s (x16 instance steps)."""
-    import copy
+    """The headline: 16 heterogeneous 2D J1-J2 instances (L in {6..12}, J2 in
+    {0, .25, .5, .6}, Ns in {256..4096}, dh in {32..128}) stepped together by
+    nqs_minsr_step_batched (one graph per batched step, launch shapes from
+    the autotuner); value = batched steps/s (x16 instance steps).  Beside it:
+    the same instances one at a time on the plain FP64 GPU path, the
+    matched-energy leg (mixed batched vs FP64 one at a time from the same
+    theta_0 and Philox keys, on four L <= 8 instances), the FP64 oracle on
+    the host cores, the end-to-end rate through host buffers, and a summary
+    line of each other workload (configs 1-4)."""
     import torch
     import torch.distributed as dist
     from paper_2608_18065_b300 import nqs
@@ -663,9 +796,8 @@ def run_batched(args):
     st = [nqs.decode_stats(stats[i]) for i in range(n)]
 
     # per-instance stage times: every instance alone, eager, one step
-    solo = []
-    tot_stage = {}
-    eloc_ms = eloc_flops = gram_ms = gram_fl = 0.0
+    solo, stage_list, sites_list = [], [], []
+    gram_ms = gram_fl = 0.0
     launches = 0
     for i, (c, w) in enumerate(zip(ctxs, insts)):
         c.timing_begin(1)
@@ -677,32 +809,22 @@ def run_batched(args):
         sm, nt = c.timing_end()
         cfg, sites = c.eloc_work()
         R = w.hp.ns * (2 if w.model.cplx else 1)
-        np_ = param_count(w.model)
-        for k, v in sm.items():
-            tot_stage[k] = tot_stage.get(k, 0.0) + v
-        eloc_ms += sm["eloc_suffix"]
-        eloc_flops += sites * site_flops(w.model)
+        stage_list.append(sm)
+        sites_list.append(sites)
         gram_ms += sm["gram"]
-        gram_fl += R * (R + 1) * np_
+        gram_fl += R * (R + 1) * param_count(w.model)
         solo.append({"instance": w.name, "ms": sum(sm.values()), "eloc_configs": cfg,
-                     "workspace_mb": round(c.workspace_bytes / 2**20, 1),
-                     "eloc_sites": sites, "E_re": st[i]["E_re"], "status": st[i]["status"],
+                     "eloc_sites": sites, "workspace_mb": round(c.workspace_bytes / 2**20, 1),
+                     "stage_ms": {k: round(v, 3) for k, v in sm.items()},
+                     "E_re": st[i]["E_re"], "status": st[i]["status"],
+                     "solve_fp64": st[i].get("solve_fp64"),
                      "tuning": {k: tuning[i][k] for k in ("eloc_grid", "gram_splits", "solve_grid")}})
     solo_ms = sum(x["ms"] for x in solo)
-    dom = max(tot_stage, key=lambda k: tot_stage[k])
-    roof = None
-    if dom == "eloc_suffix" and eloc_ms > 0:
-        ach = eloc_flops / (eloc_ms * 1e-3) / 1e12
-        roof = {"kernel": "2D E_loc engines (eloc_suffix, all instances; k_eloc2d_tc for "
-                          "mixed d_h = 64, k_forward<MODE_ELOC> otherwise; FP32-equivalent flops)",
-                "bound": "alu",
-                "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived)",
-                "flops_per_batch": eloc_flops, "ms_per_batch": eloc_ms}
-    if roof is None:
-        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "ms_per_batch": tot_stage[dom]}
+    tot_stage = {}
+    for sm in stage_list:
+        for k, v in sm.items():
+            tot_stage[k] = tot_stage.get(k, 0.0) + v
+    dom, roof = instance_roofline(insts, stage_list, sites_list)
 
     # end to end: every instance's theta and momentum from and back to pinned host memory
     e2e = None
@@ -728,8 +850,12 @@ def run_batched(args):
         nbytes = sum(t.numel() * 8 for t in thd) * 2
         e2e = {"value": aggregate_rate(world, K, ems), "unit": "batched steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + stats.numel() * 8}
+    del b
+    for c in ctxs:
+        c.close()
+    torch.cuda.empty_cache()
 
-    # the same instances one at a time on the plain FP64 GPU path
+    # the same instances one at a time on the plain FP64 GPU path (graphs on)
     fp64 = None
     if args.fp64_steps > 0:
         f_ms = 0.0
@@ -739,87 +865,281 @@ def run_batched(args):
             t64 = torch.tensor(th0[i], device=dev)
             m64 = torch.zeros_like(t64)
             s64 = c64.new_stats()
+            c64.minsr_step(t64, m64, hps[i], 0, s64)  # warm-up (not timed)
+            torch.cuda.synchronize()
             b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             b0.record()
-            for t in range(args.fp64_steps):
+            for t in range(1, 1 + args.fp64_steps):
                 c64.minsr_step(t64, m64, hps[i], t, s64)
             b1.record()
             torch.cuda.synchronize()
             d = b0.elapsed_time(b1) / args.fp64_steps
             f_ms += d
             per.append(round(d, 3))
+            c64.close()
             del c64
+        torch.cuda.empty_cache()
         fp64 = {"batched_steps_per_s": 1000.0 / f_ms, "ms_per_batched_step": f_ms,
                 "instance_ms": per, "steps_per_instance": args.fp64_steps,
                 "speedup_mixed_batched_over_fp64": (1000.0 * K / ms) / (1000.0 / f_ms)}
 
+    matched = None
+    if args.matched_steps > 0 and rank == 0:
+        matched = matched_energy_batched([w for w in insts if w.name in MATCHED_SUBSET],
+                                         args.matched_steps, dev)
+
+    per_config = None
+    if not args.no_per_config and rank == 0:
+        per_config = {}
+        for key in ("tfim16", "tfim100", "cluster64", "heis10"):
+            per_config[key] = config_summary(key, args, dev)
+            torch.cuda.empty_cache()
+
     cpu = None
     if not args.no_cpu and rank == 0:
-        tot_s, subs, thr = 0.0, [], 1
-        for w in insts:
-            v, sub, dt, thr = oracle_bounded(w, 1.5)
-            tot_s += 1.0 / v
-            subs.append(sub)
-        cpu = {"value": 1.0 / tot_s, "unit": "batched steps/s", "cores": thr, "kind": "oracle",
-               "sample": (f"one FP64 oracle step per instance on Ns_sub={min(subs)}..{max(subs)} "
-                          "samples, each scaled to its full Ns, summed over the 16 instances"),
-               "cpu": cpu_model()}
+        cpu = cpu_baseline_leg(insts, "batched steps/s", 20.0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "batched steps/s", "n_gpus": world,
                 "steps": K, "warmup": Wu, "ms_per_step": ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3+f64",
-                "data": "synthetic",
-                "config": {"workload": "batched16_j1j2", "instances": [w.name for w in insts],
-                           "n_instances": n, "precision": "mixed",
-                           "l2": "step working set > 126 MB L2", "replicas": world},
+                "precision": "mixed", "data": "synthetic",
+                "config": workload_config(args, insts=insts),
                 "instance_steps_per_s": n * value,
                 "solo_sum_ms": solo_ms, "concurrency_gain": solo_ms / (ms / K),
                 "gram_tflops": gram_fl / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches * K), "clocks": clk,
-                "cuda_graph": b.graph_active(), "concurrency": b.concurrency(),
+                "cuda_graph": True if not args.no_graph else False,
                 "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
-                "fp64_path": fp64,
-                "stage_ms_solo_sum": tot_stage, "instances": solo}
+                "fp64_path": fp64, "matched_energy": matched, "per_config": per_config,
+                "errors_vs_oracle": load_errors(),
+                "stage_ms_solo_sum": tot_stage, "dominant_stage": dom, "instances": solo}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def matched_energy(w, hp, steps, dev):
-    """Run the mixed and the FP64 GPU paths for `steps` steps from theta_0
-    with the same Philox seeds; report the mean relative error of E over the
-    last 10 steps against the exact energy (Jordan-Wigner for the TFIM)."""
+def load_errors():
+    """Maxima of the mixed path's errors against the FP64 oracle (log Psi,
+    E_loc, T, delta theta, energy trajectory) as measured by the full-size
+    parity tests on a B300 and recorded in profiles/errors_vs_oracle.json."""
+    p = os.path.join(ROOT, "profiles", "errors_vs_oracle.json")
+    try:
+        return json.load(open(p))
+    except (ValueError, OSError):
+        return None
+
+
+def _mean_stderr(es, vs, ns):
+    last = np.array(es[-10:])
+    se = float(np.sqrt(np.mean(np.array(vs[-10:]) / ns) / 10.0))
+    return float(last.mean()), se
+
+
+def matched_energy(w, hp, steps, dev, E_ref=None):
+    """Mixed and plain FP64 GPU paths for `steps` steps from theta_0 with the
+    same Philox keys.  Reported: the mean of E over the last 10 steps and its
+    standard error (sqrt(mean Var / Ns / 10)), the relative error against
+    E_ref when one exists; matched when the two paths' means (or relative
+    errors) differ by no more than the larger standard error."""
     import torch
     from paper_2608_18065_b300 import nqs
     from paper_2608_18065_b300.inputs import init_theta
-    if w.ham.family != "tfim":
-        return None
-    N = w.model.N
-    B = np.diag(np.full(N, w.ham.h)) + np.diag(np.full(N - 1, w.ham.J), 1)
-    E0 = -float(np.sum(np.linalg.svd(B, compute_uv=False)))
-    out = {"E_exact": E0, "steps": steps, "eta0": hp.eta0}
+    out = {"E_ref": E_ref, "steps": steps, "eta0": hp.eta0}
     for prec in ("mixed", "fp64"):
         c = nqs.Context(w.model, w.ham, prec, hp.ns, device=dev)
         th = torch.tensor(init_theta(w.model, w.theta_seed), device=dev)
         m = torch.zeros_like(th)
-        es, se = [], []
+        es, vs = [], []
         s = c.new_stats()
+        t0 = time.perf_counter()
         for t in range(steps):
             c.minsr_step(th, m, hp, t, s)
             d = nqs.decode_stats(s)
             es.append(d["E_re"])
-            se.append(np.sqrt(d["var"] / hp.ns))
-        last = np.array(es[-10:])
-        rel = (last - E0) / abs(E0)
-        out[prec] = {"rel_err_last10": float(rel.mean()),
-                     "stderr": float(np.mean(se[-10:]) / abs(E0) / np.sqrt(10)),
-                     "E_first": es[0], "E_last": es[-1]}
+            vs.append(d["var"])
+        mean, se = _mean_stderr(es, vs, hp.ns)
+        r = {"E_last10": mean, "stderr": se, "E_first": es[0], "E_last": es[-1],
+             "seconds": time.perf_counter() - t0}
+        if E_ref is not None:
+            r["rel_err_last10"] = (mean - E_ref) / abs(E_ref)
+            r["rel_stderr"] = se / abs(E_ref)
+        out[prec] = r
+        c.close()
         del c
-    d = abs(out["mixed"]["rel_err_last10"] - out["fp64"]["rel_err_last10"])
+    d = abs(out["mixed"]["E_last10"] - out["fp64"]["E_last10"])
     out["matched"] = bool(d <= max(out["mixed"]["stderr"], out["fp64"]["stderr"]))
+    return out
+
+
+def matched_energy_batched(insts, steps, dev):
+    """Matched-energy leg of the batched workload: the given instances
+    stepped together in the mixed batched form and one at a time on the FP64
+    GPU path, from theta_0 with the same Philox keys, `steps` steps each;
+    per instance the mean E over the last 10 steps with its standard error,
+    matched when the two differ by no more than the larger one.  (No exact
+    energy exists for these lattices; the paper's reference values per site
+    are -0.628656 (J2 = 0, QMC, 10 x 10 and larger) and -0.48654 (J2 = 0.5,
+    PEPS), context only.)"""
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import init_theta
+    n = len(insts)
+    ctxs = [nqs.Context(w.model, w.ham, "mixed", w.hp.ns, device=dev) for w in insts]
+    ths = [torch.tensor(init_theta(w.model, w.theta_seed), device=dev) for w in insts]
+    ms_ = [torch.zeros_like(t) for t in ths]
+    b = nqs.Batch(ctxs)
+    b.use_graph(True)
+    stats = b.new_stats()
+    es = [[] for _ in range(n)]
+    vs = [[] for _ in range(n)]
+    t0 = time.perf_counter()
+    for t in range(steps):
+        b.step(ths, ms_, [w.hp for w in insts], t, stats)
+        for i in range(n):
+            d = nqs.decode_stats(stats[i])
+            es[i].append(d["E_re"])
+            vs[i].append(d["var"])
+    mixed_s = time.perf_counter() - t0
+    del b
+    for c in ctxs:
+        c.close()
+    out = {"steps": steps, "instances": [], "mixed_batched_seconds": mixed_s}
+    t0 = time.perf_counter()
+    allm = True
+    for i, w in enumerate(insts):
+        c = nqs.Context(w.model, w.ham, "fp64", w.hp.ns, device=dev)
+        th = torch.tensor(init_theta(w.model, w.theta_seed), device=dev)
+        m = torch.zeros_like(th)
+        s = c.new_stats()
+        e64, v64 = [], []
+        for t in range(steps):
+            c.minsr_step(th, m, w.hp, t, s)
+            d = nqs.decode_stats(s)
+            e64.append(d["E_re"])
+            v64.append(d["var"])
+        c.close()
+        mm, ms1 = _mean_stderr(es[i], vs[i], w.hp.ns)
+        fm, fs = _mean_stderr(e64, v64, w.hp.ns)
+        ok = bool(abs(mm - fm) <= max(ms1, fs))
+        allm &= ok
+        out["instances"].append({"instance": w.name, "N": w.model.N,
+                                 "mixed": {"E_last10": mm, "stderr": ms1, "E_first": es[i][0]},
+                                 "fp64": {"E_last10": fm, "stderr": fs, "E_first": e64[0]},
+                                 "matched": ok})
+    out["fp64_one_at_a_time_seconds"] = time.perf_counter() - t0
+    out["matched"] = allm
+    return out
+
+
+def reference_energy(w):
+    """Exact ground energy where one exists: Jordan-Wigner for the open TFIM
+    chain, -(N - 2) for the ZXZ cluster chain (None otherwise)."""
+    if w.ham.family == "tfim":
+        N = w.model.N
+        B = np.diag(np.full(N, w.ham.h)) + np.diag(np.full(N - 1, w.ham.J), 1)
+        return -float(np.sum(np.linalg.svd(B, compute_uv=False)))
+    if w.ham.family == "cluster_zxz":
+        return -float(w.model.N - 2)
+    return None
+
+
+def config_summary(key, args, dev):
+    """One line per other workload (configs 1-4): steps/s of its own
+    precision with graphs, the plain FP64 path's ms/step and the ratio, the
+    dominant stage's roofline fraction, and the matched-energy comparison
+    (50 steps; 500 for the 1D TFIM N = 100 workload, at eta0 = 0.1 for the
+    TFIM where Tab. I's 0.5 collapses onto the product state).  The FP64-only
+    workload reports its us/step with and without graph replay."""
+    import copy
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import init_theta, workloads
+    w = workloads()[key]
+    hp = w.hp
+    out = {"workload": w.name, "precision": w.precision}
+    th0 = init_theta(w.model, w.theta_seed)
+
+    def timed(ctx, graph, steps=20, warm=3):
+        ctx.use_graph(graph)
+        th = torch.tensor(th0, device=dev)
+        m = torch.zeros_like(th)
+        s = ctx.new_stats()
+        for t in range(warm):
+            ctx.minsr_step(th, m, hp, t, s)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for t in range(warm, warm + steps):
+            ctx.minsr_step(th, m, hp, t, s)
+        z.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / steps, th, m
+
+    c = nqs.Context(w.model, w.ham, w.precision, hp.ns, device=dev)
+    ms, th, m = timed(c, True)
+    out["steps_per_s"] = 1000.0 / ms
+    out["ms_per_step"] = ms
+    if w.precision == "fp64":
+        ms_eager, _, _ = timed(c, False)
+        out["us_per_step_graph"] = 1000.0 * ms
+        out["us_per_step_eager"] = 1000.0 * ms_eager
+        out["graph_replay_saving_us"] = 1000.0 * (ms_eager - ms)
+    c.timing_begin(3)
+    s = c.new_stats()
+    for t in range(3):
+        c.minsr_step(th, m, hp, 100 + t, s)
+    torch.cuda.synchronize()
+    sm, nt = c.timing_end()
+    cfg, sites = c.eloc_work()
+    R = hp.ns * (2 if w.model.cplx else 1)
+    sm = {k: v / max(nt, 1) for k, v in sm.items()}
+    kern = stage_rooflines(w, sm, sites, R, c.np)
+    dom = max(sm, key=lambda k: sm[k])
+    k = kern.get(dom)
+    out["dominant_stage"] = dom
+    out["roofline"] = ({x: k[x] for x in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+                       if k else None)
+    out["stage_ms"] = {x: round(v, 4) for x, v in sm.items()}
+    c.close()
+    if w.precision != "fp64":
+        c64 = nqs.Context(w.model, w.ham, "fp64", hp.ns, device=dev)
+        ms64, _, _ = timed(c64, True, steps=3, warm=1)
+        c64.close()
+        out["fp64_ms_per_step"] = ms64
+        out["speedup_over_fp64"] = ms64 / ms
+    if args.matched_steps > 0:
+        hpm = copy.copy(hp)
+        steps = 50
+        if w.ham.family == "tfim":
+            hpm.eta0 = args.matched_eta0
+            if w.model.N == 100:
+                steps = 500
+        E_ref = reference_energy(w)
+        if w.precision == "fp64":
+            # config 1 is the plain FP64 method itself: its energy after the run
+            c = nqs.Context(w.model, w.ham, "fp64", hp.ns, device=dev)
+            th = torch.tensor(th0, device=dev)
+            m = torch.zeros_like(th)
+            s = c.new_stats()
+            es, vs = [], []
+            for t in range(steps):
+                c.minsr_step(th, m, hpm, t, s)
+                d = nqs.decode_stats(s)
+                es.append(d["E_re"])
+                vs.append(d["var"])
+            c.close()
+            mean, se = _mean_stderr(es, vs, hp.ns)
+            out["energy"] = {"E_ref": E_ref, "steps": steps, "eta0": hpm.eta0,
+                             "E_last10": mean, "stderr": se,
+                             "rel_err_last10": (mean - E_ref) / abs(E_ref)}
+        else:
+            out["matched_energy"] = matched_energy(w, hpm, steps, dev, E_ref)
+            if w.model.dim == 2:
+                out["matched_energy"]["context"] = ("Tab. II QMC value for the 2D Heisenberg "
+                                                    "model: -0.628656 per site")
     return out
 
 

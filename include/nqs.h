@@ -370,6 +370,62 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,
                               const nqs_step_hparams *hps, int flags,
                               double *step_ms, void *stream);
 
+/* ------------------------------------------------ sample-sharded step */
+
+/* One minSR step (Algorithm 1) with the Ns samples split over G ranks, one
+ * context per rank (each created with max_samples >= Ns: T and the gathered
+ * rows are Ns-sized).  The paper runs one instance per GPU; the split below
+ * follows from the samples being independent (exact autoregressive
+ * sampling, Sec. II.A): rank r draws samples s0 .. s0 + n - 1 of the draw
+ * with their own Philox counters, so the ranks together draw exactly the
+ * single-rank step's samples.  Per step, on every rank, in order:
+ *   nqs_shard_forward   sampling, local energies and O of the rank's
+ *                       samples; partial sums
+ *   (caller)            sum of the partial sums over the ranks (allreduce)
+ *   nqs_shard_center    the rank's centred rows O' and eps-bar'; E, Var
+ *   (caller)            gather of every rank's rows and eps-bar' in rank order
+ *   nqs_shard_solve     T of the gathered rows, lambda, x, eta; the entries
+ *                       [p0, p1) of delta theta
+ *   (caller)            gather of the delta theta ranges (allgather)
+ *   nqs_shard_apply     momentum and update of theta
+ * Rows gathered in rank order are a permutation of the single-rank rows;
+ * T, x and eps-bar' permute alike and delta theta = eta O'^T x does not
+ * change (up to rounding).  The Levenberg-Marquardt damping is not applied
+ * on this path.  All calls are asynchronous on `stream`; host-side argument
+ * errors return at once, device-side ones go to dev_stats.status. */
+
+/* Sampling (Sec. II.A), local energies (Sec. II.C) and O (Sec. II.D) of
+ * samples s0 .. s0 + n - 1 (s0 + n <= 2^32, n <= max_samples), kept in the
+ * context.  sums: device FP64 [nblk*Np + 3], nblk = 2 for the complex head
+ * else 1: the column sums of O per block (real rows, imaginary rows), then
+ * sum Re E_loc, sum Im E_loc, sum |E_loc|^2 over the n samples. */
+nqs_status nqs_shard_forward(nqs_ctx *ctx, const double *theta, const nqs_step_hparams *hp,
+                             int64_t s0, int64_t n, double *sums, void *stream);
+
+/* From the sums of all ranks (device, layout of nqs_shard_forward) and the
+ * total Ns: E, Var = sum|E_loc|^2/Ns - |E|^2 and the V-score into dev_stats
+ * (status reset); rows: device [nblk*n][Np], working precision (FP64
+ * context: double, mixed: float), the rank's rows of O' = (O - mean) /
+ * sqrt(Ns) (Eq. real-valued; real block then imaginary block); eps: device
+ * FP64 [nblk*n], the rank's rows of eps-bar'.  n: the last forward's n. */
+nqs_status nqs_shard_center(nqs_ctx *ctx, const double *sums, int64_t ns, int64_t n,
+                            void *rows, double *eps, nqs_step_stats *dev_stats, void *stream);
+
+/* On the gathered rows (device [R][Np], working precision, R = nblk*Ns) and
+ * eps-bar' (device FP64 [R]): T = O'O'^T (Algorithm 1, Gram step), lambda
+ * (Tab. I modes), the solve and eta (Eq. minsrR, App. F; as
+ * nqs_minsr_step), and delta theta entries p0 .. p1 - 1 into dtheta (device
+ * FP64 [p1 - p0]; eta_eff included).  0 <= p0 <= p1 <= Np. */
+nqs_status nqs_shard_solve(nqs_ctx *ctx, const void *rows, int64_t R, const double *eps,
+                           const nqs_step_hparams *hp, int64_t p0, int64_t p1, double *dtheta,
+                           nqs_step_stats *dev_stats, void *stream);
+
+/* Momentum and update (App. B) with the gathered delta theta (device FP64
+ * [Np]); a non-finite entry sets NQS_ERR_NONFINITE and, as any device-side
+ * error, leaves theta and momentum unchanged. */
+nqs_status nqs_shard_apply(nqs_ctx *ctx, double *theta, double *momentum, const double *dtheta,
+                           const nqs_step_hparams *hp, nqs_step_stats *dev_stats, void *stream);
+
 /* ------------------------------------------------- allocation-free log Psi */
 
 /* Size of the static device scratch array behind nqs_logpsi_noalloc. */

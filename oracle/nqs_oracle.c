@@ -417,8 +417,11 @@ int or_conditionals(const or_model *m, const double *theta, const uint8_t *spins
 
 /* ------------------------------------------------------------ sampler */
 
-int or_sample(const or_model *m, const double *theta, int64_t ns, uint64_t seed,
-              uint64_t step, uint8_t *spins, double *logpsi) {
+/* Samples s0 .. s0 + n - 1 of a draw: sample s uses the Philox uniforms of
+ * counter (k, s, step) at every site k, so disjoint ranges of one draw are
+ * drawn independently (a rank of a sharded step draws its own range). */
+int or_sample_range(const or_model *m, const double *theta, int64_t s0, int64_t n,
+                    uint64_t seed, uint64_t step, uint8_t *spins, double *logpsi) {
   or_layout L = or_make_layout(m);
   int err = 0;
 #pragma omp parallel
@@ -430,8 +433,9 @@ int or_sample(const or_model *m, const double *theta, int64_t ns, uint64_t seed,
       err = -1;
     } else {
 #pragma omp for schedule(dynamic, 1)
-      for (int64_t s = 0; s < ns; ++s) {
-        for (int k = 0; k < L.N; ++k) u[k] = or_uniform(seed, step, (uint64_t)s, (uint64_t)k);
+      for (int64_t s = 0; s < n; ++s) {
+        for (int k = 0; k < L.N; ++k)
+          u[k] = or_uniform(seed, step, (uint64_t)(s0 + s), (uint64_t)k);
         or_forward(m, &L, theta, &F, spins + s * L.N, u, &logpsi[2 * s],
                    &logpsi[2 * s + 1]);
       }
@@ -440,6 +444,11 @@ int or_sample(const or_model *m, const double *theta, int64_t ns, uint64_t seed,
     or_fwd_free(&F);
   }
   return err;
+}
+
+int or_sample(const or_model *m, const double *theta, int64_t ns, uint64_t seed,
+              uint64_t step, uint8_t *spins, double *logpsi) {
+  return or_sample_range(m, theta, 0, ns, seed, step, spins, logpsi);
 }
 
 /* ------------------------------------------------------- local energy */

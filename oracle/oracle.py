@@ -189,13 +189,15 @@ def conditionals(spec, theta, spins) -> np.ndarray:
     return out
 
 
-def sample(spec, theta, ns, seed, step):
+def sample(spec, theta, ns, seed, step, s0=0):
+    """ns configurations drawn with the Philox counters of samples
+    s0 .. s0 + ns - 1 (Sec. II.A inverse-CDF sampling)."""
     m = model_struct(spec)
     th = np.ascontiguousarray(theta, dtype=np.float64)
     sp = np.zeros((ns, spec.N), dtype=np.uint8)
     lp = np.zeros((ns, 2))
-    rc = lib().or_sample(C.byref(m), _p(th), C.c_int64(ns), C.c_uint64(seed),
-                         C.c_uint64(step), _p(sp), _p(lp))
+    rc = lib().or_sample_range(C.byref(m), _p(th), C.c_int64(s0), C.c_int64(ns),
+                               C.c_uint64(seed), C.c_uint64(step), _p(sp), _p(lp))
     assert rc == 0
     return sp, lp[:, 0] + 1j * lp[:, 1]
 

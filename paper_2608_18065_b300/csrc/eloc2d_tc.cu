@@ -1,5 +1,7 @@
 // eloc2d_tc.cu -- log Psi of every connected configuration (Sec. II.C) for
-// 2D lattices on the zig-zag path (Sec. II.B), hidden size 64, mixed
+// 2D lattices on the zig-zag path (Sec. II.B), hidden size 64 (and 32, run
+// with its units padded to 64 by zero weights, biases and head columns: a
+// padded unit keeps h' = 0, c = tanh(0) = 0, h = 0 and adds nothing), mixed
 // precision, on the tensor cores (sm_103a).
 //
 // A connected configuration sigma' first differs from its sample at site
@@ -118,6 +120,9 @@ __device__ __forceinline__ void issue_atom(uint32_t d, uint32_t a, uint32_t b, u
   }
 }
 
+// DHM: the model's hidden size (64, or 32 padded to 64); it fixes only how
+// the weights and the cached states are read.
+template <int DHM>
 __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) {
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
@@ -142,25 +147,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
 
   // weights as B[n][k] planes: W row n = 64 j + unit (gate j), U atoms
   // B[unit][k] over the horizontal (atom 0) and vertical (atom 1) inputs
+  constexpr int ngm = 3 * DHM;
   for (int e = tid; e < NG * DH; e += THREADS) {
     const int n = e / DH, k = e % DH, j = n / DH, q = n % DH;
-    split_at(Wh, Wl, sw128_off(n, k), a.pack[a.oWgT + k * NG + 3 * q + j]);
+    split_at(Wh, Wl, sw128_off(n, k),
+             q < DHM && k < DHM ? a.pack[a.oWgT + k * ngm + 3 * q + j] : 0.f);
   }
   for (int e = tid; e < 2 * DH * DH; e += THREADS) {
     const int at = e / (DH * DH), r = e % (DH * DH), n = r / DH, k = r % DH;
-    split_at(Uh + at * BU, Ul + at * BU, sw128_off(n, k), a.pack[a.oU12T + (DH * at + k) * DH + n]);
+    split_at(Uh + at * BU, Ul + at * BU, sw128_off(n, k),
+             n < DHM && k < DHM ? a.pack[a.oU12T + (DHM * at + k) * DHM + n] : 0.f);
   }
   // additive terms per input pair (d0, d1), 2 = no input: update and reset
   // gates b + W_x x, candidate input W_in x + b_in (outside the reset gate)
   for (int e = tid; e < 9 * NG; e += THREADS) {
     const int c = e / NG, r = e % NG, j = r / DH, q = r % DH, d0 = c / 3, d1 = c % 3;
-    float v = a.pack[a.obias + 4 * q + (j == 2 ? 3 : j)];
-    if (d0 < 2) v += a.pack[a.oxw + d0 * NG + 3 * q + j];
-    if (d1 < 2) v += a.pack[a.oxw + (2 + d1) * NG + 3 * q + j];
+    float v = 0.f;
+    if (q < DHM) {
+      v = a.pack[a.obias + 4 * q + (j == 2 ? 3 : j)];
+      if (d0 < 2) v += a.pack[a.oxw + d0 * ngm + 3 * q + j];
+      if (d1 < 2) v += a.pack[a.oxw + (2 + d1) * ngm + 3 * q + j];
+    }
     tab[c * TS + r] = v;
   }
-  for (int e = tid; e < DH; e += THREADS) sbh[e] = a.pack[a.obias + 4 * e + 2];
-  for (int e = tid; e < 4 * DH; e += THREADS) shead[e] = a.pack[a.ohead + e];
+  for (int e = tid; e < DH; e += THREADS) sbh[e] = e < DHM ? a.pack[a.obias + 4 * e + 2] : 0.f;
+  for (int e = tid; e < 4 * DH; e += THREADS)
+    shead[e] = e % DH < DHM ? a.pack[a.ohead + (e / DH) * DHM + e % DH] : 0.f;
   if (tid < 4) shc[tid] = a.pack[a.ohc + tid];
   if (tid == 0) {
     for (int t = 0; t < 3; ++t) mbar_init(smem_u32(&bars[t]), 1);  // one commit each
@@ -219,9 +231,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
       const int jr = k / Lx, m = k - jr * Lx;
       const int col = (jr & 1) ? (Lx - 1 - m) : m;
       const int ver = k >= Lx ? k - 2 * m - 1 : -1;
-      if (valid && ver >= 0) {
+      // (units of a padded half have no cached state: zero)
+      if (valid && ver >= 0 && (ver >= kst || UH * half < DHM)) {
         const float4 *src = reinterpret_cast<const float4 *>(
-            ver >= kst ? cb + col * DH : a.hcache + ((int64_t)s * N + ver) * DH + UH * half);
+            ver >= kst ? cb + col * DH : a.hcache + ((int64_t)s * N + ver) * DHM + UH * half);
 #pragma unroll
         for (int q = 0; q < UH / 4; ++q) cp_async16(vs + q, src + q);
       } else {
@@ -231,8 +244,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
     };
     // h_{kst-1} of this thread's units into the S planes
     {
-      const float4 *src = valid && kst > 0
-          ? reinterpret_cast<const float4 *>(a.hcache + ((int64_t)s * N + kst - 1) * DH + UH * half)
+      const float4 *src = valid && kst > 0 && UH * half < DHM
+          ? reinterpret_cast<const float4 *>(a.hcache + ((int64_t)s * N + kst - 1) * DHM + UH * half)
           : nullptr;
 #pragma unroll
       for (int g8 = 0; g8 < UH / 8; ++g8) {
@@ -447,15 +460,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
 
 }  // namespace
 
-bool eloc2d_tc_supported(int dim, int dh) { return dim == 2 && dh == DH; }
+bool eloc2d_tc_supported(int dim, int dh) { return dim == 2 && (dh == DH || dh == DH / 2); }
 
-cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_eloc2d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st) {
+  if (dh != DH && dh != DH / 2) return cudaErrorInvalidValue;
+  const void *kern = dh == DH ? (const void *)k_eloc2d_tc<DH> : (const void *)k_eloc2d_tc<DH / 2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int grid = args.ntiles < sm_count ? args.ntiles : sm_count;
   if (grid <= 0) return cudaSuccess;
-  k_eloc2d_tc<<<grid, THREADS, SMEM_BYTES, st>>>(args);
+  if (dh == DH)
+    k_eloc2d_tc<DH><<<grid, THREADS, SMEM_BYTES, st>>>(args);
+  else
+    k_eloc2d_tc<DH / 2><<<grid, THREADS, SMEM_BYTES, st>>>(args);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,8 @@
 // eloc2d_tc.h -- tensor-core engines for the connected-configuration
 // suffixes of 2D lattices (mixed precision, zig-zag path, every state
-// cached): weights resident in shared memory for hidden size 64
-// (eloc2d_tc.cu), streamed from L2 for hidden sizes 96 and 128
-// (eloc2d_tcs.cu).
+// cached): weights resident in shared memory for hidden size 64 and 32
+// (padded to 64; eloc2d_tc.cu), streamed from L2 for hidden sizes 96 and
+// 128 (eloc2d_tcs.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,7 +23,8 @@ struct Eloc2dTcArgs {
   const double *item_e;   // [n_off][ns] matrix elements
   const int *item_cnt;    // [n_off]
   double *contrib;        // [n_off][ns][2]
-  float *colbuf;          // [grid][128][Lx][64]: recomputed states by lattice column
+  float *colbuf;          // [grid][128][Lx][max(dh, 64)]: recomputed states (U2 h in
+                          // the streamed engine) by lattice column
   int *err;               // device status word (NQS_ERR_TIMEOUT on a wait that ran out)
   int *tile_ctr;          // zeroed before the launch: tiles handed out in rank order
                           // (op_f[4 i + 3] = the operator of rank i, longest suffix first)
@@ -34,8 +35,9 @@ struct Eloc2dTcArgs {
 constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)
 
 bool eloc2d_tc_supported(int dim, int dh);
-// grid <= sm_count; the column buffer must hold grid x 128 rows
-cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st);
+// dh = the model's hidden size (64, or 32 padded to 64); grid <= sm_count;
+// the column buffer must hold grid x 128 rows of Lx x 64 floats
+cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st);
 
 // Streamed-weight engine, hidden sizes 96 and 128: column buffer [grid][128]
 // [Lx][dh] of U2 h (FP32); grid <= sm_count.

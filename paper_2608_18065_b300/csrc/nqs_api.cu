@@ -179,7 +179,10 @@ void carve(nqs_ctx *c) {
   if (c->L.dim == 2 && c->es == 4 &&
       (eloc2d_tc_supported(c->L.dim, (int)dh) || eloc2d_tcs_supported(c->L.dim, (int)dh)))
     cb_rows = std::max(cb_rows, (size_t)c->rd.sm_count * ELOC2D_TC_ROWS);
-  o.colbuf = take(c->L.dim == 2 ? cb_rows * c->L.Lx * dh * es : 0);
+  // (a hidden size 32 lattice on the tensor-core engine runs padded to 64)
+  const size_t cbw = (c->L.dim == 2 && c->es == 4 && eloc2d_tc_supported(c->L.dim, (int)dh))
+                         ? std::max<int64_t>(dh, 64) : dh;
+  o.colbuf = take(c->L.dim == 2 ? cb_rows * c->L.Lx * cbw * es : 0);
   o.adj = take(R * (c->ck ? c->ck : N) * c->adjw * es);
   o.adjcol = take(c->L.dim == 2 ? R * c->L.Lx * dh * es : 0);
   o.O = take(R * np * es);
@@ -345,7 +348,7 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.err = W<int>(c, c->off.sstat);
       e.tile_ctr = W<int>(c, c->off.tctr);
       CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
-      CU(eloc2d_tc_run(e, eloc_grid_cap(c, c->rd.sm_count), st));
+      CU(eloc2d_tc_run(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
     } else if (f32(c) && c->ck == 0 && gram_tc_available() &&
                eloc2d_tcs_supported(c->L.dim, c->L.dh)) {
       // 2D tensor-core engine with the weights streamed from L2 (d_h 96, 128)
@@ -1257,7 +1260,10 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
   double *eloc = W<double>(c, c->off.eloc);
   // (1) grid of the connected-configuration engine
   {
-    const bool tce = f32(c) && gram_tc_available() && eloc_tc_supported(c->L.dim, c->L.dh);
+    const bool tce = f32(c) && gram_tc_available() &&
+                     (eloc_tc_supported(c->L.dim, c->L.dh) ||
+                      (c->ck == 0 && (eloc2d_tc_supported(c->L.dim, c->L.dh) ||
+                                      eloc2d_tcs_supported(c->L.dim, c->L.dh))));
     const int emax = tce ? c->rd.sm_count : c->eloc_grid;
     std::vector<int> cand;
     for (int d : {1, 2, 4}) uniq_push(cand, emax / d);
@@ -1426,6 +1432,157 @@ nqs_status nqs_set_damping(nqs_ctx *c, double omega, double lambda0) {
 }
 
 // ------------------------------------------------------------ batched step
+
+}  // extern "C"
+
+// ---------------------------------------------------- sample-sharded step
+// The steps of Algorithm 1 with the Ns samples split over G ranks: each rank
+// samples, evaluates and differentiates its own range of samples; the
+// centring sums are added over the ranks, the centred rows gathered, and the
+// Gram, the solve and (by parameter ranges) delta theta formed from them.
+namespace {
+
+template <typename T>
+nqs_status shard_forward_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *hp,
+                           int64_t s0, int64_t n, double *sums, cudaStream_t st) {
+  const int64_t np = c->L.np;
+  uint8_t *spins = W<uint8_t>(c, c->off.spins);
+  double *eloc = W<double>(c, c->off.eloc);
+  T *O = W<T>(c, c->off.O);
+  c->cur_ns = n;
+  CU(cudaMemsetAsync(W<int32_t>(c, c->off.sstat), 0, 64, st));
+  k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hp->step_index);
+  c->launches += 1;
+  ST(pack_theta<T>(c, theta, st));
+  {
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = n; a.seed = hp->seed; a.step = (uint64_t)hp->step_index; a.s0 = s0;
+    a.step_dev = W<int64_t>(c, c->off.dstep);
+    a.spins = spins; a.logpsi = W<double>(c, c->off.logpsi);
+    if (c->ck == 0) {
+      a.gcache = W<T>(c, c->off.gcache);
+      a.gw = c->gw;
+    }
+    c->launches += 1;
+    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+  }
+  ST(eloc_T<T>(c, n, spins, eloc, st));
+  const unsigned nblk = c->L.cplx ? 2u : 1u;
+  k_energy_sums<<<1, 1024, 0, st>>>(eloc, n, sums + nblk * np);
+  ST(jac_T<T>(c, n, spins, O, st));
+  const int chunks = (int)((n + COL_ROWS - 1) / COL_ROWS);
+  dim3 g((unsigned)((np + 255) / 256), nblk * chunks);
+  k_colsum_part<T><<<g, 256, 0, st>>>(O, n, np, chunks, W<double>(c, c->off.part));
+  k_colsum_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
+      W<double>(c, c->off.part), np, chunks, sums);
+  c->launches += 3;
+  return cu(cudaGetLastError());
+}
+
+template <typename T>
+nqs_status shard_center_T(nqs_ctx *c, const double *sums, int64_t ns, int64_t n, void *rows,
+                          double *eps, nqs_step_stats *stats, cudaStream_t st) {
+  const int64_t np = c->L.np, nblk = c->L.cplx ? 2 : 1;
+  k_shard_eps<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      W<double>(c, c->off.eloc), n, c->L.N, c->L.cplx, sums + nblk * np, ns, stats, eps);
+  const int64_t tot = nblk * n * np;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+  k_shard_center<T><<<blocks, 256, 0, st>>>(W<T>(c, c->off.O), n, np, nblk * n, sums, ns,
+                                            static_cast<T *>(rows));
+  c->launches += 2;
+  return cu(cudaGetLastError());
+}
+
+template <typename T>
+nqs_status shard_solve_T(nqs_ctx *c, const void *A, int64_t R, const double *eps,
+                         const nqs_step_hparams *hp, int64_t p0, int64_t p1, double *dtheta,
+                         nqs_step_stats *stats, cudaStream_t st) {
+  const int64_t np = c->L.np;
+  double *Tm = W<double>(c, c->off.T);
+  double *x = W<double>(c, c->off.x);
+  int32_t *sstat = W<int32_t>(c, c->off.sstat);
+  ST(gram_any(c, A, R, np, Tm, st));
+  {
+    const int nparts = 256;
+    c->launches += 2;
+    k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
+    k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts,
+                                        hp->lambda_mode, hp->lambda, hp->lambda_coeff,
+                                        hp->lambda_pow, stats, nullptr, nullptr);
+    CU(cudaGetLastError());
+  }
+  const RetryInfo rinfo{hp, stats};
+  ST(chol_solve(c, Tm, R, eps, x, sstat, st, f32(c) && gram_tc_available() ? &rinfo : nullptr));
+  k_eta<<<1, 1024, 0, st>>>(eps, x, R, hp->eta0, hp->decay_T, hp->trust_region,
+                            W<int64_t>(c, c->off.dstep), stats, sstat,
+                            reinterpret_cast<int32_t *>(W<unsigned>(c, c->off.cbar) + 4));
+  const int64_t nc = p1 - p0;
+  if (nc > 0) {
+    const int rows_per = 64;
+    const int nparts = (int)((R + rows_per - 1) / rows_per);
+    dim3 g((unsigned)((nc + 255) / 256), (unsigned)nparts);
+    k_gemv_cols<T><<<g, 256, 0, st>>>(static_cast<const T *>(A), R, np, p0, nc, x, rows_per,
+                                      W<double>(c, c->off.part));
+    k_dtheta<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts,
+                                                          nc, stats, dtheta);
+    c->launches += 2;
+  }
+  c->launches += 1;
+  return cu(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+nqs_status nqs_shard_forward(nqs_ctx *c, const double *theta, const nqs_step_hparams *hp,
+                             int64_t s0, int64_t n, double *sums, void *stream) {
+  if (!c || !theta || !hp || !sums || n < 1 || n > c->max_ns || s0 < 0 ||
+      s0 + n > ((int64_t)1 << 32))
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  c->gnext = -1;  // the device step counter changes: a replayed step must set it again
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? shard_forward_T<float>(c, theta, hp, s0, n, sums, st)
+                : shard_forward_T<double>(c, theta, hp, s0, n, sums, st);
+}
+
+nqs_status nqs_shard_center(nqs_ctx *c, const double *sums, int64_t ns, int64_t n, void *rows,
+                            double *eps, nqs_step_stats *dev_stats, void *stream) {
+  if (!c || !sums || !rows || !eps || !dev_stats || n < 1 || n > c->max_ns || ns < n ||
+      n != c->cur_ns)
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? shard_center_T<float>(c, sums, ns, n, rows, eps, dev_stats, st)
+                : shard_center_T<double>(c, sums, ns, n, rows, eps, dev_stats, st);
+}
+
+nqs_status nqs_shard_solve(nqs_ctx *c, const void *rows, int64_t R, const double *eps,
+                           const nqs_step_hparams *hp, int64_t p0, int64_t p1, double *dtheta,
+                           nqs_step_stats *dev_stats, void *stream) {
+  const int64_t rmax = c ? (c->L.cplx ? 2 * c->max_ns : c->max_ns) : 0;
+  if (!c || !rows || !eps || !hp || !dev_stats || R < 2 || R > rmax ||
+      (c->L.cplx && R % 2) || p0 < 0 || p1 < p0 || p1 > c->L.np || (p1 > p0 && !dtheta) ||
+      (hp->lambda_mode != 0 && hp->lambda_mode != 1))
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? shard_solve_T<float>(c, rows, R, eps, hp, p0, p1, dtheta, dev_stats, st)
+                : shard_solve_T<double>(c, rows, R, eps, hp, p0, p1, dtheta, dev_stats, st);
+}
+
+nqs_status nqs_shard_apply(nqs_ctx *c, double *theta, double *mom, const double *dtheta,
+                           const nqs_step_hparams *hp, nqs_step_stats *dev_stats, void *stream) {
+  if (!c || !theta || !mom || !dtheta || !hp || !dev_stats) return NQS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t np = c->L.np;
+  const unsigned blocks = (unsigned)((np + 255) / 256);
+  k_check_finite<<<blocks, 256, 0, st>>>(dtheta, np, dev_stats);
+  k_apply<<<blocks, 256, 0, st>>>(theta, mom, dtheta, np, hp->mu, dev_stats);
+  c->launches += 2;
+  return cu(cudaGetLastError());
+}
 
 }  // extern "C"
 

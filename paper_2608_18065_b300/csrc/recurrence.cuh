@@ -122,6 +122,7 @@ template <typename T> struct FwdArgs {
   // SAMPLE
   uint64_t seed, step;
   const int64_t *step_dev; // optional: step counter on the device (overrides step)
+  int64_t s0;              // Philox sample index of row 0 (a rank's range of a sharded draw)
   // SAMPLE/GIVEN/ELOC spins: SAMPLE writes, others read
   uint8_t *spins;
   double *logpsi;          // [rows*2]
@@ -477,10 +478,10 @@ k_forward(const FwdArgs<T> A) {
           const uint64_t stp = A.step_dev ? (uint64_t)*A.step_dev : A.step;
           if constexpr (F32) {
             const float p0 = forced == 0 ? 1.f : (forced == 1 ? 0.f : (float)ex(lp0));
-            sg = uniform24(A.seed, stp, (uint32_t)my_s, (uint32_t)k) < p0 ? 0 : 1;
+            sg = uniform24(A.seed, stp, (uint32_t)(my_s + A.s0), (uint32_t)k) < p0 ? 0 : 1;
           } else {
             double p0 = forced == 0 ? 1.0 : (forced == 1 ? 0.0 : (double)ex(lp0));
-            double uu = uniform53(A.seed, stp, (uint32_t)my_s, (uint32_t)k);
+            double uu = uniform53(A.seed, stp, (uint32_t)(my_s + A.s0), (uint32_t)k);
             sg = uu < p0 ? 0 : 1;
           }
           ssp[r * NP + k] = (uint8_t)sg;

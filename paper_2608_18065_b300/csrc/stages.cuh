@@ -331,6 +331,98 @@ __global__ void k_dtheta(const double *__restrict__ part, int nparts, int64_t np
   if (!isfinite(d)) atomicCAS(reinterpret_cast<int *>(&st->status), (int)NQS_OK, (int)NQS_ERR_NONFINITE);
 }
 
+// ------------------------------------------------- sample-sharded step
+// Partial sums of a rank's samples: the chunk partials of k_colsum_part
+// added up without dividing (per block, [blk][np]).
+__global__ void k_colsum_fin(const double *__restrict__ part, int64_t np, int chunks,
+                             double *sums) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int blk = blockIdx.y;
+  double acc = 0.0;
+  for (int c = 0; c < chunks; ++c) acc += part[((int64_t)blk * chunks + c) * np + p];
+  sums[(int64_t)blk * np + p] = acc;
+}
+
+// sum Re eps, sum Im eps, sum |eps|^2 of a rank's local energies (one block)
+__global__ void k_energy_sums(const double *__restrict__ eloc, int64_t n, double *out) {
+  __shared__ double a[1024], b[1024], q[1024];
+  double r = 0.0, i = 0.0, m = 0.0;
+  for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
+    const double x = eloc[2 * s], y = eloc[2 * s + 1];
+    r += x; i += y; m += x * x + y * y;
+  }
+  a[threadIdx.x] = r; b[threadIdx.x] = i; q[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      a[threadIdx.x] += a[threadIdx.x + o];
+      b[threadIdx.x] += b[threadIdx.x + o];
+      q[threadIdx.x] += q[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = a[0]; out[1] = b[0]; out[2] = q[0]; }
+}
+
+// E, Var (= sum |eps|^2 / Ns - |E|^2) and the V-score from the summed
+// energies of all ranks, and this rank's rows of eps-bar' (as k_energy)
+__global__ void k_shard_eps(const double *__restrict__ eloc, int64_t n, int N, int cplx,
+                            const double *__restrict__ esum, int64_t ns, nqs_step_stats *st,
+                            double *eps) {
+  const double Er = esum[0] / (double)ns, Ei = esum[1] / (double)ns;
+  const double isq = 1.0 / sqrt((double)ns);
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    eps[s] = 2.0 * (eloc[2 * s] - Er) * isq;
+    if (cplx) eps[n + s] = 2.0 * (eloc[2 * s + 1] - Ei) * isq;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double var = esum[2] / (double)ns - (Er * Er + Ei * Ei);
+    st->E_re = Er; st->E_im = Ei; st->var = var;
+    st->vscore = (double)N * var / (Er * Er);
+    int bad = !(isfinite(Er) && isfinite(Ei) && isfinite(var));
+    st->status = bad ? NQS_ERR_NONFINITE : NQS_OK;
+  }
+}
+
+// A rank's rows of O' = (O - sum / Ns) / sqrt(Ns) into out (FP64
+// arithmetic, rounded once to the working precision); sums per block.
+template <typename T>
+__global__ void k_shard_center(const T *__restrict__ O, int64_t n, int64_t np, int64_t rows,
+                               const double *__restrict__ sums, int64_t ns, T *__restrict__ out) {
+  const double isq = 1.0 / sqrt((double)ns), ins = 1.0 / (double)ns;
+  const int64_t tot = rows * np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / np, p = e - r * np;
+    const double m = sums[(r / n) * np + p] * ins;
+    out[e] = (T)(((double)O[e] - m) * isq);
+  }
+}
+
+// partial products of columns p0 .. p0 + nc - 1 of a row-major A (row
+// stride lda) with x over rows_per rows per grid.y block
+template <typename T>
+__global__ void k_gemv_cols(const T *__restrict__ A, int64_t R, int64_t lda, int64_t p0,
+                            int64_t nc, const double *__restrict__ x, int rows_per, double *part) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nc) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+  const int64_t r1 = min64(R, r0 + rows_per);
+  double acc = 0.0;
+  for (int64_t r = r0; r < r1; ++r) acc += (double)A[r * lda + p0 + q] * x[r];
+  part[(int64_t)blockIdx.y * nc + q] = acc;
+}
+
+// flags a non-finite delta theta (all shards gathered) in the step status
+__global__ void k_check_finite(const double *__restrict__ v, int64_t n, nqs_step_stats *st) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i]))
+      atomicCAS(reinterpret_cast<int *>(&st->status), (int)NQS_OK, (int)NQS_ERR_NONFINITE);
+}
+
 // m <- mu m + (1-mu) dtheta; theta <- theta - m (App. B), only when the
 // step's status is OK.
 __global__ void k_apply(double *theta, double *mom, const double *__restrict__ dth, int64_t np,

@@ -64,7 +64,8 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_destroy", "nqs_minsr_step_batched", "nqs_batch_set_graph",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
-           "nqs_set_damping", "nqs_spectrum",
+           "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
+           "nqs_shard_solve", "nqs_shard_apply",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -253,6 +254,42 @@ class Context:
             _check(lib().nqs_minsr_step_ex(self._h, _ptr(theta), _ptr(mom), C.byref(hps),
                                            _ptr(stats), C.byref(o), _stream(stream)))
         return stats
+
+    # ------------------------------------------------ sample-sharded step
+    def shard_sums_len(self):
+        return self.rows_per_sample * self.np + 3
+
+    def shard_forward(self, theta, hp: HParams, step_index, s0, n, sums=None, stream=None):
+        """Sampling, E_loc and O of samples s0 .. s0 + n - 1; partial sums."""
+        if sums is None:
+            sums = torch.empty(self.shard_sums_len(), dtype=torch.float64, device=self.device)
+        hps = step_hparams(hp, step_index)
+        _check(lib().nqs_shard_forward(self._h, _ptr(theta), C.byref(hps), C.c_int64(s0),
+                                       C.c_int64(n), _ptr(sums), _stream(stream)))
+        return sums
+
+    def shard_center(self, sums, ns, n, stats, stream=None):
+        """This rank's centred rows O' [nblk*n, Np] and eps-bar' [nblk*n]."""
+        rows = torch.empty((self.rows_per_sample * n, self.np), dtype=self.odtype,
+                           device=self.device)
+        eps = torch.empty(self.rows_per_sample * n, dtype=torch.float64, device=self.device)
+        _check(lib().nqs_shard_center(self._h, _ptr(sums), C.c_int64(ns), C.c_int64(n),
+                                      _ptr(rows), _ptr(eps), _ptr(stats), _stream(stream)))
+        return rows, eps
+
+    def shard_solve(self, rows, eps, hp: HParams, step_index, p0, p1, stats, stream=None):
+        """T, lambda, x, eta from the gathered rows; delta theta [p0, p1)."""
+        dth = torch.empty(max(p1 - p0, 1), dtype=torch.float64, device=self.device)
+        hps = step_hparams(hp, step_index)
+        _check(lib().nqs_shard_solve(self._h, _ptr(rows), C.c_int64(rows.shape[0]), _ptr(eps),
+                                     C.byref(hps), C.c_int64(p0), C.c_int64(p1), _ptr(dth),
+                                     _ptr(stats), _stream(stream)))
+        return dth[:p1 - p0]
+
+    def shard_apply(self, theta, mom, dtheta, hp: HParams, step_index, stats, stream=None):
+        hps = step_hparams(hp, step_index)
+        _check(lib().nqs_shard_apply(self._h, _ptr(theta), _ptr(mom), _ptr(dtheta),
+                                     C.byref(hps), _ptr(stats), _stream(stream)))
 
     def set_damping(self, omega, lambda0):
         """Levenberg-Marquardt damping (App. G): omega > 1 on, else off."""

@@ -1,5 +1,8 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the
 C-ABI binding and the oracle on the same seeded inputs."""
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -50,3 +53,29 @@ def near_ties(model, theta, spins, seed, step, tol):
         u = np.array([O.uniform(seed, step, s, k) for k in range(model.N)])
         out += int(np.sum(np.abs(u - p0) < tol))
     return out
+
+
+def max_elem_err(a, b):
+    """Largest element-wise error, relative to the largest |b| (one sample
+    or entry off by the tolerance fails, unlike a vector-norm bound)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def max_row_err(a, b):
+    """Largest element-wise error, each row relative to its own largest |b|."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = np.maximum(np.max(np.abs(b), axis=1, keepdims=True), 1e-300)
+    return float(np.max(np.abs(a - b) / scale))
+
+
+def record_error(case, **errors):
+    """Append measured errors of the mixed path against the oracle to the
+    JSON-lines file named by NQS_ERRORS_OUT (nothing when unset)."""
+    path = os.environ.get("NQS_ERRORS_OUT")
+    if not path:
+        return
+    with open(path, "a") as f:
+        f.write(json.dumps({"case": case, **{k: float(v) for k, v in errors.items()}}) + "\n")

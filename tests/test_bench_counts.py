@@ -31,6 +31,9 @@ def test_tensor_core_flops_per_site():
     assert bench.eloc_tc_site_flops(ModelSpec(1, 100, 1, 64)) == 3 * 2 * 64 * 192
     assert bench.eloc_tc_site_flops(ModelSpec(1, 200, 1, 32)) == 3 * 2 * 64 * 192  # padded
     assert bench.eloc_tc_site_flops(ModelSpec(2, 10, 10, 64)) == 3 * 2 * (64 * 192 + 128 * 64)
+    # streamed engine: [U1; U2] h_{k-1} (K = dh, N = 2dh) and the gates (K = dh, N = 3dh)
+    assert bench.eloc_tc_site_flops(ModelSpec(2, 8, 8, 96)) == 3 * 2 * (96 * 192 + 96 * 288)
+    assert bench.eloc_tc_site_flops(ModelSpec(2, 8, 8, 128)) == 3 * 2 * (128 * 256 + 128 * 384)
 
 
 def test_fma_flops_per_site():
@@ -43,8 +46,9 @@ def test_fma_flops_per_site():
 
 
 def test_engine_selection_matches_the_library():
-    # tensor-core E_loc engines: mixed 1D d_h 32 / 64, mixed 2D d_h 64
+    # tensor-core E_loc engines: mixed 1D d_h 32 / 64, mixed 2D d_h 64, 96, 128
     used = [(d, dh) for d in (1, 2) for dh in (8, 16, 32, 64, 96, 128)
             if bench.eloc_tc_used(ModelSpec(d, 4, 4 if d == 2 else 1, dh), "mixed")]
-    assert used == [(1, 32), (1, 64), (2, 64)]
+    assert used == [(1, 32), (1, 64)] + [(2, dh) for dh in bench.ENGINE2D_DH]
+    assert set(bench.ENGINE2D_DH) >= {64, 96, 128}
     assert not bench.eloc_tc_used(ModelSpec(1, 10, 1, 64), "fp64")
