@@ -273,6 +273,34 @@ def test_minsr_step_mixed_error_report(model, ham, hp):
                  dtheta_end_to_end=err, kappa=kappa)
 
 
+@pytest.mark.parametrize("model,ham,hp", STEP_CASES[:2], ids=STEP_IDS[:2])
+def test_energy_trajectory_mixed_vs_oracle(model, ham, hp):
+    """Eight chained steps of the mixed path and of the FP64 oracle, each from
+    its own previous state with the same Philox keys: while the two draw the
+    same samples the energies agree to the mixed E_loc tolerance (the states
+    drift apart by the steps' own delta theta errors, ~1e-4)."""
+    c = ctx(model, ham, "mixed", hp.ns)
+    th, thd = theta_dev(model, 1234)
+    mo = np.zeros_like(th)
+    momd = torch.zeros_like(thd)
+    from paper_2608_18065_b300.nqs import decode_stats
+    worst, same = 0.0, 0
+    for t in range(8):
+        outs = c.step_outputs(hp.ns)
+        st = decode_stats(c.minsr_step(thd, momd, hp, t, outputs=outs))
+        torch.cuda.synchronize()
+        th, mo, st_o, b = O.minsr_step(model, ham, th, mo, hp, t, want=("spins",))
+        assert st["status"] == 0
+        if not np.array_equal(outs["spins"].cpu().numpy(), b["spins"]):
+            break
+        same += 1
+        worst = max(worst, abs(st["E_re"] - st_o["E_re"]) / abs(st_o["E_re"]))
+    assert same >= 3
+    assert worst < TOL_MIXED_ELOC
+    record_error(f"trajectory_{model.dim}d_{model.Lx}x{model.Ly}_dh{model.dh}_{ham.family}",
+                 E_rel_max=worst, steps_same_samples=same)
+
+
 # hidden size 64 on 1D chains takes the tensor-core connected-configuration
 # engine in the mixed path, and so does 32 (units padded with zeros); 300
 # samples = two full 128-row tiles + a ragged one
