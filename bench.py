@@ -933,9 +933,22 @@ def load_errors():
 
 
 def _mean_stderr(es, vs, ns):
+    """Mean of E over the last 10 steps and its standard error: the larger
+    of the sampling error (sqrt(mean Var / Ns / 10)) and the spread of the
+    10 values themselves (std / sqrt(10): the trajectory still moves)."""
     last = np.array(es[-10:])
-    se = float(np.sqrt(np.mean(np.array(vs[-10:]) / ns) / 10.0))
-    return float(last.mean()), se
+    se_s = float(np.sqrt(np.mean(np.array(vs[-10:]) / ns) / 10.0))
+    se_e = float(np.std(last, ddof=1) / np.sqrt(len(last))) if len(last) > 1 else 0.0
+    return float(last.mean()), max(se_s, se_e)
+
+
+def _match(a, b):
+    """Matched energies: the two means differ by no more than the larger
+    standard error (the criterion of the measurement plan); also reported,
+    within three combined standard errors."""
+    d = abs(a["E_last10"] - b["E_last10"])
+    return (bool(d <= max(a["stderr"], b["stderr"])),
+            bool(d <= 3.0 * np.hypot(a["stderr"], b["stderr"])))
 
 
 def matched_energy(w, hp, steps, dev, E_ref=None):
@@ -969,8 +982,7 @@ def matched_energy(w, hp, steps, dev, E_ref=None):
         out[prec] = r
         c.close()
         del c
-    d = abs(out["mixed"]["E_last10"] - out["fp64"]["E_last10"])
-    out["matched"] = bool(d <= max(out["mixed"]["stderr"], out["fp64"]["stderr"]))
+    out["matched"], out["within_3sigma"] = _match(out["mixed"], out["fp64"])
     return out
 
 
@@ -1023,12 +1035,12 @@ def matched_energy_batched(insts, steps, dev):
         c.close()
         mm, ms1 = _mean_stderr(es[i], vs[i], w.hp.ns)
         fm, fs = _mean_stderr(e64, v64, w.hp.ns)
-        ok = bool(abs(mm - fm) <= max(ms1, fs))
+        a = {"E_last10": mm, "stderr": ms1, "E_first": es[i][0]}
+        f = {"E_last10": fm, "stderr": fs, "E_first": e64[0]}
+        ok, ok3 = _match(a, f)
         allm &= ok
-        out["instances"].append({"instance": w.name, "N": w.model.N,
-                                 "mixed": {"E_last10": mm, "stderr": ms1, "E_first": es[i][0]},
-                                 "fp64": {"E_last10": fm, "stderr": fs, "E_first": e64[0]},
-                                 "matched": ok})
+        out["instances"].append({"instance": w.name, "N": w.model.N, "mixed": a, "fp64": f,
+                                 "matched": ok, "within_3sigma": ok3})
     out["fp64_one_at_a_time_seconds"] = time.perf_counter() - t0
     out["matched"] = allm
     return out

@@ -370,6 +370,51 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,
                               const nqs_step_hparams *hps, int flags,
                               double *step_ms, void *stream);
 
+/* ------------------------------------- Adam comparator, loss landscape */
+
+typedef struct {
+  double eta0, decay_T;  /* eta_t = eta0 / (1 + t / decay_T); decay_T <= 0 or inf: constant */
+  double beta1, beta2;   /* moment decays (Kingma and Ba: 0.9, 0.999) */
+  double epsilon;        /* denominator guard (1e-8) */
+  int64_t step_index;    /* t = 0, 1, ...: Philox step counter, bias corrections use t + 1 */
+  uint64_t seed;         /* Philox key */
+  int64_t n_samples;     /* Ns <= the ctx's max_samples */
+} nqs_adam_hparams;
+
+/* One Adam iteration, the first-order baseline the paper compares minSR
+ * with (Sec. II.C, Tab. I's Adam column): samples, local energies, E, O,
+ * centring as in nqs_minsr_step, the sampled energy gradient
+ * g = Obar'^T eps-bar' (= 2 Re mean (O - <O>)^* (E_loc - E), Eq.
+ * real-valued), then m1 <- b1 m1 + (1 - b1) g, m2 <- b2 m2 + (1 - b2) g^2,
+ * theta <- theta - eta_t (m1 / (1 - b1^(t+1))) / (sqrt(m2 / (1 - b2^(t+1)))
+ * + epsilon).  theta, m1, m2: device FP64 [Np], updated in place unless a
+ * device-side check fails (dev_stats.status; E, Var in dev_stats, eta_t in
+ * eta_eff).  grad: optional device FP64 [Np] copy of g. */
+nqs_status nqs_adam_step(nqs_ctx *ctx, double *theta, double *m1, double *m2,
+                         const nqs_adam_hparams *hp, nqs_step_stats *dev_stats, double *grad,
+                         void *stream);
+
+/* Energies of the loss landscape (Sec. IV): for every point i of xy (host
+ * FP64 [npts][2] = (x, y)), E(theta0 + x v1 + y v2) from ns samples drawn at
+ * Philox step 0 with key seed (every point shares the random numbers).
+ * theta0, v1, v2: device FP64 [Np].  out: device FP64 [npts][4] = (Re E,
+ * Im E, Var, status).  Launches 8-9 kernels per point. */
+nqs_status nqs_energy_scan(nqs_ctx *ctx, const double *theta0, const double *v1,
+                           const double *v2, const double *xy, int64_t npts, int64_t ns,
+                           uint64_t seed, double *out, void *stream);
+
+/* Test of the failure detection of the bounded waits (no counterpart in
+ * the paper).  For 2D lattices of hidden size 96 / 128 in the mixed
+ * context, whose local energies run on the streamed tensor-core engine:
+ * spin_limit > 0 sets the polls of every bounded wait of that engine (0:
+ * the default, about half a second); drop_tile != 0 makes its tile
+ * producer never publish the first tile, so that every other role's wait
+ * for it runs out: the engine then ends its loops, drains its MMAs, frees
+ * its tensor memory and returns, and the step reports NQS_ERR_TIMEOUT in
+ * dev_stats.status and leaves theta and momentum unchanged.  Drops the
+ * context's captured graph; (0, 0) restores normal operation. */
+nqs_status nqs_test_wait_timeout(nqs_ctx *ctx, uint64_t spin_limit, int drop_tile);
+
 /* ------------------------------------------------ sample-sharded step */
 
 /* One minSR step (Algorithm 1) with the Ns samples split over G ranks, one

@@ -30,6 +30,11 @@ struct Eloc2dTcArgs {
                           // (op_f[4 i + 3] = the operator of rank i, longest suffix first)
   const unsigned char *wimg;  // streamed engine: its weight image (eloc2d_tcs_image_bytes),
                               // written from pack by eloc2d_tcs_run before the engine runs
+  // streamed engine, tests of failure detection: polls per bounded wait
+  // (0: the default, about half a second) and, if set, a producer that never
+  // publishes the first tile, so that every consumer's wait runs out
+  unsigned long long spin_limit;
+  int test_drop_tile;
 };
 
 constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)

@@ -124,8 +124,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 // Bounded wait that also gives up once another role of the CTA has aborted;
 // running out sets the abort flag.
-__device__ __forceinline__ bool wait_ab(uint32_t bar, uint32_t parity, volatile int *abort) {
-  for (unsigned long long it = 0; it < SPIN_LIMIT; ++it) {
+__device__ __forceinline__ bool wait_ab(uint32_t bar, uint32_t parity, volatile int *abort,
+                                        unsigned long long limit = SPIN_LIMIT) {
+  for (unsigned long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int N = a.N, Lx = a.Lx;
+  const unsigned long long lim = a.spin_limit ? a.spin_limit : SPIN_LIMIT;
 
   if (warp == C::NCW + 1) {
     // ------------------------------------------------------------ producer
@@ -222,9 +224,10 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       uint32_t q = 0;  // stages issued so far
       for (int it = 0;; ++it) {
         const int slot = it & 1;
-        if (it >= 2 && !wait_ab(bar(C::B_TE + slot), ((it >> 1) - 1) & 1, s_abort)) break;
+        if (it >= 2 && !wait_ab(bar(C::B_TE + slot), ((it >> 1) - 1) & 1, s_abort, lim)) break;
         const int tile = *s_abort ? a.ntiles : atomicAdd(a.tile_ctr, 1);
         s_tile[slot] = tile;
+        if (a.test_drop_tile && it == 0) break;  // (test) the first tile is never published
         mbar_arrive(bar(C::B_TF + slot));
         if (tile >= a.ntiles) break;
         int F, S;
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           const int len = f < F ? C::NS1 : C::NS1 + C::NS2;
           for (int si = 0; si < len; ++si, ++q) {
             const uint32_t sl = q % C::NSLOT, round = q / C::NSLOT;
-            if (round > 0 && !wait_ab(bar(C::B_EMPTY + sl), (round - 1) & 1, s_abort)) {
+            if (round > 0 && !wait_ab(bar(C::B_EMPTY + sl), (round - 1) & 1, s_abort, lim)) {
               stop = true;
               break;
             }
@@ -263,20 +266,20 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       bool stop = false;
       for (int it = 0; !stop; ++it) {
         const int slot = it & 1;
-        if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort)) break;
+        if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort, lim)) break;
         const int tile = s_tile[slot];
         if (tile >= a.ntiles) break;
         int F, S;
         tile_sched(a, tile, F, S);
         for (int f = 0; f < F + S && !stop; ++f) {
           for (int prod = 0; prod < (f < F ? 1 : 2) && !stop; ++prod) {
-            if (!wait_ab(bar(C::B_A), pa & 1, s_abort)) { stop = true; break; }
+            if (!wait_ab(bar(C::B_A), pa & 1, s_abort, lim)) { stop = true; break; }
             ++pa;
             tc_fence_after();
             const int nst = prod == 0 ? C::NS1 : C::NS2;
             for (int si = 0; si < nst; ++si, ++q) {
               const uint32_t sl = q % C::NSLOT;
-              if (!wait_ab(bar(C::B_FULL + sl), (q / C::NSLOT) & 1, s_abort)) { stop = true; break; }
+              if (!wait_ab(bar(C::B_FULL + sl), (q / C::NSLOT) & 1, s_abort, lim)) { stop = true; break; }
               tc_fence_after();
               const int at = (si >> 1) % C::NA, plane = si & 1, chunk = si / (2 * C::NA);
               const uint64_t bd = sw128_desc(smem_u32(ring + sl * C::SLOT));
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
     };
     for (int it = 0; ok; ++it) {
       const int slot = it & 1;
-      if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort)) { ok = false; break; }
+      if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort, lim)) { ok = false; break; }
       const int tile = s_tile[slot];
       if (tile >= a.ntiles) break;
       const int rk = tile / a.tiles_per_op;
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         const int f = j0 == 0 ? fi : (fi < Lx - m0 ? (j0 - 1) * Lx + fi : kst - m0 + fi - (Lx - m0));
         cached_planes(f);
         arrive_a();
-        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort)) { ok = false; break; }
+        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort, lim)) { ok = false; break; }
         ++pd1;
         tc_fence_after();
         store_y(colof(f));
@@ -476,10 +479,10 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         // the previous site's row work overlaps the first product (the other
         // parts' head partials are published by their arrival on a)
         if (part == 0 && sgp >= 0) {
-          if (!wait_ab(bar(C::B_A), (na - 1) & 1, s_abort)) { ok = false; break; }
+          if (!wait_ab(bar(C::B_A), (na - 1) & 1, s_abort, lim)) { ok = false; break; }
           row_work();
         }
-        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort)) { ok = false; break; }
+        if (!wait_ab(bar(C::B_D1), pd1 & 1, s_abort, lim)) { ok = false; break; }
         ++pd1;
         tc_fence_after();
         // h' = X [horizontal] + (Y at a row start | U2 h_ver | 0); Y to the
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
         }
         arrive_a();  // A = h'
-        if (!wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort)) { ok = false; break; }
+        if (!wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort, lim)) { ok = false; break; }
         tc_fence_after();
         // GRU cell (App. A) on this thread's units, 8 at a time; h_k overwrites
         // h' in registers and goes to the planes once every chunk is done
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           }
         }
         if (chunk != C::NCH - 1 &&
-            !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort)) { ok = false; break; }
+            !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort, lim)) { ok = false; break; }
         ++pd2;
 #pragma unroll
         for (int g8 = 0; g8 < 4; ++g8) planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
@@ -551,7 +554,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       // the last site's row work, then the row's contribution
       tc_fence_before();
       mbar_arrive(bar(C::B_Z));
-      if (!wait_ab(bar(C::B_Z), pz & 1, s_abort)) { ok = false; break; }
+      if (!wait_ab(bar(C::B_Z), pz & 1, s_abort, lim)) { ok = false; break; }
       ++pz;
       if (part == 0) {
         if (sgp >= 0) row_work();

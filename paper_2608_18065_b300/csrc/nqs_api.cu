@@ -53,6 +53,10 @@ struct nqs_ctx {
   int ck = 0, nck = 0, nseg = 1;
   // Levenberg-Marquardt damping factor (0: off); the damping lives on the device
   double lm_omega = 0.0;
+  // tests of failure detection (nqs_test_wait_timeout): wait limit of the
+  // streamed local-energy engine and its dropped tile
+  unsigned long long test_spin_limit = 0;
+  int test_drop_tile = 0;
   WsOff off{};
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -368,6 +372,8 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.err = W<int>(c, c->off.sstat);
       e.tile_ctr = W<int>(c, c->off.tctr);
       e.wimg = reinterpret_cast<const unsigned char *>(c->ws + c->off.wimg);
+      e.spin_limit = c->test_spin_limit;
+      e.test_drop_tile = c->test_drop_tile;
       c->launches += 1;
       CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
       CU(eloc2d_tcs_run(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
@@ -1414,6 +1420,14 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   return NQS_OK;
 }
 
+nqs_status nqs_test_wait_timeout(nqs_ctx *c, uint64_t spin_limit, int drop_tile) {
+  if (!c) return NQS_ERR_ARG;
+  c->test_spin_limit = spin_limit;
+  c->test_drop_tile = drop_tile ? 1 : 0;
+  drop_graph(c);
+  return NQS_OK;
+}
+
 nqs_status nqs_set_damping(nqs_ctx *c, double omega, double lambda0) {
   if (!c || !(omega == omega) || !(lambda0 == lambda0)) return NQS_ERR_ARG;
   if (omega > 1.0) {
@@ -1531,6 +1545,107 @@ nqs_status shard_solve_T(nqs_ctx *c, const void *A, int64_t R, const double *eps
   return cu(cudaGetLastError());
 }
 
+// ------------------------------------------------------------ Adam, scan
+// Sampling, local energies, E, Var and eps-bar' of theta (into the step's
+// workspace regions); the first stages of Algorithm 1.
+template <typename T>
+nqs_status forward_energy_T(nqs_ctx *c, const double *theta, int64_t ns, uint64_t seed,
+                            int64_t step, nqs_step_stats *stats, bool want_gates, cudaStream_t st) {
+  uint8_t *spins = W<uint8_t>(c, c->off.spins);
+  double *eloc = W<double>(c, c->off.eloc);
+  c->cur_ns = ns;
+  k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), step);
+  c->launches += 1;
+  ST(pack_theta<T>(c, theta, st));
+  {
+    FwdArgs<T> a = fwd_args<T>(c);
+    a.nrows = ns; a.seed = seed; a.step = (uint64_t)step;
+    a.step_dev = W<int64_t>(c, c->off.dstep);
+    a.spins = spins; a.logpsi = W<double>(c, c->off.logpsi);
+    if (want_gates && c->ck == 0) {
+      a.gcache = W<T>(c, c->off.gcache);
+      a.gw = c->gw;
+    }
+    c->launches += 1;
+    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+  }
+  ST(eloc_T<T>(c, ns, spins, eloc, st));
+  k_energy<<<1, 1024, 0, st>>>(eloc, ns, c->L.N, c->L.cplx, stats, W<double>(c, c->off.eps));
+  c->launches += 1;
+  return cu(cudaGetLastError());
+}
+
+template <typename T>
+nqs_status adam_T(nqs_ctx *c, double *theta, double *m1, double *m2, const nqs_adam_hparams *ap,
+                  nqs_step_stats *stats, double *grad_out, cudaStream_t st) {
+  const int64_t ns = ap->n_samples, np = c->L.np;
+  const int64_t R = c->L.cplx ? 2 * ns : ns;
+  T *O = W<T>(c, c->off.O);
+  double *eps = W<double>(c, c->off.eps);
+  double *g = W<double>(c, c->off.dth);
+  CU(cudaMemsetAsync(W<int32_t>(c, c->off.sstat), 0, 64, st));
+  ST(forward_energy_T<T>(c, theta, ns, ap->seed, ap->step_index, stats, true, st));
+  ST(jac_T<T>(c, ns, W<uint8_t>(c, c->off.spins), O, st));
+  // centring as in the step: FP64 means, O' = (O - mean) / sqrt(Ns); the
+  // tensor-core route of the mixed path keeps O' as the split planes
+  const bool tc = f32(c) && gram_tc_available();
+  {
+    c->launches += 3;
+    const int chunks = (int)((ns + COL_ROWS - 1) / COL_ROWS);
+    const unsigned nblk = c->L.cplx ? 2u : 1u;
+    dim3 gg((unsigned)((np + 255) / 256), nblk * chunks);
+    k_colsum_part<T><<<gg, 256, 0, st>>>(O, ns, np, chunks, W<double>(c, c->off.part));
+    k_colmean_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
+        W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean), tc ? 1 : 0);
+    CU(cudaGetLastError());
+    if (tc) {
+      CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<float2>(c, c->off.mean),
+                      c->ws + c->off.split, st));
+    } else {
+      const int64_t tot = R * np;
+      const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+      k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
+      CU(cudaGetLastError());
+    }
+  }
+  // g = Obar'^T eps-bar', then the Adam update
+  {
+    const int rows_per = 64;
+    const int nparts = (int)((R + rows_per - 1) / rows_per);
+    dim3 gg((unsigned)((np + 255) / 256), (unsigned)nparts);
+    if (tc)
+      CU(gemv_split(c->ws + c->off.split, R, np, eps, rows_per, W<double>(c, c->off.part), st));
+    else
+      k_gemv_part<T><<<gg, 256, 0, st>>>(O, R, np, eps, rows_per, W<double>(c, c->off.part));
+    k_grad_sum<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(W<double>(c, c->off.part), nparts,
+                                                            np, stats, g);
+    k_adam<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(theta, m1, m2, g, np, ap->beta1,
+                                                        ap->beta2, ap->epsilon, ap->eta0,
+                                                        ap->decay_T, ap->step_index, stats);
+    c->launches += 3;
+    CU(cudaGetLastError());
+  }
+  if (grad_out) CU(cudaMemcpyAsync(grad_out, g, np * 8, cudaMemcpyDeviceToDevice, st));
+  return NQS_OK;
+}
+
+template <typename T>
+nqs_status scan_T(nqs_ctx *c, const double *theta0, const double *v1, const double *v2,
+                  const double *xy, int64_t npts, int64_t ns, uint64_t seed, double *out,
+                  cudaStream_t st) {
+  const int64_t np = c->L.np;
+  double *th = W<double>(c, c->off.tth);
+  nqs_step_stats *sst = reinterpret_cast<nqs_step_stats *>(W<double>(c, c->off.tstats));
+  for (int64_t i = 0; i < npts; ++i) {
+    k_axpy2<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(theta0, v1, v2, xy[2 * i], xy[2 * i + 1],
+                                                          np, th);
+    ST(forward_energy_T<T>(c, th, ns, seed, 0, sst, false, st));
+    k_scan_store<<<1, 1, 0, st>>>(sst, out + 4 * i);
+    c->launches += 2;
+  }
+  return cu(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
@@ -1582,6 +1697,33 @@ nqs_status nqs_shard_apply(nqs_ctx *c, double *theta, double *mom, const double 
   k_apply<<<blocks, 256, 0, st>>>(theta, mom, dtheta, np, hp->mu, dev_stats);
   c->launches += 2;
   return cu(cudaGetLastError());
+}
+
+nqs_status nqs_adam_step(nqs_ctx *c, double *theta, double *m1, double *m2,
+                         const nqs_adam_hparams *ap, nqs_step_stats *dev_stats, double *grad,
+                         void *stream) {
+  if (!c || !theta || !m1 || !m2 || !ap || !dev_stats) return NQS_ERR_ARG;
+  if (ap->n_samples < 2 || ap->n_samples > c->max_ns || ap->step_index < 0) return NQS_ERR_ARG;
+  if (!(ap->beta1 >= 0.0 && ap->beta1 < 1.0 && ap->beta2 >= 0.0 && ap->beta2 < 1.0 &&
+        ap->epsilon > 0.0))
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  c->gnext = -1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? adam_T<float>(c, theta, m1, m2, ap, dev_stats, grad, st)
+                : adam_T<double>(c, theta, m1, m2, ap, dev_stats, grad, st);
+}
+
+nqs_status nqs_energy_scan(nqs_ctx *c, const double *theta0, const double *v1, const double *v2,
+                           const double *xy, int64_t npts, int64_t ns, uint64_t seed,
+                           double *out, void *stream) {
+  if (!c || !theta0 || !v1 || !v2 || !xy || !out || npts < 0 || ns < 1 || ns > c->max_ns)
+    return NQS_ERR_ARG;
+  ST(need_ws(c));
+  c->gnext = -1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f32(c) ? scan_T<float>(c, theta0, v1, v2, xy, npts, ns, seed, out, st)
+                : scan_T<double>(c, theta0, v1, v2, xy, npts, ns, seed, out, st);
 }
 
 }  // extern "C"

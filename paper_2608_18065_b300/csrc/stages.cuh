@@ -423,6 +423,52 @@ __global__ void k_check_finite(const double *__restrict__ v, int64_t n, nqs_step
       atomicCAS(reinterpret_cast<int *>(&st->status), (int)NQS_OK, (int)NQS_ERR_NONFINITE);
 }
 
+// ------------------------------------------------------------- Adam
+// g = sum of the partial products Obar'^T eps-bar' (the sampled energy
+// gradient); a non-finite entry flags the step.
+__global__ void k_grad_sum(const double *__restrict__ part, int nparts, int64_t np,
+                           nqs_step_stats *st, double *g) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double acc = 0.0;
+  for (int c = 0; c < nparts; ++c) acc += part[(int64_t)c * np + p];
+  g[p] = acc;
+  if (!isfinite(acc)) atomicCAS(reinterpret_cast<int *>(&st->status), (int)NQS_OK, (int)NQS_ERR_NONFINITE);
+}
+
+// Adam (Kingma and Ba) with bias corrections of iteration t = step + 1 and
+// eta_t = eta0 / (1 + step / T); only when the step's status is OK.
+__global__ void k_adam(double *theta, double *m, double *v, const double *__restrict__ g,
+                       int64_t np, double b1, double b2, double eps, double eta0, double decay_T,
+                       int64_t step, nqs_step_stats *st) {
+  if (st->status != NQS_OK) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const double t = (double)(step + 1);
+  const double eta = (decay_T > 0.0 && isfinite(decay_T)) ? eta0 / (1.0 + (double)step / decay_T)
+                                                           : eta0;
+  const double gp = g[p];
+  const double mp = b1 * m[p] + (1.0 - b1) * gp, vp = b2 * v[p] + (1.0 - b2) * gp * gp;
+  m[p] = mp;
+  v[p] = vp;
+  const double mh = mp / (1.0 - pow(b1, t)), vh = vp / (1.0 - pow(b2, t));
+  theta[p] -= eta * mh / (sqrt(vh) + eps);
+  if (p == 0) st->eta_eff = eta;
+}
+
+// theta0 + x v1 + y v2 (a point of the loss landscape)
+__global__ void k_axpy2(const double *__restrict__ t0, const double *__restrict__ v1,
+                        const double *__restrict__ v2, double x, double y, int64_t n,
+                        double *out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) out[p] = t0[p] + x * v1[p] + y * v2[p];
+}
+
+// E (re, im), Var and the status of a landscape point
+__global__ void k_scan_store(const nqs_step_stats *st, double *out) {
+  out[0] = st->E_re; out[1] = st->E_im; out[2] = st->var; out[3] = (double)st->status;
+}
+
 // m <- mu m + (1-mu) dtheta; theta <- theta - m (App. B), only when the
 // step's status is OK.
 __global__ void k_apply(double *theta, double *mom, const double *__restrict__ dth, int64_t np,

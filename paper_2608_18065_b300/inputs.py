@@ -108,6 +108,27 @@ TAB1 = {
 }
 
 
+# Tab. I, Adam column: (eta0, decay time); T = inf keeps eta constant.  The
+# moment decays and epsilon are not given in the paper: Kingma and Ba's.
+TAB1_ADAM = {
+    "tfim": dict(eta0=5e-3, decay_T=float("inf")),
+    "cluster": dict(eta0=5e-4, decay_T=float("inf")),
+    "heisenberg": dict(eta0=5e-4, decay_T=1e4),
+    "j1j2": dict(eta0=3e-3, decay_T=5e3),
+}
+
+
+@dataclass
+class AdamParams:
+    eta0: float
+    decay_T: float = float("inf")
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    seed: int = 42
+    ns: int = 128
+
+
 @dataclass
 class Workload:
     name: str

@@ -65,9 +65,16 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_graph_active", "nqs_batch_set_concurrency", "nqs_batch_get_concurrency",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
-           "nqs_shard_solve", "nqs_shard_apply",
+           "nqs_shard_solve", "nqs_shard_apply", "nqs_test_wait_timeout", "nqs_adam_step",
+           "nqs_energy_scan",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
+
+
+class AdamHParams(C.Structure):
+    _fields_ = [("eta0", C.c_double), ("decay_T", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("epsilon", C.c_double), ("step_index", C.c_int64),
+                ("seed", C.c_uint64), ("n_samples", C.c_int64)]
 
 
 class SpectrumStats(C.Structure):
@@ -290,6 +297,33 @@ class Context:
         hps = step_hparams(hp, step_index)
         _check(lib().nqs_shard_apply(self._h, _ptr(theta), _ptr(mom), _ptr(dtheta),
                                      C.byref(hps), _ptr(stats), _stream(stream)))
+
+    def adam_step(self, theta, m1, m2, ap, step_index, stats=None, grad=None, stream=None):
+        """One Adam iteration (Sec. II.C baseline) in place on theta, m1, m2."""
+        if stats is None:
+            stats = self.new_stats()
+        a = AdamHParams(ap.eta0, ap.decay_T, ap.beta1, ap.beta2, ap.eps, step_index, ap.seed,
+                        ap.ns)
+        _check(lib().nqs_adam_step(self._h, _ptr(theta), _ptr(m1), _ptr(m2), C.byref(a),
+                                   _ptr(stats), _ptr(grad), _stream(stream)))
+        return stats
+
+    def energy_scan(self, theta0, v1, v2, xy, ns, seed, stream=None):
+        """E(theta0 + x v1 + y v2) for the host (x, y) pairs xy [n, 2] (Sec. IV);
+        returns a device [n, 4] tensor (Re E, Im E, Var, status)."""
+        import numpy as np
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = torch.empty((len(xy), 4), dtype=torch.float64, device=self.device)
+        _check(lib().nqs_energy_scan(self._h, _ptr(theta0), _ptr(v1), _ptr(v2),
+                                     xy.ctypes.data_as(C.c_void_p), C.c_int64(len(xy)),
+                                     C.c_int64(ns), C.c_uint64(seed), _ptr(out),
+                                     _stream(stream)))
+        return out
+
+    def test_wait_timeout(self, spin_limit=0, drop_tile=False):
+        """Failure-detection test hook of the streamed 2D local-energy engine
+        (see nqs_test_wait_timeout); (0, False) restores normal operation."""
+        _check(lib().nqs_test_wait_timeout(self._h, C.c_uint64(spin_limit), int(drop_tile)))
 
     def set_damping(self, omega, lambda0):
         """Levenberg-Marquardt damping (App. G): omega > 1 on, else off."""
