@@ -431,7 +431,7 @@ def run_reference(args):
         unit = "batched steps/s"
         nsub = [min(w.hp.ns, max(4, O.num_threads())) for w in insts]
     else:
-        w = workloads()[args.workload]
+        w = resolve_workload(args.workload)
         insts = [w]
         cfg = workload_config(args, w=w)
         unit = UNIT
@@ -499,6 +499,18 @@ def cpu_baseline_leg(insts, unit, budget_s=20.0):
 
 
 # -------------------------------------------------------------------- ours
+def resolve_workload(name):
+    """A single-instance workload: a key of inputs.workloads(), or
+    b16:<instance name> for one of the batched instances."""
+    from paper_2608_18065_b300.inputs import batched_instances, workloads
+    if name.startswith("b16:"):
+        for w in batched_instances():
+            if w.name == name[4:]:
+                return w
+        raise SystemExit(f"no batched instance named {name[4:]}")
+    return workloads()[name]
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -511,7 +523,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workloads()[args.workload]
+    w = resolve_workload(args.workload)
     hp = w.hp
     K, Wu = args.steps, args.warmup
 
