@@ -26,8 +26,9 @@
 // puts U2 h of those states into the column buffer.  K is padded to two 64-wide atoms; the
 // padded k-steps are not issued.
 //
-// Warp roles: 4 d_h / 32 compute warps (thread (quarter q, part p) owns row
-// 32 q + lane, its tensor-memory lane, and units 32 p .. 32 p + 31), one MMA
+// Warp roles: 4 d_h / UT compute warps (thread (quarter q, part p) owns row
+// 32 q + lane, its tensor-memory lane, and units UT p .. UT p + UT - 1; UT =
+// 64 at d_h = 128, 32 at 96, so that no register spills), one MMA
 // warp (one thread issues every tcgen05.mma and commit) and one producer warp
 // (one thread hands out tiles and streams the weight stages).  The producer
 // takes tiles from the launch's counter, longest suffixes first, and
@@ -48,7 +49,8 @@ namespace {
 template <int DH>
 struct Tcs {
   static constexpr int TR = ELOC2D_TC_ROWS;         // rows per tile (the MMA's M)
-  static constexpr int P = DH / 32;                 // unit parts per row
+  static constexpr int UT = DH == 128 ? 64 : 32;    // hidden units per compute thread
+  static constexpr int P = DH / UT;                 // unit parts per row
   static constexpr int NCW = 4 * P;                 // compute warps
   static constexpr int NCT = 32 * NCW;              // compute threads
   static constexpr int THREADS = NCT + 64;          // + MMA warp + producer warp
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
   } else {
     // ------------------------------------------------------ compute warps
     const int quarter = warp & 3, part = warp >> 2;
-    const int row = 32 * quarter + lane, u0 = 32 * part;
+    constexpr int UT = C::UT, G8 = UT / 8;
+    const int row = 32 * quarter + lane, u0 = UT * part;
     const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
     const int chunk = u0 / C::CU, uo = u0 - chunk * C::CU;
     const uint32_t gcol = lanes + (uint32_t)(chunk * C::N2 + uo);  // gate j at + CU j
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       auto cached_planes = [&](int k) {
         const float4 *src = reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH);
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
+        for (int g8 = 0; g8 < G8; ++g8) {
           float h8[8];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       // column buffer at lattice column col
       auto store_y = [&](int col) {
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
+        for (int g8 = 0; g8 < G8; ++g8) {
           float y[8];
           tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
           tmem_wait_ld();
@@ -454,12 +457,12 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         const int d0 = hor ? s_prev : 2, d1 = ver >= 0 ? s_ver : 2;
         arrive_a();  // A = h_{k-1}
         // the vertical term from the column buffer (in flight during the product)
-        float hp[32];
+        float hp[UT];
         const bool vbuf = valid && ver >= 0 && ver != k - 1;
         {
           const float4 *src = reinterpret_cast<const float4 *>(cb + col * DH);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < UT / 4; ++q) {
             const float4 v = vbuf ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
             hp[4 * q] = v.x; hp[4 * q + 1] = v.y; hp[4 * q + 2] = v.z; hp[4 * q + 3] = v.w;
           }
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         // h' = X [horizontal] + (Y at a row start | U2 h_ver | 0); Y to the
         // buffer; h' to the planes, 8 units at a time
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
+        for (int g8 = 0; g8 < G8; ++g8) {
           float x[8], y[8];
           tmem_ld8(lanes + (uint32_t)(u0 + 8 * g8), x);
           tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
@@ -513,7 +516,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         const float *tb = tab + (d0 * 3 + d1) * C::TS + u0;
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
+        for (int g8 = 0; g8 < G8; ++g8) {
           float gu[8], gr[8], gg[8];
           tmem_ld8(gcol + (uint32_t)(8 * g8), gu);
           tmem_ld8(gcol + (uint32_t)(C::CU + 8 * g8), gr);
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
             !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort, lim)) { ok = false; break; }
         ++pd2;
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
+        for (int g8 = 0; g8 < G8; ++g8) planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
         if (part > 0) {
           zx[(part - 1) * C::TR + row] = make_float4(z0, z1, z2, z3);
         } else {

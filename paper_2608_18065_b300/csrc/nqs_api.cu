@@ -233,8 +233,10 @@ int eloc_grid_cap(const nqs_ctx *c, int dflt) {
   return tuned(c) && c->t_eloc_grid > 0 ? std::min(c->t_eloc_grid, dflt) : dflt;
 }
 int gram_splits(const nqs_ctx *c) { return tuned(c) ? c->t_gram_splits : 0; }
+// grid of the cooperative solve: the tuned value (at most two CTAs per SM,
+// which the launch checks against the kernel's occupancy), else one per SM
 int solve_grid(const nqs_ctx *c) {
-  return tuned(c) && c->t_solve_grid > 0 ? std::min(c->t_solve_grid, c->rd.sm_count)
+  return tuned(c) && c->t_solve_grid > 0 ? std::min(c->t_solve_grid, 2 * c->rd.sm_count)
                                          : c->rd.sm_count;
 }
 
@@ -664,9 +666,14 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     const bool wt = tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var == 1 : false;
     const void *kern = wt ? (const void *)k_chol_ir<true> : (const void *)k_chol_ir<false>;
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a grid above one CTA per SM only where the occupancy allows it: every
+    // CTA of the cooperative launch must be resident at once
+    int per = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, IR_THREADS, smem));
+    const int Gi = std::min(G, std::max(per, 1) * c->rd.sm_count);
     void *args[] = {&ir};
     c->launches += 1;
-    CU(cudaLaunchCooperativeKernel(kern, dim3(G), dim3(IR_THREADS), args, smem, st));
+    CU(cudaLaunchCooperativeKernel(kern, dim3(Gi), dim3(IR_THREADS), args, smem, st));
   } else {
     k_set_i32<<<1, 1, 0, st>>>(need, 1);
     c->launches += 1;
@@ -685,9 +692,11 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
   int per = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop, CC_THREADS, smem));
   if (per < 1) return NQS_ERR_UNSUPPORTED;
+  // one CTA per SM at most: its partial sums are sized for that grid
+  const int Gc = std::min(G, c->rd.sm_count);
   void *args[] = {&a};
   c->launches += 1;
-  CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
+  CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(Gc), dim3(CC_THREADS), args, smem, st));
   if (retry && f32(c) && gram_tc_available()) {
     // T from the tensor cores can miss positive definiteness by its rounding
     // when lambda is tiny against ||T||: then rebuild T in FP64 from the same
@@ -707,7 +716,7 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     CU(cudaMemsetAsync(bar, 0, 4, st));
     a.gate = rflag;
     c->launches += 5;
-    CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(G), dim3(CC_THREADS), args, smem, st));
+    CU(cudaLaunchCooperativeKernel((void *)k_chol_coop, dim3(Gc), dim3(CC_THREADS), args, smem, st));
   }
   mark(c, 12, st);
   return NQS_OK;
@@ -1336,8 +1345,7 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
       }
     c->t_chol_var = pvar;
     c->t_chol_subst = psub;
-    for (int d : {2, 4, 8}) {
-      const int g = G0 / d;
+    for (int g : {2 * G0, G0 / 2, G0 / 4, G0 / 8}) {
       if (g < 1) continue;
       c->t_solve_grid = g;
       double ms = 0;
