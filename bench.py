@@ -63,6 +63,12 @@ def parse():
     p.add_argument("--spectrum-steps", type=int, default=64,
                    help="Lanczos steps of the conditioning diagnostics")
     p.add_argument("--no-graph", action="store_true", help="launch every kernel eagerly")
+    p.add_argument("--train-steps", type=int, default=10000,
+                   help="train:<workload>: minSR steps of the training run")
+    p.add_argument("--train-eta0", type=float, default=None,
+                   help="train:<workload>: eta0 instead of Tab. I's")
+    p.add_argument("--train-window", type=int, default=300,
+                   help="train:<workload>: steps averaged at the end (the paper's window)")
     return p.parse_args()
 
 
@@ -1067,6 +1073,8 @@ def reference_energy(w):
         return -float(np.sum(np.linalg.svd(B, compute_uv=False)))
     if w.ham.family == "cluster_zxz":
         return -float(w.model.N - 2)
+    if w.ham.family == "cluster_paper":
+        return -float(w.model.N)
     return None
 
 
@@ -1307,8 +1315,63 @@ def run_qgt_subsample(args):
     return 0
 
 
+# Tab. II: final minSR energies per site and the reference energies per site
+TAB2 = {"tfim": (-1.2714254, -1.27142590795), "cluster_paper": (-0.999947, -1.0),
+        "heisenberg": (-0.628486, -0.628656), "j1j2": (-0.48514, -0.48654)}
+
+
+def run_train(args):
+    """A training run of one workload (train:<key>): --train-steps minSR steps
+    from theta_0 with graphs, E/N averaged over the last --train-window
+    steps against Tab. II's minSR result and reference energy."""
+    import copy
+    import torch
+    from paper_2608_18065_b300 import nqs
+    from paper_2608_18065_b300.inputs import init_theta
+    w = resolve_workload(args.workload[6:])
+    hp = copy.copy(w.hp)
+    if args.train_eta0 is not None:
+        hp.eta0 = args.train_eta0
+    dev = torch.device("cuda", 0)
+    c = nqs.Context(w.model, w.ham, w.precision, hp.ns, device=dev)
+    c.use_graph(True)
+    th = torch.tensor(init_theta(w.model, w.theta_seed), device=dev)
+    m = torch.zeros_like(th)
+    K = args.train_steps
+    stats = torch.zeros((K, 11), dtype=torch.float64, device=dev)
+    one = c.new_stats()
+    t0 = time.perf_counter()
+    for t in range(K):
+        c.minsr_step(th, m, hp, t, one)
+        stats[t].copy_(one)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    st = stats.cpu().numpy()
+    status = st[:, 8:9].copy().view(np.int32)[:, 0]
+    E = st[:, 0] / w.model.N
+    win = min(args.train_window, K)
+    key = ("heisenberg" if w.ham.J2 == 0.0 else "j1j2") if w.ham.family == "j1j2" else w.ham.family
+    E_ref = reference_energy(w)
+    line = {"metric": "minSR training run (E per site after K steps)", "workload": w.name,
+            "steps": K, "eta0": hp.eta0, "seconds": secs, "steps_per_s": K / secs,
+            "E_per_site_last_window": float(E[-win:].mean()),
+            "stderr": float(E[-win:].std(ddof=1) / np.sqrt(win)) if win > 1 else None,
+            "window": win, "rejected_steps": int(np.sum(status != 0)),
+            "E_exact_per_site": E_ref / w.model.N if E_ref is not None else None,
+            "tab2_minsr_per_site": TAB2.get(key, (None, None))[0],
+            "tab2_reference_per_site": TAB2.get(key, (None, None))[1],
+            "trajectory_every_10pct": [float(E[min(K - 1, i * K // 10)]) for i in range(11)]}
+    ref = line["E_exact_per_site"] or line["tab2_reference_per_site"]
+    if ref:
+        line["rel_err_last_window"] = (line["E_per_site_last_window"] - ref) / abs(ref)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload.startswith("train:"):
+        return run_train(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched16":

@@ -43,7 +43,7 @@ template <int DH, int DIM> struct Adj {
 
 // Unit groups of the reverse sweep: two units per thread at dh >= 64.
 template <int DH> struct BTile {
-  static constexpr int UG = DH >= 32 ? 32 : DH;
+  static constexpr int UG = DH == 200 ? 8 : (DH >= 32 ? 32 : DH);
   static constexpr int UT = DH / UG;
 };
 
@@ -348,8 +348,12 @@ template <typename T, typename TO> struct GradArgs {
 };
 
 template <int DH> struct GTile {
-  static constexpr int TA = DH >= 16 ? DH / 16 : 1;       // tile edge per thread
-  static constexpr int GT = DH / TA;                       // threads per edge
+  // tile edge per thread, threads per edge (d_h = 200: 10 x 10 threads of
+  // 10 x 10 tiles, 2 x 2 sub-blocks)
+  static constexpr int TA = DH == 200 ? 10 : DH >= 16 ? (DH / 16 < 8 ? DH / 16 : 8) : 1;
+  static constexpr int GT = DH == 200 ? 10 : (DH / TA < 16 ? DH / TA : 16);
+  static constexpr int SB = DH / (GT * TA);  // sub-blocks per edge (one per pass above 128)
+  static_assert(GT * TA * SB == DH, "tiles cover the block");
 };
 
 // Sites per shared-memory chunk of k_jac_grad: static shared memory <= ~45 KB.
@@ -360,13 +364,14 @@ template <typename T, int DH, int DIM> __host__ __device__ constexpr int grad_kc
 
 template <typename T, typename TO, int DH, int DIM>
 __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
-  constexpr int TA = GTile<DH>::TA, GT = GTile<DH>::GT;
+  constexpr int TA = GTile<DH>::TA, GT = GTile<DH>::GT, SB = GTile<DH>::SB;
   constexpr int KC = grad_kc<T, DH, DIM>();
   constexpr int DIN = DIM == 2 ? 4 : 2;
   constexpr int NB = DIM == 2 ? 5 : 3;  // big blocks: Wu_h Wr_h Wh (U1 U2)
   // above dh = 64 the big blocks are accumulated one per pass (registers)
   constexpr int BPP = TA <= 4 ? NB : 1;
-  constexpr int NPASS = (NB + BPP - 1) / BPP;
+  // passes: groups of BPP big blocks, each block in SB x SB sub-blocks
+  constexpr int NPASS = ((NB + BPP - 1) / BPP) * SB * SB;
   using AJ = Adj<DH, DIM>;
   const int row = blockIdx.x;
   const int64_t s = row % A.ns;
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
   const bool big = tid < GT * GT;
   constexpr int NA = (KC * AJ::W + 255) / 256;   // adjoint values per thread and chunk
   constexpr int NH = (KC * DH + 255) / 256;      // state values per thread and chunk
-  const int ta = (tid / GT) * TA, tb = (tid % GT) * TA;
+  const int ta0 = (tid / GT) * TA, tb0 = (tid % GT) * TA;
   // small entries: heads (4 dh), x-columns (3 dh din), biases (4 dh + 4)
   const int nsmall = 4 * DH + 3 * DH * DIN + 4 * DH + 4;
   constexpr int SPT = (4 * DH + 3 * DH * DIN + 4 * DH + 4 + 255) / 256;
@@ -400,6 +405,8 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
   // big block qb: 0 Wu_h, 1 Wr_h, 2 Wh (adjoint x h'), 3 U1, 4 U2 (adjoint of h' x h_hor/h_ver)
   auto adj_off = [&](int qb) { return qb == 0 ? 0 : qb == 1 ? DH : qb == 2 ? 2 * DH : AJ::DHP; };
   for (int pass = 0; pass < NPASS; ++pass) {
+    const int pgrp = pass / (SB * SB), psub = pass % (SB * SB);
+    const int ta = ta0 + (psub / SB) * GT * TA, tb = tb0 + (psub % SB) * GT * TA;
     T accB[BPP][TA][TA];
 #pragma unroll
     for (int q = 0; q < BPP; ++q)
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
         for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
           for (int q = 0; q < BPP; ++q) {
-            const int qb = pass * BPP + q;
+            const int qb = pgrp * BPP + q;
             if (qb >= NB) break;
             const T *Qv = qb < 3 ? sQ[kk] : (qb == 3 ? sHh[kk] : sHv[kk]);
             const int po = adj_off(qb);
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(256) k_jac_grad(const GradArgs<T, TO> A) {
     if (big) {
 #pragma unroll
       for (int q = 0; q < BPP; ++q) {
-        const int qb = pass * BPP + q;
+        const int qb = pgrp * BPP + q;
         if (qb >= NB) break;
 #pragma unroll
         for (int i = 0; i < TA; ++i)

@@ -20,9 +20,16 @@ template <typename T> struct Rows {
   static constexpr int BWD_RT = 1, BWD_RG = 8;
 };
 
+// Rows per thread of the local-energy sweep: fewer at hidden size 256 in 2D
+// FP32, where four state buffers of 64 rows would exceed shared memory, and
+// one at 200, where each thread holds 25 units.
+template <typename T> constexpr int eloc_rt(int dim, int dh) {
+  return dh == 200 ? 1  // 25 units per thread
+         : dim == 2 ? (sizeof(T) == 4 && dh >= 256 ? 2 : Rows<T>::ELOC_RT_2D) : Rows<T>::ELOC_RT;
+}
+
 inline int eloc_rows(const RecDesc &d, bool f32) {
-  if (f32) return (d.dim == 2 ? Rows<float>::ELOC_RT_2D : Rows<float>::ELOC_RT) * 16;
-  return (d.dim == 2 ? Rows<double>::ELOC_RT_2D : Rows<double>::ELOC_RT) * 16;
+  return (f32 ? eloc_rt<float>(d.dim, d.dh) : eloc_rt<double>(d.dim, d.dh)) * 16;
 }
 
 // mode: MODE_SAMPLE / MODE_GIVEN / MODE_ELOC.  For MODE_ELOC, a.ntiles must

@@ -2060,6 +2060,7 @@ const char *nqs_status_string(int s) {
 
 namespace nqs {
 bool dh_supported(int dh) {
-  return dh == 8 || dh == 16 || dh == 32 || dh == 64 || dh == 96 || dh == 128;
+  return dh == 8 || dh == 16 || dh == 32 || dh == 64 || dh == 96 || dh == 128 || dh == 200 ||
+         dh == 256;
 }
 }  // namespace nqs

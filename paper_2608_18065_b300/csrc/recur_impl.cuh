@@ -14,6 +14,8 @@ namespace nqs {
     case 64: { constexpr int DH = 64; __VA_ARGS__; } break;  \
     case 96: { constexpr int DH = 96; __VA_ARGS__; } break;  \
     case 128: { constexpr int DH = 128; __VA_ARGS__; } break;  \
+    case 200: { constexpr int DH = 200; __VA_ARGS__; } break;  \
+    case 256: { constexpr int DH = 256; __VA_ARGS__; } break;  \
     default: return cudaErrorInvalidValue;                \
   }
 
@@ -51,7 +53,7 @@ static cudaError_t fwd_one(const RecDesc &d, FwdArgs<T> a, int max_grid, cudaStr
 
 template <typename T, int DH, int DIM>
 static cudaError_t fwd_dim(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, cudaStream_t st) {
-  constexpr int ERT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
+  constexpr int ERT = eloc_rt<T>(DIM, DH);
   if (mode == MODE_SAMPLE)
     return fwd_one<T, DH, DIM, Rows<T>::SAMPLE_RT, Rows<T>::SAMPLE_RG, MODE_SAMPLE,
                    sample_groups<T, DH>()>(d, a, max_grid, st);
@@ -72,7 +74,7 @@ cudaError_t run_forward(const RecDesc &d, int mode, FwdArgs<T> a, int max_grid, 
 
 template <typename T, int DH, int DIM>
 static int eloc_grid_dim(const RecDesc &d) {
-  constexpr int RT = DIM == 2 ? Rows<T>::ELOC_RT_2D : Rows<T>::ELOC_RT;
+  constexpr int RT = eloc_rt<T>(DIM, DH);
   constexpr int RG = Rows<T>::ELOC_RG;
   auto kern = k_forward<T, DH, DIM, RT, RG, MODE_ELOC, true>;
   size_t smem = fwd_smem_bytes<T, DH, DIM, RT * RG>(d.N, true);
@@ -98,6 +100,8 @@ template <typename T> int eloc_max_grid(const RecDesc &d) {
     case 64: return d.dim == 1 ? eloc_grid_dim<T, 64, 1>(d) : eloc_grid_dim<T, 64, 2>(d);
     case 96: return d.dim == 1 ? eloc_grid_dim<T, 96, 1>(d) : eloc_grid_dim<T, 96, 2>(d);
     case 128: return d.dim == 1 ? eloc_grid_dim<T, 128, 1>(d) : eloc_grid_dim<T, 128, 2>(d);
+    case 200: return d.dim == 1 ? eloc_grid_dim<T, 200, 1>(d) : eloc_grid_dim<T, 200, 2>(d);
+    case 256: return d.dim == 1 ? eloc_grid_dim<T, 256, 1>(d) : eloc_grid_dim<T, 256, 2>(d);
   }
   return 0;
 }

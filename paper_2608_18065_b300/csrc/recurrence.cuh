@@ -14,8 +14,9 @@
 namespace nqs {
 
 template <int DH> struct Tile {
-  static constexpr int UG = DH >= 16 ? 16 : DH;  // unit groups (lanes)
-  static constexpr int UT = DH / UG;             // hidden units per thread
+  // unit groups (lanes): a power of two dividing d_h (8 for d_h = 200)
+  static constexpr int UG = DH == 200 ? 8 : DH >= 256 ? 32 : (DH >= 16 ? 16 : DH);
+  static constexpr int UT = DH / UG;  // hidden units per thread
 };
 
 // n consecutive values from shared or global memory, as 16-byte vectors when

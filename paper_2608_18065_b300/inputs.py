@@ -160,6 +160,22 @@ def workloads() -> dict:
     w["tfim200"] = Workload(
         "tfim_N200_dh32_ns100_mixed", ModelSpec(1, 200, 1, 32),
         HamSpec("tfim", J=1.0, h=1.0), HParams(ns=100, **TAB1["tfim"]), "mixed")
+    # the paper's cluster-state configuration (Sec. III.A: XZX form with its
+    # boundary terms, E_0 = -N; Tab. I: d_h = 256, N_s = 100)
+    w["cluster100p"] = Workload(
+        "cluster_paper_N100_dh256_ns100_mixed", ModelSpec(1, 100, 1, 256, cplx=1),
+        HamSpec("cluster_paper"), HParams(ns=100, **TAB1["cluster"]), "mixed")
+    # the paper's 2D configurations (Sec. III.C, Tab. I: 10 x 10 open lattice,
+    # d_h = 200, N_s = 200): the Heisenberg point with a positive RNN and the
+    # Marshall sign, J2 = 0.5 with a complex RNN on the Marshall prior
+    w["heis10p"] = Workload(
+        "heisenberg_10x10_dh200_ns200_prnn_mixed",
+        ModelSpec(2, 10, 10, 200, cplx=0, marshall=1, zmask=1),
+        HamSpec("j1j2", J1=1.0, J2=0.0), HParams(ns=200, **TAB1["heisenberg"]), "mixed")
+    w["j1j2_10p"] = Workload(
+        "j1j2_10x10_J2_0.5_dh200_ns200_mixed",
+        ModelSpec(2, 10, 10, 200, cplx=1, marshall=1, zmask=1),
+        HamSpec("j1j2", J1=1.0, J2=0.5), HParams(ns=200, **TAB1["j1j2"]), "mixed")
     w["cluster64"] = Workload(
         "cluster_zxz_N64_dh64_ns512_mixed", ModelSpec(1, 64, 1, 64, cplx=1),
         HamSpec("cluster_zxz"), HParams(ns=512, **TAB1["cluster"]), "mixed")

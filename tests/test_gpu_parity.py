@@ -439,11 +439,19 @@ BIG = [
     (ModelSpec(1, 9, 1, 128, cplx=1), HamSpec("cluster_zxz")),
     (ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.25)),
     (ModelSpec(2, 4, 3, 96, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.6)),
+    # the paper's cluster-state hidden size (Tab. I): 32 lanes x 8 units per
+    # thread in the sweeps, 2 x 2 sub-blocks per pass in the O assembly
+    (ModelSpec(1, 8, 1, 256, cplx=1), HamSpec("cluster_paper")),
+    (ModelSpec(2, 3, 4, 256, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.5)),
+    # and the 2D one (200 = 8 lanes x 25 units; O in 10 x 10 tiles)
+    (ModelSpec(2, 4, 3, 200, marshall=1, zmask=1), HamSpec("j1j2", J2=0.0)),
+    (ModelSpec(1, 9, 1, 200), HamSpec("tfim")),
 ]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("model,ham", BIG, ids=["1d96", "1d128", "2d128", "2d96"])
+@pytest.mark.parametrize("model,ham", BIG, ids=["1d96", "1d128", "2d128", "2d96", "1d256", "2d256",
+                                                "2d200", "1d200"])
 def test_large_hidden_sizes(model, ham, prec):
     ns = 37
     c = ctx(model, ham, prec, ns)
