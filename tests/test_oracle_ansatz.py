@@ -35,7 +35,13 @@ def test_uniform_definition_and_moments():
 def test_param_counts_match_layout():
     # counts implied by the layout of App. A for the benchmark models
     expect = {"tfim16": 962, "tfim100": 13058, "tfim200": 3458, "cluster64": 13188,
-              "heis10": 21764}
+              "heis10": 21764,
+              # 1D, d_h 256, complex head: 2 (256 x 258) + 256^2 + 4 x 256 + 256 x 2 + 2 x (2 x 256 + 2)
+              "cluster100p": 2 * 256 * 258 + 256 ** 2 + 4 * 256 + 256 * 2 + 2 * (2 * 256 + 2),
+              # 2D, d_h 200: U1, U2, 2 (200 x 204), 200^2, 4 x 200, 200 x 4, heads (+ phase head)
+              "heis10p": 2 * 200 ** 2 + 2 * 200 * 204 + 200 ** 2 + 4 * 200 + 200 * 4 + 2 * 200 + 2,
+              "j1j2_10p": 2 * 200 ** 2 + 2 * 200 * 204 + 200 ** 2 + 4 * 200 + 200 * 4 +
+              2 * (2 * 200 + 2)}
     for key, w in workloads().items():
         assert O.param_count(w.model) == param_count(w.model) == expect[key]
     assert O.param_count(ModelSpec(2, 6, 6, 32, cplx=1)) == 5764
