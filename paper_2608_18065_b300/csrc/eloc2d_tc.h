@@ -35,6 +35,20 @@ struct Eloc2dTcArgs {
   // publishes the first tile, so that every consumer's wait runs out
   unsigned long long spin_limit;
   int test_drop_tile;
+  // streamed engine, sampling (Sec. II.A, eloc2d_tcs_sample): tiles of 128
+  // samples from site 0, sigma_k drawn with the Philox uniforms of sample
+  // s0 + s, step *step_dev, key seed; outputs as the sampler of the
+  // recurrence kernels
+  uint64_t seed;
+  uint64_t step;           // used when step_dev is null
+  const int64_t *step_dev;
+  int64_t s0;
+  int marshall;
+  uint8_t *spins_out;      // [ns][N]
+  double *logpsi;          // [ns][2]
+  float *hcache_out;       // [ns][N][dh]: h_k
+  float *lccache_out;      // [ns][N][2]: 1/2 log p(sigma_k), phi_k
+  float *gcache;           // [ns][N][5 dh]: u, r, c, W_h h' + b_h, h' (or null)
 };
 
 constexpr int ELOC2D_TC_ROWS = 128;  // rows per tile (the MMA's M)
@@ -49,5 +63,9 @@ cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaSt
 bool eloc2d_tcs_supported(int dim, int dh);
 size_t eloc2d_tcs_image_bytes(int dh);
 cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st);
+// Sampling of ns configurations with the same engine (args.ns, ntiles =
+// ceil(ns / 128), Lx <= 16, the column buffer and counter as above).
+bool eloc2d_tcs_sample_supported(int dim, int dh, int Lx);
+cudaError_t eloc2d_tcs_sample(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st);
 
 }  // namespace nqs

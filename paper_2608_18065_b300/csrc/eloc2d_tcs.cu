@@ -76,7 +76,8 @@ struct Tcs {
   static constexpr int OFF_HEAD = OFF_BH + DH * 4;         // float [4][DH]: head rows
   static constexpr int OFF_HC = OFF_HEAD + 4 * DH * 4;     // float [4]: head biases
   static constexpr int OFF_ZX = OFF_HC + 16;               // float4 [P-1][TR]: head partials
-  static constexpr int OFF_BAR = OFF_ZX + (P - 1) * TR * 16;
+  static constexpr int OFF_SPR = OFF_ZX + (P - 1) * TR * 16;  // uint8 [TR][32]: sampled spins
+  static constexpr int OFF_BAR = OFF_SPR + TR * 32;
   // mbarriers: full[NSLOT], empty[NSLOT], a, d1, d2[NCH], z, tfull[2], tempty[2], drain
   static constexpr int B_FULL = 0, B_EMPTY = NSLOT, B_A = 2 * NSLOT, B_D1 = B_A + 1,
                        B_D2 = B_D1 + 1, B_Z = B_D2 + NCH, B_TF = B_Z + 1, B_TE = B_TF + 2,
@@ -146,7 +147,9 @@ __device__ __forceinline__ bool wait_ab(uint32_t bar, uint32_t parity, volatile 
 
 // Stage schedule of a tile: F frontier passes (first product only) and S
 // sites (both products); zero for a tile past its operator's row count.
+template <bool SMP>
 __device__ __forceinline__ void tile_sched(const Eloc2dTcArgs &a, int tile, int &F, int &S) {
+  if (SMP) { F = 0; S = a.N; return; }  // sampling: every site from the first
   const int rk = tile / a.tiles_per_op;
   const int op = a.op_f[4 * rk + 3];
   const int base = (tile - rk * a.tiles_per_op) * ELOC2D_TC_ROWS;
@@ -156,7 +159,9 @@ __device__ __forceinline__ void tile_sched(const Eloc2dTcArgs &a, int tile, int 
   S = a.N - kst;
 }
 
-template <int DH>
+// SMP: sampling mode (tiles of 128 samples from site 0, sigma_k drawn from
+// the conditionals) instead of the connected configurations' suffixes.
+template <int DH, bool SMP>
 __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k_eloc2d_tcs(const Eloc2dTcArgs a) {
   using C = Tcs<DH>;
   extern __shared__ __align__(1024) unsigned char eraw[];
@@ -169,6 +174,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
   float *shead = reinterpret_cast<float *>(sm + C::OFF_HEAD);
   float *shc = reinterpret_cast<float *>(sm + C::OFF_HC);
   float4 *zx = reinterpret_cast<float4 *>(sm + C::OFF_ZX);
+  uint8_t *spr = sm + C::OFF_SPR;  // [row][32]: sampled spins, by site mod 32
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
   int *s_tile = reinterpret_cast<int *>(sm + C::OFF_MISC);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + C::OFF_MISC + 8);
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         mbar_arrive(bar(C::B_TF + slot));
         if (tile >= a.ntiles) break;
         int F, S;
-        tile_sched(a, tile, F, S);
+        tile_sched<SMP>(a, tile, F, S);
         bool stop = false;
         for (int f = 0; f < F + S && !stop; ++f) {
           const int len = f < F ? C::NS1 : C::NS1 + C::NS2;
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         const int tile = s_tile[slot];
         if (tile >= a.ntiles) break;
         int F, S;
-        tile_sched(a, tile, F, S);
+        tile_sched<SMP>(a, tile, F, S);
         for (int f = 0; f < F + S && !stop; ++f) {
           for (int prod = 0; prod < (f < F ? 1 : 2) && !stop; ++prod) {
             if (!wait_ab(bar(C::B_A), pa & 1, s_abort, lim)) { stop = true; break; }
@@ -333,19 +339,26 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       if (!wait_ab(bar(C::B_TF + slot), (it >> 1) & 1, s_abort, lim)) { ok = false; break; }
       const int tile = s_tile[slot];
       if (tile >= a.ntiles) break;
-      const int rk = tile / a.tiles_per_op;
-      const int op = a.op_f[4 * rk + 3];
-      const int base = (tile - rk * a.tiles_per_op) * C::TR;
-      const int cnt = a.item_cnt[op];
+      int op = 0, base, cnt;
+      if (SMP) {
+        base = tile * C::TR;
+        cnt = (int)a.ns;
+      } else {
+        const int rk = tile / a.tiles_per_op;
+        op = a.op_f[4 * rk + 3];
+        base = (tile - rk * a.tiles_per_op) * C::TR;
+        cnt = a.item_cnt[op];
+      }
       if (base >= cnt) {
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(C::B_TE + slot));
         continue;
       }
-      const int f1 = a.op_f[4 * op], f2 = a.op_f[4 * op + 1], kst = a.op_f[4 * op + 2];
+      const int f1 = SMP ? -1 : a.op_f[4 * op], f2 = SMP ? -1 : a.op_f[4 * op + 1];
+      const int kst = SMP ? 0 : a.op_f[4 * op + 2];
       const bool valid = base + row < cnt;
       const int64_t item = (int64_t)op * a.ns + base + row;
-      const int s = valid ? __ldcg(a.item_s + item) : 0;
+      const int s = SMP ? (valid ? base + row : 0) : (valid ? __ldcg(a.item_s + item) : 0);
       const uint8_t *sp = a.spins + (int64_t)s * N;
       const float *lcrow = a.lccache + (int64_t)s * N * 2;
       const float *hrow = a.hcache + (int64_t)s * N * DH + u0;
@@ -405,23 +418,24 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       cached_planes(kst - 1);
 
       // spins of the first site: sigma'_{k-1} (horizontal input), sigma'_k, vertical input
-      int s_prev = kst > 0 ? spin_at(kst - 1) : 2;
-      int s_cur = spin_at(kst);
-      int s_ver;
-      {
+      int s_prev = 2, s_cur = 2, s_ver = 2;
+      if (!SMP) {
+        s_prev = kst > 0 ? spin_at(kst - 1) : 2;
+        s_cur = spin_at(kst);
         const int m = kst % Lx;
         s_ver = kst >= Lx ? spin_at(kst - 2 * m - 1) : 2;
       }
-      int n_up = 0, n_dn = 0;
-      if (a.zmask && part == 0)
+      int n_up = 0, n_dn = 0, nA = 0;
+      if (!SMP && a.zmask && part == 0)
         for (int k = 0; k < kst; ++k) { if (__ldcg(sp + k) == 0) ++n_up; else ++n_dn; }
       // log |psi(sigma')/psi(sigma)| and the phase difference as error-free
       // FP32 TwoSum pairs; dead: the mask forces the amplitude of sigma' to zero
       float sre = 0.f, cre = 0.f, sim = 0.f, cim = 0.f;
       bool dead = false;
       float zp[4] = {0.f, 0.f, 0.f, 0.f};
-      int sgp = -1;
+      int sgp = -1, kr = -1;  // pending row work: spin (or to draw), site
       float2 lcp = make_float2(0.f, 0.f);
+      const uint64_t stp = SMP ? (a.step_dev ? (uint64_t)*a.step_dev : a.step) : 0;
       auto row_work = [&]() {
         float4 zo = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -436,6 +450,11 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           if (n_up >= N / 2) forced = 1;
           else if (n_dn >= N / 2) forced = 0;
         }
+        if (SMP) {  // draw sigma_k: 0 iff u < p_k(0) (FP32, 24-bit uniform)
+          const float p0 = forced == 0 ? 1.f : (forced == 1 ? 0.f : ex(lp0));
+          sgp = uniform24(a.seed, stp, (uint32_t)(s + a.s0), (uint32_t)kr) < p0 ? 0 : 1;
+          spr[row * 32 + (kr & 31)] = (uint8_t)sgp;
+        }
         const bool kill = forced >= 0 && sgp != forced;
         const float hl = forced >= 0 ? 0.f : 0.5f * (sgp == 0 ? lp0 : lp1);
         float pp = 0.f, pe = 0.f;
@@ -447,6 +466,13 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         two_add(sim, cim, pp);
         two_add(sim, cim, pe - lcp.y);
         if (sgp == 0) ++n_up; else ++n_dn;
+        if (SMP && valid) {
+          a.spins_out[(int64_t)s * N + kr] = (uint8_t)sgp;
+          reinterpret_cast<float2 *>(a.lccache_out)[(int64_t)s * N + kr] =
+              make_float2(kill ? -INFINITY : hl, pp + pe);
+          if (a.marshall && sgp == 1 && (((kr / Lx) & 1 ? Lx - 1 - kr % Lx : kr % Lx) + kr / Lx) & 1)
+            ++nA;
+        }
       };
 
       for (int k = kst; k < N; ++k) {
@@ -454,7 +480,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         const int col = (jr & 1) ? (Lx - 1 - m) : m;
         const bool hor = m != 0;
         const int ver = k >= Lx ? k - 2 * m - 1 : -1;
-        const int d0 = hor ? s_prev : 2, d1 = ver >= 0 ? s_ver : 2;
+        int d0 = hor ? s_prev : 2, d1 = ver >= 0 ? s_ver : 2;
         arrive_a();  // A = h_{k-1}
         // the vertical term from the column buffer (in flight during the product)
         float hp[UT];
@@ -469,7 +495,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         }
         // next site's raw spins (flipped when used) and this site's cached terms
         int r_next = 0, r_vnext = 0, k_v = -1;
-        if (k + 1 < N) {
+        if (!SMP && k + 1 < N) {
           const int m1 = (k + 1) % Lx;
           r_next = __ldcg(sp + k + 1);
           if (k + 1 >= Lx) {
@@ -478,10 +504,10 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           }
         }
         float2 lc = make_float2(0.f, 0.f);
-        if (part == 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * k));
+        if (!SMP && part == 0 && valid) lc = __ldcg(reinterpret_cast<const float2 *>(lcrow + 2 * k));
         // the previous site's row work overlaps the first product (the other
         // parts' head partials are published by their arrival on a)
-        if (part == 0 && sgp >= 0) {
+        if (part == 0 && (SMP ? k > 0 : sgp >= 0)) {
           if (!wait_ab(bar(C::B_A), (na - 1) & 1, s_abort, lim)) { ok = false; break; }
           row_work();
         }
@@ -509,11 +535,18 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
         }
         arrive_a();  // A = h'
+        // sampling: part 0 drew sigma_{k-1} before its arrival on a
+        if (SMP && part > 0 && !wait_ab(bar(C::B_A), (na - 1) & 1, s_abort, lim)) { ok = false; break; }
         if (!wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort, lim)) { ok = false; break; }
         tc_fence_after();
+        if (SMP) {
+          d0 = hor ? spr[row * 32 + ((k - 1) & 31)] : 2;
+          d1 = ver >= 0 ? spr[row * 32 + (ver & 31)] : 2;
+        }
         // GRU cell (App. A) on this thread's units, 8 at a time; h_k overwrites
         // h' in registers and goes to the planes once every chunk is done
         const float *tb = tab + (d0 * 3 + d1) * C::TS + u0;
+        float *grow = SMP && a.gcache ? a.gcache + ((int64_t)s * N + k) * 5 * DH + u0 : nullptr;
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
@@ -522,12 +555,14 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           tmem_ld8(gcol + (uint32_t)(C::CU + 8 * g8), gr);
           tmem_ld8(gcol + (uint32_t)(2 * C::CU + 8 * g8), gg);
           tmem_wait_ld();
+          float su[8], sr[8], sc[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int i = 8 * g8 + u, un = u0 + i;
             const float uu = sigm_f(gu[u] + tb[i]), rr = sigm_f(gr[u] + tb[DH + i]);
             const float cc = tanh_f(fmaf(rr, gg[u] + sbh[un], tb[2 * DH + i]));
             const float hn = fmaf(uu, cc - hp[i], hp[i]);
+            if (SMP) { su[u] = uu; sr[u] = rr; sc[u] = cc; gg[u] += sbh[un]; gu[u] = hp[i]; }
             hp[i] = hn;
             z0 = fmaf(shead[un], hn, z0);
             z1 = fmaf(shead[DH + un], hn, z1);
@@ -535,6 +570,20 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
               z2 = fmaf(shead[2 * DH + un], hn, z2);
               z3 = fmaf(shead[3 * DH + un], hn, z3);
             }
+          }
+          if (SMP && valid) {  // gate cache (u, r, c, W_h h' + b_h, h') and h_k
+            auto st8 = [&](float *dst, const float *v) {
+              reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+              reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+            };
+            if (grow) {
+              st8(grow + 8 * g8, su);
+              st8(grow + DH + 8 * g8, sr);
+              st8(grow + 2 * DH + 8 * g8, sc);
+              st8(grow + 3 * DH + 8 * g8, gg);
+              st8(grow + 4 * DH + 8 * g8, gu);
+            }
+            st8(a.hcache_out + ((int64_t)s * N + k) * DH + u0 + 8 * g8, hp + 8 * g8);
           }
         }
         if (chunk != C::NCH - 1 &&
@@ -548,6 +597,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
           zp[0] = z0; zp[1] = z1; zp[2] = z2; zp[3] = z3;
           sgp = s_cur;
           lcp = lc;
+          kr = k;
         }
         s_prev = s_cur;
         s_cur = k + 1 < N ? r_next ^ ((k + 1 == f1 || k + 1 == f2) ? 1 : 0) : 2;
@@ -559,7 +609,14 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       mbar_arrive(bar(C::B_Z));
       if (!wait_ab(bar(C::B_Z), pz & 1, s_abort, lim)) { ok = false; break; }
       ++pz;
-      if (part == 0) {
+      if (part == 0 && SMP) {
+        row_work();
+        if (valid) {
+          a.logpsi[2 * (int64_t)s] = dead ? -INFINITY : (double)sre + (double)cre;
+          a.logpsi[2 * (int64_t)s + 1] =
+              (double)sim + (double)cim + (a.marshall && (nA & 1) ? NQS_PI : 0.0);
+        }
+      } else if (part == 0) {
         if (sgp >= 0) row_work();
         if (valid) {
           const double e = a.item_e[item];
@@ -620,19 +677,19 @@ __global__ void k_eloc2d_tcs_image(const float *__restrict__ pack, int oWgT, int
   }
 }
 
-template <int DH>
+template <int DH, bool SMP>
 cudaError_t run_dh(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st) {
   using C = Tcs<DH>;
   k_eloc2d_tcs_image<DH><<<C::IMG / 2 / 256 / 4 + 1, 256, 0, st>>>(
       args.pack, args.oWgT, args.oU12T, const_cast<unsigned char *>(args.wimg));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_eloc2d_tcs<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_eloc2d_tcs<DH, SMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::SMEM);
   if (e != cudaSuccess) return e;
   const int grid = args.ntiles < sm_count ? args.ntiles : sm_count;
   if (grid <= 0) return cudaSuccess;
-  k_eloc2d_tcs<DH><<<grid, C::THREADS, C::SMEM, st>>>(args);
+  k_eloc2d_tcs<DH, SMP><<<grid, C::THREADS, C::SMEM, st>>>(args);
   return cudaGetLastError();
 }
 
@@ -645,8 +702,23 @@ size_t eloc2d_tcs_image_bytes(int dh) {
 }
 
 cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st) {
-  if (dh == 128) return run_dh<128>(args, sm_count, st);
-  if (dh == 96) return run_dh<96>(args, sm_count, st);
+  if (dh == 128) return run_dh<128, false>(args, sm_count, st);
+  if (dh == 96) return run_dh<96, false>(args, sm_count, st);
+  return cudaErrorInvalidValue;
+}
+
+// The sampled spins of a row are kept in a 32-site ring: the vertical
+// neighbour of site k is at most 2 Lx - 1 sites back.
+bool eloc2d_tcs_sample_supported(int dim, int dh, int Lx) {
+  return eloc2d_tcs_supported(dim, dh) && Lx >= 1 && 2 * Lx - 1 <= 31;
+}
+
+cudaError_t eloc2d_tcs_sample(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st) {
+  if (!eloc2d_tcs_sample_supported(2, dh, args.Lx) || !args.spins_out || !args.logpsi ||
+      !args.hcache_out || !args.lccache_out || !args.colbuf || !args.tile_ctr || !args.err)
+    return cudaErrorInvalidValue;
+  if (dh == 128) return run_dh<128, true>(args, sm_count, st);
+  if (dh == 96) return run_dh<96, true>(args, sm_count, st);
   return cudaErrorInvalidValue;
 }
 

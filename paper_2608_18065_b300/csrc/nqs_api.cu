@@ -265,6 +265,39 @@ FwdArgs<T> fwd_args(nqs_ctx *c) {
   return a;
 }
 
+// Alg. 1, sampling.  Mixed-precision 2D models of hidden size 96 or 128
+// with every state cached draw on the streamed tensor-core engine (the same
+// uniforms, the same FP32 decision, the same caches); the others on the
+// recurrence kernels' sampler.
+template <typename T>
+nqs_status run_sample(nqs_ctx *c, const FwdArgs<T> &a, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->ck == 0 && gram_tc_available() &&
+        eloc2d_tcs_sample_supported(c->L.dim, c->L.dh, c->L.Lx)) {
+      Eloc2dTcArgs e{};
+      e.pack = a.pack;
+      e.oWgT = (int)c->P.WgT; e.oxw = (int)c->P.xw; e.obias = (int)c->P.bias;
+      e.ohead = (int)c->P.head; e.ohc = (int)c->P.hc; e.oU12T = (int)c->P.U12T;
+      e.N = c->L.N; e.Lx = c->L.Lx; e.cplx = c->L.cplx; e.zmask = c->L.zmask; e.ns = a.nrows;
+      e.ntiles = (int)((a.nrows + ELOC2D_TC_ROWS - 1) / ELOC2D_TC_ROWS);
+      e.colbuf = W<float>(c, c->off.colbuf);
+      e.err = W<int>(c, c->off.sstat);
+      e.tile_ctr = W<int>(c, c->off.tctr);
+      e.wimg = reinterpret_cast<const unsigned char *>(c->ws + c->off.wimg);
+      e.spin_limit = c->test_spin_limit;
+      e.seed = a.seed; e.step = a.step; e.step_dev = a.step_dev; e.s0 = a.s0;
+      e.marshall = c->L.marshall;
+      e.spins_out = a.spins; e.logpsi = a.logpsi;
+      e.hcache_out = a.hcache; e.lccache_out = a.lccache; e.gcache = a.gcache;
+      c->launches += 2;
+      CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
+      return cu(eloc2d_tcs_sample(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
+    }
+  }
+  c->launches += 1;
+  return cu(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+}
+
 // with_gates: also store the gate activations the reverse sweep reads.
 template <typename T>
 nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t step, uint8_t *spins,
@@ -275,6 +308,7 @@ nqs_status forward_T(nqs_ctx *c, int mode, int64_t n, uint64_t seed, uint64_t st
     a.gcache = W<T>(c, c->off.gcache);
     a.gw = c->gw;
   }
+  if (mode == MODE_SAMPLE) return run_sample<T>(c, a, st);
   c->launches += 1;
   return cu(run_forward<T>(c->rd, mode, a, 0, st));
 }
@@ -376,7 +410,7 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.wimg = reinterpret_cast<const unsigned char *>(c->ws + c->off.wimg);
       e.spin_limit = c->test_spin_limit;
       e.test_drop_tile = c->test_drop_tile;
-      c->launches += 1;
+      c->launches += 2;
       CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
       CU(eloc2d_tcs_run(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
@@ -750,8 +784,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
       a.gcache = W<T>(c, c->off.gcache);
       a.gw = c->gw;
     }
-    c->launches += 1;
-    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+    ST(run_sample<T>(c, a, st));
   }
   // Alg. 1, energy: local energies, E, variance; eps-bar'
   ST(eloc_T<T>(c, ns, spins, eloc, st));
@@ -856,8 +889,8 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
     a.nrows = ns; a.seed = hp->seed + LM_KEY_OFFSET; a.step = (uint64_t)hp->step_index;
     a.step_dev = W<int64_t>(c, c->off.dstep);
     a.spins = spins; a.logpsi = logpsi;
-    c->launches += 3;
-    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+    c->launches += 1;
+    ST(run_sample<T>(c, a, st));
     ST(eloc_T<T>(c, ns, spins, eloc, st));
     k_lm_update<<<1, 1024, 0, st>>>(eloc, ns, eps, x, R, stats, W<double>(c, c->off.dlm),
                                     c->lm_omega);
@@ -1485,8 +1518,7 @@ nqs_status shard_forward_T(nqs_ctx *c, const double *theta, const nqs_step_hpara
       a.gcache = W<T>(c, c->off.gcache);
       a.gw = c->gw;
     }
-    c->launches += 1;
-    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+    ST(run_sample<T>(c, a, st));
   }
   ST(eloc_T<T>(c, n, spins, eloc, st));
   const unsigned nblk = c->L.cplx ? 2u : 1u;
@@ -1574,8 +1606,7 @@ nqs_status forward_energy_T(nqs_ctx *c, const double *theta, int64_t ns, uint64_
       a.gcache = W<T>(c, c->off.gcache);
       a.gw = c->gw;
     }
-    c->launches += 1;
-    CU(run_forward<T>(c->rd, MODE_SAMPLE, a, 0, st));
+    ST(run_sample<T>(c, a, st));
   }
   ST(eloc_T<T>(c, ns, spins, eloc, st));
   k_energy<<<1, 1024, 0, st>>>(eloc, ns, c->L.N, c->L.cplx, stats, W<double>(c, c->off.eps));
@@ -1971,8 +2002,42 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
     if (s != NQS_OK) break;
     if (ms < best) { best = ms; pick = q; }
   }
-  b->graph_enabled = saved_graph;
   b->conc = pick;
+  // (3) grids of the instances' cooperative solves: each takes the whole
+  // GPU alone, so one other instance's kernels wait for it; a fraction of
+  // the SMs per solve lets them run beside it
+  std::vector<int> g0(n);
+  for (int i = 0; i < n; ++i) g0[i] = b->ctx[i]->t_solve_grid;
+  int pdiv = 1;
+  for (int div : {2, 4}) {
+    if (s != NQS_OK) break;
+    for (int i = 0; i < n; ++i) {
+      const int g = g0[i] > 0 ? g0[i] : b->ctx[i]->rd.sm_count;
+      b->ctx[i]->t_solve_grid = std::max(1, g / div);
+    }
+    double ms = 0;
+    s = best_ms(st, 2, [&] {
+      for (int i = 0; i < n; ++i) {
+        const int64_t np = b->ctx[i]->L.np;
+        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
+      }
+      return NQS_OK;
+    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
+    if (s == NQS_OK && ms < best) { best = ms; pdiv = div; }
+  }
+  for (int i = 0; i < n; ++i) {
+    const int g = g0[i] > 0 ? g0[i] : b->ctx[i]->rd.sm_count;
+    b->ctx[i]->t_solve_grid = pdiv == 1 ? g0[i] : std::max(1, g / pdiv);
+  }
+  if (pdiv != 1) {  // the process-wide choices follow, so a context tuned later matches
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int i = 0; i < n; ++i) {
+      auto it = g_tune_cache.find(tune_key(b->ctx[i], b->ctx[i]->tuned_ns));
+      if (it != g_tune_cache.end()) it->second.solve_grid = b->ctx[i]->t_solve_grid;
+    }
+  }
+  b->graph_enabled = saved_graph;
   if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
   if (step_ms) *step_ms = best;
   return s;

@@ -85,6 +85,30 @@ def record_error(case, **errors):
         f.write(json.dumps({"case": case, **{k: float(v) for k, v in errors.items()}}) + "\n")
 
 
+#  Mixed 2D models of hidden size 96 / 128 (rows of at most 16 sites) draw
+#  their samples on the streamed tensor-core engine, whose gate products take
+#  BF16 hi/lo splits of both operands (hi.hi + lo.hi + hi.lo): each product
+#  term carries a relative error up to 3 * 2^-18 (two split residuals of
+#  2^-18 and the dropped lo.lo term), about 2^-16.4, against FP32's 2^-24.
+#  A state error of that order enters every site's logits; the sites'
+#  log-probabilities add up to |Delta log Psi| <= 1e-4 + 2^-14 N, a per-site
+#  budget of four such units (weights up to 1.5 times the initialisation
+#  scale, whose row sums of |W h| stay below a few units).
+TOL_TC_LOGPSI_SITE = 2.0 ** -14
+
+
+def tc_sampled(model, precision):
+    """Whether the context draws its samples on the streamed engine."""
+    return (precision == "mixed" and model.dim == 2 and model.dh in (96, 128)
+            and 2 * model.Lx - 1 <= 31)
+
+
+def logpsi_err_tc(lp, lp_o, N):
+    """Largest per-sample |Delta log Psi| in units of the tensor-core
+    sampler's bound 1e-4 + 2^-14 N (<= 1 passes)."""
+    return float(np.max(np.abs(lp - lp_o)) / (TOL_MIXED_LOGPSI + TOL_TC_LOGPSI_SITE * N))
+
+
 def logpsi_err(lp, lp_o):
     """Largest per-sample |Delta log Psi| in units of the mixed path's bound
     1e-4 + 1e-5 |log Psi| (<= 1 passes)."""

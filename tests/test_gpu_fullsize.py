@@ -24,6 +24,7 @@ from oracle import oracle as O
 from paper_2608_18065_b300 import nqs
 from paper_2608_18065_b300.inputs import init_theta, workloads
 from tests.gpu_helpers import (RTOL64, TOL_MIXED_ELOC, TOL_MIXED_JAC, cplx, logpsi_err,
+                               logpsi_err_tc, tc_sampled,
                                max_elem_err, max_row_err, record_error, rel_err)
 
 pytestmark = pytest.mark.gpu
@@ -93,6 +94,8 @@ def test_full_size_step(key, prec):
     lp_o = O.logpsi(model, th, spins)
     if f64:
         np.testing.assert_allclose(lp, lp_o, rtol=RTOL64, atol=RTOL64)
+    elif tc_sampled(model, prec):
+        assert logpsi_err_tc(lp, lp_o, model.N) <= 1.0
     else:
         assert logpsi_err(lp, lp_o) <= 1.0
     # E_loc on sampled rows, every one of them
