@@ -286,7 +286,8 @@ typedef struct {
   int eloc_grid;      /* CTAs of the connected-configuration engine */
   int gram_splits;    /* K-slices per 128x128 tile of the tensor-core Gram */
   int solve_grid;     /* CTAs of the cooperative Cholesky / refinement */
-  int solve_tiles_per_warp; /* refinement tiles: 1 per warp, 0 per CTA, -1 built-in */
+  int solve_form;           /* mixed solve: 0 32-wide panels, tiles per CTA; 1 the
+                               same, tiles per warp; 2 128-wide panels; -1 built-in */
   int solve_substitution;   /* refinement sweeps: 1 block substitution, 0 explicit inverse, -1 built-in */
   int reserved;
   double ms[3];         /* time of the chosen shape: eloc, gram, solve */
@@ -317,6 +318,13 @@ nqs_status nqs_autotune(nqs_ctx *ctx, const double *theta,
 nqs_status nqs_get_tuning(const nqs_ctx *ctx, nqs_tuning *out);
 /* Back to the built-in shapes. */
 nqs_status nqs_clear_tuning(nqs_ctx *ctx);
+/* Fix the form of the mixed context's regularized solve (Eq. minsrR; the
+ * values of nqs_tuning.solve_form; -1: the built-in choice, 128-wide panels
+ * from R = 1024 on where R % 4 == 0, otherwise 32-wide) for every later
+ * solve, over any tuning.  The 128-wide form needs R % 4 == 0 and R >= 256
+ * and takes the 32-wide one otherwise.  Every form ends at FP64 backward
+ * error or in the FP64 Cholesky.  NQS_ERR_ARG for another value. */
+nqs_status nqs_set_solve_form(nqs_ctx *ctx, int form);
 
 /* ------------------------------------------------------ batched instances */
 

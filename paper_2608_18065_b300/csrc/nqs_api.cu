@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "chol_coop.cuh"
+#include "chol_blk.cuh"
 #include "chol_ir.cuh"
 #include "eloc_tc.h"
 #include "eloc2d_tc.h"
@@ -56,6 +57,7 @@ struct nqs_ctx {
   // tests of failure detection (nqs_test_wait_timeout): wait limit of the
   // streamed local-energy engine and its dropped tile
   unsigned long long test_spin_limit = 0;
+  int solve_form = -1;  // nqs_set_solve_form (-1: tuned or built-in)
   int test_drop_tile = 0;
   WsOff off{};
   char *ws = nullptr;
@@ -673,7 +675,33 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
   int32_t *need = reinterpret_cast<int32_t *>(bar + 4);
   const int G = solve_grid(c);
   CU(cudaMemsetAsync(bar, 0, 32, st));
-  if (f32(c)) {
+  // blocked FP32 factor (128-wide panels) where it applies and is chosen:
+  // by the autotuner, else from R = 1024 on
+  const int var = c->solve_form >= 0                  ? c->solve_form
+                  : tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var
+                                                   : (R >= 1024 ? 2 : 0);
+  if (f32(c) && var == 2 && chol_blk_supported(R)) {
+    CholBlkArgs bk;
+    bk.A = T; bk.n = R; bk.b = b; bk.x = x;
+    bk.L = W<float>(c, c->off.L32);
+    bk.Dinv = W<float>(c, c->off.Tm32);
+    bk.t = W<float>(c, c->off.dpart32);
+    bk.w = W<float>(c, c->off.wv32);
+    bk.r = W<double>(c, c->off.crhs);
+    bk.part = W<double>(c, c->off.cpart);
+    bk.bar = bar + 2;
+    bk.status = status;
+    bk.need_fp64 = need;
+    bk.maxit = 12;
+    const size_t smem = chol_blk_smem();
+    CU(cudaFuncSetAttribute((const void *)k_chol_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    const int Gb = std::min(G, c->rd.sm_count);
+    void *args[] = {&bk};
+    c->launches += 1;
+    CU(cudaLaunchCooperativeKernel((const void *)k_chol_blk, dim3(Gb), dim3(BKB_THREADS), args, smem,
+                                   st));
+  } else if (f32(c)) {
     CholIrArgs ir;
     ir.A = T; ir.n = R; ir.b = b; ir.x = x;
     ir.L = W<float>(c, c->off.L32);
@@ -697,7 +725,7 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     // CTA tiles in batches of four at every size (measured: factor 4.7 ms
     // against 6.6 ms with a tile per warp at n = 4096; 0.26 ms against 0.93
     // at n = 1024)
-    const bool wt = tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var == 1 : false;
+    const bool wt = var == 1;
     const void *kern = wt ? (const void *)k_chol_ir<true> : (const void *)k_chol_ir<false>;
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // a grid above one CTA per SM only where the occupancy allows it: every
@@ -1362,13 +1390,15 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
                                          W<double>(c, c->off.x), W<int32_t>(c, c->off.sstat), st);
                      }, ms);
     };
-    const int var0 = R >= 2048 ? 1 : 0, sub0 = R >= 2048 ? 1 : 0;
+    const bool blk_ok = f32(c) && chol_blk_supported(R);
+    const int var0 = blk_ok && R >= 1024 ? 2 : (R >= 2048 ? 1 : 0), sub0 = R >= 2048 ? 1 : 0;
     double best = 1e300;
     int pvar = var0, psub = sub0, pick = G0;
     c->t_solve_grid = G0;
-    for (int var : {0, 1})
+    for (int var : {0, 1, 2})
       for (int sub : {0, 1}) {
         if (!f32(c) && (var != var0 || sub != sub0)) continue;  // FP64 path: one form
+        if (var == 2 && (!blk_ok || sub != sub0)) continue;     // blocked: no sweep variants
         c->t_chol_var = var;
         c->t_chol_subst = sub;
         double ms = 0;
@@ -1446,7 +1476,7 @@ nqs_status nqs_get_tuning(const nqs_ctx *c, nqs_tuning *out) {
   out->eloc_grid = c->t_eloc_grid;
   out->gram_splits = c->t_gram_splits;
   out->solve_grid = c->t_solve_grid;
-  out->solve_tiles_per_warp = c->t_chol_var;
+  out->solve_form = c->t_chol_var;
   out->solve_substitution = c->t_chol_subst;
   for (int i = 0; i < 3; ++i) { out->ms[i] = c->t_ms[i]; out->ms_default[i] = c->t_ms_default[i]; }
   return NQS_OK;
@@ -1458,6 +1488,13 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   c->tuned_ns = 0;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
   c->t_chol_var = c->t_chol_subst = -1;
+  return NQS_OK;
+}
+
+nqs_status nqs_set_solve_form(nqs_ctx *c, int form) {
+  if (!c || form < -1 || form > 2) return NQS_ERR_ARG;
+  drop_graph(c);
+  c->solve_form = form;
   return NQS_OK;
 }
 

@@ -66,7 +66,7 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
            "nqs_shard_solve", "nqs_shard_apply", "nqs_test_wait_timeout", "nqs_adam_step",
-           "nqs_energy_scan",
+           "nqs_energy_scan", "nqs_set_solve_form",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -86,7 +86,7 @@ class SpectrumStats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("eloc_grid", C.c_int), ("gram_splits", C.c_int),
-                ("solve_grid", C.c_int), ("solve_tiles_per_warp", C.c_int),
+                ("solve_grid", C.c_int), ("solve_form", C.c_int),
                 ("solve_substitution", C.c_int), ("reserved", C.c_int),
                 ("ms", C.c_double * 3), ("ms_default", C.c_double * 3)]
 
@@ -374,13 +374,18 @@ class Context:
         names = ("eloc", "gram", "solve")
         return {"n_samples": t.n_samples, "eloc_grid": t.eloc_grid,
                 "gram_splits": t.gram_splits, "solve_grid": t.solve_grid,
-                "solve_tiles_per_warp": t.solve_tiles_per_warp,
+                "solve_form": t.solve_form,
                 "solve_substitution": t.solve_substitution,
                 "ms": dict(zip(names, list(t.ms))),
                 "ms_default": dict(zip(names, list(t.ms_default)))}
 
     def clear_tuning(self):
         _check(lib().nqs_clear_tuning(self._h))
+
+    def set_solve_form(self, form):
+        """Form of the mixed regularized solve: 0 / 1 32-wide panels (tiles
+        per CTA / per warp), 2 128-wide panels, -1 built-in (nqs_set_solve_form)."""
+        _check(lib().nqs_set_solve_form(self._h, int(form)))
 
     def step_outputs(self, ns):
         R = ns * self.rows_per_sample

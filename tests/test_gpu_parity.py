@@ -433,6 +433,43 @@ def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
     assert rel_err(x.cpu().numpy(), xr) < 100 * kappa * 2.2e-16
 
 
+@pytest.mark.parametrize("R", [256, 260, 1000, 2304])
+def test_regularized_solve_128_wide_panels(R):
+    """Mixed context, the 128-wide panel form (two panels at R = 256; ragged
+    last blocks of 4 and 104 rows at 260 and 1000): the FP32 factor with
+    explicitly inverted 128 x 128 diagonal blocks and the FP64 refinement
+    reach the FP64 solution at FP64 backward error; an indefinite matrix
+    reports NOT_SPD; a matrix whose FP32 factor breaks down (kappa ~ 1e12)
+    is solved by the FP64 Cholesky that follows."""
+    model, ham = ModelSpec(1, 8, 1, 8), HamSpec("tfim")
+    c = ctx(model, ham, "mixed", R)
+    c.set_solve_form(2)
+    rng = np.random.default_rng(R + 7)
+    M = rng.standard_normal((R, R + 5))
+    T = M @ M.T / R
+    b = rng.standard_normal(R)
+    lam = 1e-2
+    x, st = c.regularized_solve(torch.tensor(T, device="cuda"), lam, torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 0
+    A = T + lam * np.eye(R)
+    xr = np.linalg.solve(A, b)
+    kappa = np.linalg.cond(A)
+    xg = x.cpu().numpy()
+    assert rel_err(xg, xr) < max(1e-10, 100 * kappa * 2.2e-16)
+    berr = np.max(np.abs(A @ xg - b)) / (np.max(np.abs(A).sum(1)) * np.max(np.abs(xg)))
+    assert berr < 100 * np.sqrt(R) * 1.11e-16
+    x, st = c.regularized_solve(torch.tensor(-T - np.eye(R), device="cuda"), 0.0,
+                                torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 5
+    Q, _ = np.linalg.qr(rng.standard_normal((R, R)))
+    Ts = (Q * np.logspace(0, -12, R)) @ Q.T
+    Ts = 0.5 * (Ts + Ts.T)
+    x, st = c.regularized_solve(torch.tensor(Ts, device="cuda"), 0.0, torch.tensor(b, device="cuda"))
+    assert int(st.item()) == 0
+    xr = np.linalg.solve(Ts, b)
+    assert rel_err(x.cpu().numpy(), xr) < 100 * np.linalg.cond(Ts) * 2.2e-16
+
+
 # hidden sizes whose weights do not fit shared memory (read through L1)
 BIG = [
     (ModelSpec(1, 10, 1, 96), HamSpec("tfim")),
