@@ -322,10 +322,22 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
     // ------------------------------------------------------ compute warps
     const int quarter = warp & 3, part = warp >> 2;
     constexpr int UT = C::UT, G8 = UT / 8;
+    // A thread's units, 8 at a time.  Where the units divide evenly, a part
+    // takes CU / P units of every gate chunk (group g8 in chunk g8 / GPC), so
+    // that every part starts its cell update as soon as the first chunk of
+    // the gate product lands; otherwise part p takes units UT p .. UT p + UT - 1.
+    constexpr bool SPLIT = C::NCH > 1 && UT % (8 * C::NCH) == 0;
+    constexpr int GPC = SPLIT ? G8 / C::NCH : G8;
     const int row = 32 * quarter + lane, u0 = UT * part;
+    auto unit_of = [&](int g8) {
+      return SPLIT ? (g8 / GPC) * C::CU + part * (C::CU / C::P) + 8 * (g8 % GPC) : u0 + 8 * g8;
+    };
     const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
-    const int chunk = u0 / C::CU, uo = u0 - chunk * C::CU;
-    const uint32_t gcol = lanes + (uint32_t)(chunk * C::N2 + uo);  // gate j at + CU j
+    // gate j of unit un in the second product's accumulator
+    auto gcol = [&](int un) {
+      return lanes + (uint32_t)((un / C::CU) * C::N2 + un % C::CU);
+    };
+    const int chunk = u0 / C::CU;  // the chunk of a part's units when not split
     uint32_t na = 0, pd1 = 0, pd2 = 0, pz = 0;  // arrivals on a; phases of d1, d2, z waited
     bool ok = true;
     auto arrive_a = [&]() {
@@ -361,8 +373,8 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       const int s = SMP ? (valid ? base + row : 0) : (valid ? __ldcg(a.item_s + item) : 0);
       const uint8_t *sp = a.spins + (int64_t)s * N;
       const float *lcrow = a.lccache + (int64_t)s * N * 2;
-      const float *hrow = a.hcache + (int64_t)s * N * DH + u0;
-      float *cb = a.colbuf + ((int64_t)blockIdx.x * C::TR + row) * Lx * DH + u0;
+      const float *hrow = a.hcache + (int64_t)s * N * DH;
+      float *cb = a.colbuf + ((int64_t)blockIdx.x * C::TR + row) * Lx * DH;
       auto colof = [&](int k) {
         const int jr = k / Lx, m = k - jr * Lx;
         return (jr & 1) ? (Lx - 1 - m) : m;
@@ -370,16 +382,16 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       auto spin_at = [&](int k) { return (int)__ldcg(sp + k) ^ ((k == f1 || k == f2) ? 1 : 0); };
       // cached state h_k (this thread's units) into the A planes, zero if k < 0
       auto cached_planes = [&](int k) {
-        const float4 *src = reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH);
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
+          const float4 *src = reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH + unit_of(g8));
           float h8[8];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            const float4 v = (valid && k >= 0) ? __ldcg(src + 2 * g8 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v = (valid && k >= 0) ? __ldcg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
             h8[4 * q] = v.x; h8[4 * q + 1] = v.y; h8[4 * q + 2] = v.z; h8[4 * q + 3] = v.w;
           }
-          planes8<DH>(Sh, row, u0 + 8 * g8, h8);
+          planes8<DH>(Sh, row, unit_of(g8), h8);
         }
       };
       // Y = U2 h (columns DH + units) of the last first product into the
@@ -388,10 +400,10 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
           float y[8];
-          tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
+          tmem_ld8(lanes + (uint32_t)(DH + unit_of(g8)), y);
           tmem_wait_ld();
           if (valid) {
-            float4 *dst = reinterpret_cast<float4 *>(cb + col * DH + 8 * g8);
+            float4 *dst = reinterpret_cast<float4 *>(cb + col * DH + unit_of(g8));
             dst[0] = make_float4(y[0], y[1], y[2], y[3]);
             dst[1] = make_float4(y[4], y[5], y[6], y[7]);
           }
@@ -485,12 +497,14 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         // the vertical term from the column buffer (in flight during the product)
         float hp[UT];
         const bool vbuf = valid && ver >= 0 && ver != k - 1;
-        {
-          const float4 *src = reinterpret_cast<const float4 *>(cb + col * DH);
 #pragma unroll
-          for (int q = 0; q < UT / 4; ++q) {
+        for (int g8 = 0; g8 < G8; ++g8) {
+          const float4 *src = reinterpret_cast<const float4 *>(cb + col * DH + unit_of(g8));
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
             const float4 v = vbuf ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            hp[4 * q] = v.x; hp[4 * q + 1] = v.y; hp[4 * q + 2] = v.z; hp[4 * q + 3] = v.w;
+            float *h = hp + 8 * g8 + 4 * q;
+            h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
           }
         }
         // next site's raw spins (flipped when used) and this site's cached terms
@@ -519,8 +533,8 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
           float x[8], y[8];
-          tmem_ld8(lanes + (uint32_t)(u0 + 8 * g8), x);
-          tmem_ld8(lanes + (uint32_t)(DH + u0 + 8 * g8), y);
+          tmem_ld8(lanes + (uint32_t)unit_of(g8), x);
+          tmem_ld8(lanes + (uint32_t)(DH + unit_of(g8)), y);
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -528,16 +542,16 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
             hp[8 * g8 + i] = hor ? x[i] + v : v;
           }
           if (valid && k >= 1) {
-            float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + 8 * g8);
+            float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + unit_of(g8));
             dst[0] = make_float4(y[0], y[1], y[2], y[3]);
             dst[1] = make_float4(y[4], y[5], y[6], y[7]);
           }
-          planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
+          planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
         }
         arrive_a();  // A = h'
         // sampling: part 0 drew sigma_{k-1} before its arrival on a
         if (SMP && part > 0 && !wait_ab(bar(C::B_A), (na - 1) & 1, s_abort, lim)) { ok = false; break; }
-        if (!wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort, lim)) { ok = false; break; }
+        if (!SPLIT && !wait_ab(bar(C::B_D2 + chunk), pd2 & 1, s_abort, lim)) { ok = false; break; }
         tc_fence_after();
         if (SMP) {
           d0 = hor ? spr[row * 32 + ((k - 1) & 31)] : 2;
@@ -545,22 +559,28 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         }
         // GRU cell (App. A) on this thread's units, 8 at a time; h_k overwrites
         // h' in registers and goes to the planes once every chunk is done
-        const float *tb = tab + (d0 * 3 + d1) * C::TS + u0;
-        float *grow = SMP && a.gcache ? a.gcache + ((int64_t)s * N + k) * 5 * DH + u0 : nullptr;
+        const float *tb = tab + (d0 * 3 + d1) * C::TS;
+        float *grow = SMP && a.gcache ? a.gcache + ((int64_t)s * N + k) * 5 * DH : nullptr;
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+        bool dok = true;
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
+          const int ug = unit_of(g8);
+          if (SPLIT && g8 % GPC == 0) {  // the next chunk of the gate product
+            dok = dok && wait_ab(bar(C::B_D2 + g8 / GPC), pd2 & 1, s_abort, lim);
+            tc_fence_after();
+          }
           float gu[8], gr[8], gg[8];
-          tmem_ld8(gcol + (uint32_t)(8 * g8), gu);
-          tmem_ld8(gcol + (uint32_t)(C::CU + 8 * g8), gr);
-          tmem_ld8(gcol + (uint32_t)(2 * C::CU + 8 * g8), gg);
+          tmem_ld8(gcol(ug), gu);
+          tmem_ld8(gcol(ug) + (uint32_t)C::CU, gr);
+          tmem_ld8(gcol(ug) + (uint32_t)(2 * C::CU), gg);
           tmem_wait_ld();
           float su[8], sr[8], sc[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int i = 8 * g8 + u, un = u0 + i;
-            const float uu = sigm_f(gu[u] + tb[i]), rr = sigm_f(gr[u] + tb[DH + i]);
-            const float cc = tanh_f(fmaf(rr, gg[u] + sbh[un], tb[2 * DH + i]));
+            const int i = 8 * g8 + u, un = ug + u;
+            const float uu = sigm_f(gu[u] + tb[un]), rr = sigm_f(gr[u] + tb[DH + un]);
+            const float cc = tanh_f(fmaf(rr, gg[u] + sbh[un], tb[2 * DH + un]));
             const float hn = fmaf(uu, cc - hp[i], hp[i]);
             if (SMP) { su[u] = uu; sr[u] = rr; sc[u] = cc; gg[u] += sbh[un]; gu[u] = hp[i]; }
             hp[i] = hn;
@@ -577,20 +597,22 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
               reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
             };
             if (grow) {
-              st8(grow + 8 * g8, su);
-              st8(grow + DH + 8 * g8, sr);
-              st8(grow + 2 * DH + 8 * g8, sc);
-              st8(grow + 3 * DH + 8 * g8, gg);
-              st8(grow + 4 * DH + 8 * g8, gu);
+              st8(grow + ug, su);
+              st8(grow + DH + ug, sr);
+              st8(grow + 2 * DH + ug, sc);
+              st8(grow + 3 * DH + ug, gg);
+              st8(grow + 4 * DH + ug, gu);
             }
-            st8(a.hcache_out + ((int64_t)s * N + k) * DH + u0 + 8 * g8, hp + 8 * g8);
+            st8(a.hcache_out + ((int64_t)s * N + k) * DH + ug, hp + 8 * g8);
           }
         }
-        if (chunk != C::NCH - 1 &&
+        if (!dok) { ok = false; break; }
+        // every chunk of the gate product has read the planes before h_k goes in
+        if (!SPLIT && chunk != C::NCH - 1 &&
             !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort, lim)) { ok = false; break; }
         ++pd2;
 #pragma unroll
-        for (int g8 = 0; g8 < G8; ++g8) planes8<DH>(Sh, row, u0 + 8 * g8, hp + 8 * g8);
+        for (int g8 = 0; g8 < G8; ++g8) planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
         if (part > 0) {
           zx[(part - 1) * C::TR + row] = make_float4(z0, z1, z2, z3);
         } else {

@@ -45,23 +45,6 @@ template <int DH> struct JtShape {
   static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + sizeof(float) * 128 * TRS + 64;
 };
 
-// Byte offset of element k (< 16) of row r in a non-swizzled K-major block:
-// core matrices of 8 rows x 16 bytes, the two K halves 128 bytes apart, 8-row
-// groups 256 bytes apart.
-__device__ __forceinline__ uint32_t kmaj_off(int r, int k) {
-  return (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
-         (uint32_t)(k & 7) * 2u;
-}
-
-__device__ __forceinline__ uint64_t kmaj_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);  // start address
-  d |= (uint64_t)(128 >> 4) << 16;        // leading byte offset: next core matrix in K
-  d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                 // descriptor version (tcgen05)
-  return d;                               // layout 0: no swizzle
-}
-
 // Stage layout: A block (ks, plane, tile) at ((ks * 2 + plane) * 3 + tile)
 // * JT_ASUB, then B block (ks, plane) at A_BYTES + (ks * 2 + plane) * BSUB.
 template <int DH>

@@ -482,6 +482,20 @@ nqs_status jac_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, T *O, cudaStream_
         j.err = W<int>(c, c->off.sstat);
         return cu(jac_tc_run(j, c->rd.sm_count, st));
       }
+      if (gram_tc_available() && jac2d_tc_supported(c->L.dim, c->L.dh)) {
+        // mixed 2D lattices: the rows of O as tensor-core products
+        Jac2dTcArgs j{};
+        j.N = N; j.Lx = c->L.Lx; j.cplx = c->L.cplx; j.dh = c->L.dh;
+        j.ns = ns; j.nrows = R; j.spins = spins;
+        j.hcache = b.hcache; j.adj = b.adj; j.adjw = c->adjw;
+        j.odz = 4 * c->L.dh; j.odhp = 4 * c->L.dh + 4; j.ohp = 5 * c->L.dh + 4;
+        j.O = O; j.np = c->L.np;
+        j.U1 = c->L.U1; j.U2 = c->L.U2; j.Wu = c->L.Wu; j.bu = c->L.bu; j.Wr = c->L.Wr;
+        j.br = c->L.br; j.Wh = c->L.Wh; j.bh = c->L.bh; j.Win = c->L.Win; j.bin = c->L.bin;
+        j.Uo = c->L.Uo; j.co = c->L.co; j.Up = c->L.Up; j.cp = c->L.cp;
+        j.err = W<int>(c, c->off.sstat);
+        return cu(jac2d_tc_run(j, c->rd.sm_count, st));
+      }
     }
     return cu(run_grad<T>(c->rd, g, st));
   }

@@ -136,6 +136,23 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Byte offset of element k (< 16) of row r in a non-swizzled K-major block:
+// core matrices of 8 rows x 16 bytes, the two K halves 128 bytes apart, 8-row
+// groups 256 bytes apart.
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k) {
+  return (uint32_t)(r >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ uint64_t kmaj_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);  // start address
+  d |= (uint64_t)(128 >> 4) << 16;        // leading byte offset: next core matrix in K
+  d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                 // descriptor version (tcgen05)
+  return d;                               // layout 0: no swizzle
+}
+
 // Byte offset of element k (bf16) of row r in a K-major tile whose rows are
 // 128 bytes with the 128-byte swizzle (16-byte chunk index XOR row mod 8).
 __device__ __forceinline__ uint32_t sw128_off(int r, int k) {

@@ -413,6 +413,42 @@ def test_jacobian_2d_warp_mma_mixed(model, ham, ns):
     assert np.max(np.abs(J - J_o) / scale) < TOL_MIXED_JAC
 
 
+# 2D lattices of hidden size 32, 64, 96 and 128 assemble the five large
+# weight blocks of every row of O (W_u, W_r, W_h on h'; U1, U2) as
+# tensor-core products over the sites, the rest of the row on SIMT: chains
+# that are not a multiple of the 16-site chunk, real and complex heads (two
+# rows per sample), a tile of gate adjoints only partly filled (d_h 96: 288
+# of 384 rows), the mask
+E2DJT_MODELS = [
+    (ModelSpec(2, 5, 3, 32, cplx=1, marshall=1), HamSpec("j1j2", J1=1.0, J2=0.5), 90),
+    (ModelSpec(2, 4, 5, 96, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.25), 70),
+    (ModelSpec(2, 3, 7, 128), HamSpec("j1j2", J1=1.0, J2=0.0), 60),
+    (ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J1=1.0, J2=0.5), 50),
+]
+
+
+@pytest.mark.parametrize("model,ham,ns", E2DJT_MODELS,
+                         ids=["5x3_dh32_c", "4x5_dh96_cmask", "3x7_dh128", "4x4_dh128_cmask"])
+def test_jacobian_2d_tensor_core_blocks_mixed(model, ham, ns):
+    from paper_2608_18065_b300.inputs import param_blocks
+    c = ctx(model, ham, "mixed", ns)
+    th, thd = theta_dev(model, 8)
+    sp = random_spins(model, ns, seed=17, zero_mag=bool(model.zmask))
+    J = c.jacobian(thd, torch.tensor(sp, device="cuda")).cpu().numpy().astype(np.float64)
+    J_o = O.jacobian(model, th, sp)
+    assert J.shape == J_o.shape
+    scale = np.max(np.abs(J_o), axis=1, keepdims=True)
+    assert np.max(np.abs(J - J_o) / scale) < TOL_MIXED_JAC
+    # block by block against each block's own largest entry
+    off = 0
+    for name, r, cols, _ in param_blocks(model):
+        sl = slice(off, off + r * cols)
+        off += r * cols
+        bmax = np.max(np.abs(J_o[:, sl]))
+        assert np.max(np.abs(J[:, sl] - J_o[:, sl])) <= 5e-3 * bmax, name
+    record_error(f"jac2d_tc_{model.Lx}x{model.Ly}_dh{model.dh}", O_row=max_row_err(J, J_o))
+
+
 def test_refinement_falls_back_to_fp64_when_fp32_factor_fails():
     """A matrix whose FP32 Cholesky breaks down (kappa ~ 1e12) but is SPD in
     FP64: the mixed context must still return the FP64 solution."""
