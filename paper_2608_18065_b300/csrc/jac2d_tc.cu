@@ -50,22 +50,30 @@ template <int DH> struct J2 {
   static constexpr int COLS = TG * NG > BROWS ? TG * NG : BROWS;
   static constexpr int TCOLS = COLS > 256 ? 512 : 256;
   static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + sizeof(float) * 128 * J2_TRS + 64;
-  // value pairs (two consecutive sites of one column) per thread and chunk
-  static constexpr int P1 = J2_KC * DH / J2_THREADS / 2;
-  static_assert(J2_KC * DH % (2 * J2_THREADS) == 0, "whole site pairs per thread");
   static_assert(TG <= 3 && COLS <= 512 && NU0 <= 256, "MMA shapes, tensor memory");
   static_assert(SMEM <= 227 * 1024, "one CTA per SM");
 };
 
-// hi, lo planes of the pair (v0, v1) at sites kk, kk + 1 (kk even) of row r
-__device__ __forceinline__ void put_pair2(unsigned char *hi, unsigned char *lo, int r, int kk,
-                                          float v0, float v1) {
-  const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-  const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-  const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-  const uint32_t o = kmaj_off(r, kk & 15);
-  *reinterpret_cast<__nv_bfloat162 *>(hi + o) = __halves2bfloat162(h0, h1);
-  *reinterpret_cast<__nv_bfloat162 *>(lo + o) = __halves2bfloat162(l0, l1);
+// BF16 hi and lo of (x0, x1) as packed pairs (x0 in the low half)
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+  const float r0 = x0 - __uint_as_float(hi << 16), r1 = x1 - __uint_as_float(hi & 0xffff0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r1), "f"(r0));
+}
+
+// rows r .. r + 3 of a K-major block at sites kk, kk + 1 (kk even): the
+// values of site kk in v0, of site kk + 1 in v1
+__device__ __forceinline__ void put_quad(unsigned char *hi, unsigned char *lo, int r, int kk,
+                                         float4 v0, float4 v1) {
+  const float a0[4] = {v0.x, v0.y, v0.z, v0.w}, a1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint32_t h, l;
+    split2(a0[i], a1[i], h, l);
+    const uint32_t o = kmaj_off(r + i, kk & 15);
+    *reinterpret_cast<uint32_t *>(hi + o) = h;
+    *reinterpret_cast<uint32_t *>(lo + o) = l;
+  }
 }
 
 // an exact value (0 or 1): lo plane zero
@@ -76,56 +84,75 @@ __device__ __forceinline__ void put_exact(unsigned char *hi, unsigned char *lo, 
   *reinterpret_cast<__nv_bfloat16 *>(lo + o) = __float2bfloat16_rn(0.f);
 }
 
-// One chunk (sites 16 c .. 16 c + 15) of an item in registers: value pairs
-// of one column each (columns contiguous over the threads, coalesced loads;
-// zero past the chain), the one-hot word of one site, one head adjoint.
+// Work units of a chunk: (site pair, four consecutive columns) of a column
+// range of C values per site; unit counts per thread.
+template <int C> struct Units {
+  static constexpr int N = 8 * (C / 4), PER = (N + J2_THREADS - 1) / J2_THREADS;
+  static_assert(C % 4 == 0, "column quads");
+};
+
+// One chunk (sites 16 c .. 16 c + 15) of an item in registers: per work
+// unit the four columns at the two sites (coalesced 16-byte loads; zero past
+// the chain), the one-hot word of one site, one head adjoint.
 template <int DH> struct Chunk2 {
-  float g[3 * J2<DH>::P1][2];  // gates: dau | dar | dg;  rest: dh' | dac | (unused)
-  float b[3 * J2<DH>::P1][2];  // gates: h' (first P1);  rest: h_hor | h_ver | h_k
-  float z;                     // rest: dz of (site, component) tid / 4, tid % 4
-  int x;                       // one-hot bits of site tid / 16 (bit 4: inside the chain)
+  static constexpr int UA = Units<3 * DH>::PER > Units<2 * DH>::PER ? Units<3 * DH>::PER : Units<2 * DH>::PER;
+  static constexpr int UB = Units<3 * DH>::PER;
+  float4 a[UA][2];  // gates: dau | dar | dg;  rest: dh' | dac
+  float4 b[UB][2];  // gates: h';  rest: h_hor | h_ver | h_k
+  float z;          // rest: dz of (site, component) tid / 4, tid % 4
+  int x;            // one-hot bits of site tid / 16 (bit 4: inside the chain)
 };
 
 template <int DH>
 __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int64_t row, int pass,
                                        int c, int tid) {
-  constexpr int P1 = J2<DH>::P1;
   const int N = a.N, Lx = a.Lx, k0 = c * J2_KC;
   const int64_t s = row % a.ns;
   const float *arow = a.adj + row * (int64_t)N * a.adjw;
   const float *hrow = a.hcache + s * (int64_t)N * DH;
-  auto rec = [&](int k, int off) { return k < N ? __ldcg(arow + (int64_t)k * a.adjw + off) : 0.f; };
-  auto hst = [&](int k, int b) { return k >= 0 && k < N ? __ldcg(hrow + (int64_t)k * DH + b) : 0.f; };
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto rec = [&](int k, int off) {
+    return k < N ? __ldcg(reinterpret_cast<const float4 *>(arow + (int64_t)k * a.adjw + off)) : zero;
+  };
+  auto hst = [&](int k, int b) {
+    return k >= 0 && k < N ? __ldcg(reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH + b)) : zero;
+  };
   if (pass == 0) {
+    using UA = Units<3 * DH>;
 #pragma unroll
-    for (int q = 0; q < 3 * P1; ++q) {  // dau | dar | dg: record columns 0 .. 3 dh
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH), m = e - kp * (3 * DH), k = k0 + 2 * kp;
-      r.g[q][0] = rec(k, m);
-      r.g[q][1] = rec(k + 1, m);
+    for (int q = 0; q < UA::PER; ++q) {  // dau | dar | dg: record columns 0 .. 3 dh
+      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), m = 4 * (e - kp * (3 * DH / 4));
+      const int k = k0 + 2 * kp;
+      r.a[q][0] = e < UA::N ? rec(k, m) : zero;
+      r.a[q][1] = e < UA::N ? rec(k + 1, m) : zero;
     }
+    using UB = Units<DH>;
 #pragma unroll
-    for (int q = 0; q < P1; ++q) {  // h'
-      const int e = tid + q * J2_THREADS, kp = e / DH, n = e - kp * DH, k = k0 + 2 * kp;
-      r.b[q][0] = rec(k, a.ohp + n);
-      r.b[q][1] = rec(k + 1, a.ohp + n);
+    for (int q = 0; q < UB::PER; ++q) {  // h'
+      const int e = tid + q * J2_THREADS, kp = e / (DH / 4), n = 4 * (e - kp * (DH / 4));
+      const int k = k0 + 2 * kp;
+      r.b[q][0] = e < UB::N ? rec(k, a.ohp + n) : zero;
+      r.b[q][1] = e < UB::N ? rec(k + 1, a.ohp + n) : zero;
     }
   } else {
+    using UA = Units<2 * DH>;
 #pragma unroll
-    for (int q = 0; q < 2 * P1; ++q) {  // dh' | dac
-      const int e = tid + q * J2_THREADS, kp = e / (2 * DH), m = e - kp * (2 * DH), k = k0 + 2 * kp;
-      const int off = m < DH ? a.odhp + m : 3 * DH + (m - DH);
-      r.g[q][0] = rec(k, off);
-      r.g[q][1] = rec(k + 1, off);
+    for (int q = 0; q < UA::PER; ++q) {  // dh' | dac
+      const int e = tid + q * J2_THREADS, kp = e / (2 * DH / 4), m = 4 * (e - kp * (2 * DH / 4));
+      const int k = k0 + 2 * kp, off = m < DH ? a.odhp + m : 3 * DH + (m - DH);
+      r.a[q][0] = e < UA::N ? rec(k, off) : zero;
+      r.a[q][1] = e < UA::N ? rec(k + 1, off) : zero;
     }
+    using UB = Units<3 * DH>;
 #pragma unroll
-    for (int q = 0; q < 3 * P1; ++q) {  // h_hor | h_ver | h_k
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH), n = e - kp * (3 * DH);
+    for (int q = 0; q < UB::PER; ++q) {  // h_hor | h_ver | h_k
+      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), n = 4 * (e - kp * (3 * DH / 4));
       const int part = n / DH, b = n - part * DH;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = k0 + 2 * kp + h;
         int src = -1;
-        if (k < N) {
+        if (e < UB::N && k < N) {
           const int m = k % Lx;
           src = part == 0 ? (m != 0 ? k - 1 : -1) : part == 1 ? (k >= Lx ? k - 2 * m - 1 : -1) : k;
         }
@@ -133,7 +160,10 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
       }
     }
     r.z = 0.f;
-    if (tid < 4 * J2_KC) r.z = rec(k0 + (tid >> 2), a.odz + (tid & 3));
+    if (tid < 4 * J2_KC) {
+      const int k = k0 + (tid >> 2);
+      r.z = k < N ? __ldcg(arow + (int64_t)k * a.adjw + a.odz + (tid & 3)) : 0.f;
+    }
   }
   r.x = 0;
   if ((tid & 15) == 0) {  // one-hot word of site tid / 16
@@ -152,31 +182,35 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
 template <int DH>
 __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage, int pass, int tid) {
   using S = J2<DH>;
-  constexpr int P1 = S::P1;
   unsigned char *bh = stage + S::A_BYTES, *bl = bh + S::BSUB;
   // the one-hot word of each site goes from its thread to the whole warp set
   const int xk = __shfl_sync(0xffffffffu, r.x, (tid & 16));  // site tid / 16 (two sites per warp)
   const int kk = tid >> 4, j = tid & 15;
   const float sv = j == 0 ? (float)((xk >> 4) & 1) : (j <= 4 ? (float)((xk >> (j - 1)) & 1) : 0.f);
   if (pass == 0) {
+    using UA = Units<3 * DH>;
 #pragma unroll
-    for (int q = 0; q < 3 * P1; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH), m = e - kp * (3 * DH);
+    for (int q = 0; q < UA::PER; ++q) {
+      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), m = 4 * (e - kp * (3 * DH / 4));
       const int t = m >> 7;
-      put_pair2(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, m & 127, 2 * kp, r.g[q][0], r.g[q][1]);
+      if (e < UA::N)
+        put_quad(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, m & 127, 2 * kp, r.a[q][0], r.a[q][1]);
     }
+    using UB = Units<DH>;
 #pragma unroll
-    for (int q = 0; q < P1; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / DH, n = e - kp * DH;
-      put_pair2(bh, bl, n, 2 * kp, r.b[q][0], r.b[q][1]);
+    for (int q = 0; q < UB::PER; ++q) {
+      const int e = tid + q * J2_THREADS, kp = e / (DH / 4), n = 4 * (e - kp * (DH / 4));
+      if (e < UB::N) put_quad(bh, bl, n, 2 * kp, r.b[q][0], r.b[q][1]);
     }
     put_exact(bh, bl, DH + j, kk, sv);  // [1, x_0 .. x_3, 0 ..]
   } else {
+    using UA = Units<2 * DH>;
 #pragma unroll
-    for (int q = 0; q < 2 * P1; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (2 * DH), m = e - kp * (2 * DH);
+    for (int q = 0; q < UA::PER; ++q) {
+      const int e = tid + q * J2_THREADS, kp = e / (2 * DH / 4), m = 4 * (e - kp * (2 * DH / 4));
       const int t = m < DH ? 0 : 1, rr = m < DH ? m : m - DH;
-      put_pair2(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, rr, 2 * kp, r.g[q][0], r.g[q][1]);
+      if (e < UA::N)
+        put_quad(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, rr, 2 * kp, r.a[q][0], r.a[q][1]);
     }
     if (tid < 4 * J2_KC) {  // dz into rows 0..3 of tile 2
       const __nv_bfloat16 h = __float2bfloat16_rn(r.z);
@@ -185,45 +219,61 @@ __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage
       *reinterpret_cast<__nv_bfloat16 *>(stage + 2 * J2_ASUB + o) = h;
       *reinterpret_cast<__nv_bfloat16 *>(stage + 5 * J2_ASUB + o) = l;
     }
+    using UB = Units<3 * DH>;
 #pragma unroll
-    for (int q = 0; q < 3 * P1; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH), n = e - kp * (3 * DH);
+    for (int q = 0; q < UB::PER; ++q) {
+      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), n = 4 * (e - kp * (3 * DH / 4));
       // rows: h_hor, h_ver at 0 .. 2 dh; h_k after the 16 one-hot rows
       const int rr = n < 2 * DH ? n : n + S::NU1;
-      put_pair2(bh, bl, rr, 2 * kp, r.b[q][0], r.b[q][1]);
+      if (e < UB::N) put_quad(bh, bl, rr, 2 * kp, r.b[q][0], r.b[q][1]);
     }
     put_exact(bh, bl, S::NU0 + j, kk, sv);                                   // [1; x]
     put_exact(bh, bl, S::NU0 + S::NU1 + DH + j, kk, j == 0 ? sv : 0.f);     // h_k's [1]
   }
 }
 
-// Entry c of accumulator row r of tile t of an item into the row of O, or
-// -1 (padding, and the W_h input columns, which do not exist).
+// Row r of tile t of an item into the row of O: its nc accumulator entries
+// from column cb on (a block of the transpose buffer at v), one warp.
 template <int DH>
-__device__ __forceinline__ int64_t dest2(const Jac2dTcArgs &a, int pass, int t, int r, int c) {
+__device__ __forceinline__ void write_row2(const Jac2dTcArgs &a, float *orow, int pass, int t,
+                                           int r, int cb, int nc, const float *v, int lane) {
   using S = J2<DH>;
   const int w = DH + 4;  // row length of W_u and W_r: h part, then the four input columns
   if (pass == 0) {
     const int m = 128 * t + r;
-    if (m >= 3 * DH || c >= DH + 5) return -1;
+    if (m >= 3 * DH) return;
     const int blk = m / DH, q = m - blk * DH;
-    if (c < DH) return blk == 0 ? a.Wu + (int64_t)q * w + c
-                     : blk == 1 ? a.Wr + (int64_t)q * w + c : a.Wh + (int64_t)q * DH + c;
-    if (c == DH) return (blk == 0 ? a.bu : blk == 1 ? a.br : a.bh) + q;
-    if (blk == 2) return -1;
-    return (blk == 0 ? a.Wu : a.Wr) + (int64_t)q * w + DH + (c - DH - 1);
+    float *hb = orow + (blk == 0 ? a.Wu + (int64_t)q * w : blk == 1 ? a.Wr + (int64_t)q * w
+                                                                  : a.Wh + (int64_t)q * DH);
+    float *bias = orow + (blk == 0 ? a.bu : blk == 1 ? a.br : a.bh) + q;
+    for (int cc = lane; cc < nc; cc += 32) {
+      const int c = cb + cc;
+      if (c < DH) hb[c] = v[cc];
+      else if (c == DH) *bias = v[cc];
+      else if (c <= DH + 4 && blk < 2) hb[c - 1] = v[cc];  // x-column c - DH - 1 at DH + (c - DH - 1)
+    }
+  } else if (t == 0) {
+    if (r >= DH) return;
+    float *u1 = orow + a.U1 + (int64_t)r * DH, *u2 = orow + a.U2 + (int64_t)r * DH - DH;
+    for (int cc = lane; cc < nc; cc += 32) {
+      const int c = cb + cc;
+      if (c < DH) u1[c] = v[cc];
+      else u2[c] = v[cc];
+    }
+  } else if (t == 1) {
+    if (r >= DH) return;
+    if (lane == 0) orow[a.bin + r] = v[0];
+    if (lane >= 1 && lane <= 4) orow[a.Win + (int64_t)r * 4 + (lane - 1)] = v[lane];
+  } else {
+    if (r >= (a.cplx ? 4 : 2)) return;
+    float *hd = orow + (r < 2 ? a.Uo + (int64_t)r * DH : a.Up + (int64_t)(r - 2) * DH);
+    for (int cc = lane; cc < nc; cc += 32) {
+      const int c = cb + cc;
+      if (c < DH) hd[c] = v[cc];
+      else if (c == DH) orow[r < 2 ? a.co + r : a.cp + (r - 2)] = v[cc];
+    }
   }
-  if (t == 0) {
-    if (r >= DH || c >= S::NU0) return -1;
-    return c < DH ? a.U1 + (int64_t)r * DH + c : a.U2 + (int64_t)r * DH + (c - DH);
-  }
-  if (t == 1) {
-    if (r >= DH || c >= 5) return -1;
-    return c == 0 ? a.bin + r : a.Win + (int64_t)r * 4 + (c - 1);
-  }
-  if (r >= (a.cplx ? 4 : 2) || c > DH) return -1;
-  if (c < DH) return (r < 2 ? a.Uo + (int64_t)r * DH : a.Up + (int64_t)(r - 2) * DH) + c;
-  return r < 2 ? a.co + r : a.cp + (r - 2);
+  (void)S::NU0;
 }
 
 template <int DH>
@@ -336,13 +386,8 @@ __global__ void __launch_bounds__(J2_THREADS, 1) k_jac2d_tc(const Jac2dTcArgs a)
           }
         }
         __syncthreads();
-        for (int r = warp; r < 128; r += J2_THREADS / 32) {
-          if (dest2<DH>(a, pass, t, r, cb) < 0 && dest2<DH>(a, pass, t, r, 0) < 0) continue;
-          for (int cc = lane; cc < nc; cc += 32) {
-            const int64_t d = dest2<DH>(a, pass, t, r, cb + cc);
-            if (d >= 0) orow[d] = tr[r * J2_TRS + cc];
-          }
-        }
+        for (int r = warp; r < 128; r += J2_THREADS / 32)
+          write_row2<DH>(a, orow, pass, t, r, cb, nc, tr + r * J2_TRS, lane);
         __syncthreads();
       }
     }
