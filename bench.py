@@ -809,6 +809,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    batch_graph = bool(b.graph_active())
     ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     value = aggregate_rate(world, K, ms)
     st = [nqs.decode_stats(stats[i]) for i in range(n)]
@@ -928,7 +929,7 @@ def run_batched(args):
                 "gram_tflops": gram_fl / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches * K), "clocks": clk,
-                "cuda_graph": True if not args.no_graph else False,
+                "cuda_graph": batch_graph,
                 "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
                 "fp64_path": fp64, "matched_energy": matched, "per_config": per_config,
                 "errors_vs_oracle": load_errors(),

@@ -370,8 +370,11 @@ nqs_status nqs_batch_graph_active(const nqs_batch *b, int *active);
 nqs_status nqs_batch_set_concurrency(nqs_batch *b, int streams);
 nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams);
 
-/* nqs_autotune for every instance, then the concurrency, chosen by timing
- * whole batched steps (best of two) on the workspace copies of theta; the
+/* nqs_autotune for every instance, then, by timing whole batched steps
+ * (best of two or three) on the workspace copies of theta: the concurrency,
+ * the fraction of the SMs each instance's cooperative solve takes, and, if
+ * graphs are enabled (nqs_batch_set_graph), whether a graph replay or the
+ * eager launches are faster (graphs stay off when they are not).  The
  * fastest batched step time goes to *step_ms (may be NULL).  Synchronous;
  * the callers' thetas are not modified. */
 nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,

@@ -710,7 +710,12 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
     const size_t smem = chol_blk_smem();
     CU(cudaFuncSetAttribute((const void *)k_chol_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem));
-    const int Gb = std::min(G, c->rd.sm_count);
+    // no more CTAs than the first panel has trailing tiles (plus the CTA
+    // that factors the diagonal blocks): the rest of the SMs stay free for
+    // the other instances of a batch
+    const int64_t nr = (R + BKB - 1) / BKB - 1;
+    const int Gb = (int)std::max<int64_t>(2, std::min<int64_t>(std::min(G, c->rd.sm_count),
+                                                                 nr * (nr + 1) / 2 + 1));
     void *args[] = {&bk};
     c->launches += 1;
     CU(cudaLaunchCooperativeKernel((const void *)k_chol_blk, dim3(Gb), dim3(BKB_THREADS), args, smem,
@@ -2088,7 +2093,24 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
       if (it != g_tune_cache.end()) it->second.solve_grid = b->ctx[i]->t_solve_grid;
     }
   }
+  // (4) one graph replay per step, or the launches themselves, whichever is
+  // faster for this batch (a captured step can order the instances' kernels
+  // less favourably than the eager issue)
   b->graph_enabled = saved_graph;
+  if (saved_graph && s == NQS_OK) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    double gms = 0;
+    s = best_ms(st, 3, [&] {
+      for (int i = 0; i < n; ++i) {
+        const int64_t np = b->ctx[i]->L.np;
+        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
+      }
+      return NQS_OK;
+    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &gms);
+    if (s == NQS_OK && gms > best) b->graph_enabled = 0;
+    else if (s == NQS_OK) best = gms;
+  }
   if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
   if (step_ms) *step_ms = best;
   return s;
