@@ -294,9 +294,11 @@ def stage_rooflines(w, ms, sites, R, np_):
     library).  sample, jac_bwd, jac_grad: FP32 (FP64) FMA-pipe work of the
     recurrence, N_s N (sample) or R N (reverse sweep, O assembly) sites of
     site_flops each (the mixed 1D O assembly on the tensor cores is
-    reported by its HBM bytes).  cholesky: n^3/3 factor + n^3/3 triangular inverse
-    (n = R) in FP32 for the mixed path (refinement sweeps: 2n^2 each, not
-    counted).  gram: BF16x3 tensor work 3 R(R+1) Np.  center: HBM bytes of
+    reported by its HBM bytes, as is the mixed 2D one; mixed 2D sampling at
+    d_h 96 / 128 runs on the tensor cores and is reported by its BF16x3
+    products).  cholesky: n^3/3 factor (128-wide panels, R >= 1024) or n^3/3
+    factor + n^3/3 triangular inverse (32-wide panels) in FP32 for the mixed
+    path (refinement sweeps: 2n^2 each, not counted).  gram: BF16x3 tensor work 3 R(R+1) Np.  center: HBM bytes of
     the column sums and the split (read O twice, write hi and lo)."""
     out = {}
     f32 = w.precision == "mixed"
@@ -320,9 +322,33 @@ def stage_rooflines(w, ms, sites, R, np_):
             out["eloc_suffix"] = eloc_roofline(w, ms["eloc_suffix"], sites)
         else:
             alu("eloc_suffix", "k_forward<MODE_ELOC>", sites * sf)
-    alu("sample", "k_forward<MODE_SAMPLE>", w.hp.ns * N * sf)
+    dh = w.model.dh
+    if f32 and w.model.dim == 2 and dh in (96, 128) and 2 * w.model.Lx - 1 <= 31 \
+            and ms.get("sample", 0) > 0:
+        # sampling on the streamed tensor-core engine: per sample and site the
+        # products [U1; U2] h (2 dh x dh) and W h' (3 dh x dh), BF16x3
+        t = ms["sample"]
+        fl = w.hp.ns * N * 3 * 2 * (2 * dh * dh + 3 * dh * dh)
+        pk, src = measured_peak("bf16_tflops_sustained", 1400.0)
+        a = fl / (t * 1e-3) / 1e12
+        out["sample"] = {"kernel": "k_eloc2d_tcs (sampling)", "bound": "tensor", "achieved": a,
+                         "peak": pk, "unit": "TFLOP/s", "frac": a / pk, "traffic": None,
+                         "peak_source": src + ", BF16 dense, sustained", "flops_per_launch": fl,
+                         "ms_per_launch": t}
+    else:
+        alu("sample", "k_forward<MODE_SAMPLE>", w.hp.ns * N * sf)
     alu("jac_bwd", "k_jac_bwd", R * N * sf)
-    if f32 and w.model.dim == 1 and w.model.dh in (32, 64) and ms.get("jac_grad", 0) > 0:
+    if f32 and w.model.dim == 2 and dh in (32, 64, 96, 128) and ms.get("jac_grad", 0) > 0:
+        # tensor-core rows of O: HBM reads of the adjoint records (6 dh + 4
+        # per site and row) and the states, write of O
+        t = ms["jac_grad"]
+        byts = R * N * (6 * dh + 4) * 4 + w.hp.ns * N * dh * 4 + R * np_ * 4
+        pk, src = measured_peak("hbm_gbs", 6400.0)
+        a = byts / (t * 1e-3) / 1e9
+        out["jac_grad"] = {"kernel": "k_jac2d_tc", "bound": "hbm", "achieved": a, "peak": pk,
+                           "unit": "GB/s", "frac": a / pk, "traffic": None, "peak_source": src,
+                           "bytes_per_launch": byts, "ms_per_launch": t}
+    elif f32 and w.model.dim == 1 and w.model.dh in (32, 64) and ms.get("jac_grad", 0) > 0:
         # tensor-core O assembly: HBM-bound reads of the adjoint records and
         # states, write of O
         t = ms["jac_grad"]
@@ -335,7 +361,10 @@ def stage_rooflines(w, ms, sites, R, np_):
                            "bytes_per_launch": byts, "ms_per_launch": t}
     else:
         alu("jac_grad", "k_jac_grad", R * N * sf)
-    alu("cholesky", "k_chol_ir" if f32 else "k_chol_coop", 2 * R ** 3 / 3)
+    if f32 and R >= 1024 and R % 4 == 0:
+        alu("cholesky", "k_chol_blk", R ** 3 / 3)  # 128-wide panels: the factor
+    else:
+        alu("cholesky", "k_chol_ir" if f32 else "k_chol_coop", 2 * R ** 3 / 3)
     if ms.get("gram", 0) > 0:
         t = ms["gram"]
         if f32:
