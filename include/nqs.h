@@ -325,6 +325,13 @@ nqs_status nqs_clear_tuning(nqs_ctx *ctx);
  * and takes the 32-wide one otherwise.  Every form ends at FP64 backward
  * error or in the FP64 Cholesky.  NQS_ERR_ARG for another value. */
 nqs_status nqs_set_solve_form(nqs_ctx *ctx, int form);
+/* Sampler of a mixed 2D context of hidden size 96 or 128 with every state
+ * cached (Sec. II.A): 1 (or -1, the built-in choice) the streamed
+ * tensor-core engine, 0 the recurrence kernels.  Both draw with the same
+ * Philox uniforms and decide in FP32; their conditionals differ by the
+ * rounding of their products.  Other contexts always take the recurrence
+ * kernels.  NQS_ERR_ARG for another value. */
+nqs_status nqs_set_sampler(nqs_ctx *ctx, int form);
 
 /* ------------------------------------------------------ batched instances */
 

@@ -85,7 +85,9 @@ __device__ __forceinline__ void put_exact(unsigned char *hi, unsigned char *lo, 
 }
 
 // Work units of a chunk: (site pair, four consecutive columns) of a column
-// range of C values per site; unit counts per thread.
+// range of C values per site, the site pair fastest over the threads (so that
+// a warp's stores of one row quad fall in eight banks, not two); unit counts
+// per thread.
 template <int C> struct Units {
   static constexpr int N = 8 * (C / 4), PER = (N + J2_THREADS - 1) / J2_THREADS;
   static_assert(C % 4 == 0, "column quads");
@@ -121,7 +123,7 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
     using UA = Units<3 * DH>;
 #pragma unroll
     for (int q = 0; q < UA::PER; ++q) {  // dau | dar | dg: record columns 0 .. 3 dh
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), m = 4 * (e - kp * (3 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, m = 4 * (e >> 3);
       const int k = k0 + 2 * kp;
       r.a[q][0] = e < UA::N ? rec(k, m) : zero;
       r.a[q][1] = e < UA::N ? rec(k + 1, m) : zero;
@@ -129,7 +131,7 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
     using UB = Units<DH>;
 #pragma unroll
     for (int q = 0; q < UB::PER; ++q) {  // h'
-      const int e = tid + q * J2_THREADS, kp = e / (DH / 4), n = 4 * (e - kp * (DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, n = 4 * (e >> 3);
       const int k = k0 + 2 * kp;
       r.b[q][0] = e < UB::N ? rec(k, a.ohp + n) : zero;
       r.b[q][1] = e < UB::N ? rec(k + 1, a.ohp + n) : zero;
@@ -138,7 +140,7 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
     using UA = Units<2 * DH>;
 #pragma unroll
     for (int q = 0; q < UA::PER; ++q) {  // dh' | dac
-      const int e = tid + q * J2_THREADS, kp = e / (2 * DH / 4), m = 4 * (e - kp * (2 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, m = 4 * (e >> 3);
       const int k = k0 + 2 * kp, off = m < DH ? a.odhp + m : 3 * DH + (m - DH);
       r.a[q][0] = e < UA::N ? rec(k, off) : zero;
       r.a[q][1] = e < UA::N ? rec(k + 1, off) : zero;
@@ -146,7 +148,7 @@ __device__ __forceinline__ void fetch2(const Jac2dTcArgs &a, Chunk2<DH> &r, int6
     using UB = Units<3 * DH>;
 #pragma unroll
     for (int q = 0; q < UB::PER; ++q) {  // h_hor | h_ver | h_k
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), n = 4 * (e - kp * (3 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, n = 4 * (e >> 3);
       const int part = n / DH, b = n - part * DH;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -191,7 +193,7 @@ __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage
     using UA = Units<3 * DH>;
 #pragma unroll
     for (int q = 0; q < UA::PER; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), m = 4 * (e - kp * (3 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, m = 4 * (e >> 3);
       const int t = m >> 7;
       if (e < UA::N)
         put_quad(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, m & 127, 2 * kp, r.a[q][0], r.a[q][1]);
@@ -199,7 +201,7 @@ __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage
     using UB = Units<DH>;
 #pragma unroll
     for (int q = 0; q < UB::PER; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (DH / 4), n = 4 * (e - kp * (DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, n = 4 * (e >> 3);
       if (e < UB::N) put_quad(bh, bl, n, 2 * kp, r.b[q][0], r.b[q][1]);
     }
     put_exact(bh, bl, DH + j, kk, sv);  // [1, x_0 .. x_3, 0 ..]
@@ -207,7 +209,7 @@ __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage
     using UA = Units<2 * DH>;
 #pragma unroll
     for (int q = 0; q < UA::PER; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (2 * DH / 4), m = 4 * (e - kp * (2 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, m = 4 * (e >> 3);
       const int t = m < DH ? 0 : 1, rr = m < DH ? m : m - DH;
       if (e < UA::N)
         put_quad(stage + t * J2_ASUB, stage + (3 + t) * J2_ASUB, rr, 2 * kp, r.a[q][0], r.a[q][1]);
@@ -222,7 +224,7 @@ __device__ __forceinline__ void store2(const Chunk2<DH> &r, unsigned char *stage
     using UB = Units<3 * DH>;
 #pragma unroll
     for (int q = 0; q < UB::PER; ++q) {
-      const int e = tid + q * J2_THREADS, kp = e / (3 * DH / 4), n = 4 * (e - kp * (3 * DH / 4));
+      const int e = tid + q * J2_THREADS, kp = e & 7, n = 4 * (e >> 3);
       // rows: h_hor, h_ver at 0 .. 2 dh; h_k after the 16 one-hot rows
       const int rr = n < 2 * DH ? n : n + S::NU1;
       if (e < UB::N) put_quad(bh, bl, rr, 2 * kp, r.b[q][0], r.b[q][1]);

@@ -58,6 +58,7 @@ struct nqs_ctx {
   // streamed local-energy engine and its dropped tile
   unsigned long long test_spin_limit = 0;
   int solve_form = -1;  // nqs_set_solve_form (-1: tuned or built-in)
+  int sampler_form = -1;  // nqs_set_sampler (-1: built-in)
   int test_drop_tile = 0;
   WsOff off{};
   char *ws = nullptr;
@@ -274,7 +275,7 @@ FwdArgs<T> fwd_args(nqs_ctx *c) {
 template <typename T>
 nqs_status run_sample(nqs_ctx *c, const FwdArgs<T> &a, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
-    if (c->ck == 0 && gram_tc_available() &&
+    if (c->sampler_form != 0 && c->ck == 0 && gram_tc_available() &&
         eloc2d_tcs_sample_supported(c->L.dim, c->L.dh, c->L.Lx)) {
       Eloc2dTcArgs e{};
       e.pack = a.pack;
@@ -1507,6 +1508,13 @@ nqs_status nqs_clear_tuning(nqs_ctx *c) {
   c->tuned_ns = 0;
   c->t_eloc_grid = c->t_gram_splits = c->t_solve_grid = 0;
   c->t_chol_var = c->t_chol_subst = -1;
+  return NQS_OK;
+}
+
+nqs_status nqs_set_sampler(nqs_ctx *c, int form) {
+  if (!c || form < -1 || form > 1) return NQS_ERR_ARG;
+  drop_graph(c);
+  c->sampler_form = form;
   return NQS_OK;
 }
 

@@ -66,7 +66,7 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
            "nqs_shard_solve", "nqs_shard_apply", "nqs_test_wait_timeout", "nqs_adam_step",
-           "nqs_energy_scan", "nqs_set_solve_form",
+           "nqs_energy_scan", "nqs_set_solve_form", "nqs_set_sampler",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -381,6 +381,11 @@ class Context:
 
     def clear_tuning(self):
         _check(lib().nqs_clear_tuning(self._h))
+
+    def set_sampler(self, form):
+        """Sampler of a mixed 2D d_h 96/128 context: 1 tensor-core engine,
+        0 recurrence kernels, -1 built-in (nqs_set_sampler)."""
+        _check(lib().nqs_set_sampler(self._h, int(form)))
 
     def set_solve_form(self, form):
         """Form of the mixed regularized solve: 0 / 1 32-wide panels (tiles
