@@ -38,6 +38,11 @@ FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 x 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12    # SMs x FP64 lane-FMAs x 2 x max SM clock
 
 
+
+# NVTX range around the timed steps (ncu --nvtx --nvtx-include "nqs_timed_steps/"
+# lists exactly the kernels of the timed region)
+TIMED_RANGE = "nqs_timed_steps"
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -586,10 +591,12 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
+    torch.cuda.nvtx.range_push(TIMED_RANGE)
     e0.record()
     for t in range(Wu, Wu + K):
         ctx.minsr_step(thd, momd, hp, t, stats)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -831,10 +838,12 @@ def run_batched(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
+    torch.cuda.nvtx.range_push(TIMED_RANGE)
     e0.record()
     for t in range(Wu, Wu + K):
         b.step(thd, mod, hps, t, stats)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
