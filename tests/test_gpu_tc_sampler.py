@@ -158,3 +158,28 @@ def test_tc_sampler_sample_ranges_in_sharded_step():
     step_b = (ths[0] - torch.tensor(th0, device="cuda")).cpu().numpy()
     assert rel_err(step_b, step_a) < 5e-4
     assert torch.equal(ths[0], ths[1])
+
+
+def test_tc_and_recurrence_samplers_agree():
+    """The two samplers of a mixed 2D d_h 128 context (nqs_set_sampler) draw
+    the same configurations from the same uniforms: a row may differ only
+    where the first differing site is a near-tie of the oracle's p_k(0), and
+    log Psi of the common rows agrees within the tensor-core bound."""
+    model = ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1)
+    ns = 300
+    c = ctx(model, HamSpec("j1j2", J2=0.5), "mixed", ns)
+    th, thd = theta_dev(model, 31)
+    c.set_sampler(1)
+    s1, l1 = c.sample(thd, ns, seed=9, step=4)
+    c.set_sampler(0)
+    s0, l0 = c.sample(thd, ns, seed=9, step=4)
+    c.set_sampler(-1)
+    a, b = s1.cpu().numpy(), s0.cpu().numpy()
+    same = np.all(a == b, axis=1)
+    for s in np.where(~same)[0]:
+        k = int(np.argmax(a[s] != b[s]))
+        p0 = O.conditionals(model, th, a[s])[k]
+        assert abs(O.uniform(9, 4, int(s), k) - p0) <= 1e-5
+    assert np.sum(~same) <= 0.02 * ns
+    d = np.abs(cplx(l1)[same] - cplx(l0)[same])
+    assert np.max(d) <= 1e-4 + 2.0 ** -14 * model.N
