@@ -529,24 +529,32 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         ++pd1;
         tc_fence_after();
         // h' = X [horizontal] + (Y at a row start | U2 h_ver | 0); Y to the
-        // buffer; h' to the planes, 8 units at a time
+        // buffer; h' to the planes, 8 units at a time (the next group's
+        // tensor-memory loads in flight while this one is used)
+        {
+          float x[2][8], y[2][8];
+          tmem_ld8(lanes + (uint32_t)unit_of(0), x[0]);
+          tmem_ld8(lanes + (uint32_t)(DH + unit_of(0)), y[0]);
 #pragma unroll
-        for (int g8 = 0; g8 < G8; ++g8) {
-          float x[8], y[8];
-          tmem_ld8(lanes + (uint32_t)unit_of(g8), x);
-          tmem_ld8(lanes + (uint32_t)(DH + unit_of(g8)), y);
-          tmem_wait_ld();
+          for (int g8 = 0; g8 < G8; ++g8) {
+            const int cu = g8 & 1;
+            tmem_wait_ld();
+            if (g8 + 1 < G8) {
+              tmem_ld8(lanes + (uint32_t)unit_of(g8 + 1), x[cu ^ 1]);
+              tmem_ld8(lanes + (uint32_t)(DH + unit_of(g8 + 1)), y[cu ^ 1]);
+            }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float v = ver == k - 1 ? y[i] : hp[8 * g8 + i];
-            hp[8 * g8 + i] = hor ? x[i] + v : v;
+            for (int i = 0; i < 8; ++i) {
+              const float v = ver == k - 1 ? y[cu][i] : hp[8 * g8 + i];
+              hp[8 * g8 + i] = hor ? x[cu][i] + v : v;
+            }
+            if (valid && k >= 1) {
+              float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + unit_of(g8));
+              dst[0] = make_float4(y[cu][0], y[cu][1], y[cu][2], y[cu][3]);
+              dst[1] = make_float4(y[cu][4], y[cu][5], y[cu][6], y[cu][7]);
+            }
+            planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
           }
-          if (valid && k >= 1) {
-            float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + unit_of(g8));
-            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
-            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
-          }
-          planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
         }
         arrive_a();  // A = h'
         // sampling: part 0 drew sigma_{k-1} before its arrival on a
@@ -563,18 +571,28 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
         float *grow = SMP && a.gcache ? a.gcache + ((int64_t)s * N + k) * 5 * DH : nullptr;
         float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
         bool dok = true;
+        // gate values of group g8 in slot g8 % 2; the next group's loads are
+        // issued before this one is used, within a chunk of the product
+        float gq[2][3][8];
+        auto gate_ld = [&](int g, int sl) {
+          const int ugl = unit_of(g);
+          tmem_ld8(gcol(ugl), gq[sl][0]);
+          tmem_ld8(gcol(ugl) + (uint32_t)C::CU, gq[sl][1]);
+          tmem_ld8(gcol(ugl) + (uint32_t)(2 * C::CU), gq[sl][2]);
+        };
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
-          const int ug = unit_of(g8);
-          if (SPLIT && g8 % GPC == 0) {  // the next chunk of the gate product
-            dok = dok && wait_ab(bar(C::B_D2 + g8 / GPC), pd2 & 1, s_abort, lim);
-            tc_fence_after();
+          const int ug = unit_of(g8), cu = g8 & 1;
+          if (g8 % GPC == 0) {  // the first group of a chunk: its loads are issued here
+            if (SPLIT) {  // the next chunk of the gate product
+              dok = dok && wait_ab(bar(C::B_D2 + g8 / GPC), pd2 & 1, s_abort, lim);
+              tc_fence_after();
+            }
+            gate_ld(g8, cu);
           }
-          float gu[8], gr[8], gg[8];
-          tmem_ld8(gcol(ug), gu);
-          tmem_ld8(gcol(ug) + (uint32_t)C::CU, gr);
-          tmem_ld8(gcol(ug) + (uint32_t)(2 * C::CU), gg);
           tmem_wait_ld();
+          if (g8 + 1 < G8 && (g8 + 1) % GPC != 0) gate_ld(g8 + 1, cu ^ 1);
+          float *gu = gq[cu][0], *gr = gq[cu][1], *gg = gq[cu][2];
           float su[8], sr[8], sc[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {

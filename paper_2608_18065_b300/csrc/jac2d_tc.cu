@@ -327,49 +327,17 @@ __global__ void __launch_bounds__(J2_THREADS, 1) k_jac2d_tc(const Jac2dTcArgs a)
     return flag_s == 0;
   };
 
-  Chunk2<DH> cr;
-  if ((int64_t)blockIdx.x < nitems) fetch2<DH>(a, cr, blockIdx.x >> 1, (int)(blockIdx.x & 1), 0, tid);
-  for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-    const int64_t row = item >> 1;
-    const int pass = (int)(item & 1);
-    for (int c = 0; c < NC; ++c) {
-      const int st = c & 1;
-      if (pending[st] && !drain(st)) { ok = false; break; }
-      store2<DH>(cr, stg[st], pass, tid);
-      if (c + 1 < NC) {
-        fetch2<DH>(a, cr, row, pass, c + 1, tid);
-      } else if (item + gridDim.x < nitems) {
-        const int64_t nx = item + gridDim.x;
-        fetch2<DH>(a, cr, nx >> 1, (int)(nx & 1), 0, tid);
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t base = smem_u32(stg[st]), bb = base + S::A_BYTES;
-        const uint32_t acc = c == 0 ? 0u : 1u;
-        auto mma3 = [&](int t, uint32_t d, uint32_t brow, uint32_t id) {
-          const uint64_t ah = kmaj_desc(base + t * J2_ASUB), al = kmaj_desc(base + (3 + t) * J2_ASUB);
-          const uint64_t bh = kmaj_desc(bb + (brow / 8) * 256), bl = kmaj_desc(bb + S::BSUB + (brow / 8) * 256);
-          mma_bf16(d, ah, bh, id, acc);
-          mma_bf16(d, ah, bl, id, 1u);
-          mma_bf16(d, al, bh, id, 1u);
-        };
-        if (pass == 0) {
-#pragma unroll
-          for (int t = 0; t < S::TG; ++t) mma3(t, tmem + (uint32_t)(t * S::NG), 0u, id_g);
-        } else {
-          mma3(0, tmem, 0u, id_u0);
-          mma3(1, tmem + (uint32_t)S::NU0, (uint32_t)S::NU0, id_u1);
-          mma3(2, tmem + (uint32_t)(S::NU0 + S::NU1), (uint32_t)(S::NU0 + S::NU1), id_u2);
-        }
-        mma_commit(smem_u32(&bars[st]));
-      }
-      pending[st] = 1;
-    }
-    if (!ok) break;
-    if ((pending[0] && !drain(0)) || (pending[1] && !drain(1))) { ok = false; break; }
-    tc_fence_after();
+  // This CTA's (item, chunk) sequence, q = 0 .. Q - 1; the loads of chunk
+  // q + 2 are issued as soon as chunk q is staged (two chunks in flight,
+  // across item boundaries), into the register set chunk q used.
+  const int64_t nmy = (int64_t)blockIdx.x < nitems ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t Q = nmy * NC;
+  auto fetch_q = [&](Chunk2<DH> &r, int64_t q) {
+    const int64_t it = blockIdx.x + (q / NC) * gridDim.x;
+    fetch2<DH>(a, r, it >> 1, (int)(it & 1), (int)(q % NC), tid);
+  };
+  // the accumulators of an item into its row of O
+  auto epilogue = [&](int64_t row, int pass) {
     float *orow = a.O + row * a.np;
     const int ntile = pass == 0 ? S::TG : 3;
     for (int t = 0; t < ntile; ++t) {
@@ -393,7 +361,53 @@ __global__ void __launch_bounds__(J2_THREADS, 1) k_jac2d_tc(const Jac2dTcArgs a)
         __syncthreads();
       }
     }
-    tc_fence_before();  // the next item's first products overwrite the accumulators
+  };
+  auto body = [&](int64_t q, Chunk2<DH> &r) -> bool {
+    const int c = (int)(q % NC);
+    const int64_t item = blockIdx.x + (q / NC) * gridDim.x;
+    const int64_t row = item >> 1;
+    const int pass = (int)(item & 1), st = (int)(q & 1);
+    if (pending[st] && !drain(st)) return false;
+    store2<DH>(r, stg[st], pass, tid);
+    if (q + 2 < Q) fetch_q(r, q + 2);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t base = smem_u32(stg[st]), bb = base + S::A_BYTES;
+      const uint32_t acc = c == 0 ? 0u : 1u;
+      auto mma3 = [&](int t, uint32_t d, uint32_t brow, uint32_t id) {
+        const uint64_t ah = kmaj_desc(base + t * J2_ASUB), al = kmaj_desc(base + (3 + t) * J2_ASUB);
+        const uint64_t bh = kmaj_desc(bb + (brow / 8) * 256), bl = kmaj_desc(bb + S::BSUB + (brow / 8) * 256);
+        mma_bf16(d, ah, bh, id, acc);
+        mma_bf16(d, ah, bl, id, 1u);
+        mma_bf16(d, al, bh, id, 1u);
+      };
+      if (pass == 0) {
+#pragma unroll
+        for (int t = 0; t < S::TG; ++t) mma3(t, tmem + (uint32_t)(t * S::NG), 0u, id_g);
+      } else {
+        mma3(0, tmem, 0u, id_u0);
+        mma3(1, tmem + (uint32_t)S::NU0, (uint32_t)S::NU0, id_u1);
+        mma3(2, tmem + (uint32_t)(S::NU0 + S::NU1), (uint32_t)(S::NU0 + S::NU1), id_u2);
+      }
+      mma_commit(smem_u32(&bars[st]));
+    }
+    pending[st] = 1;
+    if (c == NC - 1) {  // the item's products are complete once both stages' commits are
+      if ((pending[0] && !drain(0)) || (pending[1] && !drain(1))) return false;
+      tc_fence_after();
+      epilogue(row, pass);
+      tc_fence_before();  // the next item's first products overwrite the accumulators
+    }
+    return true;
+  };
+  Chunk2<DH> cr0, cr1;
+  if (Q > 0) fetch_q(cr0, 0);
+  if (Q > 1) fetch_q(cr1, 1);
+  for (int64_t q = 0; q < Q && ok; q += 2) {
+    if (!body(q, cr0)) { ok = false; break; }
+    if (q + 1 < Q && !body(q + 1, cr1)) { ok = false; break; }
   }
   if (!ok) {
     if (tid == 0) atomicCAS(a.err, 0, (int)NQS_ERR_TIMEOUT);
