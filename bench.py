@@ -301,7 +301,7 @@ def stage_rooflines(w, ms, sites, R, np_):
     site_flops each (the mixed 1D O assembly on the tensor cores is
     reported by its HBM bytes, as is the mixed 2D one; mixed 2D sampling at
     d_h 96 / 128 runs on the tensor cores and is reported by its BF16x3
-    products).  cholesky: n^3/3 factor (128-wide panels, R >= 1024) or n^3/3
+    products).  cholesky: n^3/3 factor (128-wide panels, R >= 3072) or n^3/3
     factor + n^3/3 triangular inverse (32-wide panels) in FP32 for the mixed
     path (refinement sweeps: 2n^2 each, not counted).  gram: BF16x3 tensor work 3 R(R+1) Np.  center: HBM bytes of
     the column sums and the split (read O twice, write hi and lo)."""
@@ -366,7 +366,7 @@ def stage_rooflines(w, ms, sites, R, np_):
                            "bytes_per_launch": byts, "ms_per_launch": t}
     else:
         alu("jac_grad", "k_jac_grad", R * N * sf)
-    if f32 and R >= 1024 and R % 4 == 0:
+    if f32 and R >= 3072 and R % 4 == 0:
         alu("cholesky", "k_chol_blk", R ** 3 / 3)  # 128-wide panels: the factor
     else:
         alu("cholesky", "k_chol_ir" if f32 else "k_chol_coop", 2 * R ** 3 / 3)

@@ -320,7 +320,7 @@ nqs_status nqs_get_tuning(const nqs_ctx *ctx, nqs_tuning *out);
 nqs_status nqs_clear_tuning(nqs_ctx *ctx);
 /* Fix the form of the mixed context's regularized solve (Eq. minsrR; the
  * values of nqs_tuning.solve_form; -1: the built-in choice, 128-wide panels
- * from R = 1024 on where R % 4 == 0, otherwise 32-wide) for every later
+ * from R = 3072 on where R % 4 == 0, otherwise 32-wide) for every later
  * solve, over any tuning.  The 128-wide form needs R % 4 == 0 and R >= 256
  * and takes the 32-wide one otherwise.  Every form ends at FP64 backward
  * error or in the FP64 Cholesky.  NQS_ERR_ARG for another value. */

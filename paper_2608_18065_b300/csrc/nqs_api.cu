@@ -691,10 +691,12 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
   const int G = solve_grid(c);
   CU(cudaMemsetAsync(bar, 0, 32, st));
   // blocked FP32 factor (128-wide panels) where it applies and is chosen:
-  // by the autotuner, else from R = 1024 on
+  // by the autotuner, else from R = 3072 on (measured: 0.49 against 1.2 ms
+  // at R = 1024 for the 32-wide panels, 4.1 against 6.2 ms at R = 4096 for
+  // the 128-wide ones)
   const int var = c->solve_form >= 0                  ? c->solve_form
                   : tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var
-                                                   : (R >= 1024 ? 2 : 0);
+                                                   : (R >= 3072 ? 2 : 0);
   if (f32(c) && var == 2 && chol_blk_supported(R)) {
     CholBlkArgs bk;
     bk.A = T; bk.n = R; bk.b = b; bk.x = x;
@@ -1411,7 +1413,7 @@ nqs_status autotune_T(nqs_ctx *c, const double *theta, const nqs_step_hparams *h
                      }, ms);
     };
     const bool blk_ok = f32(c) && chol_blk_supported(R);
-    const int var0 = blk_ok && R >= 1024 ? 2 : (R >= 2048 ? 1 : 0), sub0 = R >= 2048 ? 1 : 0;
+    const int var0 = blk_ok && R >= 3072 ? 2 : (R >= 2048 ? 1 : 0), sub0 = R >= 2048 ? 1 : 0;
     double best = 1e300;
     int pvar = var0, psub = sub0, pick = G0;
     c->t_solve_grid = G0;
