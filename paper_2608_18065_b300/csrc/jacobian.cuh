@@ -47,9 +47,14 @@ template <int DH> struct BTile {
   static constexpr int UT = DH / UG;
 };
 
-template <typename T, int DH, int DIM, int R>
+// Row stride of the shared [unit][row] arrays of k_jac_bwd: padded by RT
+// (the lanes of a warp, consecutive units, spread over the banks; a thread's
+// RT rows stay aligned for its vector loads).
+template <int R, int RT> __host__ __device__ constexpr int bwd_rp() { return R % 8 == 0 ? R + RT : R; }
+
+template <typename T, int DH, int DIM, int R, int RT>
 inline size_t bwd_smem_bytes(int N, bool wsmem = true) {
-  constexpr int RP = R == 8 ? R + 1 : R;                   // padded row stride (see k_jac_bwd)
+  constexpr int RP = bwd_rp<R, RT>();                       // padded row stride (see k_jac_bwd)
   size_t t = 4 * DH + 8;                                   // head, hc
   if (wsmem) t += 3 * (size_t)DH * DH + (DIM == 2 ? 2 * (size_t)DH * DH : 0);  // Wg, U12
   if (DIM == 2) t += (size_t)DH * RP;                      // sdp
@@ -80,9 +85,10 @@ k_jac_bwd(const BwdArgs<T> A) {
   T *swb = shc + 8;                        // staged Wg [3dh][dh] and U12 [dh][2dh] (wsmem)
   const T *sWg = swb;
   const T *sU12 = swb + C3 * DH;
-  // the 8 rows of a unit are stored 9 floats apart, so the lanes of a warp
-  // (one row, consecutive units) spread over the banks
-  constexpr int RP = R == 8 ? R + 1 : R;
+  // the R rows of a unit are stored R + RT floats apart, so the lanes of a
+  // warp (one row group, consecutive units) spread over the banks and every
+  // thread's RT rows stay aligned for its vector loads (bwd_rp)
+  constexpr int RP = bwd_rp<R, RT>();
   T *sdp = swb + (WS ? C3 * DH + (DIM == 2 ? 2 * DH * DH : 0) : 0);  // 2D: [dh][RP]
   T *sda = sdp + (DIM == 2 ? DH * RP : 0);  // gate adjoints [3dh][RP]
   const int NP = (A.N + 15) & ~15;

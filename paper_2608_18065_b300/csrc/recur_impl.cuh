@@ -110,10 +110,10 @@ template <typename T, int DH, int DIM>
 static cudaError_t bwd_dim(const RecDesc &d, BwdArgs<T> a, cudaStream_t st) {
   constexpr int RT = Rows<T>::BWD_RT, RG = Rows<T>::BWD_RG, R = RT * RG;
   auto kern = k_jac_bwd<T, DH, DIM, RT, RG, true>;
-  size_t smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, true);
+  size_t smem = bwd_smem_bytes<T, DH, DIM, R, RT>(d.N, true);
   if constexpr (DH >= 96) {
     if (smem > SMEM_STAGE_LIMIT) {
-      smem = bwd_smem_bytes<T, DH, DIM, R>(d.N, false);
+      smem = bwd_smem_bytes<T, DH, DIM, R, RT>(d.N, false);
       kern = k_jac_bwd<T, DH, DIM, RT, RG, false>;
     }
   }
