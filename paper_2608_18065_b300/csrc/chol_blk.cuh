@@ -160,16 +160,19 @@ __device__ __forceinline__ void tile_product(float *Xs, float *Ys, float *Cs, co
   __syncthreads();
 }
 
-// y = D v for a 128 x 128 block D in global memory (row stride 128) and v
-// in shared memory: thread (row tid / 2, half tid % 2) with its 16 loads in
-// flight together; y to shared memory.  Ends with a barrier.
-__device__ __forceinline__ void matvec(const float *D, const float *v, float *y, int tid) {
+// y = D v for a 128 x 128 block D in global memory (row stride ld, rows
+// from `rows` on zero) and v in shared memory: thread (row tid / 2, half
+// tid % 2) with its 16 loads in flight together; y (or sub - D v) to shared
+// memory.  Ends with a barrier.
+__device__ __forceinline__ void matvec(const float *D, const float *v, float *y, int tid,
+                                       int64_t ld = BKB, int rows = BKB,
+                                       const float *sub = nullptr) {
   const int j = tid >> 1, h = tid & 1;
-  const float4 *dr = reinterpret_cast<const float4 *>(D + j * BKB + 64 * h);
+  const float4 *dr = reinterpret_cast<const float4 *>(D + j * ld + 64 * h);
   const float4 *vr = reinterpret_cast<const float4 *>(v + 64 * h);
   float4 d[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) d[q] = __ldcg(dr + q);
+  for (int q = 0; q < 16; ++q) d[q] = j < rows ? __ldcg(dr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
   float s = 0.f;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -180,19 +183,23 @@ __device__ __forceinline__ void matvec(const float *D, const float *v, float *y,
     s = fmaf(d[q].w, x.w, s);
   }
   s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if (h == 0) y[j] = s;
+  if (h == 0) y[j] = sub ? sub[j] - s : s;  // in place (y = sub) is allowed
   __syncthreads();
 }
 
-// y = D^T v: thread (four columns 4 (tid % 32) .., sixteen rows 16 (tid / 32) ..)
-// with its 16 loads in flight together, the eight row groups summed through
-// part ([8][128] floats).  Ends with a barrier.
+// y = D^T v (or sub - D^T v) for a 128-column block D (row stride ld, rows
+// from `rows` on zero): thread (four columns 4 (tid % 32) .., sixteen rows
+// 16 (tid / 32) ..) with its 16 loads in flight together, the eight row
+// groups summed through part ([8][128] floats).  Ends with a barrier.
 __device__ __forceinline__ void matvec_t(const float *D, const float *v, float *y, float *part,
-                                         int tid) {
+                                         int tid, int64_t ld = BKB, int rows = BKB,
+                                         const float *sub = nullptr) {
   const int k4 = tid & 31, r8 = tid >> 5;
   float4 d[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) d[q] = __ldcg(reinterpret_cast<const float4 *>(D + (16 * r8 + q) * BKB) + k4);
+  for (int q = 0; q < 16; ++q)
+    d[q] = 16 * r8 + q < rows ? __ldcg(reinterpret_cast<const float4 *>(D + (16 * r8 + q) * ld) + k4)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -208,7 +215,7 @@ __device__ __forceinline__ void matvec_t(const float *D, const float *v, float *
     float t = 0.f;
 #pragma unroll
     for (int r = 0; r < 8; ++r) t += part[r * BKB + tid];
-    y[tid] = t;
+    y[tid] = sub ? sub[tid] - t : t;  // in place (y = sub) is allowed
   }
   __syncthreads();
 }
@@ -356,16 +363,18 @@ __device__ __forceinline__ void stage_diag(float *S, const float *L, int64_t n, 
 
 }  // namespace blk
 
-__global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
+// The solve of one instance by CTAs g = 0 .. G-1 of the launch (all of a
+// k_chol_blk grid, or the instance's range of a grouped grid).
+__device__ __forceinline__ void chol_blk_run(const CholBlkArgs &a, const int g, const int G) {
   extern __shared__ __align__(16) float blk_smem[];
   float *Xs = blk_smem, *Ys = Xs + BKB * BKB_LD, *Cs = Ys + BKB * BKB_LD, *PT = Cs + BKB * BKB_LD;
   float *vx = PT + 32 * BKB_LD, *vy = vx + BKB, *colb = vy + BKB;
+  float *vz = PT + 2048, *vw = PT + 2048 + BKB;  // refinement: the second block of a pair
   __shared__ int bad_s;
   __shared__ double red_s[BKB_THREADS / 32][3];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tx = tid & 15, ty = tid >> 4;
-  const int G = gridDim.x, g = blockIdx.x;
   const int64_t n = a.n;
   const int nb = (int)((n + BKB - 1) / BKB);
   float *L = a.L;
@@ -475,23 +484,39 @@ __global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
     for (int64_t i = (int64_t)g * BKB_THREADS + tid; i < n; i += (int64_t)G * BKB_THREADS)
       __stcg(a.t + i, (float)__ldcg(rs + i));
     if (!gsync()) return;
-    // forward: w_p = D_p t_p; t_i -= L_ip w_p below the block
-    for (int p = 0; p < nb; ++p) {
-      const int64_t c0 = (int64_t)p * BKB;
+    // forward, two blocks per grid barrier: w_p = D_p t_p, w_{p+1} =
+    // D_{p+1} (t_{p+1} - L_{p+1,p} w_p) in every CTA; t_i -= L_ip w_p +
+    // L_i,p+1 w_{p+1} below the pair
+    for (int p = 0; p < nb; p += 2) {
+      const int64_t c0 = (int64_t)p * BKB, c1 = c0 + BKB;
       const int m = (int)min64(BKB, n - c0);
-      const float *Dp = a.Dinv + (size_t)p * BKB * BKB;
-      if (tid < BKB) vx[tid] = tid < m ? __ldcg(a.t + c0 + tid) : 0.f;
+      const bool two = p + 1 < nb;
+      const int m1 = two ? (int)min64(BKB, n - c1) : 0;
+      if (tid < BKB) {
+        vx[tid] = tid < m ? __ldcg(a.t + c0 + tid) : 0.f;
+        vz[tid] = tid < m1 ? __ldcg(a.t + c1 + tid) : 0.f;
+      }
       __syncthreads();
-      blk::matvec(Dp, vx, vy, tid);
+      blk::matvec(a.Dinv + (size_t)p * BKB * BKB, vx, vy, tid);
+      if (two) {
+        blk::matvec(L + c1 * n + c0, vy, vz, tid, n, m1, vz);
+        blk::matvec(a.Dinv + (size_t)(p + 1) * BKB * BKB, vz, vw, tid);
+      }
       if (g == 0 && tid < m) __stcg(a.w + c0 + tid, vy[tid]);
+      if (g == 0 && tid < m1) __stcg(a.w + c1 + tid, vw[tid]);
       // rows below, four per warp with their loads in flight together
-      for (int64_t i0 = c0 + BKB + 4 * (int64_t)gw; i0 < n; i0 += 4 * (int64_t)nwarps) {
+      for (int64_t i0 = c0 + (two ? 2 : 1) * BKB + 4 * (int64_t)gw; i0 < n; i0 += 4 * (int64_t)nwarps) {
         const float4 v = *reinterpret_cast<const float4 *>(vy + 4 * lane);
-        float4 l[4];
+        const float4 v2 = *reinterpret_cast<const float4 *>(vw + 4 * lane);
+        float4 l[4], l2[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          l[q] = i0 + q < n ? __ldcg(reinterpret_cast<const float4 *>(L + (i0 + q) * n + c0) + lane)
+        for (int q = 0; q < 4; ++q) {
+          const bool ok = i0 + q < n;
+          l[q] = ok ? __ldcg(reinterpret_cast<const float4 *>(L + (i0 + q) * n + c0) + lane)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          l2[q] = ok && two ? __ldcg(reinterpret_cast<const float4 *>(L + (i0 + q) * n + c1) + lane)
                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float sq[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -499,6 +524,10 @@ __global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
           s = fmaf(l[q].y, v.y, s);
           s = fmaf(l[q].z, v.z, s);
           s = fmaf(l[q].w, v.w, s);
+          s = fmaf(l2[q].x, v2.x, s);
+          s = fmaf(l2[q].y, v2.y, s);
+          s = fmaf(l2[q].z, v2.z, s);
+          s = fmaf(l2[q].w, v2.w, s);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
           sq[q] = s;
@@ -510,32 +539,49 @@ __global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
       }
       if (!gsync()) return;
     }
-    // backward: d_p = D_p^T w_p; x_p += d_p; w_j -= (L_pj)^T d_p left of the block
-    for (int p = nb - 1; p >= 0; --p) {
-      const int64_t c0 = (int64_t)p * BKB;
+    // backward, two blocks per grid barrier: d_p = D_p^T w_p, d_{p-1} =
+    // D_{p-1}^T (w_{p-1} - L_{p,p-1}^T d_p); x += d; w_j -= L_pj d_p +
+    // L_{p-1},j d_{p-1} left of the pair
+    for (int p = nb - 1; p >= 0; p -= 2) {
+      const int64_t c0 = (int64_t)p * BKB, cm = c0 - BKB;
       const int m = (int)min64(BKB, n - c0);
-      const float *Dp = a.Dinv + (size_t)p * BKB * BKB;
-      if (tid < BKB) vx[tid] = tid < m ? __ldcg(a.w + c0 + tid) : 0.f;
+      const bool two = p >= 1;
+      if (tid < BKB) {
+        vx[tid] = tid < m ? __ldcg(a.w + c0 + tid) : 0.f;
+        vz[tid] = two ? __ldcg(a.w + cm + tid) : 0.f;
+      }
       __syncthreads();
-      blk::matvec_t(Dp, vx, vy, PT, tid);
+      blk::matvec_t(a.Dinv + (size_t)p * BKB * BKB, vx, vy, PT, tid);
       if (g == 0 && tid < m) __stcg(a.x + c0 + tid, __ldcg(a.x + c0 + tid) + (double)vy[tid]);
-      // columns left of the block: 64 columns x 4 quarters of the block's
+      if (two) {
+        blk::matvec_t(L + c0 * n + cm, vy, vz, PT, tid, n, m, vz);
+        blk::matvec_t(a.Dinv + (size_t)(p - 1) * BKB * BKB, vz, vw, PT, tid);
+        if (g == 0 && tid < BKB) __stcg(a.x + cm + tid, __ldcg(a.x + cm + tid) + (double)vw[tid]);
+      }
+      // columns left of the pair: 64 columns x 4 quarters of each block's
       // rows per CTA pass, 32 loads per thread in flight together
-      for (int64_t jb = (int64_t)g * 64; jb < c0; jb += (int64_t)G * 64) {
+      const int64_t cl = two ? cm : c0;
+      for (int64_t jb = (int64_t)g * 64; jb < cl; jb += (int64_t)G * 64) {
         const int jj = tid & 63, q = tid >> 6;
         const int64_t j = jb + jj;
         float s = 0.f;
-        if (j < c0) {
+        if (j < cl) {
           float lv[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i)
             lv[i] = 32 * q + i < m ? __ldcg(L + (c0 + 32 * q + i) * n + j) : 0.f;
 #pragma unroll
           for (int i = 0; i < 32; ++i) s = fmaf(lv[i], vy[32 * q + i], s);
+          if (two) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) lv[i] = __ldcg(L + (cm + 32 * q + i) * n + j);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) s = fmaf(lv[i], vw[32 * q + i], s);
+          }
         }
         PT[BKB * 8 + q * 64 + jj] = s;
         __syncthreads();
-        if (q == 0 && j < c0) {
+        if (q == 0 && j < cl) {
           const float *ps = PT + BKB * 8 + jj;
           __stcg(a.w + j, __ldcg(a.w + j) - (((ps[0] + ps[64]) + ps[128]) + ps[192]));
         }
@@ -593,6 +639,26 @@ __global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
     converged = q0 <= sqrt((double)n) * 1.1102230246251565e-16 * normA * q1;
   }
   if (!converged && g == 0 && tid == 0) *a.need_fp64 = 1;
+}
+
+__global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk(CholBlkArgs a) {
+  chol_blk_run(a, blockIdx.x, gridDim.x);
+}
+
+// Several independent solves in one cooperative launch: instance i owns the
+// CTAs [cta0[i], cta0[i + 1]) and its own barrier counter, so the instances'
+// panel chains run side by side on disjoint SMs.
+constexpr int BLK_GROUP_MAX = 32;
+struct CholBlkGroup {
+  int n;
+  int cta0[BLK_GROUP_MAX + 1];
+  CholBlkArgs inst[BLK_GROUP_MAX];
+};
+
+__global__ void __launch_bounds__(BKB_THREADS, 1) k_chol_blk_group(const __grid_constant__ CholBlkGroup gr) {
+  int i = 0;
+  while (i + 1 < gr.n && (int)blockIdx.x >= gr.cta0[i + 1]) ++i;
+  chol_blk_run(gr.inst[i], (int)blockIdx.x - gr.cta0[i], gr.cta0[i + 1] - gr.cta0[i]);
 }
 
 }  // namespace nqs

@@ -84,7 +84,13 @@ struct nqs_ctx {
   int64_t cur_ns = 0;  // sample count of the step being issued
   // batched steps: order this context's cooperative solve after another's
   cudaEvent_t solve_wait = nullptr, solve_rec = nullptr;
+  // batched steps by stage: issue only the part of the step before the
+  // solve (STEP_PRE) or from it on (STEP_POST); in_group: the FP32 factor
+  // runs in the batch's grouped launch, not in this context's step
+  int phase = 0, in_group = 0;
 };
+
+constexpr int STEP_ALL = 0, STEP_PRE = 1, STEP_POST = 2;
 
 namespace {
 
@@ -684,12 +690,41 @@ struct RetryInfo {
   nqs_step_stats *stats;
 };
 
+// Arguments of the blocked FP32 factor and refinement for this context.
+CholBlkArgs blk_args(nqs_ctx *c, const double *T, int64_t R, const double *b, double *x,
+                     int32_t *status) {
+  unsigned *bar = W<unsigned>(c, c->off.cbar);
+  CholBlkArgs bk;
+  bk.A = T; bk.n = R; bk.b = b; bk.x = x;
+  bk.L = W<float>(c, c->off.L32);
+  bk.Dinv = W<float>(c, c->off.Tm32);
+  bk.t = W<float>(c, c->off.dpart32);
+  bk.w = W<float>(c, c->off.wv32);
+  bk.r = W<double>(c, c->off.crhs);
+  bk.part = W<double>(c, c->off.cpart);
+  bk.bar = bar + 2;
+  bk.status = status;
+  bk.need_fp64 = reinterpret_cast<int32_t *>(bar + 4);
+  bk.maxit = 12;
+  return bk;
+}
+
+// Whether a batch may run this context's FP32 factor in its grouped launch.
+bool group_solvable(const nqs_ctx *c, int64_t R) {
+  return f32(c) && chol_blk_supported(R) && (c->solve_form < 0 || c->solve_form == 2);
+}
+
+// part: 0 the whole solve; 1 only the reset of the barrier counters and
+// flags (the factor follows in a grouped launch); 2 what follows the FP32
+// factor (the gated FP64 fallback and the FP64 Gram retry).
 nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double *x,
-                      int32_t *status, cudaStream_t st, const RetryInfo *retry = nullptr) {
+                      int32_t *status, cudaStream_t st, const RetryInfo *retry = nullptr,
+                      int part = 0) {
   unsigned *bar = W<unsigned>(c, c->off.cbar);
   int32_t *need = reinterpret_cast<int32_t *>(bar + 4);
   const int G = solve_grid(c);
-  CU(cudaMemsetAsync(bar, 0, 32, st));
+  if (part != 2) CU(cudaMemsetAsync(bar, 0, 32, st));
+  if (part == 1) return NQS_OK;
   // blocked FP32 factor (128-wide panels) where it applies and is chosen:
   // by the autotuner, else from R = 3072 on (measured: 0.49 against 1.2 ms
   // at R = 1024 for the 32-wide panels, 4.1 against 6.2 ms at R = 4096 for
@@ -697,19 +732,10 @@ nqs_status chol_solve(nqs_ctx *c, double *T, int64_t R, const double *b, double 
   const int var = c->solve_form >= 0                  ? c->solve_form
                   : tuned(c) && c->t_chol_var >= 0 ? c->t_chol_var
                                                    : (R >= 3072 ? 2 : 0);
-  if (f32(c) && var == 2 && chol_blk_supported(R)) {
-    CholBlkArgs bk;
-    bk.A = T; bk.n = R; bk.b = b; bk.x = x;
-    bk.L = W<float>(c, c->off.L32);
-    bk.Dinv = W<float>(c, c->off.Tm32);
-    bk.t = W<float>(c, c->off.dpart32);
-    bk.w = W<float>(c, c->off.wv32);
-    bk.r = W<double>(c, c->off.crhs);
-    bk.part = W<double>(c, c->off.cpart);
-    bk.bar = bar + 2;
-    bk.status = status;
-    bk.need_fp64 = need;
-    bk.maxit = 12;
+  if (part == 2) {
+    // the grouped launch ran the FP32 factor and refinement
+  } else if (f32(c) && var == 2 && chol_blk_supported(R)) {
+    CholBlkArgs bk = blk_args(c, T, R, b, x, status);
     const size_t smem = chol_blk_smem();
     CU(cudaFuncSetAttribute((const void *)k_chol_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem));
@@ -820,79 +846,84 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   double *x = W<double>(c, c->off.x);
   int32_t *sstat = W<int32_t>(c, c->off.sstat);
   c->cur_ns = ns;
-  mark(c, 0, st);
-  CU(cudaMemsetAsync(sstat, 0, 64, st));
-  // Alg. 1, sampling: sample (also fills the hidden-state caches)
-  ST(pack_theta<T>(c, theta, st));
-  mark(c, 1, st);
-  {
-    FwdArgs<T> a = fwd_args<T>(c);
-    a.nrows = ns; a.seed = hp->seed; a.step = (uint64_t)hp->step_index;
-    a.step_dev = W<int64_t>(c, c->off.dstep);
-    a.spins = spins; a.logpsi = logpsi;
-    if (c->ck == 0) {  // gates for the reverse sweep (recomputed per segment otherwise)
-      a.gcache = W<T>(c, c->off.gcache);
-      a.gw = c->gw;
-    }
-    ST(run_sample<T>(c, a, st));
-  }
-  // Alg. 1, energy: local energies, E, variance; eps-bar'
-  ST(eloc_T<T>(c, ns, spins, eloc, st));
-  mark(c, 5, st);
-  k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
-  c->launches += 1;
-  CU(cudaGetLastError());
-  // Alg. 1, log-derivatives: O, centred over samples per block, / sqrt(Ns)
-  ST(jac_T<T>(c, ns, spins, O, st));
-  mark(c, 8, st);
   // tensor-core route of the mixed path: centring writes the BF16 hi/lo
   // planes that the Gram and O'x read; otherwise O is centred in place
   const bool tc = f32(c) && gram_tc_available();
-  {
-    c->launches += 3;
-    const int chunks = (int)((ns + COL_ROWS - 1) / COL_ROWS);
-    const unsigned nblk = c->L.cplx ? 2u : 1u;
-    dim3 g((unsigned)((np + 255) / 256), nblk * chunks);
-    k_colsum_part<T><<<g, 256, 0, st>>>(O, ns, np, chunks, W<double>(c, c->off.part));
-    k_colmean_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
-        W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean), tc ? 1 : 0);
+  const RetryInfo rinfo{hp, stats};
+  const int ph = c->phase;
+  if (ph != STEP_POST) {
+    mark(c, 0, st);
+    CU(cudaMemsetAsync(sstat, 0, 64, st));
+    // Alg. 1, sampling: sample (also fills the hidden-state caches)
+    ST(pack_theta<T>(c, theta, st));
+    mark(c, 1, st);
+    {
+      FwdArgs<T> a = fwd_args<T>(c);
+      a.nrows = ns; a.seed = hp->seed; a.step = (uint64_t)hp->step_index;
+      a.step_dev = W<int64_t>(c, c->off.dstep);
+      a.spins = spins; a.logpsi = logpsi;
+      if (c->ck == 0) {  // gates for the reverse sweep (recomputed per segment otherwise)
+        a.gcache = W<T>(c, c->off.gcache);
+        a.gw = c->gw;
+      }
+      ST(run_sample<T>(c, a, st));
+    }
+    // Alg. 1, energy: local energies, E, variance; eps-bar'
+    ST(eloc_T<T>(c, ns, spins, eloc, st));
+    mark(c, 5, st);
+    k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
+    c->launches += 1;
     CU(cudaGetLastError());
+    // Alg. 1, log-derivatives: O, centred over samples per block, / sqrt(Ns)
+    ST(jac_T<T>(c, ns, spins, O, st));
+    mark(c, 8, st);
+    {
+      c->launches += 3;
+      const int chunks = (int)((ns + COL_ROWS - 1) / COL_ROWS);
+      const unsigned nblk = c->L.cplx ? 2u : 1u;
+      dim3 g((unsigned)((np + 255) / 256), nblk * chunks);
+      k_colsum_part<T><<<g, 256, 0, st>>>(O, ns, np, chunks, W<double>(c, c->off.part));
+      k_colmean_fin<<<dim3((unsigned)((np + 255) / 256), nblk), 256, 0, st>>>(
+          W<double>(c, c->off.part), ns, np, chunks, W<double>(c, c->off.mean), tc ? 1 : 0);
+      CU(cudaGetLastError());
+      if (tc) {
+        CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<float2>(c, c->off.mean),
+                        c->ws + c->off.split, st));
+      } else {
+        const int64_t tot = R * np;
+        const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+        k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
+        CU(cudaGetLastError());
+      }
+    }
+    // Alg. 1, Gram: T = O'^T O'
+    mark(c, 9, st);
     if (tc) {
-      CU(center_split(reinterpret_cast<const float *>(O), ns, np, R, W<float2>(c, c->off.mean),
-                      c->ws + c->off.split, st));
+      c->launches += 2;
+      CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, sstat, st, gram_splits(c)));
     } else {
-      const int64_t tot = R * np;
-      const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
-      k_center<T><<<blocks, 256, 0, st>>>(O, ns, np, R, W<double>(c, c->off.mean));
+      ST(gram_any(c, O, R, np, Tm, st));
+    }
+    mark(c, 10, st);
+    if (out && out->T) CU(cudaMemcpyAsync(out->T, Tm, R * R * 8, cudaMemcpyDeviceToDevice, st));
+    // lambda and shift
+    {
+      const int nparts = 256;
+      c->launches += 2;
+      k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
+      k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts, hp->lambda_mode,
+                                          hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats,
+                                          nullptr,
+                                          c->lm_omega > 1.0 ? W<double>(c, c->off.dlm) : nullptr);
       CU(cudaGetLastError());
     }
-  }
-  // Alg. 1, Gram: T = O'^T O'
-  mark(c, 9, st);
-  if (tc) {
-    c->launches += 2;
-    CU(gram_from_center_split(c->ws + c->off.split, R, np, Tm, sstat, st, gram_splits(c)));
-  } else {
-    ST(gram_any(c, O, R, np, Tm, st));
-  }
-  mark(c, 10, st);
-  if (out && out->T) CU(cudaMemcpyAsync(out->T, Tm, R * R * 8, cudaMemcpyDeviceToDevice, st));
-  // lambda and shift
-  {
-    const int nparts = 256;
-    c->launches += 2;
-    k_frob_part<<<nparts, 256, 0, st>>>(Tm, R * R, W<double>(c, c->off.frob));
-    k_lambda_finish<<<1, 1024, 0, st>>>(Tm, R, W<double>(c, c->off.frob), nparts, hp->lambda_mode,
-                                        hp->lambda, hp->lambda_coeff, hp->lambda_pow, stats,
-                                        nullptr,
-                                        c->lm_omega > 1.0 ? W<double>(c, c->off.dlm) : nullptr);
-    CU(cudaGetLastError());
-  }
+    mark(c, 11, st);
+    if (ph == STEP_PRE)
+      return c->in_group ? chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo, 1) : NQS_OK;
+  }  // ph != STEP_POST
   // Alg. 1, solve: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
-  mark(c, 11, st);
   if (c->solve_wait) CU(cudaStreamWaitEvent(st, c->solve_wait, 0));
-  const RetryInfo rinfo{hp, stats};
-  ST(chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo));
+  ST(chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo, ph == STEP_POST && c->in_group ? 2 : 0));
   if (c->solve_rec) CU(cudaEventRecord(c->solve_rec, st));
   mark(c, 13, st);
   k_eta<<<1, 1024, 0, st>>>(eps, x, R, hp->eta0, hp->decay_T, hp->trust_region,
@@ -1842,10 +1873,11 @@ struct nqs_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_enabled = 0, graph_broken = 0;
+  int grouped = 0;  // by stage: the FP32 solves of all instances in one launch
   struct Key {
     std::vector<const void *> ptr;  // theta, momentum, stats of every instance
     std::vector<nqs_step_hparams> hp;
-    int conc;
+    int conc, grouped;
   } key;
   std::vector<int64_t> gnext;
 };
@@ -1867,11 +1899,141 @@ int batch_conc(const nqs_batch *b) {
   return b->conc > 0 && b->conc < n ? b->conc : n;
 }
 
+// Predicted duration (us) of the blocked solve of order n on G CTAs: per
+// panel one tile product per row block for the panel rows, then the
+// trailing tiles on G - 1 CTAs while CTA 0 factors the next diagonal block,
+// at least the panel's dependent chain (panel solve, diagonal tile, factor
+// and inverse, publish: about 80 us, measured at n = 8192); three
+// refinement sweeps of 2 nb block steps.  A tile product takes about 22 us
+// (8.6 ms for the n = 8192 factor on 148 CTAs).
+double blk_solve_us(int64_t n, int G) {
+  const double tile = 22.0, chain = 80.0, step = 8.0;
+  const int64_t nb = (n + BKB - 1) / BKB;
+  double t = 0.0;
+  for (int64_t p = 0; p + 1 < nb; ++p) {
+    const int64_t nr = nb - 1 - p, tiles = nr * (nr + 1) / 2;
+    t += (double)((nr + G - 1) / G) * tile;
+    const int64_t Gr = std::max(G - 1, 1);
+    t += std::max((double)((tiles - 1 + Gr - 1) / Gr) * tile, chain);
+  }
+  return t + 3.0 * 2.0 * (double)nb * step;
+}
+
+// CTAs per instance of a grouped solve on S SMs (two at least): each spare
+// CTA goes to the instance predicted to finish last, up to the CTAs its
+// first panel can use.  Empty if S cannot give every instance two.
+std::vector<int> blk_split(const std::vector<int64_t> &n, int S) {
+  const int k = (int)n.size();
+  if (2 * k > S) return {};
+  std::vector<int> G(k, 2);
+  std::vector<double> t(k);
+  for (int i = 0; i < k; ++i) t[i] = blk_solve_us(n[i], 2);
+  for (int used = 2 * k; used < S; ++used) {
+    int w = -1;
+    for (int i = 0; i < k; ++i) {
+      const int64_t nr = (n[i] + BKB - 1) / BKB - 1;
+      if (G[i] < nr * (nr + 1) / 2 + 1 && (w < 0 || t[i] > t[w])) w = i;
+    }
+    if (w < 0) break;
+    t[w] = blk_solve_us(n[w], ++G[w]);
+  }
+  return G;
+}
+
+// One cooperative launch of the FP32 factors and refinements of the
+// instances in `idx` (batches of BLK_GROUP_MAX, each on the whole GPU).
+nqs_status batch_group_solve(nqs_batch *b, const std::vector<int> &idx,
+                             const nqs_step_hparams *hps, cudaStream_t st) {
+  if (idx.empty()) return NQS_OK;
+  const size_t smem = chol_blk_smem();
+  CU(cudaFuncSetAttribute((const void *)k_chol_blk_group,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_blk_group, BKB_THREADS, smem));
+  const int S = std::max(per, 1) * b->ctx[idx[0]]->rd.sm_count;
+  const int chunk = std::min<int>(BLK_GROUP_MAX, S / 2);
+  for (size_t i0 = 0; i0 < idx.size(); i0 += chunk) {
+    const int k = (int)std::min<size_t>(chunk, idx.size() - i0);
+    std::vector<int64_t> R(k);
+    for (int j = 0; j < k; ++j) {
+      const nqs_ctx *c = b->ctx[idx[i0 + j]];
+      R[j] = c->L.cplx ? 2 * hps[idx[i0 + j]].n_samples : hps[idx[i0 + j]].n_samples;
+    }
+    const std::vector<int> G = blk_split(R, S);
+    if ((int)G.size() != k) return NQS_ERR_UNSUPPORTED;
+    CholBlkGroup gr{};
+    gr.n = k;
+    gr.cta0[0] = 0;
+    for (int j = 0; j < k; ++j) {
+      nqs_ctx *c = b->ctx[idx[i0 + j]];
+      gr.inst[j] = blk_args(c, W<double>(c, c->off.T), R[j], W<double>(c, c->off.eps),
+                            W<double>(c, c->off.x), W<int32_t>(c, c->off.sstat));
+      gr.cta0[j + 1] = gr.cta0[j] + G[j];
+      if (j == 0) c->launches += 1;  // the grouped launch, counted once
+    }
+    void *args[] = {&gr};
+    CU(cudaLaunchCooperativeKernel((const void *)k_chol_blk_group, dim3(gr.cta0[k]),
+                                   dim3(BKB_THREADS), args, smem, st));
+  }
+  return NQS_OK;
+}
+
+// The batched step by stage: every instance's step up to its solve on the
+// instance streams, one grouped launch of the FP32 solves, then the rest of
+// every step on the instance streams.
+nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *mo,
+                               const nqs_step_hparams *hps, nqs_step_stats *const *stats,
+                               bool set_steps, cudaStream_t origin) {
+  const int n = (int)b->ctx.size(), q = batch_conc(b);
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    const int64_t R = c->L.cplx ? 2 * hps[i].n_samples : hps[i].n_samples;
+    c->in_group = group_solvable(c, R) ? 1 : 0;
+    if (c->in_group) idx.push_back(i);
+  }
+  nqs_status s = NQS_OK;
+  for (int ph : {STEP_PRE, STEP_POST}) {
+    CU(cudaEventRecord(b->fork, origin));
+    for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+    // cooperative solves outside the group (and the gated FP64 fallbacks)
+    // still run one after another
+    int prev = -1;
+    for (int i = 0; i < n && s == NQS_OK; ++i) {
+      nqs_ctx *c = b->ctx[i];
+      cudaStream_t st = b->st[i % q];
+      if (set_steps && ph == STEP_PRE) {
+        k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
+        c->launches += 1;
+      }
+      c->phase = ph;
+      if (ph == STEP_POST) {
+        c->solve_wait = prev >= 0 ? b->solved[prev] : nullptr;
+        c->solve_rec = b->solved[i];
+        prev = i;
+      }
+      s = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, st);
+      c->solve_wait = c->solve_rec = nullptr;
+      c->phase = STEP_ALL;
+    }
+    for (int j = 0; j < q; ++j) {
+      CU(cudaEventRecord(b->done[j], b->st[j]));
+      CU(cudaStreamWaitEvent(origin, b->done[j], 0));
+    }
+    if (s != NQS_OK) break;
+    if (ph == STEP_PRE) s = batch_group_solve(b, idx, hps, origin);
+    if (s != NQS_OK) break;
+  }
+  for (nqs_ctx *c : b->ctx) c->in_group = 0;
+  return s;
+}
+
 // Fork the instances' steps from `origin` onto the instance streams and join
 // them back; cooperative solves run one after another (instance order).
 nqs_status batch_issue(nqs_batch *b, double *const *th, double *const *mo,
                        const nqs_step_hparams *hps, nqs_step_stats *const *stats, bool set_steps,
                        cudaStream_t origin) {
+  if (b->grouped) return batch_issue_grouped(b, th, mo, hps, stats, set_steps, origin);
   const int n = (int)b->ctx.size(), q = batch_conc(b);
   CU(cudaEventRecord(b->fork, origin));
   for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
@@ -1921,7 +2083,9 @@ nqs_status batch_step(nqs_batch *b, double *const *th, double *const *mo,
       k.hp.push_back(h);
     }
     k.conc = batch_conc(b);
-    bool same = b->gexec && k.ptr == b->key.ptr && k.conc == b->key.conc;
+    k.grouped = b->grouped;
+    bool same = b->gexec && k.ptr == b->key.ptr && k.conc == b->key.conc &&
+                k.grouped == b->key.grouped;
     for (int i = 0; same && i < n; ++i)
       same = std::memcmp(&k.hp[i], &b->key.hp[i], sizeof(nqs_step_hparams)) == 0;
     if (!same) {
@@ -2020,6 +2184,18 @@ nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams) {
   return NQS_OK;
 }
 
+nqs_status nqs_batch_set_grouped(nqs_batch *b, int enable) {
+  if (!b || (enable != 0 && enable != 1)) return NQS_ERR_ARG;
+  b->grouped = enable;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *enabled) {
+  if (!b || !enabled) return NQS_ERR_ARG;
+  *enabled = b->grouped;
+  return NQS_OK;
+}
+
 nqs_status nqs_minsr_step_batched(nqs_batch *b, double *const *thetas, double *const *moms,
                                   const nqs_step_hparams *hps, nqs_step_stats *dev_stats,
                                   void *stream) {
@@ -2103,7 +2279,24 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
       if (it != g_tune_cache.end()) it->second.solve_grid = b->ctx[i]->t_solve_grid;
     }
   }
-  // (4) one graph replay per step, or the launches themselves, whichever is
+  // (4) by stage (the FP32 solves of all instances in one launch) or whole
+  // steps per stream
+  if (s == NQS_OK) {
+    const int g_saved = b->grouped;
+    b->grouped = 1 - g_saved;
+    double ms = 0;
+    s = best_ms(st, 2, [&] {
+      for (int i = 0; i < n; ++i) {
+        const int64_t np = b->ctx[i]->L.np;
+        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
+      }
+      return NQS_OK;
+    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
+    if (s == NQS_OK && ms < best) best = ms;
+    else b->grouped = g_saved;
+  }
+  // (5) one graph replay per step, or the launches themselves, whichever is
   // faster for this batch (a captured step can order the instances' kernels
   // less favourably than the eager issue)
   b->graph_enabled = saved_graph;

@@ -66,7 +66,8 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_batch_autotune", "nqs_eloc_work", "nqs_create_ex", "nqs_checkpoint_stride",
            "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
            "nqs_shard_solve", "nqs_shard_apply", "nqs_test_wait_timeout", "nqs_adam_step",
-           "nqs_energy_scan", "nqs_set_solve_form", "nqs_set_sampler",
+           "nqs_energy_scan", "nqs_set_solve_form", "nqs_set_sampler", "nqs_batch_set_grouped",
+           "nqs_batch_get_grouped",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -473,6 +474,16 @@ class Batch:
         v = C.c_int()
         _check(lib().nqs_batch_get_concurrency(self._h, C.byref(v)))
         return v.value
+
+    def set_grouped(self, enable=True):
+        """Batched step by stage: the FP32 solves of all instances in one
+        cooperative launch (nqs_batch_set_grouped)."""
+        _check(lib().nqs_batch_set_grouped(self._h, 1 if enable else 0))
+
+    def grouped(self):
+        v = C.c_int()
+        _check(lib().nqs_batch_get_grouped(self._h, C.byref(v)))
+        return bool(v.value)
 
 
 def decode_stats(stats: torch.Tensor) -> dict:

@@ -224,3 +224,51 @@ def test_batch_autotune_then_step():
     th0, mo0, st0 = _solo(sub, 2, tuned=True)
     for i in range(len(sub)):
         assert torch.equal(th[i], th0[i]), i
+
+
+@pytest.mark.parametrize("graph", [True, False], ids=["graph", "eager"])
+def test_grouped_solves_equal_solo(graph):
+    """The batched step by stage (one cooperative launch for the FP32
+    solves of all mixed instances, each on its own CTA range) gives every
+    instance exactly what its own step gives with the same solve form (128-wide
+    panels): the factor's tiles and the refinement's rows do not depend on
+    how many CTAs share them.  A mixed instance outside the group (R = 150,
+    below one 256-row block pair) and the FP64 instances take their own
+    solves in the second half of the step."""
+    inst = INSTANCES + [(ModelSpec(1, 16, 1, 32), HamSpec("tfim"), "mixed", 150, "tfim")]
+    steps = 3
+    ctxs0, th0, mo0, hps = _setup(inst)
+    n00 = sum(c.launch_count() for c in ctxs0)
+    st0 = []
+    for c, t, m, hp, (_, _, prec, ns, _) in zip(ctxs0, th0, mo0, hps, inst):
+        R = ns * (2 if c.model.cplx else 1)
+        if prec == "mixed" and R >= 256 and R % 4 == 0:
+            c.set_solve_form(2)
+        s = c.new_stats()
+        for k in range(steps):
+            c.minsr_step(t, m, hp, k, s)
+        st0.append(s)
+    torch.cuda.synchronize()
+    ctxs, th, mo, hps = _setup(inst)
+    b = nqs.Batch(ctxs)
+    b.use_graph(graph)
+    b.set_grouped(True)
+    assert b.grouped()
+    stats = b.new_stats()
+    n0 = sum(c.launch_count() for c in ctxs)
+    for k in range(steps):
+        b.step(th, mo, hps, k, stats)
+    torch.cuda.synchronize()
+    assert b.graph_active() == graph
+    for i in range(len(inst)):
+        d = nqs.decode_stats(stats[i])
+        assert d["status"] == 0, (i, d)
+        assert d["solve_fp64"] == (inst[i][2] == "fp64"), (i, d)
+        assert torch.equal(th[i], th0[i]), i
+        assert torch.equal(mo[i], mo0[i]), i
+        assert torch.equal(stats[i], st0[i]), i
+    if not graph:
+        # per step: one grouped launch instead of four cooperative factors
+        solo = sum(c.launch_count() for c in ctxs0) - n00
+        assert sum(c.launch_count() for c in ctxs) - n0 == solo - 3 * steps
+    b.close()
