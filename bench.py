@@ -848,11 +848,15 @@ def run_batched(args):
     barrier()
     clk = clocks.stop()
     batch_graph = bool(b.graph_active())
-    batch_grouped = bool(b.grouped())
+    batch_grouped = b.grouped()
     # by stage, the FP32 solves of the mixed instances with R % 4 == 0 and
-    # R >= 256 are one launch
+    # R >= 256 are one launch (bit 1), the streamed local-energy engines one
+    # launch per hidden size (bit 2)
     n_group = sum(1 for w in insts
                   if (lambda R: R >= 256 and R % 4 == 0)(w.hp.ns * (2 if w.model.cplx else 1)))
+    tcs_dh = [w.model.dh for w in insts if w.model.dim == 2 and w.model.dh in (96, 128)]
+    saved = ((max(n_group - 1, 0) if batch_grouped & 1 else 0) +
+             (len(tcs_dh) - len(set(tcs_dh)) if batch_grouped & 2 else 0))
     ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     value = aggregate_rate(world, K, ms)
     st = [nqs.decode_stats(stats[i]) for i in range(n)]
@@ -971,8 +975,8 @@ def run_batched(args):
                 "solo_sum_ms": solo_ms, "concurrency_gain": solo_ms / (ms / K),
                 "gram_tflops": gram_fl / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int((launches - (max(n_group - 1, 0) if batch_grouped else 0)) * K),
-                "clocks": clk, "cuda_graph": batch_graph, "solves_grouped": batch_grouped,
+                "gpu_launches": int((launches - saved) * K),
+                "clocks": clk, "cuda_graph": batch_graph, "grouped_stages": {"solve": bool(batch_grouped & 1), "eloc": bool(batch_grouped & 2)},
                 "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
                 "fp64_path": fp64, "matched_energy": matched, "per_config": per_config,
                 "errors_vs_oracle": load_errors(),

@@ -377,23 +377,27 @@ nqs_status nqs_batch_graph_active(const nqs_batch *b, int *active);
 nqs_status nqs_batch_set_concurrency(nqs_batch *b, int streams);
 nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams);
 
-/* Batched step by stage (enable = 1): every instance's step up to its solve
- * on the instance streams; then one cooperative launch of the FP32 factors
- * and refinements (128-wide panels, Eq. minsrR) of all mixed instances with
- * R % 4 == 0 and R >= 256 (unless nqs_set_solve_form picked another form),
- * each instance on its own range of CTAs sized by a model of its panel
- * chain, so that the solves no longer run one after another; then the rest
- * of every step on the instance streams.  x stays FP64-accurate (the same
- * refinement test and FP64 fallback) and is bit-identical to the instance's
- * own step with solve form 2.  enable = 0 (default): whole steps per
- * instance stream. */
-nqs_status nqs_batch_set_grouped(nqs_batch *b, int enable);
-nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *enabled);
+/* Batched step by stage.  stages = 0 (default): whole steps per instance
+ * stream.  Bit 1: every instance's step up to its solve on the instance
+ * streams; then one cooperative launch of the FP32 factors and refinements
+ * (128-wide panels, Eq. minsrR) of all mixed instances with R % 4 == 0 and
+ * R >= 256 (unless nqs_set_solve_form picked another form), each instance on
+ * its own range of CTAs sized by a model of its panel chain; then the rest
+ * of every step.  x stays FP64-accurate (the same refinement test and FP64
+ * fallback) and is bit-identical to the instance's own step with solve form
+ * 2.  Bit 2: the local-energy engines of the mixed 2D instances of hidden
+ * size 96 or 128 (Sec. II.C) run as one launch per hidden size, each instance
+ * on its own range of CTAs (shares from the autotuner's engine times) with
+ * its own tile counter; the local energies are bit-identical to the
+ * instance's own step. */
+nqs_status nqs_batch_set_grouped(nqs_batch *b, int stages);
+nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *stages);
 
 /* nqs_autotune for every instance, then, by timing whole batched steps
  * (best of two or three) on the workspace copies of theta: the concurrency,
- * the fraction of the SMs each instance's cooperative solve takes, whether
- * the batched step runs by stage (nqs_batch_set_grouped), and, if
+ * the fraction of the SMs each instance's cooperative solve takes, which
+ * stages run grouped (nqs_batch_set_grouped: none, the solves, the solves
+ * and the local-energy engines), and, if
  * graphs are enabled (nqs_batch_set_graph), whether a graph replay or the
  * eager launches are faster (graphs stay off when they are not).  The
  * fastest batched step time goes to *step_ms (may be NULL).  Synchronous;

@@ -63,6 +63,19 @@ cudaError_t eloc2d_tc_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaSt
 bool eloc2d_tcs_supported(int dim, int dh);
 size_t eloc2d_tcs_image_bytes(int dh);
 cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st);
+// The same in two parts, for a grouped launch: the weight image of one
+// instance, then one launch over several instances of hidden size dh (each
+// with its image written, its counter zeroed and cta0[i + 1] - cta0[i] CTAs,
+// at most its tile count; the column buffer of instance i must hold that
+// many CTAs' slices; grid = cta0[n] <= the SM count).
+constexpr int ELOC2D_GROUP_MAX = 32;
+struct Eloc2dTcGroup {
+  int n;
+  int cta0[ELOC2D_GROUP_MAX + 1];
+  Eloc2dTcArgs inst[ELOC2D_GROUP_MAX];
+};
+cudaError_t eloc2d_tcs_image(const Eloc2dTcArgs &args, int dh, cudaStream_t st);
+cudaError_t eloc2d_tcs_group_run(const Eloc2dTcGroup &g, int dh, cudaStream_t st);
 // Sampling of ns configurations with the same engine (args.ns, ntiles =
 // ceil(ns / 128), Lx <= 16, the column buffer and counter as above).
 bool eloc2d_tcs_sample_supported(int dim, int dh, int Lx);

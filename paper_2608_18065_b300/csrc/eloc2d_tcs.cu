@@ -160,9 +160,11 @@ __device__ __forceinline__ void tile_sched(const Eloc2dTcArgs &a, int tile, int 
 }
 
 // SMP: sampling mode (tiles of 128 samples from site 0, sigma_k drawn from
-// the conditionals) instead of the connected configurations' suffixes.
+// the conditionals) instead of the connected configurations' suffixes.  The
+// engine of one instance as CTA `cta` of those that share its tile counter
+// (its column buffer slice is the CTA's).
 template <int DH, bool SMP>
-__global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k_eloc2d_tcs(const Eloc2dTcArgs a) {
+__device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
   using C = Tcs<DH>;
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
       const uint8_t *sp = a.spins + (int64_t)s * N;
       const float *lcrow = a.lccache + (int64_t)s * N * 2;
       const float *hrow = a.hcache + (int64_t)s * N * DH;
-      float *cb = a.colbuf + ((int64_t)blockIdx.x * C::TR + row) * Lx * DH;
+      float *cb = a.colbuf + ((int64_t)cta * C::TR + row) * Lx * DH;
       auto colof = [&](int k) {
         const int jr = k / Lx, m = k - jr * Lx;
         return (jr & 1) ? (Lx - 1 - m) : m;
@@ -682,6 +684,31 @@ __global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS) k
                  : "memory");
 }
 
+template <int DH, bool SMP>
+__global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS)
+    k_eloc2d_tcs(const __grid_constant__ Eloc2dTcArgs a) {
+  tcs_body<DH, SMP>(a, (int)blockIdx.x);
+}
+
+// The local energies of several instances of one hidden size in one
+// launch: instance i owns the CTAs [cta0[i], cta0[i + 1]) and its own tile
+// counter, so the instances' tiles run side by side instead of one launch
+// after another.
+template <int DH>
+__global__ void __launch_bounds__(Tcs<DH>::THREADS) __maxnreg__(Tcs<DH>::REGS)
+    k_eloc2d_tcs_group(const __grid_constant__ Eloc2dTcGroup g) {
+  // the instance's arguments in shared memory (uniform loads, no indexed
+  // parameter reads in the loops)
+  __shared__ Eloc2dTcArgs s_args;
+  int i = 0;
+  while (i + 1 < g.n && (int)blockIdx.x >= g.cta0[i + 1]) ++i;
+  static_assert(sizeof(Eloc2dTcArgs) % 8 == 0, "argument copy");
+  for (int e = threadIdx.x; e < (int)(sizeof(Eloc2dTcArgs) / 8); e += blockDim.x)
+    reinterpret_cast<uint64_t *>(&s_args)[e] = reinterpret_cast<const uint64_t *>(&g.inst[i])[e];
+  __syncthreads();
+  tcs_body<DH, false>(s_args, (int)blockIdx.x - g.cta0[i]);
+}
+
 // The weight image: every stage of the two products as a K atom (64 k, 128 B
 // rows, 128-byte swizzle) of BF16 hi then lo, in the order the MMAs use them:
 // [U1; U2] atom 0 hi, lo, atom 1 hi, lo; then per gate chunk the same four.
@@ -717,12 +744,18 @@ __global__ void k_eloc2d_tcs_image(const float *__restrict__ pack, int oWgT, int
   }
 }
 
-template <int DH, bool SMP>
-cudaError_t run_dh(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st) {
+template <int DH>
+cudaError_t image_dh(const Eloc2dTcArgs &args, cudaStream_t st) {
   using C = Tcs<DH>;
   k_eloc2d_tcs_image<DH><<<C::IMG / 2 / 256 / 4 + 1, 256, 0, st>>>(
       args.pack, args.oWgT, args.oU12T, const_cast<unsigned char *>(args.wimg));
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+template <int DH, bool SMP>
+cudaError_t run_dh(const Eloc2dTcArgs &args, int sm_count, cudaStream_t st) {
+  using C = Tcs<DH>;
+  cudaError_t e = image_dh<DH>(args, st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_eloc2d_tcs<DH, SMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::SMEM);
@@ -744,6 +777,34 @@ size_t eloc2d_tcs_image_bytes(int dh) {
 cudaError_t eloc2d_tcs_run(const Eloc2dTcArgs &args, int dh, int sm_count, cudaStream_t st) {
   if (dh == 128) return run_dh<128, false>(args, sm_count, st);
   if (dh == 96) return run_dh<96, false>(args, sm_count, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t eloc2d_tcs_image(const Eloc2dTcArgs &args, int dh, cudaStream_t st) {
+  if (dh == 128) return image_dh<128>(args, st);
+  if (dh == 96) return image_dh<96>(args, st);
+  return cudaErrorInvalidValue;
+}
+
+namespace {
+template <int DH>
+cudaError_t group_dh(const Eloc2dTcGroup &g, cudaStream_t st) {
+  using C = Tcs<DH>;
+  cudaError_t e = cudaFuncSetAttribute(k_eloc2d_tcs_group<DH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  k_eloc2d_tcs_group<DH><<<g.cta0[g.n], C::THREADS, C::SMEM, st>>>(g);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t eloc2d_tcs_group_run(const Eloc2dTcGroup &g, int dh, cudaStream_t st) {
+  if (g.n < 1 || g.n > ELOC2D_GROUP_MAX || g.cta0[0] != 0) return cudaErrorInvalidValue;
+  for (int i = 0; i < g.n; ++i)
+    if (g.cta0[i + 1] <= g.cta0[i] || g.cta0[i + 1] - g.cta0[i] > g.inst[i].ntiles)
+      return cudaErrorInvalidValue;
+  if (dh == 128) return group_dh<128>(g, st);
+  if (dh == 96) return group_dh<96>(g, st);
   return cudaErrorInvalidValue;
 }
 

@@ -84,13 +84,17 @@ struct nqs_ctx {
   int64_t cur_ns = 0;  // sample count of the step being issued
   // batched steps: order this context's cooperative solve after another's
   cudaEvent_t solve_wait = nullptr, solve_rec = nullptr;
-  // batched steps by stage: issue only the part of the step before the
-  // solve (STEP_PRE) or from it on (STEP_POST); in_group: the FP32 factor
-  // runs in the batch's grouped launch, not in this context's step
-  int phase = 0, in_group = 0;
+  // batched steps by stage: issue only the part of the step up to the
+  // local-energy engine (STEP_PRE_A), from there to the solve (STEP_PRE_B)
+  // or from the solve on (STEP_POST); in_group: the FP32 factor runs in the
+  // batch's grouped launch; in_eloc_group: so does the streamed local-energy
+  // engine, with the arguments left in eloc_args
+  int phase = 0, in_group = 0, in_eloc_group = 0;
+  Eloc2dTcArgs eloc_args{};
 };
 
-constexpr int STEP_ALL = 0, STEP_PRE = 1, STEP_POST = 2;
+constexpr int STEP_ALL = 0, STEP_PRE_A = 1, STEP_PRE_B = 2, STEP_POST = 3;
+constexpr int GROUP_SOLVE = 1, GROUP_ELOC = 2;
 
 namespace {
 
@@ -337,7 +341,18 @@ nqs_status pack_any(nqs_ctx *c, const double *theta, cudaStream_t st) {
 
 // Local energies of the ns configurations whose hidden states are cached.
 template <typename T>
-nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cudaStream_t st) {
+// part: 0 the whole stage; 1 up to the engine of the streamed local-energy
+// engine, whose arguments go to c->eloc_args for a grouped launch; 2 the
+// reduction after that launch.
+nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cudaStream_t st,
+                  int part = 0) {
+  if (part == 2) {
+    mark(c, 4, st);
+    c->launches += 1;
+    k_eloc_reduce<<<(unsigned)((eloc_reduce_threads(ns) + 255) / 256), 256, 0, st>>>(
+        c->d_diag, c->n_diag, c->n_off, spins, c->L.N, ns, W<double>(c, c->off.contrib), eloc);
+    return cu(cudaGetLastError());
+  }
   mark(c, 2, st);
   if (c->n_off > 0) {
     c->launches += 2;
@@ -419,8 +434,13 @@ nqs_status eloc_T(nqs_ctx *c, int64_t ns, const uint8_t *spins, double *eloc, cu
       e.wimg = reinterpret_cast<const unsigned char *>(c->ws + c->off.wimg);
       e.spin_limit = c->test_spin_limit;
       e.test_drop_tile = c->test_drop_tile;
-      c->launches += 2;
+      c->launches += part == 1 ? 1 : 2;
       CU(cudaMemsetAsync(e.tile_ctr, 0, sizeof(int), st));
+      if (part == 1) {  // the engine runs in the batch's grouped launch
+        c->eloc_args = e;
+        CU(eloc2d_tcs_image(e, c->L.dh, st));
+        return NQS_OK;
+      }
       CU(eloc2d_tcs_run(e, c->L.dh, eloc_grid_cap(c, c->rd.sm_count), st));
     } else {
       CU(run_forward<T>(c->rd, MODE_ELOC, a, eloc_grid_cap(c, c->eloc_grid), st));
@@ -851,7 +871,7 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
   const bool tc = f32(c) && gram_tc_available();
   const RetryInfo rinfo{hp, stats};
   const int ph = c->phase;
-  if (ph != STEP_POST) {
+  if (ph == STEP_ALL || ph == STEP_PRE_A) {
     mark(c, 0, st);
     CU(cudaMemsetAsync(sstat, 0, 64, st));
     // Alg. 1, sampling: sample (also fills the hidden-state caches)
@@ -869,7 +889,11 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
       ST(run_sample<T>(c, a, st));
     }
     // Alg. 1, energy: local energies, E, variance; eps-bar'
-    ST(eloc_T<T>(c, ns, spins, eloc, st));
+    ST(eloc_T<T>(c, ns, spins, eloc, st, ph == STEP_PRE_A && c->in_eloc_group ? 1 : 0));
+    if (ph == STEP_PRE_A) return NQS_OK;
+  }  // ph == STEP_ALL || ph == STEP_PRE_A
+  if (ph == STEP_ALL || ph == STEP_PRE_B) {
+    if (ph == STEP_PRE_B && c->in_eloc_group) ST(eloc_T<T>(c, ns, spins, eloc, st, 2));
     mark(c, 5, st);
     k_energy<<<1, 1024, 0, st>>>(eloc, ns, (int)N, c->L.cplx, stats, eps);
     c->launches += 1;
@@ -918,9 +942,9 @@ nqs_status step_T(nqs_ctx *c, double *theta, double *mom, const nqs_step_hparams
       CU(cudaGetLastError());
     }
     mark(c, 11, st);
-    if (ph == STEP_PRE)
+    if (ph == STEP_PRE_B)
       return c->in_group ? chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo, 1) : NQS_OK;
-  }  // ph != STEP_POST
+  }  // ph == STEP_ALL || ph == STEP_PRE_B
   // Alg. 1, solve: x = (T + lambda I)^{-1} eps', eta, delta theta = eta O' x
   if (c->solve_wait) CU(cudaStreamWaitEvent(st, c->solve_wait, 0));
   ST(chol_solve(c, Tm, R, eps, x, sstat, st, &rinfo, ph == STEP_POST && c->in_group ? 2 : 0));
@@ -1873,7 +1897,9 @@ struct nqs_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_enabled = 0, graph_broken = 0;
-  int grouped = 0;  // by stage: the FP32 solves of all instances in one launch
+  // by stage: GROUP_SOLVE, the FP32 solves of all instances in one launch;
+  // GROUP_ELOC, the streamed local-energy engines in one launch per hidden size
+  int grouped = 0;
   struct Key {
     std::vector<const void *> ptr;  // theta, momentum, stats of every instance
     std::vector<nqs_step_hparams> hp;
@@ -1978,9 +2004,71 @@ nqs_status batch_group_solve(nqs_batch *b, const std::vector<int> &idx,
   return NQS_OK;
 }
 
-// The batched step by stage: every instance's step up to its solve on the
-// instance streams, one grouped launch of the FP32 solves, then the rest of
-// every step on the instance streams.
+// Whether a batch may run this context's local-energy engine in its grouped
+// launch (the streamed tensor-core engine, hidden sizes 96 and 128).
+bool eloc_groupable(const nqs_ctx *c) {
+  return f32(c) && c->ck == 0 && c->n_off > 0 && gram_tc_available() &&
+         eloc2d_tcs_supported(c->L.dim, c->L.dh) && !eloc2d_tc_supported(c->L.dim, c->L.dh);
+}
+
+// CTAs per instance of a grouped engine launch on S SMs: one each, then each
+// spare CTA to the instance with the most work per CTA, up to its tile count.
+std::vector<int> eloc_split(const std::vector<double> &work, const std::vector<int> &cap, int S) {
+  const int k = (int)work.size();
+  std::vector<int> G(k, 1);
+  for (int used = k; used < S; ++used) {
+    int w = -1;
+    for (int i = 0; i < k; ++i)
+      if (G[i] < cap[i] && (w < 0 || work[i] / G[i] > work[w] / G[w])) w = i;
+    if (w < 0) break;
+    ++G[w];
+  }
+  return G;
+}
+
+// One launch of the streamed local-energy engine per hidden size over the
+// instances whose step left its arguments (in_eloc_group).  An instance's
+// share of the SMs follows its engine time measured by the autotuner (times
+// the CTAs it was measured on), else its tiles times its sites.
+nqs_status batch_group_eloc(nqs_batch *b, cudaStream_t st) {
+  for (int dh : {128, 96}) {
+    std::vector<int> idx;
+    for (int i = 0; i < (int)b->ctx.size(); ++i)
+      if (b->ctx[i]->in_eloc_group && b->ctx[i]->L.dh == dh) idx.push_back(i);
+    if (idx.empty()) continue;
+    const int S = b->ctx[idx[0]]->rd.sm_count;
+    bool measured = true;
+    for (int i : idx) measured = measured && tuned(b->ctx[i]) && b->ctx[i]->t_ms[0] > 0;
+    const int chunk = std::min(ELOC2D_GROUP_MAX, S);
+    for (size_t i0 = 0; i0 < idx.size(); i0 += chunk) {
+      const int k = (int)std::min<size_t>(chunk, idx.size() - i0);
+      std::vector<double> work(k);
+      std::vector<int> cap(k);
+      for (int j = 0; j < k; ++j) {
+        const nqs_ctx *c = b->ctx[idx[i0 + j]];
+        cap[j] = c->eloc_args.ntiles;
+        work[j] = measured ? c->t_ms[0] * eloc_grid_cap(c, S)
+                           : (double)c->eloc_args.ntiles * (double)c->L.N;
+      }
+      const std::vector<int> G = eloc_split(work, cap, S);
+      Eloc2dTcGroup g{};
+      g.n = k;
+      g.cta0[0] = 0;
+      for (int j = 0; j < k; ++j) {
+        g.inst[j] = b->ctx[idx[i0 + j]]->eloc_args;
+        g.cta0[j + 1] = g.cta0[j] + G[j];
+      }
+      b->ctx[idx[i0]]->launches += 1;  // the grouped launch, counted once
+      CU(eloc2d_tcs_group_run(g, dh, st));
+    }
+  }
+  return NQS_OK;
+}
+
+// The batched step by stage: every instance's step up to its local-energy
+// engine on the instance streams, one launch of the streamed engine per
+// hidden size over the instances that use it, every step on to its solve,
+// one grouped launch of the FP32 solves, then the rest of every step.
 nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *mo,
                                const nqs_step_hparams *hps, nqs_step_stats *const *stats,
                                bool set_steps, cudaStream_t origin) {
@@ -1990,10 +2078,12 @@ nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *m
     nqs_ctx *c = b->ctx[i];
     const int64_t R = c->L.cplx ? 2 * hps[i].n_samples : hps[i].n_samples;
     c->in_group = group_solvable(c, R) ? 1 : 0;
+    c->in_group = (b->grouped & GROUP_SOLVE) && c->in_group;
+    c->in_eloc_group = (b->grouped & GROUP_ELOC) && eloc_groupable(c) ? 1 : 0;
     if (c->in_group) idx.push_back(i);
   }
   nqs_status s = NQS_OK;
-  for (int ph : {STEP_PRE, STEP_POST}) {
+  for (int ph : {STEP_PRE_A, STEP_PRE_B, STEP_POST}) {
     CU(cudaEventRecord(b->fork, origin));
     for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
     // cooperative solves outside the group (and the gated FP64 fallbacks)
@@ -2002,7 +2092,7 @@ nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *m
     for (int i = 0; i < n && s == NQS_OK; ++i) {
       nqs_ctx *c = b->ctx[i];
       cudaStream_t st = b->st[i % q];
-      if (set_steps && ph == STEP_PRE) {
+      if (set_steps && ph == STEP_PRE_A) {
         k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
         c->launches += 1;
       }
@@ -2021,10 +2111,11 @@ nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *m
       CU(cudaStreamWaitEvent(origin, b->done[j], 0));
     }
     if (s != NQS_OK) break;
-    if (ph == STEP_PRE) s = batch_group_solve(b, idx, hps, origin);
+    if (ph == STEP_PRE_A) s = batch_group_eloc(b, origin);
+    if (ph == STEP_PRE_B) s = batch_group_solve(b, idx, hps, origin);
     if (s != NQS_OK) break;
   }
-  for (nqs_ctx *c : b->ctx) c->in_group = 0;
+  for (nqs_ctx *c : b->ctx) c->in_group = c->in_eloc_group = 0;
   return s;
 }
 
@@ -2184,15 +2275,15 @@ nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams) {
   return NQS_OK;
 }
 
-nqs_status nqs_batch_set_grouped(nqs_batch *b, int enable) {
-  if (!b || (enable != 0 && enable != 1)) return NQS_ERR_ARG;
-  b->grouped = enable;
+nqs_status nqs_batch_set_grouped(nqs_batch *b, int stages) {
+  if (!b || stages < 0 || stages > 3) return NQS_ERR_ARG;
+  b->grouped = stages;
   return NQS_OK;
 }
 
-nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *enabled) {
-  if (!b || !enabled) return NQS_ERR_ARG;
-  *enabled = b->grouped;
+nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *stages) {
+  if (!b || !stages) return NQS_ERR_ARG;
+  *stages = b->grouped;
   return NQS_OK;
 }
 
@@ -2279,22 +2370,26 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
       if (it != g_tune_cache.end()) it->second.solve_grid = b->ctx[i]->t_solve_grid;
     }
   }
-  // (4) by stage (the FP32 solves of all instances in one launch) or whole
-  // steps per stream
-  if (s == NQS_OK) {
+  // (4) by stage (the FP32 solves, and the streamed local-energy engines,
+  // of all instances in grouped launches) or whole steps per stream
+  {
     const int g_saved = b->grouped;
-    b->grouped = 1 - g_saved;
-    double ms = 0;
-    s = best_ms(st, 2, [&] {
-      for (int i = 0; i < n; ++i) {
-        const int64_t np = b->ctx[i]->L.np;
-        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
-        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
-      }
-      return NQS_OK;
-    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
-    if (s == NQS_OK && ms < best) best = ms;
-    else b->grouped = g_saved;
+    int g_pick = g_saved;
+    for (int g : {0, GROUP_SOLVE, GROUP_SOLVE | GROUP_ELOC}) {
+      if (s != NQS_OK || g == g_saved) continue;
+      b->grouped = g;
+      double ms = 0;
+      s = best_ms(st, 2, [&] {
+        for (int i = 0; i < n; ++i) {
+          const int64_t np = b->ctx[i]->L.np;
+          CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+          CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
+        }
+        return NQS_OK;
+      }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
+      if (s == NQS_OK && ms < best) { best = ms; g_pick = g; }
+    }
+    b->grouped = g_pick;
   }
   // (5) one graph replay per step, or the launches themselves, whichever is
   // faster for this batch (a captured step can order the instances' kernels

@@ -475,15 +475,18 @@ class Batch:
         _check(lib().nqs_batch_get_concurrency(self._h, C.byref(v)))
         return v.value
 
-    def set_grouped(self, enable=True):
-        """Batched step by stage: the FP32 solves of all instances in one
-        cooperative launch (nqs_batch_set_grouped)."""
-        _check(lib().nqs_batch_set_grouped(self._h, 1 if enable else 0))
+    def set_grouped(self, stages=3):
+        """Batched step by stage (nqs_batch_set_grouped): bit 1 the FP32
+        solves of all instances in one cooperative launch, bit 2 the
+        streamed local-energy engines in one launch per hidden size; True
+        is both, False neither."""
+        stages = 3 if stages is True else 0 if stages is False else int(stages)
+        _check(lib().nqs_batch_set_grouped(self._h, stages))
 
     def grouped(self):
         v = C.c_int()
         _check(lib().nqs_batch_get_grouped(self._h, C.byref(v)))
-        return bool(v.value)
+        return v.value
 
 
 def decode_stats(stats: torch.Tensor) -> dict:

@@ -226,34 +226,52 @@ def test_batch_autotune_then_step():
         assert torch.equal(th[i], th0[i]), i
 
 
-@pytest.mark.parametrize("graph", [True, False], ids=["graph", "eager"])
-def test_grouped_solves_equal_solo(graph):
-    """The batched step by stage (one cooperative launch for the FP32
-    solves of all mixed instances, each on its own CTA range) gives every
-    instance exactly what its own step gives with the same solve form (128-wide
-    panels): the factor's tiles and the refinement's rows do not depend on
-    how many CTAs share them.  A mixed instance outside the group (R = 150,
-    below one 256-row block pair) and the FP64 instances take their own
-    solves in the second half of the step."""
-    inst = INSTANCES + [(ModelSpec(1, 16, 1, 32), HamSpec("tfim"), "mixed", 150, "tfim")]
+GROUPED = INSTANCES + [
+    (ModelSpec(1, 16, 1, 32), HamSpec("tfim"), "mixed", 150, "tfim"),
+    (ModelSpec(2, 4, 4, 128, cplx=1, marshall=1, zmask=1), HamSpec("j1j2", J2=0.5), "mixed", 150, "j1j2"),
+    (ModelSpec(2, 5, 3, 96), HamSpec("j1j2", J2=0.0), "mixed", 130, "heisenberg"),
+]
+
+
+@pytest.mark.parametrize("graph,stages", [(True, 3), (False, 3), (False, 2), (False, 1)],
+                         ids=["graph-both", "eager-both", "eager-eloc", "eager-solve"])
+def test_grouped_stages_equal_solo(graph, stages):
+    """The batched step by stage (one launch of the streamed local-energy
+    engine per hidden size over the mixed 2D d_h 96 / 128 instances, one
+    cooperative launch for the FP32 solves of all mixed instances, each
+    instance on its own CTA range) gives every instance exactly what its own
+    step gives with the same solve form (128-wide panels): a tile's local
+    energies, the factor's tiles and the refinement's rows do not depend on
+    how many CTAs share them.  Mixed instances outside the solve group
+    (R = 150 and R = 130, not a multiple of 4) and the FP64 instances take
+    their own solves in the last part of the step."""
+    inst = GROUPED
     steps = 3
     ctxs0, th0, mo0, hps = _setup(inst)
     n00 = sum(c.launch_count() for c in ctxs0)
     st0 = []
-    for c, t, m, hp, (_, _, prec, ns, _) in zip(ctxs0, th0, mo0, hps, inst):
+    n_solve, eloc_dh, blk = 0, [], []
+    for i, (c, t, m, hp, (mod, _, prec, ns, _)) in enumerate(zip(ctxs0, th0, mo0, hps, inst)):
         R = ns * (2 if c.model.cplx else 1)
         if prec == "mixed" and R >= 256 and R % 4 == 0:
             c.set_solve_form(2)
+            n_solve += 1
+            blk.append(i)
+        if prec == "mixed" and mod.dim == 2 and mod.dh in (96, 128):
+            eloc_dh.append(mod.dh)
         s = c.new_stats()
         for k in range(steps):
             c.minsr_step(t, m, hp, k, s)
         st0.append(s)
     torch.cuda.synchronize()
+    assert n_solve == 5 and sorted(eloc_dh) == [96, 96, 128]
     ctxs, th, mo, hps = _setup(inst)
+    for i in blk:  # the same solve form where the solves stay apart (stages without bit 1)
+        ctxs[i].set_solve_form(2)
     b = nqs.Batch(ctxs)
     b.use_graph(graph)
-    b.set_grouped(True)
-    assert b.grouped()
+    b.set_grouped(stages)
+    assert b.grouped() == stages
     stats = b.new_stats()
     n0 = sum(c.launch_count() for c in ctxs)
     for k in range(steps):
@@ -268,7 +286,10 @@ def test_grouped_solves_equal_solo(graph):
         assert torch.equal(mo[i], mo0[i]), i
         assert torch.equal(stats[i], st0[i]), i
     if not graph:
-        # per step: one grouped launch instead of four cooperative factors
+        # per step: one grouped solve instead of five cooperative factors, one
+        # engine launch per hidden size instead of one per instance
         solo = sum(c.launch_count() for c in ctxs0) - n00
-        assert sum(c.launch_count() for c in ctxs) - n0 == solo - 3 * steps
+        saved = ((n_solve - 1) if stages & 1 else 0) + \
+            ((len(eloc_dh) - len(set(eloc_dh))) if stages & 2 else 0)
+        assert sum(c.launch_count() for c in ctxs) - n0 == solo - saved * steps
     b.close()
