@@ -393,8 +393,10 @@ nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams);
 nqs_status nqs_batch_set_grouped(nqs_batch *b, int stages);
 nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *stages);
 
-/* nqs_autotune for every instance, then, by timing whole batched steps
- * (best of two or three) on the workspace copies of theta: the concurrency,
+/* nqs_autotune for every instance, then, by timing whole batched steps on
+ * the workspace copies of theta (best of two for the concurrency and the
+ * solve SMs; candidates in turn, median of three, for the grouped stages and
+ * the graph): the concurrency,
  * the fraction of the SMs each instance's cooperative solve takes, which
  * stages run grouped (nqs_batch_set_grouped: none, the solves, the solves
  * and the local-energy engines), and, if

@@ -2371,25 +2371,40 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
     }
   }
   // (4) by stage (the FP32 solves, and the streamed local-energy engines,
-  // of all instances in grouped launches) or whole steps per stream
-  {
-    const int g_saved = b->grouped;
-    int g_pick = g_saved;
-    for (int g : {0, GROUP_SOLVE, GROUP_SOLVE | GROUP_ELOC}) {
-      if (s != NQS_OK || g == g_saved) continue;
-      b->grouped = g;
-      double ms = 0;
-      s = best_ms(st, 2, [&] {
-        for (int i = 0; i < n; ++i) {
-          const int64_t np = b->ctx[i]->L.np;
-          CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
-          CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
-        }
-        return NQS_OK;
-      }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &ms);
-      if (s == NQS_OK && ms < best) { best = ms; g_pick = g; }
+  // of all instances in grouped launches) or whole steps per stream: the
+  // candidates in turn, three rounds, the median of each (consecutive
+  // batched steps of one setting vary by several per cent with the clocks
+  // and the power cap, so a best-of-two favours the noisier setting)
+  auto reset = [&] {
+    for (int i = 0; i < n; ++i) {
+      const int64_t np = b->ctx[i]->L.np;
+      CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
     }
-    b->grouped = g_pick;
+    return NQS_OK;
+  };
+  auto step = [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); };
+  auto median3 = [](std::vector<double> v) {
+    std::sort(v.begin(), v.end());
+    return v[v.size() / 2];
+  };
+  if (s == NQS_OK) {
+    const int cands[3] = {0, GROUP_SOLVE, GROUP_SOLVE | GROUP_ELOC};
+    std::vector<double> t[3];
+    for (int r = 0; r < 3 && s == NQS_OK; ++r)
+      for (int j = 0; j < 3 && s == NQS_OK; ++j) {
+        b->grouped = cands[j];
+        double ms = 0;
+        s = best_ms(st, 1, reset, step, &ms);
+        t[j].push_back(ms);
+      }
+    if (s == NQS_OK) {
+      int pj = 0;
+      for (int j = 1; j < 3; ++j)
+        if (median3(t[j]) < median3(t[pj])) pj = j;
+      b->grouped = cands[pj];
+      best = median3(t[pj]);
+    }
   }
   // (5) one graph replay per step, or the launches themselves, whichever is
   // faster for this batch (a captured step can order the instances' kernels
@@ -2397,17 +2412,24 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
   b->graph_enabled = saved_graph;
   if (saved_graph && s == NQS_OK) {
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-    double gms = 0;
-    s = best_ms(st, 3, [&] {
-      for (int i = 0; i < n; ++i) {
-        const int64_t np = b->ctx[i]->L.np;
-        CU(cudaMemcpyAsync(th[i], thetas[i], np * 8, cudaMemcpyDeviceToDevice, st));
-        CU(cudaMemsetAsync(mo[i], 0, np * 8, st));
-      }
-      return NQS_OK;
-    }, [&] { return batch_step(b, th.data(), mo.data(), hps, sp.data(), st); }, &gms);
-    if (s == NQS_OK && gms > best) b->graph_enabled = 0;
-    else if (s == NQS_OK) best = gms;
+    // graph and eager steps in turn after one capture, medians of three
+    std::vector<double> tg, te;
+    double ms = 0;
+    s = best_ms(st, 1, reset, step, &ms);  // the capture
+    for (int r = 0; r < 3 && s == NQS_OK; ++r) {
+      b->graph_enabled = saved_graph;
+      s = best_ms(st, 1, reset, step, &ms);
+      tg.push_back(ms);
+      if (s != NQS_OK) break;
+      b->graph_enabled = 0;
+      s = best_ms(st, 1, reset, step, &ms);
+      te.push_back(ms);
+    }
+    if (s == NQS_OK) {
+      const bool g = median3(tg) <= median3(te);
+      b->graph_enabled = g ? saved_graph : 0;
+      best = g ? median3(tg) : median3(te);
+    }
   }
   if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
   if (step_ms) *step_ms = best;
