@@ -1895,6 +1895,11 @@ struct nqs_batch {
   std::vector<cudaEvent_t> done, solved;
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;
+  // by stage: an instance's part issued (part), the grouped launches' stream
+  // and their completion (grp)
+  std::vector<cudaEvent_t> part;
+  cudaStream_t gst = nullptr;
+  cudaEvent_t grp = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_enabled = 0, graph_broken = 0;
   // by stage: GROUP_SOLVE, the FP32 solves of all instances in one launch;
@@ -1915,8 +1920,11 @@ void batch_free(nqs_batch *b) {
   for (cudaStream_t s : b->st) if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : b->solved) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->part) if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->grp) cudaEventDestroy(b->grp);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->gst) cudaStreamDestroy(b->gst);
   delete b;
 }
 
@@ -2065,56 +2073,87 @@ nqs_status batch_group_eloc(nqs_batch *b, cudaStream_t st) {
   return NQS_OK;
 }
 
-// The batched step by stage: every instance's step up to its local-energy
-// engine on the instance streams, one launch of the streamed engine per
-// hidden size over the instances that use it, every step on to its solve,
-// one grouped launch of the FP32 solves, then the rest of every step.
+// The batched step by stage.  Every instance's step runs on its instance
+// stream in three parts; only the members of a grouped launch wait for it:
+// the streamed local-energy engine of the members of that group runs as one
+// launch per hidden size on the batch's group stream once their first parts
+// are done, and their second parts wait for it; the FP32 solves of the solve
+// group run as one cooperative launch once those members' second parts are
+// done.  The cooperative work after it (the members' gated FP64 fallbacks,
+// the other instances' own solves) stays chained in instance order behind
+// the grouped solve, so that no two cooperative kernels are resident at once.
 nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *mo,
                                const nqs_step_hparams *hps, nqs_step_stats *const *stats,
                                bool set_steps, cudaStream_t origin) {
   const int n = (int)b->ctx.size(), q = batch_conc(b);
   std::vector<int> idx;
+  bool any_eloc = false;
   for (int i = 0; i < n; ++i) {
     nqs_ctx *c = b->ctx[i];
     const int64_t R = c->L.cplx ? 2 * hps[i].n_samples : hps[i].n_samples;
-    c->in_group = group_solvable(c, R) ? 1 : 0;
-    c->in_group = (b->grouped & GROUP_SOLVE) && c->in_group;
+    c->in_group = (b->grouped & GROUP_SOLVE) && group_solvable(c, R) ? 1 : 0;
     c->in_eloc_group = (b->grouped & GROUP_ELOC) && eloc_groupable(c) ? 1 : 0;
     if (c->in_group) idx.push_back(i);
+    any_eloc = any_eloc || c->in_eloc_group;
   }
+  CU(cudaEventRecord(b->fork, origin));
+  for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+  CU(cudaStreamWaitEvent(b->gst, b->fork, 0));
   nqs_status s = NQS_OK;
-  for (int ph : {STEP_PRE_A, STEP_PRE_B, STEP_POST}) {
-    CU(cudaEventRecord(b->fork, origin));
-    for (int j = 0; j < q; ++j) CU(cudaStreamWaitEvent(b->st[j], b->fork, 0));
-    // cooperative solves outside the group (and the gated FP64 fallbacks)
-    // still run one after another
-    int prev = -1;
-    for (int i = 0; i < n && s == NQS_OK; ++i) {
-      nqs_ctx *c = b->ctx[i];
-      cudaStream_t st = b->st[i % q];
-      if (set_steps && ph == STEP_PRE_A) {
-        k_set_i64<<<1, 1, 0, st>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
-        c->launches += 1;
-      }
-      c->phase = ph;
-      if (ph == STEP_POST) {
-        c->solve_wait = prev >= 0 ? b->solved[prev] : nullptr;
-        c->solve_rec = b->solved[i];
-        prev = i;
-      }
-      s = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, st);
-      c->solve_wait = c->solve_rec = nullptr;
-      c->phase = STEP_ALL;
+  auto issue = [&](int i, int ph) {
+    nqs_ctx *c = b->ctx[i];
+    c->phase = ph;
+    const nqs_status r = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, b->st[i % q]);
+    c->phase = STEP_ALL;
+    return r;
+  };
+  // first parts; the engine group waits for its members'
+  for (int i = 0; i < n && s == NQS_OK; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    if (set_steps) {
+      k_set_i64<<<1, 1, 0, b->st[i % q]>>>(W<int64_t>(c, c->off.dstep), hps[i].step_index);
+      c->launches += 1;
     }
-    for (int j = 0; j < q; ++j) {
-      CU(cudaEventRecord(b->done[j], b->st[j]));
-      CU(cudaStreamWaitEvent(origin, b->done[j], 0));
+    s = issue(i, STEP_PRE_A);
+    if (s == NQS_OK && c->in_eloc_group) {
+      CU(cudaEventRecord(b->part[i], b->st[i % q]));
+      CU(cudaStreamWaitEvent(b->gst, b->part[i], 0));
     }
-    if (s != NQS_OK) break;
-    if (ph == STEP_PRE_A) s = batch_group_eloc(b, origin);
-    if (ph == STEP_PRE_B) s = batch_group_solve(b, idx, hps, origin);
-    if (s != NQS_OK) break;
   }
+  if (s == NQS_OK && any_eloc) {
+    s = batch_group_eloc(b, b->gst);
+    if (s == NQS_OK) CU(cudaEventRecord(b->grp, b->gst));
+  }
+  // second parts; the solve group waits for its members'
+  for (int i = 0; i < n && s == NQS_OK; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    if (c->in_eloc_group) CU(cudaStreamWaitEvent(b->st[i % q], b->grp, 0));
+    s = issue(i, STEP_PRE_B);
+    if (s == NQS_OK && c->in_group) {
+      CU(cudaEventRecord(b->part[i], b->st[i % q]));
+      CU(cudaStreamWaitEvent(b->gst, b->part[i], 0));
+    }
+  }
+  bool solve_grouped = false;
+  if (s == NQS_OK && !idx.empty()) {
+    s = batch_group_solve(b, idx, hps, b->gst);
+    if (s == NQS_OK) CU(cudaEventRecord(b->grp, b->gst));
+    solve_grouped = s == NQS_OK;
+  }
+  // the rest: cooperative work chained in instance order behind the group
+  for (int i = 0; i < n && s == NQS_OK; ++i) {
+    nqs_ctx *c = b->ctx[i];
+    c->solve_wait = i > 0 ? b->solved[i - 1] : (solve_grouped ? b->grp : nullptr);
+    c->solve_rec = b->solved[i];
+    s = issue(i, STEP_POST);
+    c->solve_wait = c->solve_rec = nullptr;
+  }
+  for (int j = 0; j < q; ++j) {
+    CU(cudaEventRecord(b->done[j], b->st[j]));
+    CU(cudaStreamWaitEvent(origin, b->done[j], 0));
+  }
+  CU(cudaEventRecord(b->grp, b->gst));
+  CU(cudaStreamWaitEvent(origin, b->grp, 0));
   for (nqs_ctx *c : b->ctx) c->in_group = c->in_eloc_group = 0;
   return s;
 }
@@ -2233,12 +2272,16 @@ nqs_status nqs_batch_create(int n, nqs_ctx *const *ctxs, nqs_batch **out) {
   b->st.assign(n, nullptr);
   b->done.assign(n, nullptr);
   b->solved.assign(n, nullptr);
+  b->part.assign(n, nullptr);
   bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+            cudaEventCreateWithFlags(&b->grp, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking) == cudaSuccess;
   for (int i = 0; ok && i < n; ++i)
     ok = cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&b->solved[i], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&b->solved[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->part[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) { batch_free(b); return NQS_ERR_CUDA; }
   *out = b;
   return NQS_OK;
