@@ -98,7 +98,10 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // acc[a][b] = sum_k X[ty + 16 a][k] Y[tx + 16 b][k] over k = k0 .. k0 + 31.
 // A warp reads two rows of X (broadcasts) and sixteen rows of Y (row
-// stride 132 floats: eight consecutive rows fall in distinct banks).
+// stride 132 floats: eight consecutive rows fall in distinct banks).  The
+// 64 accumulators take k, then k + 1, ... in turn, so that consecutive FMAs
+// are independent (measured: 11.3 against 12.7 us per 128-cube tile with
+// each accumulator's four k in a row; the same sums in the same order).
 __device__ __forceinline__ void mac_piece(const float *X, const float *Y, int k0, int tx, int ty,
                                           float (&acc)[8][8]) {
 #pragma unroll 2
@@ -111,12 +114,19 @@ __device__ __forceinline__ void mac_piece(const float *X, const float *Y, int k0
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        acc[a][b] = fmaf(xa[a].x, yb[b].x, acc[a][b]);
-        acc[a][b] = fmaf(xa[a].y, yb[b].y, acc[a][b]);
-        acc[a][b] = fmaf(xa[a].z, yb[b].z, acc[a][b]);
-        acc[a][b] = fmaf(xa[a].w, yb[b].w, acc[a][b]);
-      }
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(xa[a].x, yb[b].x, acc[a][b]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(xa[a].y, yb[b].y, acc[a][b]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(xa[a].z, yb[b].z, acc[a][b]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(xa[a].w, yb[b].w, acc[a][b]);
   }
 }
 
