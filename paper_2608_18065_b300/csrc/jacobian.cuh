@@ -284,7 +284,7 @@ k_jac_bwd(const BwdArgs<T> A) {
           dh1[0][1] = (T)c[1];
         }
       } else {
-        if (DIM == 2 || k > 0) mm_acc<T, RT, UT>(sda, RP, r0, sWg, DH, a0, C3, dh1);
+        if (DIM == 2 || k > 0) mm_acc<T, RT, UT, 8>(sda, RP, r0, sWg, DH, a0, C3, dh1);
       }
       if (DIM == 1) {
 #pragma unroll
@@ -308,8 +308,8 @@ k_jac_bwd(const BwdArgs<T> A) {
         for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int uu = 0; uu < UT; ++uu) { dhh[i][uu] = T(0); dhv[i][uu] = T(0); }
-        mm_acc<T, RT, UT>(sdp, RP, r0, sU12, 2 * DH, a0, DH, dhh);
-        mm_acc<T, RT, UT>(sdp, RP, r0, sU12 + DH, 2 * DH, a0, DH, dhv);
+        mm_acc<T, RT, UT, 8>(sdp, RP, r0, sU12, 2 * DH, a0, DH, dhh);
+        mm_acc<T, RT, UT, 8>(sdp, RP, r0, sU12 + DH, 2 * DH, a0, DH, dhv);
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
           const int g = srow[r0 + i];

@@ -50,12 +50,13 @@ __device__ __forceinline__ void load_run(const T *__restrict__ p, T (&v)[n]) {
   }
 }
 
-// acc[i][j] += sum_k At[k*lda + r0 + i] * B[k*ldb + c0 + j]
-template <typename T, int RT, int CT>
+// acc[i][j] += sum_k At[k*lda + r0 + i] * B[k*ldb + c0 + j]; U: k steps
+// unrolled (loads of U steps in flight; the sums keep their order)
+template <typename T, int RT, int CT, int U = 2>
 __device__ __forceinline__ void mm_acc(const T *__restrict__ At, int lda, int r0,
                                        const T *__restrict__ B, int ldb, int c0,
                                        int K, T (&acc)[RT][CT]) {
-#pragma unroll 2
+#pragma unroll U
   for (int k = 0; k < K; ++k) {
     T a[RT], b[CT];
     load_run<T, RT>(At + k * lda + r0, a);
@@ -80,11 +81,11 @@ __device__ __forceinline__ int ssw(int a, int r) {
 }
 
 // mm_acc with the A operand in the swizzled [k][r] layout.
-template <typename T, int RT, int CT, int R, int UT>
+template <typename T, int RT, int CT, int R, int UT, int U = 2>
 __device__ __forceinline__ void mm_acc_s(const T *__restrict__ At, int r0,
                                          const T *__restrict__ B, int ldb, int c0,
                                          int K, T (&acc)[RT][CT]) {
-#pragma unroll 2
+#pragma unroll U
   for (int k = 0; k < K; ++k) {
     T a[RT], b[CT];
     load_run<T, RT>(At + ssw<R, RT, UT>(k, r0), a);
@@ -176,6 +177,9 @@ k_forward(const FwdArgs<T> A) {
   constexpr int NTH = UG * RG;
   constexpr int DIN = DIM == 2 ? 4 : 2;
   constexpr int C3 = 3 * DH;
+  // k steps of the per-site products unrolled: loads of several steps in
+  // flight (fewer where the accumulators already fill the registers)
+  constexpr int MMU = (RT * 3 * UT <= 12) ? 8 : 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sxw = reinterpret_cast<T *>(smraw);
   T *sbias = sxw + DIN * C3;
@@ -349,8 +353,8 @@ k_forward(const FwdArgs<T> A) {
         for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int j2 = 0; j2 < UT; ++j2) acc1[i][j2] = T(0);
-        if (hor_ok) mm_acc_s<T, RT, UT, R, UT>(hcur, r0, sU12T, DH, a0, DH, acc1);
-        if (ver >= 0) mm_acc_s<T, RT, UT, R, UT>(shv, r0, sU12T + DH * DH, DH, a0, DH, acc1);
+        if (hor_ok) mm_acc_s<T, RT, UT, R, UT, MMU>(hcur, r0, sU12T, DH, a0, DH, acc1);
+        if (ver >= 0) mm_acc_s<T, RT, UT, R, UT, MMU>(shv, r0, sU12T + DH * DH, DH, a0, DH, acc1);
 #pragma unroll
         for (int i = 0; i < RT; ++i)
 #pragma unroll
@@ -397,7 +401,7 @@ k_forward(const FwdArgs<T> A) {
             for (int j = 0; j < 3; ++j) acc[0][3 * uu + j] = (T)sgate[(r0 * DH + a0 + uu) * 3 + j];
         }
       } else {
-        if (DIM == 2 || k > 0) mm_acc_s<T, RT, 3 * UT, R, UT>(Ag, r0, sWgT, C3, 3 * a0, DH, acc);
+        if (DIM == 2 || k > 0) mm_acc_s<T, RT, 3 * UT, R, UT, MMU>(Ag, r0, sWgT, C3, 3 * a0, DH, acc);
       }
 
       // epilogue: GRU cell (App. A), partial heads, then the row's head on
