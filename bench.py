@@ -68,6 +68,11 @@ def parse():
     p.add_argument("--spectrum-steps", type=int, default=64,
                    help="Lanczos steps of the conditioning diagnostics")
     p.add_argument("--no-graph", action="store_true", help="launch every kernel eagerly")
+    p.add_argument("--instances", default="",
+                   help="batched16: only these instances (comma-separated names; for profiles)")
+    p.add_argument("--grouped", type=int, default=-1,
+                   help="batched16: grouped stages after the autotuner (nqs_batch_set_grouped "
+                        "mask; -1: the autotuner's choice)")
     p.add_argument("--train-steps", type=int, default=10000,
                    help="train:<workload>: minSR steps of the training run")
     p.add_argument("--train-eta0", type=float, default=None,
@@ -467,6 +472,8 @@ def run_reference(args):
     from paper_2608_18065_b300.inputs import batched_instances, workloads
     if args.workload == "batched16":
         insts = batched_instances()
+        if args.instances:
+            insts = [w for w in insts if w.name in args.instances.split(",")]
         cfg = workload_config(args, insts=insts)
         unit = "batched steps/s"
         nsub = [min(w.hp.ns, max(4, O.num_threads())) for w in insts]
@@ -809,6 +816,11 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     insts = batched_instances()
+    if args.instances:
+        keep = args.instances.split(",")
+        insts = [w for w in insts if w.name in keep]
+        if len(insts) != len(keep):
+            raise SystemExit(f"--instances: unknown names in {args.instances}")
     n = len(insts)
     K, Wu = args.steps, args.warmup
 
@@ -827,6 +839,8 @@ def run_batched(args):
     t0 = time.perf_counter()
     tune_ms = b.autotune(thd, hps, 0)
     tune_s = time.perf_counter() - t0
+    if args.grouped >= 0:
+        b.set_grouped(args.grouped)
     tuning = [c.tuning() for c in ctxs]
     stats = b.new_stats()
     for t in range(Wu):
