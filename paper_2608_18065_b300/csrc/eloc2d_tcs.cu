@@ -26,6 +26,14 @@
 // puts U2 h of those states into the column buffer.  K is padded to two 64-wide atoms; the
 // padded k-steps are not issued.
 //
+// The A operand of both products (h_{k-1}, then h', as BF16 hi and lo
+// planes, two K per 32-bit column) lives in tensor memory beside the
+// accumulators, written by the compute threads with tcgen05.st (a thread's
+// row is its lane), so that the MMAs read only B from shared memory and the
+// ring holds six slots at d_h 128, eight at 96 (measured: local energies of
+// the 12 x 12 d_h 128 instance 88.5 -> 85.3 ms, of the d_h 96 one 22.2 ->
+// 21.0 ms against A planes in shared memory with four and five slots).
+//
 // Warp roles: 4 d_h / UT compute warps (thread (quarter q, part p) owns row
 // 32 q + lane, its tensor-memory lane, and units UT p .. UT p + UT - 1; UT =
 // 64 at d_h = 128, 32 at 96, so that no register spills), one MMA
@@ -66,11 +74,12 @@ struct Tcs {
   static constexpr int SB1 = N1 * 128, SB2 = N2 * 128;    // stage bytes (one atom, one plane)
   static constexpr int NS1 = 2 * NA, NS2 = NCH * 2 * NA;  // stages per product
   static constexpr int SLOT = SB1 > SB2 ? SB1 : SB2;
-  static constexpr int NSLOT = DH == 128 ? 4 : 5;
-  static constexpr int ATOM = TR * 128;             // one K atom of the 128-row A tile
+  static constexpr int NSLOT = DH == 128 ? 6 : 8;
   static constexpr int TS = 3 * DH + 4;             // bias / input table row stride (floats)
-  static constexpr int OFF_S = 0;                   // A planes: hi atoms, then lo atoms
-  static constexpr int OFF_RING = OFF_S + 2 * NA * ATOM;
+  // tensor memory: accumulators in columns [0, 3 d_h), the A operand (BF16
+  // hi, lo planes, two K per column) in [TA_HI, TA_HI + 64), [TA_LO, TA_LO + 64)
+  static constexpr int TA_HI = 384, TA_LO = TA_HI + 64;
+  static constexpr int OFF_RING = 0;
   static constexpr int OFF_TAB = OFF_RING + NSLOT * SLOT;  // float [9][TS]
   static constexpr int OFF_BH = OFF_TAB + 9 * TS * 4;      // float [DH]: b_h
   static constexpr int OFF_HEAD = OFF_BH + DH * 4;         // float [4][DH]: head rows
@@ -85,10 +94,11 @@ struct Tcs {
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;      // int tile[2], abort, tmem base
   static constexpr size_t SMEM = 1024 + OFF_MISC + 32;
   static constexpr int IMG = NS1 * SB1 + NS2 * SB2;        // weight image bytes
-  static_assert(OFF_RING % 1024 == 0 && SLOT % 1024 == 0 && ATOM % 1024 == 0, "atom alignment");
+  static_assert(OFF_RING % 1024 == 0 && SLOT % 1024 == 0, "atom alignment");
   static_assert(OFF_ZX % 16 == 0 && OFF_BAR % 8 == 0, "vector and barrier alignment");
   static_assert(SMEM <= 227 * 1024, "one CTA per SM");
-  static_assert(3 * DH <= 512 && N1 <= 256 && N2 <= 256 && N2 % 16 == 0, "MMA shapes, TMEM");
+  static_assert(3 * DH <= TA_HI && N1 <= 256 && N2 <= 256 && N2 % 16 == 0 && DH <= 128,
+                "MMA shapes, TMEM");
 };
 
 __device__ __forceinline__ uint32_t pack2(float x0, float x1) {
@@ -99,10 +109,12 @@ __device__ __forceinline__ uint32_t pack2(float x0, float x1) {
 __device__ __forceinline__ float sigm_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float tanh_f(float x) { return 2.0f * sigm_f(2.0f * x) - 1.0f; }
 
-// BF16 hi/lo planes of units k0 .. k0 + 7 of row `row`; k0 is the unit index,
-// which lands in K atom k0 / 64 (the lo plane sits NA atoms after the hi one).
+// BF16 hi/lo planes of units k0 .. k0 + 7 (k0 % 8 == 0, the same in the
+// whole warp) of this thread's row into the A operand in tensor memory
+// (`lanes`: the warp's lane quarter); columns k0 / 2 .. k0 / 2 + 3 of each
+// plane.  The MMA reads them after tmem_wait_st and the arrival on a.
 template <int DH>
-__device__ __forceinline__ void planes8(unsigned char *hi, int row, int k0, const float *h) {
+__device__ __forceinline__ void planes8(uint32_t lanes, int k0, const float *h) {
   uint32_t hp[4], lp[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -110,10 +122,8 @@ __device__ __forceinline__ void planes8(unsigned char *hi, int row, int k0, cons
     hp[q] = pack2(x0, x1);
     lp[q] = pack2(x0 - __uint_as_float(hp[q] << 16), x1 - __uint_as_float(hp[q] & 0xffff0000u));
   }
-  const uint32_t off = (uint32_t)(k0 >> 6) * Tcs<DH>::ATOM + sw128_off(row, k0 & 63);
-  *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-  *reinterpret_cast<uint4 *>(hi + Tcs<DH>::NA * Tcs<DH>::ATOM + off) =
-      make_uint4(lp[0], lp[1], lp[2], lp[3]);
+  tmem_st4(lanes + (uint32_t)(Tcs<DH>::TA_HI + (k0 >> 1)), hp);
+  tmem_st4(lanes + (uint32_t)(Tcs<DH>::TA_LO + (k0 >> 1)), lp);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
@@ -169,7 +179,6 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
   extern __shared__ __align__(1024) unsigned char eraw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(eraw) + 1023) & ~uintptr_t(1023));
-  unsigned char *Sh = sm + C::OFF_S;
   unsigned char *ring = sm + C::OFF_RING;
   float *tab = reinterpret_cast<float *>(sm + C::OFF_TAB);
   float *sbh = reinterpret_cast<float *>(sm + C::OFF_BH);
@@ -271,7 +280,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t id1 = idesc_bf16(C::TR, C::N1), id2 = idesc_bf16(C::TR, C::N2);
-      const uint32_t aH = smem_u32(Sh), aL = aH + C::NA * C::ATOM;
+      const uint32_t aH = tmem + (uint32_t)C::TA_HI, aL = tmem + (uint32_t)C::TA_LO;
       uint32_t q = 0, pa = 0;
       bool stop = false;
       for (int it = 0; !stop; ++it) {
@@ -293,17 +302,19 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
               tc_fence_after();
               const int at = (si >> 1) % C::NA, plane = si & 1, chunk = si / (2 * C::NA);
               const uint64_t bd = sw128_desc(smem_u32(ring + sl * C::SLOT));
-              const uint64_t ah = sw128_desc(aH + at * C::ATOM), al = sw128_desc(aL + at * C::ATOM);
+              const uint32_t ah = aH + (uint32_t)(32 * at), al = aL + (uint32_t)(32 * at);
               const uint32_t d = prod == 0 ? tmem : tmem + (uint32_t)(chunk * C::N2);
               const uint32_t idn = prod == 0 ? id1 : id2;
               const int ks = at == C::NA - 1 ? C::KS_LAST : 4;
               for (int kk = 0; kk < ks; ++kk) {
+                // B: 16 K = 32 bytes along the swizzled row; A: 8 columns
                 const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                const uint32_t ac = (uint32_t)(8 * kk);
                 if (plane == 0) {
-                  mma_bf16(d, ah + adv, bd + adv, idn, (at == 0 && kk == 0) ? 0u : 1u);
-                  mma_bf16(d, al + adv, bd + adv, idn, 1u);
+                  mma_bf16_ts(d, ah + ac, bd + adv, idn, (at == 0 && kk == 0) ? 0u : 1u);
+                  mma_bf16_ts(d, al + ac, bd + adv, idn, 1u);
                 } else {
-                  mma_bf16(d, ah + adv, bd + adv, idn, 1u);
+                  mma_bf16_ts(d, ah + ac, bd + adv, idn, 1u);
                 }
               }
               mma_commit(bar(C::B_EMPTY + sl));
@@ -343,6 +354,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
     uint32_t na = 0, pd1 = 0, pd2 = 0, pz = 0;  // arrivals on a; phases of d1, d2, z waited
     bool ok = true;
     auto arrive_a = [&]() {
+      tmem_wait_st();  // this thread's A-operand stores have landed
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(bar(C::B_A));
@@ -393,7 +405,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
             const float4 v = (valid && k >= 0) ? __ldcg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
             h8[4 * q] = v.x; h8[4 * q + 1] = v.y; h8[4 * q + 2] = v.z; h8[4 * q + 3] = v.w;
           }
-          planes8<DH>(Sh, row, unit_of(g8), h8);
+          planes8<DH>(lanes, unit_of(g8), h8);
         }
       };
       // Y = U2 h (columns DH + units) of the last first product into the
@@ -555,7 +567,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
               dst[0] = make_float4(y[cu][0], y[cu][1], y[cu][2], y[cu][3]);
               dst[1] = make_float4(y[cu][4], y[cu][5], y[cu][6], y[cu][7]);
             }
-            planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
+            planes8<DH>(lanes, unit_of(g8), hp + 8 * g8);
           }
         }
         arrive_a();  // A = h'
@@ -632,7 +644,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
             !wait_ab(bar(C::B_D2 + C::NCH - 1), pd2 & 1, s_abort, lim)) { ok = false; break; }
         ++pd2;
 #pragma unroll
-        for (int g8 = 0; g8 < G8; ++g8) planes8<DH>(Sh, row, unit_of(g8), hp + 8 * g8);
+        for (int g8 = 0; g8 < G8; ++g8) planes8<DH>(lanes, unit_of(g8), hp + 8 * g8);
         if (part > 0) {
           zx[(part - 1) * C::TR + row] = make_float4(z0, z1, z2, z3);
         } else {
