@@ -991,6 +991,7 @@ def run_batched(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int((launches - saved) * K),
                 "clocks": clk, "cuda_graph": batch_graph, "grouped_stages": {"solve": bool(batch_grouped & 1), "eloc": bool(batch_grouped & 2)},
+                "eloc_share_eighths": b.eloc_share(),
                 "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
                 "fp64_path": fp64, "matched_energy": matched, "per_config": per_config,
                 "errors_vs_oracle": load_errors(),

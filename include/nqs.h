@@ -393,17 +393,27 @@ nqs_status nqs_batch_get_concurrency(const nqs_batch *b, int *streams);
 nqs_status nqs_batch_set_grouped(nqs_batch *b, int stages);
 nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *stages);
 
+/* Share of its grid (eighths, 1..8; default 8) that each instance's
+ * local-energy engine takes inside a batched step (whole steps per stream;
+ * the grouped engine launch splits all SMs itself): an engine CTA fills its
+ * SM's shared and tensor memory, so the SMs it leaves free serve the other
+ * instances' kernels.  Steps of a context outside the batch use the whole
+ * grid.  Results do not depend on the grid.  (Measured on the headline
+ * batch: 7/8 and 3/4 were no faster than the whole grid, so the batch
+ * autotuner leaves it at 8.) */
+nqs_status nqs_batch_set_eloc_share(nqs_batch *b, int eighths);
+nqs_status nqs_batch_get_eloc_share(const nqs_batch *b, int *eighths);
+
 /* nqs_autotune for every instance, then, by timing whole batched steps on
  * the workspace copies of theta (best of two for the concurrency and the
- * solve SMs; candidates in turn, median of three, for the grouped stages and
- * the graph): the concurrency,
- * the fraction of the SMs each instance's cooperative solve takes, which
- * stages run grouped (nqs_batch_set_grouped: none, the solves, the solves
- * and the local-energy engines), and, if
- * graphs are enabled (nqs_batch_set_graph), whether a graph replay or the
- * eager launches are faster (graphs stay off when they are not).  The
- * fastest batched step time goes to *step_ms (may be NULL).  Synchronous;
- * the callers' thetas are not modified. */
+ * solve SMs; candidates in turn and the median of five or three rounds for
+ * the grouped stages and the graph): the concurrency, the fraction of the
+ * SMs each instance's cooperative solve takes, which stages run grouped
+ * (nqs_batch_set_grouped: none, the solves, the solves and the
+ * local-energy engines), and, if graphs are enabled (nqs_batch_set_graph),
+ * whether a graph replay or the eager launches are faster (graphs stay off
+ * when they are not).  The fastest batched step time goes to *step_ms (may
+ * be NULL).  Synchronous; the callers' thetas are not modified. */
 nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas,
                               const nqs_step_hparams *hps, int flags,
                               double *step_ms, void *stream);

@@ -91,6 +91,9 @@ struct nqs_ctx {
   // engine, with the arguments left in eloc_args
   int phase = 0, in_group = 0, in_eloc_group = 0;
   Eloc2dTcArgs eloc_args{};
+  // batched steps: the local-energy engine takes this many eighths of its
+  // grid (the rest of the SMs stays free for the other instances' kernels)
+  int eloc_eighths = 8;
 };
 
 constexpr int STEP_ALL = 0, STEP_PRE_A = 1, STEP_PRE_B = 2, STEP_POST = 3;
@@ -243,7 +246,8 @@ nqs_status need_ws(nqs_ctx *c) { return c->ws ? NQS_OK : NQS_ERR_WORKSPACE; }
 // Tuned launch shapes apply to the sample count they were measured for.
 bool tuned(const nqs_ctx *c) { return c->tuned_ns > 0 && c->tuned_ns == c->cur_ns; }
 int eloc_grid_cap(const nqs_ctx *c, int dflt) {
-  return tuned(c) && c->t_eloc_grid > 0 ? std::min(c->t_eloc_grid, dflt) : dflt;
+  const int g = tuned(c) && c->t_eloc_grid > 0 ? std::min(c->t_eloc_grid, dflt) : dflt;
+  return std::max(1, g * c->eloc_eighths / 8);
 }
 int gram_splits(const nqs_ctx *c) { return tuned(c) ? c->t_gram_splits : 0; }
 // grid of the cooperative solve: the tuned value (at most two CTAs per SM,
@@ -1905,10 +1909,11 @@ struct nqs_batch {
   // by stage: GROUP_SOLVE, the FP32 solves of all instances in one launch;
   // GROUP_ELOC, the streamed local-energy engines in one launch per hidden size
   int grouped = 0;
+  int eloc_eighths = 8;  // the local-energy engines' share of their grids
   struct Key {
     std::vector<const void *> ptr;  // theta, momentum, stats of every instance
     std::vector<nqs_step_hparams> hp;
-    int conc, grouped;
+    int conc, grouped, eloc_eighths;
   } key;
   std::vector<int64_t> gnext;
 };
@@ -2103,7 +2108,9 @@ nqs_status batch_issue_grouped(nqs_batch *b, double *const *th, double *const *m
   auto issue = [&](int i, int ph) {
     nqs_ctx *c = b->ctx[i];
     c->phase = ph;
+    c->eloc_eighths = b->eloc_eighths;
     const nqs_status r = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, b->st[i % q]);
+    c->eloc_eighths = 8;
     c->phase = STEP_ALL;
     return r;
   };
@@ -2177,7 +2184,9 @@ nqs_status batch_issue(nqs_batch *b, double *const *th, double *const *mo,
     }
     c->solve_wait = i > 0 ? b->solved[i - 1] : nullptr;
     c->solve_rec = b->solved[i];
+    c->eloc_eighths = b->eloc_eighths;
     s = step_body(c, th[i], mo[i], &hps[i], stats[i], nullptr, st);
+    c->eloc_eighths = 8;
     c->solve_wait = c->solve_rec = nullptr;
   }
   for (int j = 0; j < q; ++j) {
@@ -2214,8 +2223,9 @@ nqs_status batch_step(nqs_batch *b, double *const *th, double *const *mo,
     }
     k.conc = batch_conc(b);
     k.grouped = b->grouped;
+    k.eloc_eighths = b->eloc_eighths;
     bool same = b->gexec && k.ptr == b->key.ptr && k.conc == b->key.conc &&
-                k.grouped == b->key.grouped;
+                k.grouped == b->key.grouped && k.eloc_eighths == b->key.eloc_eighths;
     for (int i = 0; same && i < n; ++i)
       same = std::memcmp(&k.hp[i], &b->key.hp[i], sizeof(nqs_step_hparams)) == 0;
     if (!same) {
@@ -2324,6 +2334,18 @@ nqs_status nqs_batch_set_grouped(nqs_batch *b, int stages) {
   return NQS_OK;
 }
 
+nqs_status nqs_batch_set_eloc_share(nqs_batch *b, int eighths) {
+  if (!b || eighths < 1 || eighths > 8) return NQS_ERR_ARG;
+  b->eloc_eighths = eighths;
+  return NQS_OK;
+}
+
+nqs_status nqs_batch_get_eloc_share(const nqs_batch *b, int *eighths) {
+  if (!b || !eighths) return NQS_ERR_ARG;
+  *eighths = b->eloc_eighths;
+  return NQS_OK;
+}
+
 nqs_status nqs_batch_get_grouped(const nqs_batch *b, int *stages) {
   if (!b || !stages) return NQS_ERR_ARG;
   *stages = b->grouped;
@@ -2415,7 +2437,7 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
   }
   // (4) by stage (the FP32 solves, and the streamed local-energy engines,
   // of all instances in grouped launches) or whole steps per stream: the
-  // candidates in turn, three rounds, the median of each (consecutive
+  // candidates in turn, five rounds, the median of each (consecutive
   // batched steps of one setting vary by several per cent with the clocks
   // and the power cap, so a best-of-two favours the noisier setting)
   auto reset = [&] {
@@ -2434,7 +2456,7 @@ nqs_status nqs_batch_autotune(nqs_batch *b, double *const *thetas, const nqs_ste
   if (s == NQS_OK) {
     const int cands[3] = {0, GROUP_SOLVE, GROUP_SOLVE | GROUP_ELOC};
     std::vector<double> t[3];
-    for (int r = 0; r < 3 && s == NQS_OK; ++r)
+    for (int r = 0; r < 5 && s == NQS_OK; ++r)
       for (int j = 0; j < 3 && s == NQS_OK; ++j) {
         b->grouped = cands[j];
         double ms = 0;

@@ -67,7 +67,7 @@ SYMBOLS = ["nqs_create", "nqs_destroy", "nqs_param_count", "nqs_workspace_size",
            "nqs_set_damping", "nqs_spectrum", "nqs_shard_forward", "nqs_shard_center",
            "nqs_shard_solve", "nqs_shard_apply", "nqs_test_wait_timeout", "nqs_adam_step",
            "nqs_energy_scan", "nqs_set_solve_form", "nqs_set_sampler", "nqs_batch_set_grouped",
-           "nqs_batch_get_grouped",
+           "nqs_batch_get_grouped", "nqs_batch_set_eloc_share", "nqs_batch_get_eloc_share",
            "nqs_stage_name", "nqs_last_cuda_error", "nqs_status_string"]
 TUNE_FORCE = 1
 
@@ -486,6 +486,16 @@ class Batch:
     def grouped(self):
         v = C.c_int()
         _check(lib().nqs_batch_get_grouped(self._h, C.byref(v)))
+        return v.value
+
+    def set_eloc_share(self, eighths):
+        """Eighths of its grid each instance's local-energy engine takes in
+        a batched step (nqs_batch_set_eloc_share)."""
+        _check(lib().nqs_batch_set_eloc_share(self._h, int(eighths)))
+
+    def eloc_share(self):
+        v = C.c_int()
+        _check(lib().nqs_batch_get_eloc_share(self._h, C.byref(v)))
         return v.value
 
 

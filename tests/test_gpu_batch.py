@@ -293,3 +293,26 @@ def test_grouped_stages_equal_solo(graph, stages):
             ((len(eloc_dh) - len(set(eloc_dh))) if stages & 2 else 0)
         assert sum(c.launch_count() for c in ctxs) - n0 == solo - saved * steps
     b.close()
+
+
+def test_batched_eloc_share_equals_solo():
+    """Local-energy engines on 6/8 of their grids inside the batch (the
+    other SMs free for the other instances' kernels): every instance's step
+    is still the one it takes alone, bit for bit, since a tile's local
+    energies do not depend on the CTA that runs it."""
+    steps = 2
+    th0, mo0, st0 = _solo(INSTANCES, steps)
+    ctxs, th, mo, hps = _setup()
+    b = nqs.Batch(ctxs)
+    b.set_eloc_share(6)
+    assert b.eloc_share() == 6
+    stats = b.new_stats()
+    for k in range(steps):
+        b.step(th, mo, hps, k, stats)
+    torch.cuda.synchronize()
+    for i in range(len(INSTANCES)):
+        assert torch.equal(th[i], th0[i]), i
+        assert torch.equal(stats[i], st0[i]), i
+    with pytest.raises(nqs.NqsError):
+        b.set_eloc_share(9)
+    b.close()
