@@ -1989,7 +1989,9 @@ nqs_status batch_group_solve(nqs_batch *b, const std::vector<int> &idx,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_blk_group, BKB_THREADS, smem));
-  const int S = std::max(per, 1) * b->ctx[idx[0]]->rd.sm_count;
+  if (per < 1) return NQS_ERR_UNSUPPORTED;
+  // one CTA per SM at most: an instance's partial norms are sized for that
+  const int S = b->ctx[idx[0]]->rd.sm_count;
   const int chunk = std::min<int>(BLK_GROUP_MAX, S / 2);
   for (size_t i0 = 0; i0 < idx.size(); i0 += chunk) {
     const int k = (int)std::min<size_t>(chunk, idx.size() - i0);
