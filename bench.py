@@ -863,6 +863,7 @@ def run_batched(args):
     clk = clocks.stop()
     batch_graph = bool(b.graph_active())
     batch_grouped = b.grouped()
+    batch_eloc_share = b.eloc_share()
     # by stage, the FP32 solves of the mixed instances with R % 4 == 0 and
     # R >= 256 are one launch (bit 1), the streamed local-energy engines one
     # launch per hidden size (bit 2)
@@ -991,7 +992,7 @@ def run_batched(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int((launches - saved) * K),
                 "clocks": clk, "cuda_graph": batch_graph, "grouped_stages": {"solve": bool(batch_grouped & 1), "eloc": bool(batch_grouped & 2)},
-                "eloc_share_eighths": b.eloc_share(),
+                "eloc_share_eighths": batch_eloc_share,
                 "autotune": {"seconds": tune_s, "best_batched_ms": tune_ms},
                 "fp64_path": fp64, "matched_energy": matched, "per_config": per_config,
                 "errors_vs_oracle": load_errors(),
