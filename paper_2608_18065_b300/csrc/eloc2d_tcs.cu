@@ -416,11 +416,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
           float y[8];
           tmem_ld8(lanes + (uint32_t)(DH + unit_of(g8)), y);
           tmem_wait_ld();
-          if (valid) {
-            float4 *dst = reinterpret_cast<float4 *>(cb + col * DH + unit_of(g8));
-            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
-            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
-          }
+          if (valid) st_global_v8(cb + col * DH + unit_of(g8), y);
         }
       };
 
@@ -562,11 +558,7 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
               const float v = ver == k - 1 ? y[cu][i] : hp[8 * g8 + i];
               hp[8 * g8 + i] = hor ? x[cu][i] + v : v;
             }
-            if (valid && k >= 1) {
-              float4 *dst = reinterpret_cast<float4 *>(cb + colof(k - 1) * DH + unit_of(g8));
-              dst[0] = make_float4(y[cu][0], y[cu][1], y[cu][2], y[cu][3]);
-              dst[1] = make_float4(y[cu][4], y[cu][5], y[cu][6], y[cu][7]);
-            }
+            if (valid && k >= 1) st_global_v8(cb + colof(k - 1) * DH + unit_of(g8), y[cu]);
             planes8<DH>(lanes, unit_of(g8), hp + 8 * g8);
           }
         }
@@ -624,18 +616,16 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
             }
           }
           if (SMP && valid) {  // gate cache (u, r, c, W_h h' + b_h, h') and h_k
-            auto st8 = [&](float *dst, const float *v) {
-              reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-              reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-            };
+            // (rows are 5 d_h and d_h floats, units in groups of 8: every
+            // store starts on a 32-byte boundary)
             if (grow) {
-              st8(grow + ug, su);
-              st8(grow + DH + ug, sr);
-              st8(grow + 2 * DH + ug, sc);
-              st8(grow + 3 * DH + ug, gg);
-              st8(grow + 4 * DH + ug, gu);
+              st_global_v8(grow + ug, su);
+              st_global_v8(grow + DH + ug, sr);
+              st_global_v8(grow + 2 * DH + ug, sc);
+              st_global_v8(grow + 3 * DH + ug, gg);
+              st_global_v8(grow + 4 * DH + ug, gu);
             }
-            st8(a.hcache_out + ((int64_t)s * N + k) * DH + ug, hp + 8 * g8);
+            st_global_v8(a.hcache_out + ((int64_t)s * N + k) * DH + ug, hp + 8 * g8);
           }
         }
         if (!dok) { ok = false; break; }
