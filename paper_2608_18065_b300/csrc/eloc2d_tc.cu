@@ -406,11 +406,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_eloc2d_tc(const Eloc2dTcArgs a) 
           }
         }
         planes8(Sh, Sl, row, UH * half + 8 * g8, h8);
-        if (valid) {
-          float4 *dst = reinterpret_cast<float4 *>(cb + col * DH + 8 * g8);
-          dst[0] = make_float4(h8[0], h8[1], h8[2], h8[3]);
-          dst[1] = make_float4(h8[4], h8[5], h8[6], h8[7]);
-        }
+        if (valid) st_global_v8(cb + col * DH + 8 * g8, h8);  // 32-byte aligned: whole sectors
         if (turn) {  // the next site's vertical input is this state
           vs[2 * g8] = valid ? make_float4(h8[0], h8[1], h8[2], h8[3]) : make_float4(0.f, 0.f, 0.f, 0.f);
           vs[2 * g8 + 1] = valid ? make_float4(h8[4], h8[5], h8[6], h8[7]) : make_float4(0.f, 0.f, 0.f, 0.f);

@@ -398,12 +398,12 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
       auto cached_planes = [&](int k) {
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
-          const float4 *src = reinterpret_cast<const float4 *>(hrow + (int64_t)k * DH + unit_of(g8));
           float h8[8];
+          if (valid && k >= 0) {
+            ld_global_cg_v8(hrow + (int64_t)k * DH + unit_of(g8), h8);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float4 v = (valid && k >= 0) ? __ldcg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            h8[4 * q] = v.x; h8[4 * q + 1] = v.y; h8[4 * q + 2] = v.z; h8[4 * q + 3] = v.w;
+            for (int i = 0; i < 8; ++i) h8[i] = 0.f;
           }
           planes8<DH>(lanes, unit_of(g8), h8);
         }
@@ -509,13 +509,15 @@ __device__ __forceinline__ void tcs_body(const Eloc2dTcArgs &a, const int cta) {
         const bool vbuf = valid && ver >= 0 && ver != k - 1;
 #pragma unroll
         for (int g8 = 0; g8 < G8; ++g8) {
-          const float4 *src = reinterpret_cast<const float4 *>(cb + col * DH + unit_of(g8));
+          float v[8];
+          if (vbuf) {
+            ld_global_v8(cb + col * DH + unit_of(g8), v);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float4 v = vbuf ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float *h = hp + 8 * g8 + 4 * q;
-            h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+            for (int i = 0; i < 8; ++i) v[i] = 0.f;
           }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) hp[8 * g8 + i] = v[i];
         }
         // next site's raw spins (flipped when used) and this site's cached terms
         int r_next = 0, r_vnext = 0, k_v = -1;

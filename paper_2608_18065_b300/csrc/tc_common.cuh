@@ -109,6 +109,21 @@ __device__ __forceinline__ void st_global_v8(float *dst, const float *v) {
                : "memory");
 }
 
+// Eight consecutive floats from global memory in one 32-byte load (src
+// 32-byte aligned); _cg: cached in L2 only (data another CTA wrote).
+__device__ __forceinline__ void ld_global_v8(const float *src, float (&v)[8]) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(src));
+}
+__device__ __forceinline__ void ld_global_cg_v8(const float *src, float (&v)[8]) {
+  asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(src));
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
