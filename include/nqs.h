@@ -410,7 +410,8 @@ nqs_status nqs_batch_get_eloc_share(const nqs_batch *b, int *eighths);
  * the grouped stages and the graph): the concurrency, the fraction of the
  * SMs each instance's cooperative solve takes, which stages run grouped
  * (nqs_batch_set_grouped: none, the solves, the solves and the
- * local-energy engines), and, if graphs are enabled (nqs_batch_set_graph),
+ * local-energy engines; the fewest within 2 % of the fastest), and, if
+ * graphs are enabled (nqs_batch_set_graph),
  * whether a graph replay or the eager launches are faster (graphs stay off
  * when they are not).  The fastest batched step time goes to *step_ms (may
  * be NULL).  Synchronous; the callers' thetas are not modified. */
